@@ -1,0 +1,335 @@
+"""Throughput of the full HPM force solve (tree build + all solve stages).
+
+Default workload: 2^21 particles from a truncated Plummer sphere, adaptive
+tree (> 32 splits, depth <= 12), 4^3 gridlets, eps = 1e-4, on one GPU.
+One step = hpm_build_tree + hpm_solve on device-resident inputs. Prints one
+JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the paper's FFT algorithm, plain
+C with OpenMP) on the host cores instead, on a bounded sample of the same
+workload. Multi-GPU runs (torchrun) solve one independent problem per rank
+(replicas: the method has no exchange between problems).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1906_10734_gb300 import inputs as I  # noqa: E402
+
+METRIC = "particles/s for full HPM force solve at stated force error; p50/p99 latency"
+UNIT = "particles/s"
+FP32_LANES_PER_SM = 128
+SM_COUNT_GB300 = 152
+
+
+def m2l_flops_per_target(ng: int) -> float:
+    """Nominal FFT-convolution work per target: forward r2c + inverse c2r of P^3 points at
+    2.5 n log2 n each, plus the real Green product on the half spectrum (P = 8 Ng)."""
+    P = 8 * ng
+    return 5.0 * P ** 3 * math.log2(P ** 3) + 2.0 * P * P * (P // 2 + 1)
+
+
+def workload_for(rank: int, n_override: int | None = None) -> I.Workload:
+    n = n_override or (1 << 21)
+    w = I.plummer_2m_adaptive(ng=4, n=n) if rank == 0 else I.Workload(
+        f"plummer{n}_adaptive32_depth12_rank{rank}", I.plummer_sphere(n, 2 + 1000 * rank),
+        I.equal_masses(n), max_depth=12, leaf_max=32, ng=4, eps=1e-4)
+    return w
+
+
+def config_of(n: int, max_depth=12, leaf_max=32, ng=4, eps=1e-4, extra=None) -> dict:
+    c = {"workload": f"plummer sphere N={n} (a=0.05, r<=0.5), adaptive tree >{leaf_max}/leaf, "
+                     f"depth<={max_depth}, gridlet {ng}^3, eps={eps:g}",
+         "n": n, "max_depth": max_depth, "leaf_max": leaf_max, "gridlet_order": ng, "eps": eps,
+         "stated_force_error": "FP32 solve within 1e-5 rel RMS of the FP64 HPM (parity tests)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for k, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(k)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def profile_traffic(kernel_src: str) -> float | None:
+    """DRAM bytes per full launch from the committed ncu summary, if it was taken on the
+    kernel source as it is now (its sha256 matches); else None."""
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.startswith("m2l_") or not fn.endswith(".md"):
+            continue
+        text = open(os.path.join(pdir, fn)).read()
+        m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+        m_tr = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+        if m_sha and m_tr and m_sha.group(1) == h:
+            return float(m_tr.group(1))
+    return None
+
+
+# ---------------------------------------------------------------------------
+def run_gpu(args) -> None:
+    import torch
+    import torch.distributed as dist
+    from paper_1906_10734_gb300 import hpm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_1906_10734_gb300 import build as B
+    B.build()
+
+    w = workload_for(rank, args.n)
+    stream = torch.cuda.current_stream(dev)
+    pos = torch.from_numpy(w.pos).to(dev)
+    mass = torch.from_numpy(w.mass).to(dev)
+    phi = torch.empty(w.n, dtype=torch.float32, device=dev)
+    acc = torch.empty((w.n, 3), dtype=torch.float32, device=dev)
+    plan = hpm.hpm_plan((0.0, 0.0, 0.0), 1.0, w.max_depth, w.ng, w.eps, w.leaf_max, flags=1)
+    l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step():
+        hpm.hpm_build_tree(plan, pos, w.n, stream)
+        hpm.hpm_solve(plan, pos, mass, phi, acc, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    info = hpm.hpm_get_lists_info(plan)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    ms_m2l, launches = [], 0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            l2_flush.fill_(k & 0xff)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            st = hpm.hpm_get_stats(plan)       # waits for this step's last event
+            ms_m2l.append(st["ms_m2l"])
+            launches += st["launches"]
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    clocks = clk.summary()
+
+    # end to end through the host-memory entry point: pinned inputs in, results out
+    hp = torch.from_numpy(w.pos).pin_memory()
+    hm = torch.from_numpy(w.mass).pin_memory()
+    hphi = torch.empty(w.n, dtype=torch.float32).pin_memory()
+    hacc = torch.empty((w.n, 3), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    hpm.hpm_solve_host(plan, hp.numpy(), hm.numpy(), hphi.numpy(), hacc.numpy(), stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        hpm.hpm_solve_host(plan, hp.numpy(), hm.numpy(), hphi.numpy(), hacc.numpy(), stream)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    hpm.hpm_destroy(plan)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    n_total = w.n * world
+    ms_per_step = total_ms / args.steps
+    value = n_total * args.steps / (total_ms / 1e3)
+    peaks = measured_peaks()
+    sm_mhz_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
+    m2l_ms = statistics.mean(ms_m2l)
+    flop = m2l_flops_per_target(w.ng) * info["n_targets"]
+    achieved = flop / (m2l_ms / 1e3) / 1e12
+    traffic = profile_traffic(os.path.join(ROOT, "paper_1906_10734_gb300", "csrc", "m2l.cu"))
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_of(w.n, w.max_depth, w.leaf_max, w.ng, w.eps, {"parallelism": "replicas" if world > 1 else "single",
+                                "l2": "flushed between steps (256 MiB write outside the timed events)",
+                                "cells": info["n_cells"], "targets": info["n_targets"],
+                                "leaves": info["n_leaves"], "boxes": info["n_boxes"],
+                                "depth_reached": info["depth_reached"]}),
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "min": min(step_ms), "max": max(step_ms)},
+        "e2e": {"value": n_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 32 * w.n,
+                "d2h_bytes_per_step": 16 * w.n, "api": "hpm_solve_host (pinned host buffers)"},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "source-to-target FFT convolution (k_m2l4)", "bound": "alu",
+                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": traffic, "ms_per_launch": m2l_ms, "launches_per_step": 1,
+                     "flop_per_target": m2l_flops_per_target(w.ng), "targets_per_launch": info["n_targets"],
+                     "peak_basis": f"{SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                   f"{sm_mhz_max:.0f} MHz (nominal FFMA rate)"},
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def oracle_step(n: int):
+    """One timed oracle solve on a reduced Plummer problem of the same recipe."""
+    import oracle as O
+    w = I.small_plummer(n, 2, leaf_max=32, max_depth=12, ng=4, eps=1e-4)
+    t0 = time.perf_counter()
+    tr = O.Tree(w.pos, max_depth=w.max_depth, leaf_max=w.leaf_max)
+    O.solve_fft(tr, w.mass, w.ng, w.eps)
+    return time.perf_counter() - t0, w.n
+
+
+def cpu_baseline(args) -> dict:
+    import oracle as O
+    n = args.cpu_sample
+    oracle_step(n // 8)                      # load and warm the library
+    times = [oracle_step(n)[0] for _ in range(2)]
+    t = min(times)
+    return {"value": n / t, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle, paper's FFT algorithm (solve_fft), Plummer N={n} same recipe "
+                      f"(adaptive >32, depth<=12, 4^3, eps=1e-4), best of 2, {t:.2f} s per solve"}
+
+
+def run_reference(args) -> None:
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    n = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_step(max(1024, n // 8))
+    times = []
+    for _ in range(args.steps):
+        dt, _ = oracle_step(n)
+        times.append(dt)
+    total = sum(times)
+    value = n * args.steps / total
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": config_of(args.n or (1 << 21), extra={
+               "sample": f"each step solves a Plummer N={n} problem of the same recipe on the host"}),
+           "latency_ms": {"p50": float(np.percentile(times, 50)) * 1e3,
+                          "p99": float(np.percentile(times, 99)) * 1e3},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                            "sample": f"FP64 oracle (paper's FFT algorithm), Plummer N={n} per step"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=None, help="particles per problem (default 2^21)")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 15)
+    ap.add_argument("--ref-sample", type=int, default=1 << 14)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

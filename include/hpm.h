@@ -1,0 +1,224 @@
+/*
+ * hpm.h - C ABI of a GB300 (sm_103a) solver for the Hierarchical
+ * Particle-Mesh fast multipole method (Gnedin 2019, "Hierarchical
+ * Particle-Mesh: an FFT-accelerated Fast Multipole Method").
+ *
+ * Problem (Sec. 1): N bodies in a cubic domain, gravity as potential and
+ * acceleration. The domain is the level-0 cell of a cubic oct-tree whose cells
+ * split into 8 children; the tree may be adaptive. The solve follows the
+ * paper's four steps (Sec. 1): leaf parameterisation by gridlets of effective
+ * masses (Sec. 2.2), child-to-parent transformation (Sec. 2.3),
+ * source-to-target transformation by one FFT convolution per target cell
+ * over its interaction zone (Sec. 2.1), parent-to-child transformation and
+ * evaluation (Sec. 2.4); the near zone is summed directly (Sec. 1, item 1).
+ *
+ * Kernel: g(r) = 1/sqrt(r^2 + eps^2) with G = 1 (eps = 0: Newtonian 1/r; the
+ * 1/(4 pi) of Eq. gf is not used). Outputs:
+ *   phi_i = -sum_{j != i} m_j g(|x_i - x_j|)   (self term excluded)
+ *   a_i   = -grad phi_i
+ * approximated by the method (exact for pairs in the near zone).
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are device pointers on the current CUDA device; h_*
+ *    pointers are host memory. The caller owns every buffer it passes; the
+ *    library never frees or keeps a caller pointer past the call.
+ *  - The library owns the plan, the tree, the gridlets and all scratch
+ *    memory, and frees them in hpm_destroy.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Calls are
+ *    stream ordered; a call returns after its work is enqueued except where a
+ *    host read-back is documented.
+ *  - Errors are returned as hpm_status; nothing is thrown across the ABI.
+ *    After HPM_ERR_CUDA the CUDA context may be unusable.
+ *  - Arrays of particles are in the caller's order; outputs come back in the
+ *    caller's order.
+ *  - A plan is not thread safe: one host thread at a time per plan.
+ */
+#ifndef HPM_H
+#define HPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hpm_plan_s *hpm_plan_t;
+
+typedef enum {
+  HPM_OK = 0,
+  HPM_ERR_INVALID_ARG = -1,   /* bad argument (null pointer, range, size)          */
+  HPM_ERR_OUT_OF_DOMAIN = -2, /* a position outside [o, o+S]^3 or not a number      */
+  HPM_ERR_OOM = -3,           /* device allocation failed                           */
+  HPM_ERR_CUDA = -4,          /* a CUDA runtime error; see hpm_last_cuda_error()    */
+  HPM_ERR_TIMEOUT = -5,       /* a bounded device wait gave up                      */
+  HPM_ERR_NOT_BUILT = -6,     /* hpm_solve before hpm_build_tree, or N mismatch     */
+  HPM_ERR_BUSY = -7,          /* no free slot (serving)                             */
+  HPM_ERR_UNSUPPORTED = -8    /* a valid request this build does not implement      */
+} hpm_status;
+
+/* Cubic domain [origin, origin + side)^3 with open (non-periodic) boundaries
+ * (Sec. 1: only a cubic domain and cubic cells are considered). A particle at
+ * exactly origin + side on an axis is placed in the last cell. */
+typedef struct {
+  double origin[3];
+  double side;
+} hpm_domain;
+
+/* Green function. The paper's method only convolves with it (Sec. 4: "any
+ * Green function ... would work equally well"); this build provides the
+ * Plummer-softened Newtonian kernel. */
+enum { HPM_GREEN_PLUMMER = 0 };
+typedef struct {
+  int kind;    /* HPM_GREEN_PLUMMER                                    */
+  double eps;  /* softening length, >= 0 (0 = Newtonian)               */
+} hpm_green;
+
+/* Tree options (Sec. 1: the tree "may or may not be of uniform depth").
+ * leaf_max = 0: uniform tree, every nonempty cell above max_depth splits.
+ * leaf_max > 0: a cell splits iff it holds more than leaf_max particles and
+ * its level is below max_depth. */
+typedef struct {
+  int leaf_max;
+  int flags;   /* HPM_FLAG_* bits */
+} hpm_plan_opts;
+
+enum {
+  HPM_FLAG_TIMINGS = 1,        /* record per-stage CUDA-event timings (hpm_get_stats)   */
+  HPM_FLAG_GENERIC_M2L = 2     /* use the any-order convolution kernel for every Ng   */
+};
+
+/*
+ * hpm_plan - geometry-only set-up, outside any timed region (Sec. 4: the
+ * exact Green function and the matrices A, B, T are tabulated before timing).
+ *   dom           domain (host struct, copied)
+ *   max_depth     deepest tree level, 0..21
+ *   gridlet_order Ng, gridlet points per dimension, 1..8 (Sec. 2.2 uses
+ *                 Ng^3 effective masses at x_p = (p + 1/2)/Ng - 1/2)
+ *   green         kernel (host struct, copied)
+ *   opts          may be NULL (uniform tree, no timings)
+ *   out           receives the plan handle
+ * Precomputes, on the current device: the 1-D child-to-parent matrices
+ * T^{+-} (Sec. 2.3) and, for every level 2..max_depth, the transform of the
+ * exact Green function on the (8 Ng)^3 periodic grid (Sec. 2.1, Eq. gf),
+ * evaluated in FP64 and stored in FP32. Synchronises the device.
+ * Errors: HPM_ERR_INVALID_ARG, HPM_ERR_OOM, HPM_ERR_CUDA.
+ */
+hpm_status hpm_plan(const hpm_domain *dom, int max_depth, int gridlet_order,
+                    const hpm_green *green, const hpm_plan_opts *opts, hpm_plan_t *out);
+
+/*
+ * hpm_build_tree - the oct-tree and its lists for N particles (Sec. 1).
+ *   d_pos  N x 3 FP64 positions, array of structs (x0 y0 z0 x1 ...), device
+ *   n      N >= 0 (N < 2^31)
+ * Builds Morton keys from the FP64 positions, sorts the particles by their
+ * level-max_depth key (ties by index), the per-level cell tables, the near
+ * zone of every leaf and the interaction-zone occupancy of every cell at
+ * level >= 2. Reads back one small count per level (host synchronisation on
+ * `stream`). Errors: HPM_ERR_INVALID_ARG, HPM_ERR_OUT_OF_DOMAIN, HPM_ERR_OOM,
+ * HPM_ERR_CUDA.
+ */
+hpm_status hpm_build_tree(hpm_plan_t plan, const double *d_pos, int64_t n, void *stream);
+
+/*
+ * hpm_solve - potential and acceleration of every particle (Sec. 1, steps
+ * 1-4 plus the near zone).
+ *   d_pos   N x 3 FP64 positions, the same values given to hpm_build_tree
+ *   d_mass  N FP64 masses
+ *   d_phi   N FP32 output potentials (may be NULL)
+ *   d_acc   N x 3 FP32 output accelerations, AoS (may be NULL)
+ * Stream ordered, no host synchronisation. Errors: HPM_ERR_NOT_BUILT,
+ * HPM_ERR_INVALID_ARG, HPM_ERR_CUDA.
+ */
+hpm_status hpm_solve(hpm_plan_t plan, const double *d_pos, const double *d_mass, float *d_phi,
+                     float *d_acc, void *stream);
+
+/*
+ * hpm_solve_host - the same solve from and to host memory: copies the
+ * positions and masses in, builds the tree, solves and copies phi and acc back,
+ * then synchronises `stream`. h_phi / h_acc may be NULL.
+ */
+hpm_status hpm_solve_host(hpm_plan_t plan, const double *h_pos, const double *h_mass, int64_t n,
+                          float *h_phi, float *h_acc, void *stream);
+
+/* Counts of the built tree (host). */
+typedef struct {
+  int64_t n_particles;
+  int64_t n_cells;      /* real tree cells, all levels                    */
+  int64_t n_targets;    /* cells at level >= 2 (one FFT convolution each)  */
+  int64_t n_leaves;
+  int64_t n_boxes;      /* cells plus the virtual source boxes             */
+  int max_depth;
+  int depth_reached;    /* deepest level holding a cell                     */
+} hpm_lists_info;
+
+hpm_status hpm_get_lists_info(hpm_plan_t plan, hpm_lists_info *info);
+
+/*
+ * hpm_get_lists - the tree and its lists in canonical form, for parity checks
+ * against an independent implementation. All arrays are host memory sized from
+ * hpm_get_lists_info; any pointer may be NULL to skip it. Synchronises.
+ *   level, key, begin, end, leaf   per cell, cells ordered by (level, Morton key):
+ *        level; Morton key at that level (bit k of x, y, z -> bits 3k, 3k+1,
+ *        3k+2); particle range [begin, end) in the sorted order; leaf flag
+ *   iz   n_targets x 4 words, for the cells at level >= 2 in the same order:
+ *        bit j (word j/64) set iff box j = bx + 6 by + 36 bz of the 6^3 block
+ *        2 (parent - 1) + (bx, by, bz) is a nonempty box of the target's
+ *        interaction zone (Sec. 1: in the parent's near zone, not in the
+ *        target's)
+ *   near n_leaves words, leaves in cell order: bit (dx+1) + 3(dy+1) + 9(dz+1)
+ *        set iff the box at offset (dx, dy, dz) is nonempty (itself included)
+ *   perm N: sorted position -> caller index
+ */
+hpm_status hpm_get_lists(hpm_plan_t plan, int32_t *level, uint64_t *key, int64_t *begin,
+                         int64_t *end, uint8_t *leaf, uint64_t *iz, uint32_t *near,
+                         int64_t *perm);
+
+/*
+ * hpm_get_boxes - every box of the built tree (cells and the virtual source
+ * boxes inside coarser leaves that some interaction zone needs), level-major,
+ * Morton order within a level. Host arrays of n_boxes (hpm_get_lists_info);
+ * NULL skips. flags: bit 0 cell, bit 1 internal cell, bit 2 leaf.
+ * Synchronises.
+ */
+hpm_status hpm_get_boxes(hpm_plan_t plan, int32_t *level, uint64_t *key, uint8_t *flags);
+
+/*
+ * hpm_get_stage - intermediate results of the last hpm_solve, for stage-by-
+ * stage parity checks. Host output, FP32, Ng^3 values per row with node
+ * p = i + Ng j + Ng^2 k (Sec. 2.2). Synchronises. `count` is the number of
+ * floats the caller provides; HPM_ERR_INVALID_ARG if it is too small.
+ *   HPM_STAGE_MASSES  effective masses of every box at level >= 2, rows in
+ *                     hpm_get_boxes order starting at the first level-2 box
+ *                     (Sec. 2.2 for leaves and virtual boxes, Sec. 2.3 for
+ *                     internal cells)
+ *   HPM_STAGE_M2L     source-to-target values of every target (cells at level
+ *                     >= 2 in cell order), Ng^3 values then one constant per
+ *                     target: Phi_p = row_p + const (Sec. 2.1)
+ *   HPM_STAGE_LOCAL   local gridlet after the parent-to-child pass (Sec. 2.4),
+ *                     same layout: deviations then one constant per target
+ */
+enum { HPM_STAGE_MASSES = 1, HPM_STAGE_M2L = 2, HPM_STAGE_LOCAL = 3 };
+hpm_status hpm_get_stage(hpm_plan_t plan, int stage, float *h_out, int64_t count);
+
+/* Per-stage device times of the last solve (flags bit 0), milliseconds, and
+ * launch counts. */
+typedef struct {
+  float ms_tree, ms_p2g, ms_m2m, ms_m2l, ms_l2l, ms_g2p, ms_p2p, ms_total;
+  int64_t launches;        /* kernels launched by the last build + solve */
+  int64_t m2l_launches;    /* of which source-to-target                  */
+  int64_t m2l_targets;     /* target cells convolved by the last solve    */
+} hpm_stats;
+
+hpm_status hpm_get_stats(hpm_plan_t plan, hpm_stats *stats);
+
+/* Frees the plan and everything it owns. NULL is allowed. */
+hpm_status hpm_destroy(hpm_plan_t plan);
+
+/* Static strings. */
+const char *hpm_status_str(hpm_status s);
+const char *hpm_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPM_H */

@@ -732,3 +732,105 @@ def rel_max(acc, ref) -> float:
     num = np.linalg.norm(np.asarray(acc) - np.asarray(ref), axis=-1)
     den = np.linalg.norm(np.asarray(ref), axis=-1)
     return float(np.max(num / np.maximum(den, 1e-300))) if num.size else 0.0
+
+
+# ---------------------------------------------------------------------------
+# Stage-by-stage reference values (plain definitions), for element-wise parity
+# ---------------------------------------------------------------------------
+def _boxes(tree: Tree, levels, keys):
+    levels = np.asarray(levels, dtype=np.int64)
+    keys = np.asarray(keys, dtype=np.uint64)
+    idx = np.zeros(levels.shape[0], dtype=np.int64)
+    for l in np.unique(levels):
+        m = levels == l
+        idx[m] = tree.levels[int(l)].find(keys[m])
+    if np.any(idx < 0):
+        raise KeyError("empty box")
+    return idx
+
+
+def box_masses(tree: Tree, mass, ng, levels, keys):
+    """Effective masses of the given (level, key) boxes straight from their particles
+    (Sec. 2.2, Lagrange form of Eq. mp)."""
+    smass = _f64(np.asarray(mass, dtype=np.float64)[tree.perm])
+    levels = np.asarray(levels, dtype=np.int64)
+    idx = _boxes(tree, levels, keys)
+    beg = np.zeros_like(idx)
+    end = np.zeros_like(idx)
+    cen = np.zeros((idx.shape[0], 3))
+    side = np.zeros(idx.shape[0])
+    for l in np.unique(levels):
+        m = levels == l
+        lv = tree.levels[int(l)]
+        beg[m], end[m] = lv.begin[idx[m]], lv.end[idx[m]]
+        cen[m] = tree.centers(int(l), idx[m])
+        side[m] = tree.box_side(int(l))
+    return p2g(ng, beg, end, cen, side, tree.spos, smass)
+
+
+def m2l_values(tree: Tree, mass, ng, eps, levels, keys):
+    """Source-to-target values Phi_{t,p} of the given target cells, direct IZ sum (Sec. 2.1)."""
+    levels = np.asarray(levels, dtype=np.int64)
+    keys = np.asarray(keys, dtype=np.uint64)
+    idx = _boxes(tree, levels, keys)
+    out = np.zeros((levels.shape[0], ng ** 3))
+    for l in np.unique(levels):
+        sel = np.flatnonzero(levels == l)
+        rows, _ = tree.iz_rows(int(l), idx[sel])
+        src = np.unique(rows[rows >= 0])
+        lv = tree.levels[int(l)]
+        grid = box_masses(tree, mass, ng, np.full(src.shape[0], l), lv.keys[src]) if src.size else np.zeros((0, ng ** 3))
+        pos_of = {int(b): k for k, b in enumerate(src)}
+        soff = [0]
+        sidx = []
+        for r in rows:
+            sidx.extend(pos_of[int(b)] for b in r[r >= 0])
+            soff.append(len(sidx))
+        out[sel] = m2l_direct(ng, eps, tree.centers(int(l), idx[sel]), np.full(sel.shape[0], tree.box_side(int(l))),
+                              np.asarray(soff), np.asarray(sidx, dtype=np.int64),
+                              tree.centers(int(l), src) if src.size else np.zeros((0, 3)), grid)
+    return out
+
+
+def local_values(tree: Tree, mass, ng, eps, levels, keys):
+    """Local gridlet of each target after the parent-to-child pass: the sum over the target
+    and its ancestors down to level 2 of their interpolants (Eqs. c2pmat/phix), evaluated at
+    the target's nodes (Sec. 2.4: Phi^C_p = Phi^P((a^C + x_p)/2) plus its own values)."""
+    levels = np.asarray(levels, dtype=np.int64)
+    keys = np.asarray(keys, dtype=np.uint64)
+    chain_l, chain_k = [], []
+    for l, k in zip(levels, keys):
+        for la in range(2, int(l) + 1):
+            chain_l.append(la)
+            chain_k.append(int(k) >> (3 * (int(l) - la)))
+    cl = np.asarray(chain_l, dtype=np.int64)
+    ck = np.asarray(chain_k, dtype=np.uint64)
+    uniq = {}
+    for a, b in zip(cl, ck):
+        uniq.setdefault((int(a), int(b)), len(uniq))
+    ul = np.asarray([a for a, _ in uniq], dtype=np.int64)
+    uk = np.asarray([b for _, b in uniq], dtype=np.uint64)
+    phi_c = m2l_values(tree, mass, ng, eps, ul, uk)
+    idx_c = _boxes(tree, ul, uk)
+    cen_c = np.zeros((ul.shape[0], 3))
+    side_c = np.zeros(ul.shape[0])
+    for l in np.unique(ul):
+        m = ul == l
+        cen_c[m] = tree.centers(int(l), idx_c[m])
+        side_c[m] = tree.box_side(int(l))
+    x = nodes(ng)
+    m3 = ng ** 3
+    node_off = np.array([[x[p % ng], x[(p // ng) % ng], x[p // (ng * ng)]] for p in range(m3)])
+    idx = _boxes(tree, levels, keys)
+    pts = np.zeros((levels.shape[0] * m3, 3))
+    coff = [0]
+    ccell = []
+    for t, (l, k) in enumerate(zip(levels, keys)):
+        c = tree.centers(int(l), [idx[t]])[0]
+        pts[t * m3:(t + 1) * m3] = c + tree.box_side(int(l)) * node_off
+        chain = [uniq[(la, int(k) >> (3 * (int(l) - la)))] for la in range(2, int(l) + 1)]
+        for _ in range(m3):
+            ccell.extend(chain)
+            coff.append(len(ccell))
+    phi, _ = far_eval(ng, pts, np.asarray(coff), np.asarray(ccell, dtype=np.int64), cen_c, side_c, phi_c)
+    return phi.reshape(levels.shape[0], m3)

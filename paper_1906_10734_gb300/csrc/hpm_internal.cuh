@@ -1,0 +1,148 @@
+// Internal declarations shared by the translation units of libhpm.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/hpm.h"
+
+namespace hpm {
+
+constexpr int kMaxNg = 8;
+constexpr int kMaxDepth = 21;
+constexpr int kMortonBits = 21;
+
+// Box flags (a "box" is a nonempty dyadic box of some level that the solve
+// needs: every real tree cell, plus the virtual boxes inside coarser leaves
+// that lie in the parent neighbourhood of some internal cell).
+enum : uint8_t {
+  kReal = 1,      // a cell of the tree
+  kInternal = 2,  // a cell that splits
+  kLeaf = 4,      // a cell that does not split
+  kExpand = 8,    // its children are needed (it neighbours an internal cell)
+};
+
+// Device error word bits.
+enum : int { kErrDomain = 1, kErrCapacity = 2, kErrTimeout = 4 };
+
+const char *set_cuda_error(cudaError_t e);
+
+// Grow-only device buffer on the stream-ordered allocator.
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  hpm_status ensure(size_t bytes, cudaStream_t s, bool keep = false);
+  void release(cudaStream_t s);
+  template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Constant tables handed to kernels by value.
+struct GridletTables {
+  int ng;
+  float node[kMaxNg];                // x_j = (j + 1/2)/Ng - 1/2
+  float t1[2][kMaxNg][kMaxNg];       // T^{s}_{pq} = ell_p((a_s + x_q)/2), a_0 = -1/2, a_1 = +1/2
+  double node_d[kMaxNg];
+  double inv_den_d[kMaxNg];          // 1 / prod_{k != j} (x_j - x_k)
+  float inv_den[kMaxNg];
+};
+
+struct TreeDev {
+  // sorted particles
+  DevBuf keys, keys_alt, perm, perm_alt;
+  DevBuf spm;        // double4 (x, y, z, m) in sorted order
+  // boxes, all levels, level-major, Morton order within a level
+  DevBuf box_key, box_beg, box_end, box_parent, box_flags, box_child, box_nb;
+  DevBuf cnt, off;   // per-box scratch for child counting
+  // work lists
+  DevBuf tgt_box, box_tgt, leaf_box, p2g_box;
+  DevBuf err;        // int error word
+  DevBuf counters;   // small device counters
+};
+
+struct SolveDev {
+  DevBuf grid;       // effective masses, row = box - lvl_off[2], Ng^3 floats
+  DevBuf m2l_raw;    // source-to-target values per target, Ng^3
+  DevBuf loc;        // local gridlets per target, Ng^3 deviations
+  DevBuf locc;       // local constant per target
+  DevBuf m2lc;       // constant part of each target's source-to-target values
+  DevBuf far;        // far field per sorted particle: float4 (phi, ax, ay, az)
+  DevBuf m2l_scratch;
+  DevBuf work;       // int work counters
+};
+
+}  // namespace hpm
+
+struct hpm_plan_s {
+  hpm_domain dom;
+  int max_depth;
+  int ng;
+  hpm_green green;
+  hpm_plan_opts opts;
+  int device;
+  hpm::GridletTables tab;
+  // Green transforms, reduced (P/2+1)^3 FP32 tables per level, scaled -1/P^3
+  hpm::DevBuf ghat;
+  int64_t ghat_level_stride;  // floats per level
+  // mean of the periodic Green function per level, removed from the DC bin of
+  // the stored transform and added back to each target's constant
+  hpm::DevBuf gmean;
+  // tree
+  hpm::TreeDev t;
+  hpm::SolveDev s;
+  bool built = false;
+  int64_t n = 0;
+  std::vector<int64_t> lvl_off;    // box offsets per level, size depth+2
+  int depth_reached = -1;
+  int64_t nbox = 0, ntgt = 0, nleaf = 0, np2g = 0, ncell = 0;
+  std::vector<int64_t> tgt_lvl_off;  // target offsets per level (levels 2..D)
+  std::vector<int64_t> leaf_lvl_off;
+  hpm_stats stats{};
+  cudaEvent_t ev[10] = {};
+  bool events_ready = false;
+  hpm::DevBuf host_io_pos, host_io_mass, host_io_phi, host_io_acc;
+};
+
+namespace hpm {
+// tree.cu
+hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream_t st);
+// sort.cu
+hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&vals,
+                            uint32_t *&vals_alt, int64_t n, int bits, DevBuf &scratch,
+                            cudaStream_t st, int64_t *launches);
+hpm_status exclusive_scan_i32(const int *in, int *out, int64_t n, int *d_total, DevBuf &scratch,
+                              cudaStream_t st, int64_t *launches);
+// solve.cu
+hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, float *d_phi,
+                 float *d_acc, cudaStream_t st);
+hpm_status precompute_green(hpm_plan_s *pl, cudaStream_t st);
+// m2l.cu
+hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches);
+}  // namespace hpm
+
+#define HPM_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) {                            \
+      hpm::set_cuda_error(e_);                          \
+      return e_ == cudaErrorMemoryAllocation ? HPM_ERR_OOM : HPM_ERR_CUDA; \
+    }                                                   \
+  } while (0)
+
+#define HPM_TRY(call)                 \
+  do {                                \
+    hpm_status s_ = (call);           \
+    if (s_ != HPM_OK) return s_;      \
+  } while (0)
+
+#define HPM_LAUNCHED(counter)                           \
+  do {                                                  \
+    cudaError_t e_ = cudaGetLastError();                \
+    if (e_ != cudaSuccess) {                            \
+      hpm::set_cuda_error(e_);                          \
+      return HPM_ERR_CUDA;                              \
+    }                                                   \
+    if (counter) ++*(counter);                          \
+  } while (0)

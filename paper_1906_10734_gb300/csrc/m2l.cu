@@ -1,0 +1,487 @@
+// Source-to-target transformation (Sec. 2.1): for every target cell t at level
+// l >= 2, the effective masses of the 6^3 level-l boxes around t's parent
+// (zero where a box is empty, outside the domain or in t's near zone) form a
+// (6 Ng)^3 grid that is zero padded to P^3 = (8 Ng)^3 and convolved with the
+// exact Green function by one FFT; the Ng^3 values at t's gridlet nodes are
+// kept.
+//
+// The convolution is periodic with period P, so the block may be placed at
+// any circular offset. Both kernels here place it so that the target's nodes
+// sit at FFT positions 0 .. Ng-1: the Green transform then needs no phase
+// factor per child parity (one real table per level serves all 8 parities)
+// and the inverse transform is pruned to those Ng outputs per axis.
+#include <cmath>
+
+#include "hpm_internal.cuh"
+
+namespace hpm {
+namespace {
+
+struct Levels {
+  int64_t off[kMaxDepth + 3];
+  int nlev;
+};
+
+__device__ __forceinline__ int level_of(const Levels &lt, int64_t box) {
+  int l = 0;
+  while (l + 1 < lt.nlev && lt.off[l + 1] <= box) ++l;
+  return l;
+}
+
+struct TreeRefs {
+  const float *grid;
+  float *out;
+  float *outc;          // per target: -mean(G) * sum(rho), the constant part
+  const float *gmean;   // per level: mean of G over the periodic grid
+  const int *tgt_box;
+  const int *parent;
+  const int *nb;
+  const int *child;
+  const uint64_t *key;
+  const float *ghat;
+  int64_t ghat_stride;
+  int64_t off2;
+  int64_t ntgt;
+};
+
+// Block table of one target: row of each of the 216 boxes, -1 where the box
+// is empty, outside the domain or within Chebyshev distance 1 of the target.
+__device__ __forceinline__ void fill_block(const TreeRefs &r, int box, int tx, int ty, int tz, int *blk) {
+  const int p = r.parent[box];
+  for (int j = threadIdx.x; j < 216; j += blockDim.x) {
+    const int bx = j % 6, by = (j / 6) % 6, bz = j / 36;
+    int row = -1;
+    const int cheb = max(abs(bx - tx), max(abs(by - ty), abs(bz - tz)));
+    if (cheb >= 2) {
+      const int q = r.nb[(int64_t)p * 27 + (bx >> 1) + 3 * (by >> 1) + 9 * (bz >> 1)];
+      if (q >= 0) {
+        const int c = r.child[(int64_t)q * 8 + (bx & 1) + 2 * (by & 1) + 4 * (bz & 1)];
+        if (c >= 0) row = (int)(c - r.off2);
+      }
+    }
+    blk[j] = row;
+  }
+}
+
+// ===========================================================================
+// Fast path, Ng = 4 (P = 32).
+// ===========================================================================
+namespace f4 {
+constexpr int kP = 32, kB = 24, kH = 17;
+constexpr int kLS = 25;                // line stride of the x-pass output [z][y]
+constexpr int kYS = 33;                // line stride of the y-pass output [z][ky]
+constexpr int kSlab = kB * kYS;        // float2 per kx slab (>= 24 * 25)
+constexpr int kThreads = 288;          // 9 warps; 288 line pairs in the x pass
+constexpr int kWarps = kThreads / 32;
+constexpr size_t kSmem = sizeof(float2) * kH * kSlab + sizeof(int) * 216 + sizeof(float) * kH * 32 +
+                         sizeof(float2) * 32 + 16;
+
+struct Params {
+  float2 w[kP];  // w[e] = exp(-2 pi i e / 32)
+  TreeRefs r;
+  Levels lt;
+};
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+constexpr int brev5(int i) {
+  return ((i & 1) << 4) | ((i & 2) << 2) | (i & 4) | ((i & 8) >> 2) | ((i & 16) >> 4);
+}
+
+// In-register radix-2 decimation-in-time FFT of 32 points.
+// SIGN = -1: forward (w), SIGN = +1: backward (conj w). Unnormalised.
+template <int SIGN>
+__device__ __forceinline__ void fft32(float2 (&a)[32], const float2 (&w)[kP]) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int j = brev5(i);
+    if (j > i) {
+      const float2 t = a[i];
+      a[i] = a[j];
+      a[j] = t;
+    }
+  }
+#pragma unroll
+  for (int half = 1; half < 32; half <<= 1) {
+#pragma unroll
+    for (int i = 0; i < 32; i += 2 * half) {
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const int e = k * (16 / half);
+        float2 v = a[i + k + half];
+        if (e == 8) {
+          v = SIGN < 0 ? make_float2(v.y, -v.x) : make_float2(-v.y, v.x);
+        } else if (e != 0) {
+          float2 wv = w[e];
+          if (SIGN > 0) wv.y = -wv.y;
+          v = cmul(v, wv);
+        }
+        const float2 u = a[i + k];
+        a[i + k] = cadd(u, v);
+        a[i + k + half] = csub(u, v);
+      }
+    }
+  }
+}
+
+// x pass: two real x-lines (y0, y0+1) at height z as one complex FFT, block
+// placed so that the target's x nodes land at 0..3. Writes 2x the spectra
+// (the 1/2 of the two-for-one split is applied at the end).
+template <int TX>
+__device__ __forceinline__ void pass_x(const Params &pr, const int *blk, float2 *X) {
+  const int t = threadIdx.x;
+  const int z = t / 12, y0 = 2 * (t % 12);
+  const int bz = z >> 2, kz = z & 3, by = y0 >> 2, ky0 = y0 & 3;
+  float2 a[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) a[i] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int bx = 0; bx < 6; ++bx) {
+    const int slot = (bx - TX) & 7;
+    const int row = blk[bx + 6 * by + 36 * bz];
+    if (row >= 0) {
+      const float *g = pr.r.grid + (int64_t)row * 64 + 16 * kz + 4 * ky0;
+      const float4 v0 = __ldg(reinterpret_cast<const float4 *>(g));
+      const float4 v1 = __ldg(reinterpret_cast<const float4 *>(g + 4));
+      a[4 * slot + 0] = make_float2(v0.x, v1.x);
+      a[4 * slot + 1] = make_float2(v0.y, v1.y);
+      a[4 * slot + 2] = make_float2(v0.z, v1.z);
+      a[4 * slot + 3] = make_float2(v0.w, v1.w);
+    }
+  }
+  fft32<-1>(a, pr.w);
+#pragma unroll
+  for (int k = 0; k <= 16; ++k) {
+    const float2 zk = a[k], zm = a[(32 - k) & 31];
+    X[k * kSlab + z * kLS + y0] = make_float2(zk.x + zm.x, zk.y - zm.y);
+    X[k * kSlab + z * kLS + y0 + 1] = make_float2(zk.y + zm.y, zm.x - zk.x);
+  }
+}
+
+// y and z passes, Green product, pruned inverse z and y for one kx slab (one warp).
+__device__ __forceinline__ void pass_slab(const Params &pr, int kx, int n0y, int n0z, float2 *slab,
+                                          const float *ghat, const float2 *tw, float *V, float *dc) {
+  const int lane = threadIdx.x & 31;
+  float2 a[32];
+  // y pass: lane = z
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    const int u = (r + n0y) & 31;
+    a[r] = (lane < kB && u < kB) ? slab[lane * kLS + u] : make_float2(0.f, 0.f);
+  }
+  fft32<-1>(a, pr.w);
+  __syncwarp();
+  if (lane < kB) {
+#pragma unroll
+    for (int r = 0; r < 32; ++r) slab[lane * kYS + r] = a[r];
+  }
+  __syncwarp();
+  // z pass: lane = ky
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    const int u = (r + n0z) & 31;
+    a[r] = u < kB ? slab[u * kYS + lane] : make_float2(0.f, 0.f);
+  }
+  fft32<-1>(a, pr.w);
+  if (kx == 0 && lane == 0) *dc = 0.5f * a[0].x;  // sum of the block (x pass doubles)
+  {
+    const int kyr = lane <= 16 ? lane : 32 - lane;
+    const float *g = ghat + kx + kH * kyr;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int kzr = r <= 16 ? r : 32 - r;
+      const float gv = __ldg(g + kH * kH * kzr);
+      a[r].x *= gv;
+      a[r].y *= gv;
+    }
+  }
+  // pruned inverse over kz: W(z') = sum_kz a[kz] e^{+2 pi i kz z'/32}, z' = 0..3,
+  // with kz = 8 al + be: e^{+2 pi i kz z'/32} = i^(al z') e^{+2 pi i be z'/32}
+  float2 W0 = make_float2(0.f, 0.f), W1 = W0, W2 = W0, W3 = W0;
+#pragma unroll
+  for (int be = 0; be < 8; ++be) {
+    const float2 f0 = a[be], f1 = a[8 + be], f2 = a[16 + be], f3 = a[24 + be];
+    const float2 s02 = cadd(f0, f2), d02 = csub(f0, f2), s13 = cadd(f1, f3), d13 = csub(f1, f3);
+    const float2 z0 = cadd(s02, s13), z2 = csub(s02, s13);
+    const float2 z1 = make_float2(d02.x - d13.y, d02.y + d13.x);
+    const float2 z3 = make_float2(d02.x + d13.y, d02.y - d13.x);
+    W0 = cadd(W0, z0);
+    if (be == 0) {
+      W1 = cadd(W1, z1);
+      W2 = cadd(W2, z2);
+      W3 = cadd(W3, z3);
+    } else {
+      const float2 t1 = make_float2(pr.w[be].x, -pr.w[be].y);
+      const float2 t2 = make_float2(pr.w[2 * be].x, -pr.w[2 * be].y);
+      const float2 t3 = make_float2(pr.w[3 * be].x, -pr.w[3 * be].y);
+      W1 = cadd(W1, cmul(z1, t1));
+      W2 = cadd(W2, cmul(z2, t2));
+      W3 = cadd(W3, cmul(z3, t3));
+    }
+  }
+  // inverse over ky for y' = 0..3: products, then a transposed warp reduction
+  const float2 Wz[4] = {W0, W1, W2, W3};
+  float v[32];
+#pragma unroll
+  for (int yy = 0; yy < 4; ++yy) {
+    const float2 t = tw[(lane * yy) & 31];  // e^{+2 pi i ky y'/32}
+#pragma unroll
+    for (int zz = 0; zz < 4; ++zz) {
+      const float2 pz = yy == 0 ? Wz[zz] : cmul(Wz[zz], t);
+      v[2 * (yy + 4 * zz)] = pz.x;
+      v[2 * (yy + 4 * zz) + 1] = pz.y;
+    }
+  }
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const float send = upper ? v[i] : v[i + s];
+      const float keep = upper ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  V[kx * 32 + lane] = v[0];
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_m2l4(const __grid_constant__ Params pr) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2 *X = reinterpret_cast<float2 *>(smem);
+  int *blk = reinterpret_cast<int *>(X + kH * kSlab);
+  float *V = reinterpret_cast<float *>(blk + 216);
+  float2 *tw = reinterpret_cast<float2 *>(V + kH * 32);
+  float *dc = reinterpret_cast<float *>(tw + 32);
+  if (threadIdx.x < 32) tw[threadIdx.x] = make_float2(pr.w[threadIdx.x].x, -pr.w[threadIdx.x].y);
+  const int warp = threadIdx.x >> 5;
+  for (int64_t t = blockIdx.x; t < pr.r.ntgt; t += gridDim.x) {
+    const int box = pr.r.tgt_box[t];
+    const int oc = (int)(pr.r.key[box] & 7u);
+    const int tx = 2 + (oc & 1), ty = 2 + ((oc >> 1) & 1), tz = 2 + ((oc >> 2) & 1);
+    const int lev = level_of(pr.lt, box);
+    const float *ghat = pr.r.ghat + pr.r.ghat_stride * lev;
+    fill_block(pr.r, box, tx, ty, tz, blk);
+    __syncthreads();
+    if (tx == 2) pass_x<2>(pr, blk, X);
+    else pass_x<3>(pr, blk, X);
+    __syncthreads();
+    for (int kx = warp; kx < kH; kx += kWarps)
+      pass_slab(pr, kx, 4 * ty, 4 * tz, X + kx * kSlab, ghat, tw, V, dc);
+    __syncthreads();
+    if (threadIdx.x == 64) pr.r.outc[t] = -pr.r.gmean[lev] * *dc;
+    if (threadIdx.x < 64) {
+      const int p = threadIdx.x;
+      const int xx = p & 3, yz = p >> 2;  // yz = y' + 4 z'
+      float s = 0.f;
+#pragma unroll
+      for (int kx = 0; kx < kH; ++kx) {
+        const float2 vv = make_float2(V[kx * 32 + 2 * yz], V[kx * 32 + 2 * yz + 1]);
+        const float2 t2 = tw[(kx * xx) & 31];
+        const float re = vv.x * t2.x - vv.y * t2.y;
+        s += (kx == 0 || kx == 16) ? re : 2.f * re;
+      }
+      pr.r.out[t * 64 + p] = 0.5f * s;
+    }
+  }
+}
+}  // namespace f4
+
+// ===========================================================================
+// Generic path, any Ng in 1..8: the same convolution done as separable
+// discrete Fourier sums per line with the same circular placement, one target
+// per block at a time, intermediate spectra in per-block global scratch.
+// ===========================================================================
+namespace gen {
+constexpr int kThreads = 256;
+
+struct Params {
+  TreeRefs r;
+  Levels lt;
+  int ng;
+  float2 *scratch;
+  int64_t scratch_per_block;
+};
+
+__global__ void __launch_bounds__(kThreads) k_m2l_generic(const __grid_constant__ Params pr) {
+  __shared__ float2 tw[64];
+  __shared__ int blk[216];
+  const int ng = pr.ng, P = 8 * ng, B = 6 * ng, H = P / 2 + 1, m3 = ng * ng * ng;
+  for (int e = threadIdx.x; e < P; e += blockDim.x) {
+    double s, c;
+    sincospi(2.0 * e / P, &s, &c);
+    tw[e] = make_float2((float)c, (float)s);  // e^{+2 pi i e/P}
+  }
+  float2 *X1 = pr.scratch + pr.scratch_per_block * blockIdx.x;  // [kx][z][y]   H*B*B
+  float2 *X2 = X1 + (int64_t)H * B * B;                          // [kx][ky][z]  H*P*B
+  float2 *X4 = X2 + (int64_t)H * P * B;                          // [kx][ky][z'] H*P*ng
+  float2 *X5 = X4 + (int64_t)H * P * ng;                         // [kx][y'][z'] H*ng*ng
+  __syncthreads();
+  for (int64_t t = blockIdx.x; t < pr.r.ntgt; t += gridDim.x) {
+    const int box = pr.r.tgt_box[t];
+    const int oc = (int)(pr.r.key[box] & 7u);
+    const int tx = 2 + (oc & 1), ty = 2 + ((oc >> 1) & 1), tz = 2 + ((oc >> 2) & 1);
+    const int n0[3] = {ng * tx, ng * ty, ng * tz};
+    const int lev = level_of(pr.lt, box);
+    const float *ghat = pr.r.ghat + pr.r.ghat_stride * lev;
+    fill_block(pr.r, box, tx, ty, tz, blk);
+    __syncthreads();
+    // x: X1[kx][z][y] = sum_x rho(x,y,z) e^{-2 pi i kx ((x - n0x) mod P)/P}
+    for (int64_t i = threadIdx.x; i < (int64_t)H * B * B; i += blockDim.x) {
+      const int y = (int)(i % B), z = (int)((i / B) % B), kx = (int)(i / ((int64_t)B * B));
+      float2 s = make_float2(0.f, 0.f);
+      for (int x = 0; x < B; ++x) {
+        const int row = blk[x / ng + 6 * (y / ng) + 36 * (z / ng)];
+        if (row < 0) continue;
+        const float v = pr.r.grid[(int64_t)row * m3 + (x % ng) + ng * ((y % ng) + ng * (z % ng))];
+        const int e = (kx * ((x - n0[0] + P) % P)) % P;
+        s.x += v * tw[e].x;
+        s.y -= v * tw[e].y;
+      }
+      X1[i] = s;
+    }
+    __syncthreads();
+    // y: X2[kx][ky][z] = sum_y X1[kx][z][y] e^{-2 pi i ky ((y - n0y) mod P)/P}
+    for (int64_t i = threadIdx.x; i < (int64_t)H * P * B; i += blockDim.x) {
+      const int z = (int)(i % B), ky = (int)((i / B) % P), kx = (int)(i / ((int64_t)B * P));
+      float2 s = make_float2(0.f, 0.f);
+      for (int y = 0; y < B; ++y) {
+        const float2 v = X1[((int64_t)kx * B + z) * B + y];
+        const float2 c = tw[(ky * ((y - n0[1] + P) % P)) % P];
+        s.x += v.x * c.x + v.y * c.y;
+        s.y += v.y * c.x - v.x * c.y;
+      }
+      X2[i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float sum = 0.f;
+      for (int z = 0; z < B; ++z) sum += X2[z].x;  // kx = ky = 0
+      pr.r.outc[t] = -pr.r.gmean[lev] * sum;
+    }
+    // z, Green product, inverse z to z' = 0..ng-1
+    for (int64_t i = threadIdx.x; i < (int64_t)H * P; i += blockDim.x) {
+      const int ky = (int)(i % P), kx = (int)(i / P);
+      float2 acc[kMaxNg];
+      for (int q = 0; q < ng; ++q) acc[q] = make_float2(0.f, 0.f);
+      const int kyr = ky <= P / 2 ? ky : P - ky;
+      for (int kz = 0; kz < P; ++kz) {
+        float2 s = make_float2(0.f, 0.f);
+        for (int z = 0; z < B; ++z) {
+          const float2 v = X2[((int64_t)kx * P + ky) * B + z];
+          const float2 c = tw[(kz * ((z - n0[2] + P) % P)) % P];
+          s.x += v.x * c.x + v.y * c.y;
+          s.y += v.y * c.x - v.x * c.y;
+        }
+        const int kzr = kz <= P / 2 ? kz : P - kz;
+        const float g = ghat[kx + H * (kyr + H * kzr)];
+        s.x *= g;
+        s.y *= g;
+        for (int q = 0; q < ng; ++q) {
+          const float2 c = tw[(kz * q) % P];
+          acc[q].x += s.x * c.x - s.y * c.y;
+          acc[q].y += s.x * c.y + s.y * c.x;
+        }
+      }
+      for (int q = 0; q < ng; ++q) X4[i * ng + q] = acc[q];
+    }
+    __syncthreads();
+    // inverse y to y' = 0..ng-1
+    for (int64_t i = threadIdx.x; i < (int64_t)H * ng * ng; i += blockDim.x) {
+      const int zq = (int)(i % ng), yq = (int)((i / ng) % ng), kx = (int)(i / ((int64_t)ng * ng));
+      float2 s = make_float2(0.f, 0.f);
+      for (int ky = 0; ky < P; ++ky) {
+        const float2 v = X4[((int64_t)kx * P + ky) * ng + zq];
+        const float2 c = tw[(ky * yq) % P];
+        s.x += v.x * c.x - v.y * c.y;
+        s.y += v.x * c.y + v.y * c.x;
+      }
+      X5[i] = s;
+    }
+    __syncthreads();
+    // inverse x (complex to real) to x' = 0..ng-1
+    for (int p = threadIdx.x; p < m3; p += blockDim.x) {
+      const int xq = p % ng, yq = (p / ng) % ng, zq = p / (ng * ng);
+      float s = 0.f;
+      for (int kx = 0; kx < H; ++kx) {
+        const float2 v = X5[((int64_t)kx * ng + yq) * ng + zq];
+        const float2 c = tw[(kx * xq) % P];
+        const float re = v.x * c.x - v.y * c.y;
+        s += (kx == 0 || 2 * kx == P) ? re : 2.f * re;
+      }
+      pr.r.out[t * m3 + p] = s;
+    }
+    __syncthreads();
+  }
+}
+}  // namespace gen
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+
+hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
+  TreeRefs r{};
+  r.grid = pl->s.grid.as<float>();
+  r.out = pl->s.m2l_raw.as<float>();
+  r.outc = pl->s.m2lc.as<float>();
+  r.gmean = pl->gmean.as<float>();
+  r.tgt_box = pl->t.tgt_box.as<int>();
+  r.parent = pl->t.box_parent.as<int>();
+  r.nb = pl->t.box_nb.as<int>();
+  r.child = pl->t.box_child.as<int>();
+  r.key = pl->t.box_key.as<uint64_t>();
+  r.ghat = pl->ghat.as<float>();
+  r.ghat_stride = pl->ghat_level_stride;
+  r.off2 = pl->lvl_off[2];
+  r.ntgt = pl->ntgt;
+  Levels lt{};
+  lt.nlev = pl->max_depth + 1;
+  for (int l = 0; l <= pl->max_depth + 1; ++l) lt.off[l] = pl->lvl_off[l];
+  const int nsm = sm_count();
+  if (pl->ng == 4 && !(pl->opts.flags & HPM_FLAG_GENERIC_M2L)) {
+    f4::Params p{};
+    for (int e = 0; e < f4::kP; ++e) {
+      const double a = -2.0 * M_PI * e / f4::kP;
+      p.w[e] = make_float2((float)cos(a), (float)sin(a));
+    }
+    p.r = r;
+    p.lt = lt;
+    static bool attr = false;
+    if (!attr) {
+      HPM_CUDA(cudaFuncSetAttribute(f4::k_m2l4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f4::kSmem));
+      attr = true;
+    }
+    const int64_t grid = std::min<int64_t>(pl->ntgt, (int64_t)2 * nsm);
+    f4::k_m2l4<<<(unsigned)grid, f4::kThreads, f4::kSmem, st>>>(p);
+    HPM_LAUNCHED(launches);
+    return HPM_OK;
+  }
+  gen::Params p{};
+  p.r = r;
+  p.lt = lt;
+  p.ng = pl->ng;
+  const int P = 8 * pl->ng, B = 6 * pl->ng, H = P / 2 + 1;
+  p.scratch_per_block = (int64_t)H * B * B + (int64_t)H * P * B + (int64_t)H * P * pl->ng +
+                        (int64_t)H * pl->ng * pl->ng;
+  const int64_t grid = std::min<int64_t>(pl->ntgt, (int64_t)nsm);
+  HPM_TRY(pl->s.m2l_scratch.ensure(sizeof(float2) * p.scratch_per_block * grid, st));
+  p.scratch = pl->s.m2l_scratch.as<float2>();
+  gen::k_m2l_generic<<<(unsigned)grid, gen::kThreads, 0, st>>>(p);
+  HPM_LAUNCHED(launches);
+  return HPM_OK;
+}
+
+}  // namespace hpm

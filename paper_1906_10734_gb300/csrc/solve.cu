@@ -1,0 +1,575 @@
+// Solve stages other than the source-to-target convolution:
+//   gather      sorted particle copies (FP64 for the gridlet weights, FP32
+//               hi/lo for the near field)
+//   P2G         effective masses of leaves and virtual boxes (Sec. 2.2)
+//   M2M         child-to-parent with the separable T^C (Sec. 2.3)
+//   L2L         parent-to-child, Phi^C_p = Phi^P((a^C + x_p)/2) (Sec. 2.4)
+//   G2P         interpolant of Eq. phix and its gradient at the particles
+//   P2P         near zone by direct summation with Kahan-compensated FP32
+//   Green       FP64 transform of the exact Green function (Sec. 2.1, Eq. gf)
+#include <cmath>
+
+#include "hpm_internal.cuh"
+
+namespace hpm {
+namespace {
+
+// Sorted particle: FP64 position and mass.
+struct __align__(32) PM {
+  double x, y, z, m;
+};
+
+constexpr int kThreads = 256;
+constexpr int kWarpsPerBlock = kThreads / 32;
+
+inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+inline unsigned warp_blocks(int64_t n) { return (unsigned)((n + kWarpsPerBlock - 1) / kWarpsPerBlock); }
+
+// M2M and L2L hold three Ng^3 buffers per warp: 4 warps per block keep the
+// static shared memory under 48 KB for Ng = 8.
+constexpr int kGThreads = 128;
+constexpr int kGWarps = kGThreads / 32;
+inline unsigned gwarp_blocks(int64_t n) { return (unsigned)((n + kGWarps - 1) / kGWarps); }
+
+struct LevelTable {
+  int64_t off[kMaxDepth + 3];
+  int nlev;
+};
+
+__device__ __forceinline__ uint32_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ull;
+  x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+  x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+  x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+  x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+  x = (x ^ (x >> 32)) & 0x1fffffull;
+  return (uint32_t)x;
+}
+
+__device__ __forceinline__ int level_of(const LevelTable &lt, int64_t box) {
+  int l = 0;
+  while (l + 1 < lt.nlev && lt.off[l + 1] <= box) ++l;
+  return l;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_gather(int64_t n, const uint32_t *__restrict__ perm, const double *__restrict__ pos,
+                         const double *__restrict__ mass, double ox, double oy, double oz,
+                         PM *__restrict__ spm, float4 *__restrict__ hi, float4 *__restrict__ lo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t p = perm[i];
+  const double x = pos[3 * (int64_t)p], y = pos[3 * (int64_t)p + 1], z = pos[3 * (int64_t)p + 2];
+  const double m = mass[p];
+  spm[i] = PM{x, y, z, m};
+  // position relative to the domain origin as an unevaluated sum hi + lo of
+  // two floats: differences of nearby particles stay accurate to FP32
+  // relative precision of the difference itself
+  const double rx = x - ox, ry = y - oy, rz = z - oz;
+  const float hx = (float)rx, hy = (float)ry, hz = (float)rz;
+  hi[i] = make_float4(hx, hy, hz, (float)m);
+  lo[i] = make_float4((float)(rx - (double)hx), (float)(ry - (double)hy), (float)(rz - (double)hz), 0.f);
+}
+
+// 1-D Lagrange weights on the gridlet nodes, FP64 (the moment-matching solve).
+__device__ __forceinline__ void lagrange_d(const GridletTables &tb, double t, float *w) {
+  const int ng = tb.ng;
+  double diff[kMaxNg];
+  for (int k = 0; k < ng; ++k) diff[k] = t - tb.node_d[k];
+  for (int j = 0; j < ng; ++j) {
+    double v = tb.inv_den_d[j];
+    for (int k = 0; k < ng; ++k)
+      if (k != j) v *= diff[k];
+    w[j] = (float)v;
+  }
+}
+
+// Effective masses of one box per warp, M_p = sum_i m_i prod_d ell_{p_d}(xi_d)
+// (Eq. mp in Lagrange form: sum_n B_pn t^n = ell_p(t)).
+__global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__restrict__ list,
+                                                  LevelTable lt, GridletTables tb, double ox, double oy,
+                                                  double oz, double side, const uint64_t *__restrict__ key,
+                                                  const int *__restrict__ beg, const int *__restrict__ end,
+                                                  const PM *__restrict__ spm, int64_t off2,
+                                                  float *__restrict__ grid) {
+  __shared__ float ws[kWarpsPerBlock][32][3][kMaxNg];
+  __shared__ float ms[kWarpsPerBlock][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + w;
+  if (item >= nbox) return;
+  const int box = list[item];
+  const int l = level_of(lt, box);
+  const double L = side / (double)(1u << l);
+  const uint64_t k = key[box];
+  const double cc[3] = {(double)compact3(k) + 0.5, (double)compact3(k >> 1) + 0.5,
+                        (double)compact3(k >> 2) + 0.5};
+  const double o[3] = {ox, oy, oz};
+  const int ng = tb.ng, m3 = ng * ng * ng;
+  float acc[16];
+  for (int r = 0; r < 16; ++r) acc[r] = 0.f;
+  const int b = beg[box], e = end[box];
+  for (int c0 = b; c0 < e; c0 += 32) {
+    const int i = c0 + lane;
+    if (i < e) {
+      const PM q = spm[i];
+      const double xs[3] = {q.x, q.y, q.z};
+      for (int d = 0; d < 3; ++d) {
+        const double xi = (xs[d] - o[d]) / L - cc[d];
+        lagrange_d(tb, xi, ws[w][lane][d]);
+      }
+      ms[w][lane] = (float)q.m;
+    } else {
+      ms[w][lane] = 0.f;
+      for (int d = 0; d < 3; ++d)
+        for (int j = 0; j < ng; ++j) ws[w][lane][d][j] = 0.f;
+    }
+    __syncwarp();
+    const int cnt = min(32, e - c0);
+    for (int r = 0; r * 32 + lane < m3; ++r) {
+      const int p = r * 32 + lane;
+      const int px = p % ng, py = (p / ng) % ng, pz = p / (ng * ng);
+      float s = acc[r];
+      for (int j = 0; j < cnt; ++j) s += ms[w][j] * ws[w][j][0][px] * ws[w][j][1][py] * ws[w][j][2][pz];
+      acc[r] = s;
+    }
+    __syncwarp();
+  }
+  float *out = grid + (int64_t)(box - off2) * m3;
+  for (int r = 0; r * 32 + lane < m3; ++r) out[r * 32 + lane] = acc[r];
+}
+
+// Separable application of a 1-D operator along one axis of an Ng^3 gridlet
+// held in shared memory: dst[.., p_axis, ..] = sum_q op[p][q] src[.., q, ..]
+// (or op[q][p] when transposed).
+__device__ __forceinline__ void apply_axis(const float *__restrict__ op, bool transpose, int axis,
+                                           int ng, const float *src, float *dst, bool accumulate) {
+  const int lane = threadIdx.x & 31, m3 = ng * ng * ng;
+  const int stride = axis == 0 ? 1 : (axis == 1 ? ng : ng * ng);
+  for (int p = lane; p < m3; p += 32) {
+    const int c = (p / stride) % ng;
+    const int base = p - c * stride;
+    float s = 0.f;
+    for (int q = 0; q < ng; ++q) s += (transpose ? op[q * kMaxNg + c] : op[c * kMaxNg + q]) * src[base + q * stride];
+    dst[p] = accumulate ? dst[p] + s : s;
+  }
+  __syncwarp();
+}
+
+// Child-to-parent: M^P = sum_C (T^{a_x} (x) T^{a_y} (x) T^{a_z}) M^C, one parent per warp.
+__global__ void __launch_bounds__(kGThreads) k_m2m(int64_t b, int64_t e, GridletTables tb,
+                                                  const uint8_t *__restrict__ flags,
+                                                  const int *__restrict__ child, int64_t off2,
+                                                  float *__restrict__ grid) {
+  __shared__ float T[2][kMaxNg * kMaxNg];
+  __shared__ float bufA[kGWarps][512], bufB[kGWarps][512], res[kGWarps][512];
+  for (int i = threadIdx.x; i < 2 * kMaxNg * kMaxNg; i += blockDim.x)
+    T[i / (kMaxNg * kMaxNg)][i % (kMaxNg * kMaxNg)] = tb.t1[i / (kMaxNg * kMaxNg)][(i / kMaxNg) % kMaxNg][i % kMaxNg];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t box = b + (int64_t)blockIdx.x * kGWarps + w;
+  if (box >= e || !(flags[box] & kInternal)) return;
+  const int ng = tb.ng, m3 = ng * ng * ng;
+  for (int p = lane; p < m3; p += 32) res[w][p] = 0.f;
+  for (int o = 0; o < 8; ++o) {
+    const int c = child[box * 8 + o];
+    if (c < 0) continue;
+    const float *src = grid + (int64_t)(c - off2) * m3;
+    for (int p = lane; p < m3; p += 32) bufA[w][p] = src[p];
+    __syncwarp();
+    apply_axis(T[o & 1], false, 0, ng, bufA[w], bufB[w], false);
+    apply_axis(T[(o >> 1) & 1], false, 1, ng, bufB[w], bufA[w], false);
+    apply_axis(T[(o >> 2) & 1], false, 2, ng, bufA[w], res[w], true);
+  }
+  float *dst = grid + (int64_t)(box - off2) * m3;
+  for (int p = lane; p < m3; p += 32) dst[p] = res[w][p];
+}
+
+// Parent-to-child plus the target's own source-to-target values, with the
+// local kept as (constant, deviations): the interpolation reproduces
+// constants exactly (the Lagrange weights sum to one), so the constant is
+// carried separately and the FP32 deviations only hold the variation across
+// the cell.
+__global__ void __launch_bounds__(kGThreads) k_l2l(int64_t tb0, int64_t tb1, int level,
+                                                  GridletTables tab, const int *__restrict__ tgt_box,
+                                                  const int *__restrict__ box_tgt,
+                                                  const int *__restrict__ parent,
+                                                  const uint64_t *__restrict__ key,
+                                                  const float *__restrict__ raw,
+                                                  float *__restrict__ loc, float *__restrict__ locc,
+                                                  const float *__restrict__ m2lc) {
+  __shared__ float T[2][kMaxNg * kMaxNg];
+  __shared__ float bufA[kGWarps][512], bufB[kGWarps][512], res[kGWarps][512];
+  for (int i = threadIdx.x; i < 2 * kMaxNg * kMaxNg; i += blockDim.x)
+    T[i / (kMaxNg * kMaxNg)][i % (kMaxNg * kMaxNg)] = tab.t1[i / (kMaxNg * kMaxNg)][(i / kMaxNg) % kMaxNg][i % kMaxNg];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t t = tb0 + (int64_t)blockIdx.x * kGWarps + w;
+  if (t >= tb1) return;
+  const int ng = tab.ng, m3 = ng * ng * ng;
+  float *mine = loc + t * m3;
+  for (int p = lane; p < m3; p += 32) res[w][p] = raw[t * m3 + p];
+  float cpar = 0.f;
+  if (level >= 3) {
+    const int box = tgt_box[t];
+    const int tp = box_tgt[parent[box]];
+    const int o = (int)(key[box] & 7u);
+    const float *pl = loc + (int64_t)tp * m3;
+    for (int p = lane; p < m3; p += 32) bufA[w][p] = pl[p];
+    __syncwarp();
+    apply_axis(T[o & 1], true, 0, ng, bufA[w], bufB[w], false);
+    apply_axis(T[(o >> 1) & 1], true, 1, ng, bufB[w], bufA[w], false);
+    apply_axis(T[(o >> 2) & 1], true, 2, ng, bufA[w], res[w], true);
+    cpar = locc[tp];
+  }
+  __syncwarp();
+  float s = 0.f;
+  for (int p = lane; p < m3; p += 32) s += res[w][p];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  const float mean = s / (float)m3;
+  for (int p = lane; p < m3; p += 32) mine[p] = res[w][p] - mean;
+  if (lane == 0) locc[t] = cpar + (mean + m2lc[t]);
+}
+
+// 1-D Lagrange weights and derivatives, FP32.
+__device__ __forceinline__ void lagrange_f(const GridletTables &tb, float t, float *w, float *dw) {
+  const int ng = tb.ng;
+  float diff[kMaxNg];
+  for (int k = 0; k < ng; ++k) diff[k] = t - tb.node[k];
+  for (int j = 0; j < ng; ++j) {
+    float v = tb.inv_den[j], d = 0.f;
+    for (int k = 0; k < ng; ++k) {
+      if (k == j) continue;
+      d = d * diff[k] + v;
+      v *= diff[k];
+    }
+    w[j] = v;
+    dw[j] = d;
+  }
+}
+
+// Far field at the particles of each leaf: phi = c + sum_p delta_p prod ell,
+// a = -(1/L) sum_p delta_p grad_xi prod ell (Eq. phix and its gradient).
+__global__ void __launch_bounds__(kThreads) k_g2p(int64_t lb, int64_t le, const int *__restrict__ leaf_box,
+                                                  const int *__restrict__ box_tgt, LevelTable lt,
+                                                  GridletTables tb, double ox, double oy, double oz,
+                                                  double side, const uint64_t *__restrict__ key,
+                                                  const int *__restrict__ beg, const int *__restrict__ end,
+                                                  const PM *__restrict__ spm,
+                                                  const float *__restrict__ loc,
+                                                  const float *__restrict__ locc,
+                                                  float4 *__restrict__ far) {
+  __shared__ float dl[kWarpsPerBlock][512];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t item = lb + (int64_t)blockIdx.x * kWarpsPerBlock + w;
+  if (item >= le) return;
+  const int box = leaf_box[item];
+  const int t = box_tgt[box];
+  const int ng = tb.ng, m3 = ng * ng * ng;
+  for (int p = lane; p < m3; p += 32) dl[w][p] = loc[(int64_t)t * m3 + p];
+  const float c0 = locc[t];
+  __syncwarp();
+  const int l = level_of(lt, box);
+  const double L = side / (double)(1u << l);
+  const uint64_t k = key[box];
+  const double cc[3] = {(double)compact3(k) + 0.5, (double)compact3(k >> 1) + 0.5,
+                        (double)compact3(k >> 2) + 0.5};
+  const double o[3] = {ox, oy, oz};
+  const float invL = (float)(1.0 / L);
+  for (int i = beg[box] + lane; i < end[box]; i += 32) {
+    const PM q = spm[i];
+    const double xs[3] = {q.x, q.y, q.z};
+    float wv[3][kMaxNg], dw[3][kMaxNg];
+    for (int d = 0; d < 3; ++d) lagrange_f(tb, (float)((xs[d] - o[d]) / L - cc[d]), wv[d], dw[d]);
+    float f = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    for (int pz = 0; pz < ng; ++pz)
+      for (int py = 0; py < ng; ++py) {
+        const float wyz = wv[1][py] * wv[2][pz], dyz = dw[1][py] * wv[2][pz], ydz = wv[1][py] * dw[2][pz];
+        for (int px = 0; px < ng; ++px) {
+          const float v = dl[w][px + ng * (py + ng * pz)];
+          f += v * wv[0][px] * wyz;
+          gx += v * dw[0][px] * wyz;
+          gy += v * wv[0][px] * dyz;
+          gz += v * wv[0][px] * ydz;
+        }
+      }
+    far[i] = make_float4(c0 + f, -gx * invL, -gy * invL, -gz * invL);
+  }
+}
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// Near zone of each leaf by direct summation (one warp per leaf). The G lanes
+// of a target particle split the sources; sums are Kahan compensated. Adds
+// the far field and writes the caller-ordered outputs.
+__global__ void __launch_bounds__(kThreads) k_p2p(int64_t nleaf, const int *__restrict__ leaf_box,
+                                                  const int *__restrict__ nb, const int *__restrict__ beg,
+                                                  const int *__restrict__ end, const float4 *__restrict__ hi,
+                                                  const float4 *__restrict__ lo,
+                                                  const float4 *__restrict__ far,
+                                                  const uint32_t *__restrict__ perm, float eps2,
+                                                  float *__restrict__ out_phi, float *__restrict__ out_acc) {
+  __shared__ float4 shi[kWarpsPerBlock][32], slo[kWarpsPerBlock][32];
+  __shared__ int sidx[kWarpsPerBlock][32];
+  __shared__ int rb[kWarpsPerBlock][27], re[kWarpsPerBlock][27];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + w;
+  if (item >= nleaf) return;
+  const int box = leaf_box[item];
+  if (lane < 27) {
+    const int q = nb[(int64_t)box * 27 + lane];
+    rb[w][lane] = q >= 0 ? beg[q] : 0;
+    re[w][lane] = q >= 0 ? end[q] : 0;
+  }
+  __syncwarp();
+  const int tb = beg[box], te = end[box];
+  const int nt = te - tb;
+  int G = 1;
+  if (nt <= 16) {
+    G = 2;
+    while (nt * G * 2 <= 32 && G < 32) G *= 2;
+  }
+  const int per = 32 / G;  // targets per pass
+  for (int t0 = tb; t0 < te; t0 += per) {
+    const int ti = t0 + lane / G, sub = lane % G;
+    const bool active = ti < te;
+    float4 mh = make_float4(0.f, 0.f, 0.f, 0.f), ml = mh;
+    if (active) {
+      mh = hi[ti];
+      ml = lo[ti];
+    }
+    float sp = 0.f, cp = 0.f, sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
+    for (int r = 0; r < 27; ++r) {
+      const int b = rb[w][r], e = re[w][r];
+      for (int c0 = b; c0 < e; c0 += 32) {
+        const int j = c0 + lane;
+        if (j < e) {
+          shi[w][lane] = hi[j];
+          slo[w][lane] = lo[j];
+          sidx[w][lane] = j;
+        }
+        __syncwarp();
+        const int cnt = min(32, e - c0);
+        if (active) {
+          for (int k = sub; k < cnt; k += G) {
+            const float4 h = shi[w][k], q = slo[w][k];
+            const float dx = (h.x - mh.x) + (q.x - ml.x);
+            const float dy = (h.y - mh.y) + (q.y - ml.y);
+            const float dz = (h.z - mh.z) + (q.z - ml.z);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+            float ir = rsqrtf(r2);
+            if (sidx[w][k] == ti) ir = 0.f;
+            const float mir = h.w * ir;
+            const float mir3 = mir * ir * ir;
+            kahan_add(sp, cp, -mir);
+            kahan_add(sx, cx, mir3 * dx);
+            kahan_add(sy, cy, mir3 * dy);
+            kahan_add(sz, cz, mir3 * dz);
+          }
+        }
+        __syncwarp();
+      }
+    }
+    float vp = sp - cp, vx = sx - cx, vy = sy - cy, vz = sz - cz;
+    for (int off = 1; off < G; off <<= 1) {
+      vp += __shfl_xor_sync(0xffffffffu, vp, off);
+      vx += __shfl_xor_sync(0xffffffffu, vx, off);
+      vy += __shfl_xor_sync(0xffffffffu, vy, off);
+      vz += __shfl_xor_sync(0xffffffffu, vz, off);
+    }
+    if (active && sub == 0) {
+      const float4 f = far[ti];
+      const uint32_t o = perm[ti];
+      if (out_phi) out_phi[o] = f.x + vp;
+      if (out_acc) {
+        out_acc[3 * (int64_t)o] = f.y + vx;
+        out_acc[3 * (int64_t)o + 1] = f.z + vy;
+        out_acc[3 * (int64_t)o + 2] = f.w + vz;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Green function transform, FP64. g(d) = 1/sqrt(h^2 |d|_p^2 + eps^2) on the
+// P^3 periodic grid, g(0) := g(unit offset). g is real and even in every
+// axis, so its transform is the separable cosine sum
+//   G^(k) = sum_d g(d) cos(2 pi kx dx/P) cos(2 pi ky dy/P) cos(2 pi kz dz/P),
+// real and even; only k in [0, P/2]^3 is stored.
+__global__ void k_green_pass(int P, int pass, double h, double eps, const double *__restrict__ in,
+                             double *__restrict__ out) {
+  const int H = P / 2 + 1;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)H * H * H) return;
+  const int a = (int)(i % H), b = (int)((i / H) % H), c = (int)(i / ((int64_t)H * H));
+  // pass 0: a = kx, (b, c) = (|dy|, |dz|); pass 1: a = kx, b = ky, c = |dz|; pass 2: (a, b, c) = k
+  const int k = pass == 0 ? a : (pass == 1 ? b : c);
+  double s = 0.0;
+  for (int d = 0; d < P; ++d) {
+    const int dr = d <= P / 2 ? d : P - d;
+    double v;
+    if (pass == 0) {
+      double r2 = (double)dr * dr + (double)b * b + (double)c * c;
+      if (r2 == 0.0) r2 = 1.0;
+      v = 1.0 / sqrt(h * h * r2 + eps * eps);
+    } else if (pass == 1) {
+      v = in[a + (int64_t)H * (dr + (int64_t)H * c)];
+    } else {
+      v = in[a + (int64_t)H * (b + (int64_t)H * dr)];
+    }
+    s += v * cospi(2.0 * (double)((k * d) % P) / (double)P);
+  }
+  out[i] = s;
+}
+
+// Stores -G^/P^3 in FP32 with the DC term removed: G^(0)/P^3 is the mean m of
+// G over the periodic grid, and convolving with G - m instead of G changes every
+// output by the same constant m * sum(rho). That constant is added back to the
+// target's local constant (it carries no force), while the FP32 transform no
+// longer carries the large DC product, the dominant term of its round-off.
+__global__ void k_green_store(int64_t n, const double *__restrict__ in, double scale, float *__restrict__ out,
+                              float *__restrict__ mean_out, double inv_p3) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *mean_out = (float)(in[0] * inv_p3);
+  if (i < n) out[i] = i == 0 ? 0.f : (float)(in[i] * scale);
+}
+
+}  // namespace
+
+hpm_status precompute_green(hpm_plan_s *pl, cudaStream_t st) {
+  const int P = 8 * pl->ng, H = P / 2 + 1;
+  const int64_t h3 = (int64_t)H * H * H;
+  const int D = pl->max_depth;
+  pl->ghat_level_stride = h3;
+  HPM_TRY(pl->ghat.ensure(sizeof(float) * h3 * (D + 1), st));
+  HPM_CUDA(cudaMemsetAsync(pl->ghat.p, 0, sizeof(float) * h3 * (D + 1), st));
+  HPM_TRY(pl->gmean.ensure(sizeof(float) * (D + 1), st));
+  HPM_CUDA(cudaMemsetAsync(pl->gmean.p, 0, sizeof(float) * (D + 1), st));
+  double *a = nullptr, *b = nullptr;
+  HPM_CUDA(cudaMallocAsync((void **)&a, sizeof(double) * h3, st));
+  HPM_CUDA(cudaMallocAsync((void **)&b, sizeof(double) * h3, st));
+  const double scale = -1.0 / ((double)P * P * P);
+  for (int l = 2; l <= D; ++l) {
+    const double h = pl->dom.side / (double)(1u << l) / (double)pl->ng;
+    k_green_pass<<<blocks_for(h3), kThreads, 0, st>>>(P, 0, h, pl->green.eps, nullptr, a);
+    HPM_LAUNCHED((int64_t *)nullptr);
+    k_green_pass<<<blocks_for(h3), kThreads, 0, st>>>(P, 1, h, pl->green.eps, a, b);
+    HPM_LAUNCHED((int64_t *)nullptr);
+    k_green_pass<<<blocks_for(h3), kThreads, 0, st>>>(P, 2, h, pl->green.eps, b, a);
+    HPM_LAUNCHED((int64_t *)nullptr);
+    k_green_store<<<blocks_for(h3), kThreads, 0, st>>>(h3, a, scale, pl->ghat.as<float>() + h3 * l,
+                                                       pl->gmean.as<float>() + l, -scale);
+    HPM_LAUNCHED((int64_t *)nullptr);
+  }
+  HPM_CUDA(cudaFreeAsync(a, st));
+  HPM_CUDA(cudaFreeAsync(b, st));
+  return HPM_OK;
+}
+
+static LevelTable make_levels(const hpm_plan_s *pl) {
+  LevelTable lt{};
+  lt.nlev = pl->max_depth + 1;
+  for (int l = 0; l <= pl->max_depth + 1; ++l) lt.off[l] = pl->lvl_off[l];
+  return lt;
+}
+
+static void record(hpm_plan_s *pl, int i, cudaStream_t st) {
+  if (pl->events_ready) cudaEventRecord(pl->ev[i], st);
+}
+
+hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, float *d_phi, float *d_acc,
+                 cudaStream_t st) {
+  TreeDev &t = pl->t;
+  SolveDev &s = pl->s;
+  const int64_t n = pl->n;
+  int64_t launches = 0;
+  pl->stats.m2l_launches = 0;
+  pl->stats.m2l_targets = pl->ntgt;
+  if (n == 0) return HPM_OK;
+  const int ng = pl->ng, m3 = ng * ng * ng;
+  const int D = pl->max_depth;
+  const int64_t off2 = D >= 2 ? pl->lvl_off[2] : pl->nbox;
+  const int64_t nrow = pl->nbox - off2;
+  HPM_TRY(t.spm.ensure(sizeof(PM) * n + 2 * sizeof(float4) * n, st));
+  HPM_TRY(s.grid.ensure(sizeof(float) * m3 * (nrow > 0 ? nrow : 1), st));
+  HPM_TRY(s.loc.ensure(sizeof(float) * m3 * (pl->ntgt > 0 ? pl->ntgt : 1), st));
+  HPM_TRY(s.m2l_raw.ensure(sizeof(float) * m3 * (pl->ntgt > 0 ? pl->ntgt : 1), st));
+  HPM_TRY(s.locc.ensure(sizeof(float) * (pl->ntgt > 0 ? pl->ntgt : 1), st));
+  HPM_TRY(s.m2lc.ensure(sizeof(float) * (pl->ntgt > 0 ? pl->ntgt : 1), st));
+  HPM_TRY(s.far.ensure(sizeof(float4) * n, st));
+  PM *spm = t.spm.as<PM>();
+  float4 *hi = reinterpret_cast<float4 *>(spm + n);
+  float4 *lo = hi + n;
+  const LevelTable lt = make_levels(pl);
+  const double *o = pl->dom.origin;
+
+  record(pl, 0, st);
+  k_gather<<<blocks_for(n), kThreads, 0, st>>>(n, t.perm.as<uint32_t>(), d_pos, d_mass, o[0], o[1], o[2],
+                                               spm, hi, lo);
+  HPM_LAUNCHED(&launches);
+  record(pl, 1, st);
+  if (pl->np2g) {
+    k_p2g<<<warp_blocks(pl->np2g), kThreads, 0, st>>>(pl->np2g, t.p2g_box.as<int>(), lt, pl->tab, o[0], o[1],
+                                                      o[2], pl->dom.side, t.box_key.as<uint64_t>(),
+                                                      t.box_beg.as<int>(), t.box_end.as<int>(), spm, off2,
+                                                      s.grid.as<float>());
+    HPM_LAUNCHED(&launches);
+  }
+  record(pl, 2, st);
+  for (int l = pl->depth_reached - 1; l >= 2; --l) {
+    const int64_t b = pl->lvl_off[l], e = pl->lvl_off[l + 1];
+    if (e <= b) continue;
+    k_m2m<<<gwarp_blocks(e - b), kGThreads, 0, st>>>(b, e, pl->tab, t.box_flags.as<uint8_t>(),
+                                                   t.box_child.as<int>(), off2, s.grid.as<float>());
+    HPM_LAUNCHED(&launches);
+  }
+  record(pl, 3, st);
+  if (pl->ntgt) {
+    int64_t ml = 0;
+    HPM_TRY(launch_m2l(pl, st, &ml));
+    launches += ml;
+    pl->stats.m2l_launches = ml;
+  }
+  record(pl, 4, st);
+  for (int l = 2; l <= pl->depth_reached; ++l) {
+    const int64_t b = pl->tgt_lvl_off[l], e = pl->tgt_lvl_off[l + 1];
+    if (e <= b) continue;
+    k_l2l<<<gwarp_blocks(e - b), kGThreads, 0, st>>>(b, e, l, pl->tab, t.tgt_box.as<int>(), t.box_tgt.as<int>(),
+                                                   t.box_parent.as<int>(), t.box_key.as<uint64_t>(),
+                                                   s.m2l_raw.as<float>(), s.loc.as<float>(), s.locc.as<float>(),
+                                                   s.m2lc.as<float>());
+    HPM_LAUNCHED(&launches);
+  }
+  record(pl, 5, st);
+  HPM_CUDA(cudaMemsetAsync(s.far.p, 0, sizeof(float4) * n, st));
+  {
+    const int64_t lb = pl->leaf_lvl_off[2 <= D ? 2 : D + 1], le = pl->nleaf;
+    if (le > lb) {
+      k_g2p<<<warp_blocks(le - lb), kThreads, 0, st>>>(lb, le, t.leaf_box.as<int>(), t.box_tgt.as<int>(), lt,
+                                                       pl->tab, o[0], o[1], o[2], pl->dom.side,
+                                                       t.box_key.as<uint64_t>(), t.box_beg.as<int>(),
+                                                       t.box_end.as<int>(), spm, s.loc.as<float>(),
+                                                       s.locc.as<float>(), s.far.as<float4>());
+      HPM_LAUNCHED(&launches);
+    }
+  }
+  record(pl, 6, st);
+  {
+    const float eps2 = (float)(pl->green.eps * pl->green.eps);
+    k_p2p<<<warp_blocks(pl->nleaf), kThreads, 0, st>>>(pl->nleaf, t.leaf_box.as<int>(), t.box_nb.as<int>(),
+                                                       t.box_beg.as<int>(), t.box_end.as<int>(), hi, lo,
+                                                       s.far.as<float4>(), t.perm.as<uint32_t>(), eps2,
+                                                       d_phi, d_acc);
+    HPM_LAUNCHED(&launches);
+  }
+  record(pl, 7, st);
+  pl->stats.launches += launches;
+  return HPM_OK;
+}
+
+}  // namespace hpm

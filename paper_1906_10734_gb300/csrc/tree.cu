@@ -1,0 +1,415 @@
+// Device oct-tree build (Sec. 1): Morton keys from FP64 positions, stable
+// sort, then level by level the needed boxes with their particle ranges,
+// child maps and 27-neighbour tables.
+//
+// Adaptive zones ("virtual completion", the reading used where the paper is
+// silent on non-uniform trees): at level l the sources are all nonempty
+// level-l dyadic boxes. A level-l box is needed iff its parent lies in the
+// 3^3 neighbourhood of an internal cell at level l-1; those boxes hold every
+// interaction-zone source of the cells at level l and every near box of the
+// leaves at level l. The set is closed under taking parents, so it forms a
+// tree of its own and the neighbours of a cell are the children of the
+// neighbours of its parent.
+#include <utility>
+
+#include "hpm_internal.cuh"
+
+namespace hpm {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1fffffu;
+  x = (x | x << 32) & 0x1f00000000ffffull;
+  x = (x | x << 16) & 0x1f0000ff0000ffull;
+  x = (x | x << 8) & 0x100f00f00f00f00full;
+  x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+  x = (x | x << 2) & 0x1249249249249249ull;
+  return x;
+}
+
+__device__ __forceinline__ uint32_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ull;
+  x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+  x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+  x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+  x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+  x = (x ^ (x >> 32)) & 0x1fffffull;
+  return (uint32_t)x;
+}
+
+// Unit coordinate v = (x - o)/S in IEEE FP64 (no contraction); outside
+// [0, 1] (or NaN) is an error; 21-bit cell coordinate min(floor(v 2^21),
+// 2^21 - 1); level-D key from the top D bits of each coordinate.
+__global__ void k_keys(const double *__restrict__ pos, int64_t n, double ox, double oy, double oz,
+                       double side, int depth, uint64_t *__restrict__ keys, int *__restrict__ err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double o[3] = {ox, oy, oz};
+  uint32_t c[3];
+  bool bad = false;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double v = __ddiv_rn(__dsub_rn(pos[3 * i + d], o[d]), side);
+    if (!(v >= 0.0 && v <= 1.0)) {
+      bad = true;
+      v = 0.0;
+    }
+    const double s = floor(__dmul_rn(v, 2097152.0));
+    const uint32_t q = s >= 2097151.0 ? 2097151u : (uint32_t)s;
+    c[d] = q >> (kMortonBits - depth);
+  }
+  if (bad) atomicOr(err, kErrDomain);
+  keys[i] = spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+}
+
+__global__ void k_root(int64_t n, int depth, int leaf_max, uint64_t *key, int *beg, int *end,
+                       int *parent, uint8_t *flags, int *child, int *nb, int *counters) {
+  key[0] = 0;
+  beg[0] = 0;
+  end[0] = (int)n;
+  parent[0] = -1;
+  const bool internal = depth > 0 && n > leaf_max;
+  flags[0] = kReal | (internal ? kInternal : kLeaf);
+  for (int k = 0; k < 8; ++k) child[k] = -1;
+  for (int k = 0; k < 27; ++k) nb[k] = k == 13 ? 0 : -1;
+  counters[0] = 1;                     // real cells at level 0
+  counters[32 + 0] = internal ? 0 : 1; // leaves at level 0
+}
+
+__global__ void k_expand(int64_t pb, int64_t pe, uint8_t *__restrict__ flags,
+                         const int *__restrict__ nb) {
+  const int64_t i = pb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= pe || !(flags[i] & kInternal)) return;
+  for (int k = 0; k < 27; ++k) {
+    const int q = nb[i * 27 + k];
+    if (q >= 0) flags[q] |= kExpand;  // only this bit is written here: races are benign
+  }
+}
+
+// First index in [lo, hi) whose level-l key is >= kc.
+__device__ __forceinline__ int lower_bound_key(const uint64_t *__restrict__ skeys, int lo, int hi,
+                                               int shift, uint64_t kc) {
+  while (lo < hi) {
+    const int mid = lo + ((hi - lo) >> 1);
+    if ((skeys[mid] >> shift) < kc) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void octant_bounds(const uint64_t *__restrict__ skeys, int b, int e,
+                                              int shift, uint64_t kparent, int bnd[9]) {
+  bnd[0] = b;
+  bnd[8] = e;
+#pragma unroll
+  for (int o = 1; o < 8; ++o)
+    bnd[o] = lower_bound_key(skeys, bnd[o - 1], e, shift, (kparent << 3) | (uint64_t)o);
+}
+
+__global__ void k_count_children(int64_t pb, int64_t pe, const uint8_t *__restrict__ flags,
+                                 const uint64_t *__restrict__ key, const int *__restrict__ beg,
+                                 const int *__restrict__ end, const uint64_t *__restrict__ skeys,
+                                 int shift, int *__restrict__ cnt) {
+  const int64_t i = pb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= pe) return;
+  int c = 0;
+  if (flags[i] & kExpand) {
+    int bnd[9];
+    octant_bounds(skeys, beg[i], end[i], shift, key[i], bnd);
+#pragma unroll
+    for (int o = 0; o < 8; ++o) c += bnd[o + 1] > bnd[o];
+  }
+  cnt[i - pb] = c;
+}
+
+__global__ void k_fill_children(int64_t pb, int64_t pe, int64_t cb, int level, int depth,
+                                int leaf_max, uint8_t *__restrict__ flags, uint64_t *__restrict__ key,
+                                int *__restrict__ beg, int *__restrict__ end,
+                                int *__restrict__ parent, int *__restrict__ child,
+                                const uint64_t *__restrict__ skeys, int shift,
+                                const int *__restrict__ off, int *__restrict__ counters) {
+  const int64_t q = pb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= pe) return;
+  if (!(flags[q] & kExpand)) {
+#pragma unroll
+    for (int o = 0; o < 8; ++o) child[q * 8 + o] = -1;
+    return;
+  }
+  int bnd[9];
+  const uint64_t kq = key[q];
+  octant_bounds(skeys, beg[q], end[q], shift, kq, bnd);
+  const bool real = flags[q] & kInternal;
+  int64_t idx = cb + off[q - pb];
+  int nreal = 0, nleaf = 0;
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    if (bnd[o + 1] > bnd[o]) {
+      child[q * 8 + o] = (int)idx;
+      key[idx] = (kq << 3) | (uint64_t)o;
+      beg[idx] = bnd[o];
+      end[idx] = bnd[o + 1];
+      parent[idx] = (int)q;
+      const bool internal = real && level < depth && (bnd[o + 1] - bnd[o]) > leaf_max;
+      const bool leaf = real && !internal;
+      flags[idx] = (real ? kReal : 0) | (internal ? kInternal : 0) | (leaf ? kLeaf : 0);
+      nreal += real;
+      nleaf += leaf;
+      ++idx;
+    } else {
+      child[q * 8 + o] = -1;
+    }
+  }
+  if (nreal) atomicAdd(&counters[level], nreal);
+  if (nleaf) atomicAdd(&counters[32 + level], nleaf);
+}
+
+__global__ void k_neighbours(int64_t cb, int64_t ce, int level, const uint8_t *__restrict__ flags,
+                             const uint64_t *__restrict__ key, const int *__restrict__ parent,
+                             const int *__restrict__ child, int *__restrict__ nb) {
+  const int64_t i = cb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ce) return;
+  if (!(flags[i] & kReal)) {
+    for (int k = 0; k < 27; ++k) nb[i * 27 + k] = -1;
+    return;
+  }
+  const uint64_t k0 = key[i];
+  const int c[3] = {(int)compact3(k0), (int)compact3(k0 >> 1), (int)compact3(k0 >> 2)};
+  const int side = 1 << level;
+  const int p = parent[i];
+  for (int k = 0; k < 27; ++k) {
+    const int n[3] = {c[0] + k % 3 - 1, c[1] + (k / 3) % 3 - 1, c[2] + k / 9 - 1};
+    int r = -1;
+    if (n[0] >= 0 && n[0] < side && n[1] >= 0 && n[1] < side && n[2] >= 0 && n[2] < side) {
+      const int dp = ((n[0] >> 1) - (c[0] >> 1) + 1) + 3 * ((n[1] >> 1) - (c[1] >> 1) + 1) +
+                     9 * ((n[2] >> 1) - (c[2] >> 1) + 1);
+      const int q = nb[(int64_t)p * 27 + dp];
+      if (q >= 0) r = child[(int64_t)q * 8 + ((n[0] & 1) | ((n[1] & 1) << 1) | ((n[2] & 1) << 2))];
+    }
+    nb[i * 27 + k] = r;
+  }
+}
+
+// Work-list selection. mode 0: real cells; 1: leaves; 2: boxes that get their
+// effective masses by P2G (not internal).
+__global__ void k_select(int64_t b, int64_t e, const uint8_t *__restrict__ flags, int mode,
+                         int *__restrict__ sel) {
+  const int64_t i = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= e) return;
+  const uint8_t f = flags[i];
+  int v;
+  if (mode == 0) v = (f & kReal) != 0;
+  else if (mode == 1) v = (f & kLeaf) != 0;
+  else v = (f & kInternal) == 0;
+  sel[i - b] = v;
+}
+
+__global__ void k_compact(int64_t b, int64_t e, const int *__restrict__ sel,
+                          const int *__restrict__ pos, int *__restrict__ out) {
+  const int64_t i = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= e) return;
+  if (sel[i - b]) out[pos[i - b]] = (int)i;
+}
+
+__global__ void k_box_tgt(int64_t ntgt, const int *__restrict__ tgt_box, int *__restrict__ box_tgt) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < ntgt) box_tgt[tgt_box[t]] = (int)t;
+}
+
+hpm_status ensure_boxes(TreeDev &t, int64_t nbox, cudaStream_t st) {
+  HPM_TRY(t.box_key.ensure(sizeof(uint64_t) * nbox, st, true));
+  HPM_TRY(t.box_beg.ensure(sizeof(int) * nbox, st, true));
+  HPM_TRY(t.box_end.ensure(sizeof(int) * nbox, st, true));
+  HPM_TRY(t.box_parent.ensure(sizeof(int) * nbox, st, true));
+  HPM_TRY(t.box_flags.ensure(sizeof(uint8_t) * nbox, st, true));
+  HPM_TRY(t.box_child.ensure(sizeof(int) * 8 * nbox, st, true));
+  HPM_TRY(t.box_nb.ensure(sizeof(int) * 27 * nbox, st, true));
+  return HPM_OK;
+}
+
+// Compacts the boxes in [b, e) selected by `mode` into out (resized); returns the count.
+hpm_status select_boxes(hpm_plan_s *pl, int64_t b, int64_t e, int mode, DevBuf &out, int64_t *count,
+                        cudaStream_t st, int64_t *launches) {
+  TreeDev &t = pl->t;
+  const int64_t n = e - b;
+  *count = 0;
+  if (n <= 0) return HPM_OK;
+  HPM_TRY(t.cnt.ensure(sizeof(int) * n, st));
+  HPM_TRY(t.off.ensure(sizeof(int) * (n + 1), st));
+  k_select<<<blocks_for(n), kThreads, 0, st>>>(b, e, t.box_flags.as<uint8_t>(), mode, t.cnt.as<int>());
+  HPM_LAUNCHED(launches);
+  HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), n, t.counters.as<int>() + 64, t.keys_alt,
+                             st, launches));
+  int h = 0;
+  HPM_CUDA(cudaMemcpyAsync(&h, t.counters.as<int>() + 64, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HPM_CUDA(cudaStreamSynchronize(st));
+  *count = h;
+  HPM_TRY(out.ensure(sizeof(int) * (h > 0 ? h : 1), st));
+  k_compact<<<blocks_for(n), kThreads, 0, st>>>(b, e, t.cnt.as<int>(), t.off.as<int>(), out.as<int>());
+  HPM_LAUNCHED(launches);
+  return HPM_OK;
+}
+
+}  // namespace
+
+hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream_t st) {
+  TreeDev &t = pl->t;
+  const int D = pl->max_depth;
+  int64_t launches = 0;
+  pl->built = false;
+  pl->n = n;
+  HPM_TRY(t.err.ensure(sizeof(int) * 4, st));
+  HPM_TRY(t.counters.ensure(sizeof(int) * 128, st));
+  HPM_CUDA(cudaMemsetAsync(t.err.p, 0, sizeof(int) * 4, st));
+  HPM_CUDA(cudaMemsetAsync(t.counters.p, 0, sizeof(int) * 128, st));
+
+  pl->lvl_off.assign(D + 2, 0);
+  pl->depth_reached = -1;
+  pl->nbox = pl->ntgt = pl->nleaf = pl->np2g = pl->ncell = 0;
+  pl->tgt_lvl_off.assign(D + 2, 0);
+  pl->leaf_lvl_off.assign(D + 2, 0);
+  if (n == 0) {
+    pl->built = true;
+    pl->stats.launches = 0;
+    return HPM_OK;
+  }
+
+  // keys and the stable sort by (level-D key, index)
+  HPM_TRY(t.keys.ensure(sizeof(uint64_t) * n, st));
+  HPM_TRY(t.keys_alt.ensure(sizeof(uint64_t) * n, st));
+  HPM_TRY(t.perm.ensure(sizeof(uint32_t) * n, st));
+  HPM_TRY(t.perm_alt.ensure(sizeof(uint32_t) * n, st));
+  k_keys<<<blocks_for(n), kThreads, 0, st>>>(d_pos, n, pl->dom.origin[0], pl->dom.origin[1],
+                                             pl->dom.origin[2], pl->dom.side, D, t.keys.as<uint64_t>(),
+                                             t.err.as<int>());
+  HPM_LAUNCHED(&launches);
+  uint64_t *k0 = t.keys.as<uint64_t>(), *k1 = t.keys_alt.as<uint64_t>();
+  uint32_t *v0 = t.perm.as<uint32_t>(), *v1 = t.perm_alt.as<uint32_t>();
+  DevBuf &scratch = t.off;
+  HPM_TRY(radix_sort_pairs(k0, k1, v0, v1, n, 3 * D, scratch, st, &launches));
+  // keep the sorted arrays in keys/perm
+  if (k0 != t.keys.as<uint64_t>()) {
+    std::swap(t.keys.p, t.keys_alt.p);
+    std::swap(t.keys.cap, t.keys_alt.cap);
+  }
+  if (v0 != t.perm.as<uint32_t>()) {
+    std::swap(t.perm.p, t.perm_alt.p);
+    std::swap(t.perm.cap, t.perm_alt.cap);
+  }
+  const uint64_t *skeys = t.keys.as<uint64_t>();
+
+  // level 0
+  int64_t cap = t.box_key.cap / sizeof(uint64_t);
+  if (cap < 1024) cap = 1024;
+  HPM_TRY(ensure_boxes(t, cap, st));
+  k_root<<<1, 1, 0, st>>>(n, D, pl->opts.leaf_max, t.box_key.as<uint64_t>(), t.box_beg.as<int>(),
+                          t.box_end.as<int>(), t.box_parent.as<int>(), t.box_flags.as<uint8_t>(),
+                          t.box_child.as<int>(), t.box_nb.as<int>(), t.counters.as<int>());
+  HPM_LAUNCHED(&launches);
+  pl->lvl_off[0] = 0;
+  pl->lvl_off[1] = 1;
+  int reached = 0;
+  for (int l = 1; l <= D; ++l) {
+    const int64_t pb = pl->lvl_off[l - 1], pe = pl->lvl_off[l];
+    const int64_t np = pe - pb;
+    const int shift = 3 * (D - l);
+    k_expand<<<blocks_for(np), kThreads, 0, st>>>(pb, pe, t.box_flags.as<uint8_t>(), t.box_nb.as<int>());
+    HPM_LAUNCHED(&launches);
+    HPM_TRY(t.cnt.ensure(sizeof(int) * np, st));
+    HPM_TRY(t.off.ensure(sizeof(int) * (np + 1), st));
+    k_count_children<<<blocks_for(np), kThreads, 0, st>>>(pb, pe, t.box_flags.as<uint8_t>(),
+                                                          t.box_key.as<uint64_t>(), t.box_beg.as<int>(),
+                                                          t.box_end.as<int>(), skeys, shift,
+                                                          t.cnt.as<int>());
+    HPM_LAUNCHED(&launches);
+    HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), np, t.counters.as<int>() + 64,
+                               t.keys_alt, st, &launches));
+    int hv[2] = {0, 0};
+    HPM_CUDA(cudaMemcpyAsync(&hv[0], t.counters.as<int>() + 64, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaMemcpyAsync(&hv[1], t.err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaStreamSynchronize(st));
+    if (hv[1] & kErrDomain) return HPM_ERR_OUT_OF_DOMAIN;
+    const int64_t nc = hv[0];
+    if (nc == 0) {
+      // still write the (empty) child maps of level l-1
+      k_fill_children<<<blocks_for(np), kThreads, 0, st>>>(
+          pb, pe, pe, l, D, pl->opts.leaf_max, t.box_flags.as<uint8_t>(), t.box_key.as<uint64_t>(),
+          t.box_beg.as<int>(), t.box_end.as<int>(), t.box_parent.as<int>(), t.box_child.as<int>(), skeys,
+          shift, t.off.as<int>(), t.counters.as<int>());
+      HPM_LAUNCHED(&launches);
+      for (int r = l; r <= D; ++r) pl->lvl_off[r + 1] = pe;
+      break;
+    }
+    const int64_t need = pe + nc;
+    if (need > cap) {
+      cap = need + need / 2;
+      HPM_TRY(ensure_boxes(t, cap, st));
+    }
+    k_fill_children<<<blocks_for(np), kThreads, 0, st>>>(
+        pb, pe, pe, l, D, pl->opts.leaf_max, t.box_flags.as<uint8_t>(), t.box_key.as<uint64_t>(),
+        t.box_beg.as<int>(), t.box_end.as<int>(), t.box_parent.as<int>(), t.box_child.as<int>(), skeys,
+        shift, t.off.as<int>(), t.counters.as<int>());
+    HPM_LAUNCHED(&launches);
+    k_neighbours<<<blocks_for(nc), kThreads, 0, st>>>(pe, need, l, t.box_flags.as<uint8_t>(),
+                                                      t.box_key.as<uint64_t>(), t.box_parent.as<int>(),
+                                                      t.box_child.as<int>(), t.box_nb.as<int>());
+    HPM_LAUNCHED(&launches);
+    pl->lvl_off[l + 1] = need;
+    reached = l;
+  }
+  if (D == 0) {
+    // the root is the only box; its children do not exist
+    pl->lvl_off[1] = 1;
+  }
+  {
+    // child maps of the deepest level are never filled: mark them empty
+    const int64_t b = pl->lvl_off[reached], e = pl->lvl_off[reached + 1];
+    if (e > b) HPM_CUDA(cudaMemsetAsync(t.box_child.as<int>() + b * 8, 0xff, sizeof(int) * 8 * (e - b), st));
+  }
+  for (int r = reached + 1; r <= D; ++r) pl->lvl_off[r + 1] = pl->lvl_off[reached + 1];
+  pl->nbox = pl->lvl_off[D + 1];
+
+  // per-level counts of cells and leaves
+  int hc[64];
+  HPM_CUDA(cudaMemcpyAsync(hc, t.counters.p, sizeof(int) * 64, cudaMemcpyDeviceToHost, st));
+  HPM_CUDA(cudaStreamSynchronize(st));
+  int depth_reached = 0;
+  int64_t ncell = 0, nleaf = 0;
+  for (int l = 0; l <= D; ++l) {
+    ncell += hc[l];
+    nleaf += hc[32 + l];
+    if (hc[l] > 0) depth_reached = l;
+  }
+  pl->depth_reached = depth_reached;
+  pl->ncell = ncell;
+  pl->tgt_lvl_off.assign(D + 2, 0);
+  pl->leaf_lvl_off.assign(D + 2, 0);
+  for (int l = 0; l <= D; ++l) {
+    pl->tgt_lvl_off[l + 1] = pl->tgt_lvl_off[l] + (l >= 2 ? hc[l] : 0);
+    pl->leaf_lvl_off[l + 1] = pl->leaf_lvl_off[l] + hc[32 + l];
+  }
+
+  // work lists: targets (cells at level >= 2), leaves, P2G boxes (level >= 2, not internal)
+  const int64_t off2 = D >= 2 ? pl->lvl_off[2] : pl->nbox;
+  int64_t cnt = 0;
+  HPM_TRY(select_boxes(pl, off2, pl->nbox, 0, t.tgt_box, &cnt, st, &launches));
+  pl->ntgt = cnt;
+  HPM_TRY(select_boxes(pl, 0, pl->nbox, 1, t.leaf_box, &cnt, st, &launches));
+  pl->nleaf = cnt;
+  HPM_TRY(select_boxes(pl, off2, pl->nbox, 2, t.p2g_box, &cnt, st, &launches));
+  pl->np2g = cnt;
+  HPM_TRY(t.box_tgt.ensure(sizeof(int) * (pl->nbox > 0 ? pl->nbox : 1), st));
+  HPM_CUDA(cudaMemsetAsync(t.box_tgt.p, 0xff, sizeof(int) * pl->nbox, st));
+  if (pl->ntgt) {
+    k_box_tgt<<<blocks_for(pl->ntgt), kThreads, 0, st>>>(pl->ntgt, t.tgt_box.as<int>(), t.box_tgt.as<int>());
+    HPM_LAUNCHED(&launches);
+  }
+  pl->stats.launches = launches;
+  pl->built = true;
+  return HPM_OK;
+}
+
+}  // namespace hpm

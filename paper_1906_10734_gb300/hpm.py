@@ -1,0 +1,252 @@
+"""ctypes binding of libhpm (include/hpm.h): argument marshalling only.
+
+Every step of the solve runs in the CUDA library. Torch tensors are accepted
+for device buffers and passed as raw pointers with the current CUDA stream.
+Importing this module fails loudly if the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhpm.so")
+
+HPM_OK = 0
+STATUS = {0: "HPM_OK", -1: "HPM_ERR_INVALID_ARG", -2: "HPM_ERR_OUT_OF_DOMAIN", -3: "HPM_ERR_OOM",
+          -4: "HPM_ERR_CUDA", -5: "HPM_ERR_TIMEOUT", -6: "HPM_ERR_NOT_BUILT", -7: "HPM_ERR_BUSY",
+          -8: "HPM_ERR_UNSUPPORTED"}
+HPM_GREEN_PLUMMER = 0
+HPM_FLAG_TIMINGS = 1
+HPM_FLAG_GENERIC_M2L = 2
+HPM_STAGE_MASSES, HPM_STAGE_M2L, HPM_STAGE_LOCAL = 1, 2, 3
+
+# Every symbol include/hpm.h declares, with its ctypes signature.
+_vp, _i32, _i64, _f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+
+
+class hpm_domain(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_double * 3), ("side", ctypes.c_double)]
+
+
+class hpm_green(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("eps", ctypes.c_double)]
+
+
+class hpm_plan_opts(ctypes.Structure):
+    _fields_ = [("leaf_max", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class hpm_lists_info(ctypes.Structure):
+    _fields_ = [("n_particles", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("n_targets", ctypes.c_int64),
+                ("n_leaves", ctypes.c_int64), ("n_boxes", ctypes.c_int64), ("max_depth", ctypes.c_int),
+                ("depth_reached", ctypes.c_int)]
+
+
+class hpm_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("ms_tree", "ms_p2g", "ms_m2m", "ms_m2l", "ms_l2l", "ms_g2p",
+                                              "ms_p2p", "ms_total")] + \
+               [("launches", ctypes.c_int64), ("m2l_launches", ctypes.c_int64), ("m2l_targets", ctypes.c_int64)]
+
+
+SIGNATURES = {
+    "hpm_plan": ([ctypes.POINTER(hpm_domain), _i32, _i32, ctypes.POINTER(hpm_green),
+                  ctypes.POINTER(hpm_plan_opts), ctypes.POINTER(_vp)], _i32),
+    "hpm_build_tree": ([_vp, _vp, _i64, _vp], _i32),
+    "hpm_solve": ([_vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "hpm_solve_host": ([_vp, _vp, _vp, _i64, _vp, _vp, _vp], _i32),
+    "hpm_get_lists_info": ([_vp, ctypes.POINTER(hpm_lists_info)], _i32),
+    "hpm_get_lists": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "hpm_get_stats": ([_vp, ctypes.POINTER(hpm_stats)], _i32),
+    "hpm_get_boxes": ([_vp, _vp, _vp, _vp], _i32),
+    "hpm_get_stage": ([_vp, _i32, _vp, _i64], _i32),
+    "hpm_destroy": ([_vp], _i32),
+    "hpm_status_str": ([_i32], ctypes.c_char_p),
+    "hpm_last_cuda_error": ([], ctypes.c_char_p),
+}
+
+
+class HpmError(RuntimeError):
+    def __init__(self, call: str, status: int):
+        self.status = status
+        detail = ""
+        if status == -4 and _lib is not None:
+            detail = " (" + _lib.hpm_last_cuda_error().decode() + ")"
+        super().__init__(f"{call}: {STATUS.get(status, status)}{detail}")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libhpm; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libhpm is not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(call: str, status: int):
+    if status != HPM_OK:
+        raise HpmError(call, status)
+
+
+def _ptr(t) -> int:
+    """Device pointer of a torch tensor (or an int address); None -> NULL."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def hpm_plan(origin=(0.0, 0.0, 0.0), side=1.0, max_depth=3, gridlet_order=4, eps=0.0, leaf_max=0,
+             flags=0) -> int:
+    L = load()
+    dom = hpm_domain((ctypes.c_double * 3)(*origin), side)
+    green = hpm_green(HPM_GREEN_PLUMMER, eps)
+    opts = hpm_plan_opts(leaf_max, flags)
+    out = _vp()
+    _check("hpm_plan", L.hpm_plan(ctypes.byref(dom), max_depth, gridlet_order, ctypes.byref(green),
+                                  ctypes.byref(opts), ctypes.byref(out)))
+    return out.value
+
+
+def hpm_build_tree(plan: int, d_pos, n: int, stream=None):
+    _check("hpm_build_tree", load().hpm_build_tree(plan, _ptr(d_pos), n, _stream(stream)))
+
+
+def hpm_solve(plan: int, d_pos, d_mass, d_phi, d_acc, stream=None):
+    _check("hpm_solve", load().hpm_solve(plan, _ptr(d_pos), _ptr(d_mass), _ptr(d_phi), _ptr(d_acc),
+                                         _stream(stream)))
+
+
+def hpm_solve_host(plan: int, h_pos: np.ndarray, h_mass: np.ndarray, h_phi: np.ndarray = None,
+                   h_acc: np.ndarray = None, stream=None):
+    """Host-memory solve: numpy (or pinned-memory) arrays in and out."""
+    n = int(h_pos.shape[0])
+    assert h_pos.dtype == np.float64 and h_pos.flags["C_CONTIGUOUS"]
+    assert h_mass.dtype == np.float64 and h_mass.flags["C_CONTIGUOUS"]
+    for a in (h_phi, h_acc):
+        assert a is None or (a.dtype == np.float32 and a.flags["C_CONTIGUOUS"])
+    addr = lambda a: None if a is None else a.ctypes.data
+    _check("hpm_solve_host", load().hpm_solve_host(plan, addr(h_pos), addr(h_mass), n, addr(h_phi),
+                                                   addr(h_acc), _stream(stream)))
+
+
+def hpm_get_lists_info(plan: int) -> dict:
+    info = hpm_lists_info()
+    _check("hpm_get_lists_info", load().hpm_get_lists_info(plan, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in hpm_lists_info._fields_}
+
+
+def hpm_get_lists(plan: int) -> dict:
+    info = hpm_get_lists_info(plan)
+    nc, nt, nl, n = info["n_cells"], info["n_targets"], info["n_leaves"], info["n_particles"]
+    out = {"level": np.zeros(nc, np.int32), "key": np.zeros(nc, np.uint64), "begin": np.zeros(nc, np.int64),
+           "end": np.zeros(nc, np.int64), "leaf": np.zeros(nc, np.uint8), "iz": np.zeros((nt, 4), np.uint64),
+           "near": np.zeros(nl, np.uint32), "perm": np.zeros(n, np.int64)}
+    a = lambda k: out[k].ctypes.data if out[k].size else None
+    _check("hpm_get_lists", load().hpm_get_lists(plan, a("level"), a("key"), a("begin"), a("end"), a("leaf"),
+                                                 a("iz"), a("near"), a("perm")))
+    return out
+
+
+def hpm_get_boxes(plan: int) -> dict:
+    nb = hpm_get_lists_info(plan)["n_boxes"]
+    out = {"level": np.zeros(nb, np.int32), "key": np.zeros(nb, np.uint64), "flags": np.zeros(nb, np.uint8)}
+    a = lambda k: out[k].ctypes.data if nb else None
+    _check("hpm_get_boxes", load().hpm_get_boxes(plan, a("level"), a("key"), a("flags")))
+    return out
+
+
+def hpm_get_stage(plan: int, stage: int, ng: int) -> np.ndarray:
+    """Stage buffer as float32: (rows, Ng^3) for masses; (targets, Ng^3 + 1) otherwise
+    (values then the constant)."""
+    info = hpm_get_lists_info(plan)
+    m3 = ng ** 3
+    if stage == HPM_STAGE_MASSES:
+        boxes = hpm_get_boxes(plan)
+        rows = int(np.sum(boxes["level"] >= 2))
+        out = np.zeros(max(rows * m3, 1), np.float32)
+        _check("hpm_get_stage", load().hpm_get_stage(plan, stage, out.ctypes.data, out.size))
+        return out[:rows * m3].reshape(rows, m3)
+    nt = info["n_targets"]
+    out = np.zeros(max(nt * (m3 + 1), 1), np.float32)
+    _check("hpm_get_stage", load().hpm_get_stage(plan, stage, out.ctypes.data, out.size))
+    vals = out[:nt * m3].reshape(nt, m3)
+    const = out[nt * m3:nt * m3 + nt]
+    return np.concatenate([vals, const[:, None]], axis=1)
+
+
+def hpm_get_stats(plan: int) -> dict:
+    st = hpm_stats()
+    _check("hpm_get_stats", load().hpm_get_stats(plan, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in hpm_stats._fields_}
+
+
+def hpm_destroy(plan: int):
+    _check("hpm_destroy", load().hpm_destroy(plan))
+
+
+def hpm_status_str(status: int) -> str:
+    return load().hpm_status_str(status).decode()
+
+
+class Solver:
+    """Convenience owner of one plan: build + solve on torch device tensors."""
+
+    def __init__(self, max_depth, gridlet_order=4, eps=0.0, leaf_max=0, origin=(0.0, 0.0, 0.0), side=1.0,
+                 timings=False, flags=0):
+        self.ng = gridlet_order
+        self.plan = hpm_plan(origin, side, max_depth, gridlet_order, eps, leaf_max,
+                             (HPM_FLAG_TIMINGS if timings else 0) | flags)
+
+    def __call__(self, pos, mass, phi=None, acc=None, stream=None):
+        import torch
+        n = pos.shape[0]
+        if phi is None:
+            phi = torch.empty(n, dtype=torch.float32, device=pos.device)
+        if acc is None:
+            acc = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+        hpm_build_tree(self.plan, pos, n, stream)
+        hpm_solve(self.plan, pos, mass, phi, acc, stream)
+        return phi, acc
+
+    def lists(self):
+        return hpm_get_lists(self.plan)
+
+    def boxes(self):
+        return hpm_get_boxes(self.plan)
+
+    def stage(self, which):
+        return hpm_get_stage(self.plan, which, self.ng)
+
+    def close(self):
+        if self.plan:
+            hpm_destroy(self.plan)
+            self.plan = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
