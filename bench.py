@@ -183,6 +183,8 @@ def run_gpu(args) -> None:
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     ms_m2l, launches = [], 0
+    stage_keys = ("ms_tree", "ms_p2g", "ms_m2m", "ms_m2l", "ms_l2l", "ms_g2p", "ms_p2p")
+    stage_sum = {k: 0.0 for k in stage_keys}
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -194,6 +196,8 @@ def run_gpu(args) -> None:
             ev[k][1].record(stream)
             st = hpm.hpm_get_stats(plan)       # waits for this step's last event
             ms_m2l.append(st["ms_m2l"])
+            for key in stage_keys:
+                stage_sum[key] += st[key]
             launches += st["launches"]
         torch.cuda.synchronize(dev)
     if world > 1:
@@ -248,6 +252,7 @@ def run_gpu(args) -> None:
         "e2e": {"value": n_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 32 * w.n,
                 "d2h_bytes_per_step": 16 * w.n, "api": "hpm_solve_host (pinned host buffers)"},
         "gpu_launches": int(launches),
+        "stages_ms": {k[3:]: v / args.steps for k, v in stage_sum.items()},
         "roofline": {"kernel": "source-to-target FFT convolution (k_m2l4)", "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": traffic, "ms_per_launch": m2l_ms, "launches_per_step": 1,
