@@ -211,6 +211,35 @@ typedef struct {
 
 hpm_status hpm_get_stats(hpm_plan_t plan, hpm_stats *stats);
 
+/*
+ * hpm_sort_particles_static - the Morton keys of N positions and their stable
+ * sort, the first step of hpm_build_tree, without allocating any memory. The
+ * paper has no counterpart: it is a service for callers that cannot call
+ * cudaMalloc or any other allocator, for example code that runs under a
+ * fixed device-memory budget set by a host application that owns all
+ * allocation, or that must not allocate between set-up and shutdown.
+ *   dom, max_depth  as for hpm_plan; keys are taken at level max_depth
+ *   d_pos           N x 3 FP64 positions (device), AoS
+ *   n               0 <= N <= HPM_STATIC_SORT_MAX_N
+ *   d_keys          N u64 (device, caller-owned): the level-max_depth Morton
+ *                   keys in ascending order (ties kept in caller order)
+ *   d_perm          N u32 (device, caller-owned): sorted position -> caller
+ *                   index, the same permutation hpm_get_lists reports
+ * Scratch lives in one static device array of about 12.6 MiB that every GPU
+ * loading the library holds until the process exits; it limits N to
+ * HPM_STATIC_SORT_MAX_N and a larger N returns HPM_ERR_INVALID_ARG without
+ * touching the device. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, once per device, under a lock); make that
+ * first call before any stream capture on that device. All calls share the
+ * array and each call overwrites it, so calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller. Reads
+ * back one error word and synchronises `stream`.
+ * Errors: HPM_ERR_INVALID_ARG, HPM_ERR_OUT_OF_DOMAIN, HPM_ERR_CUDA.
+ */
+#define HPM_STATIC_SORT_MAX_N 1048576
+hpm_status hpm_sort_particles_static(const hpm_domain *dom, int max_depth, const double *d_pos, int64_t n,
+                                     uint64_t *d_keys, uint32_t *d_perm, void *stream);
+
 /* Frees the plan and everything it owns. NULL is allowed. */
 hpm_status hpm_destroy(hpm_plan_t plan);
 

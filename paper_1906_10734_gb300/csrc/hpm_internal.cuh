@@ -107,6 +107,8 @@ struct hpm_plan_s {
 
 namespace hpm {
 // tree.cu
+hpm_status launch_morton_keys(const hpm_domain &dom, int depth, const double *d_pos, int64_t n,
+                              uint64_t *d_keys, int *d_err, cudaStream_t st);
 hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream_t st);
 // sort.cu
 hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&vals,

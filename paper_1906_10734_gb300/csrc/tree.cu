@@ -255,6 +255,15 @@ hpm_status select_boxes(hpm_plan_s *pl, int64_t b, int64_t e, int mode, DevBuf &
 
 }  // namespace
 
+hpm_status launch_morton_keys(const hpm_domain &dom, int depth, const double *d_pos, int64_t n,
+                              uint64_t *d_keys, int *d_err, cudaStream_t st) {
+  if (n <= 0) return HPM_OK;
+  k_keys<<<blocks_for(n), kThreads, 0, st>>>(d_pos, n, dom.origin[0], dom.origin[1], dom.origin[2], dom.side,
+                                             depth, d_keys, d_err);
+  HPM_LAUNCHED((int64_t *)nullptr);
+  return HPM_OK;
+}
+
 hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream_t st) {
   TreeDev &t = pl->t;
   const int D = pl->max_depth;

@@ -62,6 +62,7 @@ SIGNATURES = {
     "hpm_get_stats": ([_vp, ctypes.POINTER(hpm_stats)], _i32),
     "hpm_get_boxes": ([_vp, _vp, _vp, _vp], _i32),
     "hpm_get_stage": ([_vp, _i32, _vp, _i64], _i32),
+    "hpm_sort_particles_static": ([ctypes.POINTER(hpm_domain), _i32, _vp, _i64, _vp, _vp, _vp], _i32),
     "hpm_destroy": ([_vp], _i32),
     "hpm_status_str": ([_i32], ctypes.c_char_p),
     "hpm_last_cuda_error": ([], ctypes.c_char_p),
@@ -201,6 +202,18 @@ def hpm_get_stats(plan: int) -> dict:
     st = hpm_stats()
     _check("hpm_get_stats", load().hpm_get_stats(plan, ctypes.byref(st)))
     return {k: getattr(st, k) for k, _ in hpm_stats._fields_}
+
+
+HPM_STATIC_SORT_MAX_N = 1048576
+
+
+def hpm_sort_particles_static(d_pos, n: int, d_keys, d_perm, max_depth: int, origin=(0.0, 0.0, 0.0),
+                              side=1.0, stream=None):
+    """Morton keys and stable sort into caller buffers, no allocation (scratch is static)."""
+    dom = hpm_domain((ctypes.c_double * 3)(*origin), side)
+    _check("hpm_sort_particles_static",
+           load().hpm_sort_particles_static(ctypes.byref(dom), max_depth, _ptr(d_pos), n, _ptr(d_keys),
+                                            _ptr(d_perm), _stream(stream)))
 
 
 def hpm_destroy(plan: int):
