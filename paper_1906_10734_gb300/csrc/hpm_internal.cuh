@@ -28,6 +28,11 @@ enum : uint8_t {
 // Device error word bits.
 enum : int { kErrDomain = 1, kErrCapacity = 2, kErrTimeout = 4 };
 
+// Near-field work item size: pairs per warp-sized item (and at least this many
+// sources per item).
+constexpr int64_t kP2PPairsPerItem = 16384;
+constexpr int kP2PMinSources = 32;
+
 const char *set_cuda_error(cudaError_t e);
 
 // Grow-only device buffer on the stream-ordered allocator.
@@ -58,6 +63,9 @@ struct TreeDev {
   DevBuf cnt, off;   // per-box scratch for child counting
   // work lists
   DevBuf tgt_box, box_tgt, leaf_box, p2g_box;
+  // near-field work items: each leaf's concatenated near sources split into
+  // items of bounded pair count
+  DevBuf item_leaf, item_s0, item_s1, leaf_nitem, leaf_item0, leaf_part0;
   DevBuf err;        // int error word
   DevBuf counters;   // small device counters
 };
@@ -69,6 +77,7 @@ struct SolveDev {
   DevBuf locc;       // local constant per target
   DevBuf m2lc;       // constant part of each target's source-to-target values
   DevBuf far;        // far field per sorted particle: float4 (phi, ax, ay, az)
+  DevBuf part;       // near-field partial sums of leaves split over several items
   DevBuf m2l_scratch;
   DevBuf work;       // int work counters
 };
@@ -97,6 +106,7 @@ struct hpm_plan_s {
   std::vector<int64_t> lvl_off;    // box offsets per level, size depth+2
   int depth_reached = -1;
   int64_t nbox = 0, ntgt = 0, nleaf = 0, np2g = 0, ncell = 0;
+  int64_t nitem = 0, npart = 0;   // near-field work items, partial-sum rows
   std::vector<int64_t> tgt_lvl_off;  // target offsets per level (levels 2..D)
   std::vector<int64_t> leaf_lvl_off;
   hpm_stats stats{};

@@ -304,93 +304,175 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
   s = t;
 }
 
-// Near zone of each leaf by direct summation (one warp per leaf). The G lanes
-// of a target particle split the sources; sums are Kahan compensated. Adds
-// the far field and writes the caller-ordered outputs.
-__global__ void __launch_bounds__(kThreads) k_p2p(int64_t nleaf, const int *__restrict__ leaf_box,
-                                                  const int *__restrict__ nb, const int *__restrict__ beg,
-                                                  const int *__restrict__ end, const float4 *__restrict__ hi,
-                                                  const float4 *__restrict__ lo,
+// One source's contribution to a target, accumulated into a short plain-FP32
+// block sum; positions are hi/lo pairs relative to the domain origin, so the
+// coordinate difference keeps FP32 precision relative to itself.
+__device__ __forceinline__ void pair_add(const float4 &mh, const float4 &ml, const float4 &h, const float4 &q,
+                                         bool self, float eps2, float &bp, float &bx, float &by, float &bz) {
+  const float dx = (h.x - mh.x) + (q.x - ml.x);
+  const float dy = (h.y - mh.y) + (q.y - ml.y);
+  const float dz = (h.z - mh.z) + (q.z - ml.z);
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+  float ir = rsqrtf(r2);
+  if (self) ir = 0.f;
+  const float mir = h.w * ir;
+  const float mir3 = mir * ir * ir;
+  bp -= mir;
+  bx = fmaf(mir3, dx, bx);
+  by = fmaf(mir3, dy, by);
+  bz = fmaf(mir3, dz, bz);
+}
+
+// Near zone by direct summation (Sec. 1, item 1), one warp per work item: an
+// item is a leaf's targets against a contiguous part of the concatenation of
+// its near boxes' particles. floor(32 / nt) lanes share a target and split its
+// sources; blocks of four pairs are summed in plain FP32 and the block sums are
+// Kahan compensated. A leaf with one item writes far + near to the caller's
+// order; a leaf split over several items writes partial sums for k_p2p_combine.
+__global__ void __launch_bounds__(kThreads) k_p2p(int64_t nitem, const int *__restrict__ item_leaf,
+                                                  const int *__restrict__ item_s0, const int *__restrict__ item_s1,
+                                                  const int *__restrict__ leaf_nitem,
+                                                  const int *__restrict__ leaf_item0,
+                                                  const int *__restrict__ leaf_part0,
+                                                  const int *__restrict__ leaf_box, const int *__restrict__ nb,
+                                                  const int *__restrict__ beg, const int *__restrict__ end,
+                                                  const float4 *__restrict__ hi, const float4 *__restrict__ lo,
                                                   const float4 *__restrict__ far,
                                                   const uint32_t *__restrict__ perm, float eps2,
-                                                  float *__restrict__ out_phi, float *__restrict__ out_acc) {
-  __shared__ float4 shi[kWarpsPerBlock][32], slo[kWarpsPerBlock][32];
-  __shared__ int sidx[kWarpsPerBlock][32];
-  __shared__ int rb[kWarpsPerBlock][27], re[kWarpsPerBlock][27];
+                                                  float *__restrict__ out_phi, float *__restrict__ out_acc,
+                                                  float4 *__restrict__ part) {
+  __shared__ int rb[kWarpsPerBlock][28], cum[kWarpsPerBlock][28];
+  __shared__ float4 red[kWarpsPerBlock][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + w;
-  if (item >= nleaf) return;
-  const int box = leaf_box[item];
-  if (lane < 27) {
-    const int q = nb[(int64_t)box * 27 + lane];
-    rb[w][lane] = q >= 0 ? beg[q] : 0;
-    re[w][lane] = q >= 0 ? end[q] : 0;
+  const int64_t it = (int64_t)blockIdx.x * kWarpsPerBlock + w;
+  if (it >= nitem) return;
+  const int leaf = item_leaf[it];
+  const int box = leaf_box[leaf];
+  {
+    int b = 0, c = 0;
+    if (lane < 27) {
+      const int q = nb[(int64_t)box * 27 + lane];
+      if (q >= 0) {
+        b = beg[q];
+        c = end[q] - b;
+      }
+    }
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane < 28) {
+      rb[w][lane] = b;
+      cum[w][lane] = inc - c;  // exclusive prefix; cum[27] = total
+    }
   }
   __syncwarp();
-  const int tb = beg[box], te = end[box];
-  const int nt = te - tb;
-  int G = 1;
-  if (nt <= 16) {
-    G = 2;
-    while (nt * G * 2 <= 32 && G < 32) G *= 2;
-  }
-  const int per = 32 / G;  // targets per pass
+  const int s0 = item_s0[it], s1 = item_s1[it];
+  const int tb = beg[box], te = end[box], nt = te - tb;
+  const int G = nt >= 32 ? 1 : 32 / nt;
+  const int per = 32 / G;
+  const int nitems = leaf_nitem[leaf];
+  const int kidx = (int)(it - leaf_item0[leaf]);
   for (int t0 = tb; t0 < te; t0 += per) {
-    const int ti = t0 + lane / G, sub = lane % G;
-    const bool active = ti < te;
-    float4 mh = make_float4(0.f, 0.f, 0.f, 0.f), ml = mh;
-    if (active) {
-      mh = hi[ti];
-      ml = lo[ti];
-    }
+    const int slot = lane / G, sub = lane % G;
+    const int ti = t0 + slot;
+    const bool active = slot < per && ti < te;
     float sp = 0.f, cp = 0.f, sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
-    for (int r = 0; r < 27; ++r) {
-      const int b = rb[w][r], e = re[w][r];
-      for (int c0 = b; c0 < e; c0 += 32) {
-        const int j = c0 + lane;
-        if (j < e) {
-          shi[w][lane] = hi[j];
-          slo[w][lane] = lo[j];
-          sidx[w][lane] = j;
-        }
-        __syncwarp();
-        const int cnt = min(32, e - c0);
-        if (active) {
-          for (int k = sub; k < cnt; k += G) {
-            const float4 h = shi[w][k], q = slo[w][k];
-            const float dx = (h.x - mh.x) + (q.x - ml.x);
-            const float dy = (h.y - mh.y) + (q.y - ml.y);
-            const float dz = (h.z - mh.z) + (q.z - ml.z);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-            float ir = rsqrtf(r2);
-            if (sidx[w][k] == ti) ir = 0.f;
-            const float mir = h.w * ir;
-            const float mir3 = mir * ir * ir;
-            kahan_add(sp, cp, -mir);
-            kahan_add(sx, cx, mir3 * dx);
-            kahan_add(sy, cy, mir3 * dy);
-            kahan_add(sz, cz, mir3 * dz);
+    if (active) {
+      const float4 mh = hi[ti], ml = lo[ti];
+      for (int r = 0; r < 27; ++r) {
+        const int rs = max(cum[w][r], s0), re2 = min(cum[w][r + 1], s1);
+        if (rs >= re2) continue;
+        int q = rs + ((sub - (rs - s0)) % G + G) % G;
+        const int off = rb[w][r] - cum[w][r];  // particle index = q + off
+        for (; q + 3 * G < re2; q += 4 * G) {
+          float bp = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = q + u * G + off;
+            pair_add(mh, ml, hi[j], lo[j], j == ti, eps2, bp, bx, by, bz);
           }
+          kahan_add(sp, cp, bp);
+          kahan_add(sx, cx, bx);
+          kahan_add(sy, cy, by);
+          kahan_add(sz, cz, bz);
         }
-        __syncwarp();
+        float bp = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+        for (; q < re2; q += G) {
+          const int j = q + off;
+          pair_add(mh, ml, hi[j], lo[j], j == ti, eps2, bp, bx, by, bz);
+        }
+        kahan_add(sp, cp, bp);
+        kahan_add(sx, cx, bx);
+        kahan_add(sy, cy, by);
+        kahan_add(sz, cz, bz);
       }
     }
-    float vp = sp - cp, vx = sx - cx, vy = sy - cy, vz = sz - cz;
-    for (int off = 1; off < G; off <<= 1) {
-      vp += __shfl_xor_sync(0xffffffffu, vp, off);
-      vx += __shfl_xor_sync(0xffffffffu, vx, off);
-      vy += __shfl_xor_sync(0xffffffffu, vy, off);
-      vz += __shfl_xor_sync(0xffffffffu, vz, off);
-    }
+    red[w][lane] = make_float4(sp - cp, sx - cx, sy - cy, sz - cz);
+    __syncwarp();
     if (active && sub == 0) {
-      const float4 f = far[ti];
-      const uint32_t o = perm[ti];
-      if (out_phi) out_phi[o] = f.x + vp;
-      if (out_acc) {
-        out_acc[3 * (int64_t)o] = f.y + vx;
-        out_acc[3 * (int64_t)o + 1] = f.z + vy;
-        out_acc[3 * (int64_t)o + 2] = f.w + vz;
+      float4 v = red[w][lane];
+      for (int g = 1; g < G; ++g) {
+        const float4 o = red[w][lane + g];
+        v.x += o.x;
+        v.y += o.y;
+        v.z += o.z;
+        v.w += o.w;
       }
+      if (nitems == 1) {
+        const float4 f = far[ti];
+        const uint32_t o = perm[ti];
+        if (out_phi) out_phi[o] = f.x + v.x;
+        if (out_acc) {
+          out_acc[3 * (int64_t)o] = f.y + v.y;
+          out_acc[3 * (int64_t)o + 1] = f.z + v.z;
+          out_acc[3 * (int64_t)o + 2] = f.w + v.w;
+        }
+      } else {
+        part[(int64_t)leaf_part0[leaf] + (int64_t)kidx * nt + (ti - tb)] = v;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Leaves whose near zone was split over several items: sum the items' partial
+// sums in item order (deterministic), add the far field, write the outputs.
+__global__ void __launch_bounds__(kThreads) k_p2p_combine(int64_t nleaf, const int *__restrict__ leaf_nitem,
+                                                          const int *__restrict__ leaf_part0,
+                                                          const int *__restrict__ leaf_box,
+                                                          const int *__restrict__ beg, const int *__restrict__ end,
+                                                          const float4 *__restrict__ part,
+                                                          const float4 *__restrict__ far,
+                                                          const uint32_t *__restrict__ perm,
+                                                          float *__restrict__ out_phi, float *__restrict__ out_acc) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t leaf = (int64_t)blockIdx.x * kWarpsPerBlock + w;
+  if (leaf >= nleaf) return;
+  const int n = leaf_nitem[leaf];
+  if (n <= 1) return;
+  const int box = leaf_box[leaf];
+  const int tb = beg[box], nt = end[box] - tb;
+  const float4 *pp = part + leaf_part0[leaf];
+  for (int t = lane; t < nt; t += 32) {
+    float sp = 0.f, cp = 0.f, sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
+    for (int k = 0; k < n; ++k) {
+      const float4 v = pp[(int64_t)k * nt + t];
+      kahan_add(sp, cp, v.x);
+      kahan_add(sx, cx, v.y);
+      kahan_add(sy, cy, v.z);
+      kahan_add(sz, cz, v.w);
+    }
+    const int ti = tb + t;
+    const float4 f = far[ti];
+    const uint32_t o = perm[ti];
+    if (out_phi) out_phi[o] = f.x + (sp - cp);
+    if (out_acc) {
+      out_acc[3 * (int64_t)o] = f.y + (sx - cx);
+      out_acc[3 * (int64_t)o + 1] = f.z + (sy - cy);
+      out_acc[3 * (int64_t)o + 2] = f.w + (sz - cz);
     }
   }
 }
@@ -561,11 +643,19 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
   record(pl, 6, st);
   {
     const float eps2 = (float)(pl->green.eps * pl->green.eps);
-    k_p2p<<<warp_blocks(pl->nleaf), kThreads, 0, st>>>(pl->nleaf, t.leaf_box.as<int>(), t.box_nb.as<int>(),
-                                                       t.box_beg.as<int>(), t.box_end.as<int>(), hi, lo,
-                                                       s.far.as<float4>(), t.perm.as<uint32_t>(), eps2,
-                                                       d_phi, d_acc);
+    HPM_TRY(s.part.ensure(sizeof(float4) * (pl->npart > 0 ? pl->npart : 1), st));
+    k_p2p<<<warp_blocks(pl->nitem), kThreads, 0, st>>>(
+        pl->nitem, t.item_leaf.as<int>(), t.item_s0.as<int>(), t.item_s1.as<int>(), t.leaf_nitem.as<int>(),
+        t.leaf_item0.as<int>(), t.leaf_part0.as<int>(), t.leaf_box.as<int>(), t.box_nb.as<int>(),
+        t.box_beg.as<int>(), t.box_end.as<int>(), hi, lo, s.far.as<float4>(), t.perm.as<uint32_t>(), eps2, d_phi,
+        d_acc, s.part.as<float4>());
     HPM_LAUNCHED(&launches);
+    if (pl->npart > 0) {
+      k_p2p_combine<<<warp_blocks(pl->nleaf), kThreads, 0, st>>>(
+          pl->nleaf, t.leaf_nitem.as<int>(), t.leaf_part0.as<int>(), t.leaf_box.as<int>(), t.box_beg.as<int>(),
+          t.box_end.as<int>(), s.part.as<float4>(), s.far.as<float4>(), t.perm.as<uint32_t>(), d_phi, d_acc);
+      HPM_LAUNCHED(&launches);
+    }
   }
   record(pl, 7, st);
   pl->stats.launches += launches;

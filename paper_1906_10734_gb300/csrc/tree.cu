@@ -219,6 +219,49 @@ __global__ void k_box_tgt(int64_t ntgt, const int *__restrict__ tgt_box, int *__
   if (t < ntgt) box_tgt[tgt_box[t]] = (int)t;
 }
 
+// Near-field work per leaf: nt targets times ns near sources, split into
+// items of at most kP2PPairsPerItem pairs and at least kP2PMinSources sources.
+__global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, const int *__restrict__ nb,
+                            const int *__restrict__ beg, const int *__restrict__ end, int *__restrict__ nitem,
+                            int *__restrict__ npart) {
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nleaf) return;
+  const int box = leaf_box[l];
+  int64_t ns = 0;
+  for (int k = 0; k < 27; ++k) {
+    const int q = nb[(int64_t)box * 27 + k];
+    if (q >= 0) ns += end[q] - beg[q];
+  }
+  const int64_t nt = end[box] - beg[box];
+  int64_t items = (nt * ns + kP2PPairsPerItem - 1) / kP2PPairsPerItem;
+  const int64_t cap = (ns + kP2PMinSources - 1) / kP2PMinSources;
+  if (items > cap) items = cap;
+  if (items < 1) items = 1;
+  nitem[l] = (int)items;
+  npart[l] = items > 1 ? (int)(items * nt) : 0;
+}
+
+__global__ void k_fill_items(int64_t nleaf, const int *__restrict__ leaf_box, const int *__restrict__ nb,
+                             const int *__restrict__ beg, const int *__restrict__ end,
+                             const int *__restrict__ nitem, const int *__restrict__ item0,
+                             int *__restrict__ item_leaf, int *__restrict__ item_s0, int *__restrict__ item_s1) {
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nleaf) return;
+  const int box = leaf_box[l];
+  int64_t ns = 0;
+  for (int k = 0; k < 27; ++k) {
+    const int q = nb[(int64_t)box * 27 + k];
+    if (q >= 0) ns += end[q] - beg[q];
+  }
+  const int n = nitem[l];
+  const int64_t i0 = item0[l];
+  for (int k = 0; k < n; ++k) {
+    item_leaf[i0 + k] = (int)l;
+    item_s0[i0 + k] = (int)(ns * k / n);
+    item_s1[i0 + k] = (int)(ns * (k + 1) / n);
+  }
+}
+
 hpm_status ensure_boxes(TreeDev &t, int64_t nbox, cudaStream_t st) {
   HPM_TRY(t.box_key.ensure(sizeof(uint64_t) * nbox, st, true));
   HPM_TRY(t.box_beg.ensure(sizeof(int) * nbox, st, true));
@@ -278,6 +321,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream
   pl->lvl_off.assign(D + 2, 0);
   pl->depth_reached = -1;
   pl->nbox = pl->ntgt = pl->nleaf = pl->np2g = pl->ncell = 0;
+  pl->nitem = pl->npart = 0;
   pl->tgt_lvl_off.assign(D + 2, 0);
   pl->leaf_lvl_off.assign(D + 2, 0);
   if (n == 0) {
@@ -410,6 +454,36 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream
   pl->nleaf = cnt;
   HPM_TRY(select_boxes(pl, off2, pl->nbox, 2, t.p2g_box, &cnt, st, &launches));
   pl->np2g = cnt;
+  // near-field work items
+  {
+    const int64_t nl = pl->nleaf;
+    HPM_TRY(t.leaf_nitem.ensure(sizeof(int) * (nl + 1), st));
+    HPM_TRY(t.leaf_item0.ensure(sizeof(int) * (nl + 1), st));
+    HPM_TRY(t.leaf_part0.ensure(sizeof(int) * (nl + 1), st));
+    HPM_TRY(t.cnt.ensure(sizeof(int) * (nl + 1), st));
+    k_leaf_work<<<blocks_for(nl), kThreads, 0, st>>>(nl, t.leaf_box.as<int>(), t.box_nb.as<int>(),
+                                                     t.box_beg.as<int>(), t.box_end.as<int>(),
+                                                     t.leaf_nitem.as<int>(), t.cnt.as<int>());
+    HPM_LAUNCHED(&launches);
+    HPM_TRY(exclusive_scan_i32(t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(), nl, t.counters.as<int>() + 64,
+                               t.keys_alt, st, &launches));
+    HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.leaf_part0.as<int>(), nl, t.counters.as<int>() + 65,
+                               t.keys_alt, st, &launches));
+    int hv[2] = {0, 0};
+    HPM_CUDA(cudaMemcpyAsync(hv, t.counters.as<int>() + 64, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaStreamSynchronize(st));
+    pl->nitem = hv[0];
+    pl->npart = hv[1];
+    HPM_TRY(t.item_leaf.ensure(sizeof(int) * (pl->nitem + 1), st));
+    HPM_TRY(t.item_s0.ensure(sizeof(int) * (pl->nitem + 1), st));
+    HPM_TRY(t.item_s1.ensure(sizeof(int) * (pl->nitem + 1), st));
+    k_fill_items<<<blocks_for(nl), kThreads, 0, st>>>(nl, t.leaf_box.as<int>(), t.box_nb.as<int>(),
+                                                      t.box_beg.as<int>(), t.box_end.as<int>(),
+                                                      t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(),
+                                                      t.item_leaf.as<int>(), t.item_s0.as<int>(),
+                                                      t.item_s1.as<int>());
+    HPM_LAUNCHED(&launches);
+  }
   HPM_TRY(t.box_tgt.ensure(sizeof(int) * (pl->nbox > 0 ? pl->nbox : 1), st));
   HPM_CUDA(cudaMemsetAsync(t.box_tgt.p, 0xff, sizeof(int) * pl->nbox, st));
   if (pl->ntgt) {
