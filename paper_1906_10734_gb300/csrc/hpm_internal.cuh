@@ -60,9 +60,9 @@ struct TreeDev {
   DevBuf spm;        // double4 (x, y, z, m) in sorted order
   // boxes, all levels, level-major, Morton order within a level
   DevBuf box_key, box_beg, box_end, box_parent, box_flags, box_child, box_nb;
-  DevBuf cnt, off;   // per-box scratch for child counting
+  DevBuf cnt, off, bnd;   // per-box scratch for child counting
   // work lists
-  DevBuf tgt_box, box_tgt, leaf_box, p2g_box;
+  DevBuf tgt_box, box_tgt, leaf_box, p2g_box, p2g_off;
   // near-field work items: each leaf's concatenated near sources split into
   // items of bounded pair count
   DevBuf item_leaf, item_s0, item_s1, leaf_nitem, leaf_item0, leaf_part0;

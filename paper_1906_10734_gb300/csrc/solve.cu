@@ -84,58 +84,69 @@ __device__ __forceinline__ void lagrange_d(const GridletTables &tb, double t, fl
   }
 }
 
-// Effective masses of one box per warp, M_p = sum_i m_i prod_d ell_{p_d}(xi_d)
-// (Eq. mp in Lagrange form: sum_n B_pn t^n = ell_p(t)).
+// Effective masses, M_p = sum_i m_i prod_d ell_{p_d}(xi_d) (Eq. mp in Lagrange
+// form: sum_n B_pn t^n = ell_p(t)). A block takes 8 boxes; all its threads
+// evaluate the FP64 weights of the (box, particle) pairs of those boxes, 256
+// pairs at a time, then warp w accumulates box w from shared memory.
 __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__restrict__ list,
-                                                  LevelTable lt, GridletTables tb, double ox, double oy,
-                                                  double oz, double side, const uint64_t *__restrict__ key,
-                                                  const int *__restrict__ beg, const int *__restrict__ end,
+                                                  const int *__restrict__ pair_off, LevelTable lt,
+                                                  GridletTables tb, double ox, double oy, double oz, double side,
+                                                  const uint64_t *__restrict__ key, const int *__restrict__ beg,
                                                   const PM *__restrict__ spm, int64_t off2,
                                                   float *__restrict__ grid) {
-  __shared__ float ws[kWarpsPerBlock][32][3][kMaxNg];
-  __shared__ float ms[kWarpsPerBlock][32];
+  __shared__ float ws[kThreads][3][kMaxNg];
+  __shared__ float ms[kThreads];
+  __shared__ int off[kWarpsPerBlock + 1];
+  __shared__ int bx[kWarpsPerBlock], bbeg[kWarpsPerBlock];
+  __shared__ double bc[kWarpsPerBlock][3], binv[kWarpsPerBlock];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + w;
-  if (item >= nbox) return;
-  const int box = list[item];
-  const int l = level_of(lt, box);
-  const double L = side / (double)(1u << l);
-  const uint64_t k = key[box];
-  const double cc[3] = {(double)compact3(k) + 0.5, (double)compact3(k >> 1) + 0.5,
-                        (double)compact3(k >> 2) + 0.5};
-  const double o[3] = {ox, oy, oz};
+  const int64_t b0 = (int64_t)blockIdx.x * kWarpsPerBlock;
+  const int nb = (int)min((int64_t)kWarpsPerBlock, nbox - b0);
+  if (threadIdx.x <= nb) off[threadIdx.x] = pair_off[b0 + threadIdx.x];
+  if (threadIdx.x < nb) {
+    const int box = list[b0 + threadIdx.x];
+    const int l = level_of(lt, box);
+    const uint64_t k = key[box] & ((1ull << (3 * l)) - 1ull);
+    bx[threadIdx.x] = box;
+    bbeg[threadIdx.x] = beg[box];
+    binv[threadIdx.x] = (double)(1u << l) / side;
+    bc[threadIdx.x][0] = (double)compact3(k) + 0.5;
+    bc[threadIdx.x][1] = (double)compact3(k >> 1) + 0.5;
+    bc[threadIdx.x][2] = (double)compact3(k >> 2) + 0.5;
+  }
+  __syncthreads();
   const int ng = tb.ng, m3 = ng * ng * ng;
+  const double o[3] = {ox, oy, oz};
   float acc[16];
   for (int r = 0; r < 16; ++r) acc[r] = 0.f;
-  const int b = beg[box], e = end[box];
-  for (int c0 = b; c0 < e; c0 += 32) {
-    const int i = c0 + lane;
-    if (i < e) {
-      const PM q = spm[i];
+  const int P0 = off[0], P1 = off[nb];
+  for (int c0 = P0; c0 < P1; c0 += kThreads) {
+    const int p = c0 + threadIdx.x;
+    if (p < P1) {
+      int lb = 0;
+      while (lb + 1 < nb && off[lb + 1] <= p) ++lb;
+      const PM q = spm[bbeg[lb] + (p - off[lb])];
       const double xs[3] = {q.x, q.y, q.z};
-      for (int d = 0; d < 3; ++d) {
-        const double xi = (xs[d] - o[d]) / L - cc[d];
-        lagrange_d(tb, xi, ws[w][lane][d]);
+      for (int d = 0; d < 3; ++d) lagrange_d(tb, fma(xs[d] - o[d], binv[lb], -bc[lb][d]), ws[threadIdx.x][d]);
+      ms[threadIdx.x] = (float)q.m;
+    }
+    __syncthreads();
+    if (w < nb) {
+      const int jb = max(off[w], c0) - c0, je = min(off[w + 1], c0 + kThreads) - c0;
+      for (int r = 0; r * 32 + lane < m3; ++r) {
+        const int pp = r * 32 + lane;
+        const int px = pp % ng, py = (pp / ng) % ng, pz = pp / (ng * ng);
+        float s = acc[r];
+        for (int j = jb; j < je; ++j) s += ms[j] * ws[j][0][px] * ws[j][1][py] * ws[j][2][pz];
+        acc[r] = s;
       }
-      ms[w][lane] = (float)q.m;
-    } else {
-      ms[w][lane] = 0.f;
-      for (int d = 0; d < 3; ++d)
-        for (int j = 0; j < ng; ++j) ws[w][lane][d][j] = 0.f;
     }
-    __syncwarp();
-    const int cnt = min(32, e - c0);
-    for (int r = 0; r * 32 + lane < m3; ++r) {
-      const int p = r * 32 + lane;
-      const int px = p % ng, py = (p / ng) % ng, pz = p / (ng * ng);
-      float s = acc[r];
-      for (int j = 0; j < cnt; ++j) s += ms[w][j] * ws[w][j][0][px] * ws[w][j][1][py] * ws[w][j][2][pz];
-      acc[r] = s;
-    }
-    __syncwarp();
+    __syncthreads();
   }
-  float *out = grid + (int64_t)(box - off2) * m3;
-  for (int r = 0; r * 32 + lane < m3; ++r) out[r * 32 + lane] = acc[r];
+  if (w < nb) {
+    float *out = grid + (int64_t)(bx[w] - off2) * m3;
+    for (int r = 0; r * 32 + lane < m3; ++r) out[r * 32 + lane] = acc[r];
+  }
 }
 
 // Separable application of a 1-D operator along one axis of an Ng^3 gridlet
@@ -270,17 +281,17 @@ __global__ void __launch_bounds__(kThreads) k_g2p(int64_t lb, int64_t le, const 
   const float c0 = locc[t];
   __syncwarp();
   const int l = level_of(lt, box);
-  const double L = side / (double)(1u << l);
-  const uint64_t k = key[box];
+  const double inv = (double)(1u << l) / side;
+  const uint64_t k = key[box] & ((1ull << (3 * l)) - 1ull);
   const double cc[3] = {(double)compact3(k) + 0.5, (double)compact3(k >> 1) + 0.5,
                         (double)compact3(k >> 2) + 0.5};
   const double o[3] = {ox, oy, oz};
-  const float invL = (float)(1.0 / L);
+  const float invL = (float)inv;
   for (int i = beg[box] + lane; i < end[box]; i += 32) {
     const PM q = spm[i];
     const double xs[3] = {q.x, q.y, q.z};
     float wv[3][kMaxNg], dw[3][kMaxNg];
-    for (int d = 0; d < 3; ++d) lagrange_f(tb, (float)((xs[d] - o[d]) / L - cc[d]), wv[d], dw[d]);
+    for (int d = 0; d < 3; ++d) lagrange_f(tb, (float)fma(xs[d] - o[d], inv, -cc[d]), wv[d], dw[d]);
     float f = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
     for (int pz = 0; pz < ng; ++pz)
       for (int py = 0; py < ng; ++py) {
@@ -596,9 +607,9 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
   HPM_LAUNCHED(&launches);
   record(pl, 1, st);
   if (pl->np2g) {
-    k_p2g<<<warp_blocks(pl->np2g), kThreads, 0, st>>>(pl->np2g, t.p2g_box.as<int>(), lt, pl->tab, o[0], o[1],
-                                                      o[2], pl->dom.side, t.box_key.as<uint64_t>(),
-                                                      t.box_beg.as<int>(), t.box_end.as<int>(), spm, off2,
+    k_p2g<<<warp_blocks(pl->np2g), kThreads, 0, st>>>(pl->np2g, t.p2g_box.as<int>(), t.p2g_off.as<int>(), lt,
+                                                      pl->tab, o[0], o[1], o[2], pl->dom.side,
+                                                      t.box_key.as<uint64_t>(), t.box_beg.as<int>(), spm, off2,
                                                       s.grid.as<float>());
     HPM_LAUNCHED(&launches);
   }

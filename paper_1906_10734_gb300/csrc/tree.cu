@@ -101,27 +101,32 @@ __device__ __forceinline__ int lower_bound_key(const uint64_t *__restrict__ skey
   return lo;
 }
 
-__device__ __forceinline__ void octant_bounds(const uint64_t *__restrict__ skeys, int b, int e,
-                                              int shift, uint64_t kparent, int bnd[9]) {
-  bnd[0] = b;
-  bnd[8] = e;
-#pragma unroll
-  for (int o = 1; o < 8; ++o)
-    bnd[o] = lower_bound_key(skeys, bnd[o - 1], e, shift, (kparent << 3) | (uint64_t)o);
+
+// Child boundaries of every expanded box, one thread per (box, octant): the
+// seven searches of a box run in parallel instead of one after another.
+__global__ void k_octant_bounds(int64_t pb, int64_t pe, const uint8_t *__restrict__ flags,
+                                const uint64_t *__restrict__ key, const int *__restrict__ beg,
+                                const int *__restrict__ end, const uint64_t *__restrict__ skeys, int shift,
+                                int *__restrict__ bnd) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = pb + t / 8;
+  const int o = (int)(t % 8);
+  if (i >= pe) return;
+  int v = beg[i];
+  if (o > 0 && (flags[i] & kExpand)) v = lower_bound_key(skeys, beg[i], end[i], shift, (key[i] << 3) | (uint64_t)o);
+  bnd[t] = v;
 }
 
 __global__ void k_count_children(int64_t pb, int64_t pe, const uint8_t *__restrict__ flags,
-                                 const uint64_t *__restrict__ key, const int *__restrict__ beg,
-                                 const int *__restrict__ end, const uint64_t *__restrict__ skeys,
-                                 int shift, int *__restrict__ cnt) {
+                                 const int *__restrict__ end, const int *__restrict__ bnd,
+                                 int *__restrict__ cnt) {
   const int64_t i = pb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= pe) return;
   int c = 0;
   if (flags[i] & kExpand) {
-    int bnd[9];
-    octant_bounds(skeys, beg[i], end[i], shift, key[i], bnd);
+    const int *b = bnd + (i - pb) * 8;
 #pragma unroll
-    for (int o = 0; o < 8; ++o) c += bnd[o + 1] > bnd[o];
+    for (int o = 0; o < 8; ++o) c += (o < 7 ? b[o + 1] : end[i]) > b[o];
   }
   cnt[i - pb] = c;
 }
@@ -130,8 +135,8 @@ __global__ void k_fill_children(int64_t pb, int64_t pe, int64_t cb, int level, i
                                 int leaf_max, uint8_t *__restrict__ flags, uint64_t *__restrict__ key,
                                 int *__restrict__ beg, int *__restrict__ end,
                                 int *__restrict__ parent, int *__restrict__ child,
-                                const uint64_t *__restrict__ skeys, int shift,
-                                const int *__restrict__ off, int *__restrict__ counters) {
+                                const int *__restrict__ bnds, const int *__restrict__ off,
+                                int *__restrict__ counters) {
   const int64_t q = pb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= pe) return;
   if (!(flags[q] & kExpand)) {
@@ -141,7 +146,9 @@ __global__ void k_fill_children(int64_t pb, int64_t pe, int64_t cb, int level, i
   }
   int bnd[9];
   const uint64_t kq = key[q];
-  octant_bounds(skeys, beg[q], end[q], shift, kq, bnd);
+#pragma unroll
+  for (int o = 0; o < 8; ++o) bnd[o] = bnds[(q - pb) * 8 + o];
+  bnd[8] = end[q];
   const bool real = flags[q] & kInternal;
   int64_t idx = cb + off[q - pb];
   int nreal = 0, nleaf = 0;
@@ -212,6 +219,12 @@ __global__ void k_compact(int64_t b, int64_t e, const int *__restrict__ sel,
   const int64_t i = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= e) return;
   if (sel[i - b]) out[pos[i - b]] = (int)i;
+}
+
+__global__ void k_box_counts(int64_t n, const int *__restrict__ list, const int *__restrict__ beg,
+                             const int *__restrict__ end, int *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = end[list[i]] - beg[list[i]];
 }
 
 __global__ void k_box_tgt(int64_t ntgt, const int *__restrict__ tgt_box, int *__restrict__ box_tgt) {
@@ -373,10 +386,13 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream
     HPM_LAUNCHED(&launches);
     HPM_TRY(t.cnt.ensure(sizeof(int) * np, st));
     HPM_TRY(t.off.ensure(sizeof(int) * (np + 1), st));
-    k_count_children<<<blocks_for(np), kThreads, 0, st>>>(pb, pe, t.box_flags.as<uint8_t>(),
-                                                          t.box_key.as<uint64_t>(), t.box_beg.as<int>(),
-                                                          t.box_end.as<int>(), skeys, shift,
-                                                          t.cnt.as<int>());
+    HPM_TRY(t.bnd.ensure(sizeof(int) * 8 * np, st));
+    k_octant_bounds<<<blocks_for(8 * np), kThreads, 0, st>>>(pb, pe, t.box_flags.as<uint8_t>(),
+                                                             t.box_key.as<uint64_t>(), t.box_beg.as<int>(),
+                                                             t.box_end.as<int>(), skeys, shift, t.bnd.as<int>());
+    HPM_LAUNCHED(&launches);
+    k_count_children<<<blocks_for(np), kThreads, 0, st>>>(pb, pe, t.box_flags.as<uint8_t>(), t.box_end.as<int>(),
+                                                          t.bnd.as<int>(), t.cnt.as<int>());
     HPM_LAUNCHED(&launches);
     HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), np, t.counters.as<int>() + 64,
                                t.keys_alt, st, &launches));
@@ -390,8 +406,8 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream
       // still write the (empty) child maps of level l-1
       k_fill_children<<<blocks_for(np), kThreads, 0, st>>>(
           pb, pe, pe, l, D, pl->opts.leaf_max, t.box_flags.as<uint8_t>(), t.box_key.as<uint64_t>(),
-          t.box_beg.as<int>(), t.box_end.as<int>(), t.box_parent.as<int>(), t.box_child.as<int>(), skeys,
-          shift, t.off.as<int>(), t.counters.as<int>());
+          t.box_beg.as<int>(), t.box_end.as<int>(), t.box_parent.as<int>(), t.box_child.as<int>(),
+          t.bnd.as<int>(), t.off.as<int>(), t.counters.as<int>());
       HPM_LAUNCHED(&launches);
       for (int r = l; r <= D; ++r) pl->lvl_off[r + 1] = pe;
       break;
@@ -403,8 +419,8 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream
     }
     k_fill_children<<<blocks_for(np), kThreads, 0, st>>>(
         pb, pe, pe, l, D, pl->opts.leaf_max, t.box_flags.as<uint8_t>(), t.box_key.as<uint64_t>(),
-        t.box_beg.as<int>(), t.box_end.as<int>(), t.box_parent.as<int>(), t.box_child.as<int>(), skeys,
-        shift, t.off.as<int>(), t.counters.as<int>());
+        t.box_beg.as<int>(), t.box_end.as<int>(), t.box_parent.as<int>(), t.box_child.as<int>(),
+        t.bnd.as<int>(), t.off.as<int>(), t.counters.as<int>());
     HPM_LAUNCHED(&launches);
     k_neighbours<<<blocks_for(nc), kThreads, 0, st>>>(pe, need, l, t.box_flags.as<uint8_t>(),
                                                       t.box_key.as<uint64_t>(), t.box_parent.as<int>(),
@@ -454,6 +470,16 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream
   pl->nleaf = cnt;
   HPM_TRY(select_boxes(pl, off2, pl->nbox, 2, t.p2g_box, &cnt, st, &launches));
   pl->np2g = cnt;
+  // particle offsets of the P2G boxes (n + 1 entries, the last one the total)
+  HPM_TRY(t.p2g_off.ensure(sizeof(int) * (pl->np2g + 1), st));
+  if (pl->np2g) {
+    HPM_TRY(t.cnt.ensure(sizeof(int) * pl->np2g, st));
+    k_box_counts<<<blocks_for(pl->np2g), kThreads, 0, st>>>(pl->np2g, t.p2g_box.as<int>(), t.box_beg.as<int>(),
+                                                            t.box_end.as<int>(), t.cnt.as<int>());
+    HPM_LAUNCHED(&launches);
+    HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.p2g_off.as<int>(), pl->np2g, t.p2g_off.as<int>() + pl->np2g,
+                               t.keys_alt, st, &launches));
+  }
   // near-field work items
   {
     const int64_t nl = pl->nleaf;
