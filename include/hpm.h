@@ -133,6 +133,39 @@ hpm_status hpm_solve(hpm_plan_t plan, const double *d_pos, const double *d_mass,
                      float *d_acc, void *stream);
 
 /*
+ * hpm_build_tree_batch - trees of P independent problems at once, with the
+ * same launches as one problem: particle i of problem p lies in
+ * [h_offsets[p], h_offsets[p+1]) of the packed arrays. All problems share the
+ * plan's domain, depth, gridlet order, kernel and split rule. hpm_solve then
+ * solves every problem of the batch in one pass over the packed arrays (masses
+ * and outputs packed the same way). Problems may be empty. Needs 3 max_depth +
+ * ceil(log2 P) <= 63. Reads back one count per level (host synchronisation).
+ * Errors as hpm_build_tree.
+ */
+hpm_status hpm_build_tree_batch(hpm_plan_t plan, const double *d_pos, const int64_t *h_offsets, int n_problems,
+                                void *stream);
+
+/* One problem of hpm_solve_batch: caller-owned device buffers, layouts as for
+ * hpm_solve (d_phi / d_acc may be NULL). */
+typedef struct {
+  const double *d_pos;
+  const double *d_mass;
+  int64_t n;
+  float *d_phi;
+  float *d_acc;
+} hpm_problem;
+
+/*
+ * hpm_solve_batch - P independent problems (h_problems, host array of P
+ * descriptors) solved together: the particles are gathered into library-owned
+ * packed buffers by one kernel, the batch tree is built, one solve covers all
+ * problems and one kernel scatters the results back to each problem's buffers.
+ * Each problem's result equals its solve alone (same lists, same arithmetic in
+ * the same order). Host synchronisation as hpm_build_tree_batch.
+ */
+hpm_status hpm_solve_batch(hpm_plan_t plan, const hpm_problem *h_problems, int n_problems, void *stream);
+
+/*
  * hpm_solve_host - the same solve from and to host memory: copies the
  * positions and masses in, builds the tree, solves and copies phi and acc back,
  * then synchronises `stream`. h_phi / h_acc may be NULL.

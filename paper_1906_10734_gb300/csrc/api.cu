@@ -73,7 +73,8 @@ static void release_all(hpm_plan_s *pl, cudaStream_t s) {
                     &pl->t.box_tgt, &pl->t.leaf_box, &pl->t.p2g_box, &pl->t.item_leaf, &pl->t.item_s0,
                     &pl->t.item_s1, &pl->t.leaf_nitem, &pl->t.leaf_item0, &pl->t.leaf_part0, &pl->s.part, &pl->t.err, &pl->t.counters,
                     &pl->s.grid, &pl->s.m2l_raw, &pl->s.loc, &pl->s.locc, &pl->s.m2lc, &pl->gmean, &pl->s.far, &pl->s.m2l_scratch, &pl->s.work,
-                    &pl->host_io_pos, &pl->host_io_mass, &pl->host_io_phi, &pl->host_io_acc};
+                    &pl->host_io_pos, &pl->host_io_mass, &pl->host_io_phi, &pl->host_io_acc, &pl->batch_desc,
+                    &pl->t.offsets};
   for (DevBuf *b : bufs) b->release(s);
 }
 
@@ -156,9 +157,56 @@ hpm_status hpm_build_tree(hpm_plan_t plan, const double *d_pos, int64_t n, void 
   if (!plan || n < 0 || n >= (int64_t)1 << 31 || (n > 0 && !d_pos)) return HPM_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   if (plan->events_ready) cudaEventRecord(plan->ev[8], st);
-  hpm_status s = build_tree(plan, d_pos, n, st);
+  hpm_status s = build_tree(plan, d_pos, n, nullptr, 1, st);
   if (plan->events_ready) cudaEventRecord(plan->ev[9], st);
   return s;
+}
+
+hpm_status hpm_build_tree_batch(hpm_plan_t plan, const double *d_pos, const int64_t *h_offsets, int n_problems,
+                                void *stream) {
+  if (!plan || !h_offsets || n_problems < 1) return HPM_ERR_INVALID_ARG;
+  if (h_offsets[0] != 0) return HPM_ERR_INVALID_ARG;
+  for (int p = 0; p < n_problems; ++p)
+    if (h_offsets[p + 1] < h_offsets[p]) return HPM_ERR_INVALID_ARG;
+  const int64_t n = h_offsets[n_problems];
+  if (n >= (int64_t)1 << 31 || (n > 0 && !d_pos)) return HPM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->events_ready) cudaEventRecord(plan->ev[8], st);
+  hpm_status s = build_tree(plan, d_pos, n, h_offsets, n_problems, st);
+  if (plan->events_ready) cudaEventRecord(plan->ev[9], st);
+  if (s == HPM_OK) plan->prob_off.assign(h_offsets, h_offsets + n_problems + 1);
+  return s;
+}
+
+hpm_status hpm_solve_batch(hpm_plan_t plan, const hpm_problem *h_problems, int n_problems, void *stream) {
+  if (!plan || !h_problems || n_problems < 1) return HPM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int64_t> off(n_problems + 1, 0);
+  for (int p = 0; p < n_problems; ++p) {
+    if (h_problems[p].n < 0 || (h_problems[p].n > 0 && (!h_problems[p].d_pos || !h_problems[p].d_mass)))
+      return HPM_ERR_INVALID_ARG;
+    off[p + 1] = off[p] + h_problems[p].n;
+  }
+  const int64_t n = off[n_problems];
+  if (n >= (int64_t)1 << 31) return HPM_ERR_INVALID_ARG;
+  const size_t nn = n > 0 ? (size_t)n : 1;
+  HPM_TRY(plan->host_io_pos.ensure(sizeof(double) * 3 * nn, st));
+  HPM_TRY(plan->host_io_mass.ensure(sizeof(double) * nn, st));
+  HPM_TRY(plan->host_io_phi.ensure(sizeof(float) * nn, st));
+  HPM_TRY(plan->host_io_acc.ensure(sizeof(float) * 3 * nn, st));
+  HPM_TRY(plan->batch_desc.ensure(sizeof(hpm_problem) * n_problems + sizeof(int64_t) * (n_problems + 1), st));
+  hpm_problem *d_desc = plan->batch_desc.as<hpm_problem>();
+  int64_t *d_off = reinterpret_cast<int64_t *>(d_desc + n_problems);
+  HPM_CUDA(cudaMemcpyAsync(d_desc, h_problems, sizeof(hpm_problem) * n_problems, cudaMemcpyHostToDevice, st));
+  HPM_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * (n_problems + 1), cudaMemcpyHostToDevice, st));
+  HPM_TRY(batch_gather(d_desc, d_off, n_problems, n, plan->host_io_pos.as<double>(), plan->host_io_mass.as<double>(),
+                       st));
+  HPM_TRY(hpm_build_tree_batch(plan, plan->host_io_pos.as<double>(), off.data(), n_problems, stream));
+  HPM_TRY(hpm_solve(plan, plan->host_io_pos.as<double>(), plan->host_io_mass.as<double>(),
+                    plan->host_io_phi.as<float>(), plan->host_io_acc.as<float>(), stream));
+  HPM_TRY(batch_scatter(d_desc, d_off, n_problems, n, plan->host_io_phi.as<float>(), plan->host_io_acc.as<float>(),
+                        st));
+  return HPM_OK;
 }
 
 hpm_status hpm_solve(hpm_plan_t plan, const double *d_pos, const double *d_mass, float *d_phi, float *d_acc,

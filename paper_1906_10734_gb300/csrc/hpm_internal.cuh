@@ -67,6 +67,7 @@ struct TreeDev {
   // items of bounded pair count
   DevBuf item_leaf, item_s0, item_s1, leaf_nitem, leaf_item0, leaf_part0;
   DevBuf err;        // int error word
+  DevBuf offsets;    // problem offsets of a batched build (int64, nprob + 1)
   DevBuf counters;   // small device counters
 };
 
@@ -103,6 +104,8 @@ struct hpm_plan_s {
   hpm::SolveDev s;
   bool built = false;
   int64_t n = 0;
+  int nprob = 1;                   // problems in the built tree (batched builds)
+  std::vector<int64_t> prob_off;   // host copy of the problem offsets
   std::vector<int64_t> lvl_off;    // box offsets per level, size depth+2
   int depth_reached = -1;
   int64_t nbox = 0, ntgt = 0, nleaf = 0, np2g = 0, ncell = 0;
@@ -113,13 +116,15 @@ struct hpm_plan_s {
   cudaEvent_t ev[10] = {};
   bool events_ready = false;
   hpm::DevBuf host_io_pos, host_io_mass, host_io_phi, host_io_acc;
+  hpm::DevBuf batch_desc;          // device copy of a batch's problem table and offsets
 };
 
 namespace hpm {
 // tree.cu
 hpm_status launch_morton_keys(const hpm_domain &dom, int depth, const double *d_pos, int64_t n,
                               uint64_t *d_keys, int *d_err, cudaStream_t st);
-hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream_t st);
+hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int64_t *h_offsets, int nprob,
+                      cudaStream_t st);
 // sort.cu
 hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&vals,
                             uint32_t *&vals_alt, int64_t n, int bits, DevBuf &scratch,
@@ -130,6 +135,10 @@ hpm_status exclusive_scan_i32(const int *in, int *out, int64_t n, int *d_total, 
 hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, float *d_phi,
                  float *d_acc, cudaStream_t st);
 hpm_status precompute_green(hpm_plan_s *pl, cudaStream_t st);
+hpm_status batch_gather(const hpm_problem *d_desc, const int64_t *d_off, int nprob, int64_t n, double *pos,
+                        double *mass, cudaStream_t st);
+hpm_status batch_scatter(const hpm_problem *d_desc, const int64_t *d_off, int nprob, int64_t n, const float *phi,
+                         const float *acc, cudaStream_t st);
 // m2l.cu
 hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches);
 }  // namespace hpm

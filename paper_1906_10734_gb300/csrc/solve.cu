@@ -532,6 +532,44 @@ __global__ void k_green_store(int64_t n, const double *__restrict__ in, double s
   if (i < n) out[i] = i == 0 ? 0.f : (float)(in[i] * scale);
 }
 
+// Packed-array gather and scatter of a batch of separately stored problems.
+__device__ __forceinline__ int problem_of(const int64_t *off, int nprob, int64_t i) {
+  int lo = 0, hi = nprob;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_batch_gather(const hpm_problem *__restrict__ desc, const int64_t *__restrict__ off, int nprob,
+                               int64_t n, double *__restrict__ pos, double *__restrict__ mass) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p = problem_of(off, nprob, i);
+  const int64_t j = i - off[p];
+  const double *src = desc[p].d_pos;
+  pos[3 * i] = src[3 * j];
+  pos[3 * i + 1] = src[3 * j + 1];
+  pos[3 * i + 2] = src[3 * j + 2];
+  mass[i] = desc[p].d_mass[j];
+}
+
+__global__ void k_batch_scatter(const hpm_problem *__restrict__ desc, const int64_t *__restrict__ off, int nprob,
+                                int64_t n, const float *__restrict__ phi, const float *__restrict__ acc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p = problem_of(off, nprob, i);
+  const int64_t j = i - off[p];
+  if (desc[p].d_phi) desc[p].d_phi[j] = phi[i];
+  if (desc[p].d_acc) {
+    desc[p].d_acc[3 * j] = acc[3 * i];
+    desc[p].d_acc[3 * j + 1] = acc[3 * i + 1];
+    desc[p].d_acc[3 * j + 2] = acc[3 * i + 2];
+  }
+}
+
 }  // namespace
 
 hpm_status precompute_green(hpm_plan_s *pl, cudaStream_t st) {
@@ -561,6 +599,22 @@ hpm_status precompute_green(hpm_plan_s *pl, cudaStream_t st) {
   }
   HPM_CUDA(cudaFreeAsync(a, st));
   HPM_CUDA(cudaFreeAsync(b, st));
+  return HPM_OK;
+}
+
+hpm_status batch_gather(const hpm_problem *d_desc, const int64_t *d_off, int nprob, int64_t n, double *pos,
+                        double *mass, cudaStream_t st) {
+  if (n <= 0) return HPM_OK;
+  k_batch_gather<<<blocks_for(n), kThreads, 0, st>>>(d_desc, d_off, nprob, n, pos, mass);
+  HPM_LAUNCHED((int64_t *)nullptr);
+  return HPM_OK;
+}
+
+hpm_status batch_scatter(const hpm_problem *d_desc, const int64_t *d_off, int nprob, int64_t n, const float *phi,
+                         const float *acc, cudaStream_t st) {
+  if (n <= 0) return HPM_OK;
+  k_batch_scatter<<<blocks_for(n), kThreads, 0, st>>>(d_desc, d_off, nprob, n, phi, acc);
+  HPM_LAUNCHED((int64_t *)nullptr);
   return HPM_OK;
 }
 

@@ -44,10 +44,24 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
 // Unit coordinate v = (x - o)/S in IEEE FP64 (no contraction); outside
 // [0, 1] (or NaN) is an error; 21-bit cell coordinate min(floor(v 2^21),
 // 2^21 - 1); level-D key from the top D bits of each coordinate.
+// Batched trees: particle i of problem p (offsets[p] <= i < offsets[p+1]) gets
+// the key (p << 3 D) | morton; sorting then groups particles by problem and
+// the levels of all problems are built by the same launches.
 __global__ void k_keys(const double *__restrict__ pos, int64_t n, double ox, double oy, double oz,
-                       double side, int depth, uint64_t *__restrict__ keys, int *__restrict__ err) {
+                       double side, int depth, uint64_t *__restrict__ keys, int *__restrict__ err,
+                       const int64_t *__restrict__ offsets, int nprob) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  uint64_t prob = 0;
+  if (nprob > 1) {
+    int lo = 0, hi = nprob;  // largest p with offsets[p] <= i
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (offsets[mid] <= i) lo = mid;
+      else hi = mid;
+    }
+    prob = (uint64_t)lo;
+  }
   const double o[3] = {ox, oy, oz};
   uint32_t c[3];
   bool bad = false;
@@ -63,21 +77,53 @@ __global__ void k_keys(const double *__restrict__ pos, int64_t n, double ox, dou
     c[d] = q >> (kMortonBits - depth);
   }
   if (bad) atomicOr(err, kErrDomain);
-  keys[i] = spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+  keys[i] = (prob << (3 * depth)) | spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
 }
 
-__global__ void k_root(int64_t n, int depth, int leaf_max, uint64_t *key, int *beg, int *end,
-                       int *parent, uint8_t *flags, int *child, int *nb, int *counters) {
-  key[0] = 0;
-  beg[0] = 0;
-  end[0] = (int)n;
-  parent[0] = -1;
-  const bool internal = depth > 0 && n > leaf_max;
-  flags[0] = kReal | (internal ? kInternal : kLeaf);
-  for (int k = 0; k < 8; ++k) child[k] = -1;
-  for (int k = 0; k < 27; ++k) nb[k] = k == 13 ? 0 : -1;
-  counters[0] = 1;                     // real cells at level 0
-  counters[32 + 0] = internal ? 0 : 1; // leaves at level 0
+// Particle range of problem p in the sorted order (its level-0 key is p).
+__global__ void k_problem_ranges(int nprob, int64_t n, const uint64_t *__restrict__ skeys, int shift,
+                                 int *__restrict__ rb, int *__restrict__ cnt) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  int lo = 0, hi = (int)n;
+  while (lo < hi) {
+    const int mid = lo + ((hi - lo) >> 1);
+    if ((skeys[mid] >> shift) < (uint64_t)p) lo = mid + 1;
+    else hi = mid;
+  }
+  int e = lo, top = (int)n;
+  while (e < top) {
+    const int mid = e + ((top - e) >> 1);
+    if ((skeys[mid] >> shift) < (uint64_t)p + 1) e = mid + 1;
+    else top = mid;
+  }
+  rb[p] = lo;
+  cnt[p] = e > lo ? 1 : 0;
+}
+
+// The root cell of every nonempty problem (level 0).
+__global__ void k_roots(int nprob, int64_t n, int depth, int leaf_max, const int *__restrict__ rb,
+                        const int *__restrict__ has, const int *__restrict__ slot, uint64_t *key, int *beg,
+                        int *end, int *parent, uint8_t *flags, int *child, int *nb, int *counters) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob || !has[p]) return;
+  const int r = slot[p];
+  int e = (int)n;
+  for (int q = p + 1; q < nprob; ++q)
+    if (has[q]) {
+      e = rb[q];
+      break;
+    }
+  key[r] = (uint64_t)p;
+  beg[r] = rb[p];
+  end[r] = e;
+  parent[r] = -1;
+  const bool internal = depth > 0 && (e - rb[p]) > leaf_max;
+  flags[r] = kReal | (internal ? kInternal : kLeaf);
+  for (int k = 0; k < 8; ++k) child[(int64_t)r * 8 + k] = -1;
+  for (int k = 0; k < 27; ++k) nb[(int64_t)r * 27 + k] = k == 13 ? r : -1;
+  atomicAdd(&counters[0], 1);
+  if (!internal) atomicAdd(&counters[32 + 0], 1);
 }
 
 __global__ void k_expand(int64_t pb, int64_t pe, uint8_t *__restrict__ flags,
@@ -183,7 +229,7 @@ __global__ void k_neighbours(int64_t cb, int64_t ce, int level, const uint8_t *_
     for (int k = 0; k < 27; ++k) nb[i * 27 + k] = -1;
     return;
   }
-  const uint64_t k0 = key[i];
+  const uint64_t k0 = key[i] & ((1ull << (3 * level)) - 1ull);
   const int c[3] = {(int)compact3(k0), (int)compact3(k0 >> 1), (int)compact3(k0 >> 2)};
   const int side = 1 << level;
   const int p = parent[i];
@@ -315,12 +361,13 @@ hpm_status launch_morton_keys(const hpm_domain &dom, int depth, const double *d_
                               uint64_t *d_keys, int *d_err, cudaStream_t st) {
   if (n <= 0) return HPM_OK;
   k_keys<<<blocks_for(n), kThreads, 0, st>>>(d_pos, n, dom.origin[0], dom.origin[1], dom.origin[2], dom.side,
-                                             depth, d_keys, d_err);
+                                             depth, d_keys, d_err, nullptr, 1);
   HPM_LAUNCHED((int64_t *)nullptr);
   return HPM_OK;
 }
 
-hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream_t st) {
+hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int64_t *h_offsets, int nprob,
+                      cudaStream_t st) {
   TreeDev &t = pl->t;
   const int D = pl->max_depth;
   int64_t launches = 0;
@@ -348,14 +395,20 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream
   HPM_TRY(t.keys_alt.ensure(sizeof(uint64_t) * n, st));
   HPM_TRY(t.perm.ensure(sizeof(uint32_t) * n, st));
   HPM_TRY(t.perm_alt.ensure(sizeof(uint32_t) * n, st));
+  int pbits = 0;
+  while ((1ll << pbits) < nprob) ++pbits;
+  if (3 * D + pbits > 63) return HPM_ERR_INVALID_ARG;
+  HPM_TRY(t.offsets.ensure(sizeof(int64_t) * (nprob + 1), st));
+  if (nprob > 1)
+    HPM_CUDA(cudaMemcpyAsync(t.offsets.p, h_offsets, sizeof(int64_t) * (nprob + 1), cudaMemcpyHostToDevice, st));
   k_keys<<<blocks_for(n), kThreads, 0, st>>>(d_pos, n, pl->dom.origin[0], pl->dom.origin[1],
                                              pl->dom.origin[2], pl->dom.side, D, t.keys.as<uint64_t>(),
-                                             t.err.as<int>());
+                                             t.err.as<int>(), t.offsets.as<int64_t>(), nprob);
   HPM_LAUNCHED(&launches);
   uint64_t *k0 = t.keys.as<uint64_t>(), *k1 = t.keys_alt.as<uint64_t>();
   uint32_t *v0 = t.perm.as<uint32_t>(), *v1 = t.perm_alt.as<uint32_t>();
   DevBuf &scratch = t.off;
-  HPM_TRY(radix_sort_pairs(k0, k1, v0, v1, n, 3 * D, scratch, st, &launches));
+  HPM_TRY(radix_sort_pairs(k0, k1, v0, v1, n, 3 * D + pbits, scratch, st, &launches));
   // keep the sorted arrays in keys/perm
   if (k0 != t.keys.as<uint64_t>()) {
     std::swap(t.keys.p, t.keys_alt.p);
@@ -367,16 +420,30 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream
   }
   const uint64_t *skeys = t.keys.as<uint64_t>();
 
-  // level 0
+  // level 0: the root of every nonempty problem
+  HPM_TRY(t.cnt.ensure(sizeof(int) * (nprob + 1), st));
+  HPM_TRY(t.off.ensure(sizeof(int) * (nprob + 1), st));
+  HPM_TRY(t.bnd.ensure(sizeof(int) * (nprob + 1), st));
+  k_problem_ranges<<<blocks_for(nprob), kThreads, 0, st>>>(nprob, n, skeys, 3 * D, t.bnd.as<int>(),
+                                                           t.cnt.as<int>());
+  HPM_LAUNCHED(&launches);
+  HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), nprob, t.counters.as<int>() + 64, t.keys_alt, st,
+                             &launches));
+  int nroot = 0;
+  HPM_CUDA(cudaMemcpyAsync(&nroot, t.counters.as<int>() + 64, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HPM_CUDA(cudaStreamSynchronize(st));
   int64_t cap = t.box_key.cap / sizeof(uint64_t);
-  if (cap < 1024) cap = 1024;
+  if (cap < 1024 + 2 * (int64_t)nroot) cap = 1024 + 2 * (int64_t)nroot;
   HPM_TRY(ensure_boxes(t, cap, st));
-  k_root<<<1, 1, 0, st>>>(n, D, pl->opts.leaf_max, t.box_key.as<uint64_t>(), t.box_beg.as<int>(),
-                          t.box_end.as<int>(), t.box_parent.as<int>(), t.box_flags.as<uint8_t>(),
-                          t.box_child.as<int>(), t.box_nb.as<int>(), t.counters.as<int>());
+  k_roots<<<blocks_for(nprob), kThreads, 0, st>>>(nprob, n, D, pl->opts.leaf_max, t.bnd.as<int>(), t.cnt.as<int>(),
+                                                  t.off.as<int>(), t.box_key.as<uint64_t>(), t.box_beg.as<int>(),
+                                                  t.box_end.as<int>(), t.box_parent.as<int>(),
+                                                  t.box_flags.as<uint8_t>(), t.box_child.as<int>(),
+                                                  t.box_nb.as<int>(), t.counters.as<int>());
   HPM_LAUNCHED(&launches);
   pl->lvl_off[0] = 0;
-  pl->lvl_off[1] = 1;
+  pl->lvl_off[1] = nroot;
+  pl->nprob = nprob;
   int reached = 0;
   for (int l = 1; l <= D; ++l) {
     const int64_t pb = pl->lvl_off[l - 1], pe = pl->lvl_off[l];
@@ -429,10 +496,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, cudaStream
     pl->lvl_off[l + 1] = need;
     reached = l;
   }
-  if (D == 0) {
-    // the root is the only box; its children do not exist
-    pl->lvl_off[1] = 1;
-  }
+  if (D == 0) pl->lvl_off[1] = nroot;  // the roots are the only boxes
   {
     // child maps of the deepest level are never filled: mark them empty
     const int64_t b = pl->lvl_off[reached], e = pl->lvl_off[reached + 1];

@@ -39,6 +39,11 @@ class hpm_plan_opts(ctypes.Structure):
     _fields_ = [("leaf_max", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
+class hpm_problem(ctypes.Structure):
+    _fields_ = [("d_pos", ctypes.c_void_p), ("d_mass", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("d_phi", ctypes.c_void_p), ("d_acc", ctypes.c_void_p)]
+
+
 class hpm_lists_info(ctypes.Structure):
     _fields_ = [("n_particles", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("n_targets", ctypes.c_int64),
                 ("n_leaves", ctypes.c_int64), ("n_boxes", ctypes.c_int64), ("max_depth", ctypes.c_int),
@@ -57,6 +62,8 @@ SIGNATURES = {
     "hpm_build_tree": ([_vp, _vp, _i64, _vp], _i32),
     "hpm_solve": ([_vp, _vp, _vp, _vp, _vp, _vp], _i32),
     "hpm_solve_host": ([_vp, _vp, _vp, _i64, _vp, _vp, _vp], _i32),
+    "hpm_build_tree_batch": ([_vp, _vp, _vp, _i32, _vp], _i32),
+    "hpm_solve_batch": ([_vp, ctypes.POINTER(hpm_problem), _i32, _vp], _i32),
     "hpm_get_lists_info": ([_vp, ctypes.POINTER(hpm_lists_info)], _i32),
     "hpm_get_lists": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
     "hpm_get_stats": ([_vp, ctypes.POINTER(hpm_stats)], _i32),
@@ -138,6 +145,21 @@ def hpm_build_tree(plan: int, d_pos, n: int, stream=None):
 def hpm_solve(plan: int, d_pos, d_mass, d_phi, d_acc, stream=None):
     _check("hpm_solve", load().hpm_solve(plan, _ptr(d_pos), _ptr(d_mass), _ptr(d_phi), _ptr(d_acc),
                                          _stream(stream)))
+
+
+def hpm_build_tree_batch(plan: int, d_pos, offsets, stream=None):
+    """Trees of P problems packed in d_pos; offsets: P + 1 int64 (host)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    _check("hpm_build_tree_batch", load().hpm_build_tree_batch(plan, _ptr(d_pos), off.ctypes.data, off.shape[0] - 1,
+                                                               _stream(stream)))
+
+
+def hpm_solve_batch(plan: int, problems, stream=None):
+    """problems: sequence of (d_pos, d_mass, d_phi, d_acc) torch tensors (phi/acc may be None)."""
+    arr = (hpm_problem * len(problems))()
+    for k, (pos, mass, phi, acc) in enumerate(problems):
+        arr[k] = hpm_problem(_ptr(pos), _ptr(mass), int(pos.shape[0]), _ptr(phi), _ptr(acc))
+    _check("hpm_solve_batch", load().hpm_solve_batch(plan, arr, len(problems), _stream(stream)))
 
 
 def hpm_solve_host(plan: int, h_pos: np.ndarray, h_mass: np.ndarray, h_phi: np.ndarray = None,
