@@ -268,6 +268,130 @@ def run_gpu(args) -> None:
         dist.destroy_process_group()
 
 
+def run_batch(args) -> None:
+    """256 independent problems (N log-uniform in [1e3, 1e6], Plummer or uniform by coin
+    flip, adaptive <= 32, Ng = 4, eps = 1e-4): one batched solve per step, and the same
+    problems solved one after another with the same plan for comparison."""
+    import torch
+    from paper_1906_10734_gb300 import build as B, hpm
+    B.build()
+    dev = torch.device("cuda", 0)
+    P = args.problems
+    ws = [I.batch_problem(k) for k in range(P)]
+    bufs = [(torch.from_numpy(w.pos).to(dev), torch.from_numpy(w.mass).to(dev),
+             torch.zeros(w.n, dtype=torch.float32, device=dev), torch.zeros((w.n, 3), dtype=torch.float32, device=dev))
+            for w in ws]
+    n_total = sum(w.n for w in ws)
+    plan = hpm.hpm_plan((0.0, 0.0, 0.0), 1.0, 12, 4, 1e-4, 32, flags=1)
+    stream = torch.cuda.current_stream(dev)
+    l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        hpm.hpm_solve_batch(plan, bufs, stream)
+    torch.cuda.synchronize(dev)
+    step_ms, m2l_ms, launches = [], [], 0
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            l2_flush.fill_(k & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            hpm.hpm_solve_batch(plan, bufs, stream)
+            b.record(stream)
+            b.synchronize()
+            st = hpm.hpm_get_stats(plan)
+            m2l_ms.append(st["ms_m2l"])
+            launches += st["launches"]
+            step_ms.append(a.elapsed_time(b))
+    info = hpm.hpm_get_lists_info(plan)
+    # the same problems one by one with the same plan
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for (pos, mass, phi, acc) in bufs:
+        hpm.hpm_build_tree(plan, pos, pos.shape[0], stream)
+        hpm.hpm_solve(plan, pos, mass, phi, acc, stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    loop_ms = a.elapsed_time(b)
+    hpm.hpm_destroy(plan)
+    total = sum(step_ms)
+    value = n_total * args.steps / (total / 1e3)
+    m2l = statistics.mean(m2l_ms)
+    achieved = m2l_flops_per_target(4) * info["n_targets"] / (m2l / 1e3) / 1e12
+    peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * measured_peaks().get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch of {P} problems, N log-uniform in [1e3, 1e6] (sum {n_total}), Plummer or "
+                               "uniform by coin flip, adaptive <=32/leaf, depth<=12, gridlet 4^3, eps=1e-4",
+                   "problems": P, "n": n_total, "targets": info["n_targets"],
+                   "l2": "flushed between steps (256 MiB write outside the timed events)"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "per_problem_loop": {"value": n_total / (loop_ms / 1e3), "ms": loop_ms,
+                             "speedup_of_batch": loop_ms / (total / args.steps)},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "source-to-target FFT convolution (k_m2l4)", "bound": "alu", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "ms_per_launch": m2l},
+        "clocks": clk.summary()}), flush=True)
+
+
+def run_serve(args) -> None:
+    """Poisson request stream (mean rate --rate req/s) of solves with N log-uniform in
+    [1e4, 4e6], Plummer or uniform by coin flip, through the continuous-batching server.
+    Requests reuse a pool of --pool seeded payloads held in pinned host memory."""
+    import torch
+    from paper_1906_10734_gb300 import build as B, hpm
+    B.build()
+    pool = []
+    for k in range(args.pool):
+        w = I.batch_problem(k, 1e4, 4e6, seed=5)
+        pool.append((torch.from_numpy(w.pos).pin_memory(), torch.from_numpy(w.mass).pin_memory(),
+                     torch.zeros(w.n, dtype=torch.float32).pin_memory(),
+                     torch.zeros((w.n, 3), dtype=torch.float32).pin_memory()))
+    rng = np.random.default_rng(5)
+    sv = hpm.Server(max_depth=12, gridlet_order=4, eps=1e-4, leaf_max=32, workers=args.workers,
+                    max_batch=args.max_batch, hbm_budget_bytes=150 << 30)
+
+    def drive(seconds):
+        t0 = time.perf_counter()
+        t_next = t0
+        tickets = []
+        offered = 0
+        while True:
+            t_next += rng.exponential(1.0 / args.rate)
+            if t_next - t0 > seconds:
+                break
+            now = time.perf_counter()
+            if t_next > now:
+                time.sleep(t_next - now)
+            k = int(rng.integers(len(pool)))
+            tickets.append(sv.submit(*pool[k]))
+            offered += pool[k][0].shape[0]
+        for t in tickets:
+            sv.wait(t, 600000)
+        return offered, time.perf_counter() - t0, len(tickets)
+
+    drive(args.serve_warmup_s)
+    sv.reset_stats()
+    with ClockSampler(0) as clk:
+        offered, span, nreq = drive(args.serve_seconds)
+    st = sv.stats()
+    sv.close()
+    print(json.dumps({
+        "metric": METRIC, "value": st["particles_per_s"], "unit": UNIT, "n_gpus": 1, "steps": nreq,
+        "warmup": int(args.serve_warmup_s), "ms_per_step": st["mean_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"Poisson requests, mean {args.rate}/s, N log-uniform in [1e4, 4e6] (pool of "
+                               f"{args.pool} seeded payloads, Plummer or uniform), adaptive <=32/leaf, depth<=12, "
+                               "gridlet 4^3, eps=1e-4, pinned host buffers in and out",
+                   "workers": args.workers, "max_batch": args.max_batch, "hbm_budget_gb": 150,
+                   "seconds": args.serve_seconds},
+        "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "mean": st["mean_ms"]},
+        "offered_particles_per_s": offered / args.serve_seconds, "requests": st["completed"],
+        "batches": st["batches"], "clocks": clk.summary()}), flush=True)
+
+
 def oracle_step(n: int):
     """One timed oracle solve on a reduced Plummer problem of the same recipe."""
     import oracle as O
@@ -323,6 +447,14 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="plummer", choices=["plummer", "batch", "serve"])
+    ap.add_argument("--problems", type=int, default=256)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--pool", type=int, default=32)
+    ap.add_argument("--workers", type=int, default=2)
+    ap.add_argument("--max-batch", type=int, default=32)
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-warmup-s", type=float, default=3.0)
     ap.add_argument("--n", type=int, default=None, help="particles per problem (default 2^21)")
     ap.add_argument("--cpu-sample", type=int, default=1 << 15)
     ap.add_argument("--ref-sample", type=int, default=1 << 14)
@@ -332,6 +464,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

@@ -244,6 +244,64 @@ typedef struct {
 
 hpm_status hpm_get_stats(hpm_plan_t plan, hpm_stats *stats);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of independent solves (no counterpart in the
+ * paper; it serves the same solve to a stream of requests).
+ * ------------------------------------------------------------------------ */
+typedef struct hpm_server_s *hpm_server_t;
+
+typedef struct {
+  hpm_domain dom;           /* shared by every request                          */
+  int max_depth;
+  int gridlet_order;
+  hpm_green green;
+  int leaf_max;
+  int workers;              /* worker threads, each with its own plan and stream
+                               (>= 2 lets batches overlap on the device; 0 admits
+                               requests but never runs them)                      */
+  int max_batch;            /* requests per batch, >= 1                          */
+  int64_t hbm_budget_bytes; /* admission bound on the estimated device memory of
+                               all batches in flight                              */
+} hpm_server_opts;
+
+/* One request. pos (N x 3 FP64) and mass (N FP64) are read, phi (N FP32) and
+ * acc (N x 3 FP32) written; each may be host or device memory (copies use
+ * unified addressing). The buffers must stay valid until the request is done
+ * or cancelled. */
+typedef struct {
+  const double *pos;
+  const double *mass;
+  int64_t n;
+  float *phi;
+  float *acc;
+} hpm_request;
+
+typedef struct {
+  int64_t submitted, completed, rejected, cancelled, failed, batches, queued;
+  int64_t in_flight_bytes;  /* estimated device bytes of the batches in flight */
+  int64_t particles;        /* particles of completed requests                 */
+  double p50_ms, p99_ms, mean_ms;   /* submit -> results in the caller's buffers */
+  double particles_per_s;   /* completed particles / (last completion - first submit) */
+} hpm_server_stats;
+
+/* Creates the worker plans (hpm_plan, synchronises) and starts the workers.
+ * Errors: HPM_ERR_INVALID_ARG, and those of hpm_plan. */
+hpm_status hpm_server_create(const hpm_server_opts *opts, hpm_server_t *out);
+/* Queues a request; *ticket identifies it. A request whose estimated footprint
+ * exceeds the whole budget is refused with HPM_ERR_OOM. Never blocks on the GPU. */
+hpm_status hpm_server_submit(hpm_server_t server, const hpm_request *req, uint64_t *ticket);
+/* *done: 1 finished, 0 pending, -1 cancelled or failed; latency in ms once done. */
+hpm_status hpm_server_poll(hpm_server_t server, uint64_t ticket, int *done, double *latency_ms);
+/* Waits at most timeout_ms (bounded wait): HPM_ERR_TIMEOUT if still pending,
+ * HPM_ERR_INVALID_ARG if it was cancelled. */
+hpm_status hpm_server_wait(hpm_server_t server, uint64_t ticket, int timeout_ms, double *latency_ms);
+/* Cancels a request that is still queued; HPM_ERR_BUSY once it runs or ran. */
+hpm_status hpm_server_cancel(hpm_server_t server, uint64_t ticket);
+hpm_status hpm_server_get_stats(hpm_server_t server, hpm_server_stats *stats);
+hpm_status hpm_server_reset_stats(hpm_server_t server);
+/* Stops the workers after their current batch and frees everything. */
+hpm_status hpm_server_destroy(hpm_server_t server);
+
 /*
  * hpm_sort_particles_static - the Morton keys of N positions and their stable
  * sort, the first step of hpm_build_tree, without allocating any memory. The

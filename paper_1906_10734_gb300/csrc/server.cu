@@ -1,0 +1,341 @@
+// Serving loop: continuous batching of independent gravity solves.
+//
+// Requests join a FIFO queue. Each worker thread owns a plan, a CUDA stream
+// and packed device buffers; when free it takes the longest prefix of the
+// queue that fits the batch limit and the device-memory budget (the estimated
+// footprint of every batch in flight counts against it), copies the requests'
+// particles into its packed buffers, builds one batched tree, solves, and
+// copies each request's results back. With two or more workers, a batch that
+// arrives while another is on the GPU is admitted as soon as memory allows and
+// its work overlaps the other's on the device. A request's results equal its
+// solve alone (batched solves reproduce single solves bit for bit).
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "hpm_internal.cuh"
+
+namespace hpm {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t id = 0;
+  hpm_request req{};
+  int64_t footprint = 0;
+  Clock::time_point t_submit, t_done;
+  int state = 0;  // 0 queued, 1 running, 2 done, -1 cancelled, -2 failed
+  hpm_status status = HPM_OK;
+};
+
+struct Worker {
+  std::thread th;
+  hpm_plan_t plan = nullptr;
+  cudaStream_t stream = nullptr;
+  DevBuf pos, mass, phi, acc;
+};
+
+}  // namespace
+}  // namespace hpm
+
+struct hpm_server_s {
+  hpm_server_opts opts{};
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<hpm::Request *> queue;
+  std::unordered_map<uint64_t, hpm::Request *> reqs;
+  std::vector<hpm::Worker *> workers;
+  bool stop = false;
+  uint64_t next_id = 1;
+  int64_t inflight_bytes = 0;
+  int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, cancelled = 0, failed = 0;
+  int64_t particles_done = 0;
+  std::vector<double> latencies_ms;
+  hpm::Clock::time_point t_first, t_last;
+  bool any_done = false;
+};
+
+namespace hpm {
+namespace {
+
+// Device bytes a request needs while its batch runs: packed inputs and
+// outputs, keys and permutation (double buffered), sorted copies, and the
+// boxes, gridlets and locals of about one box per five particles.
+int64_t footprint_of(int64_t n) { return n * 512 + (1ll << 20); }
+
+void worker_loop(hpm_server_s *sv, Worker *w) {
+  cudaSetDevice(sv->device);
+  for (;;) {
+    std::vector<Request *> batch;
+    int64_t bytes = 0;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      for (;;) {
+        if (sv->stop) return;
+        while (!sv->queue.empty() && sv->queue.front()->state == -1) sv->queue.pop_front();
+        if (!sv->queue.empty()) {
+          Request *r = sv->queue.front();
+          if (sv->inflight_bytes + r->footprint <= sv->opts.hbm_budget_bytes) break;
+        }
+        sv->cv_work.wait(lk);
+      }
+      while (!sv->queue.empty() && (int)batch.size() < sv->opts.max_batch) {
+        Request *r = sv->queue.front();
+        if (r->state == -1) {
+          sv->queue.pop_front();
+          continue;
+        }
+        if (sv->inflight_bytes + bytes + r->footprint > sv->opts.hbm_budget_bytes) break;
+        sv->queue.pop_front();
+        r->state = 1;
+        bytes += r->footprint;
+        batch.push_back(r);
+      }
+      sv->inflight_bytes += bytes;
+      ++sv->batches;
+    }
+    // run the batch
+    std::vector<int64_t> off(batch.size() + 1, 0);
+    for (size_t k = 0; k < batch.size(); ++k) off[k + 1] = off[k] + batch[k]->req.n;
+    const int64_t n = off.back();
+    hpm_status s = HPM_OK;
+    const size_t nn = n > 0 ? (size_t)n : 1;
+    if (s == HPM_OK) s = w->pos.ensure(sizeof(double) * 3 * nn, w->stream);
+    if (s == HPM_OK) s = w->mass.ensure(sizeof(double) * nn, w->stream);
+    if (s == HPM_OK) s = w->phi.ensure(sizeof(float) * nn, w->stream);
+    if (s == HPM_OK) s = w->acc.ensure(sizeof(float) * 3 * nn, w->stream);
+    for (size_t k = 0; k < batch.size() && s == HPM_OK; ++k) {
+      const hpm_request &q = batch[k]->req;
+      if (q.n == 0) continue;
+      if (cudaMemcpyAsync(w->pos.as<double>() + 3 * off[k], q.pos, sizeof(double) * 3 * q.n, cudaMemcpyDefault,
+                          w->stream) != cudaSuccess ||
+          cudaMemcpyAsync(w->mass.as<double>() + off[k], q.mass, sizeof(double) * q.n, cudaMemcpyDefault,
+                          w->stream) != cudaSuccess)
+        s = HPM_ERR_CUDA;
+    }
+    if (s == HPM_OK) s = hpm_build_tree_batch(w->plan, w->pos.as<double>(), off.data(), (int)batch.size(), w->stream);
+    if (s == HPM_OK)
+      s = hpm_solve(w->plan, w->pos.as<double>(), w->mass.as<double>(), w->phi.as<float>(), w->acc.as<float>(),
+                    w->stream);
+    for (size_t k = 0; k < batch.size() && s == HPM_OK; ++k) {
+      const hpm_request &q = batch[k]->req;
+      if (q.n == 0) continue;
+      if ((q.phi && cudaMemcpyAsync(q.phi, w->phi.as<float>() + off[k], sizeof(float) * q.n, cudaMemcpyDefault,
+                                    w->stream) != cudaSuccess) ||
+          (q.acc && cudaMemcpyAsync(q.acc, w->acc.as<float>() + 3 * off[k], sizeof(float) * 3 * q.n,
+                                    cudaMemcpyDefault, w->stream) != cudaSuccess))
+        s = HPM_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(w->stream) != cudaSuccess && s == HPM_OK) s = HPM_ERR_CUDA;
+    const Clock::time_point now = Clock::now();
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->inflight_bytes -= bytes;
+      for (Request *r : batch) {
+        r->t_done = now;
+        r->status = s;
+        r->state = s == HPM_OK ? 2 : -2;
+        if (s == HPM_OK) {
+          ++sv->completed;
+          sv->particles_done += r->req.n;
+          sv->latencies_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
+          if (!sv->any_done) sv->t_first = r->t_submit;
+          sv->any_done = true;
+          sv->t_last = now;
+        } else {
+          ++sv->failed;
+        }
+      }
+    }
+    sv->cv_done.notify_all();
+    sv->cv_work.notify_all();
+  }
+}
+
+double percentile(std::vector<double> v, double q) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  const double pos = q * (double)(v.size() - 1);
+  const size_t i = (size_t)pos;
+  const double f = pos - (double)i;
+  return i + 1 < v.size() ? v[i] * (1.0 - f) + v[i + 1] * f : v[i];
+}
+
+}  // namespace
+}  // namespace hpm
+
+using namespace hpm;
+
+extern "C" {
+
+hpm_status hpm_server_create(const hpm_server_opts *opts, hpm_server_t *out) {
+  if (!opts || !out) return HPM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (opts->workers < 0 || opts->workers > 16 || opts->max_batch < 1 || opts->hbm_budget_bytes <= 0)
+    return HPM_ERR_INVALID_ARG;
+  hpm_server_s *sv = new (std::nothrow) hpm_server_s();
+  if (!sv) return HPM_ERR_OOM;
+  sv->opts = *opts;
+  cudaGetDevice(&sv->device);
+  hpm_plan_opts po{opts->leaf_max, 0};
+  for (int k = 0; k < opts->workers; ++k) {
+    Worker *w = new Worker();
+    hpm_status s = hpm_plan(&opts->dom, opts->max_depth, opts->gridlet_order, &opts->green, &po, &w->plan);
+    if (s == HPM_OK && cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) s = HPM_ERR_CUDA;
+    if (s != HPM_OK) {
+      if (w->plan) hpm_destroy(w->plan);
+      delete w;
+      for (Worker *o : sv->workers) {
+        hpm_destroy(o->plan);
+        cudaStreamDestroy(o->stream);
+        delete o;
+      }
+      delete sv;
+      return s;
+    }
+    sv->workers.push_back(w);
+  }
+  for (Worker *w : sv->workers) w->th = std::thread(worker_loop, sv, w);
+  *out = sv;
+  return HPM_OK;
+}
+
+hpm_status hpm_server_submit(hpm_server_t sv, const hpm_request *req, uint64_t *ticket) {
+  if (!sv || !req || !ticket || req->n < 0) return HPM_ERR_INVALID_ARG;
+  if (req->n > 0 && (!req->pos || !req->mass)) return HPM_ERR_INVALID_ARG;
+  Request *r = new (std::nothrow) Request();
+  if (!r) return HPM_ERR_OOM;
+  r->req = *req;
+  r->footprint = footprint_of(req->n);
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (r->footprint > sv->opts.hbm_budget_bytes) {
+      ++sv->rejected;
+      delete r;
+      return HPM_ERR_OOM;
+    }
+    r->id = sv->next_id++;
+    r->t_submit = Clock::now();
+    sv->reqs[r->id] = r;
+    sv->queue.push_back(r);
+    ++sv->submitted;
+    *ticket = r->id;
+  }
+  sv->cv_work.notify_one();
+  return HPM_OK;
+}
+
+hpm_status hpm_server_poll(hpm_server_t sv, uint64_t ticket, int *done, double *latency_ms) {
+  if (!sv || !done) return HPM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return HPM_ERR_INVALID_ARG;
+  Request *r = it->second;
+  *done = r->state == 2 ? 1 : (r->state < 0 ? -1 : 0);
+  if (latency_ms)
+    *latency_ms = r->state == 2 ? std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count() : 0.0;
+  return r->state == -2 ? r->status : HPM_OK;
+}
+
+hpm_status hpm_server_wait(hpm_server_t sv, uint64_t ticket, int timeout_ms, double *latency_ms) {
+  if (!sv) return HPM_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return HPM_ERR_INVALID_ARG;
+  Request *r = it->second;
+  const bool ok = sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
+                                       [r] { return r->state == 2 || r->state < 0; });
+  if (!ok) return HPM_ERR_TIMEOUT;
+  if (latency_ms)
+    *latency_ms = r->state == 2 ? std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count() : 0.0;
+  if (r->state == -1) return HPM_ERR_INVALID_ARG;
+  return r->state == 2 ? HPM_OK : r->status;
+}
+
+hpm_status hpm_server_cancel(hpm_server_t sv, uint64_t ticket) {
+  if (!sv) return HPM_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return HPM_ERR_INVALID_ARG;
+    Request *r = it->second;
+    if (r->state != 0) return HPM_ERR_BUSY;  // already running or finished
+    r->state = -1;
+    ++sv->cancelled;
+  }
+  sv->cv_done.notify_all();
+  sv->cv_work.notify_all();
+  return HPM_OK;
+}
+
+hpm_status hpm_server_get_stats(hpm_server_t sv, hpm_server_stats *st) {
+  if (!sv || !st) return HPM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  memset(st, 0, sizeof(*st));
+  st->submitted = sv->submitted;
+  st->completed = sv->completed;
+  st->rejected = sv->rejected;
+  st->cancelled = sv->cancelled;
+  st->failed = sv->failed;
+  st->batches = sv->batches;
+  int64_t queued = 0;
+  for (Request *r : sv->queue)
+    if (r->state == 0) ++queued;
+  st->queued = queued;
+  st->in_flight_bytes = sv->inflight_bytes;
+  st->particles = sv->particles_done;
+  st->p50_ms = percentile(sv->latencies_ms, 0.50);
+  st->p99_ms = percentile(sv->latencies_ms, 0.99);
+  double mean = 0.0;
+  for (double v : sv->latencies_ms) mean += v;
+  st->mean_ms = sv->latencies_ms.empty() ? 0.0 : mean / (double)sv->latencies_ms.size();
+  if (sv->any_done) {
+    const double span = std::chrono::duration<double>(sv->t_last - sv->t_first).count();
+    st->particles_per_s = span > 0 ? (double)sv->particles_done / span : 0.0;
+  }
+  return HPM_OK;
+}
+
+hpm_status hpm_server_reset_stats(hpm_server_t sv) {
+  if (!sv) return HPM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  sv->latencies_ms.clear();
+  sv->particles_done = 0;
+  sv->completed = sv->submitted = sv->batches = sv->rejected = sv->cancelled = sv->failed = 0;
+  sv->any_done = false;
+  return HPM_OK;
+}
+
+hpm_status hpm_server_destroy(hpm_server_t sv) {
+  if (!sv) return HPM_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv_work.notify_all();
+  for (Worker *w : sv->workers)
+    if (w->th.joinable()) w->th.join();
+  for (Worker *w : sv->workers) {
+    w->pos.release(w->stream);
+    w->mass.release(w->stream);
+    w->phi.release(w->stream);
+    w->acc.release(w->stream);
+    cudaStreamSynchronize(w->stream);
+    hpm_destroy(w->plan);
+    cudaStreamDestroy(w->stream);
+    delete w;
+  }
+  for (auto &kv : sv->reqs) delete kv.second;
+  delete sv;
+  return HPM_OK;
+}
+
+}  // extern "C"

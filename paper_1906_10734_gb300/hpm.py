@@ -44,6 +44,23 @@ class hpm_problem(ctypes.Structure):
                 ("d_phi", ctypes.c_void_p), ("d_acc", ctypes.c_void_p)]
 
 
+class hpm_server_opts(ctypes.Structure):
+    _fields_ = [("dom", hpm_domain), ("max_depth", ctypes.c_int), ("gridlet_order", ctypes.c_int),
+                ("green", hpm_green), ("leaf_max", ctypes.c_int), ("workers", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64)]
+
+
+class hpm_request(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_void_p), ("mass", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("phi", ctypes.c_void_p), ("acc", ctypes.c_void_p)]
+
+
+class hpm_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "rejected", "cancelled", "failed",
+                                              "batches", "queued", "in_flight_bytes", "particles")] + \
+               [(k, ctypes.c_double) for k in ("p50_ms", "p99_ms", "mean_ms", "particles_per_s")]
+
+
 class hpm_lists_info(ctypes.Structure):
     _fields_ = [("n_particles", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("n_targets", ctypes.c_int64),
                 ("n_leaves", ctypes.c_int64), ("n_boxes", ctypes.c_int64), ("max_depth", ctypes.c_int),
@@ -70,6 +87,14 @@ SIGNATURES = {
     "hpm_get_boxes": ([_vp, _vp, _vp, _vp], _i32),
     "hpm_get_stage": ([_vp, _i32, _vp, _i64], _i32),
     "hpm_sort_particles_static": ([ctypes.POINTER(hpm_domain), _i32, _vp, _i64, _vp, _vp, _vp], _i32),
+    "hpm_server_create": ([ctypes.POINTER(hpm_server_opts), ctypes.POINTER(_vp)], _i32),
+    "hpm_server_submit": ([_vp, ctypes.POINTER(hpm_request), ctypes.POINTER(ctypes.c_uint64)], _i32),
+    "hpm_server_poll": ([_vp, ctypes.c_uint64, ctypes.POINTER(_i32), ctypes.POINTER(_f64)], _i32),
+    "hpm_server_wait": ([_vp, ctypes.c_uint64, _i32, ctypes.POINTER(_f64)], _i32),
+    "hpm_server_cancel": ([_vp, ctypes.c_uint64], _i32),
+    "hpm_server_get_stats": ([_vp, ctypes.POINTER(hpm_server_stats)], _i32),
+    "hpm_server_reset_stats": ([_vp], _i32),
+    "hpm_server_destroy": ([_vp], _i32),
     "hpm_destroy": ([_vp], _i32),
     "hpm_status_str": ([_i32], ctypes.c_char_p),
     "hpm_last_cuda_error": ([], ctypes.c_char_p),
@@ -224,6 +249,71 @@ def hpm_get_stats(plan: int) -> dict:
     st = hpm_stats()
     _check("hpm_get_stats", load().hpm_get_stats(plan, ctypes.byref(st)))
     return {k: getattr(st, k) for k, _ in hpm_stats._fields_}
+
+
+def _addr(a):
+    """Address of a torch tensor or numpy array (host or device); None -> NULL."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+class Server:
+    """Continuous-batching solver service (hpm_server_*). Buffers of a request may be
+    host numpy arrays or device tensors and must stay alive until it is done."""
+
+    def __init__(self, max_depth=12, gridlet_order=4, eps=1e-4, leaf_max=32, workers=2, max_batch=64,
+                 hbm_budget_bytes=150 << 30, origin=(0.0, 0.0, 0.0), side=1.0):
+        L = load()
+        opts = hpm_server_opts(hpm_domain((ctypes.c_double * 3)(*origin), side), max_depth, gridlet_order,
+                               hpm_green(HPM_GREEN_PLUMMER, eps), leaf_max, workers, max_batch, hbm_budget_bytes)
+        h = _vp()
+        _check("hpm_server_create", L.hpm_server_create(ctypes.byref(opts), ctypes.byref(h)))
+        self.h = h.value
+        self._keep = {}
+
+    def submit(self, pos, mass, phi, acc) -> int:
+        req = hpm_request(_addr(pos), _addr(mass), int(pos.shape[0]), _addr(phi), _addr(acc))
+        t = ctypes.c_uint64()
+        _check("hpm_server_submit", load().hpm_server_submit(self.h, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = (pos, mass, phi, acc)
+        return t.value
+
+    def poll(self, ticket):
+        d, lat = _i32(), _f64()
+        _check("hpm_server_poll", load().hpm_server_poll(self.h, ticket, ctypes.byref(d), ctypes.byref(lat)))
+        return d.value, lat.value
+
+    def wait(self, ticket, timeout_ms=60000):
+        lat = _f64()
+        _check("hpm_server_wait", load().hpm_server_wait(self.h, ticket, timeout_ms, ctypes.byref(lat)))
+        self._keep.pop(ticket, None)
+        return lat.value
+
+    def cancel(self, ticket):
+        _check("hpm_server_cancel", load().hpm_server_cancel(self.h, ticket))
+
+    def stats(self) -> dict:
+        st = hpm_server_stats()
+        _check("hpm_server_get_stats", load().hpm_server_get_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in hpm_server_stats._fields_}
+
+    def reset_stats(self):
+        _check("hpm_server_reset_stats", load().hpm_server_reset_stats(self.h))
+
+    def close(self):
+        if self.h:
+            _check("hpm_server_destroy", load().hpm_server_destroy(self.h))
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 HPM_STATIC_SORT_MAX_N = 1048576
