@@ -145,6 +145,20 @@ def profile_traffic(kernel_src: str) -> float | None:
     return None
 
 
+def reduce_over_ranks(total_ms: float, n_local: int, device=None):
+    """Replica aggregation: the job time is the slowest rank's, the work is every rank's
+    particles (weak scaling, no data-path collective; this is bookkeeping only)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return total_ms, n_local
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    n = torch.tensor([n_local], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
+
+
 # ---------------------------------------------------------------------------
 def run_gpu(args) -> None:
     import torch
@@ -203,11 +217,7 @@ def run_gpu(args) -> None:
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, n_all = reduce_over_ranks(sum(step_ms), w.n, dev)
     clocks = clk.summary()
 
     # end to end through the host-memory entry point: pinned inputs in, results out
@@ -228,7 +238,7 @@ def run_gpu(args) -> None:
         if world > 1:
             dist.destroy_process_group()
         return
-    n_total = w.n * world
+    n_total = n_all
     ms_per_step = total_ms / args.steps
     value = n_total * args.steps / (total_ms / 1e3)
     peaks = measured_peaks()
