@@ -46,7 +46,13 @@ def m2l_flops_per_target(ng: int) -> float:
     return 5.0 * P ** 3 * math.log2(P ** 3) + 2.0 * P * P * (P // 2 + 1)
 
 
-def workload_for(rank: int, n_override: int | None = None) -> I.Workload:
+def workload_for(rank: int, n_override: int | None = None, kind: str = "plummer", ng: int = 4) -> I.Workload:
+    if kind == "uniform":
+        n = n_override or (1 << 24)
+        w = I.uniform_16m_depth7(ng=ng, n=n)
+        if rank:
+            w.pos = I.uniform_cube(n, 3 + 1000 * rank)
+        return w
     n = n_override or (1 << 21)
     w = I.plummer_2m_adaptive(ng=4, n=n) if rank == 0 else I.Workload(
         f"plummer{n}_adaptive32_depth12_rank{rank}", I.plummer_sphere(n, 2 + 1000 * rank),
@@ -55,8 +61,10 @@ def workload_for(rank: int, n_override: int | None = None) -> I.Workload:
 
 
 def config_of(n: int, max_depth=12, leaf_max=32, ng=4, eps=1e-4, extra=None) -> dict:
-    c = {"workload": f"plummer sphere N={n} (a=0.05, r<=0.5), adaptive tree >{leaf_max}/leaf, "
-                     f"depth<={max_depth}, gridlet {ng}^3, eps={eps:g}",
+    desc = (f"uniform cube N={n}, uniform tree depth {max_depth}, gridlet {ng}^3, eps={eps:g}" if leaf_max == 0 else
+            f"plummer sphere N={n} (a=0.05, r<=0.5), adaptive tree >{leaf_max}/leaf, depth<={max_depth}, "
+            f"gridlet {ng}^3, eps={eps:g}")
+    c = {"workload": desc,
          "n": n, "max_depth": max_depth, "leaf_max": leaf_max, "gridlet_order": ng, "eps": eps,
          "stated_force_error": "FP32 solve within 1e-5 rel RMS of the FP64 HPM (parity tests)"}
     if extra:
@@ -176,7 +184,7 @@ def run_gpu(args) -> None:
     from paper_1906_10734_gb300 import build as B
     B.build()
 
-    w = workload_for(rank, args.n)
+    w = workload_for(rank, args.n, args.workload, args.ng)
     stream = torch.cuda.current_stream(dev)
     pos = torch.from_numpy(w.pos).to(dev)
     mass = torch.from_numpy(w.mass).to(dev)
@@ -247,7 +255,8 @@ def run_gpu(args) -> None:
     m2l_ms = statistics.mean(ms_m2l)
     flop = m2l_flops_per_target(w.ng) * info["n_targets"]
     achieved = flop / (m2l_ms / 1e3) / 1e12
-    traffic = profile_traffic(os.path.join(ROOT, "paper_1906_10734_gb300", "csrc", "m2l.cu"))
+    traffic = (profile_traffic(os.path.join(ROOT, "paper_1906_10734_gb300", "csrc", "m2l.cu"))
+               if args.workload == "plummer" and w.ng == 4 else None)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -263,7 +272,8 @@ def run_gpu(args) -> None:
                 "d2h_bytes_per_step": 16 * w.n, "api": "hpm_solve_host (pinned host buffers)"},
         "gpu_launches": int(launches),
         "stages_ms": {k[3:]: v / args.steps for k, v in stage_sum.items()},
-        "roofline": {"kernel": "source-to-target FFT convolution (k_m2l4)", "bound": "alu",
+        "roofline": {"kernel": "source-to-target FFT convolution (k_m2l4)" if w.ng == 4 else
+                               "source-to-target convolution, any-order kernel (k_m2l_generic)", "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": traffic, "ms_per_launch": m2l_ms, "launches_per_step": 1,
                      "flop_per_target": m2l_flops_per_target(w.ng), "targets_per_launch": info["n_targets"],
@@ -457,7 +467,8 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="plummer", choices=["plummer", "batch", "serve"])
+    ap.add_argument("--workload", default="plummer", choices=["plummer", "uniform", "batch", "serve"])
+    ap.add_argument("--ng", type=int, default=4, help="gridlet order of the uniform workload")
     ap.add_argument("--problems", type=int, default=256)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--pool", type=int, default=32)
