@@ -62,7 +62,7 @@ struct TreeDev {
   DevBuf box_key, box_beg, box_end, box_parent, box_flags, box_child, box_nb;
   DevBuf cnt, off, bnd;   // per-box scratch for child counting
   // work lists
-  DevBuf tgt_box, box_tgt, leaf_box, p2g_box, p2g_off;
+  DevBuf tgt_box, box_tgt, leaf_box, p2g_box, p2g_off, par_box;
   // near-field work items: each leaf's concatenated near sources split into
   // items of bounded pair count
   DevBuf item_leaf, item_s0, item_s1, leaf_nitem, leaf_item0, leaf_part0;
@@ -99,6 +99,10 @@ struct hpm_plan_s {
   // mean of the periodic Green function per level, removed from the DC bin of
   // the stored transform and added back to each target's constant
   hpm::DevBuf gmean;
+  // Green function transformed along x only, per level: K[kx][|dy|][|dz|] =
+  // -(1/P) sum_dx (G - mean) cos(2 pi kx dx / P), kx in [0, P/2], |dy|,|dz| < 4 Ng
+  hpm::DevBuf kx_green;
+  int64_t kx_green_stride = 0;      // floats per level
   // tree
   hpm::TreeDev t;
   hpm::SolveDev s;
@@ -110,6 +114,7 @@ struct hpm_plan_s {
   int depth_reached = -1;
   int64_t nbox = 0, ntgt = 0, nleaf = 0, np2g = 0, ncell = 0;
   int64_t nitem = 0, npart = 0;   // near-field work items, partial-sum rows
+  int64_t npar = 0;                // internal cells at levels >= 1 (parents of targets)
   std::vector<int64_t> tgt_lvl_off;  // target offsets per level (levels 2..D)
   std::vector<int64_t> leaf_lvl_off;
   hpm_stats stats{};

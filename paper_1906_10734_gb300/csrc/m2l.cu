@@ -291,6 +291,229 @@ __global__ void __launch_bounds__(kThreads, 2) k_m2l4(const __grid_constant__ Pa
 }  // namespace f4
 
 // ===========================================================================
+// Orders 2, 3, 5, 6: one CTA per parent cell, the parent's whole (6 Ng)^3
+// block of effective masses resident in shared memory. For each kx in
+// [0, P/2] the x-lines of the block are transformed once (a DFT along x shared
+// by the parent's children); each child then takes its near-zone-masked copy
+// of those spectra and convolves them directly over (y, z) with the Green
+// function transformed along x, K[kx][|dy|][|dz|] (exact: every
+// interaction-zone offset is below P/2 in each axis); the target values
+// accumulate over kx in registers. This is the periodic convolution of
+// Sec. 2.1 evaluated with the transform along one axis only, which at these
+// sizes costs about the nominal FFT count and needs no (8 Ng)^3 spectrum on chip.
+// ===========================================================================
+namespace xd {
+constexpr int kThreads = 512;
+
+struct Params {
+  TreeRefs r;
+  Levels lt;
+  const int *par_box;
+  const int *box_tgt;
+  int64_t npar;
+  const float *kxg;
+  int64_t kx_stride;
+};
+
+template <int NG>
+struct Geo {
+  static constexpr int B = 6 * NG, BP = B + 1, P = 8 * NG, H = P / 2 + 1, R = 4 * NG, M3 = NG * NG * NG;
+  static constexpr int N2 = 3 * NG;  // near range of a child along one axis
+  static constexpr size_t kRho = (size_t)B * B * BP, kX = (size_t)B * B, kXn = 2 * (size_t)N2 * N2,
+                          kPart = 2 * (size_t)NG * B * NG;
+  static constexpr size_t kSmem = sizeof(float) * kRho + sizeof(float2) * (kX + kXn + kPart + B) +
+                                  sizeof(float) * 216 + sizeof(int) * (216 + 32);
+};
+
+// Partial sums over zs for one (child, y', ys): acc[z'] = sum_zs Xc(ys, zs) K[dy][|Zt + z' - zs|].
+template <int NG, int TZ>
+__device__ __forceinline__ void conv_row(const float2 *__restrict__ X, const float2 *__restrict__ Xn, int ys,
+                                         bool ynear, int ybase, const float *__restrict__ krow_g,
+                                         float2 *__restrict__ out) {
+  using G = Geo<NG>;
+  float kr[G::R];
+#pragma unroll
+  for (int d = 0; d < G::R; ++d) kr[d] = __ldg(krow_g + d);
+  float2 acc[NG];
+#pragma unroll
+  for (int q = 0; q < NG; ++q) acc[q] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int zs = 0; zs < G::B; ++zs) {
+    constexpr int zlo = NG * (TZ - 1), zhi = NG * (TZ + 2);
+    const bool znear = zs >= zlo && zs < zhi;
+    const float2 xv = (znear && ynear) ? Xn[(ys - ybase) * G::N2 + (zs - zlo)] : X[zs * G::B + ys];
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
+      const int dz = NG * TZ + q - zs;
+      const float k = kr[dz < 0 ? -dz : dz];
+      acc[q].x = fmaf(xv.x, k, acc[q].x);
+      acc[q].y = fmaf(xv.y, k, acc[q].y);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NG; ++q) out[q] = acc[q];
+}
+
+template <int NG>
+__global__ void __launch_bounds__(kThreads, 1) k_m2l_xdft(const __grid_constant__ Params pr) {
+  using G = Geo<NG>;
+  constexpr int B = G::B, BP = G::BP, P = G::P, H = G::H, R = G::R, M3 = G::M3, N2 = G::N2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float *rho = reinterpret_cast<float *>(smem);
+  float2 *X = reinterpret_cast<float2 *>(rho + G::kRho);
+  float2 *Xn = X + G::kX;
+  float2 *part = Xn + G::kXn;
+  float2 *tw = part + G::kPart;
+  float *boxsum = reinterpret_cast<float *>(tw + B);
+  int *blk = reinterpret_cast<int *>(boxsum + 216);
+  int *kid = blk + 216;  // [0..7]: child box, [8..15]: target index, [16]: count
+  const int tid = threadIdx.x;
+  for (int64_t pi = blockIdx.x; pi < pr.npar; pi += gridDim.x) {
+    const int p = pr.par_box[pi];
+    // children (targets) and the unmasked 6^3 block of level-(l) boxes
+    if (tid == 0) {
+      int n = 0;
+      for (int o = 0; o < 8; ++o) {
+        const int c = pr.r.child[(int64_t)p * 8 + o];
+        if (c >= 0) {
+          kid[n] = c;
+          kid[8 + n] = pr.box_tgt[c];
+          ++n;
+        }
+      }
+      kid[16] = n;
+    }
+    for (int j = tid; j < 216; j += blockDim.x) {
+      const int bx = j % 6, by = (j / 6) % 6, bz = j / 36;
+      int row = -1;
+      const int q = pr.r.nb[(int64_t)p * 27 + (bx >> 1) + 3 * (by >> 1) + 9 * (bz >> 1)];
+      if (q >= 0) {
+        const int c = pr.r.child[(int64_t)q * 8 + (bx & 1) + 2 * (by & 1) + 4 * (bz & 1)];
+        if (c >= 0) row = (int)(c - pr.r.off2);
+      }
+      blk[j] = row;
+    }
+    __syncthreads();
+    const int nkid = kid[16];
+    if (nkid == 0) {
+      __syncthreads();
+      continue;
+    }
+    const int lev = level_of(pr.lt, kid[0]);
+    const float *K = pr.kxg + pr.kx_stride * lev;
+    for (int64_t idx = tid; idx < (int64_t)B * B * B; idx += blockDim.x) {
+      const int x = (int)(idx % B), y = (int)((idx / B) % B), z = (int)(idx / (B * B));
+      const int row = blk[x / NG + 6 * (y / NG) + 36 * (z / NG)];
+      rho[((int64_t)z * B + y) * BP + x] =
+          row >= 0 ? __ldg(pr.r.grid + (int64_t)row * M3 + (x % NG) + NG * ((y % NG) + NG * (z % NG))) : 0.f;
+    }
+    for (int j = tid; j < 216; j += blockDim.x) {
+      float s = 0.f;
+      if (blk[j] >= 0)
+        for (int e = 0; e < M3; ++e) s += __ldg(pr.r.grid + (int64_t)blk[j] * M3 + e);
+      boxsum[j] = s;
+    }
+    // owner of Phi(kid, y', z', x' = 0..NG-1) across the kx loop
+    const bool owner = tid < nkid * NG * NG;
+    const int ok = tid / (NG * NG), oy = (tid / NG) % NG, oz = tid % NG;
+    int otx = 0;
+    if (owner) otx = 2 + (int)(pr.r.key[kid[ok]] & 1u);
+    float phi[NG];
+#pragma unroll
+    for (int q = 0; q < NG; ++q) phi[q] = 0.f;
+    for (int kx = 0; kx < H; ++kx) {
+      __syncthreads();  // rho ready / previous kx done with X, Xn, part, tw
+      for (int x = tid; x < B; x += blockDim.x) {
+        float s, c;
+        sincospif(-2.f * (float)((kx * x) % P) / (float)P, &s, &c);
+        tw[x] = make_float2(c, s);
+      }
+      __syncthreads();
+      // DFT along x of every line, shared by the children
+      for (int line = tid; line < B * B; line += blockDim.x) {
+        const int y = line % B, z = line / B;
+        const float *rr = rho + ((int64_t)z * B + y) * BP;
+        float2 s = make_float2(0.f, 0.f);
+#pragma unroll 6
+        for (int x = 0; x < B; ++x) {
+          s.x = fmaf(rr[x], tw[x].x, s.x);
+          s.y = fmaf(rr[x], tw[x].y, s.y);
+        }
+        X[z * B + y] = s;
+      }
+      const float *Kk = K + (int64_t)kx * R * R;
+      const float wk = (kx == 0 || 2 * kx == P) ? 1.f : 2.f;
+      for (int k0 = 0; k0 < nkid; k0 += 2) {
+        const int nk = min(2, nkid - k0);
+        __syncthreads();  // X complete; previous pair done with Xn, part
+        // near-zone masked lines of each child: subtract the masked boxes' part
+        for (int e = tid; e < nk * N2 * N2; e += blockDim.x) {
+          const int s = e / (N2 * N2), yl = (e / N2) % N2, zl = e % N2;
+          const int o = (int)(pr.r.key[kid[k0 + s]] & 7u);
+          const int tx = 2 + (o & 1), ty = 2 + ((o >> 1) & 1), tz = 2 + ((o >> 2) & 1);
+          const int y = yl + NG * (ty - 1), z = zl + NG * (tz - 1);
+          const float *rr = rho + ((int64_t)z * B + y) * BP;
+          float2 c = X[z * B + y];
+          for (int x = NG * (tx - 1); x < NG * (tx + 2); ++x) {
+            c.x = fmaf(-rr[x], tw[x].x, c.x);
+            c.y = fmaf(-rr[x], tw[x].y, c.y);
+          }
+          Xn[s * N2 * N2 + yl * N2 + zl] = c;
+        }
+        __syncthreads();
+        // direct (y, z) convolution: thread (child s, y', ys)
+        if (tid < nk * NG * B) {
+          const int s = tid / (NG * B), yp = (tid / B) % NG, ys = tid % B;
+          const int o = (int)(pr.r.key[kid[k0 + s]] & 7u);
+          const int ty = 2 + ((o >> 1) & 1), tz = 2 + ((o >> 2) & 1);
+          int dy = NG * ty + yp - ys;
+          dy = dy < 0 ? -dy : dy;
+          const int ybase = NG * (ty - 1);
+          const bool ynear = ys >= ybase && ys < ybase + N2;
+          float2 *out = part + ((int64_t)(s * NG + yp) * B + ys) * NG;
+          if (tz == 2) conv_row<NG, 2>(X, Xn + s * N2 * N2, ys, ynear, ybase, Kk + dy * R, out);
+          else conv_row<NG, 3>(X, Xn + s * N2 * N2, ys, ynear, ybase, Kk + dy * R, out);
+        }
+        __syncthreads();
+        // reduce over ys and accumulate the inverse transform along x
+        if (owner && ok >= k0 && ok < k0 + nk) {
+          const int s = ok - k0;
+          float2 Y = make_float2(0.f, 0.f);
+          for (int ys = 0; ys < B; ++ys) {
+            const float2 v = part[((int64_t)(s * NG + oy) * B + ys) * NG + oz];
+            Y.x += v.x;
+            Y.y += v.y;
+          }
+#pragma unroll
+          for (int q = 0; q < NG; ++q) {
+            float sn, cs;
+            sincospif(2.f * (float)((kx * (NG * otx + q)) % P) / (float)P, &sn, &cs);
+            phi[q] = fmaf(wk, Y.x * cs - Y.y * sn, phi[q]);
+          }
+        }
+      }
+    }
+    if (owner) {
+      const int t = kid[8 + ok];
+#pragma unroll
+      for (int q = 0; q < NG; ++q) pr.r.out[(int64_t)t * M3 + q + NG * (oy + NG * oz)] = phi[q];
+      if (oy == 0 && oz == 0) {
+        const int o = (int)(pr.r.key[kid[ok]] & 7u);
+        const int tx = 2 + (o & 1), ty = 2 + ((o >> 1) & 1), tz = 2 + ((o >> 2) & 1);
+        float s = 0.f;
+        for (int j = 0; j < 216; ++j) {
+          const int bx = j % 6, by = (j / 6) % 6, bz = j / 36;
+          if (max(abs(bx - tx), max(abs(by - ty), abs(bz - tz))) >= 2) s += boxsum[j];
+        }
+        pr.r.outc[t] = -pr.r.gmean[lev] * s;
+      }
+    }
+    __syncthreads();
+  }
+}
+}  // namespace xd
+
+// ===========================================================================
 // Generic path, any Ng in 1..8: the same convolution done as separable
 // discrete Fourier sums per line with the same circular placement, one target
 // per block at a time, intermediate spectra in per-block global scratch.
@@ -430,6 +653,18 @@ int sm_count() {
   return n;
 }
 
+template <int NG>
+hpm_status launch_xd(const xd::Params &p, int64_t grid, cudaStream_t st) {
+  constexpr size_t smem = xd::Geo<NG>::kSmem;
+  static bool attr = false;
+  if (!attr) {
+    HPM_CUDA(cudaFuncSetAttribute(xd::k_m2l_xdft<NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  xd::k_m2l_xdft<NG><<<(unsigned)grid, xd::kThreads, smem, st>>>(p);
+  return HPM_OK;
+}
+
 }  // namespace
 
 hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
@@ -466,6 +701,26 @@ hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
     }
     const int64_t grid = std::min<int64_t>(pl->ntgt, (int64_t)2 * nsm);
     f4::k_m2l4<<<(unsigned)grid, f4::kThreads, f4::kSmem, st>>>(p);
+    HPM_LAUNCHED(launches);
+    return HPM_OK;
+  }
+  if (!(pl->opts.flags & HPM_FLAG_GENERIC_M2L) && (pl->ng == 2 || pl->ng == 3 || pl->ng == 5 || pl->ng == 6)) {
+    xd::Params p{};
+    p.r = r;
+    p.lt = lt;
+    p.par_box = pl->t.par_box.as<int>();
+    p.box_tgt = pl->t.box_tgt.as<int>();
+    p.npar = pl->npar;
+    p.kxg = pl->kx_green.as<float>();
+    p.kx_stride = pl->kx_green_stride;
+    const int64_t grid = std::min<int64_t>(pl->npar, (int64_t)nsm);
+    if (grid <= 0) return HPM_OK;
+    switch (pl->ng) {
+      case 2: HPM_TRY(launch_xd<2>(p, grid, st)); break;
+      case 3: HPM_TRY(launch_xd<3>(p, grid, st)); break;
+      case 5: HPM_TRY(launch_xd<5>(p, grid, st)); break;
+      default: HPM_TRY(launch_xd<6>(p, grid, st)); break;
+    }
     HPM_LAUNCHED(launches);
     return HPM_OK;
   }

@@ -520,6 +520,26 @@ __global__ void k_green_pass(int P, int pass, double h, double eps, const double
   out[i] = s;
 }
 
+// Green function transformed along x only (used by the x-transform / direct
+// (y, z) convolution kernel): K[kx][a][b] = -(1/P) sum_{dx=0}^{P-1}
+// (G(|dx|_p, a, b) - mean) cos(2 pi kx dx / P), FP64, stored FP32.
+__global__ void k_green_kx(int P, int R, double h, double eps, const float *__restrict__ mean, int level,
+                           float *__restrict__ out) {
+  const int H = P / 2 + 1;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)H * R * R) return;
+  const int b = (int)(i % R), a = (int)((i / R) % R), kx = (int)(i / ((int64_t)R * R));
+  const double m = (double)mean[level];
+  double s = 0.0;
+  for (int d = 0; d < P; ++d) {
+    const int dr = d <= P / 2 ? d : P - d;
+    double r2 = (double)dr * dr + (double)a * a + (double)b * b;
+    if (r2 == 0.0) r2 = 1.0;
+    s += (1.0 / sqrt(h * h * r2 + eps * eps) - m) * cospi(2.0 * (double)((kx * d) % P) / (double)P);
+  }
+  out[i] = (float)(-s / (double)P);
+}
+
 // Stores -G^/P^3 in FP32 with the DC term removed: G^(0)/P^3 is the mean m of
 // G over the periodic grid, and convolving with G - m instead of G changes every
 // output by the same constant m * sum(rho). That constant is added back to the
@@ -599,6 +619,19 @@ hpm_status precompute_green(hpm_plan_s *pl, cudaStream_t st) {
   }
   HPM_CUDA(cudaFreeAsync(a, st));
   HPM_CUDA(cudaFreeAsync(b, st));
+  // x-transformed tables for the orders the x-transform kernel serves
+  if (pl->ng == 2 || pl->ng == 3 || pl->ng == 5 || pl->ng == 6) {
+    const int R = 4 * pl->ng;
+    pl->kx_green_stride = (int64_t)H * R * R;
+    HPM_TRY(pl->kx_green.ensure(sizeof(float) * pl->kx_green_stride * (D + 1), st));
+    HPM_CUDA(cudaMemsetAsync(pl->kx_green.p, 0, sizeof(float) * pl->kx_green_stride * (D + 1), st));
+    for (int l = 2; l <= D; ++l) {
+      const double h = pl->dom.side / (double)(1u << l) / (double)pl->ng;
+      k_green_kx<<<blocks_for(pl->kx_green_stride), kThreads, 0, st>>>(
+          P, R, h, pl->green.eps, pl->gmean.as<float>(), l, pl->kx_green.as<float>() + pl->kx_green_stride * l);
+      HPM_LAUNCHED((int64_t *)nullptr);
+    }
+  }
   return HPM_OK;
 }
 

@@ -247,7 +247,7 @@ __global__ void k_neighbours(int64_t cb, int64_t ce, int level, const uint8_t *_
 }
 
 // Work-list selection. mode 0: real cells; 1: leaves; 2: boxes that get their
-// effective masses by P2G (not internal).
+// effective masses by P2G (not internal); 3: internal cells.
 __global__ void k_select(int64_t b, int64_t e, const uint8_t *__restrict__ flags, int mode,
                          int *__restrict__ sel) {
   const int64_t i = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -256,7 +256,8 @@ __global__ void k_select(int64_t b, int64_t e, const uint8_t *__restrict__ flags
   int v;
   if (mode == 0) v = (f & kReal) != 0;
   else if (mode == 1) v = (f & kLeaf) != 0;
-  else v = (f & kInternal) == 0;
+  else if (mode == 2) v = (f & kInternal) == 0;
+  else v = (f & kInternal) != 0;
   sel[i - b] = v;
 }
 
@@ -382,6 +383,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   pl->depth_reached = -1;
   pl->nbox = pl->ntgt = pl->nleaf = pl->np2g = pl->ncell = 0;
   pl->nitem = pl->npart = 0;
+  pl->npar = 0;
   pl->tgt_lvl_off.assign(D + 2, 0);
   pl->leaf_lvl_off.assign(D + 2, 0);
   if (n == 0) {
@@ -534,6 +536,9 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   pl->nleaf = cnt;
   HPM_TRY(select_boxes(pl, off2, pl->nbox, 2, t.p2g_box, &cnt, st, &launches));
   pl->np2g = cnt;
+  // parents of the targets: internal cells at levels >= 1
+  HPM_TRY(select_boxes(pl, D >= 1 ? pl->lvl_off[1] : pl->nbox, pl->nbox, 3, t.par_box, &cnt, st, &launches));
+  pl->npar = cnt;
   // particle offsets of the P2G boxes (n + 1 entries, the last one the total)
   HPM_TRY(t.p2g_off.ensure(sizeof(int) * (pl->np2g + 1), st));
   if (pl->np2g) {
