@@ -84,7 +84,10 @@ typedef struct {
 
 enum {
   HPM_FLAG_TIMINGS = 1,        /* record per-stage CUDA-event timings (hpm_get_stats)   */
-  HPM_FLAG_GENERIC_M2L = 2     /* use the any-order convolution kernel for every Ng   */
+  HPM_FLAG_GENERIC_M2L = 2,    /* use the any-order convolution kernel for every Ng   */
+  HPM_FLAG_XTRANSFORM_M2L = 4  /* Ng = 4: evaluate the convolution with the transform
+                                  along x and direct (y, z) sums instead of the
+                                  register FFT (Ng = 2, 3, 5, 6 always do)            */
 };
 
 /*

@@ -303,7 +303,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_m2l4(const __grid_constant__ Pa
 // sizes costs about the nominal FFT count and needs no (8 Ng)^3 spectrum on chip.
 // ===========================================================================
 namespace xd {
-constexpr int kThreads = 512;
+// threads per CTA and CTAs per SM for each order (the block takes 12, 33, 73,
+// 136 and 230 KB of shared memory for Ng = 2, 3, 4, 5, 6)
+template <int NG> struct Launch { static constexpr int threads = 512, min_blocks = 1; };
+template <> struct Launch<2> { static constexpr int threads = 256, min_blocks = 2; };
+template <> struct Launch<3> { static constexpr int threads = 256, min_blocks = 2; };
+template <> struct Launch<4> { static constexpr int threads = 256, min_blocks = 2; };
 
 struct Params {
   TreeRefs r;
@@ -355,7 +360,8 @@ __device__ __forceinline__ void conv_row(const float2 *__restrict__ X, const flo
 }
 
 template <int NG>
-__global__ void __launch_bounds__(kThreads, 1) k_m2l_xdft(const __grid_constant__ Params pr) {
+__global__ void __launch_bounds__(Launch<NG>::threads, Launch<NG>::min_blocks)
+    k_m2l_xdft(const __grid_constant__ Params pr) {
   using G = Geo<NG>;
   constexpr int B = G::B, BP = G::BP, P = G::P, H = G::H, R = G::R, M3 = G::M3, N2 = G::N2;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -661,7 +667,7 @@ hpm_status launch_xd(const xd::Params &p, int64_t grid, cudaStream_t st) {
     HPM_CUDA(cudaFuncSetAttribute(xd::k_m2l_xdft<NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  xd::k_m2l_xdft<NG><<<(unsigned)grid, xd::kThreads, smem, st>>>(p);
+  xd::k_m2l_xdft<NG><<<(unsigned)grid, xd::Launch<NG>::threads, smem, st>>>(p);
   return HPM_OK;
 }
 
@@ -686,7 +692,7 @@ hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   lt.nlev = pl->max_depth + 1;
   for (int l = 0; l <= pl->max_depth + 1; ++l) lt.off[l] = pl->lvl_off[l];
   const int nsm = sm_count();
-  if (pl->ng == 4 && !(pl->opts.flags & HPM_FLAG_GENERIC_M2L)) {
+  if (pl->ng == 4 && !(pl->opts.flags & (HPM_FLAG_GENERIC_M2L | HPM_FLAG_XTRANSFORM_M2L))) {
     f4::Params p{};
     for (int e = 0; e < f4::kP; ++e) {
       const double a = -2.0 * M_PI * e / f4::kP;
@@ -704,7 +710,9 @@ hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
     HPM_LAUNCHED(launches);
     return HPM_OK;
   }
-  if (!(pl->opts.flags & HPM_FLAG_GENERIC_M2L) && (pl->ng == 2 || pl->ng == 3 || pl->ng == 5 || pl->ng == 6)) {
+  const bool xd_order = pl->ng == 2 || pl->ng == 3 || pl->ng == 5 || pl->ng == 6 ||
+                        (pl->ng == 4 && (pl->opts.flags & HPM_FLAG_XTRANSFORM_M2L));
+  if (!(pl->opts.flags & HPM_FLAG_GENERIC_M2L) && xd_order) {
     xd::Params p{};
     p.r = r;
     p.lt = lt;
@@ -713,11 +721,13 @@ hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
     p.npar = pl->npar;
     p.kxg = pl->kx_green.as<float>();
     p.kx_stride = pl->kx_green_stride;
-    const int64_t grid = std::min<int64_t>(pl->npar, (int64_t)nsm);
+    const int per_sm = pl->ng <= 4 ? 2 : 1;
+    const int64_t grid = std::min<int64_t>(pl->npar, (int64_t)nsm * per_sm);
     if (grid <= 0) return HPM_OK;
     switch (pl->ng) {
       case 2: HPM_TRY(launch_xd<2>(p, grid, st)); break;
       case 3: HPM_TRY(launch_xd<3>(p, grid, st)); break;
+      case 4: HPM_TRY(launch_xd<4>(p, grid, st)); break;
       case 5: HPM_TRY(launch_xd<5>(p, grid, st)); break;
       default: HPM_TRY(launch_xd<6>(p, grid, st)); break;
     }

@@ -620,7 +620,7 @@ hpm_status precompute_green(hpm_plan_s *pl, cudaStream_t st) {
   HPM_CUDA(cudaFreeAsync(a, st));
   HPM_CUDA(cudaFreeAsync(b, st));
   // x-transformed tables for the orders the x-transform kernel serves
-  if (pl->ng == 2 || pl->ng == 3 || pl->ng == 5 || pl->ng == 6) {
+  if (pl->ng == 2 || pl->ng == 3 || pl->ng == 4 || pl->ng == 5 || pl->ng == 6) {
     const int R = 4 * pl->ng;
     pl->kx_green_stride = (int64_t)H * R * R;
     HPM_TRY(pl->kx_green.ensure(sizeof(float) * pl->kx_green_stride * (D + 1), st));

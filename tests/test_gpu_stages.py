@@ -79,6 +79,12 @@ def test_stages_generic_kernel_at_order_4(hpm):
     check_stages(hpm, I.uniform_4096_depth3(), flags=hpm.HPM_FLAG_GENERIC_M2L)
 
 
+def test_stages_xtransform_kernel_at_order_4(hpm):
+    check_stages(hpm, I.uniform_4096_depth3(), flags=hpm.HPM_FLAG_XTRANSFORM_M2L)
+    check_stages(hpm, I.small_plummer(12000, 61, leaf_max=16), flags=hpm.HPM_FLAG_XTRANSFORM_M2L,
+                 max_targets=400)
+
+
 @pytest.mark.parametrize("ng", [2, 3, 6])
 def test_stages_other_orders(hpm, ng):
     w = I.Workload(f"u{ng}", I.uniform_cube(2500, 30 + ng), I.equal_masses(2500), max_depth=3, leaf_max=0,
