@@ -103,6 +103,11 @@ struct hpm_plan_s {
   // -(1/P) sum_dx (G - mean) cos(2 pi kx dx / P), kx in [0, P/2], |dy|,|dz| < 4 Ng
   hpm::DevBuf kx_green;
   int64_t kx_green_stride = 0;      // floats per level
+  // Ng = 4: the Green transform inverse-transformed along z only, per level:
+  // K2[kx][|ky|][|dz|] = sum_kz G^(kx, ky, kz) cos(2 pi kz dz / P) (scaled -1/P^3,
+  // DC removed), kx, |ky| in [0, P/2], |dz| < 4 Ng
+  hpm::DevBuf kz_green;
+  int64_t kz_green_stride = 0;
   // tree
   hpm::TreeDev t;
   hpm::SolveDev s;

@@ -80,6 +80,8 @@ struct Params {
   float2 w[kP];  // w[e] = exp(-2 pi i e / 32)
   TreeRefs r;
   Levels lt;
+  const float *kz;   // z-transformed Green tables, kz_stride floats per level
+  int64_t kz_stride;
 };
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -162,9 +164,11 @@ __device__ __forceinline__ void pass_x(const Params &pr, const int *blk, float2 
   }
 }
 
-// y and z passes, Green product, pruned inverse z and y for one kx slab (one warp).
-__device__ __forceinline__ void pass_slab(const Params &pr, int kx, int n0y, int n0z, float2 *slab,
-                                          const float *ghat, const float2 *tw, float *V, float *dc) {
+// y pass, direct z sums with the z-transformed Green table, pruned inverse y,
+// for one kx slab (one warp).
+template <int N0Z>
+__device__ __forceinline__ void pass_slab(const Params &pr, int kx, int n0y, float2 *slab, const float *kz,
+                                          const float2 *tw, float *V, float *dc) {
   const int lane = threadIdx.x & 31;
   float2 a[32];
   // y pass: lane = z
@@ -180,48 +184,31 @@ __device__ __forceinline__ void pass_slab(const Params &pr, int kx, int n0y, int
     for (int r = 0; r < 32; ++r) slab[lane * kYS + r] = a[r];
   }
   __syncwarp();
-  // z pass: lane = ky
-#pragma unroll
-  for (int r = 0; r < 32; ++r) {
-    const int u = (r + n0z) & 31;
-    a[r] = u < kB ? slab[u * kYS + lane] : make_float2(0.f, 0.f);
-  }
-  fft32<-1>(a, pr.w);
-  if (kx == 0 && lane == 0) *dc = 0.5f * a[0].x;  // sum of the block (x pass doubles)
+  // z: the forward transform, the Green product and the inverse pruned to the
+  // target's 4 planes are one linear map from the 24 block planes, evaluated
+  // as direct sums with the Green transform inverse-transformed along z,
+  // W(z') = sum_u Y(u) K2[kx][|ky|][|N0Z + z' - u|] (lane = ky)
+  float2 W0 = make_float2(0.f, 0.f), W1 = W0, W2 = W0, W3 = W0;
   {
     const int kyr = lane <= 16 ? lane : 32 - lane;
-    const float *g = ghat + kx + kH * kyr;
+    const float *krow = kz + (kx * kH + kyr) * 16;
+    float k[16];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      const int kzr = r <= 16 ? r : 32 - r;
-      const float gv = __ldg(g + kH * kH * kzr);
-      a[r].x *= gv;
-      a[r].y *= gv;
-    }
-  }
-  // pruned inverse over kz: W(z') = sum_kz a[kz] e^{+2 pi i kz z'/32}, z' = 0..3,
-  // with kz = 8 al + be: e^{+2 pi i kz z'/32} = i^(al z') e^{+2 pi i be z'/32}
-  float2 W0 = make_float2(0.f, 0.f), W1 = W0, W2 = W0, W3 = W0;
+    for (int d = 0; d < 16; ++d) k[d] = __ldg(krow + d);
+    float dsum = 0.f;
 #pragma unroll
-  for (int be = 0; be < 8; ++be) {
-    const float2 f0 = a[be], f1 = a[8 + be], f2 = a[16 + be], f3 = a[24 + be];
-    const float2 s02 = cadd(f0, f2), d02 = csub(f0, f2), s13 = cadd(f1, f3), d13 = csub(f1, f3);
-    const float2 z0 = cadd(s02, s13), z2 = csub(s02, s13);
-    const float2 z1 = make_float2(d02.x - d13.y, d02.y + d13.x);
-    const float2 z3 = make_float2(d02.x + d13.y, d02.y - d13.x);
-    W0 = cadd(W0, z0);
-    if (be == 0) {
-      W1 = cadd(W1, z1);
-      W2 = cadd(W2, z2);
-      W3 = cadd(W3, z3);
-    } else {
-      const float2 t1 = make_float2(pr.w[be].x, -pr.w[be].y);
-      const float2 t2 = make_float2(pr.w[2 * be].x, -pr.w[2 * be].y);
-      const float2 t3 = make_float2(pr.w[3 * be].x, -pr.w[3 * be].y);
-      W1 = cadd(W1, cmul(z1, t1));
-      W2 = cadd(W2, cmul(z2, t2));
-      W3 = cadd(W3, cmul(z3, t3));
+    for (int u = 0; u < kB; ++u) {
+      const float2 v = slab[u * kYS + lane];
+      dsum += v.x;
+      const int a0 = N0Z - u, a1 = N0Z + 1 - u, a2 = N0Z + 2 - u, a3 = N0Z + 3 - u;  // constant after unrolling
+      const float k0 = k[a0 < 0 ? -a0 : a0], k1 = k[a1 < 0 ? -a1 : a1], k2 = k[a2 < 0 ? -a2 : a2],
+                  k3 = k[a3 < 0 ? -a3 : a3];
+      W0.x = fmaf(v.x, k0, W0.x); W0.y = fmaf(v.y, k0, W0.y);
+      W1.x = fmaf(v.x, k1, W1.x); W1.y = fmaf(v.y, k1, W1.y);
+      W2.x = fmaf(v.x, k2, W2.x); W2.y = fmaf(v.y, k2, W2.y);
+      W3.x = fmaf(v.x, k3, W3.x); W3.y = fmaf(v.y, k3, W3.y);
     }
+    if (kx == 0 && lane == 0) *dc = 0.5f * dsum;  // sum of the block (x pass doubles)
   }
   // inverse over ky for y' = 0..3: products, then a transposed warp reduction
   const float2 Wz[4] = {W0, W1, W2, W3};
@@ -263,14 +250,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_m2l4(const __grid_constant__ Pa
     const int oc = (int)(pr.r.key[box] & 7u);
     const int tx = 2 + (oc & 1), ty = 2 + ((oc >> 1) & 1), tz = 2 + ((oc >> 2) & 1);
     const int lev = level_of(pr.lt, box);
-    const float *ghat = pr.r.ghat + pr.r.ghat_stride * lev;
+    const float *kzt = pr.kz + pr.kz_stride * lev;
     fill_block(pr.r, box, tx, ty, tz, blk);
     __syncthreads();
     if (tx == 2) pass_x<2>(pr, blk, X);
     else pass_x<3>(pr, blk, X);
     __syncthreads();
-    for (int kx = warp; kx < kH; kx += kWarps)
-      pass_slab(pr, kx, 4 * ty, 4 * tz, X + kx * kSlab, ghat, tw, V, dc);
+    for (int kx = warp; kx < kH; kx += kWarps) {
+      if (tz == 2) pass_slab<8>(pr, kx, 4 * ty, X + kx * kSlab, kzt, tw, V, dc);
+      else pass_slab<12>(pr, kx, 4 * ty, X + kx * kSlab, kzt, tw, V, dc);
+    }
     __syncthreads();
     if (threadIdx.x == 64) pr.r.outc[t] = -pr.r.gmean[lev] * *dc;
     if (threadIdx.x < 64) {
@@ -700,6 +689,8 @@ hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
     }
     p.r = r;
     p.lt = lt;
+    p.kz = pl->kz_green.as<float>();
+    p.kz_stride = pl->kz_green_stride;
     static bool attr = false;
     if (!attr) {
       HPM_CUDA(cudaFuncSetAttribute(f4::k_m2l4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f4::kSmem));

@@ -540,6 +540,24 @@ __global__ void k_green_kx(int P, int R, double h, double eps, const float *__re
   out[i] = (float)(-s / (double)P);
 }
 
+// Ng = 4 tables for the direct z sums: K2[kx][kyr][d] = sum_{kz=0}^{P-1}
+// Gs(kx, kyr, |kz|_p) cos(2 pi kz d / P) with Gs = -G^/P^3 and Gs(0, 0, 0) = 0
+// (the DC removal), from the FP64 transform of the reduced table `in`.
+__global__ void k_green_kz(int P, int R, const double *__restrict__ in, float *__restrict__ out) {
+  const int H = P / 2 + 1;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)H * H * R) return;
+  const int d = (int)(i % R), kyr = (int)((i / R) % H), kx = (int)(i / ((int64_t)R * H));
+  const double scale = -1.0 / ((double)P * P * P);
+  double s = 0.0;
+  for (int kz = 0; kz < P; ++kz) {
+    const int kzr = kz <= P / 2 ? kz : P - kz;
+    const double g = (kx == 0 && kyr == 0 && kzr == 0) ? 0.0 : scale * in[kx + (int64_t)H * (kyr + (int64_t)H * kzr)];
+    s += g * cospi(2.0 * (double)((kz * d) % P) / (double)P);
+  }
+  out[i] = (float)s;
+}
+
 // Stores -G^/P^3 in FP32 with the DC term removed: G^(0)/P^3 is the mean m of
 // G over the periodic grid, and convolving with G - m instead of G changes every
 // output by the same constant m * sum(rho). That constant is added back to the
@@ -605,6 +623,11 @@ hpm_status precompute_green(hpm_plan_s *pl, cudaStream_t st) {
   HPM_CUDA(cudaMallocAsync((void **)&a, sizeof(double) * h3, st));
   HPM_CUDA(cudaMallocAsync((void **)&b, sizeof(double) * h3, st));
   const double scale = -1.0 / ((double)P * P * P);
+  if (pl->ng == 4) {
+    pl->kz_green_stride = (int64_t)H * H * (4 * pl->ng);
+    HPM_TRY(pl->kz_green.ensure(sizeof(float) * pl->kz_green_stride * (D + 1), st));
+    HPM_CUDA(cudaMemsetAsync(pl->kz_green.p, 0, sizeof(float) * pl->kz_green_stride * (D + 1), st));
+  }
   for (int l = 2; l <= D; ++l) {
     const double h = pl->dom.side / (double)(1u << l) / (double)pl->ng;
     k_green_pass<<<blocks_for(h3), kThreads, 0, st>>>(P, 0, h, pl->green.eps, nullptr, a);
@@ -616,6 +639,11 @@ hpm_status precompute_green(hpm_plan_s *pl, cudaStream_t st) {
     k_green_store<<<blocks_for(h3), kThreads, 0, st>>>(h3, a, scale, pl->ghat.as<float>() + h3 * l,
                                                        pl->gmean.as<float>() + l, -scale);
     HPM_LAUNCHED((int64_t *)nullptr);
+    if (pl->ng == 4) {
+      k_green_kz<<<blocks_for(pl->kz_green_stride), kThreads, 0, st>>>(
+          P, 4 * pl->ng, a, pl->kz_green.as<float>() + pl->kz_green_stride * l);
+      HPM_LAUNCHED((int64_t *)nullptr);
+    }
   }
   HPM_CUDA(cudaFreeAsync(a, st));
   HPM_CUDA(cudaFreeAsync(b, st));
