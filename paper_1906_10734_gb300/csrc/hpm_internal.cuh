@@ -63,6 +63,10 @@ struct TreeDev {
   DevBuf cnt, off, bnd;   // per-box scratch for child counting
   // work lists
   DevBuf tgt_box, box_tgt, leaf_box, p2g_box, p2g_off, par_box;
+  // interaction zone of every target as its 6^3 parent block: row of each box's
+  // effective masses, -1 where empty, outside the domain or in the near zone;
+  // and (level << 3 | child octant) per target
+  DevBuf tgt_blk, tgt_info;
   // near-field work items: each leaf's concatenated near sources split into
   // items of bounded pair count
   DevBuf item_leaf, item_s0, item_s1, leaf_nitem, leaf_item0, leaf_part0;

@@ -82,6 +82,8 @@ struct Params {
   Levels lt;
   const float *kz;   // z-transformed Green tables, kz_stride floats per level
   int64_t kz_stride;
+  const int *tblk;   // per target: 216 source rows (interaction zone), -1 = none
+  const int *tinfo;  // per target: level << 3 | child octant
 };
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -245,13 +247,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_m2l4(const __grid_constant__ Pa
   float *dc = reinterpret_cast<float *>(tw + 32);
   if (threadIdx.x < 32) tw[threadIdx.x] = make_float2(pr.w[threadIdx.x].x, -pr.w[threadIdx.x].y);
   const int warp = threadIdx.x >> 5;
+  // the next target's interaction-zone rows and (level, octant) are loaded one
+  // target ahead, so no dependent global load stalls the CTA between targets
+  int pre_row = -1, pre_info = 0;
+  if (blockIdx.x < pr.r.ntgt) {
+    if (threadIdx.x < 216) pre_row = __ldg(pr.tblk + (int64_t)blockIdx.x * 216 + threadIdx.x);
+    pre_info = __ldg(pr.tinfo + blockIdx.x);
+  }
   for (int64_t t = blockIdx.x; t < pr.r.ntgt; t += gridDim.x) {
-    const int box = pr.r.tgt_box[t];
-    const int oc = (int)(pr.r.key[box] & 7u);
+    if (threadIdx.x < 216) blk[threadIdx.x] = pre_row;
+    const int info = pre_info;
+    const int oc = info & 7, lev = info >> 3;
     const int tx = 2 + (oc & 1), ty = 2 + ((oc >> 1) & 1), tz = 2 + ((oc >> 2) & 1);
-    const int lev = level_of(pr.lt, box);
     const float *kzt = pr.kz + pr.kz_stride * lev;
-    fill_block(pr.r, box, tx, ty, tz, blk);
+    const int64_t tn = t + gridDim.x;
+    if (tn < pr.r.ntgt) {
+      if (threadIdx.x < 216) pre_row = __ldg(pr.tblk + tn * 216 + threadIdx.x);
+      pre_info = __ldg(pr.tinfo + tn);
+    }
     __syncthreads();
     if (tx == 2) pass_x<2>(pr, blk, X);
     else pass_x<3>(pr, blk, X);
@@ -691,6 +704,8 @@ hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
     p.lt = lt;
     p.kz = pl->kz_green.as<float>();
     p.kz_stride = pl->kz_green_stride;
+    p.tblk = pl->t.tgt_blk.as<int>();
+    p.tinfo = pl->t.tgt_info.as<int>();
     static bool attr = false;
     if (!attr) {
       HPM_CUDA(cudaFuncSetAttribute(f4::k_m2l4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f4::kSmem));

@@ -19,6 +19,11 @@ namespace {
 
 constexpr int kThreads = 256;
 
+struct LevelOffsets {
+  int64_t off[kMaxDepth + 3];
+  int nlev;
+};
+
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 __device__ __forceinline__ uint64_t spread3(uint32_t v) {
@@ -266,6 +271,48 @@ __global__ void k_compact(int64_t b, int64_t e, const int *__restrict__ sel,
   const int64_t i = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= e) return;
   if (sel[i - b]) out[pos[i - b]] = (int)i;
+}
+
+// Interaction zone of each target (cells at level >= 2) as its parent's 6^3
+// block: box j = bx + 6 by + 36 bz is a child of the parent's neighbour
+// (bx/2, by/2, bz/2); it is a source iff nonempty and at Chebyshev distance >= 2
+// from the target (Sec. 1). Stored as effective-mass rows (box - off2) or -1.
+__global__ void k_target_blocks(int64_t ntgt, const int *__restrict__ tgt_box, const int *__restrict__ parent,
+                                const int *__restrict__ nb, const int *__restrict__ child,
+                                const uint64_t *__restrict__ key, int64_t off2, LevelOffsets lo,
+                                int *__restrict__ blk, int *__restrict__ info) {
+  // one thread per (target, parent neighbour): the neighbour's 8 children are the
+  // 2x2x2 boxes (2dx..2dx+1, 2dy.., 2dz..) of the block
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntgt * 27) return;
+  const int64_t t = i / 27;
+  const int k = (int)(i % 27);
+  const int box = tgt_box[t];
+  const int o = (int)(key[box] & 7u);
+  const int tc[3] = {2 + (o & 1), 2 + ((o >> 1) & 1), 2 + ((o >> 2) & 1)};
+  const int dx = k % 3, dy = (k / 3) % 3, dz = k / 9;
+  const int q = nb[(int64_t)parent[box] * 27 + k];
+  int ch[8];
+  if (q >= 0) {
+    const int4 a = *reinterpret_cast<const int4 *>(child + (int64_t)q * 8);
+    const int4 b = *reinterpret_cast<const int4 *>(child + (int64_t)q * 8 + 4);
+    ch[0] = a.x; ch[1] = a.y; ch[2] = a.z; ch[3] = a.w; ch[4] = b.x; ch[5] = b.y; ch[6] = b.z; ch[7] = b.w;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) ch[c] = -1;
+  }
+  int *out = blk + t * 216;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int bx = 2 * dx + (c & 1), by = 2 * dy + ((c >> 1) & 1), bz = 2 * dz + ((c >> 2) & 1);
+    const bool far = max(abs(bx - tc[0]), max(abs(by - tc[1]), abs(bz - tc[2]))) >= 2;
+    out[bx + 6 * by + 36 * bz] = (far && ch[c] >= 0) ? (int)(ch[c] - off2) : -1;
+  }
+  if (k == 0) {
+    int l = 0;
+    while (l + 1 < lo.nlev && lo.off[l + 1] <= box) ++l;
+    info[t] = (l << 3) | o;
+  }
 }
 
 __global__ void k_box_counts(int64_t n, const int *__restrict__ list, const int *__restrict__ beg,
@@ -583,6 +630,15 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   HPM_CUDA(cudaMemsetAsync(t.box_tgt.p, 0xff, sizeof(int) * pl->nbox, st));
   if (pl->ntgt) {
     k_box_tgt<<<blocks_for(pl->ntgt), kThreads, 0, st>>>(pl->ntgt, t.tgt_box.as<int>(), t.box_tgt.as<int>());
+    HPM_LAUNCHED(&launches);
+    HPM_TRY(t.tgt_blk.ensure(sizeof(int) * 216 * pl->ntgt, st));
+    HPM_TRY(t.tgt_info.ensure(sizeof(int) * pl->ntgt, st));
+    LevelOffsets lo{};
+    lo.nlev = D + 1;
+    for (int l = 0; l <= D + 1; ++l) lo.off[l] = pl->lvl_off[l];
+    k_target_blocks<<<blocks_for(27 * pl->ntgt), kThreads, 0, st>>>(
+        pl->ntgt, t.tgt_box.as<int>(), t.box_parent.as<int>(), t.box_nb.as<int>(), t.box_child.as<int>(),
+        t.box_key.as<uint64_t>(), off2, lo, t.tgt_blk.as<int>(), t.tgt_info.as<int>());
     HPM_LAUNCHED(&launches);
   }
   pl->stats.launches = launches;
