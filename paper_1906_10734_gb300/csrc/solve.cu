@@ -336,10 +336,14 @@ __device__ __forceinline__ void pair_add(const float4 &mh, const float4 &ml, con
 
 // Near zone by direct summation (Sec. 1, item 1), one warp per work item: an
 // item is a leaf's targets against a contiguous part of the concatenation of
-// its near boxes' particles. floor(32 / nt) lanes share a target and split its
-// sources; blocks of four pairs are summed in plain FP32 and the block sums are
-// Kahan compensated. A leaf with one item writes far + near to the caller's
-// order; a leaf split over several items writes partial sums for k_p2p_combine.
+// its near boxes' particles. The item's sources are staged in shared memory in
+// chunks (position hi/lo and index), so the pair loop is one flat loop;
+// floor(32 / nt) lanes share a target and split the chunk; blocks of four pairs
+// are summed in plain FP32 and the block sums are Kahan compensated. A leaf with
+// one item writes far + near to the caller's order; a leaf split over several
+// items writes partial sums for k_p2p_combine.
+constexpr int kP2PChunk = 128;
+
 __global__ void __launch_bounds__(kThreads) k_p2p(int64_t nitem, const int *__restrict__ item_leaf,
                                                   const int *__restrict__ item_s0, const int *__restrict__ item_s1,
                                                   const int *__restrict__ leaf_nitem,
@@ -354,6 +358,8 @@ __global__ void __launch_bounds__(kThreads) k_p2p(int64_t nitem, const int *__re
                                                   float4 *__restrict__ part) {
   __shared__ int rb[kWarpsPerBlock][28], cum[kWarpsPerBlock][28];
   __shared__ float4 red[kWarpsPerBlock][32];
+  __shared__ float4 shi[kWarpsPerBlock][kP2PChunk], slo[kWarpsPerBlock][kP2PChunk];
+  __shared__ int sidx[kWarpsPerBlock][kP2PChunk];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t it = (int64_t)blockIdx.x * kWarpsPerBlock + w;
   if (it >= nitem) return;
@@ -390,20 +396,35 @@ __global__ void __launch_bounds__(kThreads) k_p2p(int64_t nitem, const int *__re
     const int slot = lane / G, sub = lane % G;
     const int ti = t0 + slot;
     const bool active = slot < per && ti < te;
-    float sp = 0.f, cp = 0.f, sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
+    float4 mh = make_float4(0.f, 0.f, 0.f, 0.f), ml = mh;
     if (active) {
-      const float4 mh = hi[ti], ml = lo[ti];
-      for (int r = 0; r < 27; ++r) {
-        const int rs = max(cum[w][r], s0), re2 = min(cum[w][r + 1], s1);
-        if (rs >= re2) continue;
-        int q = rs + ((sub - (rs - s0)) % G + G) % G;
-        const int off = rb[w][r] - cum[w][r];  // particle index = q + off
-        for (; q + 3 * G < re2; q += 4 * G) {
+      mh = hi[ti];
+      ml = lo[ti];
+    }
+    float sp = 0.f, cp = 0.f, sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
+    for (int c0 = s0; c0 < s1; c0 += kP2PChunk) {
+      const int cn = min(kP2PChunk, s1 - c0);
+      __syncwarp();
+      for (int k = lane; k < cn; k += 32) {
+        const int q = c0 + k;
+        int r = 0;  // range holding concatenated index q
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1)
+          if (r + step < 28 && cum[w][r + step] <= q) r += step;
+        const int j = rb[w][r] + (q - cum[w][r]);
+        shi[w][k] = hi[j];
+        slo[w][k] = lo[j];
+        sidx[w][k] = j;
+      }
+      __syncwarp();
+      if (active) {
+        int k = sub;
+        for (; k + 3 * G < cn; k += 4 * G) {
           float bp = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const int j = q + u * G + off;
-            pair_add(mh, ml, hi[j], lo[j], j == ti, eps2, bp, bx, by, bz);
+            const int kk = k + u * G;
+            pair_add(mh, ml, shi[w][kk], slo[w][kk], sidx[w][kk] == ti, eps2, bp, bx, by, bz);
           }
           kahan_add(sp, cp, bp);
           kahan_add(sx, cx, bx);
@@ -411,10 +432,7 @@ __global__ void __launch_bounds__(kThreads) k_p2p(int64_t nitem, const int *__re
           kahan_add(sz, cz, bz);
         }
         float bp = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
-        for (; q < re2; q += G) {
-          const int j = q + off;
-          pair_add(mh, ml, hi[j], lo[j], j == ti, eps2, bp, bx, by, bz);
-        }
+        for (; k < cn; k += G) pair_add(mh, ml, shi[w][k], slo[w][k], sidx[w][k] == ti, eps2, bp, bx, by, bz);
         kahan_add(sp, cp, bp);
         kahan_add(sx, cx, bx);
         kahan_add(sy, cy, by);
