@@ -190,7 +190,7 @@ def run_gpu(args) -> None:
     mass = torch.from_numpy(w.mass).to(dev)
     phi = torch.empty(w.n, dtype=torch.float32, device=dev)
     acc = torch.empty((w.n, 3), dtype=torch.float32, device=dev)
-    m2l_flag = hpm.HPM_FLAG_XTRANSFORM_M2L if args.m2l == "xtransform" else 0
+    m2l_flag = {"tensor": 0, "fft": hpm.HPM_FLAG_FFT_M2L, "xtransform": hpm.HPM_FLAG_XTRANSFORM_M2L}[args.m2l]
     plan = hpm.hpm_plan((0.0, 0.0, 0.0), 1.0, w.max_depth, w.ng, w.eps, w.leaf_max, flags=1 | m2l_flag)
     l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
@@ -470,7 +470,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="plummer", choices=["plummer", "uniform", "batch", "serve"])
     ap.add_argument("--ng", type=int, default=4, help="gridlet order of the uniform workload")
-    ap.add_argument("--m2l", default="fft", choices=["fft", "xtransform"],
+    ap.add_argument("--m2l", default="tensor", choices=["tensor", "fft", "xtransform"],
                     help="Ng = 4 source-to-target kernel: register FFT or x-transform + direct (y, z)")
     ap.add_argument("--problems", type=int, default=256)
     ap.add_argument("--rate", type=float, default=200.0)

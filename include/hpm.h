@@ -85,9 +85,16 @@ typedef struct {
 enum {
   HPM_FLAG_TIMINGS = 1,        /* record per-stage CUDA-event timings (hpm_get_stats)   */
   HPM_FLAG_GENERIC_M2L = 2,    /* use the any-order convolution kernel for every Ng   */
-  HPM_FLAG_XTRANSFORM_M2L = 4  /* Ng = 4: evaluate the convolution with the transform
-                                  along x and direct (y, z) sums instead of the
-                                  register FFT (Ng = 2, 3, 5, 6 always do)            */
+  HPM_FLAG_XTRANSFORM_M2L = 4, /* Ng = 4: evaluate the convolution with the transform
+                                  along x and direct (y, z) sums (Ng = 2, 3, 5, 6
+                                  always do)                                          */
+  HPM_FLAG_FFT_M2L = 8         /* Ng = 4: evaluate the convolution by the FFT method of
+                                  Sec. 2.1 (register FFT-32 kernel) instead of the
+                                  default dense tensor-core product, which computes
+                                  the same convolution over each parent's 6^3 block
+                                  with three TF32 products per term (same result up
+                                  to FP32 rounding; needs 57 MB of device tables per
+                                  level 2..max_depth, built by hpm_plan)             */
 };
 
 /*

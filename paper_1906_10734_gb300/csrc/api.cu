@@ -69,7 +69,7 @@ static void make_tables(int ng, GridletTables &tb) {
 static void release_all(hpm_plan_s *pl, cudaStream_t s) {
   DevBuf *bufs[] = {&pl->ghat, &pl->t.keys, &pl->t.keys_alt, &pl->t.perm, &pl->t.perm_alt, &pl->t.spm,
                     &pl->t.box_key, &pl->t.box_beg, &pl->t.box_end, &pl->t.box_parent, &pl->t.box_flags,
-                    &pl->t.box_child, &pl->t.box_nb, &pl->t.cnt, &pl->t.off, &pl->t.bnd, &pl->t.p2g_off, &pl->t.par_box, &pl->t.tgt_blk, &pl->t.tgt_info, &pl->kx_green, &pl->kz_green, &pl->t.tgt_box,
+                    &pl->t.box_child, &pl->t.box_nb, &pl->t.cnt, &pl->t.off, &pl->t.bnd, &pl->t.p2g_off, &pl->t.par_box, &pl->t.tgt_blk, &pl->t.tgt_info, &pl->kx_green, &pl->kz_green, &pl->tc_w, &pl->tc_mean, &pl->t.tc_rows, &pl->t.tc_tgt, &pl->t.tgt_box,
                     &pl->t.box_tgt, &pl->t.leaf_box, &pl->t.p2g_box, &pl->t.item_leaf, &pl->t.item_s0,
                     &pl->t.item_s1, &pl->t.leaf_nitem, &pl->t.leaf_item0, &pl->t.leaf_part0, &pl->s.part, &pl->t.err, &pl->t.counters,
                     &pl->s.grid, &pl->s.m2l_raw, &pl->s.loc, &pl->s.locc, &pl->s.m2lc, &pl->gmean, &pl->s.far, &pl->s.m2l_scratch, &pl->s.work,
@@ -132,6 +132,7 @@ hpm_status hpm_plan(const hpm_domain *dom, int max_depth, int gridlet_order, con
   }
   make_tables(gridlet_order, pl->tab);
   hpm_status s = precompute_green(pl, 0);
+  if (s == HPM_OK) s = tc_precompute(pl, 0);
   if (s == HPM_OK) {
     cudaError_t e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {

@@ -67,6 +67,10 @@ struct TreeDev {
   // effective masses, -1 where empty, outside the domain or in the near zone;
   // and (level << 3 | child octant) per target
   DevBuf tgt_blk, tgt_info;
+  // Ng = 4 tensor-core source-to-target: per tile of 256 parents of one level,
+  // the rows of the 216 boxes of each parent's 6^3 block ([216][256], -1 where
+  // empty) and the targets of its 8 children ([256][8], -1 where absent)
+  DevBuf tc_rows, tc_tgt;
   // near-field work items: each leaf's concatenated near sources split into
   // items of bounded pair count
   DevBuf item_leaf, item_s0, item_s1, leaf_nitem, leaf_item0, leaf_part0;
@@ -112,6 +116,14 @@ struct hpm_plan_s {
   // DC removed), kx, |ky| in [0, P/2], |dz| < 4 Ng
   hpm::DevBuf kz_green;
   int64_t kz_green_stride = 0;
+  // Ng = 4 tensor-core source-to-target: the dense matrices W_l of levels
+  // 2..max_depth as TF32 (hi, lo) tiles in streaming order, and the tiles of
+  // the built tree (first tile of each target level)
+  hpm::DevBuf tc_w;
+  hpm::DevBuf tc_mean;                // per target level and child: mean of row (o, 0)
+  std::vector<double> tc_mean_host;
+  int64_t tc_ntiles = 0;
+  std::vector<int64_t> tc_tile_off;
   // tree
   hpm::TreeDev t;
   hpm::SolveDev s;
@@ -155,6 +167,12 @@ hpm_status batch_scatter(const hpm_problem *d_desc, const int64_t *d_off, int np
                          const float *acc, cudaStream_t st);
 // m2l.cu
 hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches);
+// m2l_tc.cu
+bool use_tc_m2l(const hpm_plan_s *pl);
+hpm_status tc_precompute(hpm_plan_s *pl, cudaStream_t st);
+hpm_status tc_build_tiles(hpm_plan_s *pl, const std::vector<int64_t> &par_per_level, cudaStream_t st,
+                          int64_t *launches);
+hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches);
 }  // namespace hpm
 
 #define HPM_CUDA(call)                                  \

@@ -693,6 +693,7 @@ hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   Levels lt{};
   lt.nlev = pl->max_depth + 1;
   for (int l = 0; l <= pl->max_depth + 1; ++l) lt.off[l] = pl->lvl_off[l];
+  if (use_tc_m2l(pl)) return launch_m2l_tc(pl, st, launches);
   const int nsm = sm_count();
   if (pl->ng == 4 && !(pl->opts.flags & (HPM_FLAG_GENERIC_M2L | HPM_FLAG_XTRANSFORM_M2L))) {
     f4::Params p{};

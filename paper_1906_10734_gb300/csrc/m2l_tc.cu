@@ -1,0 +1,589 @@
+// Source-to-target values for Ng = 4 as a dense product on the tensor cores.
+//
+// The interaction zones of the 8 children of one parent all lie in the 6^3
+// block of the parent's neighbours' children (Sec. 1), and on the level-l grid
+// the convolution of Sec. 2.1 is translation invariant, so the values at the
+// children's 8 x 64 nodes are one fixed matrix W_l (512 x 216*64 per level)
+// times the 216 gridlets of that block:
+//
+//   Phi[(o, i)][P] = sum_{s, j} W_l[(o, i)][(s, j)] rho_{block(P, s)}[j],
+//   W_l[(o, i)][(s, j)] = -g(h_l |y_{o,i} - y_{s,j}|), zero where slot s is in
+//   the near zone of child o.
+//
+// This is the same convolution the FFT path evaluates (exactly, up to
+// rounding), written as a GEMM with the parents as the N dimension. Precision:
+// W and rho are split into TF32 pairs (x = hi + lo) and three products
+// hi*hi + hi*lo + lo*hi are accumulated in FP32 in tensor memory. The tensor
+// core's accumulation drops low bits, so the accumulator is drained every
+// kBlockChunks K-chunks into a round-to-nearest FP32 total (a second region of
+// tensor memory), which keeps the chain short. Rows (o, i >= 1) hold
+// deviations from node 0 of the child, the (constant, deviations) split of the
+// local expansion that the FFT path also produces; row (o, 0) holds its
+// entries minus their mean m_o over the interaction zone, and m_o times the
+// zone's total mass (summed exactly by the gather warps) is added back to the
+// constant, which keeps that row's sum free of a large same-sign running total.
+//
+// One CTA computes 128 rows (2 children) for 256 parents of one level:
+//   warp 0       bulk-copies the W tile of each K-chunk (pre-swizzled in HBM)
+//   warp 1       allocates tensor memory and issues tcgen05.mma
+//   warps 2-9    gather the 256 parents' source gridlets, split into TF32 pairs
+//   warps 10-17  drain the accumulator and write the targets' values
+// Every wait is bounded; a wait that runs out sets kErrTimeout in the error
+// word and the CTA leaves its loops.
+#include <algorithm>
+#include <cmath>
+
+#include "hpm_internal.cuh"
+
+namespace hpm {
+namespace tc {
+
+constexpr int kM3 = 64;                         // nodes per gridlet, Ng = 4
+constexpr int kSlots = 216;                     // 6^3 source block
+constexpr int kKC = 16;                         // K elements per stage (one z plane of a gridlet)
+constexpr int kChunks = kSlots * kM3 / kKC;     // 864 stages per tile
+constexpr int kTileN = 256;                     // parents per tile
+constexpr int kRows = 128;                      // rows per CTA (2 children x 64 nodes)
+constexpr int kQuarters = 4;                    // CTAs per tile
+constexpr int kStages = 4;
+constexpr int kATile = kRows * kKC * 4;         // 8 KB, one of hi / lo
+constexpr int kABytes = 2 * kATile;             // 16 KB per stage, one bulk copy
+constexpr int kBTile = kTileN * kKC * 4;        // 16 KB, one of hi / lo
+constexpr int kStageBytes = kABytes + 2 * kBTile;  // 48 KB
+constexpr int kSmem = kStages * kStageBytes + 1024;
+constexpr int kBlockChunks = 32;                // accumulator drained every 8 slots
+constexpr int kBlocks = kChunks / kBlockChunks;
+constexpr int kWarps = 18, kThreads = kWarps * 32;
+constexpr int kProdWarp0 = 2, kEpiWarp0 = 10;
+constexpr int64_t kLevelFloats = (int64_t)kQuarters * kChunks * kABytes / 4;  // W floats per level
+static_assert(kChunks % kBlockChunks == 0, "drain blocks tile the K loop");
+
+struct Params {
+  const float *w;          // W tables, level l at w + (l - 2) * kLevelFloats
+  const float *grid;       // effective masses, Ng^3 per row
+  const int *rows;         // per tile: [216][256] source row or -1
+  const int *tgt;          // per tile: [256][8] target index or -1
+  int64_t tile_off[kMaxDepth + 2];  // tiles of target level l start at tile_off[l]
+  int nlev;                // target levels 0..nlev-1 (tiles only at l >= 2)
+  float *out;              // per target Ng^3: deviations from node 0 (node 0 holds 0)
+  float *outc;             // per target: the value at node 0
+  int *err;
+  double mean[kMaxDepth + 1][8];  // m_o per target level: mean of row (o, 0) over the zone
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t *b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t *b) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t *b, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(su32(b)),
+               "r"(bytes)
+               : "memory");
+}
+// Bounded wait for the phase of the given parity: about 2^32 cycles at most.
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity) {
+  const long long t0 = clock64();
+  uint32_t done = 0;
+  for (;;) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1ll << 32)) return false;
+  }
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(b))
+               : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// named barrier 1 between the gather and the drain warps
+constexpr int kNamedBarThreads = 16 * 32;
+__device__ __forceinline__ void nbar_arrive() { asm volatile("bar.arrive 1, %0;" ::"n"(kNamedBarThreads) : "memory"); }
+__device__ __forceinline__ void nbar_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kNamedBarThreads) : "memory"); }
+
+// Shared-memory matrix descriptor, K-major operand with 64-byte swizzle: rows
+// of 64 bytes, 8-row groups 512 bytes apart, descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+// Instruction descriptor, kind::tf32: FP32 accumulator, TF32 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
+                            ((uint32_t)(kRows >> 4) << 24);
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, int accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+          d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+               : "memory");
+}
+
+#define HPM_R32(a) \
+  "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), \
+      "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(a[16]),   \
+      "=r"(a[17]), "=r"(a[18]), "=r"(a[19]), "=r"(a[20]), "=r"(a[21]), "=r"(a[22]), "=r"(a[23]), "=r"(a[24]),  \
+      "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), "=r"(a[28]), "=r"(a[29]), "=r"(a[30]), "=r"(a[31])
+#define HPM_W32(a) \
+  "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(a[8]), "r"(a[9]), \
+      "r"(a[10]), "r"(a[11]), "r"(a[12]), "r"(a[13]), "r"(a[14]), "r"(a[15]), "r"(a[16]), "r"(a[17]),           \
+      "r"(a[18]), "r"(a[19]), "r"(a[20]), "r"(a[21]), "r"(a[22]), "r"(a[23]), "r"(a[24]), "r"(a[25]),           \
+      "r"(a[26]), "r"(a[27]), "r"(a[28]), "r"(a[29]), "r"(a[30]), "r"(a[31])
+
+// 32 lanes x 32 consecutive columns of tensor memory (lane = thread of the warp)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : HPM_R32(v)
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+      "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      HPM_W32(v)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Byte offset of 16-byte chunk k (0..3) of row r in a K-major tile of 64-byte
+// rows with 64-byte swizzle (chunk index XOR bits 1-2 of the row).
+__host__ __device__ __forceinline__ int sw64(int r, int k) { return (r >> 3) * 512 + (r & 7) * 64 + ((k ^ ((r >> 1) & 3)) << 4); }
+
+// ---------------------------------------------------------------------------
+// W_l for one level, in the order the kernel streams it: for each quarter q
+// (children 2q, 2q+1) and K-chunk c (slot c / 4, z plane c % 4 of its
+// gridlet), a 16 KB block holding the hi then the lo tile, 128 rows x 16
+// floats, swizzled as the MMA reads them. One thread per (q, c, row).
+__global__ void k_w_table(double h, double eps, const double *__restrict__ mean, float *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)kQuarters * kChunks * kRows) return;
+  const int r = (int)(i % kRows);
+  const int c = (int)((i / kRows) % kChunks);
+  const int q = (int)(i / ((int64_t)kRows * kChunks));
+  const int o = 2 * q + (r >> 6), node = r & 63;
+  const int px = 2 + (o & 1), py = 2 + ((o >> 1) & 1), pz = 2 + (o >> 2);  // child in the 6^3 block
+  const int s = c >> 2, zq = c & 3;
+  const int sx = s % 6, sy = (s / 6) % 6, sz = s / 36;
+  const bool near = max(abs(sx - px), max(abs(sy - py), abs(sz - pz))) <= 1;
+  // target node and node 0 of the child, source node base, in grid units
+  const int tx = 4 * px + (node & 3), ty = 4 * py + ((node >> 2) & 3), tz = 4 * pz + (node >> 4);
+  const int bx = 4 * sx, by = 4 * sy, bz = 4 * sz + zq;
+  float *blk = out + ((int64_t)q * kChunks + c) * (kABytes / 4);
+  char *hi_row = reinterpret_cast<char *>(blk);
+  char *lo_row = reinterpret_cast<char *>(blk + kATile / 4);
+  for (int k = 0; k < 4; ++k) {
+    float hv[4], lv[4];
+    for (int e = 0; e < 4; ++e) {
+      const int jj = 4 * k + e;  // source node (jx, jy) = (jj & 3, jj >> 2) in plane zq
+      double w = 0.0;
+      if (!near) {
+        const double dx = tx - (bx + (jj & 3)), dy = ty - (by + (jj >> 2)), dz = tz - bz;
+        w = -1.0 / sqrt(h * h * (dx * dx + dy * dy + dz * dz) + eps * eps);
+        if (node != 0) {
+          const double ex = 4 * px - (bx + (jj & 3)), ey = 4 * py - (by + (jj >> 2)), ez = 4 * pz - bz;
+          w -= -1.0 / sqrt(h * h * (ex * ex + ey * ey + ez * ez) + eps * eps);
+        } else {
+          w -= mean[o];
+        }
+      }
+      const float w32 = (float)w;
+      const float hi = tf32_rna(w32);
+      hv[e] = hi;
+      lv[e] = tf32_rna((float)(w - (double)hi));
+    }
+    *reinterpret_cast<float4 *>(hi_row + sw64(r, k)) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+    *reinterpret_cast<float4 *>(lo_row + sw64(r, k)) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+  }
+}
+
+// Source rows and target indices of every tile: tiles group the parents of one
+// level (par_box is level-major), 256 per tile, the last one padded with -1.
+struct TileLevels {
+  int64_t tile_off[kMaxDepth + 2];  // by target level
+  int64_t par_off[kMaxDepth + 2];   // parents of target level l: par_box[par_off[l] .. par_off[l + 1])
+  int nlev;
+};
+
+__global__ void k_tiles(int64_t ntiles, TileLevels tl, const int *__restrict__ par_box, const int *__restrict__ nb,
+                        const int *__restrict__ child, const int *__restrict__ box_tgt, int64_t off2,
+                        int *__restrict__ rows, int *__restrict__ tgt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntiles * kTileN) return;
+  const int64_t tile = i / kTileN;
+  const int n = (int)(i % kTileN);
+  int l = 2;
+  while (l + 1 < tl.nlev && tl.tile_off[l + 1] <= tile) ++l;
+  const int64_t pi = tl.par_off[l] + (tile - tl.tile_off[l]) * kTileN + n;
+  int *rr = rows + tile * kSlots * kTileN + n;
+  int *tt = tgt + (tile * kTileN + n) * 8;
+  if (pi >= tl.par_off[l + 1]) {
+    for (int s = 0; s < kSlots; ++s) rr[(int64_t)s * kTileN] = -1;
+    for (int o = 0; o < 8; ++o) tt[o] = -1;
+    return;
+  }
+  const int p = par_box[pi];
+  for (int k = 0; k < 27; ++k) {
+    const int q = nb[(int64_t)p * 27 + k];
+    const int dx = k % 3, dy = (k / 3) % 3, dz = k / 9;
+    for (int c = 0; c < 8; ++c) {
+      const int bx = 2 * dx + (c & 1), by = 2 * dy + ((c >> 1) & 1), bz = 2 * dz + (c >> 2);
+      int row = -1;
+      if (q >= 0) {
+        const int ch = child[(int64_t)q * 8 + c];
+        if (ch >= 0) row = (int)(ch - off2);
+      }
+      rr[(int64_t)(bx + 6 * by + 36 * bz) * kTileN] = row;
+    }
+  }
+  for (int o = 0; o < 8; ++o) {
+    const int ch = child[(int64_t)p * 8 + o];
+    tt[o] = ch >= 0 ? box_tgt[ch] : -1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_plane(const float *__restrict__ grid, int row, int zq, float4 (&v)[4]) {
+  if (row >= 0) {
+    const float4 *p = reinterpret_cast<const float4 *>(grid + (int64_t)row * kM3 + zq * kKC);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __ldg(p + k);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ Params pr) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t full[kStages], empty[kStages], accf, acce;
+  __shared__ uint32_t tmem_base;
+  __shared__ int failed;
+  __shared__ double zone_mass[kTileN][2];  // per parent: total far mass of each of the 2 children
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t tile = blockIdx.x / kQuarters;
+  const int q = (int)(blockIdx.x % kQuarters);
+  int lev = 2;
+  while (lev + 1 < pr.nlev && pr.tile_off[lev + 1] <= tile) ++lev;
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      bar_init(&full[s], 1 + 8);
+      bar_init(&empty[s], 1);
+    }
+    bar_init(&accf, 1);
+    bar_init(&acce, 8);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(&tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tacc = tmem_base, ttot = tmem_base + 256;
+
+  if (warp == 0) {
+    // W tiles: one contiguous 16 KB block per K-chunk
+    if (lane == 0) {
+      const unsigned char *src = reinterpret_cast<const unsigned char *>(
+          pr.w + (int64_t)(lev - 2) * kLevelFloats + (int64_t)q * kChunks * (kABytes / 4));
+      for (int c = 0; c < kChunks; ++c) {
+        const int st = c % kStages;
+        if (!bar_wait(&empty[st], ((c / kStages) & 1) ^ 1)) {
+          failed = 1;
+          break;
+        }
+        bar_expect(&full[st], kABytes);
+        bulk_load(sm + st * kStageBytes, src + (int64_t)c * kABytes, kABytes, &full[st]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int c = 0; c < kChunks; ++c) {
+        const int st = c % kStages;
+        const bool first = (c % kBlockChunks) == 0;
+        if (first && c > 0) {
+          if (!bar_wait(&acce, ((c / kBlockChunks) - 1) & 1)) {
+            failed = 1;
+            break;
+          }
+          tc_fence_after();
+        }
+        if (!bar_wait(&full[st], (c / kStages) & 1)) {
+          failed = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_hi = su32(sm + st * kStageBytes), a_lo = a_hi + kATile;
+        const uint32_t b_hi = a_hi + kABytes, b_lo = b_hi + kBTile;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          const uint64_t ah = sdesc(a_hi + 32 * ks), al = sdesc(a_lo + 32 * ks);
+          const uint64_t bh = sdesc(b_hi + 32 * ks), bl = sdesc(b_lo + 32 * ks);
+          mma(tacc, ah, bh, !(first && ks == 0));
+          mma(tacc, ah, bl, 1);
+          mma(tacc, al, bh, 1);
+        }
+        mma_commit(&empty[st]);
+        if (c % kBlockChunks == kBlockChunks - 1) mma_commit(&accf);
+      }
+    }
+  } else if (warp < kEpiWarp0) {
+    // one parent per thread: its gridlet's z plane of the chunk's slot, split
+    const int n = tid - 32 * kProdWarp0;
+    const int *rp = pr.rows + tile * kSlots * kTileN + n;
+    double zm0 = 0.0, zm1 = 0.0;
+    int row_a = __ldg(rp), row_b = __ldg(rp + kTileN);
+    float4 cur[4];
+    load_plane(pr.grid, row_a, 0, cur);
+    unsigned char *const b0 = sm + kABytes;
+    for (int c = 0; c < kChunks; ++c) {
+      float4 nxt[4];
+      const int c1 = c + 1;
+      if (c1 < kChunks) {
+        if ((c1 & 3) == 0) {
+          row_a = row_b;
+          const int s2 = (c1 >> 2) + 1;
+          row_b = s2 < kSlots ? __ldg(rp + (int64_t)s2 * kTileN) : -1;
+        }
+        load_plane(pr.grid, row_a, c1 & 3, nxt);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) nxt[k] = cur[k];
+      }
+      const int st = c % kStages;
+      if (!__all_sync(0xffffffffu, bar_wait(&empty[st], ((c / kStages) & 1) ^ 1))) {
+        failed = 1;
+        break;
+      }
+      unsigned char *bh = b0 + st * kStageBytes, *bl = bh + kBTile;
+      {
+        // mass of this plane, counted for each child whose zone holds the slot
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) m += (cur[k].x + cur[k].y) + (cur[k].z + cur[k].w);
+        const int sl = c >> 2, sx = sl % 6, sy = (sl / 6) % 6, sz = sl / 36;
+        const int oa = 2 * q;
+        const int py = 2 + ((oa >> 1) & 1), pz = 2 + (oa >> 2);
+        const int cyz = max(abs(sy - py), abs(sz - pz));
+        if (max(abs(sx - 2), cyz) >= 2) zm0 += (double)m;
+        if (max(abs(sx - 3), cyz) >= 2) zm1 += (double)m;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float4 v = cur[k];
+        float4 h, l;
+        h.x = tf32_rna(v.x); l.x = tf32_rna(v.x - h.x);
+        h.y = tf32_rna(v.y); l.y = tf32_rna(v.y - h.y);
+        h.z = tf32_rna(v.z); l.z = tf32_rna(v.z - h.z);
+        h.w = tf32_rna(v.w); l.w = tf32_rna(v.w - h.w);
+        *reinterpret_cast<float4 *>(bh + sw64(n, k)) = h;
+        *reinterpret_cast<float4 *>(bl + sw64(n, k)) = l;
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) bar_arrive(&full[st]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
+    }
+    zone_mass[n][0] = zm0;
+    zone_mass[n][1] = zm1;
+    nbar_arrive();
+  } else {
+    // drain: total += block accumulator; after the last block write the values
+    const int lq = warp & 3, half = (warp - kEpiWarp0) >> 2;
+    const int r = lq * 32 + lane;                 // row of this thread
+    const int o = 2 * q + (r >> 6), node = r & 63;
+    const uint32_t lane_off = (uint32_t)(lq * 32) << 16;
+    for (int b = 0; b < kBlocks; ++b) {
+      if (!__all_sync(0xffffffffu, bar_wait(&accf, b & 1))) {
+        failed = 1;
+        break;
+      }
+      tc_fence_after();
+      const bool last = b == kBlocks - 1;
+      if (last) nbar_sync();
+#pragma unroll 1
+      for (int cc = 0; cc < 4; ++cc) {
+        const int col = half * 128 + cc * 32;
+        uint32_t a[32], t[32];
+        tmem_ld32(tacc + lane_off + col, a);
+        if (b > 0) tmem_ld32(ttot + lane_off + col, t);
+        tmem_wait_ld();
+        if (b > 0) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) a[j] = __float_as_uint(__uint_as_float(a[j]) + __uint_as_float(t[j]));
+        }
+        if (!last) {
+          tmem_st32(ttot + lane_off + col, a);
+        } else {
+          const int *tg = pr.tgt + (tile * kTileN + col) * 8 + o;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int t_idx = __ldg(tg + j * 8);
+            if (t_idx >= 0) {
+              const float v = __uint_as_float(a[j]);
+              if (node == 0) {
+                pr.outc[t_idx] = (float)((double)v + pr.mean[lev][o] * zone_mass[col + j][o & 1]);
+                pr.out[(int64_t)t_idx * kM3] = 0.f;
+              } else {
+                pr.out[(int64_t)t_idx * kM3 + node] = v;
+              }
+            }
+          }
+        }
+      }
+      if (!last) {
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) bar_arrive(&acce);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
+  }
+  if (tid == 0 && failed) atomicOr(pr.err, kErrTimeout);
+}
+
+}  // namespace tc
+
+bool use_tc_m2l(const hpm_plan_s *pl) {
+  return pl->ng == 4 &&
+         !(pl->opts.flags & (HPM_FLAG_GENERIC_M2L | HPM_FLAG_XTRANSFORM_M2L | HPM_FLAG_FFT_M2L));
+}
+
+hpm_status tc_precompute(hpm_plan_s *pl, cudaStream_t st) {
+  if (!use_tc_m2l(pl)) return HPM_OK;
+  const int D = pl->max_depth;
+  if (D < 2) return HPM_OK;
+  HPM_TRY(pl->tc_w.ensure(sizeof(float) * tc::kLevelFloats * (D - 1), st));
+  HPM_TRY(pl->tc_mean.ensure(sizeof(double) * 8 * (D + 1), st));
+  // m_o: mean of -g(h |y_{o,0} - y_{s,j}|) over the zone's 189 slots x 64 nodes
+  std::vector<double> mean(8 * (D + 1), 0.0);
+  for (int l = 2; l <= D; ++l) {
+    const double h = pl->dom.side / (double)(1u << l) / (double)pl->ng, eps = pl->green.eps;
+    for (int o = 0; o < 8; ++o) {
+      const int px = 2 + (o & 1), py = 2 + ((o >> 1) & 1), pz = 2 + (o >> 2);
+      double sum = 0.0;
+      int64_t cnt = 0;
+      for (int s = 0; s < tc::kSlots; ++s) {
+        const int sx = s % 6, sy = (s / 6) % 6, sz = s / 36;
+        if (std::max(std::abs(sx - px), std::max(std::abs(sy - py), std::abs(sz - pz))) <= 1) continue;
+        for (int j = 0; j < tc::kM3; ++j) {
+          const double dx = 4 * px - (4 * sx + (j & 3)), dy = 4 * py - (4 * sy + ((j >> 2) & 3)),
+                       dz = 4 * pz - (4 * sz + (j >> 4));
+          sum += -1.0 / std::sqrt(h * h * (dx * dx + dy * dy + dz * dz) + eps * eps);
+          ++cnt;
+        }
+      }
+      mean[8 * l + o] = sum / (double)cnt;
+    }
+  }
+  pl->tc_mean_host = mean;
+  HPM_CUDA(cudaMemcpyAsync(pl->tc_mean.p, mean.data(), sizeof(double) * mean.size(), cudaMemcpyHostToDevice, st));
+  const int64_t nthr = (int64_t)tc::kQuarters * tc::kChunks * tc::kRows;
+  for (int l = 2; l <= D; ++l) {
+    const double h = pl->dom.side / (double)(1u << l) / (double)pl->ng;
+    tc::k_w_table<<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(
+        h, pl->green.eps, pl->tc_mean.as<double>() + 8 * l, pl->tc_w.as<float>() + tc::kLevelFloats * (l - 2));
+    HPM_LAUNCHED((int64_t *)nullptr);
+  }
+  return HPM_OK;
+}
+
+hpm_status tc_build_tiles(hpm_plan_s *pl, const std::vector<int64_t> &par_per_level, cudaStream_t st,
+                          int64_t *launches) {
+  pl->tc_ntiles = 0;
+  pl->tc_tile_off.assign(kMaxDepth + 2, 0);
+  if (!use_tc_m2l(pl)) return HPM_OK;
+  const int D = pl->max_depth;
+  tc::TileLevels tl{};
+  tl.nlev = D + 1;
+  int64_t tiles = 0, pars = 0;
+  for (int l = 0; l <= D + 1; ++l) {
+    tl.tile_off[l] = tiles;
+    tl.par_off[l] = pars;
+    pl->tc_tile_off[l] = tiles;
+    if (l >= 2 && l <= D) {
+      const int64_t np = par_per_level[l - 1];  // parents of level-l targets sit at level l - 1
+      tiles += (np + tc::kTileN - 1) / tc::kTileN;
+      pars += np;
+    }
+  }
+  if (pars != pl->npar) return HPM_ERR_INVALID_ARG;
+  pl->tc_ntiles = tiles;
+  if (!tiles) return HPM_OK;
+  const int64_t off2 = pl->lvl_off[2];
+  HPM_TRY(pl->t.tc_rows.ensure(sizeof(int) * tiles * tc::kSlots * tc::kTileN, st));
+  HPM_TRY(pl->t.tc_tgt.ensure(sizeof(int) * tiles * tc::kTileN * 8, st));
+  const int64_t nthr = tiles * tc::kTileN;
+  tc::k_tiles<<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(
+      tiles, tl, pl->t.par_box.as<int>(), pl->t.box_nb.as<int>(), pl->t.box_child.as<int>(),
+      pl->t.box_tgt.as<int>(), off2, pl->t.tc_rows.as<int>(), pl->t.tc_tgt.as<int>());
+  HPM_LAUNCHED(launches);
+  return HPM_OK;
+}
+
+hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
+  if (!pl->tc_ntiles) return HPM_OK;
+  tc::Params p{};
+  p.w = pl->tc_w.as<float>();
+  p.grid = pl->s.grid.as<float>();
+  p.rows = pl->t.tc_rows.as<int>();
+  p.tgt = pl->t.tc_tgt.as<int>();
+  for (int l = 0; l <= kMaxDepth + 1; ++l) p.tile_off[l] = l < (int)pl->tc_tile_off.size() ? pl->tc_tile_off[l] : 0;
+  p.nlev = pl->max_depth + 1;
+  p.out = pl->s.m2l_raw.as<float>();
+  p.outc = pl->s.m2lc.as<float>();
+  p.err = pl->t.err.as<int>();
+  for (int l = 0; l <= kMaxDepth && 8 * l + 7 < (int)pl->tc_mean_host.size(); ++l)
+    for (int o = 0; o < 8; ++o) p.mean[l][o] = pl->tc_mean_host[8 * l + o];
+  static bool attr = false;
+  if (!attr) {
+    HPM_CUDA(cudaFuncSetAttribute(tc::k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem));
+    attr = true;
+  }
+  const int64_t grid = pl->tc_ntiles * tc::kQuarters;
+  tc::k_m2l_tc<<<(unsigned)grid, tc::kThreads, tc::kSmem, st>>>(p);
+  HPM_LAUNCHED(launches);
+  return HPM_OK;
+}
+
+}  // namespace hpm

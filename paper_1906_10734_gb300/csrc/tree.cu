@@ -641,6 +641,12 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
         t.box_key.as<uint64_t>(), off2, lo, t.tgt_blk.as<int>(), t.tgt_info.as<int>());
     HPM_LAUNCHED(&launches);
   }
+  {
+    // parents per level (internal cells = cells - leaves) for the tensor-core tiles
+    std::vector<int64_t> par_per_level(D + 2, 0);
+    for (int l = 1; l <= D; ++l) par_per_level[l] = hc[l] - hc[32 + l];
+    HPM_TRY(tc_build_tiles(pl, par_per_level, st, &launches));
+  }
   pl->stats.launches = launches;
   pl->built = true;
   return HPM_OK;

@@ -22,6 +22,7 @@ HPM_GREEN_PLUMMER = 0
 HPM_FLAG_TIMINGS = 1
 HPM_FLAG_GENERIC_M2L = 2
 HPM_FLAG_XTRANSFORM_M2L = 4
+HPM_FLAG_FFT_M2L = 8
 HPM_STAGE_MASSES, HPM_STAGE_M2L, HPM_STAGE_LOCAL = 1, 2, 3
 
 # Every symbol include/hpm.h declares, with its ctypes signature.

@@ -75,6 +75,11 @@ def test_stages_adaptive_plummer(hpm):
     check_stages(hpm, I.small_plummer(12000, 60, leaf_max=16), max_targets=600)
 
 
+def test_stages_fft_kernel_at_order_4(hpm):
+    check_stages(hpm, I.uniform_4096_depth3(), flags=hpm.HPM_FLAG_FFT_M2L)
+    check_stages(hpm, I.small_plummer(12000, 62, leaf_max=16), flags=hpm.HPM_FLAG_FFT_M2L, max_targets=400)
+
+
 def test_stages_generic_kernel_at_order_4(hpm):
     check_stages(hpm, I.uniform_4096_depth3(), flags=hpm.HPM_FLAG_GENERIC_M2L)
 
