@@ -51,7 +51,7 @@ constexpr int kABytes = 2 * kATile;             // 16 KB per stage, one bulk cop
 constexpr int kBTile = kTileN * kKC * 4;        // 16 KB, one of hi / lo
 constexpr int kStageBytes = kABytes + 2 * kBTile;  // 48 KB
 constexpr int kSmem = kStages * kStageBytes + 1024;
-constexpr int kBlockChunks = 32;                // accumulator drained every 8 slots
+constexpr int kBlockChunks = 16;                // accumulator drained every 4 slots
 constexpr int kBlocks = kChunks / kBlockChunks;
 constexpr int kWarps = 18, kThreads = kWarps * 32;
 constexpr int kProdWarp0 = 2, kEpiWarp0 = 10;
@@ -365,23 +365,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     const int n = tid - 32 * kProdWarp0;
     const int *rp = pr.rows + tile * kSlots * kTileN + n;
     double zm0 = 0.0, zm1 = 0.0;
-    int row_a = __ldg(rp), row_b = __ldg(rp + kTileN);
-    float4 cur[4];
-    load_plane(pr.grid, row_a, 0, cur);
+    // planes are loaded two chunks ahead of their conversion
+    int row_l = __ldg(rp), row_n = __ldg(rp + kTileN);
+    float4 cur[4], nx1[4];
+    load_plane(pr.grid, row_l, 0, cur);
+    load_plane(pr.grid, row_l, 1, nx1);
     unsigned char *const b0 = sm + kABytes;
     for (int c = 0; c < kChunks; ++c) {
-      float4 nxt[4];
-      const int c1 = c + 1;
-      if (c1 < kChunks) {
-        if ((c1 & 3) == 0) {
-          row_a = row_b;
-          const int s2 = (c1 >> 2) + 1;
-          row_b = s2 < kSlots ? __ldg(rp + (int64_t)s2 * kTileN) : -1;
+      float4 nx2[4];
+      const int cl = c + 2;
+      if (cl < kChunks) {
+        if ((cl & 3) == 0) {
+          row_l = row_n;
+          const int s2 = (cl >> 2) + 1;
+          row_n = s2 < kSlots ? __ldg(rp + (int64_t)s2 * kTileN) : -1;
         }
-        load_plane(pr.grid, row_a, c1 & 3, nxt);
+        load_plane(pr.grid, row_l, cl & 3, nx2);
       } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) nxt[k] = cur[k];
+        for (int k = 0; k < 4; ++k) nx2[k] = nx1[k];
       }
       const int st = c % kStages;
       if (!__all_sync(0xffffffffu, bar_wait(&empty[st], ((c / kStages) & 1) ^ 1))) {
@@ -416,7 +418,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
       __syncwarp();
       if (lane == 0) bar_arrive(&full[st]);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
+      for (int k = 0; k < 4; ++k) {
+        cur[k] = nx1[k];
+        nx1[k] = nx2[k];
+      }
     }
     zone_mass[n][0] = zm0;
     zone_mass[n][1] = zm1;
