@@ -89,6 +89,8 @@ struct SolveDev {
   DevBuf part;       // near-field partial sums of leaves split over several items
   DevBuf m2l_scratch;
   DevBuf work;       // int work counters
+  DevBuf box_amax;   // Ng = 4 tensor-core path: largest |effective mass| per row
+  DevBuf col_exp;    // and the scale exponent of each tile column (parent)
 };
 
 }  // namespace hpm
@@ -120,6 +122,7 @@ struct hpm_plan_s {
   // 2..max_depth as TF32 (hi, lo) tiles in streaming order, and the tiles of
   // the built tree (first tile of each target level)
   hpm::DevBuf tc_w;
+  hpm::DevBuf tc_wexp;                // per level and row: power-of-two scale exponent
   hpm::DevBuf tc_mean;                // per target level and child: mean of row (o, 0)
   std::vector<double> tc_mean_host;
   int64_t tc_ntiles = 0;

@@ -12,8 +12,12 @@
 //
 // This is the same convolution the FFT path evaluates (exactly, up to
 // rounding), written as a GEMM with the parents as the N dimension. Precision:
-// W and rho are split into TF32 pairs (x = hi + lo) and three products
-// hi*hi + hi*lo + lo*hi are accumulated in FP32 in tensor memory. The tensor
+// each row of W and each parent's column of rho is scaled by a power of two
+// (exact) so that its largest entry lies in [2^13, 2^14), then split into FP16
+// pairs (x = hi + lo, 22 significant bits; entries far below the row's or
+// column's largest keep an absolute error under 2^-24 of the scaled unit), and
+// three products hi*hi + hi*lo + lo*hi are accumulated in FP32 in tensor
+// memory; the scales are removed when the values are written. The tensor
 // core's accumulation drops low bits, so the accumulator is drained every
 // kBlockChunks K-chunks into a round-to-nearest FP32 total (a second region of
 // tensor memory), which keeps the chain short. Rows (o, i >= 1) hold
@@ -26,10 +30,12 @@
 // One CTA computes 128 rows (2 children) for 256 parents of one level:
 //   warp 0       bulk-copies the W tile of each K-chunk (pre-swizzled in HBM)
 //   warp 1       allocates tensor memory and issues tcgen05.mma
-//   warps 2-9    gather the 256 parents' source gridlets, split into TF32 pairs
+//   warps 2-9    gather the 256 parents' source gridlets, scale and split them
 //   warps 10-17  drain the accumulator and write the targets' values
 // Every wait is bounded; a wait that runs out sets kErrTimeout in the error
 // word and the CTA leaves its loops.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -45,21 +51,24 @@ constexpr int kChunks = kSlots * kM3 / kKC;     // 864 stages per tile
 constexpr int kTileN = 256;                     // parents per tile
 constexpr int kRows = 128;                      // rows per CTA (2 children x 64 nodes)
 constexpr int kQuarters = 4;                    // CTAs per tile
-constexpr int kStages = 4;
-constexpr int kATile = kRows * kKC * 4;         // 8 KB, one of hi / lo
-constexpr int kABytes = 2 * kATile;             // 16 KB per stage, one bulk copy
-constexpr int kBTile = kTileN * kKC * 4;        // 16 KB, one of hi / lo
-constexpr int kStageBytes = kABytes + 2 * kBTile;  // 48 KB
+constexpr int kStages = 8;
+constexpr int kRowBytes = 2 * kKC * 2;          // one tile row: 16 hi then 16 lo FP16 values
+constexpr int kABytes = kRows * kRowBytes;      // 8 KB per stage, one bulk copy
+constexpr int kBBytes = kTileN * kRowBytes;     // 16 KB per stage
+constexpr int kStageBytes = kABytes + kBBytes;  // 24 KB
 constexpr int kSmem = kStages * kStageBytes + 1024;
+constexpr int kScaleTop = 14;                   // scaled maxima lie in [2^13, 2^14)
 constexpr int kBlockChunks = 16;                // accumulator drained every 4 slots
 constexpr int kBlocks = kChunks / kBlockChunks;
 constexpr int kWarps = 18, kThreads = kWarps * 32;
 constexpr int kProdWarp0 = 2, kEpiWarp0 = 10;
-constexpr int64_t kLevelFloats = (int64_t)kQuarters * kChunks * kABytes / 4;  // W floats per level
+constexpr int64_t kLevelBytes = (int64_t)kQuarters * kChunks * kABytes;  // W bytes per level
 static_assert(kChunks % kBlockChunks == 0, "drain blocks tile the K loop");
 
 struct Params {
-  const float *w;          // W tables, level l at w + (l - 2) * kLevelFloats
+  const unsigned char *w;  // W tables, level l at w + (l - 2) * kLevelBytes
+  const int *w_exp;        // per level (from 2) and row: the row's scale exponent
+  const int *col_exp;      // per tile and parent: the column's scale exponent
   const float *grid;       // effective masses, Ng^3 per row
   const int *rows;         // per tile: [216][256] source row or -1
   const int *tgt;          // per tile: [256][8] target index or -1
@@ -120,14 +129,13 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
-// Instruction descriptor, kind::tf32: FP32 accumulator, TF32 A and B, both
-// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
-                            ((uint32_t)(kRows >> 4) << 24);
+// Instruction descriptor, kind::f16: FP32 accumulator, FP16 A and B (format
+// 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
 
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, int accumulate) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
           d),
       "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
       : "memory");
@@ -167,10 +175,17 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+// exact power of two for |e| < 127
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+// exponent that brings a largest magnitude m > 0 into [2^13, 2^14)
+__device__ __forceinline__ int scale_exp(float m) {
+  if (!(m > 0.f)) return 0;
+  int e;
+  frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+  return min(max(kScaleTop - e, -120), 120);
+}
+__device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
 
 // Byte offset of 16-byte chunk k (0..3) of row r in a K-major tile of 64-byte
@@ -178,50 +193,64 @@ __device__ __forceinline__ float tf32_rna(float x) {
 __host__ __device__ __forceinline__ int sw64(int r, int k) { return (r >> 3) * 512 + (r & 7) * 64 + ((k ^ ((r >> 1) & 3)) << 4); }
 
 // ---------------------------------------------------------------------------
-// W_l for one level, in the order the kernel streams it: for each quarter q
-// (children 2q, 2q+1) and K-chunk c (slot c / 4, z plane c % 4 of its
-// gridlet), a 16 KB block holding the hi then the lo tile, 128 rows x 16
-// floats, swizzled as the MMA reads them. One thread per (q, c, row).
-__global__ void k_w_table(double h, double eps, const double *__restrict__ mean, float *__restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)kQuarters * kChunks * kRows) return;
-  const int r = (int)(i % kRows);
-  const int c = (int)((i / kRows) % kChunks);
-  const int q = (int)(i / ((int64_t)kRows * kChunks));
+// Entry (row r of quarter q, K-chunk c, source node jj of the chunk's plane)
+// of W_l: -g(h |d|) for the child's node, minus the same for node 0 (rows of
+// nodes >= 1) or minus the row mean m_o (node 0); zero in the near zone.
+__device__ __forceinline__ double w_entry(int q, int r, int c, int jj, double h, double eps,
+                                          const double *__restrict__ mean) {
   const int o = 2 * q + (r >> 6), node = r & 63;
   const int px = 2 + (o & 1), py = 2 + ((o >> 1) & 1), pz = 2 + (o >> 2);  // child in the 6^3 block
   const int s = c >> 2, zq = c & 3;
   const int sx = s % 6, sy = (s / 6) % 6, sz = s / 36;
-  const bool near = max(abs(sx - px), max(abs(sy - py), abs(sz - pz))) <= 1;
-  // target node and node 0 of the child, source node base, in grid units
-  const int tx = 4 * px + (node & 3), ty = 4 * py + ((node >> 2) & 3), tz = 4 * pz + (node >> 4);
-  const int bx = 4 * sx, by = 4 * sy, bz = 4 * sz + zq;
-  float *blk = out + ((int64_t)q * kChunks + c) * (kABytes / 4);
-  char *hi_row = reinterpret_cast<char *>(blk);
-  char *lo_row = reinterpret_cast<char *>(blk + kATile / 4);
-  for (int k = 0; k < 4; ++k) {
-    float hv[4], lv[4];
-    for (int e = 0; e < 4; ++e) {
-      const int jj = 4 * k + e;  // source node (jx, jy) = (jj & 3, jj >> 2) in plane zq
-      double w = 0.0;
-      if (!near) {
-        const double dx = tx - (bx + (jj & 3)), dy = ty - (by + (jj >> 2)), dz = tz - bz;
-        w = -1.0 / sqrt(h * h * (dx * dx + dy * dy + dz * dz) + eps * eps);
-        if (node != 0) {
-          const double ex = 4 * px - (bx + (jj & 3)), ey = 4 * py - (by + (jj >> 2)), ez = 4 * pz - bz;
-          w -= -1.0 / sqrt(h * h * (ex * ex + ey * ey + ez * ez) + eps * eps);
-        } else {
-          w -= mean[o];
-        }
-      }
-      const float w32 = (float)w;
-      const float hi = tf32_rna(w32);
-      hv[e] = hi;
-      lv[e] = tf32_rna((float)(w - (double)hi));
-    }
-    *reinterpret_cast<float4 *>(hi_row + sw64(r, k)) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-    *reinterpret_cast<float4 *>(lo_row + sw64(r, k)) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+  if (max(abs(sx - px), max(abs(sy - py), abs(sz - pz))) <= 1) return 0.0;
+  const int bx = 4 * sx + (jj & 3), by = 4 * sy + (jj >> 2), bz = 4 * sz + zq;  // source node, grid units
+  const double dx = 4 * px + (node & 3) - bx, dy = 4 * py + ((node >> 2) & 3) - by, dz = 4 * pz + (node >> 4) - bz;
+  double w = -1.0 / sqrt(h * h * (dx * dx + dy * dy + dz * dz) + eps * eps);
+  if (node != 0) {
+    const double ex = 4 * px - bx, ey = 4 * py - by, ez = 4 * pz - bz;
+    w -= -1.0 / sqrt(h * h * (ex * ex + ey * ey + ez * ez) + eps * eps);
+  } else {
+    w -= mean[o];
   }
+  return w;
+}
+
+// Largest |entry| of each of the 512 rows (as float bits, nonnegative floats
+// order like their bits). One thread per (q, c, row).
+__global__ void k_w_rowmax(double h, double eps, const double *__restrict__ mean, int *__restrict__ rowmax) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)kQuarters * kChunks * kRows) return;
+  const int r = (int)(i % kRows), c = (int)((i / kRows) % kChunks), q = (int)(i / ((int64_t)kRows * kChunks));
+  double m = 0.0;
+  for (int jj = 0; jj < kKC; ++jj) m = fmax(m, fabs(w_entry(q, r, c, jj, h, eps, mean)));
+  atomicMax(rowmax + q * kRows + r, __float_as_int((float)m));
+}
+
+// W_l in the order the kernel streams it: for each quarter q (children 2q,
+// 2q+1) and K-chunk c (slot c / 4, z plane c % 4 of its gridlet) an 8 KB tile
+// of 128 rows x (16 hi, 16 lo) FP16 values of the row-scaled entries, swizzled
+// as the MMA reads it. One thread per (q, c, row); the c = 0 threads also
+// store the row exponents.
+__global__ void k_w_table(double h, double eps, const double *__restrict__ mean, const int *__restrict__ rowmax,
+                          unsigned char *__restrict__ out, int *__restrict__ w_exp) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)kQuarters * kChunks * kRows) return;
+  const int r = (int)(i % kRows), c = (int)((i / kRows) % kChunks), q = (int)(i / ((int64_t)kRows * kChunks));
+  const int e = scale_exp(__int_as_float(rowmax[q * kRows + r]));
+  if (c == 0) w_exp[q * kRows + r] = e;
+  const double sc = ldexp(1.0, e);
+  uint32_t hw[8], lw[8];
+  for (int jj = 0; jj < kKC; jj += 2) {
+    const double a = w_entry(q, r, c, jj, h, eps, mean) * sc, b = w_entry(q, r, c, jj + 1, h, eps, mean) * sc;
+    const __half ah = __double2half(a), bh = __double2half(b);
+    hw[jj / 2] = pack_h2(ah, bh);
+    lw[jj / 2] = pack_h2(__double2half(a - (double)__half2float(ah)), __double2half(b - (double)__half2float(bh)));
+  }
+  unsigned char *tile = out + ((int64_t)q * kChunks + c) * kABytes;
+  *reinterpret_cast<uint4 *>(tile + sw64(r, 0)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  *reinterpret_cast<uint4 *>(tile + sw64(r, 1)) = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+  *reinterpret_cast<uint4 *>(tile + sw64(r, 2)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  *reinterpret_cast<uint4 *>(tile + sw64(r, 3)) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
 }
 
 // Source rows and target indices of every tile: tiles group the parents of one
@@ -267,6 +296,35 @@ __global__ void k_tiles(int64_t ntiles, TileLevels tl, const int *__restrict__ p
     const int ch = child[(int64_t)p * 8 + o];
     tt[o] = ch >= 0 ? box_tgt[ch] : -1;
   }
+}
+
+// Largest |effective mass| of every row, then of every parent's block (the
+// column scale exponent of each tile column).
+__global__ void k_box_amax(int64_t nrow, const float *__restrict__ grid, float *__restrict__ amax) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrow) return;
+  const float4 *g = reinterpret_cast<const float4 *>(grid + i * kM3);
+  float m = 0.f;
+#pragma unroll
+  for (int k = 0; k < kM3 / 4; ++k) {
+    const float4 v = g[k];
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+  amax[i] = m;
+}
+
+__global__ void k_col_exp(int64_t ntiles, const int *__restrict__ rows, const float *__restrict__ amax,
+                          int *__restrict__ col_exp) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntiles * kTileN) return;
+  const int *rr = rows + (i / kTileN) * kSlots * kTileN + (i % kTileN);
+  float m = 0.f;
+#pragma unroll 8
+  for (int s = 0; s < kSlots; ++s) {
+    const int row = rr[(int64_t)s * kTileN];
+    if (row >= 0) m = fmaxf(m, amax[row]);
+  }
+  col_exp[i] = scale_exp(m);
 }
 
 // ---------------------------------------------------------------------------
@@ -317,8 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
   if (warp == 0) {
     // W tiles: one contiguous 16 KB block per K-chunk
     if (lane == 0) {
-      const unsigned char *src = reinterpret_cast<const unsigned char *>(
-          pr.w + (int64_t)(lev - 2) * kLevelFloats + (int64_t)q * kChunks * (kABytes / 4));
+      const unsigned char *src = pr.w + (int64_t)(lev - 2) * kLevelBytes + (int64_t)q * kChunks * kABytes;
       for (int c = 0; c < kChunks; ++c) {
         const int st = c % kStages;
         if (!bar_wait(&empty[st], ((c / kStages) & 1) ^ 1)) {
@@ -346,16 +403,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
           break;
         }
         tc_fence_after();
-        const uint32_t a_hi = su32(sm + st * kStageBytes), a_lo = a_hi + kATile;
-        const uint32_t b_hi = a_hi + kABytes, b_lo = b_hi + kBTile;
-#pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-          const uint64_t ah = sdesc(a_hi + 32 * ks), al = sdesc(a_lo + 32 * ks);
-          const uint64_t bh = sdesc(b_hi + 32 * ks), bl = sdesc(b_lo + 32 * ks);
-          mma(tacc, ah, bh, !(first && ks == 0));
-          mma(tacc, ah, bl, 1);
-          mma(tacc, al, bh, 1);
-        }
+        // rows hold 16 hi then 16 lo values: hi*hi, hi*lo, lo*hi
+        const uint32_t a = su32(sm + st * kStageBytes), b = a + kABytes;
+        const uint64_t ah = sdesc(a), al = sdesc(a + 32), bh = sdesc(b), bl = sdesc(b + 32);
+        mma(tacc, ah, bh, !first);
+        mma(tacc, ah, bl, 1);
+        mma(tacc, al, bh, 1);
         mma_commit(&empty[st]);
         if (c % kBlockChunks == kBlockChunks - 1) mma_commit(&accf);
       }
@@ -364,6 +417,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     // one parent per thread: its gridlet's z plane of the chunk's slot, split
     const int n = tid - 32 * kProdWarp0;
     const int *rp = pr.rows + tile * kSlots * kTileN + n;
+    const float csc = pow2f(__ldg(pr.col_exp + tile * kTileN + n));
     double zm0 = 0.0, zm1 = 0.0;
     // planes are loaded two chunks ahead of their conversion
     int row_l = __ldg(rp), row_n = __ldg(rp + kTileN);
@@ -390,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
         failed = 1;
         break;
       }
-      unsigned char *bh = b0 + st * kStageBytes, *bl = bh + kBTile;
+      unsigned char *brow = b0 + st * kStageBytes;
       {
         // mass of this plane, counted for each child whose zone holds the slot
         float m = 0.f;
@@ -403,17 +457,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
         if (max(abs(sx - 2), cyz) >= 2) zm0 += (double)m;
         if (max(abs(sx - 3), cyz) >= 2) zm1 += (double)m;
       }
+      uint32_t hw[8], lw[8];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const float4 v = cur[k];
-        float4 h, l;
-        h.x = tf32_rna(v.x); l.x = tf32_rna(v.x - h.x);
-        h.y = tf32_rna(v.y); l.y = tf32_rna(v.y - h.y);
-        h.z = tf32_rna(v.z); l.z = tf32_rna(v.z - h.z);
-        h.w = tf32_rna(v.w); l.w = tf32_rna(v.w - h.w);
-        *reinterpret_cast<float4 *>(bh + sw64(n, k)) = h;
-        *reinterpret_cast<float4 *>(bl + sw64(n, k)) = l;
+        const float v[4] = {cur[k].x * csc, cur[k].y * csc, cur[k].z * csc, cur[k].w * csc};
+#pragma unroll
+        for (int e = 0; e < 4; e += 2) {
+          const __half ah = __float2half_rn(v[e]), bh = __float2half_rn(v[e + 1]);
+          hw[2 * k + e / 2] = pack_h2(ah, bh);
+          lw[2 * k + e / 2] = pack_h2(__float2half_rn(v[e] - __half2float(ah)), __float2half_rn(v[e + 1] - __half2float(bh)));
+        }
       }
+      *reinterpret_cast<uint4 *>(brow + sw64(n, 0)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4 *>(brow + sw64(n, 1)) = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+      *reinterpret_cast<uint4 *>(brow + sw64(n, 2)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      *reinterpret_cast<uint4 *>(brow + sw64(n, 3)) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
       fence_async_smem();
       __syncwarp();
       if (lane == 0) bar_arrive(&full[st]);
@@ -432,6 +490,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     const int r = lq * 32 + lane;                 // row of this thread
     const int o = 2 * q + (r >> 6), node = r & 63;
     const uint32_t lane_off = (uint32_t)(lq * 32) << 16;
+    const int e_row = __ldg(pr.w_exp + (lev - 2) * (kQuarters * kRows) + q * kRows + r);
     for (int b = 0; b < kBlocks; ++b) {
       if (!__all_sync(0xffffffffu, bar_wait(&accf, b & 1))) {
         failed = 1;
@@ -455,11 +514,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
           tmem_st32(ttot + lane_off + col, a);
         } else {
           const int *tg = pr.tgt + (tile * kTileN + col) * 8 + o;
+          const int *ce = pr.col_exp + tile * kTileN + col;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int t_idx = __ldg(tg + j * 8);
             if (t_idx >= 0) {
-              const float v = __uint_as_float(a[j]);
+              const float v = (__uint_as_float(a[j]) * pow2f(-e_row)) * pow2f(-__ldg(ce + j));
               if (node == 0) {
                 pr.outc[t_idx] = (float)((double)v + pr.mean[lev][o] * zone_mass[col + j][o & 1]);
                 pr.out[(int64_t)t_idx * kM3] = 0.f;
@@ -498,7 +558,9 @@ hpm_status tc_precompute(hpm_plan_s *pl, cudaStream_t st) {
   if (!use_tc_m2l(pl)) return HPM_OK;
   const int D = pl->max_depth;
   if (D < 2) return HPM_OK;
-  HPM_TRY(pl->tc_w.ensure(sizeof(float) * tc::kLevelFloats * (D - 1), st));
+  HPM_TRY(pl->tc_w.ensure((size_t)tc::kLevelBytes * (D - 1), st));
+  HPM_TRY(pl->tc_wexp.ensure(sizeof(int) * tc::kQuarters * tc::kRows * (D - 1), st));
+  HPM_CUDA(cudaMemsetAsync(pl->tc_wexp.p, 0, sizeof(int) * tc::kQuarters * tc::kRows * (D - 1), st));
   HPM_TRY(pl->tc_mean.ensure(sizeof(double) * 8 * (D + 1), st));
   // m_o: mean of -g(h |y_{o,0} - y_{s,j}|) over the zone's 189 slots x 64 nodes
   std::vector<double> mean(8 * (D + 1), 0.0);
@@ -524,12 +586,21 @@ hpm_status tc_precompute(hpm_plan_s *pl, cudaStream_t st) {
   pl->tc_mean_host = mean;
   HPM_CUDA(cudaMemcpyAsync(pl->tc_mean.p, mean.data(), sizeof(double) * mean.size(), cudaMemcpyHostToDevice, st));
   const int64_t nthr = (int64_t)tc::kQuarters * tc::kChunks * tc::kRows;
+  const unsigned nblk = (unsigned)((nthr + 255) / 256);
+  int *rowmax = nullptr;
+  HPM_CUDA(cudaMallocAsync((void **)&rowmax, sizeof(int) * tc::kQuarters * tc::kRows, st));
   for (int l = 2; l <= D; ++l) {
     const double h = pl->dom.side / (double)(1u << l) / (double)pl->ng;
-    tc::k_w_table<<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(
-        h, pl->green.eps, pl->tc_mean.as<double>() + 8 * l, pl->tc_w.as<float>() + tc::kLevelFloats * (l - 2));
+    const double *mean_l = pl->tc_mean.as<double>() + 8 * l;
+    int *wexp = pl->tc_wexp.as<int>() + tc::kQuarters * tc::kRows * (l - 2);
+    HPM_CUDA(cudaMemsetAsync(rowmax, 0, sizeof(int) * tc::kQuarters * tc::kRows, st));
+    tc::k_w_rowmax<<<nblk, 256, 0, st>>>(h, pl->green.eps, mean_l, rowmax);
+    HPM_LAUNCHED((int64_t *)nullptr);
+    tc::k_w_table<<<nblk, 256, 0, st>>>(h, pl->green.eps, mean_l, rowmax,
+                                        pl->tc_w.as<unsigned char>() + tc::kLevelBytes * (l - 2), wexp);
     HPM_LAUNCHED((int64_t *)nullptr);
   }
+  HPM_CUDA(cudaFreeAsync(rowmax, st));
   return HPM_OK;
 }
 
@@ -568,8 +639,20 @@ hpm_status tc_build_tiles(hpm_plan_s *pl, const std::vector<int64_t> &par_per_le
 
 hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   if (!pl->tc_ntiles) return HPM_OK;
+  const int64_t off2 = pl->lvl_off[2], nrow = pl->nbox - off2;
+  if (nrow <= 0) return HPM_OK;
+  HPM_TRY(pl->s.box_amax.ensure(sizeof(float) * nrow, st));
+  HPM_TRY(pl->s.col_exp.ensure(sizeof(int) * pl->tc_ntiles * tc::kTileN, st));
+  tc::k_box_amax<<<(unsigned)((nrow + 255) / 256), 256, 0, st>>>(nrow, pl->s.grid.as<float>(),
+                                                                  pl->s.box_amax.as<float>());
+  HPM_LAUNCHED(launches);
+  tc::k_col_exp<<<(unsigned)((pl->tc_ntiles * tc::kTileN + 255) / 256), 256, 0, st>>>(
+      pl->tc_ntiles, pl->t.tc_rows.as<int>(), pl->s.box_amax.as<float>(), pl->s.col_exp.as<int>());
+  HPM_LAUNCHED(launches);
   tc::Params p{};
-  p.w = pl->tc_w.as<float>();
+  p.w = pl->tc_w.as<unsigned char>();
+  p.w_exp = pl->tc_wexp.as<int>();
+  p.col_exp = pl->s.col_exp.as<int>();
   p.grid = pl->s.grid.as<float>();
   p.rows = pl->t.tc_rows.as<int>();
   p.tgt = pl->t.tc_tgt.as<int>();
