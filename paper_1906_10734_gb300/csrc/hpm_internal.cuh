@@ -89,8 +89,10 @@ struct SolveDev {
   DevBuf part;       // near-field partial sums of leaves split over several items
   DevBuf m2l_scratch;
   DevBuf work;       // int work counters
-  DevBuf box_amax;   // Ng = 4 tensor-core path: largest |effective mass| per row
-  DevBuf col_exp;    // and the scale exponent of each tile column (parent)
+  // Ng = 4 tensor-core path: effective masses as FP16 (hi, lo) planes at a
+  // per-row scale, row scale exponents and total masses, the scale exponent of
+  // each tile column (parent) and the zone mass of each of its 8 children
+  DevBuf grid_hl, box_exp, box_mass, col_exp, zone_mass;
 };
 
 }  // namespace hpm

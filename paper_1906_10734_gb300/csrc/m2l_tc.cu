@@ -30,7 +30,10 @@
 // One CTA computes 128 rows (2 children) for 256 parents of one level:
 //   warp 0       bulk-copies the W tile of each K-chunk (pre-swizzled in HBM)
 //   warp 1       allocates tensor memory and issues tcgen05.mma
-//   warps 2-9    gather the 256 parents' source gridlets, scale and split them
+//   warps 2-9    gather the 256 parents' source gridlets (FP16 pairs at a
+//                per-box scale, split once per solve by k_split) with cp.async
+//                kGatherAhead chunks ahead, then rescale them in place to the
+//                parent's column scale
 //   warps 10-17  drain the accumulator and write the targets' values
 // Every wait is bounded; a wait that runs out sets kErrTimeout in the error
 // word and the CTA leaves its loops.
@@ -58,6 +61,9 @@ constexpr int kBBytes = kTileN * kRowBytes;     // 16 KB per stage
 constexpr int kStageBytes = kABytes + kBBytes;  // 24 KB
 constexpr int kSmem = kStages * kStageBytes + 1024;
 constexpr int kScaleTop = 14;                   // scaled maxima lie in [2^13, 2^14)
+constexpr int kNoExp = 1 << 20;                 // exponent of a row without mass
+constexpr int kGatherAhead = 4;                 // chunks the gather copies run ahead (one slot)
+static_assert(kGatherAhead == 4 && kGatherAhead < kStages, "the gather cursor runs one slot ahead");
 constexpr int kBlockChunks = 16;                // accumulator drained every 4 slots
 constexpr int kBlocks = kChunks / kBlockChunks;
 constexpr int kWarps = 18, kThreads = kWarps * 32;
@@ -69,7 +75,9 @@ struct Params {
   const unsigned char *w;  // W tables, level l at w + (l - 2) * kLevelBytes
   const int *w_exp;        // per level (from 2) and row: the row's scale exponent
   const int *col_exp;      // per tile and parent: the column's scale exponent
-  const float *grid;       // effective masses, Ng^3 per row
+  const unsigned char *hl; // per row and z plane: 16 hi then 16 lo FP16 values at the row's scale
+  const int *box_exp;      // per row: its scale exponent (kNoExp where it holds no mass)
+  const float *zone_mass;  // per tile, parent and child: total mass of the child's zone
   const int *rows;         // per tile: [216][256] source row or -1
   const int *tgt;          // per tile: [256][8] target index or -1
   int64_t tile_off[kMaxDepth + 2];  // tiles of target level l start at tile_off[l]
@@ -116,12 +124,14 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                : "memory");
 }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 16-byte global -> shared copy; src_bytes = 0 fills zeros
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// named barrier 1 between the gather and the drain warps
-constexpr int kNamedBarThreads = 16 * 32;
-__device__ __forceinline__ void nbar_arrive() { asm volatile("bar.arrive 1, %0;" ::"n"(kNamedBarThreads) : "memory"); }
-__device__ __forceinline__ void nbar_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kNamedBarThreads) : "memory"); }
 
 // Shared-memory matrix descriptor, K-major operand with 64-byte swizzle: rows
 // of 64 bytes, 8-row groups 512 bytes apart, descriptor version 1.
@@ -298,54 +308,108 @@ __global__ void k_tiles(int64_t ntiles, TileLevels tl, const int *__restrict__ p
   }
 }
 
-// Largest |effective mass| of every row, then of every parent's block (the
-// column scale exponent of each tile column).
-__global__ void k_box_amax(int64_t nrow, const float *__restrict__ grid, float *__restrict__ amax) {
+// Effective masses of every row as FP16 pairs at the row's own power-of-two
+// scale (largest |value| in [2^13, 2^14)), in the order the gather copies
+// them: per z plane 16 hi then 16 lo values (64 bytes). Also the row's scale
+// exponent and total mass. One warp per 8 rows: 4 lanes per row, each lane
+// one 16-value plane.
+__global__ void k_split(int64_t nrow, const float *__restrict__ grid, unsigned char *__restrict__ hl,
+                        int *__restrict__ box_exp, float *__restrict__ box_mass) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nrow) return;
-  const float4 *g = reinterpret_cast<const float4 *>(grid + i * kM3);
-  float m = 0.f;
+  const int64_t row = i >> 2;
+  const int zq = (int)(i & 3);
+  const bool live = row < nrow;
+  float v[kKC];
+  float m = 0.f, sum = 0.f;
+  if (live) {
+    const float4 *g = reinterpret_cast<const float4 *>(grid + row * kM3 + zq * kKC);
 #pragma unroll
-  for (int k = 0; k < kM3 / 4; ++k) {
-    const float4 v = g[k];
-    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    for (int k = 0; k < 4; ++k) {
+      const float4 a = g[k];
+      v[4 * k] = a.x; v[4 * k + 1] = a.y; v[4 * k + 2] = a.z; v[4 * k + 3] = a.w;
+    }
+#pragma unroll
+    for (int k = 0; k < kKC; ++k) {
+      m = fmaxf(m, fabsf(v[k]));
+      sum += v[k];
+    }
   }
-  amax[i] = m;
+  // the row's four planes are four consecutive lanes
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+  sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+  sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+  if (!live) return;
+  const int e = m > 0.f ? scale_exp(m) : kNoExp;
+  const float sc = m > 0.f ? pow2f(e) : 0.f;
+  uint32_t hw[8], lw[8];
+#pragma unroll
+  for (int k = 0; k < kKC; k += 2) {
+    const float a = v[k] * sc, b = v[k + 1] * sc;
+    const __half ah = __float2half_rn(a), bh = __float2half_rn(b);
+    hw[k / 2] = pack_h2(ah, bh);
+    lw[k / 2] = pack_h2(__float2half_rn(a - __half2float(ah)), __float2half_rn(b - __half2float(bh)));
+  }
+  uint4 *dst = reinterpret_cast<uint4 *>(hl + (row * 4 + zq) * kRowBytes);
+  dst[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  dst[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+  dst[2] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  dst[3] = make_uint4(lw[4], lw[5], lw[6], lw[7]);
+  if (zq == 0) {
+    box_exp[row] = e;
+    box_mass[row] = sum;
+  }
 }
 
-__global__ void k_col_exp(int64_t ntiles, const int *__restrict__ rows, const float *__restrict__ amax,
-                          int *__restrict__ col_exp) {
+// Per tile column (parent): the column scale exponent (the smallest row
+// exponent of its block, i.e. the scale of its largest |value|) and the total
+// mass of each child's interaction zone, summed in FP64.
+__global__ void k_col_exp(int64_t ntiles, const int *__restrict__ rows, const int *__restrict__ box_exp,
+                          const float *__restrict__ box_mass, int *__restrict__ col_exp,
+                          float *__restrict__ zone_mass) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ntiles * kTileN) return;
   const int *rr = rows + (i / kTileN) * kSlots * kTileN + (i % kTileN);
-  float m = 0.f;
-#pragma unroll 8
+  int e = kNoExp;
+  double zm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int s = 0; s < kSlots; ++s) {
     const int row = rr[(int64_t)s * kTileN];
-    if (row >= 0) m = fmaxf(m, amax[row]);
+    if (row < 0) continue;
+    e = min(e, box_exp[row]);
+    const double bm = (double)box_mass[row];
+    const int sx = s % 6, sy = (s / 6) % 6, sz = s / 36;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int px = 2 + (o & 1), py = 2 + ((o >> 1) & 1), pz = 2 + (o >> 2);
+      if (max(abs(sx - px), max(abs(sy - py), abs(sz - pz))) >= 2) zm[o] += bm;
+    }
   }
-  col_exp[i] = scale_exp(m);
+  col_exp[i] = e == kNoExp ? 0 : e;
+#pragma unroll
+  for (int o = 0; o < 8; ++o) zone_mass[i * 8 + o] = (float)zm[o];
+}
+
+// packed FP16 x2 product, round to nearest
+__device__ __forceinline__ uint32_t hmul2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+
+// FP16 bits of 2^k (k <= 0), zero below the smallest subnormal
+__device__ __forceinline__ uint32_t half_pow2_bits(int k) {
+  if (k >= -14) return (uint32_t)(15 + k) << 10;
+  if (k >= -24) return 1u << (k + 24);
+  return 0u;
 }
 
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void load_plane(const float *__restrict__ grid, int row, int zq, float4 (&v)[4]) {
-  if (row >= 0) {
-    const float4 *p = reinterpret_cast<const float4 *>(grid + (int64_t)row * kM3 + zq * kKC);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = __ldg(p + k);
-  } else {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
-
 __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ Params pr) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t full[kStages], empty[kStages], accf, acce;
   __shared__ uint32_t tmem_base;
   __shared__ int failed;
-  __shared__ double zone_mass[kTileN][2];  // per parent: total far mass of each of the 2 children
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t tile = blockIdx.x / kQuarters;
   const int q = (int)(blockIdx.x % kQuarters);
@@ -414,76 +478,83 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
       }
     }
   } else if (warp < kEpiWarp0) {
-    // one parent per thread: its gridlet's z plane of the chunk's slot, split
-    const int n = tid - 32 * kProdWarp0;
-    const int *rp = pr.rows + tile * kSlots * kTileN + n;
-    const float csc = pow2f(__ldg(pr.col_exp + tile * kTileN + n));
-    double zm0 = 0.0, zm1 = 0.0;
-    // planes are loaded two chunks ahead of their conversion
-    int row_l = __ldg(rp), row_n = __ldg(rp + kTileN);
-    float4 cur[4], nx1[4];
-    load_plane(pr.grid, row_l, 0, cur);
-    load_plane(pr.grid, row_l, 1, nx1);
+    // 4 lanes per parent (one 16-byte piece of its 64-byte plane row each), 8
+    // parents per warp instruction, parents pw*32 + 8m + grp for m = 0..3.
+    // Chunk c + 4 is copied while chunk c is rescaled: the copy cursor runs
+    // exactly one slot ahead of the rescale cursor.
+    const int pw = warp - kProdWarp0, sub = lane & 3, grp = lane >> 2;
+    const int nbase = pw * 32 + grp;
+    const int *rp = pr.rows + tile * kSlots * kTileN + nbase;
     unsigned char *const b0 = sm + kABytes;
+    const uint32_t bsh = su32(b0);
+    uint32_t soff[4];
+    int ecol[4], r_iss[4], r_pre[4], e_iss[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      soff[m] = (uint32_t)sw64(nbase + 8 * m, sub);
+      ecol[m] = __ldg(pr.col_exp + tile * kTileN + nbase + 8 * m);
+      r_iss[m] = __ldg(rp + 8 * m);          // slot 0
+      r_pre[m] = __ldg(rp + kTileN + 8 * m);  // slot 1
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) e_iss[m] = r_iss[m] >= 0 ? __ldg(pr.box_exp + r_iss[m]) : kNoExp;
+    auto issue = [&](int ci) {
+      const int st = ci % kStages;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int row = r_iss[m];
+        const unsigned char *src = pr.hl + ((int64_t)(row >= 0 ? row : 0) * 4 + (ci & 3)) * kRowBytes + 16 * sub;
+        cp16(bsh + st * kStageBytes + soff[m], src, row >= 0 ? 16u : 0u);
+      }
+    };
+    bool ok = true;
+    // copies of slot 0 (stages 0..3 start free)
+    for (int ci = 0; ci < kGatherAhead; ++ci) {
+      issue(ci);
+      cp_commit();
+    }
+    uint32_t scale[4];
     for (int c = 0; c < kChunks; ++c) {
-      float4 nx2[4];
-      const int cl = c + 2;
-      if (cl < kChunks) {
-        if ((cl & 3) == 0) {
-          row_l = row_n;
-          const int s2 = (cl >> 2) + 1;
-          row_n = s2 < kSlots ? __ldg(rp + (int64_t)s2 * kTileN) : -1;
-        }
-        load_plane(pr.grid, row_l, cl & 3, nx2);
-      } else {
+      if ((c & 3) == 0) {
+        // entering slot c / 4: its scale; the copy cursor moves to slot c / 4 + 1
+        const int s2 = (c >> 2) + 2;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) nx2[k] = nx1[k];
+        for (int m = 0; m < 4; ++m) {
+          scale[m] = half_pow2_bits(ecol[m] - e_iss[m]);
+          scale[m] |= scale[m] << 16;
+          r_iss[m] = r_pre[m];
+          r_pre[m] = s2 < kSlots ? __ldg(rp + (int64_t)s2 * kTileN + 8 * m) : -1;
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) e_iss[m] = r_iss[m] >= 0 ? __ldg(pr.box_exp + r_iss[m]) : kNoExp;
       }
+      const int ci = c + kGatherAhead;
+      if (ci < kChunks) {
+        if (!__all_sync(0xffffffffu, bar_wait(&empty[ci % kStages], ((ci / kStages) & 1) ^ 1))) {
+          ok = false;
+          break;
+        }
+        issue(ci);
+      }
+      cp_commit();
+      cp_wait<kGatherAhead>();  // chunk c has landed
       const int st = c % kStages;
-      if (!__all_sync(0xffffffffu, bar_wait(&empty[st], ((c / kStages) & 1) ^ 1))) {
-        failed = 1;
-        break;
-      }
-      unsigned char *brow = b0 + st * kStageBytes;
-      {
-        // mass of this plane, counted for each child whose zone holds the slot
-        float m = 0.f;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) m += (cur[k].x + cur[k].y) + (cur[k].z + cur[k].w);
-        const int sl = c >> 2, sx = sl % 6, sy = (sl / 6) % 6, sz = sl / 36;
-        const int oa = 2 * q;
-        const int py = 2 + ((oa >> 1) & 1), pz = 2 + (oa >> 2);
-        const int cyz = max(abs(sy - py), abs(sz - pz));
-        if (max(abs(sx - 2), cyz) >= 2) zm0 += (double)m;
-        if (max(abs(sx - 3), cyz) >= 2) zm1 += (double)m;
+      for (int m = 0; m < 4; ++m) {
+        uint4 *p = reinterpret_cast<uint4 *>(b0 + st * kStageBytes + soff[m]);
+        uint4 v = *p;
+        v.x = hmul2(v.x, scale[m]);
+        v.y = hmul2(v.y, scale[m]);
+        v.z = hmul2(v.z, scale[m]);
+        v.w = hmul2(v.w, scale[m]);
+        *p = v;
       }
-      uint32_t hw[8], lw[8];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float v[4] = {cur[k].x * csc, cur[k].y * csc, cur[k].z * csc, cur[k].w * csc};
-#pragma unroll
-        for (int e = 0; e < 4; e += 2) {
-          const __half ah = __float2half_rn(v[e]), bh = __float2half_rn(v[e + 1]);
-          hw[2 * k + e / 2] = pack_h2(ah, bh);
-          lw[2 * k + e / 2] = pack_h2(__float2half_rn(v[e] - __half2float(ah)), __float2half_rn(v[e + 1] - __half2float(bh)));
-        }
-      }
-      *reinterpret_cast<uint4 *>(brow + sw64(n, 0)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-      *reinterpret_cast<uint4 *>(brow + sw64(n, 1)) = make_uint4(hw[4], hw[5], hw[6], hw[7]);
-      *reinterpret_cast<uint4 *>(brow + sw64(n, 2)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-      *reinterpret_cast<uint4 *>(brow + sw64(n, 3)) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
       fence_async_smem();
       __syncwarp();
       if (lane == 0) bar_arrive(&full[st]);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        cur[k] = nx1[k];
-        nx1[k] = nx2[k];
-      }
     }
-    zone_mass[n][0] = zm0;
-    zone_mass[n][1] = zm1;
-    nbar_arrive();
+    cp_wait<0>();
+    if (!ok) failed = 1;
   } else {
     // drain: total += block accumulator; after the last block write the values
     const int lq = warp & 3, half = (warp - kEpiWarp0) >> 2;
@@ -498,7 +569,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
       }
       tc_fence_after();
       const bool last = b == kBlocks - 1;
-      if (last) nbar_sync();
 #pragma unroll 1
       for (int cc = 0; cc < 4; ++cc) {
         const int col = half * 128 + cc * 32;
@@ -521,7 +591,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
             if (t_idx >= 0) {
               const float v = (__uint_as_float(a[j]) * pow2f(-e_row)) * pow2f(-__ldg(ce + j));
               if (node == 0) {
-                pr.outc[t_idx] = (float)((double)v + pr.mean[lev][o] * zone_mass[col + j][o & 1]);
+                pr.outc[t_idx] = (float)((double)v + pr.mean[lev][o] * (double)__ldg(pr.zone_mass + (tile * kTileN + col + j) * 8 + o));
                 pr.out[(int64_t)t_idx * kM3] = 0.f;
               } else {
                 pr.out[(int64_t)t_idx * kM3 + node] = v;
@@ -641,19 +711,26 @@ hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   if (!pl->tc_ntiles) return HPM_OK;
   const int64_t off2 = pl->lvl_off[2], nrow = pl->nbox - off2;
   if (nrow <= 0) return HPM_OK;
-  HPM_TRY(pl->s.box_amax.ensure(sizeof(float) * nrow, st));
+  HPM_TRY(pl->s.grid_hl.ensure((size_t)nrow * 4 * tc::kRowBytes, st));
+  HPM_TRY(pl->s.box_exp.ensure(sizeof(int) * nrow, st));
+  HPM_TRY(pl->s.box_mass.ensure(sizeof(float) * nrow, st));
   HPM_TRY(pl->s.col_exp.ensure(sizeof(int) * pl->tc_ntiles * tc::kTileN, st));
-  tc::k_box_amax<<<(unsigned)((nrow + 255) / 256), 256, 0, st>>>(nrow, pl->s.grid.as<float>(),
-                                                                  pl->s.box_amax.as<float>());
+  HPM_TRY(pl->s.zone_mass.ensure(sizeof(float) * pl->tc_ntiles * tc::kTileN * 8, st));
+  tc::k_split<<<(unsigned)((4 * nrow + 255) / 256), 256, 0, st>>>(
+      nrow, pl->s.grid.as<float>(), pl->s.grid_hl.as<unsigned char>(), pl->s.box_exp.as<int>(),
+      pl->s.box_mass.as<float>());
   HPM_LAUNCHED(launches);
   tc::k_col_exp<<<(unsigned)((pl->tc_ntiles * tc::kTileN + 255) / 256), 256, 0, st>>>(
-      pl->tc_ntiles, pl->t.tc_rows.as<int>(), pl->s.box_amax.as<float>(), pl->s.col_exp.as<int>());
+      pl->tc_ntiles, pl->t.tc_rows.as<int>(), pl->s.box_exp.as<int>(), pl->s.box_mass.as<float>(),
+      pl->s.col_exp.as<int>(), pl->s.zone_mass.as<float>());
   HPM_LAUNCHED(launches);
   tc::Params p{};
   p.w = pl->tc_w.as<unsigned char>();
   p.w_exp = pl->tc_wexp.as<int>();
   p.col_exp = pl->s.col_exp.as<int>();
-  p.grid = pl->s.grid.as<float>();
+  p.hl = pl->s.grid_hl.as<unsigned char>();
+  p.box_exp = pl->s.box_exp.as<int>();
+  p.zone_mass = pl->s.zone_mass.as<float>();
   p.rows = pl->t.tc_rows.as<int>();
   p.tgt = pl->t.tc_tgt.as<int>();
   for (int l = 0; l <= kMaxDepth + 1; ++l) p.tile_off[l] = l < (int)pl->tc_tile_off.size() ? pl->tc_tile_off[l] : 0;
