@@ -93,6 +93,7 @@ struct SolveDev {
   // per-row scale, row scale exponents and total masses, the scale exponent of
   // each tile column (parent) and the zone mass of each of its 8 children
   DevBuf grid_hl, box_exp, box_mass, col_exp, zone_mass;
+  DevBuf level_amax;  // per (problem, level): largest |effective mass| (float bits)
 };
 
 }  // namespace hpm

@@ -17,7 +17,10 @@
 // pairs (x = hi + lo, 22 significant bits; entries far below the row's or
 // column's largest keep an absolute error under 2^-24 of the scaled unit), and
 // three products hi*hi + hi*lo + lo*hi are accumulated in FP32 in tensor
-// memory; the scales are removed when the values are written. The tensor
+// memory; the scales are removed when the values are written. The column
+// scale is shared by all boxes of one level of one problem: a box whose
+// largest |mass| is 2^-k of the level's largest keeps 22 bits for k <= 17 and
+// loses bits gradually beyond (its contribution shrinks in proportion). The tensor
 // core's accumulation drops low bits, so the accumulator is drained every
 // kBlockChunks K-chunks into a round-to-nearest FP32 total (a second region of
 // tensor memory), which keeps the chain short. Rows (o, i >= 1) hold
@@ -30,11 +33,11 @@
 // One CTA computes 128 rows (2 children) for 256 parents of one level:
 //   warp 0       bulk-copies the W tile of each K-chunk (pre-swizzled in HBM)
 //   warp 1       allocates tensor memory and issues tcgen05.mma
-//   warps 2-9    gather the 256 parents' source gridlets (FP16 pairs at a
-//                per-box scale, split once per solve by k_split) with cp.async
-//                kGatherAhead chunks ahead, then rescale them in place to the
-//                parent's column scale
-//   warps 10-17  drain the accumulator and write the targets' values
+//   warps 2-5    gather the 256 parents' source gridlets with cp.async
+//                (FP16 pairs split once per solve by k_split, at one
+//                power-of-two scale per problem and level, so a parent's
+//                column needs no rescaling)
+//   warps 6-13   drain the accumulator and write the targets' values
 // Every wait is bounded; a wait that runs out sets kErrTimeout in the error
 // word and the CTA leaves its loops.
 #include <cuda_fp16.h>
@@ -62,12 +65,12 @@ constexpr int kStageBytes = kABytes + kBBytes;  // 24 KB
 constexpr int kSmem = kStages * kStageBytes + 1024;
 constexpr int kScaleTop = 14;                   // scaled maxima lie in [2^13, 2^14)
 constexpr int kNoExp = 1 << 20;                 // exponent of a row without mass
-constexpr int kGatherAhead = 4;                 // chunks the gather copies run ahead (one slot)
-static_assert(kGatherAhead == 4 && kGatherAhead < kStages, "the gather cursor runs one slot ahead");
+
 constexpr int kBlockChunks = 16;                // accumulator drained every 4 slots
 constexpr int kBlocks = kChunks / kBlockChunks;
-constexpr int kWarps = 18, kThreads = kWarps * 32;
-constexpr int kProdWarp0 = 2, kEpiWarp0 = 10;
+constexpr int kWarps = 14, kThreads = kWarps * 32;
+constexpr int kProdWarp0 = 2, kEpiWarp0 = 6;
+constexpr int kGatherThreads = (kEpiWarp0 - kProdWarp0) * 32;
 constexpr int64_t kLevelBytes = (int64_t)kQuarters * kChunks * kABytes;  // W bytes per level
 static_assert(kChunks % kBlockChunks == 0, "drain blocks tile the K loop");
 
@@ -75,8 +78,7 @@ struct Params {
   const unsigned char *w;  // W tables, level l at w + (l - 2) * kLevelBytes
   const int *w_exp;        // per level (from 2) and row: the row's scale exponent
   const int *col_exp;      // per tile and parent: the column's scale exponent
-  const unsigned char *hl; // per row and z plane: 16 hi then 16 lo FP16 values at the row's scale
-  const int *box_exp;      // per row: its scale exponent (kNoExp where it holds no mass)
+  const unsigned char *hl; // per row and z plane: 16 hi then 16 lo FP16 values at its level's scale
   const float *zone_mass;  // per tile, parent and child: total mass of the child's zone
   const int *rows;         // per tile: [216][256] source row or -1
   const int *tgt;          // per tile: [256][8] target index or -1
@@ -128,8 +130,10 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 __device__ __forceinline__ void cp16(uint32_t dst, const void *src, uint32_t src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+// arrive on the barrier once this thread's earlier cp.async have landed
+__device__ __forceinline__ void cp_arrive(uint64_t *b) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(b)) : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -308,12 +312,53 @@ __global__ void k_tiles(int64_t ntiles, TileLevels tl, const int *__restrict__ p
   }
 }
 
-// Effective masses of every row as FP16 pairs at the row's own power-of-two
-// scale (largest |value| in [2^13, 2^14)), in the order the gather copies
-// them: per z plane 16 hi then 16 lo values (64 bytes). Also the row's scale
-// exponent and total mass. One warp per 8 rows: 4 lanes per row, each lane
-// one 16-value plane.
-__global__ void k_split(int64_t nrow, const float *__restrict__ grid, unsigned char *__restrict__ hl,
+// Rows of the source grid belong to a level and a problem; the scale of a
+// row is that of its (problem, level): the largest |effective mass| over the
+// level's rows of that problem, brought into [2^13, 2^14).
+struct RowLevels {
+  int64_t off[kMaxDepth + 2];  // box offsets per level
+  int nlev;
+  int64_t off2;                // first box of level 2 (row 0)
+};
+
+__device__ __forceinline__ int row_scale_slot(const RowLevels &rl, const uint64_t *__restrict__ box_key, int64_t row) {
+  const int64_t box = row + rl.off2;
+  int l = 2;
+  while (l + 1 < rl.nlev && rl.off[l + 1] <= box) ++l;
+  const uint64_t p = box_key[box] >> (3 * l);  // problem index of a batched build (0 otherwise)
+  return (int)p * rl.nlev + l;
+}
+
+// One thread per row: atomic max of its largest |value| into its (problem,
+// level) slot, aggregated over the lanes that share the slot.
+__global__ void k_level_amax(int64_t nrow, const float *__restrict__ grid, const uint64_t *__restrict__ box_key,
+                             RowLevels rl, int *__restrict__ amax) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = row < nrow;
+  unsigned m = 0u;
+  int slot = -1;
+  if (live) {
+    const float4 *g = reinterpret_cast<const float4 *>(grid + row * kM3);
+    float a = 0.f;
+#pragma unroll
+    for (int k = 0; k < kM3 / 4; ++k) {
+      const float4 v = g[k];
+      a = fmaxf(a, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    m = __float_as_uint(a);
+    slot = row_scale_slot(rl, box_key, row);
+  }
+  const unsigned peers = __match_any_sync(0xffffffffu, slot);
+  const unsigned gm = __reduce_max_sync(peers, m);
+  if (live && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicMax(amax + slot, (int)gm);
+}
+
+// Effective masses of every row as FP16 pairs at the row's (problem, level)
+// scale, in the order the gather copies them: per z plane 16 hi then 16 lo
+// values (64 bytes); also the row's scale exponent (kNoExp without mass) and
+// total mass. 4 lanes per row, one z plane each.
+__global__ void k_split(int64_t nrow, const float *__restrict__ grid, const uint64_t *__restrict__ box_key,
+                        RowLevels rl, const int *__restrict__ amax, unsigned char *__restrict__ hl,
                         int *__restrict__ box_exp, float *__restrict__ box_mass) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t row = i >> 2;
@@ -340,8 +385,8 @@ __global__ void k_split(int64_t nrow, const float *__restrict__ grid, unsigned c
   sum += __shfl_xor_sync(0xffffffffu, sum, 1);
   sum += __shfl_xor_sync(0xffffffffu, sum, 2);
   if (!live) return;
-  const int e = m > 0.f ? scale_exp(m) : kNoExp;
-  const float sc = m > 0.f ? pow2f(e) : 0.f;
+  const int e = scale_exp(__int_as_float(amax[row_scale_slot(rl, box_key, row)]));
+  const float sc = pow2f(e);
   uint32_t hw[8], lw[8];
 #pragma unroll
   for (int k = 0; k < kKC; k += 2) {
@@ -356,7 +401,7 @@ __global__ void k_split(int64_t nrow, const float *__restrict__ grid, unsigned c
   dst[2] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
   dst[3] = make_uint4(lw[4], lw[5], lw[6], lw[7]);
   if (zq == 0) {
-    box_exp[row] = e;
+    box_exp[row] = m > 0.f ? e : kNoExp;
     box_mass[row] = sum;
   }
 }
@@ -389,20 +434,6 @@ __global__ void k_col_exp(int64_t ntiles, const int *__restrict__ rows, const in
   for (int o = 0; o < 8; ++o) zone_mass[i * 8 + o] = (float)zm[o];
 }
 
-// packed FP16 x2 product, round to nearest
-__device__ __forceinline__ uint32_t hmul2(uint32_t a, uint32_t b) {
-  uint32_t r;
-  asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
-  return r;
-}
-
-// FP16 bits of 2^k (k <= 0), zero below the smallest subnormal
-__device__ __forceinline__ uint32_t half_pow2_bits(int k) {
-  if (k >= -14) return (uint32_t)(15 + k) << 10;
-  if (k >= -24) return 1u << (k + 24);
-  return 0u;
-}
-
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ Params pr) {
   extern __shared__ __align__(1024) unsigned char smraw[];
@@ -418,7 +449,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
-      bar_init(&full[s], 1 + 8);
+      bar_init(&full[s], 1 + kGatherThreads);
       bar_init(&empty[s], 1);
     }
     bar_init(&accf, 1);
@@ -466,6 +497,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
           failed = 1;
           break;
         }
+        fence_async_smem();  // the gathered tiles were written by cp.async
         tc_fence_after();
         // rows hold 16 hi then 16 lo values: hi*hi, hi*lo, lo*hi
         const uint32_t a = su32(sm + st * kStageBytes), b = a + kABytes;
@@ -479,82 +511,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     }
   } else if (warp < kEpiWarp0) {
     // 4 lanes per parent (one 16-byte piece of its 64-byte plane row each), 8
-    // parents per warp instruction, parents pw*32 + 8m + grp for m = 0..3.
-    // Chunk c + 4 is copied while chunk c is rescaled: the copy cursor runs
-    // exactly one slot ahead of the rescale cursor.
+    // parents per warp instruction: parents pw*64 + 8m + grp, m = 0..7. Each
+    // thread arrives on the stage's full barrier when its copies have landed;
+    // rows are read two slots ahead.
     const int pw = warp - kProdWarp0, sub = lane & 3, grp = lane >> 2;
-    const int nbase = pw * 32 + grp;
+    const int nbase = pw * 64 + grp;
     const int *rp = pr.rows + tile * kSlots * kTileN + nbase;
-    unsigned char *const b0 = sm + kABytes;
-    const uint32_t bsh = su32(b0);
-    uint32_t soff[4];
-    int ecol[4], r_iss[4], r_pre[4], e_iss[4];
+    const uint32_t bsh = su32(sm + kABytes);
+    uint32_t soff[8];
+    int r0[8], r1[8], r2[8];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
+    for (int m = 0; m < 8; ++m) {
       soff[m] = (uint32_t)sw64(nbase + 8 * m, sub);
-      ecol[m] = __ldg(pr.col_exp + tile * kTileN + nbase + 8 * m);
-      r_iss[m] = __ldg(rp + 8 * m);          // slot 0
-      r_pre[m] = __ldg(rp + kTileN + 8 * m);  // slot 1
+      r0[m] = __ldg(rp + 8 * m);
+      r1[m] = __ldg(rp + kTileN + 8 * m);
+      r2[m] = __ldg(rp + 2 * kTileN + 8 * m);
     }
-#pragma unroll
-    for (int m = 0; m < 4; ++m) e_iss[m] = r_iss[m] >= 0 ? __ldg(pr.box_exp + r_iss[m]) : kNoExp;
-    auto issue = [&](int ci) {
-      const int st = ci % kStages;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int row = r_iss[m];
-        const unsigned char *src = pr.hl + ((int64_t)(row >= 0 ? row : 0) * 4 + (ci & 3)) * kRowBytes + 16 * sub;
-        cp16(bsh + st * kStageBytes + soff[m], src, row >= 0 ? 16u : 0u);
-      }
-    };
-    bool ok = true;
-    // copies of slot 0 (stages 0..3 start free)
-    for (int ci = 0; ci < kGatherAhead; ++ci) {
-      issue(ci);
-      cp_commit();
-    }
-    uint32_t scale[4];
+    const unsigned char *hsub = pr.hl + 16 * sub;
     for (int c = 0; c < kChunks; ++c) {
-      if ((c & 3) == 0) {
-        // entering slot c / 4: its scale; the copy cursor moves to slot c / 4 + 1
-        const int s2 = (c >> 2) + 2;
+      if ((c & 3) == 0 && c > 0) {
+        const int s3 = (c >> 2) + 2;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          scale[m] = half_pow2_bits(ecol[m] - e_iss[m]);
-          scale[m] |= scale[m] << 16;
-          r_iss[m] = r_pre[m];
-          r_pre[m] = s2 < kSlots ? __ldg(rp + (int64_t)s2 * kTileN + 8 * m) : -1;
+        for (int m = 0; m < 8; ++m) {
+          r0[m] = r1[m];
+          r1[m] = r2[m];
+          r2[m] = s3 < kSlots ? __ldg(rp + (int64_t)s3 * kTileN + 8 * m) : -1;
         }
-#pragma unroll
-        for (int m = 0; m < 4; ++m) e_iss[m] = r_iss[m] >= 0 ? __ldg(pr.box_exp + r_iss[m]) : kNoExp;
       }
-      const int ci = c + kGatherAhead;
-      if (ci < kChunks) {
-        if (!__all_sync(0xffffffffu, bar_wait(&empty[ci % kStages], ((ci / kStages) & 1) ^ 1))) {
-          ok = false;
-          break;
-        }
-        issue(ci);
-      }
-      cp_commit();
-      cp_wait<kGatherAhead>();  // chunk c has landed
       const int st = c % kStages;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        uint4 *p = reinterpret_cast<uint4 *>(b0 + st * kStageBytes + soff[m]);
-        uint4 v = *p;
-        v.x = hmul2(v.x, scale[m]);
-        v.y = hmul2(v.y, scale[m]);
-        v.z = hmul2(v.z, scale[m]);
-        v.w = hmul2(v.w, scale[m]);
-        *p = v;
+      if (!__all_sync(0xffffffffu, bar_wait(&empty[st], ((c / kStages) & 1) ^ 1))) {
+        failed = 1;
+        break;
       }
-      fence_async_smem();
-      __syncwarp();
-      if (lane == 0) bar_arrive(&full[st]);
+      const uint32_t dst = bsh + st * kStageBytes;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int row = r0[m];
+        cp16(dst + soff[m], hsub + ((int64_t)(row >= 0 ? row : 0) * 4 + (c & 3)) * kRowBytes, row >= 0 ? 16u : 0u);
+      }
+      cp_arrive(&full[st]);
     }
-    cp_wait<0>();
-    if (!ok) failed = 1;
   } else {
     // drain: total += block accumulator; after the last block write the values
     const int lq = warp & 3, half = (warp - kEpiWarp0) >> 2;
@@ -716,9 +712,19 @@ hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   HPM_TRY(pl->s.box_mass.ensure(sizeof(float) * nrow, st));
   HPM_TRY(pl->s.col_exp.ensure(sizeof(int) * pl->tc_ntiles * tc::kTileN, st));
   HPM_TRY(pl->s.zone_mass.ensure(sizeof(float) * pl->tc_ntiles * tc::kTileN * 8, st));
+  tc::RowLevels rl{};
+  rl.nlev = pl->max_depth + 1;
+  for (int l = 0; l <= pl->max_depth + 1; ++l) rl.off[l] = pl->lvl_off[l];
+  rl.off2 = off2;
+  const size_t nslot = (size_t)(pl->nprob > 0 ? pl->nprob : 1) * rl.nlev;
+  HPM_TRY(pl->s.level_amax.ensure(sizeof(int) * nslot, st));
+  HPM_CUDA(cudaMemsetAsync(pl->s.level_amax.p, 0, sizeof(int) * nslot, st));
+  tc::k_level_amax<<<(unsigned)((nrow + 255) / 256), 256, 0, st>>>(
+      nrow, pl->s.grid.as<float>(), pl->t.box_key.as<uint64_t>(), rl, pl->s.level_amax.as<int>());
+  HPM_LAUNCHED(launches);
   tc::k_split<<<(unsigned)((4 * nrow + 255) / 256), 256, 0, st>>>(
-      nrow, pl->s.grid.as<float>(), pl->s.grid_hl.as<unsigned char>(), pl->s.box_exp.as<int>(),
-      pl->s.box_mass.as<float>());
+      nrow, pl->s.grid.as<float>(), pl->t.box_key.as<uint64_t>(), rl, pl->s.level_amax.as<int>(),
+      pl->s.grid_hl.as<unsigned char>(), pl->s.box_exp.as<int>(), pl->s.box_mass.as<float>());
   HPM_LAUNCHED(launches);
   tc::k_col_exp<<<(unsigned)((pl->tc_ntiles * tc::kTileN + 255) / 256), 256, 0, st>>>(
       pl->tc_ntiles, pl->t.tc_rows.as<int>(), pl->s.box_exp.as<int>(), pl->s.box_mass.as<float>(),
@@ -729,7 +735,6 @@ hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   p.w_exp = pl->tc_wexp.as<int>();
   p.col_exp = pl->s.col_exp.as<int>();
   p.hl = pl->s.grid_hl.as<unsigned char>();
-  p.box_exp = pl->s.box_exp.as<int>();
   p.zone_mass = pl->s.zone_mass.as<float>();
   p.rows = pl->t.tc_rows.as<int>();
   p.tgt = pl->t.tc_tgt.as<int>();
