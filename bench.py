@@ -46,6 +46,43 @@ def m2l_flops_per_target(ng: int) -> float:
     return 5.0 * P ** 3 * math.log2(P ** 3) + 2.0 * P * P * (P // 2 + 1)
 
 
+DENSE_FLOP_PER_PARENT = 3 * 2 * 512 * 216 * 64   # three FP16 products per term of the 512 x 13824 product
+
+
+def roofline_of(stats_steps, ng, n_targets, traffic_src):
+    """Roofline object of the source-to-target kernel of the last steps.
+
+    Ng = 4 default path (dense product on the tensor cores): executed tensor FLOP of
+    the kernel alone (three FP16 products per term) per its own CUDA-event duration,
+    against the measured dense bf16 burst peak (FP16 runs at the bf16 rate). FFT and
+    any-order kernels: the nominal FFT count per target over the stage time against
+    the FP32 FFMA peak. Both report the nominal FFT rate of the whole stage too."""
+    peaks = measured_peaks()
+    stage_ms = statistics.mean(s["ms_m2l"] for s in stats_steps)
+    nominal = m2l_flops_per_target(ng) * n_targets / (stage_ms / 1e3) / 1e12
+    parents = stats_steps[-1].get("m2l_parents", 0)
+    if parents:
+        kms = statistics.mean(s["ms_m2l_kernel"] for s in stats_steps)
+        achieved = DENSE_FLOP_PER_PARENT * parents / (kms / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops", 1900.0)
+        return {"kernel": "k_m2l_tc: Ng = 4 source-to-target as a dense FP16-pair tcgen05 product per parent block",
+                "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": profile_traffic(traffic_src) if traffic_src else None, "ms_per_launch": kms,
+                "launches_per_step": 1, "flop_per_parent": DENSE_FLOP_PER_PARENT, "parents_per_launch": parents,
+                "peak_basis": "MEASURED_PEAKS.json bf16_tflops (dense, burst) of measured; FP16 has the bf16 tensor rate",
+                "flop_basis": "3 FP16 products (hi*hi, hi*lo, lo*hi) x 2 x 512 rows x 13824 K per parent",
+                "stage_ms": stage_ms, "stage_nominal_fft_tflops": nominal}
+    sm_mhz_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
+    return {"kernel": "source-to-target FFT convolution (k_m2l4)" if ng == 4 else
+                      "source-to-target convolution, x-transform kernel (k_m2l_xdft)",
+            "bound": "alu", "achieved": nominal, "peak": fp32_peak, "unit": "TFLOP/s", "frac": nominal / fp32_peak,
+            "traffic": profile_traffic(traffic_src) if traffic_src else None, "ms_per_launch": stage_ms,
+            "launches_per_step": 1, "flop_per_target": m2l_flops_per_target(ng), "targets_per_launch": n_targets,
+            "peak_basis": f"{SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_mhz_max:.0f} MHz "
+                          "(nominal FFMA rate)"}
+
+
 def workload_for(rank: int, n_override: int | None = None, kind: str = "plummer", ng: int = 4) -> I.Workload:
     if kind == "uniform":
         n = n_override or (1 << 24)
@@ -205,7 +242,7 @@ def run_gpu(args) -> None:
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    ms_m2l, launches = [], 0
+    stats_steps, launches = [], 0
     stage_keys = ("ms_tree", "ms_p2g", "ms_m2m", "ms_m2l", "ms_l2l", "ms_g2p", "ms_p2p")
     stage_sum = {k: 0.0 for k in stage_keys}
     if world > 1:
@@ -218,7 +255,7 @@ def run_gpu(args) -> None:
             step()
             ev[k][1].record(stream)
             st = hpm.hpm_get_stats(plan)       # waits for this step's last event
-            ms_m2l.append(st["ms_m2l"])
+            stats_steps.append(st)
             for key in stage_keys:
                 stage_sum[key] += st[key]
             launches += st["launches"]
@@ -250,14 +287,11 @@ def run_gpu(args) -> None:
     n_total = n_all
     ms_per_step = total_ms / args.steps
     value = n_total * args.steps / (total_ms / 1e3)
-    peaks = measured_peaks()
-    sm_mhz_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
-    m2l_ms = statistics.mean(ms_m2l)
-    flop = m2l_flops_per_target(w.ng) * info["n_targets"]
-    achieved = flop / (m2l_ms / 1e3) / 1e12
-    traffic = (profile_traffic(os.path.join(ROOT, "paper_1906_10734_gb300", "csrc", "m2l.cu"))
-               if args.workload == "plummer" and w.ng == 4 else None)
+    csrc = os.path.join(ROOT, "paper_1906_10734_gb300", "csrc")
+    traffic_src = None
+    if args.workload == "plummer" and w.ng == 4:
+        traffic_src = os.path.join(csrc, "m2l_tc.cu" if args.m2l == "tensor" else "m2l.cu")
+    roofline = roofline_of(stats_steps, w.ng, info["n_targets"], traffic_src)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -273,13 +307,7 @@ def run_gpu(args) -> None:
                 "d2h_bytes_per_step": 16 * w.n, "api": "hpm_solve_host (pinned host buffers)"},
         "gpu_launches": int(launches),
         "stages_ms": {k[3:]: v / args.steps for k, v in stage_sum.items()},
-        "roofline": {"kernel": "source-to-target FFT convolution (k_m2l4)" if w.ng == 4 else
-                               "source-to-target convolution, any-order kernel (k_m2l_generic)", "bound": "alu",
-                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": traffic, "ms_per_launch": m2l_ms, "launches_per_step": 1,
-                     "flop_per_target": m2l_flops_per_target(w.ng), "targets_per_launch": info["n_targets"],
-                     "peak_basis": f"{SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
-                                   f"{sm_mhz_max:.0f} MHz (nominal FFMA rate)"},
+        "roofline": roofline,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -309,7 +337,7 @@ def run_batch(args) -> None:
     for _ in range(args.warmup):
         hpm.hpm_solve_batch(plan, bufs, stream)
     torch.cuda.synchronize(dev)
-    step_ms, m2l_ms, launches = [], [], 0
+    step_ms, stats_steps, launches = [], [], 0
     with ClockSampler(0) as clk:
         for k in range(args.steps):
             l2_flush.fill_(k & 0xff)
@@ -319,7 +347,7 @@ def run_batch(args) -> None:
             b.record(stream)
             b.synchronize()
             st = hpm.hpm_get_stats(plan)
-            m2l_ms.append(st["ms_m2l"])
+            stats_steps.append(st)
             launches += st["launches"]
             step_ms.append(a.elapsed_time(b))
     info = hpm.hpm_get_lists_info(plan)
@@ -336,9 +364,6 @@ def run_batch(args) -> None:
     hpm.hpm_destroy(plan)
     total = sum(step_ms)
     value = n_total * args.steps / (total / 1e3)
-    m2l = statistics.mean(m2l_ms)
-    achieved = m2l_flops_per_target(4) * info["n_targets"] / (m2l / 1e3) / 1e12
-    peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * measured_peaks().get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -351,9 +376,7 @@ def run_batch(args) -> None:
         "per_problem_loop": {"value": n_total / (loop_ms / 1e3), "ms": loop_ms,
                              "speedup_of_batch": loop_ms / (total / args.steps)},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "source-to-target FFT convolution (k_m2l4)", "bound": "alu", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                     "ms_per_launch": m2l},
+        "roofline": roofline_of(stats_steps, 4, info["n_targets"], None),
         "clocks": clk.summary()}), flush=True)
 
 

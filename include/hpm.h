@@ -250,6 +250,10 @@ typedef struct {
   int64_t launches;        /* kernels launched by the last build + solve */
   int64_t m2l_launches;    /* of which source-to-target                  */
   int64_t m2l_targets;     /* target cells convolved by the last solve    */
+  float ms_m2l_kernel;     /* Ng = 4 tensor-core path: the dense product
+                              kernel alone (0 on the other paths)         */
+  int64_t m2l_parents;     /* parents whose 6^3 blocks that kernel
+                              multiplied (0 on the other paths)           */
 } hpm_stats;
 
 hpm_status hpm_get_stats(hpm_plan_t plan, hpm_stats *stats);

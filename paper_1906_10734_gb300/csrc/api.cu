@@ -52,6 +52,10 @@ static void make_tables(int ng, GridletTables &tb) {
     tb.node_d[j] = x[j];
     tb.inv_den_d[j] = 1.0 / den;
     tb.inv_den[j] = (float)(1.0 / den);
+    double den_u = 1.0;
+    for (int k = 0; k < ng; ++k)
+      if (k != j) den_u *= (double)(2 * (j - k));
+    tb.inv_den_u[j] = 1.0 / den_u;
   }
   for (int s = 0; s < 2; ++s) {
     const double a = s ? 0.5 : -0.5;
@@ -67,7 +71,7 @@ static void make_tables(int ng, GridletTables &tb) {
 }
 
 static void release_all(hpm_plan_s *pl, cudaStream_t s) {
-  DevBuf *bufs[] = {&pl->ghat, &pl->t.keys, &pl->t.keys_alt, &pl->t.perm, &pl->t.perm_alt, &pl->t.spm,
+  DevBuf *bufs[] = {&pl->ghat, &pl->t.keys, &pl->t.keys_alt, &pl->t.perm, &pl->t.perm_alt, &pl->t.spm, &pl->t.pbox,
                     &pl->t.box_key, &pl->t.box_beg, &pl->t.box_end, &pl->t.box_parent, &pl->t.box_flags,
                     &pl->t.box_child, &pl->t.box_nb, &pl->t.cnt, &pl->t.off, &pl->t.bnd, &pl->t.p2g_off, &pl->t.par_box, &pl->t.tgt_blk, &pl->t.tgt_info, &pl->kx_green, &pl->kz_green, &pl->tc_w, &pl->tc_wexp, &pl->tc_mean, &pl->t.tc_rows, &pl->t.tc_tgt, &pl->t.tgt_box,
                     &pl->t.box_tgt, &pl->t.leaf_box, &pl->t.p2g_box, &pl->t.item_leaf, &pl->t.item_s0,
@@ -384,6 +388,10 @@ hpm_status hpm_get_stats(hpm_plan_t plan, hpm_stats *st) {
     st->ms_g2p = v[5];
     st->ms_p2p = v[6];
     st->ms_total = tot + tree;
+    float mk = 0.f;
+    if (plan->stats.m2l_parents > 0 && cudaEventElapsedTime(&mk, plan->ev[10], plan->ev[11]) == cudaSuccess)
+      st->ms_m2l_kernel = mk;
+    cudaGetLastError();
   }
   return HPM_OK;
 }

@@ -51,18 +51,20 @@ struct GridletTables {
   float t1[2][kMaxNg][kMaxNg];       // T^{s}_{pq} = ell_p((a_s + x_q)/2), a_0 = -1/2, a_1 = +1/2
   double node_d[kMaxNg];
   double inv_den_d[kMaxNg];          // 1 / prod_{k != j} (x_j - x_k)
+  double inv_den_u[kMaxNg];          // the same for the nodes 2 Ng x_j = 2j + 1 - Ng (integers)
   float inv_den[kMaxNg];
 };
 
 struct TreeDev {
   // sorted particles
   DevBuf keys, keys_alt, perm, perm_alt;
-  DevBuf spm;        // double4 (x, y, z, m) in sorted order
+  DevBuf spm;        // sorted particles: float4 unit-cube position hi (x, y, z, m) then lo (x, y, z, 0)
   // boxes, all levels, level-major, Morton order within a level
   DevBuf box_key, box_beg, box_end, box_parent, box_flags, box_child, box_nb;
   DevBuf cnt, off, bnd;   // per-box scratch for child counting
   // work lists
   DevBuf tgt_box, box_tgt, leaf_box, p2g_box, p2g_off, par_box;
+  DevBuf pbox;       // leaf box of every sorted particle
   // interaction zone of every target as its 6^3 parent block: row of each box's
   // effective masses, -1 where empty, outside the domain or in the near zone;
   // and (level << 3 | child octant) per target
@@ -145,7 +147,7 @@ struct hpm_plan_s {
   std::vector<int64_t> tgt_lvl_off;  // target offsets per level (levels 2..D)
   std::vector<int64_t> leaf_lvl_off;
   hpm_stats stats{};
-  cudaEvent_t ev[10] = {};
+  cudaEvent_t ev[12] = {};  // stage boundaries 0..7, tree 8..9, dense product kernel 10..11
   bool events_ready = false;
   hpm::DevBuf host_io_pos, host_io_mass, host_io_phi, host_io_acc;
   hpm::DevBuf batch_desc;          // device copy of a batch's problem table and offsets

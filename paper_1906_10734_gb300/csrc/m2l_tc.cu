@@ -408,16 +408,18 @@ __global__ void k_split(int64_t nrow, const float *__restrict__ grid, const uint
 
 // Per tile column (parent): the column scale exponent (the smallest row
 // exponent of its block, i.e. the scale of its largest |value|) and the total
-// mass of each child's interaction zone, summed in FP64.
+// mass of each child's interaction zone, summed in FP64. One warp per column,
+// the lanes splitting the 216 slots.
 __global__ void k_col_exp(int64_t ntiles, const int *__restrict__ rows, const int *__restrict__ box_exp,
                           const float *__restrict__ box_mass, int *__restrict__ col_exp,
                           float *__restrict__ zone_mass) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ntiles * kTileN) return;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= ntiles * kTileN) return;  // whole warps
   const int *rr = rows + (i / kTileN) * kSlots * kTileN + (i % kTileN);
   int e = kNoExp;
   double zm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int s = 0; s < kSlots; ++s) {
+  for (int s = lane; s < kSlots; s += 32) {
     const int row = rr[(int64_t)s * kTileN];
     if (row < 0) continue;
     e = min(e, box_exp[row]);
@@ -429,12 +431,18 @@ __global__ void k_col_exp(int64_t ntiles, const int *__restrict__ rows, const in
       if (max(abs(sx - px), max(abs(sy - py), abs(sz - pz))) >= 2) zm[o] += bm;
     }
   }
-  col_exp[i] = e == kNoExp ? 0 : e;
+  e = __reduce_min_sync(0xffffffffu, e);
 #pragma unroll
-  for (int o = 0; o < 8; ++o) zone_mass[i * 8 + o] = (float)zm[o];
+  for (int o = 0; o < 8; ++o)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) zm[o] += __shfl_xor_sync(0xffffffffu, zm[o], off);
+  if (lane == 0) {
+    col_exp[i] = e == kNoExp ? 0 : e;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) zone_mass[i * 8 + o] = (float)zm[o];
+  }
 }
 
-// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ Params pr) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
@@ -726,7 +734,7 @@ hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
       nrow, pl->s.grid.as<float>(), pl->t.box_key.as<uint64_t>(), rl, pl->s.level_amax.as<int>(),
       pl->s.grid_hl.as<unsigned char>(), pl->s.box_exp.as<int>(), pl->s.box_mass.as<float>());
   HPM_LAUNCHED(launches);
-  tc::k_col_exp<<<(unsigned)((pl->tc_ntiles * tc::kTileN + 255) / 256), 256, 0, st>>>(
+  tc::k_col_exp<<<(unsigned)((pl->tc_ntiles * tc::kTileN * 32 + 255) / 256), 256, 0, st>>>(
       pl->tc_ntiles, pl->t.tc_rows.as<int>(), pl->s.box_exp.as<int>(), pl->s.box_mass.as<float>(),
       pl->s.col_exp.as<int>(), pl->s.zone_mass.as<float>());
   HPM_LAUNCHED(launches);
@@ -751,8 +759,11 @@ hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
     attr = true;
   }
   const int64_t grid = pl->tc_ntiles * tc::kQuarters;
+  if (pl->events_ready) cudaEventRecord(pl->ev[10], st);
   tc::k_m2l_tc<<<(unsigned)grid, tc::kThreads, tc::kSmem, st>>>(p);
   HPM_LAUNCHED(launches);
+  if (pl->events_ready) cudaEventRecord(pl->ev[11], st);
+  pl->stats.m2l_parents = pl->npar;
   return HPM_OK;
 }
 

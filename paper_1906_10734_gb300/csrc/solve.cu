@@ -15,9 +15,6 @@ namespace hpm {
 namespace {
 
 // Sorted particle: FP64 position and mass.
-struct __align__(32) PM {
-  double x, y, z, m;
-};
 
 constexpr int kThreads = 256;
 constexpr int kWarpsPerBlock = kThreads / 32;
@@ -54,51 +51,79 @@ __device__ __forceinline__ int level_of(const LevelTable &lt, int64_t box) {
 
 // ---------------------------------------------------------------------------
 __global__ void k_gather(int64_t n, const uint32_t *__restrict__ perm, const double *__restrict__ pos,
-                         const double *__restrict__ mass, double ox, double oy, double oz,
-                         PM *__restrict__ spm, float4 *__restrict__ hi, float4 *__restrict__ lo) {
+                         const double *__restrict__ mass, double ox, double oy, double oz, double inv_side,
+                         float4 *__restrict__ hi, float4 *__restrict__ lo) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t p = perm[i];
   const double x = pos[3 * (int64_t)p], y = pos[3 * (int64_t)p + 1], z = pos[3 * (int64_t)p + 2];
-  const double m = mass[p];
-  spm[i] = PM{x, y, z, m};
-  // position relative to the domain origin as an unevaluated sum hi + lo of
-  // two floats: differences of nearby particles stay accurate to FP32
-  // relative precision of the difference itself
-  const double rx = x - ox, ry = y - oy, rz = z - oz;
-  const float hx = (float)rx, hy = (float)ry, hz = (float)rz;
-  hi[i] = make_float4(hx, hy, hz, (float)m);
-  lo[i] = make_float4((float)(rx - (double)hx), (float)(ry - (double)hy), (float)(rz - (double)hz), 0.f);
+  // position in the unit cube of the domain, u = (x - o) / S, as an
+  // unevaluated sum hi + lo of two floats: a cell-relative coordinate
+  // u 2^l - c is then exact in FP32 up to one rounding, and differences of
+  // nearby particles keep FP32 precision relative to themselves
+  const double ux = (x - ox) * inv_side, uy = (y - oy) * inv_side, uz = (z - oz) * inv_side;
+  const float hx = (float)ux, hy = (float)uy, hz = (float)uz;
+  hi[i] = make_float4(hx, hy, hz, (float)mass[p]);
+  lo[i] = make_float4((float)(ux - (double)hx), (float)(uy - (double)hy), (float)(uz - (double)hz), 0.f);
+}
+
+// The same in FP64 (exact up to one FP64 rounding): the input of the
+// moment-matching weights.
+__device__ __forceinline__ double cell_coord_d(float h, float lo, float scale, float c) {
+  return (double)fmaf(h, scale, -c) + (double)lo * (double)scale;
+}
+
+// Cell-relative coordinate xi = u 2^l - c of a hi/lo unit-cube coordinate:
+// h 2^l - c is exact (the two are within a factor two of each other away from
+// the domain's first cell, where the error stays below 2^-26), so the result
+// carries one FP32 rounding.
+__device__ __forceinline__ float cell_coord(float h, float lo, float scale, float c) {
+  return fmaf(h, scale, -c) + lo * scale;
 }
 
 // 1-D Lagrange weights on the gridlet nodes, FP64 (the moment-matching solve).
-__device__ __forceinline__ void lagrange_d(const GridletTables &tb, double t, float *w) {
-  const int ng = tb.ng;
-  double diff[kMaxNg];
-  for (int k = 0; k < ng; ++k) diff[k] = t - tb.node_d[k];
-  for (int j = 0; j < ng; ++j) {
-    double v = tb.inv_den_d[j];
-    for (int k = 0; k < ng; ++k)
-      if (k != j) v *= diff[k];
-    w[j] = (float)v;
-  }
+// With u = 2 Ng xi the nodes are the integers a_k = 2k + 1 - Ng, and
+// ell_j = prod_{k != j} (u - a_k) / (a_j - a_k) is formed from prefix and
+// suffix products of the differences.
+// NG > 0 fixes the order at compile time (arrays stay in registers); NG = 0
+// takes it from the table.
+template <int NG>
+__device__ __forceinline__ void lagrange_d(const GridletTables &tb, double xi, float *w) {
+  const int ng = NG > 0 ? NG : tb.ng;
+  const double u = xi * (double)(2 * ng);
+  double d[kMaxNg], suf[kMaxNg];
+#pragma unroll
+  for (int k = 0; k < (NG > 0 ? NG : kMaxNg); ++k)
+    if (k < ng) d[k] = u - (double)(2 * k + 1 - ng);
+  suf[ng - 1] = 1.0;
+#pragma unroll
+  for (int k = (NG > 0 ? NG : kMaxNg) - 2; k >= 0; --k)
+    if (k <= ng - 2) suf[k] = suf[k + 1] * d[k + 1];
+  double pre = 1.0;
+#pragma unroll
+  for (int j = 0; j < (NG > 0 ? NG : kMaxNg); ++j)
+    if (j < ng) {
+      w[j] = (float)(tb.inv_den_u[j] * (pre * suf[j]));
+      pre *= d[j];
+    }
 }
 
 // Effective masses, M_p = sum_i m_i prod_d ell_{p_d}(xi_d) (Eq. mp in Lagrange
 // form: sum_n B_pn t^n = ell_p(t)). A block takes 8 boxes; all its threads
 // evaluate the FP64 weights of the (box, particle) pairs of those boxes, 256
 // pairs at a time, then warp w accumulates box w from shared memory.
+template <int NG>
 __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__restrict__ list,
                                                   const int *__restrict__ pair_off, LevelTable lt,
-                                                  GridletTables tb, double ox, double oy, double oz, double side,
-                                                  const uint64_t *__restrict__ key, const int *__restrict__ beg,
-                                                  const PM *__restrict__ spm, int64_t off2,
+                                                  GridletTables tb, const uint64_t *__restrict__ key,
+                                                  const int *__restrict__ beg, const float4 *__restrict__ uhi,
+                                                  const float4 *__restrict__ ulo, int64_t off2,
                                                   float *__restrict__ grid) {
   __shared__ float ws[kThreads][3][kMaxNg];
   __shared__ float ms[kThreads];
   __shared__ int off[kWarpsPerBlock + 1];
   __shared__ int bx[kWarpsPerBlock], bbeg[kWarpsPerBlock];
-  __shared__ double bc[kWarpsPerBlock][3], binv[kWarpsPerBlock];
+  __shared__ float bc[kWarpsPerBlock][3], bscale[kWarpsPerBlock];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t b0 = (int64_t)blockIdx.x * kWarpsPerBlock;
   const int nb = (int)min((int64_t)kWarpsPerBlock, nbox - b0);
@@ -109,32 +134,38 @@ __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__res
     const uint64_t k = key[box] & ((1ull << (3 * l)) - 1ull);
     bx[threadIdx.x] = box;
     bbeg[threadIdx.x] = beg[box];
-    binv[threadIdx.x] = (double)(1u << l) / side;
-    bc[threadIdx.x][0] = (double)compact3(k) + 0.5;
-    bc[threadIdx.x][1] = (double)compact3(k >> 1) + 0.5;
-    bc[threadIdx.x][2] = (double)compact3(k >> 2) + 0.5;
+    bscale[threadIdx.x] = (float)(1u << l);
+    bc[threadIdx.x][0] = (float)compact3(k) + 0.5f;
+    bc[threadIdx.x][1] = (float)compact3(k >> 1) + 0.5f;
+    bc[threadIdx.x][2] = (float)compact3(k >> 2) + 0.5f;
   }
   __syncthreads();
   const int ng = tb.ng, m3 = ng * ng * ng;
-  const double o[3] = {ox, oy, oz};
-  float acc[16];
-  for (int r = 0; r < 16; ++r) acc[r] = 0.f;
+  constexpr int kR = NG > 0 ? (NG * NG * NG + 31) / 32 : 16;  // output rounds of 32 nodes
+  float acc[kR];
+#pragma unroll
+  for (int r = 0; r < kR; ++r) acc[r] = 0.f;
   const int P0 = off[0], P1 = off[nb];
   for (int c0 = P0; c0 < P1; c0 += kThreads) {
     const int p = c0 + threadIdx.x;
     if (p < P1) {
       int lb = 0;
       while (lb + 1 < nb && off[lb + 1] <= p) ++lb;
-      const PM q = spm[bbeg[lb] + (p - off[lb])];
-      const double xs[3] = {q.x, q.y, q.z};
-      for (int d = 0; d < 3; ++d) lagrange_d(tb, fma(xs[d] - o[d], binv[lb], -bc[lb][d]), ws[threadIdx.x][d]);
-      ms[threadIdx.x] = (float)q.m;
+      const int pi = bbeg[lb] + (p - off[lb]);
+      const float4 h = uhi[pi], q = ulo[pi];
+      const float sc = bscale[lb];
+      lagrange_d<NG>(tb, cell_coord_d(h.x, q.x, sc, bc[lb][0]), ws[threadIdx.x][0]);
+      lagrange_d<NG>(tb, cell_coord_d(h.y, q.y, sc, bc[lb][1]), ws[threadIdx.x][1]);
+      lagrange_d<NG>(tb, cell_coord_d(h.z, q.z, sc, bc[lb][2]), ws[threadIdx.x][2]);
+      ms[threadIdx.x] = h.w;
     }
     __syncthreads();
     if (w < nb) {
       const int jb = max(off[w], c0) - c0, je = min(off[w + 1], c0 + kThreads) - c0;
-      for (int r = 0; r * 32 + lane < m3; ++r) {
+#pragma unroll
+      for (int r = 0; r < kR; ++r) {
         const int pp = r * 32 + lane;
+        if (pp >= m3) break;
         const int px = pp % ng, py = (pp / ng) % ng, pz = pp / (ng * ng);
         float s = acc[r];
         for (int j = jb; j < je; ++j) s += ms[j] * ws[j][0][px] * ws[j][1][py] * ws[j][2][pz];
@@ -145,8 +176,11 @@ __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__res
   }
   if (w < nb) {
     float *out = grid + (int64_t)(bx[w] - off2) * m3;
-    for (int r = 0; r * 32 + lane < m3; ++r) out[r * 32 + lane] = acc[r];
+#pragma unroll
+    for (int r = 0; r < kR; ++r)
+      if (r * 32 + lane < m3) out[r * 32 + lane] = acc[r];
   }
+
 }
 
 // Separable application of a 1-D operator along one axis of an Ng^3 gridlet
@@ -193,6 +227,147 @@ __global__ void __launch_bounds__(kGThreads) k_m2m(int64_t b, int64_t e, Gridlet
   }
   float *dst = grid + (int64_t)(box - off2) * m3;
   for (int p = lane; p < m3; p += 32) dst[p] = res[w][p];
+}
+
+// Ng = 4 child-to-parent, one parent per warp, with the transform factored
+// over the child octants: M^P = sum_cz Tz (sum_cy Ty (sum_cx Tx M^(cx,cy,cz)))
+// (T^{a} of the x, y, z axes as in k_m2m). The 8 children are loaded at once;
+// the x stage forms 4 gridlets (summed over cx), y forms 2, z the parent.
+constexpr int kM2MWarps = 8;
+__global__ void __launch_bounds__(kM2MWarps * 32) k_m2m4(int64_t b, int64_t e, GridletTables tb,
+                                                         const uint8_t *__restrict__ flags,
+                                                         const int *__restrict__ child, int64_t off2,
+                                                         float *__restrict__ grid) {
+  __shared__ float T[2][4][4];
+  __shared__ float ch[kM2MWarps][8][64], X[kM2MWarps][4][64], Y[kM2MWarps][2][64];
+  if (threadIdx.x < 32) T[threadIdx.x >> 4][(threadIdx.x >> 2) & 3][threadIdx.x & 3] =
+      tb.t1[threadIdx.x >> 4][(threadIdx.x >> 2) & 3][threadIdx.x & 3];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t box = b + (int64_t)blockIdx.x * kM2MWarps + w;
+  if (box >= e || !(flags[box] & kInternal)) return;
+  {
+    // child o = lane / 4, 16 values each
+    const int o = lane >> 2, sub = lane & 3;
+    const int c = child[box * 8 + o];
+    float4 v[4];
+    if (c >= 0) {
+      const float4 *src = reinterpret_cast<const float4 *>(grid + (int64_t)(c - off2) * 64 + 16 * sub);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = src[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float4 *dst = reinterpret_cast<float4 *>(&ch[w][o][16 * sub]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dst[k] = v[k];
+  }
+  __syncwarp();
+  // x: X[cy + 2 cz][p] = sum_cx sum_qx T[cx][px][qx] ch[cx + 2cy + 4cz][qx, py, pz]
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int idx = r * 32 + lane, g = idx >> 6, p = idx & 63, px = p & 3, rowb = p - px;
+    float acc = 0.f;
+#pragma unroll
+    for (int cx = 0; cx < 2; ++cx)
+#pragma unroll
+      for (int qx = 0; qx < 4; ++qx) acc = fmaf(T[cx][px][qx], ch[w][cx + 2 * g][rowb + qx], acc);
+    X[w][g][p] = acc;
+  }
+  __syncwarp();
+  // y: Y[cz][p] = sum_cy sum_qy T[cy][py][qy] X[cy + 2cz][px, qy, pz]
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int idx = r * 32 + lane, cz = idx >> 6, p = idx & 63, py = (p >> 2) & 3, base = p - 4 * py;
+    float acc = 0.f;
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+      for (int qy = 0; qy < 4; ++qy) acc = fmaf(T[cy][py][qy], X[w][cy + 2 * cz][base + 4 * qy], acc);
+    Y[w][cz][p] = acc;
+  }
+  __syncwarp();
+  // z: M^P[p] = sum_cz sum_qz T[cz][pz][qz] Y[cz][px, py, qz]
+  float *out = grid + (int64_t)(box - off2) * 64;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int p = r * 32 + lane, pz = p >> 4, base = p & 15;
+    float acc = 0.f;
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+      for (int qz = 0; qz < 4; ++qz) acc = fmaf(T[cz][pz][qz], Y[w][cz][base + 16 * qz], acc);
+    out[p] = acc;
+  }
+}
+
+// Ng = 4 parent-to-child as k_l2l, one target per warp with the three axis
+// passes unrolled: loc_C = (Tx^T (x) Ty^T (x) Tz^T) loc_P + own values.
+__global__ void __launch_bounds__(kM2MWarps * 32) k_l2l4(int64_t tb0, int64_t tb1, int level, GridletTables tab,
+                                                         const int *__restrict__ tgt_box,
+                                                         const int *__restrict__ box_tgt,
+                                                         const int *__restrict__ parent,
+                                                         const uint64_t *__restrict__ key,
+                                                         const float *__restrict__ raw, float *__restrict__ loc,
+                                                         float *__restrict__ locc, const float *__restrict__ m2lc) {
+  __shared__ float T[2][4][4];
+  __shared__ float A[kM2MWarps][64], B[kM2MWarps][64];
+  if (threadIdx.x < 32) T[threadIdx.x >> 4][(threadIdx.x >> 2) & 3][threadIdx.x & 3] =
+      tab.t1[threadIdx.x >> 4][(threadIdx.x >> 2) & 3][threadIdx.x & 3];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t t = tb0 + (int64_t)blockIdx.x * kM2MWarps + w;
+  if (t >= tb1) return;
+  const float2 own = reinterpret_cast<const float2 *>(raw + t * 64)[lane];
+  float r0 = own.x, r1 = own.y;  // nodes 2 lane, 2 lane + 1
+  float cpar = 0.f;
+  if (level >= 3) {
+    const int box = tgt_box[t];
+    const int tp = box_tgt[parent[box]];
+    const int o = (int)(key[box] & 7u);
+    const int ax = o & 1, ay = (o >> 1) & 1, az = (o >> 2) & 1;
+    const float2 pv = reinterpret_cast<const float2 *>(loc + (int64_t)tp * 64)[lane];
+    cpar = locc[tp];
+    A[w][2 * lane] = pv.x;
+    A[w][2 * lane + 1] = pv.y;
+    __syncwarp();
+    // x: B[p] = sum_q T[ax][q][px] A[q, py, pz]
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int p = 2 * lane + k, px = p & 3, rowb = p - px;
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc = fmaf(T[ax][q][px], A[w][rowb + q], acc);
+      B[w][p] = acc;
+    }
+    __syncwarp();
+    // y: A[p] = sum_q T[ay][q][py] B[px, q, pz]
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int p = 2 * lane + k, py = (p >> 2) & 3, base = p - 4 * py;
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc = fmaf(T[ay][q][py], B[w][base + 4 * q], acc);
+      A[w][p] = acc;
+    }
+    __syncwarp();
+    // z: own += sum_q T[az][q][pz] A[px, py, q]
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int p = 2 * lane + k, pz = p >> 4, base = p & 15;
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc = fmaf(T[az][q][pz], A[w][base + 16 * q], acc);
+      if (k == 0) r0 += acc; else r1 += acc;
+    }
+  }
+  float s = r0 + r1;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  const float mean = s / 64.f;
+  reinterpret_cast<float2 *>(loc + t * 64)[lane] = make_float2(r0 - mean, r1 - mean);
+  if (lane == 0) locc[t] = cpar + (mean + m2lc[t]);
 }
 
 // Parent-to-child plus the target's own source-to-target values, with the
@@ -242,14 +417,21 @@ __global__ void __launch_bounds__(kGThreads) k_l2l(int64_t tb0, int64_t tb1, int
   if (lane == 0) locc[t] = cpar + (mean + m2lc[t]);
 }
 
-// 1-D Lagrange weights and derivatives, FP32.
+// 1-D Lagrange weights and derivatives, FP32 (NG as for lagrange_d).
+template <int NG>
 __device__ __forceinline__ void lagrange_f(const GridletTables &tb, float t, float *w, float *dw) {
-  const int ng = tb.ng;
+  const int ng = NG > 0 ? NG : tb.ng;
   float diff[kMaxNg];
-  for (int k = 0; k < ng; ++k) diff[k] = t - tb.node[k];
-  for (int j = 0; j < ng; ++j) {
+#pragma unroll
+  for (int k = 0; k < (NG > 0 ? NG : kMaxNg); ++k)
+    if (k < ng) diff[k] = t - tb.node[k];
+#pragma unroll
+  for (int j = 0; j < (NG > 0 ? NG : kMaxNg); ++j) {
+    if (j >= ng) break;
     float v = tb.inv_den[j], d = 0.f;
-    for (int k = 0; k < ng; ++k) {
+#pragma unroll
+    for (int k = 0; k < (NG > 0 ? NG : kMaxNg); ++k) {
+      if (k >= ng) break;
       if (k == j) continue;
       d = d * diff[k] + v;
       v *= diff[k];
@@ -259,53 +441,58 @@ __device__ __forceinline__ void lagrange_f(const GridletTables &tb, float t, flo
   }
 }
 
-// Far field at the particles of each leaf: phi = c + sum_p delta_p prod ell,
-// a = -(1/L) sum_p delta_p grad_xi prod ell (Eq. phix and its gradient).
-__global__ void __launch_bounds__(kThreads) k_g2p(int64_t lb, int64_t le, const int *__restrict__ leaf_box,
+// Far field at every particle from its leaf's local gridlet (one thread per
+// sorted particle, FP32 throughout): phi = c + sum_p delta_p prod ell,
+// a = -(2^l / S) sum_p delta_p grad_xi prod ell (Eq. phix and its gradient).
+template <int NG>
+__global__ void __launch_bounds__(kThreads) k_g2p(int64_t n, const int *__restrict__ pbox,
                                                   const int *__restrict__ box_tgt, LevelTable lt,
-                                                  GridletTables tb, double ox, double oy, double oz,
-                                                  double side, const uint64_t *__restrict__ key,
-                                                  const int *__restrict__ beg, const int *__restrict__ end,
-                                                  const PM *__restrict__ spm,
+                                                  GridletTables tb, float inv_side,
+                                                  const uint64_t *__restrict__ key,
+                                                  const float4 *__restrict__ uhi, const float4 *__restrict__ ulo,
                                                   const float *__restrict__ loc,
                                                   const float *__restrict__ locc,
                                                   float4 *__restrict__ far) {
-  __shared__ float dl[kWarpsPerBlock][512];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t item = lb + (int64_t)blockIdx.x * kWarpsPerBlock + w;
-  if (item >= le) return;
-  const int box = leaf_box[item];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int box = pbox[i];
   const int t = box_tgt[box];
-  const int ng = tb.ng, m3 = ng * ng * ng;
-  for (int p = lane; p < m3; p += 32) dl[w][p] = loc[(int64_t)t * m3 + p];
-  const float c0 = locc[t];
-  __syncwarp();
-  const int l = level_of(lt, box);
-  const double inv = (double)(1u << l) / side;
-  const uint64_t k = key[box] & ((1ull << (3 * l)) - 1ull);
-  const double cc[3] = {(double)compact3(k) + 0.5, (double)compact3(k >> 1) + 0.5,
-                        (double)compact3(k >> 2) + 0.5};
-  const double o[3] = {ox, oy, oz};
-  const float invL = (float)inv;
-  for (int i = beg[box] + lane; i < end[box]; i += 32) {
-    const PM q = spm[i];
-    const double xs[3] = {q.x, q.y, q.z};
-    float wv[3][kMaxNg], dw[3][kMaxNg];
-    for (int d = 0; d < 3; ++d) lagrange_f(tb, (float)fma(xs[d] - o[d], inv, -cc[d]), wv[d], dw[d]);
-    float f = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-    for (int pz = 0; pz < ng; ++pz)
-      for (int py = 0; py < ng; ++py) {
-        const float wyz = wv[1][py] * wv[2][pz], dyz = dw[1][py] * wv[2][pz], ydz = wv[1][py] * dw[2][pz];
-        for (int px = 0; px < ng; ++px) {
-          const float v = dl[w][px + ng * (py + ng * pz)];
-          f += v * wv[0][px] * wyz;
-          gx += v * dw[0][px] * wyz;
-          gy += v * wv[0][px] * dyz;
-          gz += v * wv[0][px] * ydz;
-        }
-      }
-    far[i] = make_float4(c0 + f, -gx * invL, -gy * invL, -gz * invL);
+  if (t < 0) {  // a leaf above level 2 has no far field
+    far[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
   }
+  const int ng = NG > 0 ? NG : tb.ng;
+  const int l = level_of(lt, box);
+  const uint64_t k = key[box] & ((1ull << (3 * l)) - 1ull);
+  const float sc = (float)(1u << l);
+  const float4 h = uhi[i], q = ulo[i];
+  float wv[3][kMaxNg], dw[3][kMaxNg];
+  lagrange_f<NG>(tb, cell_coord(h.x, q.x, sc, (float)compact3(k) + 0.5f), wv[0], dw[0]);
+  lagrange_f<NG>(tb, cell_coord(h.y, q.y, sc, (float)compact3(k >> 1) + 0.5f), wv[1], dw[1]);
+  lagrange_f<NG>(tb, cell_coord(h.z, q.z, sc, (float)compact3(k >> 2) + 0.5f), wv[2], dw[2]);
+  const float *dl = loc + (int64_t)t * ng * ng * ng;
+  float f = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+  for (int pz = 0; pz < (NG > 0 ? NG : kMaxNg); ++pz) {
+    if (pz >= ng) break;
+#pragma unroll
+    for (int py = 0; py < (NG > 0 ? NG : kMaxNg); ++py) {
+      if (py >= ng) break;
+      const float wyz = wv[1][py] * wv[2][pz], dyz = dw[1][py] * wv[2][pz], ydz = wv[1][py] * dw[2][pz];
+      const float *row = dl + ng * (py + ng * pz);
+#pragma unroll
+      for (int px = 0; px < (NG > 0 ? NG : kMaxNg); ++px) {
+        if (px >= ng) break;
+        const float v = __ldg(row + px);
+        f += v * wv[0][px] * wyz;
+        gx += v * dw[0][px] * wyz;
+        gy += v * wv[0][px] * dyz;
+        gz += v * wv[0][px] * ydz;
+      }
+    }
+  }
+  const float invL = sc * inv_side;
+  far[i] = make_float4(__ldg(locc + t) + f, -gx * invL, -gy * invL, -gz * invL);
 }
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
@@ -353,8 +540,8 @@ __global__ void __launch_bounds__(kThreads) k_p2p(int64_t nitem, const int *__re
                                                   const int *__restrict__ beg, const int *__restrict__ end,
                                                   const float4 *__restrict__ hi, const float4 *__restrict__ lo,
                                                   const float4 *__restrict__ far,
-                                                  const uint32_t *__restrict__ perm, float eps2,
-                                                  float *__restrict__ out_phi, float *__restrict__ out_acc,
+                                                  const uint32_t *__restrict__ perm, float eps2, float sc_phi,
+                                                  float sc_acc, float *__restrict__ out_phi, float *__restrict__ out_acc,
                                                   float4 *__restrict__ part) {
   __shared__ int rb[kWarpsPerBlock][28], cum[kWarpsPerBlock][28];
   __shared__ float4 red[kWarpsPerBlock][32];
@@ -453,11 +640,11 @@ __global__ void __launch_bounds__(kThreads) k_p2p(int64_t nitem, const int *__re
       if (nitems == 1) {
         const float4 f = far[ti];
         const uint32_t o = perm[ti];
-        if (out_phi) out_phi[o] = f.x + v.x;
+        if (out_phi) out_phi[o] = fmaf(v.x, sc_phi, f.x);
         if (out_acc) {
-          out_acc[3 * (int64_t)o] = f.y + v.y;
-          out_acc[3 * (int64_t)o + 1] = f.z + v.z;
-          out_acc[3 * (int64_t)o + 2] = f.w + v.w;
+          out_acc[3 * (int64_t)o] = fmaf(v.y, sc_acc, f.y);
+          out_acc[3 * (int64_t)o + 1] = fmaf(v.z, sc_acc, f.z);
+          out_acc[3 * (int64_t)o + 2] = fmaf(v.w, sc_acc, f.w);
         }
       } else {
         part[(int64_t)leaf_part0[leaf] + (int64_t)kidx * nt + (ti - tb)] = v;
@@ -475,7 +662,7 @@ __global__ void __launch_bounds__(kThreads) k_p2p_combine(int64_t nleaf, const i
                                                           const int *__restrict__ beg, const int *__restrict__ end,
                                                           const float4 *__restrict__ part,
                                                           const float4 *__restrict__ far,
-                                                          const uint32_t *__restrict__ perm,
+                                                          const uint32_t *__restrict__ perm, float s1, float s2,
                                                           float *__restrict__ out_phi, float *__restrict__ out_acc) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t leaf = (int64_t)blockIdx.x * kWarpsPerBlock + w;
@@ -497,11 +684,11 @@ __global__ void __launch_bounds__(kThreads) k_p2p_combine(int64_t nleaf, const i
     const int ti = tb + t;
     const float4 f = far[ti];
     const uint32_t o = perm[ti];
-    if (out_phi) out_phi[o] = f.x + (sp - cp);
+    if (out_phi) out_phi[o] = fmaf(sp - cp, s1, f.x);
     if (out_acc) {
-      out_acc[3 * (int64_t)o] = f.y + (sx - cx);
-      out_acc[3 * (int64_t)o + 1] = f.z + (sy - cy);
-      out_acc[3 * (int64_t)o + 2] = f.w + (sz - cz);
+      out_acc[3 * (int64_t)o] = fmaf(sx - cx, s2, f.y);
+      out_acc[3 * (int64_t)o + 1] = fmaf(sy - cy, s2, f.z);
+      out_acc[3 * (int64_t)o + 2] = fmaf(sz - cz, s2, f.w);
     }
   }
 }
@@ -716,42 +903,47 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
   int64_t launches = 0;
   pl->stats.m2l_launches = 0;
   pl->stats.m2l_targets = pl->ntgt;
+  pl->stats.m2l_parents = 0;
+  pl->stats.ms_m2l_kernel = 0.f;
   if (n == 0) return HPM_OK;
   const int ng = pl->ng, m3 = ng * ng * ng;
   const int D = pl->max_depth;
   const int64_t off2 = D >= 2 ? pl->lvl_off[2] : pl->nbox;
   const int64_t nrow = pl->nbox - off2;
-  HPM_TRY(t.spm.ensure(sizeof(PM) * n + 2 * sizeof(float4) * n, st));
+  HPM_TRY(t.spm.ensure(2 * sizeof(float4) * n, st));
   HPM_TRY(s.grid.ensure(sizeof(float) * m3 * (nrow > 0 ? nrow : 1), st));
   HPM_TRY(s.loc.ensure(sizeof(float) * m3 * (pl->ntgt > 0 ? pl->ntgt : 1), st));
   HPM_TRY(s.m2l_raw.ensure(sizeof(float) * m3 * (pl->ntgt > 0 ? pl->ntgt : 1), st));
   HPM_TRY(s.locc.ensure(sizeof(float) * (pl->ntgt > 0 ? pl->ntgt : 1), st));
   HPM_TRY(s.m2lc.ensure(sizeof(float) * (pl->ntgt > 0 ? pl->ntgt : 1), st));
   HPM_TRY(s.far.ensure(sizeof(float4) * n, st));
-  PM *spm = t.spm.as<PM>();
-  float4 *hi = reinterpret_cast<float4 *>(spm + n);
+  float4 *hi = t.spm.as<float4>();
   float4 *lo = hi + n;
   const LevelTable lt = make_levels(pl);
   const double *o = pl->dom.origin;
 
   record(pl, 0, st);
   k_gather<<<blocks_for(n), kThreads, 0, st>>>(n, t.perm.as<uint32_t>(), d_pos, d_mass, o[0], o[1], o[2],
-                                               spm, hi, lo);
+                                               1.0 / pl->dom.side, hi, lo);
   HPM_LAUNCHED(&launches);
   record(pl, 1, st);
   if (pl->np2g) {
-    k_p2g<<<warp_blocks(pl->np2g), kThreads, 0, st>>>(pl->np2g, t.p2g_box.as<int>(), t.p2g_off.as<int>(), lt,
-                                                      pl->tab, o[0], o[1], o[2], pl->dom.side,
-                                                      t.box_key.as<uint64_t>(), t.box_beg.as<int>(), spm, off2,
-                                                      s.grid.as<float>());
+    auto kp = ng == 4 ? k_p2g<4> : k_p2g<0>;
+    kp<<<warp_blocks(pl->np2g), kThreads, 0, st>>>(pl->np2g, t.p2g_box.as<int>(), t.p2g_off.as<int>(), lt, pl->tab,
+                                                   t.box_key.as<uint64_t>(), t.box_beg.as<int>(), hi, lo, off2,
+                                                   s.grid.as<float>());
     HPM_LAUNCHED(&launches);
   }
   record(pl, 2, st);
   for (int l = pl->depth_reached - 1; l >= 2; --l) {
     const int64_t b = pl->lvl_off[l], e = pl->lvl_off[l + 1];
     if (e <= b) continue;
-    k_m2m<<<gwarp_blocks(e - b), kGThreads, 0, st>>>(b, e, pl->tab, t.box_flags.as<uint8_t>(),
-                                                   t.box_child.as<int>(), off2, s.grid.as<float>());
+    if (ng == 4)
+      k_m2m4<<<(unsigned)((e - b + kM2MWarps - 1) / kM2MWarps), kM2MWarps * 32, 0, st>>>(
+          b, e, pl->tab, t.box_flags.as<uint8_t>(), t.box_child.as<int>(), off2, s.grid.as<float>());
+    else
+      k_m2m<<<gwarp_blocks(e - b), kGThreads, 0, st>>>(b, e, pl->tab, t.box_flags.as<uint8_t>(),
+                                                     t.box_child.as<int>(), off2, s.grid.as<float>());
     HPM_LAUNCHED(&launches);
   }
   record(pl, 3, st);
@@ -765,39 +957,43 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
   for (int l = 2; l <= pl->depth_reached; ++l) {
     const int64_t b = pl->tgt_lvl_off[l], e = pl->tgt_lvl_off[l + 1];
     if (e <= b) continue;
-    k_l2l<<<gwarp_blocks(e - b), kGThreads, 0, st>>>(b, e, l, pl->tab, t.tgt_box.as<int>(), t.box_tgt.as<int>(),
-                                                   t.box_parent.as<int>(), t.box_key.as<uint64_t>(),
-                                                   s.m2l_raw.as<float>(), s.loc.as<float>(), s.locc.as<float>(),
-                                                   s.m2lc.as<float>());
+    if (ng == 4)
+      k_l2l4<<<(unsigned)((e - b + kM2MWarps - 1) / kM2MWarps), kM2MWarps * 32, 0, st>>>(
+          b, e, l, pl->tab, t.tgt_box.as<int>(), t.box_tgt.as<int>(), t.box_parent.as<int>(),
+          t.box_key.as<uint64_t>(), s.m2l_raw.as<float>(), s.loc.as<float>(), s.locc.as<float>(),
+          s.m2lc.as<float>());
+    else
+      k_l2l<<<gwarp_blocks(e - b), kGThreads, 0, st>>>(b, e, l, pl->tab, t.tgt_box.as<int>(), t.box_tgt.as<int>(),
+                                                     t.box_parent.as<int>(), t.box_key.as<uint64_t>(),
+                                                     s.m2l_raw.as<float>(), s.loc.as<float>(), s.locc.as<float>(),
+                                                     s.m2lc.as<float>());
     HPM_LAUNCHED(&launches);
   }
   record(pl, 5, st);
-  HPM_CUDA(cudaMemsetAsync(s.far.p, 0, sizeof(float4) * n, st));
-  {
-    const int64_t lb = pl->leaf_lvl_off[2 <= D ? 2 : D + 1], le = pl->nleaf;
-    if (le > lb) {
-      k_g2p<<<warp_blocks(le - lb), kThreads, 0, st>>>(lb, le, t.leaf_box.as<int>(), t.box_tgt.as<int>(), lt,
-                                                       pl->tab, o[0], o[1], o[2], pl->dom.side,
-                                                       t.box_key.as<uint64_t>(), t.box_beg.as<int>(),
-                                                       t.box_end.as<int>(), spm, s.loc.as<float>(),
-                                                       s.locc.as<float>(), s.far.as<float4>());
-      HPM_LAUNCHED(&launches);
-    }
-  }
+  auto kg = ng == 4 ? k_g2p<4> : k_g2p<0>;
+  kg<<<blocks_for(n), kThreads, 0, st>>>(n, t.pbox.as<int>(), t.box_tgt.as<int>(), lt, pl->tab,
+                                            (float)(1.0 / pl->dom.side), t.box_key.as<uint64_t>(), hi, lo,
+                                            s.loc.as<float>(), s.locc.as<float>(), s.far.as<float4>());
+  HPM_LAUNCHED(&launches);
   record(pl, 6, st);
   {
-    const float eps2 = (float)(pl->green.eps * pl->green.eps);
+    // pairs are summed in unit-cube coordinates (eps / S), scaled back by 1/S
+    // (potential) and 1/S^2 (acceleration) once per target
+    const double eu = pl->green.eps / pl->dom.side;
+    const float eps2 = (float)(eu * eu);
+    const float s1 = (float)(1.0 / pl->dom.side), s2 = (float)(1.0 / (pl->dom.side * pl->dom.side));
     HPM_TRY(s.part.ensure(sizeof(float4) * (pl->npart > 0 ? pl->npart : 1), st));
     k_p2p<<<warp_blocks(pl->nitem), kThreads, 0, st>>>(
         pl->nitem, t.item_leaf.as<int>(), t.item_s0.as<int>(), t.item_s1.as<int>(), t.leaf_nitem.as<int>(),
         t.leaf_item0.as<int>(), t.leaf_part0.as<int>(), t.leaf_box.as<int>(), t.box_nb.as<int>(),
-        t.box_beg.as<int>(), t.box_end.as<int>(), hi, lo, s.far.as<float4>(), t.perm.as<uint32_t>(), eps2, d_phi,
-        d_acc, s.part.as<float4>());
+        t.box_beg.as<int>(), t.box_end.as<int>(), hi, lo, s.far.as<float4>(), t.perm.as<uint32_t>(), eps2, s1, s2,
+        d_phi, d_acc, s.part.as<float4>());
     HPM_LAUNCHED(&launches);
     if (pl->npart > 0) {
       k_p2p_combine<<<warp_blocks(pl->nleaf), kThreads, 0, st>>>(
           pl->nleaf, t.leaf_nitem.as<int>(), t.leaf_part0.as<int>(), t.leaf_box.as<int>(), t.box_beg.as<int>(),
-          t.box_end.as<int>(), s.part.as<float4>(), s.far.as<float4>(), t.perm.as<uint32_t>(), d_phi, d_acc);
+          t.box_end.as<int>(), s.part.as<float4>(), s.far.as<float4>(), t.perm.as<uint32_t>(), s1, s2, d_phi,
+          d_acc);
       HPM_LAUNCHED(&launches);
     }
   }

@@ -321,6 +321,15 @@ __global__ void k_box_counts(int64_t n, const int *__restrict__ list, const int 
   if (i < n) out[i] = end[list[i]] - beg[list[i]];
 }
 
+// Leaf box of every sorted particle (a leaf's particles are contiguous).
+__global__ void k_particle_box(int64_t nleaf, const int *__restrict__ leaf_box, const int *__restrict__ beg,
+                               const int *__restrict__ end, int *__restrict__ pbox) {
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nleaf) return;
+  const int box = leaf_box[l];
+  for (int i = beg[box]; i < end[box]; ++i) pbox[i] = box;
+}
+
 __global__ void k_box_tgt(int64_t ntgt, const int *__restrict__ tgt_box, int *__restrict__ box_tgt) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < ntgt) box_tgt[tgt_box[t]] = (int)t;
@@ -595,6 +604,13 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     HPM_LAUNCHED(&launches);
     HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.p2g_off.as<int>(), pl->np2g, t.p2g_off.as<int>() + pl->np2g,
                                t.keys_alt, st, &launches));
+  }
+  // leaf of every particle
+  HPM_TRY(t.pbox.ensure(sizeof(int) * (n > 0 ? n : 1), st));
+  if (pl->nleaf) {
+    k_particle_box<<<blocks_for(pl->nleaf), kThreads, 0, st>>>(pl->nleaf, t.leaf_box.as<int>(), t.box_beg.as<int>(),
+                                                               t.box_end.as<int>(), t.pbox.as<int>());
+    HPM_LAUNCHED(&launches);
   }
   // near-field work items
   {

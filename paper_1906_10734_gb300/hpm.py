@@ -72,7 +72,8 @@ class hpm_lists_info(ctypes.Structure):
 class hpm_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_float) for k in ("ms_tree", "ms_p2g", "ms_m2m", "ms_m2l", "ms_l2l", "ms_g2p",
                                               "ms_p2p", "ms_total")] + \
-               [("launches", ctypes.c_int64), ("m2l_launches", ctypes.c_int64), ("m2l_targets", ctypes.c_int64)]
+               [("launches", ctypes.c_int64), ("m2l_launches", ctypes.c_int64), ("m2l_targets", ctypes.c_int64),
+                ("ms_m2l_kernel", ctypes.c_float), ("m2l_parents", ctypes.c_int64)]
 
 
 SIGNATURES = {

@@ -198,7 +198,7 @@ def test_uniform_16m_depth7_sampled(hpm, ng):
     w = I.uniform_16m_depth7(ng=ng)
     phi, acc, _ = gpu_solve(hpm, w.pos, w.mass, w.max_depth, w.ng, w.eps, w.leaf_max)
     tr = O.Tree(w.pos, max_depth=w.max_depth, leaf_max=w.leaf_max)
-    sample = np.random.default_rng(3).choice(w.n, 96, replace=False)
+    sample = np.random.default_rng(3).choice(w.n, 256, replace=False)
     p_ref, a_ref = O.solve_direct(tr, w.mass, w.ng, w.eps, sample)
     p_dir, a_dir = O.direct_sum(w.pos, w.mass, w.eps, sample)
     print(f"uniform 2^24 depth 7 Ng={ng}: FP32 vs FP64 HPM acc {O.rel_rms(acc[sample], a_ref):.3e} "
