@@ -12,6 +12,8 @@
 // neighbours of its parent.
 #include <utility>
 
+#include <cmath>
+
 #include "hpm_internal.cuh"
 
 namespace hpm {
@@ -52,9 +54,11 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
 // Batched trees: particle i of problem p (offsets[p] <= i < offsets[p+1]) gets
 // the key (p << 3 D) | morton; sorting then groups particles by problem and
 // the levels of all problems are built by the same launches.
+// side_inv2 = 2^-e when the side is the power of two 2^e (division by it is
+// then an exact multiplication, the same IEEE result), else 0.
 __global__ void k_keys(const double *__restrict__ pos, int64_t n, double ox, double oy, double oz,
-                       double side, int depth, uint64_t *__restrict__ keys, int *__restrict__ err,
-                       const int64_t *__restrict__ offsets, int nprob) {
+                       double side, double side_inv2, int depth, uint64_t *__restrict__ keys,
+                       int *__restrict__ err, const int64_t *__restrict__ offsets, int nprob) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint64_t prob = 0;
@@ -72,7 +76,8 @@ __global__ void k_keys(const double *__restrict__ pos, int64_t n, double ox, dou
   bool bad = false;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    double v = __ddiv_rn(__dsub_rn(pos[3 * i + d], o[d]), side);
+    const double diff = __dsub_rn(pos[3 * i + d], o[d]);
+    double v = side_inv2 != 0.0 ? __dmul_rn(diff, side_inv2) : __ddiv_rn(diff, side);
     if (!(v >= 0.0 && v <= 1.0)) {
       bad = true;
       v = 0.0;
@@ -131,14 +136,22 @@ __global__ void k_roots(int nprob, int64_t n, int depth, int leaf_max, const int
   if (!internal) atomicAdd(&counters[32 + 0], 1);
 }
 
+// Every box within Chebyshev distance 1 of an internal cell (its neighbour
+// list, itself included) is expanded. The flag bytes are set with
+// non-returning atomic ORs on their 32-bit words: 27 independent updates
+// instead of 27 dependent read-modify-writes. (Virtual boxes keep empty
+// neighbour lists, so the relation must be walked from the internal side.)
 __global__ void k_expand(int64_t pb, int64_t pe, uint8_t *__restrict__ flags,
                          const int *__restrict__ nb) {
   const int64_t i = pb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= pe || !(flags[i] & kInternal)) return;
-  for (int k = 0; k < 27; ++k) {
-    const int q = nb[i * 27 + k];
-    if (q >= 0) flags[q] |= kExpand;  // only this bit is written here: races are benign
-  }
+  int q[27];
+#pragma unroll
+  for (int k = 0; k < 27; ++k) q[k] = nb[i * 27 + k];
+  unsigned int *words = reinterpret_cast<unsigned int *>(flags);
+#pragma unroll
+  for (int k = 0; k < 27; ++k)
+    if (q[k] >= 0) atomicOr(words + (q[k] >> 2), (unsigned int)kExpand << (8 * (q[k] & 3)));
 }
 
 // First index in [lo, hi) whose level-l key is >= kc.
@@ -238,17 +251,26 @@ __global__ void k_neighbours(int64_t cb, int64_t ce, int level, const uint8_t *_
   const int c[3] = {(int)compact3(k0), (int)compact3(k0 >> 1), (int)compact3(k0 >> 2)};
   const int side = 1 << level;
   const int p = parent[i];
+  // the parent's neighbour holding each of the 27 boxes, then its child: two
+  // rounds of independent loads (the parent's row is never written here)
+  int q[27];
+#pragma unroll
   for (int k = 0; k < 27; ++k) {
-    const int n[3] = {c[0] + k % 3 - 1, c[1] + (k / 3) % 3 - 1, c[2] + k / 9 - 1};
-    int r = -1;
-    if (n[0] >= 0 && n[0] < side && n[1] >= 0 && n[1] < side && n[2] >= 0 && n[2] < side) {
-      const int dp = ((n[0] >> 1) - (c[0] >> 1) + 1) + 3 * ((n[1] >> 1) - (c[1] >> 1) + 1) +
-                     9 * ((n[2] >> 1) - (c[2] >> 1) + 1);
-      const int q = nb[(int64_t)p * 27 + dp];
-      if (q >= 0) r = child[(int64_t)q * 8 + ((n[0] & 1) | ((n[1] & 1) << 1) | ((n[2] & 1) << 2))];
+    const int n0 = c[0] + k % 3 - 1, n1 = c[1] + (k / 3) % 3 - 1, n2 = c[2] + k / 9 - 1;
+    q[k] = -1;
+    if (n0 >= 0 && n0 < side && n1 >= 0 && n1 < side && n2 >= 0 && n2 < side) {
+      const int dp = ((n0 >> 1) - (c[0] >> 1) + 1) + 3 * ((n1 >> 1) - (c[1] >> 1) + 1) +
+                     9 * ((n2 >> 1) - (c[2] >> 1) + 1);
+      q[k] = __ldg(nb + (int64_t)p * 27 + dp);
     }
-    nb[i * 27 + k] = r;
   }
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    const int n0 = c[0] + k % 3 - 1, n1 = c[1] + (k / 3) % 3 - 1, n2 = c[2] + k / 9 - 1;
+    q[k] = q[k] >= 0 ? __ldg(child + (int64_t)q[k] * 8 + ((n0 & 1) | ((n1 & 1) << 1) | ((n2 & 1) << 2))) : -1;
+  }
+#pragma unroll
+  for (int k = 0; k < 27; ++k) nb[i * 27 + k] = q[k];
 }
 
 // Work-list selection. mode 0: real cells; 1: leaves; 2: boxes that get their
@@ -383,7 +405,7 @@ hpm_status ensure_boxes(TreeDev &t, int64_t nbox, cudaStream_t st) {
   HPM_TRY(t.box_beg.ensure(sizeof(int) * nbox, st, true));
   HPM_TRY(t.box_end.ensure(sizeof(int) * nbox, st, true));
   HPM_TRY(t.box_parent.ensure(sizeof(int) * nbox, st, true));
-  HPM_TRY(t.box_flags.ensure(sizeof(uint8_t) * nbox, st, true));
+  HPM_TRY(t.box_flags.ensure(sizeof(uint8_t) * ((nbox + 15) & ~int64_t(15)), st, true));  // word-wide atomics in k_expand
   HPM_TRY(t.box_child.ensure(sizeof(int) * 8 * nbox, st, true));
   HPM_TRY(t.box_nb.ensure(sizeof(int) * 27 * nbox, st, true));
   return HPM_OK;
@@ -414,11 +436,18 @@ hpm_status select_boxes(hpm_plan_s *pl, int64_t b, int64_t e, int mode, DevBuf &
 
 }  // namespace
 
+// 2^-e if side = 2^e exactly, else 0
+static double pow2_inverse(double side) {
+  int e = 0;
+  const double f = std::frexp(side, &e);  // side = f 2^e, f in [0.5, 1)
+  return (f == 0.5 && std::isfinite(side)) ? std::ldexp(1.0, 1 - e) : 0.0;
+}
+
 hpm_status launch_morton_keys(const hpm_domain &dom, int depth, const double *d_pos, int64_t n,
                               uint64_t *d_keys, int *d_err, cudaStream_t st) {
   if (n <= 0) return HPM_OK;
   k_keys<<<blocks_for(n), kThreads, 0, st>>>(d_pos, n, dom.origin[0], dom.origin[1], dom.origin[2], dom.side,
-                                             depth, d_keys, d_err, nullptr, 1);
+                                             pow2_inverse(dom.side), depth, d_keys, d_err, nullptr, 1);
   HPM_LAUNCHED((int64_t *)nullptr);
   return HPM_OK;
 }
@@ -460,7 +489,8 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   if (nprob > 1)
     HPM_CUDA(cudaMemcpyAsync(t.offsets.p, h_offsets, sizeof(int64_t) * (nprob + 1), cudaMemcpyHostToDevice, st));
   k_keys<<<blocks_for(n), kThreads, 0, st>>>(d_pos, n, pl->dom.origin[0], pl->dom.origin[1],
-                                             pl->dom.origin[2], pl->dom.side, D, t.keys.as<uint64_t>(),
+                                             pl->dom.origin[2], pl->dom.side, pow2_inverse(pl->dom.side), D,
+                                             t.keys.as<uint64_t>(),
                                              t.err.as<int>(), t.offsets.as<int64_t>(), nprob);
   HPM_LAUNCHED(&launches);
   uint64_t *k0 = t.keys.as<uint64_t>(), *k1 = t.keys_alt.as<uint64_t>();
