@@ -408,8 +408,16 @@ __global__ void k_split(int64_t nrow, const float *__restrict__ grid, const uint
 
 // Per tile column (parent): the column scale exponent (the smallest row
 // exponent of its block, i.e. the scale of its largest |value|) and the total
-// mass of each child's interaction zone, summed in FP64. One warp per column,
-// the lanes splitting the 216 slots.
+// mass of each child's interaction zone (block total minus the child's 3^3
+// near slots). One warp per column, the lanes splitting the 216 slots with
+// compensated FP32 sums; the lane sums are reduced in FP64.
+__device__ __forceinline__ void kahan_add_f(float &s, float &c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 __global__ void k_col_exp(int64_t ntiles, const int *__restrict__ rows, const int *__restrict__ box_exp,
                           const float *__restrict__ box_mass, int *__restrict__ col_exp,
                           float *__restrict__ zone_mass) {
@@ -418,24 +426,34 @@ __global__ void k_col_exp(int64_t ntiles, const int *__restrict__ rows, const in
   if (i >= ntiles * kTileN) return;  // whole warps
   const int *rr = rows + (i / kTileN) * kSlots * kTileN + (i % kTileN);
   int e = kNoExp;
-  double zm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float ts = 0.f, tc = 0.f, ns[8], nc[8];
+#pragma unroll
+  for (int o = 0; o < 8; ++o) ns[o] = nc[o] = 0.f;
   for (int s = lane; s < kSlots; s += 32) {
     const int row = rr[(int64_t)s * kTileN];
     if (row < 0) continue;
     e = min(e, box_exp[row]);
-    const double bm = (double)box_mass[row];
+    const float m = box_mass[row];
+    kahan_add_f(ts, tc, m);
     const int sx = s % 6, sy = (s / 6) % 6, sz = s / 36;
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
       const int px = 2 + (o & 1), py = 2 + ((o >> 1) & 1), pz = 2 + (o >> 2);
-      if (max(abs(sx - px), max(abs(sy - py), abs(sz - pz))) >= 2) zm[o] += bm;
+      if (max(abs(sx - px), max(abs(sy - py), abs(sz - pz))) <= 1) kahan_add_f(ns[o], nc[o], m);
     }
   }
   e = __reduce_min_sync(0xffffffffu, e);
+  double tot = (double)ts - (double)tc;
 #pragma unroll
-  for (int o = 0; o < 8; ++o)
+  for (int off = 16; off > 0; off >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, off);
+  double zm[8];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) zm[o] += __shfl_xor_sync(0xffffffffu, zm[o], off);
+  for (int o = 0; o < 8; ++o) {
+    double v = (double)ns[o] - (double)nc[o];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    zm[o] = tot - v;
+  }
   if (lane == 0) {
     col_exp[i] = e == kNoExp ? 0 : e;
 #pragma unroll

@@ -503,17 +503,19 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 }
 
 // One source's contribution to a target, accumulated into a short plain-FP32
-// block sum; positions are hi/lo pairs relative to the domain origin, so the
-// coordinate difference keeps FP32 precision relative to itself.
-__device__ __forceinline__ void pair_add(const float4 &mh, const float4 &ml, const float4 &h, const float4 &q,
-                                         bool self, float eps2, float &bp, float &bx, float &by, float &bz) {
-  const float dx = (h.x - mh.x) + (q.x - ml.x);
-  const float dy = (h.y - mh.y) + (q.y - ml.y);
-  const float dz = (h.z - mh.z) + (q.z - ml.z);
+// block sum. Positions are (hi, lo) float pairs: hi relative to the target
+// leaf's centre, lo the residual of the unit-cube coordinate; (s.hi - t.hi) is
+// exact for nearby particles, so the difference keeps FP32 precision relative
+// to the pair distance however small it is. lo.w holds the particle index.
+__device__ __forceinline__ void pair_rel(const float4 &th, const float4 &tl, const float4 &sh, const float4 &sl,
+                                         float eps2, float &bp, float &bx, float &by, float &bz) {
+  const float dx = (sh.x - th.x) + (sl.x - tl.x), dy = (sh.y - th.y) + (sl.y - tl.y),
+              dz = (sh.z - th.z) + (sl.z - tl.z);
+  const bool self = __float_as_int(sl.w) == __float_as_int(tl.w);
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
   float ir = rsqrtf(r2);
   if (self) ir = 0.f;
-  const float mir = h.w * ir;
+  const float mir = sh.w * ir;
   const float mir3 = mir * ir * ir;
   bp -= mir;
   bx = fmaf(mir3, dx, bx);
@@ -524,14 +526,15 @@ __device__ __forceinline__ void pair_add(const float4 &mh, const float4 &ml, con
 // Near zone by direct summation (Sec. 1, item 1), one warp per work item: an
 // item is a leaf's targets against a contiguous part of the concatenation of
 // its near boxes' particles. The item's sources are staged in shared memory in
-// chunks (position hi/lo and index), so the pair loop is one flat loop;
-// floor(32 / nt) lanes share a target and split the chunk; blocks of four pairs
-// are summed in plain FP32 and the block sums are Kahan compensated. A leaf with
-// one item writes far + near to the caller's order; a leaf split over several
-// items writes partial sums for k_p2p_combine.
+// chunks (position hi relative to the target leaf's centre, lo, mass, index), so
+// the pair loop is one flat loop; floor(32 / nt) lanes share a target and split
+// the chunk; blocks of eight pairs are summed in plain FP32 and the block sums
+// are Kahan compensated. A leaf with one item writes far + near to the
+// caller's order; a leaf split over several items writes partial sums for
+// k_p2p_combine.
 constexpr int kP2PChunk = 128;
 
-__global__ void __launch_bounds__(kThreads) k_p2p(int64_t nitem, const int *__restrict__ item_leaf,
+__global__ void __launch_bounds__(kThreads, 3) k_p2p(int64_t nitem, const int *__restrict__ item_leaf,
                                                   const int *__restrict__ item_s0, const int *__restrict__ item_s1,
                                                   const int *__restrict__ leaf_nitem,
                                                   const int *__restrict__ leaf_item0,
@@ -540,13 +543,13 @@ __global__ void __launch_bounds__(kThreads) k_p2p(int64_t nitem, const int *__re
                                                   const int *__restrict__ beg, const int *__restrict__ end,
                                                   const float4 *__restrict__ hi, const float4 *__restrict__ lo,
                                                   const float4 *__restrict__ far,
-                                                  const uint32_t *__restrict__ perm, float eps2, float sc_phi,
+                                                  const uint32_t *__restrict__ perm, const uint64_t *__restrict__ key,
+                                                  LevelTable lt, float eps2, float sc_phi,
                                                   float sc_acc, float *__restrict__ out_phi, float *__restrict__ out_acc,
                                                   float4 *__restrict__ part) {
   __shared__ int rb[kWarpsPerBlock][28], cum[kWarpsPerBlock][28];
   __shared__ float4 red[kWarpsPerBlock][32];
-  __shared__ float4 shi[kWarpsPerBlock][kP2PChunk], slo[kWarpsPerBlock][kP2PChunk];
-  __shared__ int sidx[kWarpsPerBlock][kP2PChunk];
+  __shared__ float4 srh[kWarpsPerBlock][kP2PChunk], srl[kWarpsPerBlock][kP2PChunk];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t it = (int64_t)blockIdx.x * kWarpsPerBlock + w;
   if (it >= nitem) return;
@@ -575,6 +578,16 @@ __global__ void __launch_bounds__(kThreads) k_p2p(int64_t nitem, const int *__re
   __syncwarp();
   const int s0 = item_s0[it], s1 = item_s1[it];
   const int tb = beg[box], te = end[box], nt = te - tb;
+  // the target leaf's centre in unit-cube coordinates (exact in FP32)
+  float cx0, cy0, cz0;
+  {
+    const int l = level_of(lt, box);
+    const uint64_t kk = key[box] & ((1ull << (3 * l)) - 1ull);
+    const float inv = 1.f / (float)(1u << l);
+    cx0 = ((float)compact3(kk) + 0.5f) * inv;
+    cy0 = ((float)compact3(kk >> 1) + 0.5f) * inv;
+    cz0 = ((float)compact3(kk >> 2) + 0.5f) * inv;
+  }
   const int G = nt >= 32 ? 1 : 32 / nt;
   const int per = 32 / G;
   const int nitems = leaf_nitem[leaf];
@@ -583,10 +596,11 @@ __global__ void __launch_bounds__(kThreads) k_p2p(int64_t nitem, const int *__re
     const int slot = lane / G, sub = lane % G;
     const int ti = t0 + slot;
     const bool active = slot < per && ti < te;
-    float4 mh = make_float4(0.f, 0.f, 0.f, 0.f), ml = mh;
+    float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
     if (active) {
-      mh = hi[ti];
-      ml = lo[ti];
+      const float4 h = hi[ti], q = lo[ti];
+      th = make_float4(h.x - cx0, h.y - cy0, h.z - cz0, 0.f);
+      tl = make_float4(q.x, q.y, q.z, __int_as_float(ti));
     }
     float sp = 0.f, cp = 0.f, sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
     for (int c0 = s0; c0 < s1; c0 += kP2PChunk) {
@@ -599,19 +613,19 @@ __global__ void __launch_bounds__(kThreads) k_p2p(int64_t nitem, const int *__re
         for (int step = 16; step >= 1; step >>= 1)
           if (r + step < 28 && cum[w][r + step] <= q) r += step;
         const int j = rb[w][r] + (q - cum[w][r]);
-        shi[w][k] = hi[j];
-        slo[w][k] = lo[j];
-        sidx[w][k] = j;
+        const float4 h = hi[j], o = lo[j];
+        srh[w][k] = make_float4(h.x - cx0, h.y - cy0, h.z - cz0, h.w);
+        srl[w][k] = make_float4(o.x, o.y, o.z, __int_as_float(j));
       }
       __syncwarp();
       if (active) {
         int k = sub;
-        for (; k + 3 * G < cn; k += 4 * G) {
+        for (; k + 7 * G < cn; k += 8 * G) {
           float bp = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < 8; ++u) {
             const int kk = k + u * G;
-            pair_add(mh, ml, shi[w][kk], slo[w][kk], sidx[w][kk] == ti, eps2, bp, bx, by, bz);
+            pair_rel(th, tl, srh[w][kk], srl[w][kk], eps2, bp, bx, by, bz);
           }
           kahan_add(sp, cp, bp);
           kahan_add(sx, cx, bx);
@@ -619,7 +633,7 @@ __global__ void __launch_bounds__(kThreads) k_p2p(int64_t nitem, const int *__re
           kahan_add(sz, cz, bz);
         }
         float bp = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
-        for (; k < cn; k += G) pair_add(mh, ml, shi[w][k], slo[w][k], sidx[w][k] == ti, eps2, bp, bx, by, bz);
+        for (; k < cn; k += G) pair_rel(th, tl, srh[w][k], srl[w][k], eps2, bp, bx, by, bz);
         kahan_add(sp, cp, bp);
         kahan_add(sx, cx, bx);
         kahan_add(sy, cy, by);
@@ -986,8 +1000,8 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
     k_p2p<<<warp_blocks(pl->nitem), kThreads, 0, st>>>(
         pl->nitem, t.item_leaf.as<int>(), t.item_s0.as<int>(), t.item_s1.as<int>(), t.leaf_nitem.as<int>(),
         t.leaf_item0.as<int>(), t.leaf_part0.as<int>(), t.leaf_box.as<int>(), t.box_nb.as<int>(),
-        t.box_beg.as<int>(), t.box_end.as<int>(), hi, lo, s.far.as<float4>(), t.perm.as<uint32_t>(), eps2, s1, s2,
-        d_phi, d_acc, s.part.as<float4>());
+        t.box_beg.as<int>(), t.box_end.as<int>(), hi, lo, s.far.as<float4>(), t.perm.as<uint32_t>(),
+        t.box_key.as<uint64_t>(), lt, eps2, s1, s2, d_phi, d_acc, s.part.as<float4>());
     HPM_LAUNCHED(&launches);
     if (pl->npart > 0) {
       k_p2p_combine<<<warp_blocks(pl->nleaf), kThreads, 0, st>>>(
