@@ -410,12 +410,31 @@ __global__ void k_split(int64_t nrow, const float *__restrict__ grid, const uint
 // exponent of its block, i.e. the scale of its largest |value|) and the total
 // mass of each child's interaction zone (block total minus the child's 3^3
 // near slots). One warp per column, the lanes splitting the 216 slots with
-// compensated FP32 sums; the lane sums are reduced in FP64.
+// compensated FP32 sums (s, c); the lane pairs are combined with error-free
+// TwoSum steps, so no FP64 instruction is needed (each would hold the FP64
+// pipe for a whole warp).
 __device__ __forceinline__ void kahan_add_f(float &s, float &c, float x) {
   const float y = x - c;
   const float t = s + y;
   c = (t - s) - y;
   s = t;
+}
+
+// (s, e) += (s2, e2) where s + e is the value held and e is small
+__device__ __forceinline__ void twosum_add(float &s, float &e, float s2, float e2) {
+  const float t = s + s2;
+  const float bp = t - s;
+  const float err = (s - (t - bp)) + (s2 - bp);
+  s = t;
+  e = e + e2 + err;
+}
+
+__device__ __forceinline__ void warp_sum_pair(float &s, float &e) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, off), e2 = __shfl_xor_sync(0xffffffffu, e, off);
+    twosum_add(s, e, s2, e2);
+  }
 }
 
 __global__ void k_col_exp(int64_t ntiles, const int *__restrict__ rows, const int *__restrict__ box_exp,
@@ -443,21 +462,18 @@ __global__ void k_col_exp(int64_t ntiles, const int *__restrict__ rows, const in
     }
   }
   e = __reduce_min_sync(0xffffffffu, e);
-  double tot = (double)ts - (double)tc;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, off);
-  double zm[8];
+  // Kahan's (s, c) holds s - c
+  tc = -tc;
+  warp_sum_pair(ts, tc);
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
-    double v = (double)ns[o] - (double)nc[o];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    zm[o] = tot - v;
+    nc[o] = -nc[o];
+    warp_sum_pair(ns[o], nc[o]);
   }
   if (lane == 0) {
     col_exp[i] = e == kNoExp ? 0 : e;
 #pragma unroll
-    for (int o = 0; o < 8; ++o) zone_mass[i * 8 + o] = (float)zm[o];
+    for (int o = 0; o < 8; ++o) zone_mass[i * 8 + o] = (ts - ns[o]) + (tc - nc[o]);
   }
 }
 
