@@ -12,6 +12,7 @@
 // neighbours of its parent.
 #include <utility>
 
+#include <algorithm>
 #include <cmath>
 
 #include "hpm_internal.cuh"
@@ -141,17 +142,24 @@ __global__ void k_roots(int nprob, int64_t n, int depth, int leaf_max, const int
 // non-returning atomic ORs on their 32-bit words: 27 independent updates
 // instead of 27 dependent read-modify-writes. (Virtual boxes keep empty
 // neighbour lists, so the relation must be walked from the internal side.)
-__global__ void k_expand(int64_t pb, int64_t pe, uint8_t *__restrict__ flags,
+// The level kernels below read the box ranges of the levels from the device
+// (lvl[l] = first box of level l) and loop over them with a fixed grid, so the
+// host enqueues the whole build without waiting for any count.
+#define HPM_GRID_STRIDE(i, b, e) \
+  for (int64_t i = (b) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (e); i += (int64_t)gridDim.x * blockDim.x)
+
+__global__ void k_expand(const int64_t *__restrict__ lvl, int l, uint8_t *__restrict__ flags,
                          const int *__restrict__ nb) {
-  const int64_t i = pb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= pe || !(flags[i] & kInternal)) return;
-  int q[27];
-#pragma unroll
-  for (int k = 0; k < 27; ++k) q[k] = nb[i * 27 + k];
   unsigned int *words = reinterpret_cast<unsigned int *>(flags);
+  HPM_GRID_STRIDE(i, lvl[l - 1], lvl[l]) {
+    if (!(flags[i] & kInternal)) continue;
+    int q[27];
 #pragma unroll
-  for (int k = 0; k < 27; ++k)
-    if (q[k] >= 0) atomicOr(words + (q[k] >> 2), (unsigned int)kExpand << (8 * (q[k] & 3)));
+    for (int k = 0; k < 27; ++k) q[k] = nb[i * 27 + k];
+#pragma unroll
+    for (int k = 0; k < 27; ++k)
+      if (q[k] >= 0) atomicOr(words + (q[k] >> 2), (unsigned int)kExpand << (8 * (q[k] & 3)));
+  }
 }
 
 // First index in [lo, hi) whose level-l key is >= kc.
@@ -168,46 +176,79 @@ __device__ __forceinline__ int lower_bound_key(const uint64_t *__restrict__ skey
 
 // Child boundaries of every expanded box, one thread per (box, octant): the
 // seven searches of a box run in parallel instead of one after another.
-__global__ void k_octant_bounds(int64_t pb, int64_t pe, const uint8_t *__restrict__ flags,
+__global__ void k_octant_bounds(const int64_t *__restrict__ lvl, int l, const uint8_t *__restrict__ flags,
                                 const uint64_t *__restrict__ key, const int *__restrict__ beg,
                                 const int *__restrict__ end, const uint64_t *__restrict__ skeys, int shift,
                                 int *__restrict__ bnd) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = pb + t / 8;
-  const int o = (int)(t % 8);
-  if (i >= pe) return;
-  int v = beg[i];
-  if (o > 0 && (flags[i] & kExpand)) v = lower_bound_key(skeys, beg[i], end[i], shift, (key[i] << 3) | (uint64_t)o);
-  bnd[t] = v;
+  const int64_t pb = lvl[l - 1], pe = lvl[l];
+  HPM_GRID_STRIDE(t, 0, 8 * (pe - pb)) {
+    const int64_t i = pb + t / 8;
+    const int o = (int)(t % 8);
+    int v = beg[i];
+    if (o > 0 && (flags[i] & kExpand))
+      v = lower_bound_key(skeys, beg[i], end[i], shift, (key[i] << 3) | (uint64_t)o);
+    bnd[t] = v;
+  }
 }
 
-__global__ void k_count_children(int64_t pb, int64_t pe, const uint8_t *__restrict__ flags,
+__global__ void k_count_children(const int64_t *__restrict__ lvl, int l, const uint8_t *__restrict__ flags,
                                  const int *__restrict__ end, const int *__restrict__ bnd,
                                  int *__restrict__ cnt) {
-  const int64_t i = pb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= pe) return;
-  int c = 0;
-  if (flags[i] & kExpand) {
-    const int *b = bnd + (i - pb) * 8;
+  const int64_t pb = lvl[l - 1];
+  HPM_GRID_STRIDE(i, pb, lvl[l]) {
+    int c = 0;
+    if (flags[i] & kExpand) {
+      const int *b = bnd + (i - pb) * 8;
 #pragma unroll
-    for (int o = 0; o < 8; ++o) c += (o < 7 ? b[o + 1] : end[i]) > b[o];
+      for (int o = 0; o < 8; ++o) c += (o < 7 ? b[o + 1] : end[i]) > b[o];
+    }
+    cnt[i - pb] = c;
   }
-  cnt[i - pb] = c;
 }
 
-__global__ void k_fill_children(int64_t pb, int64_t pe, int64_t cb, int level, int depth,
+// Closes level l: its children are the next `*total` boxes. Past the box
+// capacity the children are dropped and kErrCapacity is set (the host then
+// rebuilds with more room).
+__global__ void k_level_close(int64_t *__restrict__ lvl, int l, const int *__restrict__ total, int64_t cap,
+                              int *__restrict__ err) {
+  const int64_t need = lvl[l] + *total;
+  if (need > cap) {
+    atomicOr(err, kErrCapacity);
+    lvl[l + 1] = lvl[l];
+  } else {
+    lvl[l + 1] = need;
+  }
+}
+
+__device__ void fill_children_of(int64_t q, int64_t pb, int64_t cb, int level, int depth, int leaf_max,
+                                 uint8_t *__restrict__ flags, uint64_t *__restrict__ key, int *__restrict__ beg,
+                                 int *__restrict__ end, int *__restrict__ parent, int *__restrict__ child,
+                                 const int *__restrict__ bnds, const int *__restrict__ off,
+                                 int *__restrict__ counters);
+
+__global__ void k_fill_children(const int64_t *__restrict__ lvl, int level, int depth,
                                 int leaf_max, uint8_t *__restrict__ flags, uint64_t *__restrict__ key,
                                 int *__restrict__ beg, int *__restrict__ end,
                                 int *__restrict__ parent, int *__restrict__ child,
                                 const int *__restrict__ bnds, const int *__restrict__ off,
-                                int *__restrict__ counters) {
-  const int64_t q = pb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= pe) return;
-  if (!(flags[q] & kExpand)) {
+                                int *__restrict__ counters, const int *__restrict__ err) {
+  const int64_t pb = lvl[level - 1], pe = lvl[level], cb = pe;
+  const bool dropped = (*err & kErrCapacity) != 0;
+  HPM_GRID_STRIDE(q, pb, pe) {
+    if (dropped || !(flags[q] & kExpand)) {
 #pragma unroll
-    for (int o = 0; o < 8; ++o) child[q * 8 + o] = -1;
-    return;
+      for (int o = 0; o < 8; ++o) child[q * 8 + o] = -1;
+      continue;
+    }
+    fill_children_of(q, pb, cb, level, depth, leaf_max, flags, key, beg, end, parent, child, bnds, off, counters);
   }
+}
+
+__device__ void fill_children_of(int64_t q, int64_t pb, int64_t cb, int level, int depth, int leaf_max,
+                                 uint8_t *__restrict__ flags, uint64_t *__restrict__ key, int *__restrict__ beg,
+                                 int *__restrict__ end, int *__restrict__ parent, int *__restrict__ child,
+                                 const int *__restrict__ bnds, const int *__restrict__ off,
+                                 int *__restrict__ counters) {
   int bnd[9];
   const uint64_t kq = key[q];
 #pragma unroll
@@ -238,15 +279,23 @@ __global__ void k_fill_children(int64_t pb, int64_t pe, int64_t cb, int level, i
   if (nleaf) atomicAdd(&counters[32 + level], nleaf);
 }
 
-__global__ void k_neighbours(int64_t cb, int64_t ce, int level, const uint8_t *__restrict__ flags,
+__device__ void neighbours_of(int64_t i, int level, const uint64_t *__restrict__ key,
+                              const int *__restrict__ parent, const int *__restrict__ child, int *__restrict__ nb);
+
+__global__ void k_neighbours(const int64_t *__restrict__ lvl, int level, const uint8_t *__restrict__ flags,
                              const uint64_t *__restrict__ key, const int *__restrict__ parent,
                              const int *__restrict__ child, int *__restrict__ nb) {
-  const int64_t i = cb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ce) return;
-  if (!(flags[i] & kReal)) {
-    for (int k = 0; k < 27; ++k) nb[i * 27 + k] = -1;
-    return;
+  HPM_GRID_STRIDE(i, lvl[level], lvl[level + 1]) {
+    if (!(flags[i] & kReal)) {
+      for (int k = 0; k < 27; ++k) nb[i * 27 + k] = -1;
+      continue;
+    }
+    neighbours_of(i, level, key, parent, child, nb);
   }
+}
+
+__device__ void neighbours_of(int64_t i, int level, const uint64_t *__restrict__ key,
+                              const int *__restrict__ parent, const int *__restrict__ child, int *__restrict__ nb) {
   const uint64_t k0 = key[i] & ((1ull << (3 * level)) - 1ull);
   const int c[3] = {(int)compact3(k0), (int)compact3(k0 >> 1), (int)compact3(k0 >> 2)};
   const int side = 1 << level;
@@ -412,23 +461,26 @@ hpm_status ensure_boxes(TreeDev &t, int64_t nbox, cudaStream_t st) {
 }
 
 // Compacts the boxes in [b, e) selected by `mode` into out (resized); returns the count.
-hpm_status select_boxes(hpm_plan_s *pl, int64_t b, int64_t e, int mode, DevBuf &out, int64_t *count,
+// Boxes of [b, e) passing `mode`, compacted into `out` in order. Their number
+// is known on the host from the per-level counts, so nothing is read back: the
+// device total goes to counters[total_slot] for the consistency check of the
+// build, and `out` is sized for the whole range (the compaction never writes
+// past e - b).
+hpm_status select_boxes(hpm_plan_s *pl, int64_t b, int64_t e, int mode, DevBuf &out, int total_slot,
                         cudaStream_t st, int64_t *launches) {
   TreeDev &t = pl->t;
   const int64_t n = e - b;
-  *count = 0;
-  if (n <= 0) return HPM_OK;
+  HPM_TRY(out.ensure(sizeof(int) * (n > 0 ? n : 1), st));
+  if (n <= 0) {
+    HPM_CUDA(cudaMemsetAsync(t.counters.as<int>() + total_slot, 0, sizeof(int), st));
+    return HPM_OK;
+  }
   HPM_TRY(t.cnt.ensure(sizeof(int) * n, st));
   HPM_TRY(t.off.ensure(sizeof(int) * (n + 1), st));
   k_select<<<blocks_for(n), kThreads, 0, st>>>(b, e, t.box_flags.as<uint8_t>(), mode, t.cnt.as<int>());
   HPM_LAUNCHED(launches);
-  HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), n, t.counters.as<int>() + 64, t.keys_alt,
+  HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), n, t.counters.as<int>() + total_slot, t.keys_alt,
                              st, launches));
-  int h = 0;
-  HPM_CUDA(cudaMemcpyAsync(&h, t.counters.as<int>() + 64, sizeof(int), cudaMemcpyDeviceToHost, st));
-  HPM_CUDA(cudaStreamSynchronize(st));
-  *count = h;
-  HPM_TRY(out.ensure(sizeof(int) * (h > 0 ? h : 1), st));
   k_compact<<<blocks_for(n), kThreads, 0, st>>>(b, e, t.cnt.as<int>(), t.off.as<int>(), out.as<int>());
   HPM_LAUNCHED(launches);
   return HPM_OK;
@@ -520,8 +572,10 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   int nroot = 0;
   HPM_CUDA(cudaMemcpyAsync(&nroot, t.counters.as<int>() + 64, sizeof(int), cudaMemcpyDeviceToHost, st));
   HPM_CUDA(cudaStreamSynchronize(st));
+  // Box capacity: grow-only across builds; the first build guesses n / 4 + 1024
+  // (trees here hold 0.14-0.19 n boxes) and retries with more if it overflows.
   int64_t cap = t.box_key.cap / sizeof(uint64_t);
-  if (cap < 1024 + 2 * (int64_t)nroot) cap = 1024 + 2 * (int64_t)nroot;
+  cap = std::max<int64_t>(cap, std::max<int64_t>(1024 + 2 * (int64_t)nroot, n / 4 + 1024));
   HPM_TRY(ensure_boxes(t, cap, st));
   k_roots<<<blocks_for(nprob), kThreads, 0, st>>>(nprob, n, D, pl->opts.leaf_max, t.bnd.as<int>(), t.cnt.as<int>(),
                                                   t.off.as<int>(), t.box_key.as<uint64_t>(), t.box_beg.as<int>(),
@@ -529,74 +583,72 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
                                                   t.box_flags.as<uint8_t>(), t.box_child.as<int>(),
                                                   t.box_nb.as<int>(), t.counters.as<int>());
   HPM_LAUNCHED(&launches);
-  pl->lvl_off[0] = 0;
-  pl->lvl_off[1] = nroot;
   pl->nprob = nprob;
-  int reached = 0;
-  for (int l = 1; l <= D; ++l) {
-    const int64_t pb = pl->lvl_off[l - 1], pe = pl->lvl_off[l];
-    const int64_t np = pe - pb;
-    const int shift = 3 * (D - l);
-    k_expand<<<blocks_for(np), kThreads, 0, st>>>(pb, pe, t.box_flags.as<uint8_t>(), t.box_nb.as<int>());
-    HPM_LAUNCHED(&launches);
-    HPM_TRY(t.cnt.ensure(sizeof(int) * np, st));
-    HPM_TRY(t.off.ensure(sizeof(int) * (np + 1), st));
-    HPM_TRY(t.bnd.ensure(sizeof(int) * 8 * np, st));
-    k_octant_bounds<<<blocks_for(8 * np), kThreads, 0, st>>>(pb, pe, t.box_flags.as<uint8_t>(),
-                                                             t.box_key.as<uint64_t>(), t.box_beg.as<int>(),
-                                                             t.box_end.as<int>(), skeys, shift, t.bnd.as<int>());
-    HPM_LAUNCHED(&launches);
-    k_count_children<<<blocks_for(np), kThreads, 0, st>>>(pb, pe, t.box_flags.as<uint8_t>(), t.box_end.as<int>(),
-                                                          t.bnd.as<int>(), t.cnt.as<int>());
-    HPM_LAUNCHED(&launches);
-    HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), np, t.counters.as<int>() + 64,
-                               t.keys_alt, st, &launches));
-    int hv[2] = {0, 0};
-    HPM_CUDA(cudaMemcpyAsync(&hv[0], t.counters.as<int>() + 64, sizeof(int), cudaMemcpyDeviceToHost, st));
-    HPM_CUDA(cudaMemcpyAsync(&hv[1], t.err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
-    HPM_CUDA(cudaStreamSynchronize(st));
-    if (hv[1] & kErrDomain) return HPM_ERR_OUT_OF_DOMAIN;
-    const int64_t nc = hv[0];
-    if (nc == 0) {
-      // still write the (empty) child maps of level l-1
-      k_fill_children<<<blocks_for(np), kThreads, 0, st>>>(
-          pb, pe, pe, l, D, pl->opts.leaf_max, t.box_flags.as<uint8_t>(), t.box_key.as<uint64_t>(),
-          t.box_beg.as<int>(), t.box_end.as<int>(), t.box_parent.as<int>(), t.box_child.as<int>(),
-          t.bnd.as<int>(), t.off.as<int>(), t.counters.as<int>());
+  HPM_TRY(t.lvl_dev.ensure(sizeof(int64_t) * (D + 2), st));
+  int64_t *lvl = t.lvl_dev.as<int64_t>();
+  int hc[64];
+  // Levels 1..D are enqueued without waiting for any count: every level kernel
+  // reads its box range from lvl on the device; one read-back at the end.
+  constexpr unsigned kLevelGrid = 152 * 8;
+  for (int attempt = 0;; ++attempt) {
+    HPM_TRY(t.cnt.ensure(sizeof(int) * cap, st));
+    HPM_TRY(t.off.ensure(sizeof(int) * (cap + 1), st));
+    HPM_TRY(t.bnd.ensure(sizeof(int) * 8 * cap, st));
+    {
+      const int64_t h0[2] = {0, nroot};
+      HPM_CUDA(cudaMemcpyAsync(lvl, h0, sizeof(h0), cudaMemcpyHostToDevice, st));
+      if (D + 2 > 2) HPM_CUDA(cudaMemsetAsync(lvl + 2, 0, sizeof(int64_t) * D, st));
+    }
+    for (int l = 1; l <= D; ++l) {
+      const int shift = 3 * (D - l);
+      k_expand<<<kLevelGrid, kThreads, 0, st>>>(lvl, l, t.box_flags.as<uint8_t>(), t.box_nb.as<int>());
       HPM_LAUNCHED(&launches);
-      for (int r = l; r <= D; ++r) pl->lvl_off[r + 1] = pe;
-      break;
+      k_octant_bounds<<<kLevelGrid, kThreads, 0, st>>>(lvl, l, t.box_flags.as<uint8_t>(), t.box_key.as<uint64_t>(),
+                                                       t.box_beg.as<int>(), t.box_end.as<int>(), skeys, shift,
+                                                       t.bnd.as<int>());
+      HPM_LAUNCHED(&launches);
+      k_count_children<<<kLevelGrid, kThreads, 0, st>>>(lvl, l, t.box_flags.as<uint8_t>(), t.box_end.as<int>(),
+                                                        t.bnd.as<int>(), t.cnt.as<int>());
+      HPM_LAUNCHED(&launches);
+      HPM_TRY(exclusive_scan_i32_dev(t.cnt.as<int>(), t.off.as<int>(), lvl + (l - 1), cap,
+                                     t.counters.as<int>() + 64, t.keys_alt, st, &launches));
+      k_level_close<<<1, 1, 0, st>>>(lvl, l, t.counters.as<int>() + 64, cap, t.err.as<int>());
+      HPM_LAUNCHED(&launches);
+      k_fill_children<<<kLevelGrid, kThreads, 0, st>>>(
+          lvl, l, D, pl->opts.leaf_max, t.box_flags.as<uint8_t>(), t.box_key.as<uint64_t>(), t.box_beg.as<int>(),
+          t.box_end.as<int>(), t.box_parent.as<int>(), t.box_child.as<int>(), t.bnd.as<int>(), t.off.as<int>(),
+          t.counters.as<int>(), t.err.as<int>());
+      HPM_LAUNCHED(&launches);
+      k_neighbours<<<kLevelGrid, kThreads, 0, st>>>(lvl, l, t.box_flags.as<uint8_t>(), t.box_key.as<uint64_t>(),
+                                                    t.box_parent.as<int>(), t.box_child.as<int>(),
+                                                    t.box_nb.as<int>());
+      HPM_LAUNCHED(&launches);
     }
-    const int64_t need = pe + nc;
-    if (need > cap) {
-      cap = need + need / 2;
-      HPM_TRY(ensure_boxes(t, cap, st));
-    }
-    k_fill_children<<<blocks_for(np), kThreads, 0, st>>>(
-        pb, pe, pe, l, D, pl->opts.leaf_max, t.box_flags.as<uint8_t>(), t.box_key.as<uint64_t>(),
-        t.box_beg.as<int>(), t.box_end.as<int>(), t.box_parent.as<int>(), t.box_child.as<int>(),
-        t.bnd.as<int>(), t.off.as<int>(), t.counters.as<int>());
-    HPM_LAUNCHED(&launches);
-    k_neighbours<<<blocks_for(nc), kThreads, 0, st>>>(pe, need, l, t.box_flags.as<uint8_t>(),
-                                                      t.box_key.as<uint64_t>(), t.box_parent.as<int>(),
-                                                      t.box_child.as<int>(), t.box_nb.as<int>());
-    HPM_LAUNCHED(&launches);
-    pl->lvl_off[l + 1] = need;
-    reached = l;
+    int herr = 0;
+    HPM_CUDA(cudaMemcpyAsync(pl->lvl_off.data(), lvl, sizeof(int64_t) * (D + 2), cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaMemcpyAsync(&herr, t.err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaMemcpyAsync(hc, t.counters.p, sizeof(int) * 64, cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaStreamSynchronize(st));
+    if (herr & kErrDomain) return HPM_ERR_OUT_OF_DOMAIN;
+    if (!(herr & kErrCapacity)) break;
+    if (attempt >= 8) return HPM_ERR_OOM;
+    // more room, then the levels again (the roots are kept; per-level counts
+    // and the error word are reset)
+    cap *= 2;
+    HPM_TRY(ensure_boxes(t, cap, st));
+    HPM_CUDA(cudaMemsetAsync(t.err.p, 0, sizeof(int), st));
+    HPM_CUDA(cudaMemsetAsync(t.counters.as<int>() + 1, 0, sizeof(int) * 31, st));
+    HPM_CUDA(cudaMemsetAsync(t.counters.as<int>() + 33, 0, sizeof(int) * 31, st));
   }
   if (D == 0) pl->lvl_off[1] = nroot;  // the roots are the only boxes
+  pl->nbox = pl->lvl_off[D + 1];
   {
     // child maps of the deepest level are never filled: mark them empty
-    const int64_t b = pl->lvl_off[reached], e = pl->lvl_off[reached + 1];
+    const int64_t b = pl->lvl_off[D], e = pl->lvl_off[D + 1];
     if (e > b) HPM_CUDA(cudaMemsetAsync(t.box_child.as<int>() + b * 8, 0xff, sizeof(int) * 8 * (e - b), st));
   }
-  for (int r = reached + 1; r <= D; ++r) pl->lvl_off[r + 1] = pl->lvl_off[reached + 1];
-  pl->nbox = pl->lvl_off[D + 1];
 
-  // per-level counts of cells and leaves
-  int hc[64];
-  HPM_CUDA(cudaMemcpyAsync(hc, t.counters.p, sizeof(int) * 64, cudaMemcpyDeviceToHost, st));
-  HPM_CUDA(cudaStreamSynchronize(st));
+  // per-level counts of cells and leaves (read back above)
   int depth_reached = 0;
   int64_t ncell = 0, nleaf = 0;
   for (int l = 0; l <= D; ++l) {
@@ -613,18 +665,30 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     pl->leaf_lvl_off[l + 1] = pl->leaf_lvl_off[l] + hc[32 + l];
   }
 
-  // work lists: targets (cells at level >= 2), leaves, P2G boxes (level >= 2, not internal)
+  // work lists: targets (cells at level >= 2), leaves, P2G boxes (level >= 2,
+  // not internal: the virtual boxes are never internal), parents of the
+  // targets (internal cells at levels >= 1); their sizes follow from the
+  // per-level counts of cells and leaves
   const int64_t off2 = D >= 2 ? pl->lvl_off[2] : pl->nbox;
-  int64_t cnt = 0;
-  HPM_TRY(select_boxes(pl, off2, pl->nbox, 0, t.tgt_box, &cnt, st, &launches));
-  pl->ntgt = cnt;
-  HPM_TRY(select_boxes(pl, 0, pl->nbox, 1, t.leaf_box, &cnt, st, &launches));
-  pl->nleaf = cnt;
-  HPM_TRY(select_boxes(pl, off2, pl->nbox, 2, t.p2g_box, &cnt, st, &launches));
-  pl->np2g = cnt;
-  // parents of the targets: internal cells at levels >= 1
-  HPM_TRY(select_boxes(pl, D >= 1 ? pl->lvl_off[1] : pl->nbox, pl->nbox, 3, t.par_box, &cnt, st, &launches));
-  pl->npar = cnt;
+  {
+    int64_t cells2 = 0, internal2 = 0, internal1 = 0;
+    for (int l = 1; l <= D; ++l) {
+      const int64_t internal = (int64_t)hc[l] - hc[32 + l];
+      internal1 += internal;
+      if (l >= 2) {
+        cells2 += hc[l];
+        internal2 += internal;
+      }
+    }
+    pl->ntgt = cells2;
+    pl->nleaf = nleaf;
+    pl->np2g = (pl->nbox - off2) - internal2;
+    pl->npar = internal1;
+  }
+  HPM_TRY(select_boxes(pl, off2, pl->nbox, 0, t.tgt_box, 70, st, &launches));
+  HPM_TRY(select_boxes(pl, 0, pl->nbox, 1, t.leaf_box, 71, st, &launches));
+  HPM_TRY(select_boxes(pl, off2, pl->nbox, 2, t.p2g_box, 72, st, &launches));
+  HPM_TRY(select_boxes(pl, D >= 1 ? pl->lvl_off[1] : pl->nbox, pl->nbox, 3, t.par_box, 73, st, &launches));
   // particle offsets of the P2G boxes (n + 1 entries, the last one the total)
   HPM_TRY(t.p2g_off.ensure(sizeof(int) * (pl->np2g + 1), st));
   if (pl->np2g) {
@@ -657,11 +721,17 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
                                t.keys_alt, st, &launches));
     HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.leaf_part0.as<int>(), nl, t.counters.as<int>() + 65,
                                t.keys_alt, st, &launches));
-    int hv[2] = {0, 0};
-    HPM_CUDA(cudaMemcpyAsync(hv, t.counters.as<int>() + 64, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+    int hv[10] = {0};
+    HPM_CUDA(cudaMemcpyAsync(hv, t.counters.as<int>() + 64, sizeof(int) * 10, cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaStreamSynchronize(st));
     pl->nitem = hv[0];
     pl->npart = hv[1];
+    // the work-list sizes the host derived must be what the device selected
+    if (hv[6] != pl->ntgt || hv[7] != pl->nleaf || hv[8] != pl->np2g || hv[9] != pl->npar) {
+      fprintf(stderr, "hpm: work-list sizes disagree (device %d %d %d %d, host %lld %lld %lld %lld)\n", hv[6], hv[7],
+              hv[8], hv[9], (long long)pl->ntgt, (long long)pl->nleaf, (long long)pl->np2g, (long long)pl->npar);
+      return HPM_ERR_INVALID_ARG;
+    }
     HPM_TRY(t.item_leaf.ensure(sizeof(int) * (pl->nitem + 1), st));
     HPM_TRY(t.item_s0.ensure(sizeof(int) * (pl->nitem + 1), st));
     HPM_TRY(t.item_s1.ensure(sizeof(int) * (pl->nitem + 1), st));

@@ -129,6 +129,28 @@ def test_edge_cases(hpm):
     assert O.rel_rms(acc, a_ref) < TOL
 
 
+def test_box_capacity_regrowth(hpm):
+    # Uniform points with leaf_max 0: every occupied cell is internal down to
+    # depth 6, about 6300 cells, several times the first build's box capacity
+    # (n / 4 + 1024). The build must grow its box arrays, redo the levels and
+    # give the same tree and fields as a rebuild that had room from the start.
+    rng = np.random.default_rng(9)
+    n = 2000
+    pos = rng.random((n, 3))
+    mass = I.equal_masses(n)
+    dev = torch.device("cuda:0")
+    s = hpm.Solver(6, 4, 1e-3, 0)
+    p = torch.from_numpy(pos).to(dev)
+    m = torch.from_numpy(mass).to(dev)
+    phi1, acc1 = (x.cpu().numpy() for x in s(p, m))
+    lst = s.lists()
+    phi2, acc2 = (x.cpu().numpy() for x in s(p, m))
+    s.close()
+    assert lst["key"].shape[0] > n // 4 + 1024
+    assert_lists_equal(lst, O.canonical_lists(O.Tree(pos, max_depth=6, leaf_max=0)))
+    assert np.array_equal(phi1, phi2) and np.array_equal(acc1, acc2)
+
+
 def test_out_of_domain_and_empty(hpm):
     dev = torch.device("cuda:0")
     s = hpm.Solver(3, 4, 0.0, 0)
