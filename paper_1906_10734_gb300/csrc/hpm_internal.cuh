@@ -180,6 +180,7 @@ hpm_status batch_scatter(const hpm_problem *d_desc, const int64_t *d_off, int np
 // m2l.cu
 hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches);
 // m2l_tc.cu
+int sm_count();
 bool use_tc_m2l(const hpm_plan_s *pl);
 hpm_status tc_precompute(hpm_plan_s *pl, cudaStream_t st);
 hpm_status tc_build_tiles(hpm_plan_s *pl, const std::vector<int64_t> &par_per_level, cudaStream_t st,

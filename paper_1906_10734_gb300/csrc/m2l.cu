@@ -650,16 +650,6 @@ __global__ void __launch_bounds__(kThreads) k_m2l_generic(const __grid_constant_
 }
 }  // namespace gen
 
-int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
 
 template <int NG>
 hpm_status launch_xd(const xd::Params &p, int64_t grid, cudaStream_t st) {
@@ -674,6 +664,18 @@ hpm_status launch_xd(const xd::Params &p, int64_t grid, cudaStream_t st) {
 }
 
 }  // namespace
+
+// Streaming multiprocessors of the current device (cached).
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
 
 hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   TreeRefs r{};

@@ -22,8 +22,9 @@
 // largest |mass| is 2^-k of the level's largest keeps 22 bits for k <= 17 and
 // loses bits gradually beyond (its contribution shrinks in proportion). The tensor
 // core's accumulation drops low bits, so the accumulator is drained every
-// kBlockChunks K-chunks into a round-to-nearest FP32 total (a second region of
-// tensor memory), which keeps the chain short. Rows (o, i >= 1) hold
+// kBlockChunks K-chunks into a round-to-nearest FP32 total held in the drain
+// warps' registers, which keeps the chain short; two accumulator buffers
+// alternate, so the MMAs of one block run while the previous block drains. Rows (o, i >= 1) hold
 // deviations from node 0 of the child, the (constant, deviations) split of the
 // local expansion that the FFT path also produces; row (o, 0) holds its
 // entries minus their mean m_o over the interaction zone, and m_o times the
@@ -33,11 +34,11 @@
 // One CTA computes 128 rows (2 children) for 256 parents of one level:
 //   warp 0       bulk-copies the W tile of each K-chunk (pre-swizzled in HBM)
 //   warp 1       allocates tensor memory and issues tcgen05.mma
-//   warps 2-5    gather the 256 parents' source gridlets with cp.async
+//   warps 4-7    gather the 256 parents' source gridlets with cp.async
 //                (FP16 pairs split once per solve by k_split, at one
 //                power-of-two scale per problem and level, so a parent's
 //                column needs no rescaling)
-//   warps 6-13   drain the accumulator and write the targets' values
+//   warps 8-15   drain the accumulators and write the targets' values
 // Every wait is bounded; a wait that runs out sets kErrTimeout in the error
 // word and the CTA leaves its loops.
 #include <cuda_fp16.h>
@@ -68,9 +69,15 @@ constexpr int kNoExp = 1 << 20;                 // exponent of a row without mas
 
 constexpr int kBlockChunks = 16;                // accumulator drained every 4 slots
 constexpr int kBlocks = kChunks / kBlockChunks;
-constexpr int kWarps = 14, kThreads = kWarps * 32;
-constexpr int kProdWarp0 = 2, kEpiWarp0 = 6;
+// 4 warpgroups: 0 = W copy (warp 0), MMA issue (warp 1), two idle warps;
+// 1 = gather; 2, 3 = drain. The drain warps keep the running totals in
+// registers (128 per thread), so they take registers from the other two:
+// 2 x 128 x kRegsLow + 2 x 128 x kRegsHigh = 512 x 128 = the launch's total.
+constexpr int kWarps = 16, kThreads = kWarps * 32;
+constexpr int kProdWarp0 = 4, kEpiWarp0 = 8;
 constexpr int kGatherThreads = (kEpiWarp0 - kProdWarp0) * 32;
+constexpr int kLaunchRegs = 128, kRegsLow = 72, kRegsHigh = 184;
+static_assert(2 * 128 * kRegsLow + 2 * 128 * kRegsHigh == kThreads * kLaunchRegs, "register split");
 constexpr int64_t kLevelBytes = (int64_t)kQuarters * kChunks * kABytes;  // W bytes per level
 static_assert(kChunks % kBlockChunks == 0, "drain blocks tile the K loop");
 
@@ -480,7 +487,8 @@ __global__ void k_col_exp(int64_t ntiles, const int *__restrict__ rows, const in
 __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ Params pr) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t full[kStages], empty[kStages], accf, acce;
+  // accf[x] / acce[x]: accumulator buffer x filled by the MMAs / emptied by the drain
+  __shared__ uint64_t full[kStages], empty[kStages], accf[2], acce[2];
   __shared__ uint32_t tmem_base;
   __shared__ int failed;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -494,8 +502,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
       bar_init(&full[s], 1 + kGatherThreads);
       bar_init(&empty[s], 1);
     }
-    bar_init(&accf, 1);
-    bar_init(&acce, 8);
+    for (int x = 0; x < 2; ++x) {
+      bar_init(&accf[x], 1);
+      bar_init(&acce[x], 8);
+    }
     failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -507,51 +517,58 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tacc = tmem_base, ttot = tmem_base + 256;
+  const uint32_t tbase = tmem_base;  // block b accumulates in columns 256 (b & 1) ...
 
-  if (warp == 0) {
-    // W tiles: one contiguous 16 KB block per K-chunk
-    if (lane == 0) {
-      const unsigned char *src = pr.w + (int64_t)(lev - 2) * kLevelBytes + (int64_t)q * kChunks * kABytes;
-      for (int c = 0; c < kChunks; ++c) {
-        const int st = c % kStages;
-        if (!bar_wait(&empty[st], ((c / kStages) & 1) ^ 1)) {
-          failed = 1;
-          break;
-        }
-        bar_expect(&full[st], kABytes);
-        bulk_load(sm + st * kStageBytes, src + (int64_t)c * kABytes, kABytes, &full[st]);
-      }
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      for (int c = 0; c < kChunks; ++c) {
-        const int st = c % kStages;
-        const bool first = (c % kBlockChunks) == 0;
-        if (first && c > 0) {
-          if (!bar_wait(&acce, ((c / kBlockChunks) - 1) & 1)) {
+  if (warp < kProdWarp0) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
+    if (warp == 0) {
+      // W tiles: one contiguous 8 KB block per K-chunk
+      if (lane == 0) {
+        const unsigned char *src = pr.w + (int64_t)(lev - 2) * kLevelBytes + (int64_t)q * kChunks * kABytes;
+        for (int c = 0; c < kChunks; ++c) {
+          const int st = c % kStages;
+          if (!bar_wait(&empty[st], ((c / kStages) & 1) ^ 1)) {
             failed = 1;
             break;
           }
+          bar_expect(&full[st], kABytes);
+          bulk_load(sm + st * kStageBytes, src + (int64_t)c * kABytes, kABytes, &full[st]);
+        }
+      }
+    } else if (warp == 1) {
+      if (lane == 0) {
+        for (int c = 0; c < kChunks; ++c) {
+          const int st = c % kStages;
+          const int b = c / kBlockChunks, x = b & 1;
+          const bool first = (c % kBlockChunks) == 0;
+          if (first && b >= 2) {
+            // buffer x was last filled by block b - 2: wait for its drain
+            if (!bar_wait(&acce[x], ((b >> 1) - 1) & 1)) {
+              failed = 1;
+              break;
+            }
+            tc_fence_after();
+          }
+          if (!bar_wait(&full[st], (c / kStages) & 1)) {
+            failed = 1;
+            break;
+          }
+          fence_async_smem();  // the gathered tiles were written by cp.async
           tc_fence_after();
+          // rows hold 16 hi then 16 lo values: hi*hi, hi*lo, lo*hi
+          const uint32_t a = su32(sm + st * kStageBytes), bb = a + kABytes;
+          const uint64_t ah = sdesc(a), al = sdesc(a + 32), bh = sdesc(bb), bl = sdesc(bb + 32);
+          const uint32_t tacc = tbase + 256u * (uint32_t)x;
+          mma(tacc, ah, bh, !first);
+          mma(tacc, ah, bl, 1);
+          mma(tacc, al, bh, 1);
+          mma_commit(&empty[st]);
+          if (c % kBlockChunks == kBlockChunks - 1) mma_commit(&accf[x]);
         }
-        if (!bar_wait(&full[st], (c / kStages) & 1)) {
-          failed = 1;
-          break;
-        }
-        fence_async_smem();  // the gathered tiles were written by cp.async
-        tc_fence_after();
-        // rows hold 16 hi then 16 lo values: hi*hi, hi*lo, lo*hi
-        const uint32_t a = su32(sm + st * kStageBytes), b = a + kABytes;
-        const uint64_t ah = sdesc(a), al = sdesc(a + 32), bh = sdesc(b), bl = sdesc(b + 32);
-        mma(tacc, ah, bh, !first);
-        mma(tacc, ah, bl, 1);
-        mma(tacc, al, bh, 1);
-        mma_commit(&empty[st]);
-        if (c % kBlockChunks == kBlockChunks - 1) mma_commit(&accf);
       }
     }
   } else if (warp < kEpiWarp0) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
     // 4 lanes per parent (one 16-byte piece of its 64-byte plane row each), 8
     // parents per warp instruction: parents pw*64 + 8m + grp, m = 0..7. Each
     // thread arrives on the stage's full barrier when its copies have landed;
@@ -594,55 +611,60 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
       cp_arrive(&full[st]);
     }
   } else {
-    // drain: total += block accumulator; after the last block write the values
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsHigh));
+    // drain: total += block accumulator (registers); after the last block
+    // write the values. Warp w reads TMEM lanes 32 (w mod 4) ...
     const int lq = warp & 3, half = (warp - kEpiWarp0) >> 2;
     const int r = lq * 32 + lane;                 // row of this thread
     const int o = 2 * q + (r >> 6), node = r & 63;
     const uint32_t lane_off = (uint32_t)(lq * 32) << 16;
     const int e_row = __ldg(pr.w_exp + (lev - 2) * (kQuarters * kRows) + q * kRows + r);
+    float tot[128];
+    bool ok = true;
     for (int b = 0; b < kBlocks; ++b) {
-      if (!__all_sync(0xffffffffu, bar_wait(&accf, b & 1))) {
+      const int x = b & 1;
+      if (!__all_sync(0xffffffffu, bar_wait(&accf[x], (b >> 1) & 1))) {
         failed = 1;
+        ok = false;
         break;
       }
       tc_fence_after();
-      const bool last = b == kBlocks - 1;
-#pragma unroll 1
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        uint32_t a[32];
+        tmem_ld32(tbase + 256u * (uint32_t)x + lane_off + half * 128 + cc * 32, a);
+        tmem_wait_ld();
+        if (b == 0) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) tot[cc * 32 + j] = __uint_as_float(a[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) tot[cc * 32 + j] = __uint_as_float(a[j]) + tot[cc * 32 + j];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) bar_arrive(&acce[x]);
+    }
+    if (ok) {
+#pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
         const int col = half * 128 + cc * 32;
-        uint32_t a[32], t[32];
-        tmem_ld32(tacc + lane_off + col, a);
-        if (b > 0) tmem_ld32(ttot + lane_off + col, t);
-        tmem_wait_ld();
-        if (b > 0) {
+        const int *tg = pr.tgt + (tile * kTileN + col) * 8 + o;
+        const int *ce = pr.col_exp + tile * kTileN + col;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) a[j] = __float_as_uint(__uint_as_float(a[j]) + __uint_as_float(t[j]));
-        }
-        if (!last) {
-          tmem_st32(ttot + lane_off + col, a);
-        } else {
-          const int *tg = pr.tgt + (tile * kTileN + col) * 8 + o;
-          const int *ce = pr.col_exp + tile * kTileN + col;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int t_idx = __ldg(tg + j * 8);
-            if (t_idx >= 0) {
-              const float v = (__uint_as_float(a[j]) * pow2f(-e_row)) * pow2f(-__ldg(ce + j));
-              if (node == 0) {
-                pr.outc[t_idx] = (float)((double)v + pr.mean[lev][o] * (double)__ldg(pr.zone_mass + (tile * kTileN + col + j) * 8 + o));
-                pr.out[(int64_t)t_idx * kM3] = 0.f;
-              } else {
-                pr.out[(int64_t)t_idx * kM3 + node] = v;
-              }
+        for (int j = 0; j < 32; ++j) {
+          const int t_idx = __ldg(tg + j * 8);
+          if (t_idx >= 0) {
+            const float v = (tot[cc * 32 + j] * pow2f(-e_row)) * pow2f(-__ldg(ce + j));
+            if (node == 0) {
+              pr.outc[t_idx] = (float)((double)v + pr.mean[lev][o] * (double)__ldg(pr.zone_mass + (tile * kTileN + col + j) * 8 + o));
+              pr.out[(int64_t)t_idx * kM3] = 0.f;
+            } else {
+              pr.out[(int64_t)t_idx * kM3 + node] = v;
             }
           }
         }
-      }
-      if (!last) {
-        tmem_wait_st();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) bar_arrive(&acce);
       }
     }
   }
@@ -790,6 +812,16 @@ hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   static bool attr = false;
   if (!attr) {
     HPM_CUDA(cudaFuncSetAttribute(tc::k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem));
+    // The drain warps raise their register count to kRegsHigh with registers
+    // the other warpgroups give back; that only adds up if the kernel was
+    // compiled with kLaunchRegs per thread. Never launch it otherwise.
+    cudaFuncAttributes fa{};
+    HPM_CUDA(cudaFuncGetAttributes(&fa, tc::k_m2l_tc));
+    if (fa.numRegs != tc::kLaunchRegs) {
+      fprintf(stderr, "hpm: k_m2l_tc compiled with %d registers per thread, expected %d\n", fa.numRegs,
+              tc::kLaunchRegs);
+      return HPM_ERR_UNSUPPORTED;
+    }
     attr = true;
   }
   const int64_t grid = pl->tc_ntiles * tc::kQuarters;

@@ -10,6 +10,7 @@
 // leaves at level l. The set is closed under taking parents, so it forms a
 // tree of its own and the neighbours of a cell are the children of the
 // neighbours of its parent.
+#include <mutex>
 #include <utility>
 
 #include <algorithm>
@@ -137,31 +138,6 @@ __global__ void k_roots(int nprob, int64_t n, int depth, int leaf_max, const int
   if (!internal) atomicAdd(&counters[32 + 0], 1);
 }
 
-// Every box within Chebyshev distance 1 of an internal cell (its neighbour
-// list, itself included) is expanded. The flag bytes are set with
-// non-returning atomic ORs on their 32-bit words: 27 independent updates
-// instead of 27 dependent read-modify-writes. (Virtual boxes keep empty
-// neighbour lists, so the relation must be walked from the internal side.)
-// The level kernels below read the box ranges of the levels from the device
-// (lvl[l] = first box of level l) and loop over them with a fixed grid, so the
-// host enqueues the whole build without waiting for any count.
-#define HPM_GRID_STRIDE(i, b, e) \
-  for (int64_t i = (b) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (e); i += (int64_t)gridDim.x * blockDim.x)
-
-__global__ void k_expand(const int64_t *__restrict__ lvl, int l, uint8_t *__restrict__ flags,
-                         const int *__restrict__ nb) {
-  unsigned int *words = reinterpret_cast<unsigned int *>(flags);
-  HPM_GRID_STRIDE(i, lvl[l - 1], lvl[l]) {
-    if (!(flags[i] & kInternal)) continue;
-    int q[27];
-#pragma unroll
-    for (int k = 0; k < 27; ++k) q[k] = nb[i * 27 + k];
-#pragma unroll
-    for (int k = 0; k < 27; ++k)
-      if (q[k] >= 0) atomicOr(words + (q[k] >> 2), (unsigned int)kExpand << (8 * (q[k] & 3)));
-  }
-}
-
 // First index in [lo, hi) whose level-l key is >= kc.
 __device__ __forceinline__ int lower_bound_key(const uint64_t *__restrict__ skeys, int lo, int hi,
                                                int shift, uint64_t kc) {
@@ -174,81 +150,14 @@ __device__ __forceinline__ int lower_bound_key(const uint64_t *__restrict__ skey
 }
 
 
-// Child boundaries of every expanded box, one thread per (box, octant): the
-// seven searches of a box run in parallel instead of one after another.
-__global__ void k_octant_bounds(const int64_t *__restrict__ lvl, int l, const uint8_t *__restrict__ flags,
-                                const uint64_t *__restrict__ key, const int *__restrict__ beg,
-                                const int *__restrict__ end, const uint64_t *__restrict__ skeys, int shift,
-                                int *__restrict__ bnd) {
-  const int64_t pb = lvl[l - 1], pe = lvl[l];
-  HPM_GRID_STRIDE(t, 0, 8 * (pe - pb)) {
-    const int64_t i = pb + t / 8;
-    const int o = (int)(t % 8);
-    int v = beg[i];
-    if (o > 0 && (flags[i] & kExpand))
-      v = lower_bound_key(skeys, beg[i], end[i], shift, (key[i] << 3) | (uint64_t)o);
-    bnd[t] = v;
-  }
-}
-
-__global__ void k_count_children(const int64_t *__restrict__ lvl, int l, const uint8_t *__restrict__ flags,
-                                 const int *__restrict__ end, const int *__restrict__ bnd,
-                                 int *__restrict__ cnt) {
-  const int64_t pb = lvl[l - 1];
-  HPM_GRID_STRIDE(i, pb, lvl[l]) {
-    int c = 0;
-    if (flags[i] & kExpand) {
-      const int *b = bnd + (i - pb) * 8;
-#pragma unroll
-      for (int o = 0; o < 8; ++o) c += (o < 7 ? b[o + 1] : end[i]) > b[o];
-    }
-    cnt[i - pb] = c;
-  }
-}
-
-// Closes level l: its children are the next `*total` boxes. Past the box
-// capacity the children are dropped and kErrCapacity is set (the host then
-// rebuilds with more room).
-__global__ void k_level_close(int64_t *__restrict__ lvl, int l, const int *__restrict__ total, int64_t cap,
-                              int *__restrict__ err) {
-  const int64_t need = lvl[l] + *total;
-  if (need > cap) {
-    atomicOr(err, kErrCapacity);
-    lvl[l + 1] = lvl[l];
-  } else {
-    lvl[l + 1] = need;
-  }
-}
-
+// The helpers below run inside the cooperative level kernel, where the box
+// arrays are written by other blocks between grid barriers: plain coherent
+// loads only (no __restrict__, no read-only cache path).
+// Children of expanded box q: octants with particles become the next boxes
+// from cb + off[q - pb] on, with their keys, ranges, parent and flags.
 __device__ void fill_children_of(int64_t q, int64_t pb, int64_t cb, int level, int depth, int leaf_max,
-                                 uint8_t *__restrict__ flags, uint64_t *__restrict__ key, int *__restrict__ beg,
-                                 int *__restrict__ end, int *__restrict__ parent, int *__restrict__ child,
-                                 const int *__restrict__ bnds, const int *__restrict__ off,
-                                 int *__restrict__ counters);
-
-__global__ void k_fill_children(const int64_t *__restrict__ lvl, int level, int depth,
-                                int leaf_max, uint8_t *__restrict__ flags, uint64_t *__restrict__ key,
-                                int *__restrict__ beg, int *__restrict__ end,
-                                int *__restrict__ parent, int *__restrict__ child,
-                                const int *__restrict__ bnds, const int *__restrict__ off,
-                                int *__restrict__ counters, const int *__restrict__ err) {
-  const int64_t pb = lvl[level - 1], pe = lvl[level], cb = pe;
-  const bool dropped = (*err & kErrCapacity) != 0;
-  HPM_GRID_STRIDE(q, pb, pe) {
-    if (dropped || !(flags[q] & kExpand)) {
-#pragma unroll
-      for (int o = 0; o < 8; ++o) child[q * 8 + o] = -1;
-      continue;
-    }
-    fill_children_of(q, pb, cb, level, depth, leaf_max, flags, key, beg, end, parent, child, bnds, off, counters);
-  }
-}
-
-__device__ void fill_children_of(int64_t q, int64_t pb, int64_t cb, int level, int depth, int leaf_max,
-                                 uint8_t *__restrict__ flags, uint64_t *__restrict__ key, int *__restrict__ beg,
-                                 int *__restrict__ end, int *__restrict__ parent, int *__restrict__ child,
-                                 const int *__restrict__ bnds, const int *__restrict__ off,
-                                 int *__restrict__ counters) {
+                                 uint8_t *flags, uint64_t *key, int *beg, int *end, int *parent, int *child,
+                                 const int *bnds, const int *off, int *counters) {
   int bnd[9];
   const uint64_t kq = key[q];
 #pragma unroll
@@ -279,29 +188,16 @@ __device__ void fill_children_of(int64_t q, int64_t pb, int64_t cb, int level, i
   if (nleaf) atomicAdd(&counters[32 + level], nleaf);
 }
 
-__device__ void neighbours_of(int64_t i, int level, const uint64_t *__restrict__ key,
-                              const int *__restrict__ parent, const int *__restrict__ child, int *__restrict__ nb);
-
-__global__ void k_neighbours(const int64_t *__restrict__ lvl, int level, const uint8_t *__restrict__ flags,
-                             const uint64_t *__restrict__ key, const int *__restrict__ parent,
-                             const int *__restrict__ child, int *__restrict__ nb) {
-  HPM_GRID_STRIDE(i, lvl[level], lvl[level + 1]) {
-    if (!(flags[i] & kReal)) {
-      for (int k = 0; k < 27; ++k) nb[i * 27 + k] = -1;
-      continue;
-    }
-    neighbours_of(i, level, key, parent, child, nb);
-  }
-}
-
-__device__ void neighbours_of(int64_t i, int level, const uint64_t *__restrict__ key,
-                              const int *__restrict__ parent, const int *__restrict__ child, int *__restrict__ nb) {
+// 27-neighbour table of box i at `level` (-1 where absent): the children of
+// its parent's neighbours.
+__device__ void neighbours_of(int64_t i, int level, const uint64_t *key, const int *parent, const int *child,
+                              int *nb) {
   const uint64_t k0 = key[i] & ((1ull << (3 * level)) - 1ull);
   const int c[3] = {(int)compact3(k0), (int)compact3(k0 >> 1), (int)compact3(k0 >> 2)};
   const int side = 1 << level;
   const int p = parent[i];
   // the parent's neighbour holding each of the 27 boxes, then its child: two
-  // rounds of independent loads (the parent's row is never written here)
+  // rounds of independent loads (the parent's row is not written at this level)
   int q[27];
 #pragma unroll
   for (int k = 0; k < 27; ++k) {
@@ -310,16 +206,211 @@ __device__ void neighbours_of(int64_t i, int level, const uint64_t *__restrict__
     if (n0 >= 0 && n0 < side && n1 >= 0 && n1 < side && n2 >= 0 && n2 < side) {
       const int dp = ((n0 >> 1) - (c[0] >> 1) + 1) + 3 * ((n1 >> 1) - (c[1] >> 1) + 1) +
                      9 * ((n2 >> 1) - (c[2] >> 1) + 1);
-      q[k] = __ldg(nb + (int64_t)p * 27 + dp);
+      q[k] = nb[(int64_t)p * 27 + dp];
     }
   }
 #pragma unroll
   for (int k = 0; k < 27; ++k) {
     const int n0 = c[0] + k % 3 - 1, n1 = c[1] + (k / 3) % 3 - 1, n2 = c[2] + k / 9 - 1;
-    q[k] = q[k] >= 0 ? __ldg(child + (int64_t)q[k] * 8 + ((n0 & 1) | ((n1 & 1) << 1) | ((n2 & 1) << 2))) : -1;
+    q[k] = q[k] >= 0 ? child[(int64_t)q[k] * 8 + ((n0 & 1) | ((n1 & 1) << 1) | ((n2 & 1) << 2))] : -1;
   }
 #pragma unroll
   for (int k = 0; k < 27; ++k) nb[i * 27 + k] = q[k];
+}
+
+// ---------------------------------------------------------------------------
+// All levels of the box tree in one cooperative launch: every block is
+// resident, so the phases of a level are separated by grid-wide barriers
+// instead of kernel boundaries (about 10 launches per level otherwise, most of
+// them tiny at the top of the tree).
+struct GridBar {
+  unsigned count, gen;
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier: the last block to arrive resets the count and bumps the
+// generation. Bounded: a block gives up after about 2^33 cycles (a few
+// seconds), or as soon as the error word shows that another block gave up;
+// false then.
+__device__ bool grid_sync(GridBar *gb, int *err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = ld_acquire(&gb->gen);
+    __threadfence();
+    if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+      gb->count = 0;
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire(&gb->gen) == g) {
+        if (*(volatile int *)err & kErrTimeout) {
+          ok = 0;
+          break;
+        }
+        if (clock64() - t0 > (1ll << 33)) {
+          atomicOr(err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+struct LevelArgs {
+  int64_t *lvl;  // lvl[0], lvl[1] set on entry; lvl[2..D+1] written here
+  int depth, leaf_max;
+  int64_t cap;
+  uint8_t *flags;
+  uint64_t *key;
+  int *beg, *end, *parent, *child, *nb;
+  const uint64_t *skeys;
+  int *bnd;   // per box of the level being split: its 8 child boundaries
+  int *off;   // per box of the level being split: first child, relative to its block's
+  int *bsum;  // per block: children of its boxes
+  int *counters, *err;
+  GridBar *gb;
+};
+
+// Level l (1..D) from level l - 1 = [pb, pe):
+//   1. expand: the 27 neighbours of every internal box get kExpand
+//   2. each block takes a contiguous run of boxes: child boundaries (8 lanes
+//      per box, one binary search each), child counts, block-local offsets
+//   3. block offsets from the per-block totals, then the children
+//   4. the neighbour tables of the new boxes
+__global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
+  __shared__ int s_warp[kThreads / 32];
+  __shared__ long long s_red[2][kThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x, gtid = (int64_t)blockIdx.x * blockDim.x + tid;
+  int64_t pb = a.lvl[0], pe = a.lvl[1];
+  for (int l = 1; l <= a.depth; ++l) {
+    // 1. expansion marks
+    {
+      unsigned int *words = reinterpret_cast<unsigned int *>(a.flags);
+      for (int64_t i = pb + gtid; i < pe; i += gthreads) {
+        if (!(a.flags[i] & kInternal)) continue;
+        int q[27];
+#pragma unroll
+        for (int k = 0; k < 27; ++k) q[k] = a.nb[i * 27 + k];
+#pragma unroll
+        for (int k = 0; k < 27; ++k)
+          if (q[k] >= 0) atomicOr(words + (q[k] >> 2), (unsigned int)kExpand << (8 * (q[k] & 3)));
+      }
+    }
+    if (!grid_sync(a.gb, a.err)) return;
+    // 2. boundaries, counts, block-local offsets
+    const int64_t m = pe - pb;
+    const int64_t chunk = ((m + gridDim.x - 1) / gridDim.x + 31) & ~int64_t(31);
+    const int64_t r0 = min((int64_t)blockIdx.x * chunk, m), r1 = min(r0 + chunk, m);
+    const int shift = 3 * (a.depth - l);
+    {
+      int carry = 0;
+      for (int64_t rb = r0; rb < r1; rb += kThreads / 8) {
+        const int64_t bi = rb + tid / 8;
+        const int oct = tid & 7;
+        const bool valid = bi < r1;
+        int v = 0, nxt = 0;
+        bool expand = false;
+        if (valid) {
+          const int64_t i = pb + bi;
+          const int bg = a.beg[i], en = a.end[i];
+          expand = (a.flags[i] & kExpand) != 0;
+          v = bg;
+          if (oct > 0 && expand) v = lower_bound_key(a.skeys, bg, en, shift, (a.key[i] << 3) | (uint64_t)oct);
+          nxt = en;
+          a.bnd[bi * 8 + oct] = v;
+        }
+        const int up = __shfl_down_sync(0xffffffffu, v, 1);
+        if (oct < 7) nxt = up;
+        const unsigned mask = __ballot_sync(0xffffffffu, valid && expand && nxt > v);
+        if (lane == 0) s_warp[wid] = __popc(mask);
+        __syncthreads();
+        int before = 0, round = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) {
+          const int c = s_warp[w];
+          before += w < wid ? c : 0;
+          round += c;
+        }
+        if (valid && oct == 0) a.off[bi] = carry + before + __popc(mask & ((1u << lane) - 1u));
+        carry += round;
+        __syncthreads();
+      }
+      if (tid == 0) a.bsum[blockIdx.x] = carry;
+    }
+    if (!grid_sync(a.gb, a.err)) return;
+    // 3. this block's first child and the level's total, then the children
+    int64_t base, total;
+    {
+      long long lo = 0, all = 0;
+      for (int b = tid; b < (int)gridDim.x; b += kThreads) {
+        const int c = a.bsum[b];
+        all += c;
+        if (b < (int)blockIdx.x) lo += c;
+      }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        lo += __shfl_xor_sync(0xffffffffu, lo, o);
+        all += __shfl_xor_sync(0xffffffffu, all, o);
+      }
+      if (lane == 0) {
+        s_red[0][wid] = lo;
+        s_red[1][wid] = all;
+      }
+      __syncthreads();
+      base = 0;
+      total = 0;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) {
+        base += s_red[0][w];
+        total += s_red[1][w];
+      }
+      __syncthreads();
+    }
+    const int64_t ne = pe + total;
+    if (ne > a.cap) {
+      // no room for level l: the host grows the box arrays and builds again
+      if (blockIdx.x == 0 && tid == 0) atomicOr(a.err, kErrCapacity);
+      return;
+    }
+    if (blockIdx.x == 0 && tid == 0) a.lvl[l + 1] = ne;
+    for (int64_t bi = r0 + tid; bi < r1; bi += kThreads) {
+      const int64_t q = pb + bi;
+      if (!(a.flags[q] & kExpand)) {
+#pragma unroll
+        for (int o = 0; o < 8; ++o) a.child[q * 8 + o] = -1;
+        continue;
+      }
+      fill_children_of(q, pb, pe + base, l, a.depth, a.leaf_max, a.flags, a.key, a.beg, a.end, a.parent, a.child,
+                       a.bnd, a.off, a.counters);
+    }
+    if (!grid_sync(a.gb, a.err)) return;
+    // 4. neighbour tables of level l
+    for (int64_t i = pe + gtid; i < ne; i += gthreads) {
+      if (!(a.flags[i] & kReal)) {
+        for (int k = 0; k < 27; ++k) a.nb[i * 27 + k] = -1;
+        continue;
+      }
+      neighbours_of(i, l, a.key, a.parent, a.child, a.nb);
+    }
+    if (!grid_sync(a.gb, a.err)) return;
+    pb = pe;
+    pe = ne;
+  }
 }
 
 // Work-list selection. mode 0: real cells; 1: leaves; 2: boxes that get their
@@ -587,42 +678,57 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   HPM_TRY(t.lvl_dev.ensure(sizeof(int64_t) * (D + 2), st));
   int64_t *lvl = t.lvl_dev.as<int64_t>();
   int hc[64];
-  // Levels 1..D are enqueued without waiting for any count: every level kernel
-  // reads its box range from lvl on the device; one read-back at the end.
-  constexpr unsigned kLevelGrid = 152 * 8;
+  // Levels 1..D in one cooperative launch (all blocks resident, grid-wide
+  // barriers between the phases of a level); one read-back at the end.
+  static int level_grid = 0;
+  if (!level_grid) {
+    int per_sm = 0;
+    HPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels, kThreads, 0));
+    level_grid = std::min(per_sm, 2) * sm_count();
+    if (level_grid <= 0) return HPM_ERR_CUDA;
+  }
   for (int attempt = 0;; ++attempt) {
-    HPM_TRY(t.cnt.ensure(sizeof(int) * cap, st));
+    HPM_TRY(t.cnt.ensure(sizeof(int) * level_grid, st));
     HPM_TRY(t.off.ensure(sizeof(int) * (cap + 1), st));
     HPM_TRY(t.bnd.ensure(sizeof(int) * 8 * cap, st));
     {
       const int64_t h0[2] = {0, nroot};
       HPM_CUDA(cudaMemcpyAsync(lvl, h0, sizeof(h0), cudaMemcpyHostToDevice, st));
       if (D + 2 > 2) HPM_CUDA(cudaMemsetAsync(lvl + 2, 0, sizeof(int64_t) * D, st));
+      HPM_CUDA(cudaMemsetAsync(t.counters.as<int>() + 96, 0, sizeof(int) * 2, st));  // grid barrier
     }
-    for (int l = 1; l <= D; ++l) {
-      const int shift = 3 * (D - l);
-      k_expand<<<kLevelGrid, kThreads, 0, st>>>(lvl, l, t.box_flags.as<uint8_t>(), t.box_nb.as<int>());
+    if (D > 0) {
+      LevelArgs la;
+      la.lvl = lvl;
+      la.depth = D;
+      la.leaf_max = pl->opts.leaf_max;
+      la.cap = cap;
+      la.flags = t.box_flags.as<uint8_t>();
+      la.key = t.box_key.as<uint64_t>();
+      la.beg = t.box_beg.as<int>();
+      la.end = t.box_end.as<int>();
+      la.parent = t.box_parent.as<int>();
+      la.child = t.box_child.as<int>();
+      la.nb = t.box_nb.as<int>();
+      la.skeys = skeys;
+      la.bnd = t.bnd.as<int>();
+      la.off = t.off.as<int>();
+      la.bsum = t.cnt.as<int>();
+      la.counters = t.counters.as<int>();
+      la.err = t.err.as<int>();
+      la.gb = reinterpret_cast<GridBar *>(t.counters.as<int>() + 96);
+      void *args[] = {&la};
+      // One level kernel on the device at a time, whatever the stream: two
+      // cooperative grids that each hold part of the GPU could wait on each
+      // other's blocks. Each launch waits for the previous one to finish.
+      static std::mutex mu;
+      static cudaEvent_t last = nullptr;
+      std::lock_guard<std::mutex> lock(mu);
+      if (!last) HPM_CUDA(cudaEventCreateWithFlags(&last, cudaEventDisableTiming));
+      HPM_CUDA(cudaStreamWaitEvent(st, last, 0));
+      HPM_CUDA(cudaLaunchCooperativeKernel((const void *)k_levels, dim3(level_grid), dim3(kThreads), args, 0, st));
       HPM_LAUNCHED(&launches);
-      k_octant_bounds<<<kLevelGrid, kThreads, 0, st>>>(lvl, l, t.box_flags.as<uint8_t>(), t.box_key.as<uint64_t>(),
-                                                       t.box_beg.as<int>(), t.box_end.as<int>(), skeys, shift,
-                                                       t.bnd.as<int>());
-      HPM_LAUNCHED(&launches);
-      k_count_children<<<kLevelGrid, kThreads, 0, st>>>(lvl, l, t.box_flags.as<uint8_t>(), t.box_end.as<int>(),
-                                                        t.bnd.as<int>(), t.cnt.as<int>());
-      HPM_LAUNCHED(&launches);
-      HPM_TRY(exclusive_scan_i32_dev(t.cnt.as<int>(), t.off.as<int>(), lvl + (l - 1), cap,
-                                     t.counters.as<int>() + 64, t.keys_alt, st, &launches));
-      k_level_close<<<1, 1, 0, st>>>(lvl, l, t.counters.as<int>() + 64, cap, t.err.as<int>());
-      HPM_LAUNCHED(&launches);
-      k_fill_children<<<kLevelGrid, kThreads, 0, st>>>(
-          lvl, l, D, pl->opts.leaf_max, t.box_flags.as<uint8_t>(), t.box_key.as<uint64_t>(), t.box_beg.as<int>(),
-          t.box_end.as<int>(), t.box_parent.as<int>(), t.box_child.as<int>(), t.bnd.as<int>(), t.off.as<int>(),
-          t.counters.as<int>(), t.err.as<int>());
-      HPM_LAUNCHED(&launches);
-      k_neighbours<<<kLevelGrid, kThreads, 0, st>>>(lvl, l, t.box_flags.as<uint8_t>(), t.box_key.as<uint64_t>(),
-                                                    t.box_parent.as<int>(), t.box_child.as<int>(),
-                                                    t.box_nb.as<int>());
-      HPM_LAUNCHED(&launches);
+      HPM_CUDA(cudaEventRecord(last, st));
     }
     int herr = 0;
     HPM_CUDA(cudaMemcpyAsync(pl->lvl_off.data(), lvl, sizeof(int64_t) * (D + 2), cudaMemcpyDeviceToHost, st));
@@ -630,6 +736,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     HPM_CUDA(cudaMemcpyAsync(hc, t.counters.p, sizeof(int) * 64, cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaStreamSynchronize(st));
     if (herr & kErrDomain) return HPM_ERR_OUT_OF_DOMAIN;
+    if (herr & kErrTimeout) return HPM_ERR_TIMEOUT;
     if (!(herr & kErrCapacity)) break;
     if (attempt >= 8) return HPM_ERR_OOM;
     // more room, then the levels again (the roots are kept; per-level counts
