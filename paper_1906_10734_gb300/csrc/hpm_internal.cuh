@@ -167,8 +167,6 @@ hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&val
 hpm_status exclusive_scan_i32(const int *in, int *out, int64_t n, int *d_total, DevBuf &scratch,
                               cudaStream_t st, int64_t *launches);
 // the same with the length on the device: n = d_range[1] - d_range[0] <= max_n
-hpm_status exclusive_scan_i32_dev(const int *in, int *out, const int64_t *d_range, int64_t max_n, int *d_total,
-                                  DevBuf &scratch, cudaStream_t st, int64_t *launches);
 // solve.cu
 hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, float *d_phi,
                  float *d_acc, cudaStream_t st);

@@ -38,12 +38,8 @@ __device__ __forceinline__ int block_excl_scan(int v, int *ex, int *sh_warp) {
   return total;
 }
 
-// dn, when given, holds [begin, end) on the device: n = end - begin (the
-// length of a tree level known only on the device); blocks past n contribute 0.
-__global__ void k_scan_reduce(const int *__restrict__ in, int64_t n, int *__restrict__ sums,
-                              const int64_t *__restrict__ dn) {
+__global__ void k_scan_reduce(const int *__restrict__ in, int64_t n, int *__restrict__ sums) {
   __shared__ int sh[32];
-  if (dn) n = dn[1] - dn[0];
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   int s = 0;
 #pragma unroll
@@ -72,9 +68,8 @@ __global__ void k_scan_sums(int *__restrict__ sums, int64_t nb, int *__restrict_
 }
 
 __global__ void k_scan_apply(const int *__restrict__ in, int *__restrict__ out, int64_t n,
-                             const int *__restrict__ sums, const int64_t *__restrict__ dn) {
+                             const int *__restrict__ sums) {
   __shared__ int sh[32];
-  if (dn) n = dn[1] - dn[0];
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
   int v[kScanItems];
   int s = 0;
@@ -169,25 +164,11 @@ hpm_status exclusive_scan_i32(const int *in, int *out, int64_t n, int *d_total, 
   const int64_t nb = (n + kScanTile - 1) / kScanTile;
   HPM_TRY(scratch.ensure(sizeof(int) * nb, st));
   int *sums = scratch.as<int>();
-  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums, nullptr);
+  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums);
   HPM_LAUNCHED(launches);
   k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, nb, d_total);
   HPM_LAUNCHED(launches);
-  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums, nullptr);
-  HPM_LAUNCHED(launches);
-  return HPM_OK;
-}
-
-hpm_status exclusive_scan_i32_dev(const int *in, int *out, const int64_t *d_range, int64_t max_n, int *d_total,
-                                  DevBuf &scratch, cudaStream_t st, int64_t *launches) {
-  const int64_t nb = max_n > 0 ? (max_n + kScanTile - 1) / kScanTile : 1;
-  HPM_TRY(scratch.ensure(sizeof(int) * nb, st));
-  int *sums = scratch.as<int>();
-  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, max_n, sums, d_range);
-  HPM_LAUNCHED(launches);
-  k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, nb, d_total);
-  HPM_LAUNCHED(launches);
-  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, max_n, sums, d_range);
+  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums);
   HPM_LAUNCHED(launches);
   return HPM_OK;
 }
