@@ -24,21 +24,29 @@
 // core's accumulation drops low bits, so the accumulator is drained every
 // kBlockChunks K-chunks into a round-to-nearest FP32 total held in the drain
 // warps' registers, which keeps the chain short; two accumulator buffers
-// alternate, so the MMAs of one block run while the previous block drains. Rows (o, i >= 1) hold
-// deviations from node 0 of the child, the (constant, deviations) split of the
-// local expansion that the FFT path also produces; row (o, 0) holds its
-// entries minus their mean m_o over the interaction zone, and m_o times the
-// zone's total mass (summed exactly by the gather warps) is added back to the
-// constant, which keeps that row's sum free of a large same-sign running total.
+// alternate, so the MMAs of one block run while the previous block drains.
+// Rows (o, i >= 1) hold deviations from node 0 of the child, the (constant,
+// deviations) split of the local expansion that the FFT path also produces;
+// row (o, 0) holds its entries minus their mean m_o over the interaction zone,
+// and m_o times the zone's total mass (summed separately in compensated FP32)
+// is added back to the constant, which keeps that row's sum free of a large
+// same-sign running total.
 //
-// One CTA computes 128 rows (2 children) for 256 parents of one level:
-//   warp 0       bulk-copies the W tile of each K-chunk (pre-swizzled in HBM)
-//   warp 1       allocates tensor memory and issues tcgen05.mma
-//   warps 4-7    gather the 256 parents' source gridlets with cp.async
-//                (FP16 pairs split once per solve by k_split, at one
-//                power-of-two scale per problem and level, so a parent's
-//                column needs no rescaling)
-//   warps 8-15   drain the accumulators and write the targets' values
+// A pair of CTAs (a cluster of 2 on neighbouring SMs) computes 256 rows (4
+// children) for 256 parents of one level with tcgen05.mma.cta_group::2: each
+// CTA holds 128 rows of W and 128 of the parents in shared memory and 128 rows
+// of the result in its tensor memory, so each SM loads half of the gathered
+// parents the pair's MMAs read. Per CTA:
+//   warp 0       bulk-copies the W tiles of each slot (pre-swizzled in HBM)
+//   warp 1       allocates tensor memory (both CTAs) and, in the leader,
+//                issues the MMAs and their commits to both CTAs' barriers
+//   warps 2, 3   in the peer, tell the leader when each stage has landed
+//   warps 4-7    gather this CTA's 128 parents' source gridlets with
+//                cp.async, one z plane each (FP16 pairs split once per solve
+//                by k_split, at one power-of-two scale per problem and
+//                level, so a parent's column needs no rescaling)
+//   warps 8-15   drain this CTA's accumulator rows and write the targets'
+//                values
 // Every wait is bounded; a wait that runs out sets kErrTimeout in the error
 // word and the CTA leaves its loops.
 #include <cuda_fp16.h>
@@ -57,29 +65,47 @@ constexpr int kKC = 16;                         // K elements per stage (one z p
 constexpr int kChunks = kSlots * kM3 / kKC;     // 864 stages per tile
 constexpr int kTileN = 256;                     // parents per tile
 constexpr int kRows = 128;                      // rows per CTA (2 children x 64 nodes)
-constexpr int kQuarters = 4;                    // CTAs per tile
-constexpr int kStages = 8;
+constexpr int kQuarters = 4;                    // CTAs per tile: two CTA pairs
+constexpr int kHalfN = kTileN / 2;              // parents gathered by each CTA of a pair
+// One stage holds the 4 K-chunks (z planes) of one slot, so the MMA thread
+// issues 12 MMAs per barrier wait and commit: the per-stage synchronisation
+// cost (a few hundred cycles of the issuing thread) stays well below the
+// MMAs' 1536 cycles. Each CTA of a pair loads its own 128 rows of W and half
+// of the parents, so a stage is 64 KB and three fit.
+constexpr int kStageChunks = 4;
+constexpr int kStages = 3;
 constexpr int kRowBytes = 2 * kKC * 2;          // one tile row: 16 hi then 16 lo FP16 values
-constexpr int kABytes = kRows * kRowBytes;      // 8 KB per stage, one bulk copy
-constexpr int kBBytes = kTileN * kRowBytes;     // 16 KB per stage
-constexpr int kStageBytes = kABytes + kBBytes;  // 24 KB
-constexpr int kSmem = kStages * kStageBytes + 1024;
+constexpr int kABytes = kRows * kRowBytes;      // W tile of one K-chunk: 8 KB
+constexpr int kBBytes = kHalfN * kRowBytes;     // gathered tile of one K-chunk: 8 KB
+constexpr int kStageABytes = kStageChunks * kABytes;                  // 32 KB, one bulk copy
+constexpr int kStageBytes = kStageChunks * (kABytes + kBBytes);       // 64 KB: 4 W tiles, then 4 B tiles
+constexpr int kSlotUses = kChunks / kStageChunks;                     // 216 stage uses per CTA
+// 1 KB for aligning the stages, 8 KB of slack past the last one
+constexpr int kSmem = kStages * kStageBytes + 1024 + 8192;
 constexpr int kScaleTop = 14;                   // scaled maxima lie in [2^13, 2^14)
 constexpr int kNoExp = 1 << 20;                 // exponent of a row without mass
 
 constexpr int kBlockChunks = 16;                // accumulator drained every 4 slots
 constexpr int kBlocks = kChunks / kBlockChunks;
-// 4 warpgroups: 0 = W copy (warp 0), MMA issue (warp 1), two idle warps;
-// 1 = gather; 2, 3 = drain. The drain warps keep the running totals in
+// 4 warpgroups: 0 = W copy (warp 0), tensor memory and MMA issue (warp 1),
+// relays of the peer's stages (warps 2, 3); 1 = gather; 2, 3 = drain. The drain warps keep the running totals in
 // registers (128 per thread), so they take registers from the other two:
-// 2 x 128 x kRegsLow + 2 x 128 x kRegsHigh = 512 x 128 = the launch's total.
+// 128 x (kRegsCtl + kRegsGather) + 2 x 128 x kRegsHigh = 512 x 128 = the
+// launch's total.
 constexpr int kWarps = 16, kThreads = kWarps * 32;
 constexpr int kProdWarp0 = 4, kEpiWarp0 = 8;
-constexpr int kGatherThreads = (kEpiWarp0 - kProdWarp0) * 32;
-constexpr int kLaunchRegs = 128, kRegsLow = 72, kRegsHigh = 184;
-static_assert(2 * 128 * kRegsLow + 2 * 128 * kRegsHigh == kThreads * kLaunchRegs, "register split");
+constexpr int kGatherWarps = kEpiWarp0 - kProdWarp0;  // one per z plane of a gridlet
+constexpr int kLaunchRegs = 128, kRegsCtl = 40, kRegsGather = 104, kRegsHigh = 184;
+static_assert(128 * kRegsCtl + 128 * kRegsGather + 2 * 128 * kRegsHigh == kThreads * kLaunchRegs, "register split");
+static_assert(kGatherWarps == 4, "gather warp g copies the z plane g of every slot");
+// setmaxnreg: .dec only lowers, .inc only raises; counts are multiples of 8 in [24, 256]
+static_assert(kRegsCtl <= kLaunchRegs && kRegsGather <= kLaunchRegs && kRegsHigh >= kLaunchRegs, "dec / inc");
+static_assert(kRegsCtl % 8 == 0 && kRegsGather % 8 == 0 && kRegsHigh % 8 == 0 && kRegsCtl >= 24 && kRegsHigh <= 256,
+              "register counts");
 constexpr int64_t kLevelBytes = (int64_t)kQuarters * kChunks * kABytes;  // W bytes per level
 static_assert(kChunks % kBlockChunks == 0, "drain blocks tile the K loop");
+static_assert(kStageChunks == 4 && kBlockChunks % kStageChunks == 0, "a stage is one slot; drain blocks hold whole stages");
+static_assert(kQuarters % 2 == 0, "CTA pairs");
 
 struct Params {
   const unsigned char *w;  // W tables, level l at w + (l - 2) * kLevelBytes
@@ -137,10 +163,6 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 __device__ __forceinline__ void cp16(uint32_t dst, const void *src, uint32_t src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
-// arrive on the barrier once this thread's earlier cp.async have landed
-__device__ __forceinline__ void cp_arrive(uint64_t *b) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(b)) : "memory");
-}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -151,19 +173,56 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
          ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
 // Instruction descriptor, kind::f16: FP32 accumulator, FP16 A and B (format
-// 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+// 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24. The MMA spans a CTA
+// pair: M = 256 rows (128 in each CTA's shared and tensor memory), N = 256
+// parents (each CTA's B rows are half of them).
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)((2 * kRows) >> 4) << 24);
 
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, int accumulate) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
           d),
       "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
       : "memory");
 }
+// arrive on the barrier at this offset in both CTAs of the pair once the MMAs
+// issued so far have completed
 __device__ __forceinline__ void mma_commit(uint64_t *b) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
-               : "memory");
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          su32(b)),
+      "h"((unsigned short)3)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// arrive on the barrier at the same offset in CTA `cta` of the cluster,
+// releasing this thread's earlier writes (and what it acquired) to it
+__device__ __forceinline__ void bar_arrive_remote(uint64_t *b, uint32_t cta) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(su32(b)), "r"(cta));
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(ra) : "memory");
+}
+// bounded wait that also acquires what the other CTA of the pair released
+__device__ __forceinline__ bool bar_wait_cl(uint64_t *b, uint32_t parity) {
+  const long long t0 = clock64();
+  uint32_t done = 0;
+  for (;;) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\tselp.u32 "
+        "%0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1ll << 32)) return false;
+  }
 }
 
 #define HPM_R32(a) \
@@ -484,131 +543,164 @@ __global__ void k_col_exp(int64_t ntiles, const int *__restrict__ rows, const in
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ Params pr) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ Params pr) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-  // accf[x] / acce[x]: accumulator buffer x filled by the MMAs / emptied by the drain
-  __shared__ uint64_t full[kStages], empty[kStages], accf[2], acce[2];
+  // full: this CTA's stage landed; pfull (leader): the peer's stage landed;
+  // empty: the pair's MMAs are done with the stage; accf[x] / acce[x]:
+  // accumulator buffer x filled by the MMAs / drained by both CTAs (leader)
+  __shared__ uint64_t full[kStages], pfull[kStages], empty[kStages], accf[2], acce[2];
   __shared__ uint32_t tmem_base;
   __shared__ int failed;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t rank = cluster_rank();  // 0: leader (issues the MMAs), 1: peer
   const int64_t tile = blockIdx.x / kQuarters;
-  const int q = (int)(blockIdx.x % kQuarters);
+  const int q = (int)(blockIdx.x % kQuarters);  // this CTA's 128 rows of W: quarter q; rank = q & 1
   int lev = 2;
   while (lev + 1 < pr.nlev && pr.tile_off[lev + 1] <= tile) ++lev;
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
-      bar_init(&full[s], 1 + kGatherThreads);
+      bar_init(&full[s], 1 + kGatherWarps);  // the W copy (with its byte count), then each plane's gather warp
+      bar_init(&pfull[s], 1);
       bar_init(&empty[s], 1);
     }
     for (int x = 0; x < 2; ++x) {
       bar_init(&accf[x], 1);
-      bar_init(&acce[x], 8);
+      bar_init(&acce[x], 16);  // the 8 drain warps of each CTA
     }
     failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  cluster_sync();  // both CTAs running, their barriers initialised
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(&tmem_base))
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(&tmem_base))
                  : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();  // tensor memory allocated in both CTAs before the first MMA
   tc_fence_after();
   const uint32_t tbase = tmem_base;  // block b accumulates in columns 256 (b & 1) ...
 
   if (warp < kProdWarp0) {
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsCtl));
     if (warp == 0) {
-      // W tiles: one contiguous 8 KB block per K-chunk
+      // W tiles: the 4 K-chunks of a slot are one contiguous 32 KB block
       if (lane == 0) {
         const unsigned char *src = pr.w + (int64_t)(lev - 2) * kLevelBytes + (int64_t)q * kChunks * kABytes;
-        for (int c = 0; c < kChunks; ++c) {
-          const int st = c % kStages;
-          if (!bar_wait(&empty[st], ((c / kStages) & 1) ^ 1)) {
+        bool ok = true;
+        for (int u = 0; u < kSlotUses; ++u) {
+          const int st = u % kStages;
+          if (!bar_wait(&empty[st], ((u / kStages) & 1) ^ 1)) {
             failed = 1;
+            ok = false;
             break;
           }
-          bar_expect(&full[st], kABytes);
-          bulk_load(sm + st * kStageBytes, src + (int64_t)c * kABytes, kABytes, &full[st]);
+          bar_expect(&full[st], kStageABytes);
+          bulk_load(sm + st * kStageBytes, src + (int64_t)u * kStageABytes, kStageABytes, &full[st]);
         }
+        // the releases of the last stages are the leader's final arrivals on
+        // this CTA's barriers: wait for them before the CTA may leave
+        for (int u = kSlotUses; ok && u < kSlotUses + kStages; ++u)
+          if (!bar_wait(&empty[u % kStages], ((u / kStages) & 1) ^ 1)) {
+            failed = 1;
+            ok = false;
+          }
       }
-    } else if (warp == 1) {
+    } else if (warp == 1 && rank == 0) {
       if (lane == 0) {
-        for (int c = 0; c < kChunks; ++c) {
-          const int st = c % kStages;
-          const int b = c / kBlockChunks, x = b & 1;
-          const bool first = (c % kBlockChunks) == 0;
+        for (int u = 0; u < kSlotUses; ++u) {
+          const int st = u % kStages;
+          const int c0 = u * kStageChunks;  // first K-chunk of the stage
+          const int b = c0 / kBlockChunks, x = b & 1;
+          const bool first = (c0 % kBlockChunks) == 0;
           if (first && b >= 2) {
-            // buffer x was last filled by block b - 2: wait for its drain
-            if (!bar_wait(&acce[x], ((b >> 1) - 1) & 1)) {
+            // buffer x was last filled by block b - 2: wait for both CTAs' drains
+            if (!bar_wait_cl(&acce[x], ((b >> 1) - 1) & 1)) {
               failed = 1;
               break;
             }
             tc_fence_after();
           }
-          if (!bar_wait(&full[st], (c / kStages) & 1)) {
+          if (!bar_wait(&full[st], (u / kStages) & 1) || !bar_wait_cl(&pfull[st], (u / kStages) & 1)) {
             failed = 1;
             break;
           }
-          fence_async_smem();  // the gathered tiles were written by cp.async
           tc_fence_after();
-          // rows hold 16 hi then 16 lo values: hi*hi, hi*lo, lo*hi
-          const uint32_t a = su32(sm + st * kStageBytes), bb = a + kABytes;
-          const uint64_t ah = sdesc(a), al = sdesc(a + 32), bh = sdesc(bb), bl = sdesc(bb + 32);
+          // rows hold 16 hi then 16 lo values: hi*hi, hi*lo, lo*hi; the same
+          // offsets in the peer CTA hold its 128 rows of W and 128 parents
+          const uint32_t sa = su32(sm + st * kStageBytes), sb = sa + kStageABytes;
           const uint32_t tacc = tbase + 256u * (uint32_t)x;
-          mma(tacc, ah, bh, !first);
-          mma(tacc, ah, bl, 1);
-          mma(tacc, al, bh, 1);
+#pragma unroll
+          for (int k = 0; k < kStageChunks; ++k) {
+            const uint32_t a = sa + k * kABytes, bb = sb + k * kBBytes;
+            const uint64_t ah = sdesc(a), al = sdesc(a + 32), bh = sdesc(bb), bl = sdesc(bb + 32);
+            mma(tacc, ah, bh, !(first && k == 0));
+            mma(tacc, ah, bl, 1);
+            mma(tacc, al, bh, 1);
+          }
           mma_commit(&empty[st]);
-          if (c % kBlockChunks == kBlockChunks - 1) mma_commit(&accf[x]);
+          if ((c0 + kStageChunks) % kBlockChunks == 0) mma_commit(&accf[x]);
+        }
+      }
+    } else if (warp >= 2 && rank == 1) {
+      // peer: relay each landed stage to the leader (warp 2 the even stage
+      // uses, warp 3 the odd ones, so each has two stages' time per arrival)
+      if (lane == 0) {
+        for (int u = warp - 2; u < kSlotUses; u += 2) {
+          const int st = u % kStages;
+          if (!bar_wait(&full[st], (u / kStages) & 1)) {
+            failed = 1;
+            break;
+          }
+          bar_arrive_remote(&pfull[st], 0);
         }
       }
     }
   } else if (warp < kEpiWarp0) {
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
-    // 4 lanes per parent (one 16-byte piece of its 64-byte plane row each), 8
-    // parents per warp instruction: parents pw*64 + 8m + grp, m = 0..7. Each
-    // thread arrives on the stage's full barrier when its copies have landed;
-    // rows are read two slots ahead.
-    const int pw = warp - kProdWarp0, sub = lane & 3, grp = lane >> 2;
-    const int nbase = pw * 64 + grp;
-    const int *rp = pr.rows + tile * kSlots * kTileN + nbase;
-    const uint32_t bsh = su32(sm + kABytes);
-    uint32_t soff[8];
-    int r0[8], r1[8], r2[8];
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsGather));
+    // Gather warp g fills the B tile of K-chunk 4 s + g (z plane g of slot
+    // s) in the stage of slot s with this CTA's 128 parents (128 rank ...):
+    // 64 bytes each, 4 lanes per parent (one 16-byte piece each), parents
+    // 8 m + lane / 4 for m = 0..15. It waits for its own copies, makes them
+    // visible to the tensor core's proxy and arrives once on the stage's
+    // full barrier: five arrivals per stage in all (the W copy and the four
+    // plane warps). Row indices of the next slot are loaded while the
+    // current one is copied.
+    const int g = warp - kProdWarp0, sub = lane & 3, grp = lane >> 2;
+    const int *rp = pr.rows + tile * kSlots * kTileN + (int)rank * kHalfN + grp;
+    // sw64 position of parent 8 m + grp, piece sub: 512 m + this lane's offset
+    const uint32_t lane_off = (uint32_t)(grp * 64 + ((sub ^ ((grp >> 1) & 3)) << 4));
+    const uint32_t bsh = su32(sm + kStageABytes + g * kBBytes) + lane_off;
+    const unsigned char *hsub = pr.hl + 16 * sub + g * kRowBytes;
+    constexpr int kPer = kHalfN / 8;
+    int rows[kPer], next[kPer];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      soff[m] = (uint32_t)sw64(nbase + 8 * m, sub);
-      r0[m] = __ldg(rp + 8 * m);
-      r1[m] = __ldg(rp + kTileN + 8 * m);
-      r2[m] = __ldg(rp + 2 * kTileN + 8 * m);
-    }
-    const unsigned char *hsub = pr.hl + 16 * sub;
-    for (int c = 0; c < kChunks; ++c) {
-      if ((c & 3) == 0 && c > 0) {
-        const int s3 = (c >> 2) + 2;
+    for (int m = 0; m < kPer; ++m) rows[m] = __ldg(rp + 8 * m);
+    for (int s = 0; s < kSlots; ++s) {
+      const int st = s % kStages;
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          r0[m] = r1[m];
-          r1[m] = r2[m];
-          r2[m] = s3 < kSlots ? __ldg(rp + (int64_t)s3 * kTileN + 8 * m) : -1;
-        }
-      }
-      const int st = c % kStages;
-      if (!__all_sync(0xffffffffu, bar_wait(&empty[st], ((c / kStages) & 1) ^ 1))) {
+      for (int m = 0; m < kPer; ++m) next[m] = s + 1 < kSlots ? __ldg(rp + (s + 1) * kTileN + 8 * m) : -1;
+      int ok = 1;
+      if (lane == 0) ok = bar_wait(&empty[st], ((s / kStages) & 1) ^ 1);
+      if (!__shfl_sync(0xffffffffu, ok, 0)) {
         failed = 1;
         break;
       }
       const uint32_t dst = bsh + st * kStageBytes;
 #pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int row = r0[m];
-        cp16(dst + soff[m], hsub + ((int64_t)(row >= 0 ? row : 0) * 4 + (c & 3)) * kRowBytes, row >= 0 ? 16u : 0u);
+      for (int m = 0; m < kPer; ++m) {
+        const int row = rows[m];
+        cp16(dst + m * 512, hsub + (int64_t)(row >= 0 ? row : 0) * 4 * kRowBytes, row >= 0 ? 16u : 0u);
       }
-      cp_arrive(&full[st]);
+      asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+      fence_async_smem();  // this warp's copies, visible to the tensor core
+      __syncwarp();
+      if (lane == 0) bar_arrive(&full[st]);
+#pragma unroll
+      for (int m = 0; m < kPer; ++m) rows[m] = next[m];
     }
   } else {
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsHigh));
@@ -623,7 +715,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     bool ok = true;
     for (int b = 0; b < kBlocks; ++b) {
       const int x = b & 1;
-      if (!__all_sync(0xffffffffu, bar_wait(&accf[x], (b >> 1) & 1))) {
+      if (!__all_sync(0xffffffffu, bar_wait_cl(&accf[x], (b >> 1) & 1))) {
         failed = 1;
         ok = false;
         break;
@@ -644,7 +736,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) bar_arrive(&acce[x]);
+      if (lane == 0) {
+        if (rank == 0) bar_arrive(&acce[x]);
+        else bar_arrive_remote(&acce[x], 0);
+      }
     }
     if (ok) {
 #pragma unroll
@@ -670,9 +765,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();  // no arrivals on, or reads of, the other CTA after this
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
   }
   if (tid == 0 && failed) atomicOr(pr.err, kErrTimeout);
 }
