@@ -108,6 +108,22 @@ __device__ __forceinline__ void lagrange_d(const GridletTables &tb, double xi, f
     }
 }
 
+// Ng = 4 in closed form: with u = 8 xi = A + B (A, B floats whose sum is
+// exact in FP64) and the nodes -3, -1, 1, 3, ell_0 = -(u+1)(u-1)(u-3)/48,
+// ell_1 = (u+3)(u-1)(u-3)/16, ell_2 = -(u+3)(u+1)(u-3)/16 and
+// ell_3 = (u+3)(u+1)(u-1)/48. The same FP64 products as the general form in
+// fewer FP64 instructions; the factors 1/16 are powers of two and are applied
+// after the rounding to FP32 (an exact scaling), so the weights are the same.
+__device__ __forceinline__ void lagrange4_d(float A, float B, float *w) {
+  const double u = (double)A + (double)B;
+  const double d0 = u + 3.0, d1 = u + 1.0, d2 = u - 1.0, d3 = u - 3.0;
+  const double e = d2 * d3, f = d0 * d1;
+  w[0] = (float)((d1 * e) * (-1.0 / 48.0));
+  w[1] = (float)(d0 * e) * 0.0625f;
+  w[2] = (float)(f * d3) * -0.0625f;
+  w[3] = (float)((f * d2) * (1.0 / 48.0));
+}
+
 // Effective masses, M_p = sum_i m_i prod_d ell_{p_d}(xi_d) (Eq. mp in Lagrange
 // form: sum_n B_pn t^n = ell_p(t)). A block takes 8 boxes; all its threads
 // evaluate the FP64 weights of the (box, particle) pairs of those boxes, 256
@@ -154,9 +170,17 @@ __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__res
       const int pi = bbeg[lb] + (p - off[lb]);
       const float4 h = uhi[pi], q = ulo[pi];
       const float sc = bscale[lb];
-      lagrange_d<NG>(tb, cell_coord_d(h.x, q.x, sc, bc[lb][0]), ws[threadIdx.x][0]);
-      lagrange_d<NG>(tb, cell_coord_d(h.y, q.y, sc, bc[lb][1]), ws[threadIdx.x][1]);
-      lagrange_d<NG>(tb, cell_coord_d(h.z, q.z, sc, bc[lb][2]), ws[threadIdx.x][2]);
+      if constexpr (NG == 4) {
+        // u = 8 xi = 8 (h sc - c) + 8 lo sc: both parts exact in FP32 (powers of two)
+        const float s8 = 8.f * sc;
+        lagrange4_d(fmaf(h.x, s8, -8.f * bc[lb][0]), q.x * s8, ws[threadIdx.x][0]);
+        lagrange4_d(fmaf(h.y, s8, -8.f * bc[lb][1]), q.y * s8, ws[threadIdx.x][1]);
+        lagrange4_d(fmaf(h.z, s8, -8.f * bc[lb][2]), q.z * s8, ws[threadIdx.x][2]);
+      } else {
+        lagrange_d<NG>(tb, cell_coord_d(h.x, q.x, sc, bc[lb][0]), ws[threadIdx.x][0]);
+        lagrange_d<NG>(tb, cell_coord_d(h.y, q.y, sc, bc[lb][1]), ws[threadIdx.x][1]);
+        lagrange_d<NG>(tb, cell_coord_d(h.z, q.z, sc, bc[lb][2]), ws[threadIdx.x][2]);
+      }
       ms[threadIdx.x] = h.w;
     }
     __syncthreads();

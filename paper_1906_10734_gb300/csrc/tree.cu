@@ -188,17 +188,16 @@ __device__ void fill_children_of(int64_t q, int64_t pb, int64_t cb, int level, i
   if (nleaf) atomicAdd(&counters[32 + level], nleaf);
 }
 
-// 27-neighbour table of box i at `level` (-1 where absent): the children of
-// its parent's neighbours.
-__device__ void neighbours_of(int64_t i, int level, const uint64_t *key, const int *parent, const int *child,
-                              int *nb) {
+// 27-neighbour list of box i at `level` into q (-1 where absent): the
+// children of its parent's neighbours (rows of nb and child at level - 1).
+__device__ __forceinline__ void neighbours_of(int64_t i, int level, const uint64_t *key, const int *parent,
+                                              const int *child, const int *nb, int (&q)[27]) {
   const uint64_t k0 = key[i] & ((1ull << (3 * level)) - 1ull);
   const int c[3] = {(int)compact3(k0), (int)compact3(k0 >> 1), (int)compact3(k0 >> 2)};
   const int side = 1 << level;
   const int p = parent[i];
   // the parent's neighbour holding each of the 27 boxes, then its child: two
   // rounds of independent loads (the parent's row is not written at this level)
-  int q[27];
 #pragma unroll
   for (int k = 0; k < 27; ++k) {
     const int n0 = c[0] + k % 3 - 1, n1 = c[1] + (k / 3) % 3 - 1, n2 = c[2] + k / 9 - 1;
@@ -214,8 +213,6 @@ __device__ void neighbours_of(int64_t i, int level, const uint64_t *key, const i
     const int n0 = c[0] + k % 3 - 1, n1 = c[1] + (k / 3) % 3 - 1, n2 = c[2] + k / 9 - 1;
     q[k] = q[k] >= 0 ? child[(int64_t)q[k] * 8 + ((n0 & 1) | ((n1 & 1) << 1) | ((n2 & 1) << 2))] : -1;
   }
-#pragma unroll
-  for (int k = 0; k < 27; ++k) nb[i * 27 + k] = q[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -285,75 +282,123 @@ struct LevelArgs {
   GridBar *gb;
 };
 
-// Level l (1..D) from level l - 1 = [pb, pe):
-//   1. expand: the 27 neighbours of every internal box get kExpand
-//   2. each block takes a contiguous run of boxes: child boundaries (8 lanes
-//      per box, one binary search each), child counts, block-local offsets
-//   3. block offsets from the per-block totals, then the children
-//   4. the neighbour tables of the new boxes
+// Marks the 27 neighbours of internal box i (its row of nb) for expansion.
+__device__ __forceinline__ void mark_neighbours(const int *q, uint8_t *flags) {
+  unsigned int *words = reinterpret_cast<unsigned int *>(flags);
+#pragma unroll
+  for (int k = 0; k < 27; ++k)
+    if (q[k] >= 0) atomicOr(words + (q[k] >> 2), (unsigned int)kExpand << (8 * (q[k] & 3)));
+}
+
+// Level l (1..D) from level l - 1 = [pb, pe), whose boxes already carry their
+// expansion marks:
+//   1. each block takes a contiguous run of boxes: the child boundaries of
+//      its boxes (one binary search per octant, four searches interleaved
+//      per thread), then their child counts and block-local offsets
+//   2. block offsets from the per-block totals, then the children
+//   3. the neighbour tables of the new boxes; an internal one marks its 27
+//      neighbours for the next level's expansion right away
+// Three grid barriers per level (and one after the roots' marks).
 __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
   __shared__ int s_warp[kThreads / 32];
   __shared__ long long s_red[2][kThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x, gtid = (int64_t)blockIdx.x * blockDim.x + tid;
   int64_t pb = a.lvl[0], pe = a.lvl[1];
-  for (int l = 1; l <= a.depth; ++l) {
-    // 1. expansion marks
-    {
-      unsigned int *words = reinterpret_cast<unsigned int *>(a.flags);
-      for (int64_t i = pb + gtid; i < pe; i += gthreads) {
-        if (!(a.flags[i] & kInternal)) continue;
-        int q[27];
+  // the roots' expansion marks (a root's only neighbour is itself)
+  for (int64_t i = pb + gtid; i < pe; i += gthreads)
+    if (a.flags[i] & kInternal) {
+      int q[27];
 #pragma unroll
-        for (int k = 0; k < 27; ++k) q[k] = a.nb[i * 27 + k];
-#pragma unroll
-        for (int k = 0; k < 27; ++k)
-          if (q[k] >= 0) atomicOr(words + (q[k] >> 2), (unsigned int)kExpand << (8 * (q[k] & 3)));
-      }
+      for (int k = 0; k < 27; ++k) q[k] = a.nb[i * 27 + k];
+      mark_neighbours(q, a.flags);
     }
-    if (!grid_sync(a.gb, a.err)) return;
-    // 2. boundaries, counts, block-local offsets
+  if (!grid_sync(a.gb, a.err)) return;
+  for (int l = 1; l <= a.depth; ++l) {
+    // 1. boundaries, counts, block-local offsets
     const int64_t m = pe - pb;
     const int64_t chunk = ((m + gridDim.x - 1) / gridDim.x + 31) & ~int64_t(31);
     const int64_t r0 = min((int64_t)blockIdx.x * chunk, m), r1 = min(r0 + chunk, m);
     const int shift = 3 * (a.depth - l);
     {
-      int carry = 0;
-      for (int64_t rb = r0; rb < r1; rb += kThreads / 8) {
-        const int64_t bi = rb + tid / 8;
-        const int oct = tid & 7;
-        const bool valid = bi < r1;
-        int v = 0, nxt = 0;
-        bool expand = false;
-        if (valid) {
-          const int64_t i = pb + bi;
-          const int bg = a.beg[i], en = a.end[i];
-          expand = (a.flags[i] & kExpand) != 0;
-          v = bg;
-          if (oct > 0 && expand) v = lower_bound_key(a.skeys, bg, en, shift, (a.key[i] << 3) | (uint64_t)oct);
-          nxt = en;
-          a.bnd[bi * 8 + oct] = v;
+      // (box, octant) items of this block: 4 binary searches in lockstep per thread
+      const int64_t nit = 8 * (r1 - r0);
+      for (int64_t t0 = tid; t0 < nit; t0 += 4 * kThreads) {
+        int lo[4], hi[4];
+        uint64_t kc[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int64_t t = t0 + (int64_t)j * kThreads;
+          lo[j] = 0;
+          hi[j] = 0;
+          kc[j] = 0;
+          if (t < nit) {
+            const int64_t i = pb + r0 + t / 8;
+            const int oct = (int)(t & 7);
+            lo[j] = a.beg[i];
+            hi[j] = lo[j];
+            if (oct > 0 && (a.flags[i] & kExpand)) {
+              hi[j] = a.end[i];
+              kc[j] = (a.key[i] << 3) | (uint64_t)oct;
+            }
+          }
         }
-        const int up = __shfl_down_sync(0xffffffffu, v, 1);
-        if (oct < 7) nxt = up;
-        const unsigned mask = __ballot_sync(0xffffffffu, valid && expand && nxt > v);
-        if (lane == 0) s_warp[wid] = __popc(mask);
+        for (;;) {
+          bool any = false;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (lo[j] < hi[j]) {
+              any = true;
+              const int mid = lo[j] + ((hi[j] - lo[j]) >> 1);
+              if ((a.skeys[mid] >> shift) < kc[j]) lo[j] = mid + 1;
+              else hi[j] = mid;
+            }
+          if (!any) break;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int64_t t = t0 + (int64_t)j * kThreads;
+          if (t < nit) a.bnd[r0 * 8 + t] = lo[j];
+        }
+      }
+      __syncthreads();
+      // child counts and their exclusive scan over the block's run of boxes
+      int carry = 0;
+      for (int64_t rb = r0; rb < r1; rb += kThreads) {
+        const int64_t bi = rb + tid;
+        int c = 0;
+        if (bi < r1) {
+          const int64_t i = pb + bi;
+          if (a.flags[i] & kExpand) {
+            const int *b = a.bnd + bi * 8;
+            const int en = a.end[i];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) c += (o < 7 ? b[o + 1] : en) > b[o];
+          }
+        }
+        int inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += v;
+        }
+        if (lane == 31) s_warp[wid] = inc;
         __syncthreads();
         int before = 0, round = 0;
 #pragma unroll
         for (int w = 0; w < kThreads / 32; ++w) {
-          const int c = s_warp[w];
-          before += w < wid ? c : 0;
-          round += c;
+          const int v = s_warp[w];
+          before += w < wid ? v : 0;
+          round += v;
         }
-        if (valid && oct == 0) a.off[bi] = carry + before + __popc(mask & ((1u << lane) - 1u));
+        if (bi < r1) a.off[bi] = carry + before + inc - c;
         carry += round;
         __syncthreads();
       }
       if (tid == 0) a.bsum[blockIdx.x] = carry;
     }
     if (!grid_sync(a.gb, a.err)) return;
-    // 3. this block's first child and the level's total, then the children
+    // 2. this block's first child and the level's total, then the children
     int64_t base, total;
     {
       long long lo = 0, all = 0;
@@ -399,13 +444,18 @@ __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
                        a.bnd, a.off, a.counters);
     }
     if (!grid_sync(a.gb, a.err)) return;
-    // 4. neighbour tables of level l
+    // 3. neighbour tables of level l, expansion marks for level l + 1
     for (int64_t i = pe + gtid; i < ne; i += gthreads) {
-      if (!(a.flags[i] & kReal)) {
+      const uint8_t f = a.flags[i];
+      if (!(f & kReal)) {
         for (int k = 0; k < 27; ++k) a.nb[i * 27 + k] = -1;
         continue;
       }
-      neighbours_of(i, l, a.key, a.parent, a.child, a.nb);
+      int q[27];
+      neighbours_of(i, l, a.key, a.parent, a.child, a.nb, q);
+#pragma unroll
+      for (int k = 0; k < 27; ++k) a.nb[i * 27 + k] = q[k];
+      if (l < a.depth && (f & kInternal)) mark_neighbours(q, a.flags);
     }
     if (!grid_sync(a.gb, a.err)) return;
     pb = pe;
