@@ -109,47 +109,102 @@ __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t n, int s
   hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void k_radix_scatter(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                                int64_t n, int shift, const int *__restrict__ offs, int nblk,
-                                uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out) {
-  constexpr int kWarps = kSortThreads / 32;
-  __shared__ int run[kRadix];
-  __shared__ int wcnt[kWarps][kRadix];
-  __shared__ int wbase[kWarps][kRadix];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  run[threadIdx.x] = offs[(int64_t)threadIdx.x * nblk + blockIdx.x];
-#pragma unroll
-  for (int k = 0; k < kWarps; ++k) wcnt[k][threadIdx.x] = 0;
-  __syncthreads();
+// Stable scatter of one tile (kSortTile consecutive elements) by the current
+// 8-bit digit. Each warp ranks its own 512 elements (16 rounds of 32) within
+// (warp, digit) with warp-private counters, so no block barrier per round;
+// the tile is then put in digit order in shared memory (order within a digit:
+// warp, round, lane, i.e. the input order) and written out with consecutive
+// threads on consecutive positions of each digit's run.
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kWarpRounds = kSortTile / kSortThreads;  // 16 rounds of 32 per warp
+constexpr int kScatterSmem = kSortTile * (int)(sizeof(uint64_t) + sizeof(uint32_t));
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n, int shift,
+    const int *__restrict__ hist, const int *__restrict__ offs, int nblk, uint64_t *__restrict__ keys_out,
+    uint32_t *__restrict__ vals_out) {
+  extern __shared__ __align__(16) unsigned char sraw[];
+  uint64_t *sk = reinterpret_cast<uint64_t *>(sraw);
+  uint32_t *sv = reinterpret_cast<uint32_t *>(sk + kSortTile);
+  __shared__ int wcnt[kSortWarps][kRadix];  // per warp and digit: count, then the warp's offset in the digit
+  __shared__ int dstart[kRadix];            // first position of each digit in the sorted tile
+  __shared__ int gbase[kRadix];             // global position of the tile's first element of each digit
+  __shared__ int wsum[kSortWarps];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll
+  for (int k = 0; k < kSortWarps; ++k) wcnt[k][tid] = 0;
+  {
+    // digit starts: exclusive scan over the digits of this tile's counts
+    const int c = hist[(int64_t)tid * nblk + blockIdx.x];
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    int before = 0;
+#pragma unroll
+    for (int k = 0; k < kSortWarps; ++k) before += k < w ? wsum[k] : 0;
+    dstart[tid] = before + inc - c;
+    gbase[tid] = offs[(int64_t)tid * nblk + blockIdx.x];
+  }
+  __syncthreads();
+  // ranks within (warp, digit), warp by warp
   const unsigned lt = (1u << lane) - 1u;
-  for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+  uint64_t kk[kWarpRounds];
+  uint32_t vv[kWarpRounds];
+  int rk[kWarpRounds];
+  const int64_t wb = base + (int64_t)w * (kWarpRounds * 32);
+#pragma unroll
+  for (int r = 0; r < kWarpRounds; ++r) {
+    const int64_t i = wb + r * 32 + lane;
     const bool valid = i < n;
-    uint64_t key = valid ? keys[i] : 0;
+    const uint64_t key = valid ? keys[i] : 0;
     const int d = valid ? (int)((key >> shift) & 0xff) : kRadix;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const int rank = __popc(peers & lt);
-    if (valid && rank == 0) wcnt[w][d] = __popc(peers);
-    __syncthreads();
-    {
-      const int t = threadIdx.x;
-      int s = run[t];
+    const int leader = __ffs(peers) - 1, rank = __popc(peers & lt);
+    int old = 0;
+    if (valid && rank == 0) {
+      old = wcnt[w][d];
+      wcnt[w][d] = old + __popc(peers);
+    }
+    old = __shfl_sync(0xffffffffu, old, leader);
+    __syncwarp();
+    rk[r] = old + rank;
+    kk[r] = key;
+    vv[r] = valid ? (vals ? vals[i] : (uint32_t)i) : 0u;
+  }
+  __syncthreads();
+  {
+    int s = 0;
 #pragma unroll
-      for (int k = 0; k < kWarps; ++k) {
-        int c = wcnt[k][t];
-        wbase[k][t] = s;
-        wcnt[k][t] = 0;
-        s += c;
-      }
-      run[t] = s;
+    for (int k = 0; k < kSortWarps; ++k) {
+      const int c = wcnt[k][tid];
+      wcnt[k][tid] = s;
+      s += c;
     }
-    __syncthreads();
-    if (valid) {
-      const int pos = wbase[w][d] + rank;
-      keys_out[pos] = key;
-      vals_out[pos] = vals ? vals[i] : (uint32_t)i;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kWarpRounds; ++r) {
+    if (wb + r * 32 + lane < n) {
+      const int d = (int)((kk[r] >> shift) & 0xff);
+      const int pos = dstart[d] + wcnt[w][d] + rk[r];
+      sk[pos] = kk[r];
+      sv[pos] = vv[r];
     }
+  }
+  __syncthreads();
+  const int nt = (int)min((int64_t)kSortTile, n - base);
+  for (int j = tid; j < nt; j += kSortThreads) {
+    const uint64_t key = sk[j];
+    const int d = (int)((key >> shift) & 0xff);
+    const int p = gbase[d] + (j - dstart[d]);
+    keys_out[p] = key;
+    vals_out[p] = sv[j];
   }
 }
 
@@ -190,13 +245,18 @@ hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&val
   DevBuf sub;  // view into scratch for the scan's block sums
   sub.p = offs + hn;
   sub.cap = sizeof(int) * (scan_nb + 64);
+  static bool attr = false;
+  if (!attr) {
+    HPM_CUDA(cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, kScatterSmem));
+    attr = true;
+  }
   bool first = true;
   for (int shift = 0; shift < bits || first; shift += 8) {
     k_radix_hist<<<nblk, kSortThreads, 0, st>>>(keys, n, shift, hist, nblk);
     HPM_LAUNCHED(launches);
     HPM_TRY(exclusive_scan_i32(hist, offs, hn, nullptr, sub, st, launches));
-    k_radix_scatter<<<nblk, kSortThreads, 0, st>>>(keys, first ? nullptr : vals, n, shift, offs,
-                                                    nblk, keys_alt, vals_alt);
+    k_radix_scatter<<<nblk, kSortThreads, kScatterSmem, st>>>(keys, first ? nullptr : vals, n, shift, hist,
+                                                               offs, nblk, keys_alt, vals_alt);
     HPM_LAUNCHED(launches);
     uint64_t *tk = keys;
     keys = keys_alt;

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "hpm_internal.cuh"
 
@@ -56,10 +57,14 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
 // Batched trees: particle i of problem p (offsets[p] <= i < offsets[p+1]) gets
 // the key (p << 3 D) | morton; sorting then groups particles by problem and
 // the levels of all problems are built by the same launches.
-// side_inv2 = 2^-e when the side is the power of two 2^e (division by it is
-// then an exact multiplication, the same IEEE result), else 0.
+// side_exp = e when the side is the power of two 2^e, else kNoPow2. Then
+// v 2^21 = (x - o) 2^(21 - e) exactly, and its floor is read from the bits of
+// the one FP64 subtraction (the same integer as the IEEE evaluation, without
+// its further FP64 instructions, of which this GPU issues few per cycle).
+constexpr int kNoPow2 = -100000;
 __global__ void k_keys(const double *__restrict__ pos, int64_t n, double ox, double oy, double oz,
-                       double side, double side_inv2, int depth, uint64_t *__restrict__ keys,
+                       double side, int side_exp, unsigned long long neg_zero, int depth,
+                       uint64_t *__restrict__ keys,
                        int *__restrict__ err, const int64_t *__restrict__ offsets, int nprob) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -79,13 +84,30 @@ __global__ void k_keys(const double *__restrict__ pos, int64_t n, double ox, dou
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const double diff = __dsub_rn(pos[3 * i + d], o[d]);
-    double v = side_inv2 != 0.0 ? __dmul_rn(diff, side_inv2) : __ddiv_rn(diff, side);
-    if (!(v >= 0.0 && v <= 1.0)) {
-      bad = true;
-      v = 0.0;
+    uint32_t q = 0;
+    if (side_exp != kNoPow2) {
+      unsigned long long b = (unsigned long long)__double_as_longlong(diff);
+      // a negative diff whose scaled value rounds to -0 (|diff| <= neg_zero) counts as 0
+      if ((b >> 63) && (b & 0x7FFFFFFFFFFFFFFFull) <= neg_zero) b = 0;
+      // 0 <= diff <= 2^e, as bit patterns (NaN and negative values order above)
+      if (b > ((unsigned long long)(side_exp + 1023) << 52)) {
+        bad = true;
+      } else {
+        const int E = (int)(b >> 52);  // biased exponent; diff = m 2^(max(E,1) - 1075)
+        const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+        const int sh = 1054 + side_exp - (E ? E : 1);  // >= 31: v 2^21 = m 2^-sh
+        const unsigned long long f = sh >= 64 ? 0ull : (m >> sh);
+        q = f >= 2097151ull ? 2097151u : (uint32_t)f;
+      }
+    } else {
+      double v = __ddiv_rn(diff, side);
+      if (!(v >= 0.0 && v <= 1.0)) {
+        bad = true;
+        v = 0.0;
+      }
+      const double s = floor(__dmul_rn(v, 2097152.0));
+      q = s >= 2097151.0 ? 2097151u : (uint32_t)s;
     }
-    const double s = floor(__dmul_rn(v, 2097152.0));
-    const uint32_t q = s >= 2097151.0 ? 2097151u : (uint32_t)s;
     c[d] = q >> (kMortonBits - depth);
   }
   if (bad) atomicOr(err, kErrDomain);
@@ -629,18 +651,28 @@ hpm_status select_boxes(hpm_plan_s *pl, int64_t b, int64_t e, int mode, DevBuf &
 
 }  // namespace
 
-// 2^-e if side = 2^e exactly, else 0
-static double pow2_inverse(double side) {
+// e if side = 2^e exactly (a normal double), else kNoPow2
+static int pow2_exponent(double side) {
   int e = 0;
   const double f = std::frexp(side, &e);  // side = f 2^e, f in [0.5, 1)
-  return (f == 0.5 && std::isfinite(side)) ? std::ldexp(1.0, 1 - e) : 0.0;
+  return (f == 0.5 && std::isfinite(side) && e - 1 >= -1022 && e - 1 <= 1023) ? e - 1 : kNoPow2;
+}
+
+// Bits of the largest |diff| whose product with 2^-e rounds to zero
+// (2^(e - 1075), ties to even), 0 when there is none but -0.
+static unsigned long long neg_zero_bits(int e) {
+  if (e == kNoPow2 || e < 1) return 0ull;
+  const double t = std::ldexp(1.0, e - 1075);
+  unsigned long long b = 0;
+  std::memcpy(&b, &t, sizeof(b));
+  return b;
 }
 
 hpm_status launch_morton_keys(const hpm_domain &dom, int depth, const double *d_pos, int64_t n,
                               uint64_t *d_keys, int *d_err, cudaStream_t st) {
   if (n <= 0) return HPM_OK;
   k_keys<<<blocks_for(n), kThreads, 0, st>>>(d_pos, n, dom.origin[0], dom.origin[1], dom.origin[2], dom.side,
-                                             pow2_inverse(dom.side), depth, d_keys, d_err, nullptr, 1);
+                                             pow2_exponent(dom.side), neg_zero_bits(pow2_exponent(dom.side)), depth, d_keys, d_err, nullptr, 1);
   HPM_LAUNCHED((int64_t *)nullptr);
   return HPM_OK;
 }
@@ -682,7 +714,8 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   if (nprob > 1)
     HPM_CUDA(cudaMemcpyAsync(t.offsets.p, h_offsets, sizeof(int64_t) * (nprob + 1), cudaMemcpyHostToDevice, st));
   k_keys<<<blocks_for(n), kThreads, 0, st>>>(d_pos, n, pl->dom.origin[0], pl->dom.origin[1],
-                                             pl->dom.origin[2], pl->dom.side, pow2_inverse(pl->dom.side), D,
+                                             pl->dom.origin[2], pl->dom.side, pow2_exponent(pl->dom.side),
+                                             neg_zero_bits(pow2_exponent(pl->dom.side)), D,
                                              t.keys.as<uint64_t>(),
                                              t.err.as<int>(), t.offsets.as<int64_t>(), nprob);
   HPM_LAUNCHED(&launches);
