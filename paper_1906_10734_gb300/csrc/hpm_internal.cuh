@@ -44,6 +44,15 @@ struct DevBuf {
   template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
+// control words of the single-pass scan (a buffer of their own, zeroed when
+// allocated): the tile ticket, one status word per tile, the error word
+struct ScanCtl {
+  unsigned *ticket = nullptr;
+  unsigned long long *status = nullptr;
+  int64_t tiles = 0;
+  int *err = nullptr;
+};
+
 // Constant tables handed to kernels by value.
 struct GridletTables {
   int ng;
@@ -80,6 +89,8 @@ struct TreeDev {
   DevBuf lvl_dev;    // box offsets per level on the device (int64, max_depth + 2)
   DevBuf offsets;    // problem offsets of a batched build (int64, nprob + 1)
   DevBuf counters;   // small device counters
+  DevBuf scan_buf;   // control words of the single-pass scan
+  ScanCtl scan;
 };
 
 struct SolveDev {
@@ -161,12 +172,13 @@ hpm_status launch_morton_keys(const hpm_domain &dom, int depth, const double *d_
 hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int64_t *h_offsets, int nprob,
                       cudaStream_t st);
 // sort.cu
+int64_t scan_tiles(int64_t n);
+hpm_status ensure_scan_ctl(DevBuf &buf, int64_t tiles, int *err, cudaStream_t st, ScanCtl *out);
 hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&vals,
-                            uint32_t *&vals_alt, int64_t n, int bits, DevBuf &scratch,
+                            uint32_t *&vals_alt, int64_t n, int bits, DevBuf &scratch, const ScanCtl &ctl,
                             cudaStream_t st, int64_t *launches);
-hpm_status exclusive_scan_i32(const int *in, int *out, int64_t n, int *d_total, DevBuf &scratch,
+hpm_status exclusive_scan_i32(const int *in, int *out, int64_t n, int *d_total, const ScanCtl &ctl,
                               cudaStream_t st, int64_t *launches);
-// the same with the length on the device: n = d_range[1] - d_range[0] <= max_n
 // solve.cu
 hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, float *d_phi,
                  float *d_acc, cudaStream_t st);

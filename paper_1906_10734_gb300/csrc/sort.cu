@@ -1,13 +1,12 @@
 // Stable LSD radix sort of (u64 key, u32 value) pairs and an exclusive scan,
 // the HBM-bound primitives of the tree build.
+#include <atomic>
+
 #include "hpm_internal.cuh"
 
 namespace hpm {
 namespace {
 
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 4;
-constexpr int kScanTile = kScanThreads * kScanItems;
 
 __device__ __forceinline__ int warp_incl_scan(int v) {
   const int lane = threadIdx.x & 31;
@@ -38,54 +37,98 @@ __device__ __forceinline__ int block_excl_scan(int v, int *ex, int *sh_warp) {
   return total;
 }
 
-__global__ void k_scan_reduce(const int *__restrict__ in, int64_t n, int *__restrict__ sums) {
-  __shared__ int sh[32];
-  const int64_t base = (int64_t)blockIdx.x * kScanTile;
-  int s = 0;
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-    if (i < n) s += in[i];
-  }
-  int ex;
-  int tot = block_excl_scan(s, &ex, sh);
-  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+// Single-pass exclusive scan with decoupled look-back. Tiles are handed out
+// in the order of a ticket counter, so every tile's predecessors are running
+// or finished; each tile publishes its sum at once and its inclusive prefix
+// as soon as it knows it, and reads back over its predecessors' published
+// values (one warp, 32 tiles per step) until it meets a prefix. A status word
+// is (flag << 62) | (epoch << 32) | value with flag 1 = sum, 2 = prefix; the
+// epoch tags one call, so the words never need clearing. The last tile to
+// take a ticket resets the counter for the next call. Waits are bounded: a
+// wait that runs out sets kErrTimeout and the tile goes on with what it has.
+constexpr int kLbThreads = 256, kLbItems = 8, kLbTile = kLbThreads * kLbItems;
+
+__device__ __forceinline__ void st_release64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
 }
 
-// Single block: exclusive scan of the block sums in place; writes the total.
-__global__ void k_scan_sums(int *__restrict__ sums, int64_t nb, int *__restrict__ total) {
+__global__ void __launch_bounds__(kLbThreads) k_scan_lb(const int *__restrict__ in, int *__restrict__ out, int64_t n,
+                                                        int *__restrict__ total, unsigned *ticket,
+                                                        unsigned long long *status, unsigned epoch, int ntiles,
+                                                        int *err) {
   __shared__ int sh[32];
-  int run = 0;
-  for (int64_t c = 0; c < nb; c += kScanThreads) {
-    int64_t i = c + threadIdx.x;
-    int v = i < nb ? sums[i] : 0;
-    int ex;
-    int tot = block_excl_scan(v, &ex, sh);
-    if (i < nb) sums[i] = run + ex;
-    run += tot;
+  __shared__ int s_tile, s_prefix;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(ticket, 1u);
+    if (t == (unsigned)ntiles - 1) atomicExch(ticket, 0u);
+    s_tile = (int)t;
   }
-  if (threadIdx.x == 0 && total) *total = run;
-}
-
-__global__ void k_scan_apply(const int *__restrict__ in, int *__restrict__ out, int64_t n,
-                             const int *__restrict__ sums) {
-  __shared__ int sh[32];
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-  int v[kScanItems];
-  int s = 0;
+  __syncthreads();
+  const int tile = s_tile;
+  const int64_t base = (int64_t)tile * kLbTile + (int64_t)threadIdx.x * kLbItems;
+  int v[kLbItems];
+  int sum = 0;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
+  for (int k = 0; k < kLbItems; ++k) {
     v[k] = base + k < n ? in[base + k] : 0;
-    s += v[k];
+    sum += v[k];
   }
   int ex;
-  block_excl_scan(s, &ex, sh);
-  int run = sums[blockIdx.x] + ex;
+  const int agg = block_excl_scan(sum, &ex, sh);
+  const unsigned long long tag = (unsigned long long)(epoch & 0x3FFFFFFFu) << 32;
+  if (threadIdx.x < 32) {
+    int prefix = 0;
+    if (tile == 0) {
+      if (lane == 0) st_release64(status, (2ull << 62) | tag | (unsigned)agg);
+    } else {
+      if (lane == 0) st_release64(status + tile, (1ull << 62) | tag | (unsigned)agg);
+      bool ok = true;
+      for (int j = tile - 1;; j -= 32) {
+        const int idx = j - lane;
+        int flag = 2, val = 0;
+        if (idx >= 0) {
+          unsigned long long w = 0;
+          for (long it = 0;; ++it) {
+            w = ld_acquire64(status + idx);
+            if ((w & (0x3FFFFFFFull << 32)) == tag && (w >> 62)) break;
+            if (it > (1l << 22)) {
+              ok = false;
+              w = (2ull << 62) | tag;  // give up: take it as a zero prefix
+              break;
+            }
+            __nanosleep(32);
+          }
+          flag = (int)(w >> 62);
+          val = (int)(unsigned)w;
+        }
+        const unsigned pm = __ballot_sync(0xffffffffu, flag == 2);
+        const int first = pm ? __ffs(pm) - 1 : 32;  // nearest published prefix in this window
+        int add = lane <= first ? val : 0;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    if (base + k < n) out[base + k] = run;
-    run += v[k];
+        for (int o = 16; o >= 1; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+        prefix += add;
+        if (pm) break;
+      }
+      if (!__all_sync(0xffffffffu, ok) && lane == 0 && err) atomicOr(err, kErrTimeout);
+      if (lane == 0) st_release64(status + tile, (2ull << 62) | tag | (unsigned)(prefix + agg));
+    }
+    if (lane == 0) s_prefix = prefix;
   }
+  __syncthreads();
+  int run = s_prefix + ex;
+#pragma unroll
+  for (int k = 0; k < kLbItems; ++k)
+    if (base + k < n) {
+      out[base + k] = run;
+      run += v[k];
+    }
+  if (total && tile == ntiles - 1 && threadIdx.x == 0) *total = s_prefix + agg;
 }
 
 // ---------------------------------------------------------------------------
@@ -210,21 +253,34 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
 
 }  // namespace
 
-hpm_status exclusive_scan_i32(const int *in, int *out, int64_t n, int *d_total, DevBuf &scratch,
+hpm_status exclusive_scan_i32(const int *in, int *out, int64_t n, int *d_total, const ScanCtl &ctl,
                               cudaStream_t st, int64_t *launches) {
   if (n <= 0) {
     if (d_total) HPM_CUDA(cudaMemsetAsync(d_total, 0, sizeof(int), st));
     return HPM_OK;
   }
-  const int64_t nb = (n + kScanTile - 1) / kScanTile;
-  HPM_TRY(scratch.ensure(sizeof(int) * nb, st));
-  int *sums = scratch.as<int>();
-  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums);
+  const int64_t nt = (n + kLbTile - 1) / kLbTile;
+  if (nt > ctl.tiles) return HPM_ERR_INVALID_ARG;
+  static std::atomic<unsigned> epoch{1};
+  k_scan_lb<<<(unsigned)nt, kLbThreads, 0, st>>>(in, out, n, d_total, ctl.ticket, ctl.status,
+                                                  epoch.fetch_add(1u), (int)nt, ctl.err);
   HPM_LAUNCHED(launches);
-  k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, nb, d_total);
-  HPM_LAUNCHED(launches);
-  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums);
-  HPM_LAUNCHED(launches);
+  return HPM_OK;
+}
+
+int64_t scan_tiles(int64_t n) { return (n + kLbTile - 1) / kLbTile; }
+
+// Control words of the scan in a buffer of its own, zeroed when it grows.
+hpm_status ensure_scan_ctl(DevBuf &buf, int64_t tiles, int *err, cudaStream_t st, ScanCtl *out) {
+  const size_t bytes = 256 + sizeof(unsigned long long) * (size_t)(tiles > 0 ? tiles : 1);
+  if (bytes > buf.cap || !buf.p) {
+    HPM_TRY(buf.ensure(bytes, st));
+    HPM_CUDA(cudaMemsetAsync(buf.p, 0, buf.cap, st));
+  }
+  out->ticket = buf.as<unsigned>();
+  out->status = reinterpret_cast<unsigned long long *>(buf.as<unsigned char>() + 256);
+  out->tiles = (int64_t)((buf.cap - 256) / sizeof(unsigned long long));
+  out->err = err;
   return HPM_OK;
 }
 
@@ -233,18 +289,14 @@ hpm_status exclusive_scan_i32(const int *in, int *out, int64_t n, int *d_total, 
 // buffers). vals may be null on entry: the original index is used then (the
 // first pass writes it).
 hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&vals,
-                            uint32_t *&vals_alt, int64_t n, int bits, DevBuf &scratch,
+                            uint32_t *&vals_alt, int64_t n, int bits, DevBuf &scratch, const ScanCtl &ctl,
                             cudaStream_t st, int64_t *launches) {
   if (n <= 0) return HPM_OK;
   const int nblk = (int)((n + kSortTile - 1) / kSortTile);
   const int64_t hn = (int64_t)kRadix * nblk;
-  const int64_t scan_nb = (hn + kScanTile - 1) / kScanTile;
-  HPM_TRY(scratch.ensure(sizeof(int) * (2 * hn + scan_nb + 64), st));
+  HPM_TRY(scratch.ensure(sizeof(int) * 2 * hn, st));
   int *hist = scratch.as<int>();
   int *offs = hist + hn;
-  DevBuf sub;  // view into scratch for the scan's block sums
-  sub.p = offs + hn;
-  sub.cap = sizeof(int) * (scan_nb + 64);
   static bool attr = false;
   if (!attr) {
     HPM_CUDA(cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, kScatterSmem));
@@ -254,7 +306,7 @@ hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&val
   for (int shift = 0; shift < bits || first; shift += 8) {
     k_radix_hist<<<nblk, kSortThreads, 0, st>>>(keys, n, shift, hist, nblk);
     HPM_LAUNCHED(launches);
-    HPM_TRY(exclusive_scan_i32(hist, offs, hn, nullptr, sub, st, launches));
+    HPM_TRY(exclusive_scan_i32(hist, offs, hn, nullptr, ctl, st, launches));
     k_radix_scatter<<<nblk, kSortThreads, kScatterSmem, st>>>(keys, first ? nullptr : vals, n, shift, hist,
                                                                offs, nblk, keys_alt, vals_alt);
     HPM_LAUNCHED(launches);
@@ -266,8 +318,6 @@ hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&val
     vals_alt = tv;
     first = false;
   }
-  sub.p = nullptr;  // not owned
-  sub.cap = 0;
   return HPM_OK;
 }
 

@@ -11,13 +11,14 @@ constexpr int64_t kMaxN = HPM_STATIC_SORT_MAX_N;
 constexpr int64_t kTile = 4096;                              // particles per sort block
 constexpr int64_t kMaxBlocks = (kMaxN + kTile - 1) / kTile;
 constexpr int64_t kHist = 256 * kMaxBlocks;                  // digit x block counters
-constexpr int64_t kScanSums = (kHist + 4095) / 4096 + 64;
+constexpr int64_t kScanStatus = (kHist + 2047) / 2048 + 64;    // tiles of the histogram scan
 constexpr size_t kHeader = 256;                              // error word
 constexpr size_t kKeysOff = kHeader;
 constexpr size_t kPermOff = kKeysOff + sizeof(uint64_t) * kMaxN;
 constexpr size_t kHistOff = kPermOff + sizeof(uint32_t) * kMaxN;
-constexpr size_t kHistBytes = sizeof(int) * (2 * kHist + kScanSums);
-constexpr size_t kBytes = kHistOff + kHistBytes;
+constexpr size_t kHistBytes = sizeof(int) * 2 * kHist;
+constexpr size_t kScanOff = (kHistOff + kHistBytes + 255) / 256 * 256;  // ticket, then status words
+constexpr size_t kBytes = kScanOff + 256 + sizeof(unsigned long long) * kScanStatus;
 
 // Held by every device that loads the library, for the life of the process.
 static __device__ __align__(256) unsigned char g_sort_scratch[kBytes];
@@ -67,7 +68,14 @@ extern "C" hpm_status hpm_sort_particles_static(const hpm_domain *dom, int max_d
   hist.cap = kHistBytes;
   uint64_t *k0 = d_keys, *k1 = reinterpret_cast<uint64_t *>(b + kKeysOff);
   uint32_t *v0 = d_perm, *v1 = reinterpret_cast<uint32_t *>(b + kPermOff);
-  hpm_status s = radix_sort_pairs(k0, k1, v0, v1, n, 3 * max_depth, hist, st, nullptr);
+  // the scan's control words (zero when the library is loaded; the scan
+  // leaves its ticket at zero and tags its status words per call)
+  ScanCtl ctl;
+  ctl.ticket = reinterpret_cast<unsigned *>(b + kScanOff);
+  ctl.status = reinterpret_cast<unsigned long long *>(b + kScanOff + 256);
+  ctl.tiles = kScanStatus;
+  ctl.err = err;
+  hpm_status s = radix_sort_pairs(k0, k1, v0, v1, n, 3 * max_depth, hist, ctl, st, nullptr);
   hist.p = nullptr;
   hist.cap = 0;
   if (s != HPM_OK) return s;
@@ -76,5 +84,6 @@ extern "C" hpm_status hpm_sort_particles_static(const hpm_domain *dom, int max_d
   int h_err = 0;
   HPM_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   HPM_CUDA(cudaStreamSynchronize(st));
+  if (h_err & kErrTimeout) return HPM_ERR_TIMEOUT;
   return (h_err & kErrDomain) ? HPM_ERR_OUT_OF_DOMAIN : HPM_OK;
 }

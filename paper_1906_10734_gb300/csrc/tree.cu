@@ -160,18 +160,6 @@ __global__ void k_roots(int nprob, int64_t n, int depth, int leaf_max, const int
   if (!internal) atomicAdd(&counters[32 + 0], 1);
 }
 
-// First index in [lo, hi) whose level-l key is >= kc.
-__device__ __forceinline__ int lower_bound_key(const uint64_t *__restrict__ skeys, int lo, int hi,
-                                               int shift, uint64_t kc) {
-  while (lo < hi) {
-    const int mid = lo + ((hi - lo) >> 1);
-    if ((skeys[mid] >> shift) < kc) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
-
 // The helpers below run inside the cooperative level kernel, where the box
 // arrays are written by other blocks between grid barriers: plain coherent
 // loads only (no __restrict__, no read-only cache path).
@@ -642,8 +630,8 @@ hpm_status select_boxes(hpm_plan_s *pl, int64_t b, int64_t e, int mode, DevBuf &
   HPM_TRY(t.off.ensure(sizeof(int) * (n + 1), st));
   k_select<<<blocks_for(n), kThreads, 0, st>>>(b, e, t.box_flags.as<uint8_t>(), mode, t.cnt.as<int>());
   HPM_LAUNCHED(launches);
-  HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), n, t.counters.as<int>() + total_slot, t.keys_alt,
-                             st, launches));
+  HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), n, t.counters.as<int>() + total_slot, t.scan, st,
+                             launches));
   k_compact<<<blocks_for(n), kThreads, 0, st>>>(b, e, t.cnt.as<int>(), t.off.as<int>(), out.as<int>());
   HPM_LAUNCHED(launches);
   return HPM_OK;
@@ -688,6 +676,10 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   HPM_TRY(t.counters.ensure(sizeof(int) * 128, st));
   HPM_CUDA(cudaMemsetAsync(t.err.p, 0, sizeof(int) * 4, st));
   HPM_CUDA(cudaMemsetAsync(t.counters.p, 0, sizeof(int) * 128, st));
+  // scans of the build: sort histograms (n / 16), problems, boxes (up to the
+  // box capacity, grown below if needed), leaves
+  HPM_TRY(ensure_scan_ctl(t.scan_buf, scan_tiles(std::max<int64_t>(std::max<int64_t>(n, nprob), n / 4 + 4096) + 1),
+                          t.err.as<int>(), st, &t.scan));
 
   pl->lvl_off.assign(D + 2, 0);
   pl->depth_reached = -1;
@@ -722,7 +714,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   uint64_t *k0 = t.keys.as<uint64_t>(), *k1 = t.keys_alt.as<uint64_t>();
   uint32_t *v0 = t.perm.as<uint32_t>(), *v1 = t.perm_alt.as<uint32_t>();
   DevBuf &scratch = t.off;
-  HPM_TRY(radix_sort_pairs(k0, k1, v0, v1, n, 3 * D + pbits, scratch, st, &launches));
+  HPM_TRY(radix_sort_pairs(k0, k1, v0, v1, n, 3 * D + pbits, scratch, t.scan, st, &launches));
   // keep the sorted arrays in keys/perm
   if (k0 != t.keys.as<uint64_t>()) {
     std::swap(t.keys.p, t.keys_alt.p);
@@ -741,7 +733,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   k_problem_ranges<<<blocks_for(nprob), kThreads, 0, st>>>(nprob, n, skeys, 3 * D, t.bnd.as<int>(),
                                                            t.cnt.as<int>());
   HPM_LAUNCHED(&launches);
-  HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), nprob, t.counters.as<int>() + 64, t.keys_alt, st,
+  HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), nprob, t.counters.as<int>() + 64, t.scan, st,
                              &launches));
   int nroot = 0;
   HPM_CUDA(cudaMemcpyAsync(&nroot, t.counters.as<int>() + 64, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -751,6 +743,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   int64_t cap = t.box_key.cap / sizeof(uint64_t);
   cap = std::max<int64_t>(cap, std::max<int64_t>(1024 + 2 * (int64_t)nroot, n / 4 + 1024));
   HPM_TRY(ensure_boxes(t, cap, st));
+  HPM_TRY(ensure_scan_ctl(t.scan_buf, scan_tiles(cap + 1), t.err.as<int>(), st, &t.scan));
   k_roots<<<blocks_for(nprob), kThreads, 0, st>>>(nprob, n, D, pl->opts.leaf_max, t.bnd.as<int>(), t.cnt.as<int>(),
                                                   t.off.as<int>(), t.box_key.as<uint64_t>(), t.box_beg.as<int>(),
                                                   t.box_end.as<int>(), t.box_parent.as<int>(),
@@ -826,6 +819,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     // and the error word are reset)
     cap *= 2;
     HPM_TRY(ensure_boxes(t, cap, st));
+    HPM_TRY(ensure_scan_ctl(t.scan_buf, scan_tiles(cap + 1), t.err.as<int>(), st, &t.scan));
     HPM_CUDA(cudaMemsetAsync(t.err.p, 0, sizeof(int), st));
     HPM_CUDA(cudaMemsetAsync(t.counters.as<int>() + 1, 0, sizeof(int) * 31, st));
     HPM_CUDA(cudaMemsetAsync(t.counters.as<int>() + 33, 0, sizeof(int) * 31, st));
@@ -887,7 +881,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
                                                             t.box_end.as<int>(), t.cnt.as<int>());
     HPM_LAUNCHED(&launches);
     HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.p2g_off.as<int>(), pl->np2g, t.p2g_off.as<int>() + pl->np2g,
-                               t.keys_alt, st, &launches));
+                               t.scan, st, &launches));
   }
   // leaf of every particle
   HPM_TRY(t.pbox.ensure(sizeof(int) * (n > 0 ? n : 1), st));
@@ -908,12 +902,14 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
                                                      t.leaf_nitem.as<int>(), t.cnt.as<int>());
     HPM_LAUNCHED(&launches);
     HPM_TRY(exclusive_scan_i32(t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(), nl, t.counters.as<int>() + 64,
-                               t.keys_alt, st, &launches));
+                               t.scan, st, &launches));
     HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.leaf_part0.as<int>(), nl, t.counters.as<int>() + 65,
-                               t.keys_alt, st, &launches));
-    int hv[10] = {0};
+                               t.scan, st, &launches));
+    int hv[10] = {0}, herr2 = 0;
     HPM_CUDA(cudaMemcpyAsync(hv, t.counters.as<int>() + 64, sizeof(int) * 10, cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaMemcpyAsync(&herr2, t.err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaStreamSynchronize(st));
+    if (herr2 & kErrTimeout) return HPM_ERR_TIMEOUT;
     pl->nitem = hv[0];
     pl->npart = hv[1];
     // the work-list sizes the host derived must be what the device selected
