@@ -238,6 +238,11 @@ def run_gpu(args) -> None:
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
+    # launch shapes picked by the library's autotuner on this input (untimed;
+    # results are the same for every shape)
+    tuning = hpm.hpm_tune(plan, pos, mass, stream) if not args.no_tune else hpm.hpm_get_tuning(plan)
+    step()
+    torch.cuda.synchronize(dev)
     info = hpm.hpm_get_lists_info(plan)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -298,6 +303,7 @@ def run_gpu(args) -> None:
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_of(w.n, w.max_depth, w.leaf_max, w.ng, w.eps, {"parallelism": "replicas" if world > 1 else "single",
                                 "l2": "flushed between steps (256 MiB write outside the timed events)",
+                                "tuning": tuning,
                                 "cells": info["n_cells"], "targets": info["n_targets"],
                                 "leaves": info["n_leaves"], "boxes": info["n_boxes"],
                                 "depth_reached": info["depth_reached"]}),
@@ -506,6 +512,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1 << 15)
     ap.add_argument("--ref-sample", type=int, default=1 << 14)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -259,6 +259,38 @@ typedef struct {
 hpm_status hpm_get_stats(hpm_plan_t plan, hpm_stats *stats);
 
 /* ------------------------------------------------------------------------
+ * Launch shapes and their autotuner (an implementation choice; the paper
+ * has none). Every shape here changes only how the work is spread over the
+ * GPU: results are bit for bit the same for every value.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int level_blocks_per_sm; /* tree build: CTAs per SM of the cooperative level
+                              kernel, 1..4 (0 = 2; capped at what fits)          */
+  int gridlet_warps;       /* Ng = 4 child-to-parent and parent-to-child: warps
+                              (one gridlet each) per CTA, 2, 4 or 8 (0 = 8)      */
+  int m2l_ctas_per_sm;     /* FFT-form source-to-target kernels (HPM_FLAG_FFT_M2L,
+                              HPM_FLAG_XTRANSFORM_M2L, Ng != 4): persistent CTAs
+                              per SM, 1 or 2 (0 = the most that fit)             */
+} hpm_tuning;
+
+/* Sets the plan's launch shapes (values outside the ranges above are
+ * HPM_ERR_INVALID_ARG); they apply from the next build / solve. */
+hpm_status hpm_set_tuning(hpm_plan_t plan, const hpm_tuning *tuning);
+hpm_status hpm_get_tuning(hpm_plan_t plan, hpm_tuning *tuning);
+
+/* Autotuner: builds and solves the given input (device positions and masses,
+ * N x 3 and N FP64, as hpm_solve) for each candidate value of one shape at a
+ * time, the others fixed, timing the stage the shape drives with CUDA events
+ * on `stream` (best of three runs per candidate), and keeps the fastest in
+ * the plan; `out` (may be null) receives the result. Shapes that do not apply
+ * to the plan (m2l_ctas_per_sm on the Ng = 4 tensor-core path, gridlet_warps
+ * at Ng != 4) keep their current value. Uses plan-owned output buffers,
+ * synchronises the stream, leaves the plan built for this input.
+ * Errors: those of hpm_build_tree and hpm_solve. */
+hpm_status hpm_tune(hpm_plan_t plan, const double *d_pos, const double *d_mass, int64_t n, void *stream,
+                    hpm_tuning *out);
+
+/* ------------------------------------------------------------------------
  * Serving: continuous batching of independent solves (no counterpart in the
  * paper; it serves the same solve to a stream of requests).
  * ------------------------------------------------------------------------ */

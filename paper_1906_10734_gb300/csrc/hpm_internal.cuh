@@ -159,6 +159,7 @@ struct hpm_plan_s {
   std::vector<int64_t> tgt_lvl_off;  // target offsets per level (levels 2..D)
   std::vector<int64_t> leaf_lvl_off;
   hpm_stats stats{};
+  hpm_tuning tuning{};             // launch shapes (0 = default), see hpm_set_tuning
   cudaEvent_t ev[12] = {};  // stage boundaries 0..7, tree 8..9, dense product kernel 10..11
   bool events_ready = false;
   hpm::DevBuf host_io_pos, host_io_mass, host_io_phi, host_io_acc;
@@ -180,6 +181,11 @@ hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&val
 hpm_status exclusive_scan_i32(const int *in, int *out, int64_t n, int *d_total, const ScanCtl &ctl,
                               cudaStream_t st, int64_t *launches);
 // solve.cu
+// warps (gridlets) per CTA of the Ng = 4 child-to-parent and parent-to-child kernels
+inline int gridlet_warps(const hpm_plan_s *pl) {
+  const int w = pl->tuning.gridlet_warps;
+  return (w == 2 || w == 4) ? w : 8;
+}
 hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, float *d_phi,
                  float *d_acc, cudaStream_t st);
 hpm_status precompute_green(hpm_plan_s *pl, cudaStream_t st);

@@ -714,7 +714,8 @@ hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
       HPM_CUDA(cudaFuncSetAttribute(f4::k_m2l4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f4::kSmem));
       attr = true;
     }
-    const int64_t grid = std::min<int64_t>(pl->ntgt, (int64_t)2 * nsm);
+    const int per_sm = pl->tuning.m2l_ctas_per_sm == 1 ? 1 : 2;  // 2 fit (111 KB each)
+    const int64_t grid = std::min<int64_t>(pl->ntgt, (int64_t)per_sm * nsm);
     f4::k_m2l4<<<(unsigned)grid, f4::kThreads, f4::kSmem, st>>>(p);
     HPM_LAUNCHED(launches);
     return HPM_OK;
@@ -730,7 +731,8 @@ hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
     p.npar = pl->npar;
     p.kxg = pl->kx_green.as<float>();
     p.kx_stride = pl->kx_green_stride;
-    const int per_sm = pl->ng <= 4 ? 2 : 1;
+    // persistent CTAs per SM: two fit up to Ng = 4, one above; the tuner may take fewer
+    const int per_sm = std::min(pl->ng <= 4 ? 2 : 1, pl->tuning.m2l_ctas_per_sm > 0 ? pl->tuning.m2l_ctas_per_sm : 2);
     const int64_t grid = std::min<int64_t>(pl->npar, (int64_t)nsm * per_sm);
     if (grid <= 0) return HPM_OK;
     switch (pl->ng) {

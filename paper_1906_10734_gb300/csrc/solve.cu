@@ -257,18 +257,20 @@ __global__ void __launch_bounds__(kGThreads) k_m2m(int64_t b, int64_t e, Gridlet
 // over the child octants: M^P = sum_cz Tz (sum_cy Ty (sum_cx Tx M^(cx,cy,cz)))
 // (T^{a} of the x, y, z axes as in k_m2m). The 8 children are loaded at once;
 // the x stage forms 4 gridlets (summed over cx), y forms 2, z the parent.
-constexpr int kM2MWarps = 8;
-__global__ void __launch_bounds__(kM2MWarps * 32) k_m2m4(int64_t b, int64_t e, GridletTables tb,
+// kW warps (gridlets) per CTA: a launch shape the tuner picks (2, 4 or 8);
+// each warp's arithmetic is the same whatever kW.
+template <int kW>
+__global__ void __launch_bounds__(kW * 32) k_m2m4(int64_t b, int64_t e, GridletTables tb,
                                                          const uint8_t *__restrict__ flags,
                                                          const int *__restrict__ child, int64_t off2,
                                                          float *__restrict__ grid) {
   __shared__ float T[2][4][4];
-  __shared__ float ch[kM2MWarps][8][64], X[kM2MWarps][4][64], Y[kM2MWarps][2][64];
+  __shared__ float ch[kW][8][64], X[kW][4][64], Y[kW][2][64];
   if (threadIdx.x < 32) T[threadIdx.x >> 4][(threadIdx.x >> 2) & 3][threadIdx.x & 3] =
       tb.t1[threadIdx.x >> 4][(threadIdx.x >> 2) & 3][threadIdx.x & 3];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t box = b + (int64_t)blockIdx.x * kM2MWarps + w;
+  const int64_t box = b + (int64_t)blockIdx.x * kW + w;
   if (box >= e || !(flags[box] & kInternal)) return;
   {
     // child o = lane / 4, 16 values each
@@ -328,7 +330,8 @@ __global__ void __launch_bounds__(kM2MWarps * 32) k_m2m4(int64_t b, int64_t e, G
 
 // Ng = 4 parent-to-child as k_l2l, one target per warp with the three axis
 // passes unrolled: loc_C = (Tx^T (x) Ty^T (x) Tz^T) loc_P + own values.
-__global__ void __launch_bounds__(kM2MWarps * 32) k_l2l4(int64_t tb0, int64_t tb1, int level, GridletTables tab,
+template <int kW>
+__global__ void __launch_bounds__(kW * 32) k_l2l4(int64_t tb0, int64_t tb1, int level, GridletTables tab,
                                                          const int *__restrict__ tgt_box,
                                                          const int *__restrict__ box_tgt,
                                                          const int *__restrict__ parent,
@@ -336,12 +339,12 @@ __global__ void __launch_bounds__(kM2MWarps * 32) k_l2l4(int64_t tb0, int64_t tb
                                                          const float *__restrict__ raw, float *__restrict__ loc,
                                                          float *__restrict__ locc, const float *__restrict__ m2lc) {
   __shared__ float T[2][4][4];
-  __shared__ float A[kM2MWarps][64], B[kM2MWarps][64];
+  __shared__ float A[kW][64], B[kW][64];
   if (threadIdx.x < 32) T[threadIdx.x >> 4][(threadIdx.x >> 2) & 3][threadIdx.x & 3] =
       tab.t1[threadIdx.x >> 4][(threadIdx.x >> 2) & 3][threadIdx.x & 3];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t t = tb0 + (int64_t)blockIdx.x * kM2MWarps + w;
+  const int64_t t = tb0 + (int64_t)blockIdx.x * kW + w;
   if (t >= tb1) return;
   const float2 own = reinterpret_cast<const float2 *>(raw + t * 64)[lane];
   float r0 = own.x, r1 = own.y;  // nodes 2 lane, 2 lane + 1
@@ -976,10 +979,12 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
   for (int l = pl->depth_reached - 1; l >= 2; --l) {
     const int64_t b = pl->lvl_off[l], e = pl->lvl_off[l + 1];
     if (e <= b) continue;
-    if (ng == 4)
-      k_m2m4<<<(unsigned)((e - b + kM2MWarps - 1) / kM2MWarps), kM2MWarps * 32, 0, st>>>(
-          b, e, pl->tab, t.box_flags.as<uint8_t>(), t.box_child.as<int>(), off2, s.grid.as<float>());
-    else
+    if (ng == 4) {
+      const int W = gridlet_warps(pl);
+      auto km = W == 2 ? k_m2m4<2> : (W == 4 ? k_m2m4<4> : k_m2m4<8>);
+      km<<<(unsigned)((e - b + W - 1) / W), W * 32, 0, st>>>(b, e, pl->tab, t.box_flags.as<uint8_t>(),
+                                                            t.box_child.as<int>(), off2, s.grid.as<float>());
+    } else
       k_m2m<<<gwarp_blocks(e - b), kGThreads, 0, st>>>(b, e, pl->tab, t.box_flags.as<uint8_t>(),
                                                      t.box_child.as<int>(), off2, s.grid.as<float>());
     HPM_LAUNCHED(&launches);
@@ -995,12 +1000,14 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
   for (int l = 2; l <= pl->depth_reached; ++l) {
     const int64_t b = pl->tgt_lvl_off[l], e = pl->tgt_lvl_off[l + 1];
     if (e <= b) continue;
-    if (ng == 4)
-      k_l2l4<<<(unsigned)((e - b + kM2MWarps - 1) / kM2MWarps), kM2MWarps * 32, 0, st>>>(
+    if (ng == 4) {
+      const int W = gridlet_warps(pl);
+      auto kl = W == 2 ? k_l2l4<2> : (W == 4 ? k_l2l4<4> : k_l2l4<8>);
+      kl<<<(unsigned)((e - b + W - 1) / W), W * 32, 0, st>>>(
           b, e, l, pl->tab, t.tgt_box.as<int>(), t.box_tgt.as<int>(), t.box_parent.as<int>(),
           t.box_key.as<uint64_t>(), s.m2l_raw.as<float>(), s.loc.as<float>(), s.locc.as<float>(),
           s.m2lc.as<float>());
-    else
+    } else
       k_l2l<<<gwarp_blocks(e - b), kGThreads, 0, st>>>(b, e, l, pl->tab, t.tgt_box.as<int>(), t.box_tgt.as<int>(),
                                                      t.box_parent.as<int>(), t.box_key.as<uint64_t>(),
                                                      s.m2l_raw.as<float>(), s.loc.as<float>(), s.locc.as<float>(),

@@ -756,13 +756,14 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   int hc[64];
   // Levels 1..D in one cooperative launch (all blocks resident, grid-wide
   // barriers between the phases of a level); one read-back at the end.
-  static int level_grid = 0;
-  if (!level_grid) {
-    int per_sm = 0;
-    HPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels, kThreads, 0));
-    level_grid = std::min(per_sm, 2) * sm_count();
-    if (level_grid <= 0) return HPM_ERR_CUDA;
+  static int level_max_per_sm = 0;  // resident CTAs per SM the kernel allows
+  if (!level_max_per_sm) {
+    HPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&level_max_per_sm, k_levels, kThreads, 0));
+    if (level_max_per_sm <= 0) return HPM_ERR_CUDA;
   }
+  // CTAs per SM: the plan's tuned value (2 by default), never above what fits
+  const int level_per_sm = std::min(level_max_per_sm, pl->tuning.level_blocks_per_sm > 0 ? pl->tuning.level_blocks_per_sm : 2);
+  const int level_grid = level_per_sm * sm_count();
   for (int attempt = 0;; ++attempt) {
     HPM_TRY(t.cnt.ensure(sizeof(int) * level_grid, st));
     HPM_TRY(t.off.ensure(sizeof(int) * (cap + 1), st));

@@ -76,6 +76,11 @@ class hpm_stats(ctypes.Structure):
                 ("ms_m2l_kernel", ctypes.c_float), ("m2l_parents", ctypes.c_int64)]
 
 
+class hpm_tuning(ctypes.Structure):
+    _fields_ = [("level_blocks_per_sm", ctypes.c_int), ("gridlet_warps", ctypes.c_int),
+                ("m2l_ctas_per_sm", ctypes.c_int)]
+
+
 SIGNATURES = {
     "hpm_plan": ([ctypes.POINTER(hpm_domain), _i32, _i32, ctypes.POINTER(hpm_green),
                   ctypes.POINTER(hpm_plan_opts), ctypes.POINTER(_vp)], _i32),
@@ -98,6 +103,9 @@ SIGNATURES = {
     "hpm_server_get_stats": ([_vp, ctypes.POINTER(hpm_server_stats)], _i32),
     "hpm_server_reset_stats": ([_vp], _i32),
     "hpm_server_destroy": ([_vp], _i32),
+    "hpm_set_tuning": ([_vp, ctypes.POINTER(hpm_tuning)], _i32),
+    "hpm_get_tuning": ([_vp, ctypes.POINTER(hpm_tuning)], _i32),
+    "hpm_tune": ([_vp, _vp, _vp, _i64, _vp, ctypes.POINTER(hpm_tuning)], _i32),
     "hpm_destroy": ([_vp], _i32),
     "hpm_status_str": ([_i32], ctypes.c_char_p),
     "hpm_last_cuda_error": ([], ctypes.c_char_p),
@@ -246,6 +254,25 @@ def hpm_get_stage(plan: int, stage: int, ng: int) -> np.ndarray:
     vals = out[:nt * m3].reshape(nt, m3)
     const = out[nt * m3:nt * m3 + nt]
     return np.concatenate([vals, const[:, None]], axis=1)
+
+
+def hpm_set_tuning(plan: int, level_blocks_per_sm=0, gridlet_warps=0, m2l_ctas_per_sm=0):
+    t = hpm_tuning(level_blocks_per_sm, gridlet_warps, m2l_ctas_per_sm)
+    _check("hpm_set_tuning", load().hpm_set_tuning(plan, ctypes.byref(t)))
+
+
+def hpm_get_tuning(plan: int) -> dict:
+    t = hpm_tuning()
+    _check("hpm_get_tuning", load().hpm_get_tuning(plan, ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in hpm_tuning._fields_}
+
+
+def hpm_tune(plan: int, d_pos, d_mass, stream=None) -> dict:
+    """Autotunes the plan's launch shapes on this input; returns the chosen shapes."""
+    t = hpm_tuning()
+    _check("hpm_tune", load().hpm_tune(plan, _ptr(d_pos), _ptr(d_mass), int(d_pos.shape[0]), _stream(stream),
+                                       ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in hpm_tuning._fields_}
 
 
 def hpm_get_stats(plan: int) -> dict:

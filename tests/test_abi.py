@@ -64,4 +64,7 @@ def test_plan_rejects_bad_arguments_before_touching_the_device(lib, kw):
 def test_null_plan_is_rejected(lib):
     assert lib.hpm_build_tree(None, None, 0, None) == -1
     assert lib.hpm_solve(None, None, None, None, None, None) == -1
+    assert lib.hpm_set_tuning(None, None) == -1
+    assert lib.hpm_get_tuning(None, None) == -1
+    assert lib.hpm_tune(None, None, None, 0, None, None) == -1
     assert lib.hpm_destroy(None) == 0

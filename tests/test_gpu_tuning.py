@@ -1,0 +1,78 @@
+"""Launch shapes and their autotuner: every shape gives the same results bit for
+bit (the shapes only spread the same work over the GPU differently), the
+tuner returns shapes from the documented ranges, and bad shapes are refused."""
+import numpy as np
+import pytest
+
+from paper_1906_10734_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hpm():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1906_10734_gb300 import hpm as H
+    assert torch.cuda.is_available()
+    return H
+
+
+def solve_with(H, w, shapes, flags=0, ng=None):
+    dev = torch.device("cuda:0")
+    s = H.Solver(w.max_depth, ng or w.ng, w.eps, w.leaf_max, flags=flags)
+    H.hpm_set_tuning(s.plan, **shapes)
+    p = torch.from_numpy(np.ascontiguousarray(w.pos)).to(dev)
+    m = torch.from_numpy(np.ascontiguousarray(w.mass)).to(dev)
+    phi, acc = s(p, m)
+    torch.cuda.synchronize()
+    out = (phi.cpu().numpy(), acc.cpu().numpy())
+    s.close()
+    return out
+
+
+def assert_same(a, b):
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_shapes_keep_results_tensor_path(hpm):
+    w = I.small_plummer(20000, 61, leaf_max=16)
+    ref = solve_with(hpm, w, {})
+    for shapes in (dict(level_blocks_per_sm=1), dict(level_blocks_per_sm=3), dict(level_blocks_per_sm=4),
+                   dict(gridlet_warps=2), dict(gridlet_warps=4)):
+        assert_same(solve_with(hpm, w, shapes), ref)
+
+
+def test_shapes_keep_results_fft_paths(hpm):
+    w = I.small_plummer(12000, 62, leaf_max=16)
+    for flags, ng in ((hpm.HPM_FLAG_FFT_M2L, 4), (0, 6)):
+        ref = solve_with(hpm, w, {}, flags=flags, ng=ng)
+        assert_same(solve_with(hpm, w, dict(m2l_ctas_per_sm=1), flags=flags, ng=ng), ref)
+
+
+def test_tune_picks_valid_shapes_and_keeps_results(hpm):
+    w = I.small_plummer(20000, 63, leaf_max=16)
+    ref = solve_with(hpm, w, {})
+    dev = torch.device("cuda:0")
+    s = hpm.Solver(w.max_depth, w.ng, w.eps, w.leaf_max)
+    p = torch.from_numpy(np.ascontiguousarray(w.pos)).to(dev)
+    m = torch.from_numpy(np.ascontiguousarray(w.mass)).to(dev)
+    t = hpm.hpm_tune(s.plan, p, m)
+    assert t["level_blocks_per_sm"] in (1, 2, 3, 4)
+    assert t["gridlet_warps"] in (2, 4, 8)
+    assert hpm.hpm_get_tuning(s.plan) == t
+    phi, acc = s(p, m)
+    torch.cuda.synchronize()
+    assert_same((phi.cpu().numpy(), acc.cpu().numpy()), ref)
+    s.close()
+
+
+def test_bad_shapes_are_refused(hpm):
+    s = hpm.Solver(3, 4, 0.0, 0)
+    for shapes in (dict(level_blocks_per_sm=5), dict(gridlet_warps=3), dict(m2l_ctas_per_sm=3),
+                   dict(level_blocks_per_sm=-1)):
+        with pytest.raises(hpm.HpmError) as e:
+            hpm.hpm_set_tuning(s.plan, **shapes)
+        assert e.value.status == -1
+    s.close()
