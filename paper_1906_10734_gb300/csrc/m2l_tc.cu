@@ -561,7 +561,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
-      bar_init(&full[s], 1 + kGatherWarps);  // the W copy (with its byte count), then each plane's gather warp
+      bar_init(&full[s], 1 + 32 * kGatherWarps);  // the W copy (with its byte count), then each gather thread
       bar_init(&pfull[s], 1);
       bar_init(&empty[s], 1);
     }
@@ -628,6 +628,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
             failed = 1;
             break;
           }
+          fence_async_smem();  // this CTA's gathered tiles were written by cp.async
           tc_fence_after();
           // rows hold 16 hi then 16 lo values: hi*hi, hi*lo, lo*hi; the same
           // offsets in the peer CTA hold its 128 rows of W and 128 parents
@@ -655,6 +656,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
             failed = 1;
             break;
           }
+          fence_async_smem();  // the gathered tiles were written by cp.async
           bar_arrive_remote(&pfull[st], 0);
         }
       }
@@ -664,10 +666,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
     // Gather warp g fills the B tile of K-chunk 4 s + g (z plane g of slot
     // s) in the stage of slot s with this CTA's 128 parents (128 rank ...):
     // 64 bytes each, 4 lanes per parent (one 16-byte piece each), parents
-    // 8 m + lane / 4 for m = 0..15. It waits for its own copies, makes them
-    // visible to the tensor core's proxy and arrives once on the stage's
-    // full barrier: five arrivals per stage in all (the W copy and the four
-    // plane warps). Row indices of the next slot are loaded while the
+    // 8 m + lane / 4 for m = 0..15. Each thread's copies arrive on the
+    // stage's full barrier when they land (cp.async.mbarrier.arrive.noinc);
+    // the thread that consumes the stage (the leader's MMA thread, the
+    // peer's relay) makes them visible to the tensor core's proxy with one
+    // fence per stage, much cheaper there than a fence per gathering warp
+    // after its copies. Row indices of the next slot are loaded while the
     // current one is copied.
     const int g = warp - kProdWarp0, sub = lane & 3, grp = lane >> 2;
     const int *rp = pr.rows + tile * kSlots * kTileN + (int)rank * kHalfN + grp;
@@ -695,10 +699,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
         const int row = rows[m];
         cp16(dst + m * 512, hsub + (int64_t)(row >= 0 ? row : 0) * 4 * kRowBytes, row >= 0 ? 16u : 0u);
       }
-      asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-      fence_async_smem();  // this warp's copies, visible to the tensor core
-      __syncwarp();
-      if (lane == 0) bar_arrive(&full[st]);
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(&full[st])) : "memory");
 #pragma unroll
       for (int m = 0; m < kPer; ++m) rows[m] = next[m];
     }
