@@ -137,7 +137,10 @@ hpm_status hpm_build_tree(hpm_plan_t plan, const double *d_pos, int64_t n, void 
  *   d_phi   N FP32 output potentials (may be NULL)
  *   d_acc   N x 3 FP32 output accelerations, AoS (may be NULL)
  * Stream ordered, no host synchronisation. Errors: HPM_ERR_NOT_BUILT,
- * HPM_ERR_INVALID_ARG, HPM_ERR_CUDA.
+ * HPM_ERR_INVALID_ARG, HPM_ERR_CUDA. Every device wait of the solve is
+ * bounded; one that runs out marks the plan, and the next synchronising call
+ * on it (hpm_build_tree, hpm_solve_host, hpm_get_stats) returns
+ * HPM_ERR_TIMEOUT once (the outputs of that solve are then not valid).
  */
 hpm_status hpm_solve(hpm_plan_t plan, const double *d_pos, const double *d_mass, float *d_phi,
                      float *d_acc, void *stream);
@@ -289,6 +292,15 @@ hpm_status hpm_get_tuning(hpm_plan_t plan, hpm_tuning *tuning);
  * Errors: those of hpm_build_tree and hpm_solve. */
 hpm_status hpm_tune(hpm_plan_t plan, const double *d_pos, const double *d_mass, int64_t n, void *stream,
                     hpm_tuning *out);
+
+/* Failure test hook. With `on` set, the source-to-target kernel of the
+ * Ng = 4 tensor-core path first waits on a barrier that nothing arrives at;
+ * every wait of that kernel is bounded by wait_limit_cycles (0 = the default,
+ * about 2^32 cycles), so the kernel gives up, records the timeout and returns
+ * (no GPU fault), and the next synchronising call on the plan returns
+ * HPM_ERR_TIMEOUT. on = 0 restores normal operation (wait_limit_cycles also
+ * applies then). Errors: HPM_ERR_INVALID_ARG. */
+hpm_status hpm_test_stall(hpm_plan_t plan, int on, long long wait_limit_cycles);
 
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of independent solves (no counterpart in the

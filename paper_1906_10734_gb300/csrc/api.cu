@@ -222,6 +222,19 @@ hpm_status hpm_solve(hpm_plan_t plan, const double *d_pos, const double *d_mass,
   return solve(plan, d_pos, d_mass, d_phi, d_acc, (cudaStream_t)stream);
 }
 
+// The solves' error word (a bounded device wait that ran out): read after the
+// stream has drained, cleared once reported.
+static hpm_status take_solve_error(hpm_plan_t plan, cudaStream_t st) {
+  if (!plan->t.err.p) return HPM_OK;
+  int e = 0;
+  HPM_CUDA(cudaMemcpyAsync(&e, plan->t.err.as<int>() + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HPM_CUDA(cudaStreamSynchronize(st));
+  if (!(e & hpm::kErrTimeout)) return HPM_OK;
+  HPM_CUDA(cudaMemsetAsync(plan->t.err.as<int>() + 1, 0, sizeof(int), st));
+  HPM_CUDA(cudaStreamSynchronize(st));
+  return HPM_ERR_TIMEOUT;
+}
+
 hpm_status hpm_solve_host(hpm_plan_t plan, const double *h_pos, const double *h_mass, int64_t n, float *h_phi,
                           float *h_acc, void *stream) {
   if (!plan || n < 0 || (n > 0 && (!h_pos || !h_mass))) return HPM_ERR_INVALID_ARG;
@@ -243,7 +256,7 @@ hpm_status hpm_solve_host(hpm_plan_t plan, const double *h_pos, const double *h_
   if (n > 0 && h_acc)
     HPM_CUDA(cudaMemcpyAsync(h_acc, plan->host_io_acc.p, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, st));
   HPM_CUDA(cudaStreamSynchronize(st));
-  return HPM_OK;
+  return take_solve_error(plan, st);
 }
 
 hpm_status hpm_get_lists_info(hpm_plan_t plan, hpm_lists_info *info) {
@@ -380,6 +393,7 @@ hpm_status hpm_get_stats(hpm_plan_t plan, hpm_stats *st) {
     cudaEventElapsedTime(&tree, plan->ev[8], plan->ev[9]);
     cudaEventElapsedTime(&tot, plan->ev[0], plan->ev[7]);
     cudaGetLastError();
+    HPM_TRY(take_solve_error(plan, 0));
     st->ms_tree = tree;
     st->ms_p2g = v[0] + v[1];
     st->ms_m2m = v[2];

@@ -160,6 +160,8 @@ struct hpm_plan_s {
   std::vector<int64_t> leaf_lvl_off;
   hpm_stats stats{};
   hpm_tuning tuning{};             // launch shapes (0 = default), see hpm_set_tuning
+  int test_stall = 0;              // failure test hook (hpm_test_stall)
+  long long test_wait_limit = 0;   // cycles per bounded wait in that test (0 = default)
   cudaEvent_t ev[12] = {};  // stage boundaries 0..7, tree 8..9, dense product kernel 10..11
   bool events_ready = false;
   hpm::DevBuf host_io_pos, host_io_mass, host_io_phi, host_io_acc;

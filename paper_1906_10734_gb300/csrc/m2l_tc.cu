@@ -120,6 +120,8 @@ struct Params {
   float *out;              // per target Ng^3: deviations from node 0 (node 0 holds 0)
   float *outc;             // per target: the value at node 0
   int *err;
+  long long wait_limit;    // cycles a barrier wait may take before it gives up
+  int stall;               // test hook: the leader's MMA thread first waits on a barrier nothing arrives at
   double mean[kMaxDepth + 1][8];  // m_o per target level: mean of row (o, 0) over the zone
 };
 
@@ -138,8 +140,9 @@ __device__ __forceinline__ void bar_expect(uint64_t *b, uint32_t bytes) {
                "r"(bytes)
                : "memory");
 }
-// Bounded wait for the phase of the given parity: about 2^32 cycles at most.
-__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity) {
+// Bounded wait for the phase of the given parity: at most `limit` cycles
+// (about 2^32 by default).
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   uint32_t done = 0;
   for (;;) {
@@ -149,7 +152,7 @@ __device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity) {
         : "r"(su32(b)), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > (1ll << 32)) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *b) {
@@ -210,7 +213,7 @@ __device__ __forceinline__ void bar_arrive_remote(uint64_t *b, uint32_t cta) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(ra) : "memory");
 }
 // bounded wait that also acquires what the other CTA of the pair released
-__device__ __forceinline__ bool bar_wait_cl(uint64_t *b, uint32_t parity) {
+__device__ __forceinline__ bool bar_wait_cl(uint64_t *b, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   uint32_t done = 0;
   for (;;) {
@@ -221,7 +224,7 @@ __device__ __forceinline__ bool bar_wait_cl(uint64_t *b, uint32_t parity) {
         : "r"(su32(b)), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > (1ll << 32)) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -549,10 +552,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
   // full: this CTA's stage landed; pfull (leader): the peer's stage landed;
   // empty: the pair's MMAs are done with the stage; accf[x] / acce[x]:
   // accumulator buffer x filled by the MMAs / drained by both CTAs (leader)
-  __shared__ uint64_t full[kStages], pfull[kStages], empty[kStages], accf[2], acce[2];
+  __shared__ uint64_t full[kStages], pfull[kStages], empty[kStages], accf[2], acce[2], never;
   __shared__ uint32_t tmem_base;
   __shared__ int failed;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long lim = pr.wait_limit;
   const uint32_t rank = cluster_rank();  // 0: leader (issues the MMAs), 1: peer
   const int64_t tile = blockIdx.x / kQuarters;
   const int q = (int)(blockIdx.x % kQuarters);  // this CTA's 128 rows of W: quarter q; rank = q & 1
@@ -569,6 +573,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
       bar_init(&accf[x], 1);
       bar_init(&acce[x], 16);  // the 8 drain warps of each CTA
     }
+    bar_init(&never, 1);  // nothing arrives here (the stall test hook)
     failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -593,7 +598,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
         bool ok = true;
         for (int u = 0; u < kSlotUses; ++u) {
           const int st = u % kStages;
-          if (!bar_wait(&empty[st], ((u / kStages) & 1) ^ 1)) {
+          if (!bar_wait(&empty[st], ((u / kStages) & 1) ^ 1, lim)) {
             failed = 1;
             ok = false;
             break;
@@ -604,27 +609,30 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
         // the releases of the last stages are the leader's final arrivals on
         // this CTA's barriers: wait for them before the CTA may leave
         for (int u = kSlotUses; ok && u < kSlotUses + kStages; ++u)
-          if (!bar_wait(&empty[u % kStages], ((u / kStages) & 1) ^ 1)) {
+          if (!bar_wait(&empty[u % kStages], ((u / kStages) & 1) ^ 1, lim)) {
             failed = 1;
             ok = false;
           }
       }
     } else if (warp == 1 && rank == 0) {
       if (lane == 0) {
-        for (int u = 0; u < kSlotUses; ++u) {
+        // test hook: a wait that runs out; the CTAs give up and report it
+        const bool stalled = pr.stall && !bar_wait(&never, 0, lim);
+        if (stalled) failed = 1;
+        for (int u = 0; !stalled && u < kSlotUses; ++u) {
           const int st = u % kStages;
           const int c0 = u * kStageChunks;  // first K-chunk of the stage
           const int b = c0 / kBlockChunks, x = b & 1;
           const bool first = (c0 % kBlockChunks) == 0;
           if (first && b >= 2) {
             // buffer x was last filled by block b - 2: wait for both CTAs' drains
-            if (!bar_wait_cl(&acce[x], ((b >> 1) - 1) & 1)) {
+            if (!bar_wait_cl(&acce[x], ((b >> 1) - 1) & 1, lim)) {
               failed = 1;
               break;
             }
             tc_fence_after();
           }
-          if (!bar_wait(&full[st], (u / kStages) & 1) || !bar_wait_cl(&pfull[st], (u / kStages) & 1)) {
+          if (!bar_wait(&full[st], (u / kStages) & 1, lim) || !bar_wait_cl(&pfull[st], (u / kStages) & 1, lim)) {
             failed = 1;
             break;
           }
@@ -652,7 +660,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
       if (lane == 0) {
         for (int u = warp - 2; u < kSlotUses; u += 2) {
           const int st = u % kStages;
-          if (!bar_wait(&full[st], (u / kStages) & 1)) {
+          if (!bar_wait(&full[st], (u / kStages) & 1, lim)) {
             failed = 1;
             break;
           }
@@ -688,7 +696,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
 #pragma unroll
       for (int m = 0; m < kPer; ++m) next[m] = s + 1 < kSlots ? __ldg(rp + (s + 1) * kTileN + 8 * m) : -1;
       int ok = 1;
-      if (lane == 0) ok = bar_wait(&empty[st], ((s / kStages) & 1) ^ 1);
+      if (lane == 0) ok = bar_wait(&empty[st], ((s / kStages) & 1) ^ 1, lim);
       if (!__shfl_sync(0xffffffffu, ok, 0)) {
         failed = 1;
         break;
@@ -716,7 +724,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
     bool ok = true;
     for (int b = 0; b < kBlocks; ++b) {
       const int x = b & 1;
-      if (!__all_sync(0xffffffffu, bar_wait_cl(&accf[x], (b >> 1) & 1))) {
+      if (!__all_sync(0xffffffffu, bar_wait_cl(&accf[x], (b >> 1) & 1, lim))) {
         failed = 1;
         ok = false;
         break;
@@ -903,7 +911,9 @@ hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   p.nlev = pl->max_depth + 1;
   p.out = pl->s.m2l_raw.as<float>();
   p.outc = pl->s.m2lc.as<float>();
-  p.err = pl->t.err.as<int>();
+  p.err = pl->t.err.as<int>() + 1;  // the solves' error word
+  p.wait_limit = pl->test_wait_limit > 0 ? pl->test_wait_limit : (1ll << 32);
+  p.stall = pl->test_stall;
   for (int l = 0; l <= kMaxDepth && 8 * l + 7 < (int)pl->tc_mean_host.size(); ++l)
     for (int o = 0; o < 8; ++o) p.mean[l][o] = pl->tc_mean_host[8 * l + o];
   static bool attr = false;

@@ -672,9 +672,11 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   int64_t launches = 0;
   pl->built = false;
   pl->n = n;
+  // error words: [0] this build's, [1] the solves' (kept until reported)
+  const bool fresh_err = t.err.p == nullptr;
   HPM_TRY(t.err.ensure(sizeof(int) * 4, st));
   HPM_TRY(t.counters.ensure(sizeof(int) * 128, st));
-  HPM_CUDA(cudaMemsetAsync(t.err.p, 0, sizeof(int) * 4, st));
+  HPM_CUDA(cudaMemsetAsync(t.err.p, 0, sizeof(int) * (fresh_err ? 4 : 1), st));
   HPM_CUDA(cudaMemsetAsync(t.counters.p, 0, sizeof(int) * 128, st));
   // scans of the build: sort histograms (n / 16), problems, boxes (up to the
   // box capacity, grown below if needed), leaves
@@ -906,11 +908,16 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
                                t.scan, st, &launches));
     HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.leaf_part0.as<int>(), nl, t.counters.as<int>() + 65,
                                t.scan, st, &launches));
-    int hv[10] = {0}, herr2 = 0;
+    int hv[10] = {0}, herr2[2] = {0, 0};
     HPM_CUDA(cudaMemcpyAsync(hv, t.counters.as<int>() + 64, sizeof(int) * 10, cudaMemcpyDeviceToHost, st));
-    HPM_CUDA(cudaMemcpyAsync(&herr2, t.err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaMemcpyAsync(herr2, t.err.as<int>(), sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaStreamSynchronize(st));
-    if (herr2 & kErrTimeout) return HPM_ERR_TIMEOUT;
+    if (herr2[1] & kErrTimeout) {
+      // a bounded wait of an earlier solve on this plan ran out: report it once
+      HPM_CUDA(cudaMemsetAsync(t.err.as<int>() + 1, 0, sizeof(int), st));
+      return HPM_ERR_TIMEOUT;
+    }
+    if (herr2[0] & kErrTimeout) return HPM_ERR_TIMEOUT;
     pl->nitem = hv[0];
     pl->npart = hv[1];
     // the work-list sizes the host derived must be what the device selected

@@ -69,6 +69,13 @@ hpm_status hpm_set_tuning(hpm_plan_t plan, const hpm_tuning *tuning) {
   return HPM_OK;
 }
 
+hpm_status hpm_test_stall(hpm_plan_t plan, int on, long long wait_limit_cycles) {
+  if (!plan || wait_limit_cycles < 0) return HPM_ERR_INVALID_ARG;
+  plan->test_stall = on ? 1 : 0;
+  plan->test_wait_limit = wait_limit_cycles;
+  return HPM_OK;
+}
+
 hpm_status hpm_get_tuning(hpm_plan_t plan, hpm_tuning *tuning) {
   if (!plan || !tuning) return HPM_ERR_INVALID_ARG;
   *tuning = plan->tuning;

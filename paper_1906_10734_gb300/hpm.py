@@ -106,6 +106,7 @@ SIGNATURES = {
     "hpm_set_tuning": ([_vp, ctypes.POINTER(hpm_tuning)], _i32),
     "hpm_get_tuning": ([_vp, ctypes.POINTER(hpm_tuning)], _i32),
     "hpm_tune": ([_vp, _vp, _vp, _i64, _vp, ctypes.POINTER(hpm_tuning)], _i32),
+    "hpm_test_stall": ([_vp, _i32, ctypes.c_longlong], _i32),
     "hpm_destroy": ([_vp], _i32),
     "hpm_status_str": ([_i32], ctypes.c_char_p),
     "hpm_last_cuda_error": ([], ctypes.c_char_p),
@@ -273,6 +274,12 @@ def hpm_tune(plan: int, d_pos, d_mass, stream=None) -> dict:
     _check("hpm_tune", load().hpm_tune(plan, _ptr(d_pos), _ptr(d_mass), int(d_pos.shape[0]), _stream(stream),
                                        ctypes.byref(t)))
     return {k: getattr(t, k) for k, _ in hpm_tuning._fields_}
+
+
+def hpm_test_stall(plan: int, on: bool, wait_limit_cycles: int = 0):
+    """Failure test hook: the next solves' source-to-target kernel waits on a barrier that
+    nothing arrives at (bounded by wait_limit_cycles), gives up and records a timeout."""
+    _check("hpm_test_stall", load().hpm_test_stall(plan, 1 if on else 0, int(wait_limit_cycles)))
 
 
 def hpm_get_stats(plan: int) -> dict:

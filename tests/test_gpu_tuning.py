@@ -76,3 +76,29 @@ def test_bad_shapes_are_refused(hpm):
             hpm.hpm_set_tuning(s.plan, **shapes)
         assert e.value.status == -1
     s.close()
+
+
+def test_a_wait_that_runs_out_is_reported_and_the_plan_recovers(hpm):
+    # failure detection without a GPU fault: the source-to-target kernel waits on a
+    # barrier nothing arrives at, gives up after ~2^24 cycles, records a timeout; the
+    # next synchronising call reports it once, and the plan then solves as before
+    w = I.small_plummer(12000, 64, leaf_max=16)
+    ref = solve_with(hpm, w, {})
+    dev = torch.device("cuda:0")
+    s = hpm.Solver(w.max_depth, w.ng, w.eps, w.leaf_max)
+    p = torch.from_numpy(np.ascontiguousarray(w.pos)).to(dev)
+    m = torch.from_numpy(np.ascontiguousarray(w.mass)).to(dev)
+    phi = torch.empty(w.n, dtype=torch.float32, device=dev)
+    acc = torch.empty((w.n, 3), dtype=torch.float32, device=dev)
+    hpm.hpm_test_stall(s.plan, True, 1 << 24)
+    hpm.hpm_build_tree(s.plan, p, w.n)
+    hpm.hpm_solve(s.plan, p, m, phi, acc)
+    torch.cuda.synchronize()
+    with pytest.raises(hpm.HpmError) as e:
+        hpm.hpm_build_tree(s.plan, p, w.n)
+    assert e.value.status == -5
+    hpm.hpm_test_stall(s.plan, False, 0)
+    phi, acc = s(p, m)
+    torch.cuda.synchronize()
+    assert_same((phi.cpu().numpy(), acc.cpu().numpy()), ref)
+    s.close()
