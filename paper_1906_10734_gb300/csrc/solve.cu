@@ -529,20 +529,42 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
   s = t;
 }
 
+// A particle's position relative to the target leaf's centre as a rounded
+// FP32 value r and its exact residual e (the hi part relative to the centre
+// plus the lo residual of the unit-cube coordinate, r + e = the sum).
+__device__ __forceinline__ float2 rel_split(float h, float c0, float lo) {
+  const float hr = h - c0;
+  const float r = hr + lo;
+  return make_float2(r, (hr - r) + lo);
+}
+
 // One source's contribution to a target, accumulated into a short plain-FP32
-// block sum. Positions are (hi, lo) float pairs: hi relative to the target
-// leaf's centre, lo the residual of the unit-cube coordinate; (s.hi - t.hi) is
-// exact for nearby particles, so the difference keeps FP32 precision relative
-// to the pair distance however small it is. lo.w holds the particle index.
-__device__ __forceinline__ void pair_rel(const float4 &th, const float4 &tl, const float4 &sh, const float4 &sl,
-                                         float eps2, float &bp, float &bx, float &by, float &bz) {
-  const float dx = (sh.x - th.x) + (sl.x - tl.x), dy = (sh.y - th.y) + (sl.y - tl.y),
-              dz = (sh.z - th.z) + (sl.z - tl.z);
-  const bool self = __float_as_int(sl.w) == __float_as_int(tl.w);
+// block sum. pair_fast takes the difference of the rounded relative positions
+// (error below 2^-23 of the leaf side) and returns r^2 for the block's check;
+// pair_exact takes (r_s - r_t) + (e_s - e_t), which keeps FP32 precision
+// relative to the pair distance however small it is, and skips the target
+// itself. sr.w holds the mass, se.w the particle index.
+__device__ __forceinline__ float pair_fast(const float4 &tr, const float4 &s, float eps2, float &bp, float &bx,
+                                           float &by, float &bz) {
+  const float dx = s.x - tr.x, dy = s.y - tr.y, dz = s.z - tr.z;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+  const float ir = rsqrtf(r2);
+  const float mir = s.w * ir;
+  const float mir3 = mir * ir * ir;
+  bp -= mir;
+  bx = fmaf(mir3, dx, bx);
+  by = fmaf(mir3, dy, by);
+  bz = fmaf(mir3, dz, bz);
+  return r2;
+}
+
+__device__ __forceinline__ void pair_exact(const float4 &tr, const float4 &te, const float4 &s, const float4 &e,
+                                           float eps2, float &bp, float &bx, float &by, float &bz) {
+  const float dx = (s.x - tr.x) + (e.x - te.x), dy = (s.y - tr.y) + (e.y - te.y), dz = (s.z - tr.z) + (e.z - te.z);
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
   float ir = rsqrtf(r2);
-  if (self) ir = 0.f;
-  const float mir = sh.w * ir;
+  if (__float_as_int(e.w) == __float_as_int(te.w)) ir = 0.f;  // the target itself
+  const float mir = s.w * ir;
   const float mir3 = mir * ir * ir;
   bp -= mir;
   bx = fmaf(mir3, dx, bx);
@@ -553,7 +575,8 @@ __device__ __forceinline__ void pair_rel(const float4 &th, const float4 &tl, con
 // Near zone by direct summation (Sec. 1, item 1), one warp per work item: an
 // item is a leaf's targets against a contiguous part of the concatenation of
 // its near boxes' particles. The item's sources are staged in shared memory in
-// chunks (position hi relative to the target leaf's centre, lo, mass, index), so
+// chunks (rounded position relative to the target leaf's centre and mass,
+// exact residual and index), so
 // the pair loop is one flat loop; floor(32 / nt) lanes share a target and split
 // the chunk; blocks of eight pairs are summed in plain FP32 and the block sums
 // are Kahan compensated. A leaf with one item writes far + near to the
@@ -618,6 +641,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2p(int64_t nitem, const int *_
   const int G = nt >= 32 ? 1 : 32 / nt;
   const int per = 32 / G;
   const int nitems = leaf_nitem[leaf];
+  float near2;
+  {
+    const float side = 1.f / (float)(1u << level_of(lt, box));  // the leaf's side (unit cube)
+    near2 = eps2 + side * side * (1.f / 64.f);  // r^2 of a pair 1/8 of the side apart
+  }
   const int kidx = (int)(it - leaf_item0[leaf]);
   for (int t0 = tb; t0 < te; t0 += per) {
     const int slot = lane / G, sub = lane % G;
@@ -626,8 +654,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2p(int64_t nitem, const int *_
     float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
     if (active) {
       const float4 h = hi[ti], q = lo[ti];
-      th = make_float4(h.x - cx0, h.y - cy0, h.z - cz0, 0.f);
-      tl = make_float4(q.x, q.y, q.z, __int_as_float(ti));
+      const float2 x = rel_split(h.x, cx0, q.x), y = rel_split(h.y, cy0, q.y), z = rel_split(h.z, cz0, q.z);
+      th = make_float4(x.x, y.x, z.x, 0.f);
+      tl = make_float4(x.y, y.y, z.y, __int_as_float(ti));
     }
     float sp = 0.f, cp = 0.f, sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
     for (int c0 = s0; c0 < s1; c0 += kP2PChunk) {
@@ -641,18 +670,27 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2p(int64_t nitem, const int *_
           if (r + step < 28 && cum[w][r + step] <= q) r += step;
         const int j = rb[w][r] + (q - cum[w][r]);
         const float4 h = hi[j], o = lo[j];
-        srh[w][k] = make_float4(h.x - cx0, h.y - cy0, h.z - cz0, h.w);
-        srl[w][k] = make_float4(o.x, o.y, o.z, __int_as_float(j));
+        const float2 x = rel_split(h.x, cx0, o.x), y = rel_split(h.y, cy0, o.y), z = rel_split(h.z, cz0, o.z);
+        srh[w][k] = make_float4(x.x, y.x, z.x, h.w);
+        srl[w][k] = make_float4(x.y, y.y, z.y, __int_as_float(j));
       }
       __syncwarp();
       if (active) {
         int k = sub;
         for (; k + 7 * G < cn; k += 8 * G) {
-          float bp = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+          // eight pairs from the rounded positions; if some lane of the warp
+          // has a pair closer than near2 in them (or meets its own particle:
+          // difference 0, r2 = eps2 <= near2) the block is summed again exactly
+          float bp = 0.f, bx = 0.f, by = 0.f, bz = 0.f, r2min = 3.4e38f;
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int kk = k + u * G;
-            pair_rel(th, tl, srh[w][kk], srl[w][kk], eps2, bp, bx, by, bz);
+          for (int u = 0; u < 8; ++u) r2min = fminf(r2min, pair_fast(th, srh[w][k + u * G], eps2, bp, bx, by, bz));
+          if (__any_sync(__activemask(), r2min <= near2)) {
+            bp = bx = by = bz = 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int kk = k + u * G;
+              pair_exact(th, tl, srh[w][kk], srl[w][kk], eps2, bp, bx, by, bz);
+            }
           }
           kahan_add(sp, cp, bp);
           kahan_add(sx, cx, bx);
@@ -660,7 +698,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2p(int64_t nitem, const int *_
           kahan_add(sz, cz, bz);
         }
         float bp = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
-        for (; k < cn; k += G) pair_rel(th, tl, srh[w][k], srl[w][k], eps2, bp, bx, by, bz);
+        for (; k < cn; k += G) pair_exact(th, tl, srh[w][k], srl[w][k], eps2, bp, bx, by, bz);
         kahan_add(sp, cp, bp);
         kahan_add(sx, cx, bx);
         kahan_add(sy, cy, by);
