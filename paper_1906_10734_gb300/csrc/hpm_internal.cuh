@@ -102,7 +102,7 @@ struct SolveDev {
   DevBuf far;        // far field per sorted particle: float4 (phi, ax, ay, az)
   DevBuf part;       // near-field partial sums of leaves split over several items
   DevBuf m2l_scratch;
-  DevBuf work;       // int work counters
+  DevBuf work;       // near-field item counter (zeroed before each launch)
   // Ng = 4 tensor-core path: effective masses as FP16 (hi, lo) planes at a
   // per-row scale, row scale exponents and total masses, the scale exponent of
   // each tile column (parent) and the zone mass of each of its 8 children

@@ -581,10 +581,12 @@ __device__ __forceinline__ void pair_exact(const float4 &tr, const float4 &te, c
 // the chunk; blocks of eight pairs are summed in plain FP32 and the block sums
 // are Kahan compensated. A leaf with one item writes far + near to the
 // caller's order; a leaf split over several items writes partial sums for
-// k_p2p_combine.
+// k_p2p_combine. Warps take items from a counter (zeroed before the launch) and
+// the grid holds as many blocks as are resident at once, so a warp whose item
+// ends early starts the next one instead of idling until its block retires.
 constexpr int kP2PChunk = 128;
 
-__global__ void __launch_bounds__(kThreads, 3) k_p2p(int64_t nitem, const int *__restrict__ item_leaf,
+__global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *__restrict__ item_leaf,
                                                   const int *__restrict__ item_s0, const int *__restrict__ item_s1,
                                                   const int *__restrict__ leaf_nitem,
                                                   const int *__restrict__ leaf_item0,
@@ -596,13 +598,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2p(int64_t nitem, const int *_
                                                   const uint32_t *__restrict__ perm, const uint64_t *__restrict__ key,
                                                   LevelTable lt, float eps2, float sc_phi,
                                                   float sc_acc, float *__restrict__ out_phi, float *__restrict__ out_acc,
-                                                  float4 *__restrict__ part) {
+                                                  float4 *__restrict__ part, unsigned long long *__restrict__ next) {
   __shared__ int rb[kWarpsPerBlock][28], cum[kWarpsPerBlock][28];
   __shared__ float4 red[kWarpsPerBlock][32];
   __shared__ float4 srh[kWarpsPerBlock][kP2PChunk], srl[kWarpsPerBlock][kP2PChunk];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t it = (int64_t)blockIdx.x * kWarpsPerBlock + w;
+  for (;;) {
+  unsigned long long it0 = 0;
+  if (lane == 0) it0 = atomicAdd(next, 1ull);
+  const int64_t it = (int64_t)__shfl_sync(0xffffffffu, it0, 0);
   if (it >= nitem) return;
+  __syncwarp();
   const int leaf = item_leaf[it];
   const int box = leaf_box[leaf];
   {
@@ -662,17 +668,33 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2p(int64_t nitem, const int *_
     for (int c0 = s0; c0 < s1; c0 += kP2PChunk) {
       const int cn = min(kP2PChunk, s1 - c0);
       __syncwarp();
-      for (int k = lane; k < cn; k += 32) {
-        const int q = c0 + k;
-        int r = 0;  // range holding concatenated index q
+      for (int k0 = 0; k0 < cn; k0 += 64) {
+        int j[2];
+        float4 h[2], o[2];
 #pragma unroll
-        for (int step = 16; step >= 1; step >>= 1)
-          if (r + step < 28 && cum[w][r + step] <= q) r += step;
-        const int j = rb[w][r] + (q - cum[w][r]);
-        const float4 h = hi[j], o = lo[j];
-        const float2 x = rel_split(h.x, cx0, o.x), y = rel_split(h.y, cy0, o.y), z = rel_split(h.z, cz0, o.z);
-        srh[w][k] = make_float4(x.x, y.x, z.x, h.w);
-        srl[w][k] = make_float4(x.y, y.y, z.y, __int_as_float(j));
+        for (int u = 0; u < 2; ++u) {
+          const int q = c0 + min(k0 + lane + 32 * u, cn - 1);
+          int r = 0;  // range holding concatenated index q
+#pragma unroll
+          for (int step = 16; step >= 1; step >>= 1)
+            if (r + step < 28 && cum[w][r + step] <= q) r += step;
+          j[u] = rb[w][r] + (q - cum[w][r]);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          h[u] = hi[j[u]];
+          o[u] = lo[j[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int k = k0 + lane + 32 * u;
+          if (k < cn) {
+            const float2 x = rel_split(h[u].x, cx0, o[u].x), y = rel_split(h[u].y, cy0, o[u].y),
+                         z = rel_split(h[u].z, cz0, o[u].z);
+            srh[w][k] = make_float4(x.x, y.x, z.x, h[u].w);
+            srl[w][k] = make_float4(x.y, y.y, z.y, __int_as_float(j[u]));
+          }
+        }
       }
       __syncwarp();
       if (active) {
@@ -730,6 +752,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2p(int64_t nitem, const int *_
       }
     }
     __syncwarp();
+  }
   }
 }
 
@@ -1066,11 +1089,20 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
     const float eps2 = (float)(eu * eu);
     const float s1 = (float)(1.0 / pl->dom.side), s2 = (float)(1.0 / (pl->dom.side * pl->dom.side));
     HPM_TRY(s.part.ensure(sizeof(float4) * (pl->npart > 0 ? pl->npart : 1), st));
-    k_p2p<<<warp_blocks(pl->nitem), kThreads, 0, st>>>(
+    static int p2p_resident = 0;
+    if (!p2p_resident) {
+      HPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2p_resident, k_p2p, kThreads, 0));
+      if (p2p_resident < 1) p2p_resident = 1;
+    }
+    HPM_TRY(s.work.ensure(sizeof(unsigned long long), st));
+    HPM_CUDA(cudaMemsetAsync(s.work.p, 0, sizeof(unsigned long long), st));
+    const unsigned p2p_grid = (unsigned)std::min<int64_t>(warp_blocks(pl->nitem), (int64_t)p2p_resident * sm_count());
+    k_p2p<<<p2p_grid, kThreads, 0, st>>>(
         pl->nitem, t.item_leaf.as<int>(), t.item_s0.as<int>(), t.item_s1.as<int>(), t.leaf_nitem.as<int>(),
         t.leaf_item0.as<int>(), t.leaf_part0.as<int>(), t.leaf_box.as<int>(), t.box_nb.as<int>(),
         t.box_beg.as<int>(), t.box_end.as<int>(), hi, lo, s.far.as<float4>(), t.perm.as<uint32_t>(),
-        t.box_key.as<uint64_t>(), lt, eps2, s1, s2, d_phi, d_acc, s.part.as<float4>());
+        t.box_key.as<uint64_t>(), lt, eps2, s1, s2, d_phi, d_acc, s.part.as<float4>(),
+        s.work.as<unsigned long long>());
     HPM_LAUNCHED(&launches);
     if (pl->npart > 0) {
       k_p2p_combine<<<warp_blocks(pl->nleaf), kThreads, 0, st>>>(
