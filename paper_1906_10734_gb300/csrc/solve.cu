@@ -108,26 +108,28 @@ __device__ __forceinline__ void lagrange_d(const GridletTables &tb, double xi, f
     }
 }
 
-// Ng = 4 in closed form: with u = 8 xi = A + B (A, B floats whose sum is
-// exact in FP64) and the nodes -3, -1, 1, 3, ell_0 = -(u+1)(u-1)(u-3)/48,
-// ell_1 = (u+3)(u-1)(u-3)/16, ell_2 = -(u+3)(u+1)(u-3)/16 and
-// ell_3 = (u+3)(u+1)(u-1)/48. The same FP64 products as the general form in
-// fewer FP64 instructions; the factors 1/16 are powers of two and are applied
-// after the rounding to FP32 (an exact scaling), so the weights are the same.
-__device__ __forceinline__ void lagrange4_d(float A, float B, float *w) {
-  const double u = (double)A + (double)B;
-  const double d0 = u + 3.0, d1 = u + 1.0, d2 = u - 1.0, d3 = u - 3.0;
-  const double e = d2 * d3, f = d0 * d1;
-  w[0] = (float)((d1 * e) * (-1.0 / 48.0));
-  w[1] = (float)(d0 * e) * 0.0625f;
-  w[2] = (float)(f * d3) * -0.0625f;
-  w[3] = (float)((f * d2) * (1.0 / 48.0));
+// Ng = 4 in closed form, FP32: with u = 8 xi = A + B (A, B floats; A plus a
+// small integer is exact) and the nodes -3, -1, 1, 3,
+// ell_0 = -(u+1)(u-1)(u-3)/48, ell_1 = (u+3)(u-1)(u-3)/16,
+// ell_2 = -(u+3)(u+1)(u-3)/16 and ell_3 = (u+3)(u+1)(u-1)/48. Each difference
+// u - a_k carries one rounding, each weight a few more: an absolute error of
+// order 1e-7 per weight for |u| <= 4, far below the FP32 solve's error budget,
+// and the FP64 pipe (a small fraction of the FP32 rate on this part) is left
+// out of the effective masses.
+__device__ __forceinline__ void lagrange4_f(float A, float B, float *w) {
+  const float d0 = (A + 3.f) + B, d1 = (A + 1.f) + B, d2 = (A - 1.f) + B, d3 = (A - 3.f) + B;
+  const float e = d2 * d3, f = d0 * d1;
+  w[0] = (d1 * e) * (-1.f / 48.f);
+  w[1] = (d0 * e) * 0.0625f;
+  w[2] = (f * d3) * -0.0625f;
+  w[3] = (f * d2) * (1.f / 48.f);
 }
 
 // Effective masses, M_p = sum_i m_i prod_d ell_{p_d}(xi_d) (Eq. mp in Lagrange
 // form: sum_n B_pn t^n = ell_p(t)). A block takes 8 boxes; all its threads
-// evaluate the FP64 weights of the (box, particle) pairs of those boxes, 256
-// pairs at a time, then warp w accumulates box w from shared memory.
+// evaluate the weights of the (box, particle) pairs of those boxes (FP32 in
+// closed form at Ng = 4, FP64 otherwise), 256 pairs at a time, then warp w
+// accumulates box w from shared memory.
 template <int NG>
 __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__restrict__ list,
                                                   const int *__restrict__ pair_off, LevelTable lt,
@@ -173,9 +175,9 @@ __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__res
       if constexpr (NG == 4) {
         // u = 8 xi = 8 (h sc - c) + 8 lo sc: both parts exact in FP32 (powers of two)
         const float s8 = 8.f * sc;
-        lagrange4_d(fmaf(h.x, s8, -8.f * bc[lb][0]), q.x * s8, ws[threadIdx.x][0]);
-        lagrange4_d(fmaf(h.y, s8, -8.f * bc[lb][1]), q.y * s8, ws[threadIdx.x][1]);
-        lagrange4_d(fmaf(h.z, s8, -8.f * bc[lb][2]), q.z * s8, ws[threadIdx.x][2]);
+        lagrange4_f(fmaf(h.x, s8, -8.f * bc[lb][0]), q.x * s8, ws[threadIdx.x][0]);
+        lagrange4_f(fmaf(h.y, s8, -8.f * bc[lb][1]), q.y * s8, ws[threadIdx.x][1]);
+        lagrange4_f(fmaf(h.z, s8, -8.f * bc[lb][2]), q.z * s8, ws[threadIdx.x][2]);
       } else {
         lagrange_d<NG>(tb, cell_coord_d(h.x, q.x, sc, bc[lb][0]), ws[threadIdx.x][0]);
         lagrange_d<NG>(tb, cell_coord_d(h.y, q.y, sc, bc[lb][1]), ws[threadIdx.x][1]);
@@ -186,14 +188,27 @@ __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__res
     __syncthreads();
     if (w < nb) {
       const int jb = max(off[w], c0) - c0, je = min(off[w + 1], c0 + kThreads) - c0;
+      if constexpr (NG == 4) {
+        // nodes lane and lane + 32: the same x and y weights, z = lane/16 and 2 + lane/16
+        const int px = lane & 3, py = (lane >> 2) & 3, pz = lane >> 4;
+        float a0 = acc[0], a1 = acc[1];
+        for (int j = jb; j < je; ++j) {
+          const float t = ms[j] * ws[j][0][px] * ws[j][1][py];
+          a0 = fmaf(t, ws[j][2][pz], a0);
+          a1 = fmaf(t, ws[j][2][pz + 2], a1);
+        }
+        acc[0] = a0;
+        acc[1] = a1;
+      } else {
 #pragma unroll
-      for (int r = 0; r < kR; ++r) {
-        const int pp = r * 32 + lane;
-        if (pp >= m3) break;
-        const int px = pp % ng, py = (pp / ng) % ng, pz = pp / (ng * ng);
-        float s = acc[r];
-        for (int j = jb; j < je; ++j) s += ms[j] * ws[j][0][px] * ws[j][1][py] * ws[j][2][pz];
-        acc[r] = s;
+        for (int r = 0; r < kR; ++r) {
+          const int pp = r * 32 + lane;
+          if (pp >= m3) break;
+          const int px = pp % ng, py = (pp / ng) % ng, pz = pp / (ng * ng);
+          float s = acc[r];
+          for (int j = jb; j < je; ++j) s += ms[j] * ws[j][0][px] * ws[j][1][py] * ws[j][2][pz];
+          acc[r] = s;
+        }
       }
     }
     __syncthreads();

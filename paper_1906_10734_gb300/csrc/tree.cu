@@ -308,7 +308,8 @@ __device__ __forceinline__ void mark_neighbours(const int *q, uint8_t *flags) {
 //   2. block offsets from the per-block totals, then the children
 //   3. the neighbour tables of the new boxes; an internal one marks its 27
 //      neighbours for the next level's expansion right away
-// Three grid barriers per level (and one after the roots' marks).
+// Three grid barriers per level (and one after the roots' marks); the launch
+// ends at the first empty level.
 __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
   __shared__ int s_warp[kThreads / 32];
   __shared__ long long s_red[2][kThreads / 32];
@@ -452,6 +453,12 @@ __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
       }
       fill_children_of(q, pb, pe + base, l, a.depth, a.leaf_max, a.flags, a.key, a.beg, a.end, a.parent, a.child,
                        a.bnd, a.off, a.counters);
+    }
+    if (total == 0) {
+      // level l is empty, and so is every deeper one (every block sees the same total)
+      if (blockIdx.x == 0 && tid == 0)
+        for (int k = l + 2; k <= a.depth + 1; ++k) a.lvl[k] = ne;
+      return;
     }
     if (!grid_sync(a.gb, a.err)) return;
     // 3. neighbour tables of level l, expansion marks for level l + 1
