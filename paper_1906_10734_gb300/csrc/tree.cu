@@ -119,6 +119,12 @@ __global__ void k_problem_ranges(int nprob, int64_t n, const uint64_t *__restric
                                  int *__restrict__ rb, int *__restrict__ cnt) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nprob) return;
+  if (nprob == 1) {
+    // a single problem holds every particle (no searches: 2 x log2 n dependent loads)
+    rb[0] = 0;
+    cnt[0] = n > 0 ? 1 : 0;
+    return;
+  }
   int lo = 0, hi = (int)n;
   while (lo < hi) {
     const int mid = lo + ((hi - lo) >> 1);
@@ -744,9 +750,12 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   HPM_LAUNCHED(&launches);
   HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), nprob, t.counters.as<int>() + 64, t.scan, st,
                              &launches));
-  int nroot = 0;
-  HPM_CUDA(cudaMemcpyAsync(&nroot, t.counters.as<int>() + 64, sizeof(int), cudaMemcpyDeviceToHost, st));
-  HPM_CUDA(cudaStreamSynchronize(st));
+  // one problem with n > 0 particles has one root; a batch reads its count back
+  int nroot = 1;
+  if (nprob > 1) {
+    HPM_CUDA(cudaMemcpyAsync(&nroot, t.counters.as<int>() + 64, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaStreamSynchronize(st));
+  }
   // Box capacity: grow-only across builds; the first build guesses n / 4 + 1024
   // (trees here hold 0.14-0.19 n boxes) and retries with more if it overflows.
   int64_t cap = t.box_key.cap / sizeof(uint64_t);
@@ -948,6 +957,10 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   if (pl->ntgt) {
     k_box_tgt<<<blocks_for(pl->ntgt), kThreads, 0, st>>>(pl->ntgt, t.tgt_box.as<int>(), t.box_tgt.as<int>());
     HPM_LAUNCHED(&launches);
+  }
+  if (pl->ntgt && !use_tc_m2l(pl)) {
+    // per-target 6^3 blocks: read by the FFT-form source-to-target kernel only
+    // (the tensor-core form builds its own per-parent tiles below)
     HPM_TRY(t.tgt_blk.ensure(sizeof(int) * 216 * pl->ntgt, st));
     HPM_TRY(t.tgt_info.ensure(sizeof(int) * pl->ntgt, st));
     LevelOffsets lo{};
