@@ -108,28 +108,29 @@ __device__ __forceinline__ void lagrange_d(const GridletTables &tb, double xi, f
     }
 }
 
-// Ng = 4 in closed form, FP32: with u = 8 xi = A + B (A, B floats; A plus a
-// small integer is exact) and the nodes -3, -1, 1, 3,
-// ell_0 = -(u+1)(u-1)(u-3)/48, ell_1 = (u+3)(u-1)(u-3)/16,
-// ell_2 = -(u+3)(u+1)(u-3)/16 and ell_3 = (u+3)(u+1)(u-1)/48. Each difference
-// u - a_k carries one rounding, each weight a few more: an absolute error of
-// order 1e-7 per weight for |u| <= 4, far below the FP32 solve's error budget,
-// and the FP64 pipe (a small fraction of the FP32 rate on this part) is left
-// out of the effective masses.
-__device__ __forceinline__ void lagrange4_f(float A, float B, float *w) {
-  const float d0 = (A + 3.f) + B, d1 = (A + 1.f) + B, d2 = (A - 1.f) + B, d3 = (A - 3.f) + B;
-  const float e = d2 * d3, f = d0 * d1;
-  w[0] = (d1 * e) * (-1.f / 48.f);
-  w[1] = (d0 * e) * 0.0625f;
-  w[2] = (f * d3) * -0.0625f;
-  w[3] = (f * d2) * (1.f / 48.f);
+// Ng = 4 in closed form: with u = 8 xi = A + B (A, B floats whose sum is
+// exact in FP64) and the nodes -3, -1, 1, 3, ell_0 = -(u+1)(u-1)(u-3)/48,
+// ell_1 = (u+3)(u-1)(u-3)/16, ell_2 = -(u+3)(u+1)(u-3)/16 and
+// ell_3 = (u+3)(u+1)(u-1)/48. The same FP64 products as the general form in
+// fewer FP64 instructions; the factors 1/16 are powers of two and are applied
+// after the rounding to FP32 (an exact scaling), so the weights are the same.
+__device__ __forceinline__ void lagrange4_d(float A, float B, float *w) {
+  const double u = (double)A + (double)B;
+  const double d0 = u + 3.0, d1 = u + 1.0, d2 = u - 1.0, d3 = u - 3.0;
+  const double e = d2 * d3, f = d0 * d1;
+  w[0] = (float)((d1 * e) * (-1.0 / 48.0));
+  w[1] = (float)(d0 * e) * 0.0625f;
+  w[2] = (float)(f * d3) * -0.0625f;
+  w[3] = (float)((f * d2) * (1.0 / 48.0));
 }
 
 // Effective masses, M_p = sum_i m_i prod_d ell_{p_d}(xi_d) (Eq. mp in Lagrange
-// form: sum_n B_pn t^n = ell_p(t)). A block takes 8 boxes; all its threads
-// evaluate the weights of the (box, particle) pairs of those boxes (FP32 in
-// closed form at Ng = 4, FP64 otherwise), 256 pairs at a time, then warp w
-// accumulates box w from shared memory.
+// form: sum_n B_pn t^n = ell_p(t)), for the boxes that are not expanded: each
+// particle's finest box (an expanded box, internal or not, gets its gridlet
+// from its children by the child-to-parent transform). A block takes 8 boxes;
+// all its threads evaluate the FP64 weights of the (box, particle) pairs of
+// those boxes, 256 pairs at a time, then warp w accumulates box w from shared
+// memory.
 template <int NG>
 __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__restrict__ list,
                                                   const int *__restrict__ pair_off, LevelTable lt,
@@ -175,9 +176,9 @@ __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__res
       if constexpr (NG == 4) {
         // u = 8 xi = 8 (h sc - c) + 8 lo sc: both parts exact in FP32 (powers of two)
         const float s8 = 8.f * sc;
-        lagrange4_f(fmaf(h.x, s8, -8.f * bc[lb][0]), q.x * s8, ws[threadIdx.x][0]);
-        lagrange4_f(fmaf(h.y, s8, -8.f * bc[lb][1]), q.y * s8, ws[threadIdx.x][1]);
-        lagrange4_f(fmaf(h.z, s8, -8.f * bc[lb][2]), q.z * s8, ws[threadIdx.x][2]);
+        lagrange4_d(fmaf(h.x, s8, -8.f * bc[lb][0]), q.x * s8, ws[threadIdx.x][0]);
+        lagrange4_d(fmaf(h.y, s8, -8.f * bc[lb][1]), q.y * s8, ws[threadIdx.x][1]);
+        lagrange4_d(fmaf(h.z, s8, -8.f * bc[lb][2]), q.z * s8, ws[threadIdx.x][2]);
       } else {
         lagrange_d<NG>(tb, cell_coord_d(h.x, q.x, sc, bc[lb][0]), ws[threadIdx.x][0]);
         lagrange_d<NG>(tb, cell_coord_d(h.y, q.y, sc, bc[lb][1]), ws[threadIdx.x][1]);
@@ -239,7 +240,10 @@ __device__ __forceinline__ void apply_axis(const float *__restrict__ op, bool tr
   __syncwarp();
 }
 
-// Child-to-parent: M^P = sum_C (T^{a_x} (x) T^{a_y} (x) T^{a_z}) M^C, one parent per warp.
+// Child-to-parent: M^P = sum_C (T^{a_x} (x) T^{a_y} (x) T^{a_z}) M^C, one parent per warp,
+// for every expanded box (an internal cell, or a leaf or virtual box whose
+// children are needed as sources): its children hold all its particles, so by
+// the moment-matching identity of Sec. 2.3 this equals its P2G to rounding.
 __global__ void __launch_bounds__(kGThreads) k_m2m(int64_t b, int64_t e, GridletTables tb,
                                                   const uint8_t *__restrict__ flags,
                                                   const int *__restrict__ child, int64_t off2,
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(kGThreads) k_m2m(int64_t b, int64_t e, Gridlet
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t box = b + (int64_t)blockIdx.x * kGWarps + w;
-  if (box >= e || !(flags[box] & kInternal)) return;
+  if (box >= e || !(flags[box] & kExpand)) return;
   const int ng = tb.ng, m3 = ng * ng * ng;
   for (int p = lane; p < m3; p += 32) res[w][p] = 0.f;
   for (int o = 0; o < 8; ++o) {
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(kW * 32) k_m2m4(int64_t b, int64_t e, GridletT
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t box = b + (int64_t)blockIdx.x * kW + w;
-  if (box >= e || !(flags[box] & kInternal)) return;
+  if (box >= e || !(flags[box] & kExpand)) return;
   {
     // child o = lane / 4, 16 values each
     const int o = lane >> 2, sub = lane & 3;

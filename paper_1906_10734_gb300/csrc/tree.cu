@@ -487,7 +487,8 @@ __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
 }
 
 // Work-list selection. mode 0: real cells; 1: leaves; 2: boxes that get their
-// effective masses by P2G (not internal); 3: internal cells.
+// effective masses by P2G (not expanded: each particle's finest box); 3:
+// internal cells.
 __global__ void k_select(int64_t b, int64_t e, const uint8_t *__restrict__ flags, int mode,
                          int *__restrict__ sel) {
   const int64_t i = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -496,7 +497,7 @@ __global__ void k_select(int64_t b, int64_t e, const uint8_t *__restrict__ flags
   int v;
   if (mode == 0) v = (f & kReal) != 0;
   else if (mode == 1) v = (f & kLeaf) != 0;
-  else if (mode == 2) v = (f & kInternal) == 0;
+  else if (mode == 2) v = (f & kExpand) == 0;
   else v = (f & kInternal) != 0;
   sel[i - b] = v;
 }
@@ -869,39 +870,26 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   }
 
   // work lists: targets (cells at level >= 2), leaves, P2G boxes (level >= 2,
-  // not internal: the virtual boxes are never internal), parents of the
-  // targets (internal cells at levels >= 1); their sizes follow from the
-  // per-level counts of cells and leaves
+  // not expanded), parents of the targets (internal cells at levels >= 1); the
+  // sizes of the first, second and fourth follow from the per-level counts of
+  // cells and leaves, the P2G count is read back with the near-field counts
   const int64_t off2 = D >= 2 ? pl->lvl_off[2] : pl->nbox;
   {
-    int64_t cells2 = 0, internal2 = 0, internal1 = 0;
+    int64_t cells2 = 0, internal1 = 0;
     for (int l = 1; l <= D; ++l) {
       const int64_t internal = (int64_t)hc[l] - hc[32 + l];
       internal1 += internal;
-      if (l >= 2) {
-        cells2 += hc[l];
-        internal2 += internal;
-      }
+      if (l >= 2) cells2 += hc[l];
     }
     pl->ntgt = cells2;
     pl->nleaf = nleaf;
-    pl->np2g = (pl->nbox - off2) - internal2;
+    pl->np2g = -1;  // counted on the device (boxes at level >= 2 that are not expanded)
     pl->npar = internal1;
   }
   HPM_TRY(select_boxes(pl, off2, pl->nbox, 0, t.tgt_box, 70, st, &launches));
   HPM_TRY(select_boxes(pl, 0, pl->nbox, 1, t.leaf_box, 71, st, &launches));
   HPM_TRY(select_boxes(pl, off2, pl->nbox, 2, t.p2g_box, 72, st, &launches));
   HPM_TRY(select_boxes(pl, D >= 1 ? pl->lvl_off[1] : pl->nbox, pl->nbox, 3, t.par_box, 73, st, &launches));
-  // particle offsets of the P2G boxes (n + 1 entries, the last one the total)
-  HPM_TRY(t.p2g_off.ensure(sizeof(int) * (pl->np2g + 1), st));
-  if (pl->np2g) {
-    HPM_TRY(t.cnt.ensure(sizeof(int) * pl->np2g, st));
-    k_box_counts<<<blocks_for(pl->np2g), kThreads, 0, st>>>(pl->np2g, t.p2g_box.as<int>(), t.box_beg.as<int>(),
-                                                            t.box_end.as<int>(), t.cnt.as<int>());
-    HPM_LAUNCHED(&launches);
-    HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.p2g_off.as<int>(), pl->np2g, t.p2g_off.as<int>() + pl->np2g,
-                               t.scan, st, &launches));
-  }
   // leaf of every particle
   HPM_TRY(t.pbox.ensure(sizeof(int) * (n > 0 ? n : 1), st));
   if (pl->nleaf) {
@@ -936,10 +924,11 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     if (herr2[0] & kErrTimeout) return HPM_ERR_TIMEOUT;
     pl->nitem = hv[0];
     pl->npart = hv[1];
+    pl->np2g = hv[8];
     // the work-list sizes the host derived must be what the device selected
-    if (hv[6] != pl->ntgt || hv[7] != pl->nleaf || hv[8] != pl->np2g || hv[9] != pl->npar) {
-      fprintf(stderr, "hpm: work-list sizes disagree (device %d %d %d %d, host %lld %lld %lld %lld)\n", hv[6], hv[7],
-              hv[8], hv[9], (long long)pl->ntgt, (long long)pl->nleaf, (long long)pl->np2g, (long long)pl->npar);
+    if (hv[6] != pl->ntgt || hv[7] != pl->nleaf || hv[9] != pl->npar) {
+      fprintf(stderr, "hpm: work-list sizes disagree (device %d %d %d, host %lld %lld %lld)\n", hv[6], hv[7],
+              hv[9], (long long)pl->ntgt, (long long)pl->nleaf, (long long)pl->npar);
       return HPM_ERR_INVALID_ARG;
     }
     HPM_TRY(t.item_leaf.ensure(sizeof(int) * (pl->nitem + 1), st));
@@ -951,6 +940,16 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
                                                       t.item_leaf.as<int>(), t.item_s0.as<int>(),
                                                       t.item_s1.as<int>());
     HPM_LAUNCHED(&launches);
+  }
+  // particle offsets of the P2G boxes (n + 1 entries, the last one the total)
+  HPM_TRY(t.p2g_off.ensure(sizeof(int) * (pl->np2g + 1), st));
+  if (pl->np2g) {
+    HPM_TRY(t.cnt.ensure(sizeof(int) * pl->np2g, st));
+    k_box_counts<<<blocks_for(pl->np2g), kThreads, 0, st>>>(pl->np2g, t.p2g_box.as<int>(), t.box_beg.as<int>(),
+                                                            t.box_end.as<int>(), t.cnt.as<int>());
+    HPM_LAUNCHED(&launches);
+    HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.p2g_off.as<int>(), pl->np2g, t.p2g_off.as<int>() + pl->np2g,
+                               t.scan, st, &launches));
   }
   HPM_TRY(t.box_tgt.ensure(sizeof(int) * (pl->nbox > 0 ? pl->nbox : 1), st));
   HPM_CUDA(cudaMemsetAsync(t.box_tgt.p, 0xff, sizeof(int) * pl->nbox, st));
