@@ -727,7 +727,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
           for (int u = 0; u < 8; ++u) r2min = fminf(r2min, pair_fast(th, srh[w][k + u * G], eps2, bp, bx, by, bz));
           if (__any_sync(__activemask(), r2min <= near2)) {
             bp = bx = by = bz = 0.f;
-#pragma unroll
+#pragma unroll 4
             for (int u = 0; u < 8; ++u) {
               const int kk = k + u * G;
               pair_exact(th, tl, srh[w][kk], srl[w][kk], eps2, bp, bx, by, bz);
