@@ -123,9 +123,9 @@ hpm_status hpm_plan(const hpm_domain *dom, int max_depth, int gridlet_order,
  * Builds Morton keys from the FP64 positions, sorts the particles by their
  * level-max_depth key (ties by index), the per-level cell tables, the near
  * zone of every leaf and the interaction-zone occupancy of every cell at
- * level >= 2. Reads back one small count per level (host synchronisation on
- * `stream`). Errors: HPM_ERR_INVALID_ARG, HPM_ERR_OUT_OF_DOMAIN, HPM_ERR_OOM,
- * HPM_ERR_CUDA.
+ * level >= 2. Reads back the per-level box counts and then the work-list
+ * sizes (two host synchronisations on `stream`). Errors: HPM_ERR_INVALID_ARG,
+ * HPM_ERR_OUT_OF_DOMAIN, HPM_ERR_OOM, HPM_ERR_CUDA, HPM_ERR_TIMEOUT.
  */
 hpm_status hpm_build_tree(hpm_plan_t plan, const double *d_pos, int64_t n, void *stream);
 
@@ -152,7 +152,8 @@ hpm_status hpm_solve(hpm_plan_t plan, const double *d_pos, const double *d_mass,
  * plan's domain, depth, gridlet order, kernel and split rule. hpm_solve then
  * solves every problem of the batch in one pass over the packed arrays (masses
  * and outputs packed the same way). Problems may be empty. Needs 3 max_depth +
- * ceil(log2 P) <= 63. Reads back one count per level (host synchronisation).
+ * ceil(log2 P) <= 63. Reads back the number of nonempty problems, the
+ * per-level box counts and the work-list sizes (three host synchronisations).
  * Errors as hpm_build_tree.
  */
 hpm_status hpm_build_tree_batch(hpm_plan_t plan, const double *d_pos, const int64_t *h_offsets, int n_problems,
