@@ -124,6 +124,37 @@ def test_child_to_parent_is_exact(ng):
     assert np.max(np.abs(acc - Mp)) < 1e-12 * mass.sum()
 
 
+@pytest.mark.parametrize("ng", [2, 4])
+def test_every_box_equals_child_to_parent_of_its_children_adaptive(ng):
+    """On an adaptive tree, every nonempty box at level >= 2 (real cells and the virtual
+    boxes inside coarser leaves alike) has P2G equal to sum_C T^C M^C of its nonempty
+    children's P2G (Sec. 2.3): the child-to-parent transform can stand in for P2G on any
+    box whose children are all present, which is how the GPU path fills expanded boxes."""
+    w = I.small_plummer(4000, 17, leaf_max=16, max_depth=7)
+    tr = O.Tree(w.pos, max_depth=w.max_depth, leaf_max=w.leaf_max)
+    smass = w.mass[tr.perm]
+    _, _, T = O.paper_matrices(ng)
+    checked = virtual = 0
+    for l in range(2, tr.depth):
+        lv, ch = tr.levels[l], tr.levels[l + 1]
+        pb, cb = np.arange(lv.keys.shape[0]), np.arange(ch.keys.shape[0])
+        Mp = O.p2g(ng, lv.begin, lv.end, tr.centers(l, pb), np.full(pb.size, tr.box_side(l)), tr.spos, smass)
+        Mc = O.p2g(ng, ch.begin, ch.end, tr.centers(l + 1, cb), np.full(cb.size, tr.box_side(l + 1)), tr.spos,
+                   smass)
+        par = lv.find(ch.keys >> np.uint64(3))
+        assert np.all(par >= 0)
+        octant = (ch.keys & np.uint64(7)).astype(np.int64)
+        acc = np.zeros_like(Mp)
+        for c in range(8):
+            sel = octant == c
+            np.add.at(acc, par[sel], Mc[sel] @ T[c].T)
+        box_mass = np.add.reduceat(smass, lv.begin) if lv.begin.size else np.zeros(0)
+        assert np.max(np.abs(acc - Mp) / box_mass[:, None]) < 1e-12
+        checked += pb.size
+        virtual += int(np.count_nonzero(~lv.real))
+    assert checked > 100 and virtual > 10
+
+
 @pytest.mark.parametrize("ng", [2, 3, 4])
 def test_parent_to_child_is_transpose_of_child_to_parent(ng):
     """Sec. 2.4: evaluating Eq. phix at (a^C + x_p)/2 after Eq. c2pmat is (T^C)^T."""
