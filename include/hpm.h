@@ -181,8 +181,11 @@ hpm_status hpm_solve_batch(hpm_plan_t plan, const hpm_problem *h_problems, int n
 
 /*
  * hpm_solve_host - the same solve from and to host memory: copies the
- * positions and masses in, builds the tree, solves and copies phi and acc back,
- * then synchronises `stream`. h_phi / h_acc may be NULL.
+ * positions in and builds the tree while the masses are copied in on a stream
+ * of the plan's own (ordered after the positions' copy; the solve waits for
+ * it), solves, copies phi and acc back, then synchronises `stream`. No copy
+ * from the caller's buffers outlives the call, error paths included.
+ * h_phi / h_acc may be NULL.
  */
 hpm_status hpm_solve_host(hpm_plan_t plan, const double *h_pos, const double *h_mass, int64_t n,
                           float *h_phi, float *h_acc, void *stream);

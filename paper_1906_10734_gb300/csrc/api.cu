@@ -245,12 +245,35 @@ hpm_status hpm_solve_host(hpm_plan_t plan, const double *h_pos, const double *h_
   HPM_TRY(plan->host_io_phi.ensure(sizeof(float) * nn, st));
   HPM_TRY(plan->host_io_acc.ensure(sizeof(float) * 3 * nn, st));
   if (n > 0) {
+    if (!plan->io_stream) {
+      HPM_CUDA(cudaStreamCreateWithFlags(&plan->io_stream, cudaStreamNonBlocking));
+      for (auto &ev : plan->io_ev) HPM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
     HPM_CUDA(cudaMemcpyAsync(plan->host_io_pos.p, h_pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
-    HPM_CUDA(cudaMemcpyAsync(plan->host_io_mass.p, h_mass, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    // the masses follow the positions on the copy engine but are first needed
+    // by the solve, so their copy overlaps the tree build
+    HPM_CUDA(cudaEventRecord(plan->io_ev[0], st));
+    HPM_CUDA(cudaStreamWaitEvent(plan->io_stream, plan->io_ev[0], 0));
+    HPM_CUDA(cudaMemcpyAsync(plan->host_io_mass.p, h_mass, sizeof(double) * n, cudaMemcpyHostToDevice,
+                             plan->io_stream));
+    HPM_CUDA(cudaEventRecord(plan->io_ev[1], plan->io_stream));
   }
-  HPM_TRY(hpm_build_tree(plan, plan->host_io_pos.as<double>(), n, stream));
-  HPM_TRY(hpm_solve(plan, plan->host_io_pos.as<double>(), plan->host_io_mass.as<double>(),
-                    plan->host_io_phi.as<float>(), plan->host_io_acc.as<float>(), stream));
+  hpm_status s = hpm_build_tree(plan, plan->host_io_pos.as<double>(), n, stream);
+  if (n > 0) {
+    const cudaError_t e = cudaStreamWaitEvent(st, plan->io_ev[1], 0);
+    if (e != cudaSuccess && s == HPM_OK) {
+      hpm::set_cuda_error(e);
+      s = HPM_ERR_CUDA;
+    }
+  }
+  if (s == HPM_OK)
+    s = hpm_solve(plan, plan->host_io_pos.as<double>(), plan->host_io_mass.as<double>(),
+                  plan->host_io_phi.as<float>(), plan->host_io_acc.as<float>(), stream);
+  if (s != HPM_OK) {
+    // no copy from the caller's buffers may outlive the call
+    if (n > 0) cudaStreamSynchronize(plan->io_stream);
+    return s;
+  }
   if (n > 0 && h_phi)
     HPM_CUDA(cudaMemcpyAsync(h_phi, plan->host_io_phi.p, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
   if (n > 0 && h_acc)
@@ -417,6 +440,9 @@ hpm_status hpm_destroy(hpm_plan_t plan) {
   cudaStreamSynchronize(0);
   for (auto &ev : plan->ev)
     if (ev) cudaEventDestroy(ev);
+  for (auto &ev : plan->io_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (plan->io_stream) cudaStreamDestroy(plan->io_stream);
   cudaGetLastError();
   delete plan;
   return HPM_OK;

@@ -165,6 +165,10 @@ struct hpm_plan_s {
   cudaEvent_t ev[12] = {};  // stage boundaries 0..7, tree 8..9, dense product kernel 10..11
   bool events_ready = false;
   hpm::DevBuf host_io_pos, host_io_mass, host_io_phi, host_io_acc;
+  // hpm_solve_host: the masses' host-to-device copy runs on a stream of its
+  // own, after the positions' copy, while the tree is built
+  cudaStream_t io_stream = nullptr;
+  cudaEvent_t io_ev[2] = {};
   hpm::DevBuf batch_desc;          // device copy of a batch's problem table and offsets
 };
 

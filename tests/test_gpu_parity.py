@@ -178,8 +178,14 @@ def test_host_entry_point_matches_device_path(hpm):
     hphi = np.zeros(w.n, np.float32)
     hacc = np.zeros((w.n, 3), np.float32)
     hpm.hpm_solve_host(plan, np.ascontiguousarray(w.pos), np.ascontiguousarray(w.mass), hphi, hacc)
-    hpm.hpm_destroy(plan)
     assert np.array_equal(hphi.astype(np.float64), phi) and np.array_equal(hacc.astype(np.float64), acc)
+    # a second call on the same plan with other masses: the solve must wait for
+    # this call's mass copy (it runs on a stream of its own)
+    m2 = np.random.default_rng(1).random(w.n) / w.n
+    phi2, acc2, _ = gpu_solve(hpm, w.pos, m2, w.max_depth, w.ng, w.eps, w.leaf_max)
+    hpm.hpm_solve_host(plan, np.ascontiguousarray(w.pos), np.ascontiguousarray(m2), hphi, hacc)
+    hpm.hpm_destroy(plan)
+    assert np.array_equal(hphi.astype(np.float64), phi2) and np.array_equal(hacc.astype(np.float64), acc2)
 
 
 def test_repeatable_and_linear(hpm):
