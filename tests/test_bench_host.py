@@ -1,0 +1,64 @@
+"""Host-side arithmetic of bench.py, without a GPU.
+
+The roofline object must be the executed tensor work of the dense kernel over
+its own duration against the measured peak; the DRAM traffic must come from a
+committed ncu summary only while the kernel source still has the sha256 the
+summary names; the clock sampler must report throttle reasons it sees.
+"""
+import os
+import tempfile
+
+import pytest
+
+import bench
+
+
+def test_dense_roofline_is_executed_work_over_kernel_time():
+    steps = [{"ms_m2l": 1.2, "ms_m2l_kernel": 1.0, "m2l_parents": 30000},
+             {"ms_m2l": 1.2, "ms_m2l_kernel": 1.0, "m2l_parents": 30000}]
+    r = bench.roofline_of(steps, 4, 240000, None)
+    flop = 3 * 2 * 512 * 13824 * 30000
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(flop / 1.0e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["traffic"] is None
+    # the nominal FFT rate of the whole stage rides along
+    assert r["stage_nominal_fft_tflops"] == pytest.approx(bench.m2l_flops_per_target(4) * 240000 / 1.2e-3 / 1e12)
+
+
+def test_fft_roofline_against_fp32_peak():
+    steps = [{"ms_m2l": 8.0, "ms_m2l_kernel": 0.0, "m2l_parents": 0}]
+    r = bench.roofline_of(steps, 4, 100000, None)
+    assert r["bound"] == "alu"
+    assert r["achieved"] == pytest.approx(bench.m2l_flops_per_target(4) * 100000 / 8.0e-3 / 1e12)
+
+
+def test_nominal_fft_count_at_order_4():
+    # P = 32: 5 P^3 log2(P^3) + 2 P^2 (P/2 + 1)
+    assert bench.m2l_flops_per_target(4) == 5 * 32 ** 3 * 15 + 2 * 32 * 32 * 17
+
+
+def test_traffic_only_for_the_profiled_source():
+    src = os.path.join(bench.ROOT, "paper_1906_10734_gb300", "csrc", "m2l_tc.cu")
+    t = bench.profile_traffic(src)
+    if t is not None:
+        assert t > 1e8      # a full-size launch moves hundreds of MB
+    with tempfile.NamedTemporaryFile("w", suffix=".cu", delete=False) as f:
+        f.write("// another kernel source\n")
+    try:
+        assert bench.profile_traffic(f.name) is None
+    finally:
+        os.unlink(f.name)
+
+
+def test_clock_summary_reports_reasons():
+    s = bench.ClockSampler(0)
+    fd, s.path = tempfile.mkstemp(suffix=".csv")
+    with os.fdopen(fd, "w") as f:
+        f.write("0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("0, 1980, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active\n")
+        f.write("0, 2010, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n")
+    out = s.summary()
+    assert out["sm_mhz"] == 2010 and out["sm_max_mhz"] == 2070 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
+    assert not os.path.exists(s.path)
