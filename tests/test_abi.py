@@ -3,7 +3,6 @@
 No compute call is made here (this suite also runs without a GPU); only the
 argument checks that return before any CUDA call are exercised.
 """
-import ctypes
 import os
 import re
 

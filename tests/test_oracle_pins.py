@@ -5,7 +5,6 @@ closed form (tests/golden), an identity the paper states, an invariant, a
 special case with a textbook answer, or brute force on a tiny input.
 """
 import json
-import math
 import os
 
 import numpy as np
