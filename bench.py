@@ -35,8 +35,7 @@ from paper_1906_10734_gb300 import inputs as I  # noqa: E402
 
 METRIC = "particles/s for full HPM force solve at stated force error; p50/p99 latency"
 UNIT = "particles/s"
-FP32_LANES_PER_SM = 128
-SM_COUNT_GB300 = 152
+P2P_FLOP_PER_PAIR = 20     # the usual N-body count (Kahan compensation not counted)
 
 
 def m2l_flops_per_target(ng: int) -> float:
@@ -49,38 +48,92 @@ def m2l_flops_per_target(ng: int) -> float:
 DENSE_FLOP_PER_PARENT = 3 * 2 * 512 * 216 * 64   # three FP16 products per term of the 512 x 13824 product
 
 
-def roofline_of(stats_steps, ng, n_targets, traffic_src):
+def alu_peaks() -> dict:
+    """FP32 / FP64 FMA and rsqrt peaks of this GPU from the committed microbenchmark summary
+    (profiles/alu_peaks_gb300.md, written by hpm_measure_alu_peaks); {} if absent."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", "alu_peaks_gb300.md")).read()
+    except OSError:
+        return {}
+    out = {}
+    for key in ("fp32_tflops", "fp64_tflops", "rsqrt_gops"):
+        m = re.search(key + r":\s*([0-9.eE+]+)", text)
+        if m:
+            out[key] = float(m.group(1))
+    return out
+
+
+def fp32_peak(live: dict | None) -> tuple[float, str]:
+    """Measured FP32 FFMA peak (TFLOP/s) and where it comes from: the committed summary,
+    else this run's own measurement."""
+    p = alu_peaks().get("fp32_tflops")
+    if p:
+        return p, "profiles/alu_peaks_gb300.md fp32_tflops (hpm_measure_alu_peaks on GB300) of measured"
+    if live and live.get("fp32_tflops"):
+        return live["fp32_tflops"], "hpm_measure_alu_peaks in this run, of measured"
+    return float("nan"), "no measured FP32 peak"
+
+
+def roofline_of(stats_steps, ng, n_targets, traffic_src, live_peaks=None):
     """Roofline object of the source-to-target kernel of the last steps.
 
-    Ng = 4 default path (dense product on the tensor cores): executed tensor FLOP of
-    the kernel alone (three FP16 products per term) per its own CUDA-event duration,
-    against the measured dense bf16 burst peak (FP16 runs at the bf16 rate). FFT and
-    any-order kernels: the nominal FFT count per target over the stage time against
-    the FP32 FFMA peak. Both report the nominal FFT rate of the whole stage too."""
+    `achieved` is the ALGORITHMIC work: the nominal FFT-convolution count per target
+    (5 P^3 log2 P^3 + 2 P^2 (P/2+1), P = 8 Ng) times the targets, per launch duration.
+    Ng = 4 default path (dense product on the tensor cores): over the kernel's own
+    CUDA-event time, against the measured dense bf16 burst peak (FP16 has the bf16
+    tensor rate); the executed dense work (three FP16 products per term) is reported
+    beside it. FFT-form and any-order kernels: over the stage time, against the measured
+    FP32 FFMA peak."""
     peaks = measured_peaks()
     stage_ms = statistics.mean(s["ms_m2l"] for s in stats_steps)
-    nominal = m2l_flops_per_target(ng) * n_targets / (stage_ms / 1e3) / 1e12
+    nominal_flop = m2l_flops_per_target(ng) * n_targets
     parents = stats_steps[-1].get("m2l_parents", 0)
     if parents:
         kms = statistics.mean(s["ms_m2l_kernel"] for s in stats_steps)
-        achieved = DENSE_FLOP_PER_PARENT * parents / (kms / 1e3) / 1e12
+        achieved = nominal_flop / (kms / 1e3) / 1e12
+        executed = DENSE_FLOP_PER_PARENT * parents / (kms / 1e3) / 1e12
         peak = peaks.get("bf16_tflops", 1900.0)
         return {"kernel": "k_m2l_tc: Ng = 4 source-to-target as a dense FP16-pair tcgen05 product per parent block",
                 "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": profile_traffic(traffic_src) if traffic_src else None, "ms_per_launch": kms,
-                "launches_per_step": 1, "flop_per_parent": DENSE_FLOP_PER_PARENT, "parents_per_launch": parents,
+                "launches_per_step": 1, "flop_per_target": m2l_flops_per_target(ng),
+                "targets_per_launch": n_targets,
+                "flop_basis": "nominal FFT convolution work per target x targets (algorithmic)",
                 "peak_basis": "MEASURED_PEAKS.json bf16_tflops (dense, burst) of measured; FP16 has the bf16 tensor rate",
-                "flop_basis": "3 FP16 products (hi*hi, hi*lo, lo*hi) x 2 x 512 rows x 13824 K per parent",
-                "stage_ms": stage_ms, "stage_nominal_fft_tflops": nominal}
-    sm_mhz_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
+                "executed": {"achieved": executed, "frac": executed / peak, "flop_per_parent": DENSE_FLOP_PER_PARENT,
+                             "parents_per_launch": parents,
+                             "basis": "3 FP16 products (hi*hi, hi*lo, lo*hi) x 2 x 512 rows x 13824 K per parent"},
+                "stage": {"ms": stage_ms, "achieved": nominal_flop / (stage_ms / 1e3) / 1e12,
+                          "frac": nominal_flop / (stage_ms / 1e3) / 1e12 / peak,
+                          "basis": "same nominal work over the whole source-to-target stage (preparation "
+                                   "kernels k_level_amax, k_split, k_col_exp included)"}}
+    peak, basis = fp32_peak(live_peaks)
+    achieved = nominal_flop / (stage_ms / 1e3) / 1e12
     return {"kernel": "source-to-target FFT convolution (k_m2l4)" if ng == 4 else
                       "source-to-target convolution, x-transform kernel (k_m2l_xdft)",
-            "bound": "alu", "achieved": nominal, "peak": fp32_peak, "unit": "TFLOP/s", "frac": nominal / fp32_peak,
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": profile_traffic(traffic_src) if traffic_src else None, "ms_per_launch": stage_ms,
             "launches_per_step": 1, "flop_per_target": m2l_flops_per_target(ng), "targets_per_launch": n_targets,
-            "peak_basis": f"{SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_mhz_max:.0f} MHz "
-                          "(nominal FFMA rate)"}
+            "flop_basis": "nominal FFT convolution work per target x targets (algorithmic)", "peak_basis": basis}
+
+
+def p2p_roofline(stats_steps, live_peaks=None) -> dict:
+    """Near field: 20 FLOP per near-zone pair over the near-field stage time against the
+    measured FP32 FFMA peak, and pairs per second against the measured rsqrt rate (one
+    reciprocal square root per pair)."""
+    pairs = stats_steps[-1].get("p2p_pairs", 0)
+    ms = statistics.mean(s["ms_p2p"] for s in stats_steps)
+    if not pairs or not ms:
+        return {}
+    peak, basis = fp32_peak(live_peaks)
+    achieved = P2P_FLOP_PER_PAIR * pairs / (ms / 1e3) / 1e12
+    out = {"kernel": "k_p2p (+ k_p2p_combine): Kahan-compensated FP32 near field", "bound": "alu",
+           "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "pairs": pairs,
+           "ms": ms, "flop_basis": f"{P2P_FLOP_PER_PAIR} FLOP per near-zone pair (j != i)", "peak_basis": basis}
+    rs = alu_peaks().get("rsqrt_gops") or (live_peaks or {}).get("rsqrt_gops")
+    if rs:
+        out["rsqrt_frac"] = pairs / (ms / 1e3) / (rs * 1e9)
+    return out
 
 
 def workload_for(rank: int, n_override: int | None = None, kind: str = "plummer", ng: int = 4) -> I.Workload:
@@ -244,6 +297,8 @@ def run_gpu(args) -> None:
     step()
     torch.cuda.synchronize(dev)
     info = hpm.hpm_get_lists_info(plan)
+    live_peaks = hpm.hpm_measure_alu_peaks(stream) if rank == 0 else None   # untimed
+    torch.cuda.synchronize(dev)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -296,7 +351,7 @@ def run_gpu(args) -> None:
     traffic_src = None
     if args.workload == "plummer" and w.ng == 4:
         traffic_src = os.path.join(csrc, "m2l_tc.cu" if args.m2l == "tensor" else "m2l.cu")
-    roofline = roofline_of(stats_steps, w.ng, info["n_targets"], traffic_src)
+    roofline = roofline_of(stats_steps, w.ng, info["n_targets"], traffic_src, live_peaks)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -314,6 +369,8 @@ def run_gpu(args) -> None:
         "gpu_launches": int(launches),
         "stages_ms": {k[3:]: v / args.steps for k, v in stage_sum.items()},
         "roofline": roofline,
+        "rooflines_other": {"p2p": p2p_roofline(stats_steps, live_peaks)},
+        "alu_peaks_this_run": live_peaks,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:

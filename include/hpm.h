@@ -92,9 +92,10 @@ enum {
                                   Sec. 2.1 (register FFT-32 kernel) instead of the
                                   default dense tensor-core product, which computes
                                   the same convolution over each parent's 6^3 block
-                                  with three TF32 products per term (same result up
-                                  to FP32 rounding; needs 57 MB of device tables per
-                                  level 2..max_depth, built by hpm_plan)             */
+                                  with three FP16 products per term (hi*hi, hi*lo,
+                                  lo*hi of FP16 pairs; same result up to FP32
+                                  rounding; needs 28.3 MB of device tables per level
+                                  2..max_depth, built by hpm_plan)                   */
 };
 
 /*
@@ -261,6 +262,8 @@ typedef struct {
                               kernel alone (0 on the other paths)         */
   int64_t m2l_parents;     /* parents whose 6^3 blocks that kernel
                               multiplied (0 on the other paths)           */
+  int64_t p2p_pairs;       /* near-zone pairs (i, j), j != i, summed by
+                              the near field of the last solve            */
 } hpm_stats;
 
 hpm_status hpm_get_stats(hpm_plan_t plan, hpm_stats *stats);
@@ -342,7 +345,9 @@ typedef struct {
   int64_t submitted, completed, rejected, cancelled, failed, batches, queued;
   int64_t in_flight_bytes;  /* estimated device bytes of the batches in flight */
   int64_t particles;        /* particles of completed requests                 */
-  double p50_ms, p99_ms, mean_ms;   /* submit -> results in the caller's buffers */
+  double p50_ms, p99_ms;    /* submit -> results in the caller's buffers, over the
+                               last 65,536 completions                           */
+  double mean_ms;           /* the same, over all completions since the last reset */
   double particles_per_s;   /* completed particles / (last completion - first submit) */
 } hpm_server_stats;
 
@@ -352,16 +357,22 @@ hpm_status hpm_server_create(const hpm_server_opts *opts, hpm_server_t *out);
 /* Queues a request; *ticket identifies it. A request whose estimated footprint
  * exceeds the whole budget is refused with HPM_ERR_OOM. Never blocks on the GPU. */
 hpm_status hpm_server_submit(hpm_server_t server, const hpm_request *req, uint64_t *ticket);
-/* *done: 1 finished, 0 pending, -1 cancelled or failed; latency in ms once done. */
+/* *done: 1 finished, 0 pending, -1 cancelled or failed; latency in ms once done.
+ * Once a call reports a final state (*done != 0) the server forgets the
+ * request: the ticket is then unknown (HPM_ERR_INVALID_ARG). */
 hpm_status hpm_server_poll(hpm_server_t server, uint64_t ticket, int *done, double *latency_ms);
 /* Waits at most timeout_ms (bounded wait): HPM_ERR_TIMEOUT if still pending,
- * HPM_ERR_INVALID_ARG if it was cancelled. */
+ * HPM_ERR_INVALID_ARG if it was cancelled, HPM_ERR_BUSY if the server is
+ * being destroyed meanwhile. A return with the final state (HPM_OK, a failed
+ * solve's status, or cancelled) ends the ticket as for hpm_server_poll. */
 hpm_status hpm_server_wait(hpm_server_t server, uint64_t ticket, int timeout_ms, double *latency_ms);
 /* Cancels a request that is still queued; HPM_ERR_BUSY once it runs or ran. */
 hpm_status hpm_server_cancel(hpm_server_t server, uint64_t ticket);
 hpm_status hpm_server_get_stats(hpm_server_t server, hpm_server_stats *stats);
 hpm_status hpm_server_reset_stats(hpm_server_t server);
-/* Stops the workers after their current batch and frees everything. */
+/* Stops the workers after their current batch and frees everything. Threads
+ * blocked in hpm_server_wait are woken first and return HPM_ERR_BUSY; no
+ * other call on the server may run concurrently with, or follow, this one. */
 hpm_status hpm_server_destroy(hpm_server_t server);
 
 /*
@@ -387,11 +398,31 @@ hpm_status hpm_server_destroy(hpm_server_t server);
  * array and each call overwrites it, so calls that overlap on the GPU (other
  * streams, other threads) race and must be serialised by the caller. Reads
  * back one error word and synchronises `stream`.
- * Errors: HPM_ERR_INVALID_ARG, HPM_ERR_OUT_OF_DOMAIN, HPM_ERR_CUDA.
+ * Errors: HPM_ERR_INVALID_ARG, HPM_ERR_OUT_OF_DOMAIN, HPM_ERR_CUDA,
+ * HPM_ERR_TIMEOUT (a bounded wait of the sort's scan gave up),
+ * HPM_ERR_UNSUPPORTED (a device index of 64 or more).
  */
 #define HPM_STATIC_SORT_MAX_N 1048576
 hpm_status hpm_sort_particles_static(const hpm_domain *dom, int max_depth, const double *d_pos, int64_t n,
                                      uint64_t *d_keys, uint32_t *d_perm, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Measured arithmetic peaks of the current device (no counterpart in the
+ * paper): the denominators of the rooflines of the kernels bound by CUDA-core
+ * arithmetic. Each rate comes from a kernel of independent dependent-FMA (or
+ * rsqrt) chains filling every SM, best of three launches of several
+ * milliseconds timed with CUDA events on `stream` (synchronised). Scratch:
+ * 64 bytes from the library's pool. Errors: HPM_ERR_INVALID_ARG,
+ * HPM_ERR_CUDA, HPM_ERR_OOM.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  double fp32_tflops;   /* FFMA, 2 FLOP per lane and instruction      */
+  double fp64_tflops;   /* DFMA, 2 FLOP per lane and instruction      */
+  double rsqrt_gops;    /* FP32 reciprocal square roots per second / 1e9 */
+  double ms_fp32, ms_fp64, ms_rsqrt;  /* best launch durations         */
+  int sm_count;
+} hpm_alu_peaks;
+hpm_status hpm_measure_alu_peaks(hpm_alu_peaks *out, void *stream);
 
 /* Frees the plan and everything it owns. NULL is allowed. */
 hpm_status hpm_destroy(hpm_plan_t plan);

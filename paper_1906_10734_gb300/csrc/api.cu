@@ -15,16 +15,49 @@ const char *set_cuda_error(cudaError_t e) {
   return g_cuda_err;
 }
 
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[kMaxDevices] = {};
+
+hpm_status lib_pool(cudaMemPool_t *out) {
+  int dev = 0;
+  HPM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return HPM_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    HPM_CUDA(cudaMemPoolCreate(&pool, &props));
+    // keep freed blocks in this pool between solves instead of returning them
+    // to the driver at every synchronisation
+    uint64_t thr = UINT64_MAX;
+    HPM_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    g_pool[dev] = pool;
+  }
+  *out = g_pool[dev];
+  return HPM_OK;
+}
+
+hpm_status lib_malloc_async(void **p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool = nullptr;
+  HPM_TRY(lib_pool(&pool));
+  const cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? HPM_ERR_OOM : HPM_ERR_CUDA;
+  }
+  return HPM_OK;
+}
+
 hpm_status DevBuf::ensure(size_t bytes, cudaStream_t s, bool keep) {
   if (bytes <= cap && p) return HPM_OK;
   size_t ncap = bytes + bytes / 4 + 256;
   void *np = nullptr;
-  cudaError_t e = cudaMallocAsync(&np, ncap, s);
-  if (e != cudaSuccess) {
-    set_cuda_error(e);
-    cudaGetLastError();
-    return HPM_ERR_OOM;
-  }
+  HPM_TRY(lib_malloc_async(&np, ncap, s));
   if (keep && p && cap) HPM_CUDA(cudaMemcpyAsync(np, p, cap, cudaMemcpyDeviceToDevice, s));
   if (p) HPM_CUDA(cudaFreeAsync(p, s));
   p = np;
@@ -125,15 +158,6 @@ hpm_status hpm_plan(const hpm_domain *dom, int max_depth, int gridlet_order, con
   pl->green = *green;
   pl->opts = opts ? *opts : hpm_plan_opts{0, 0};
   cudaGetDevice(&pl->device);
-  {
-    // keep freed device memory in the stream-ordered pool between solves
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, pl->device) == cudaSuccess) {
-      uint64_t thr = UINT64_MAX;
-      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    }
-    cudaGetLastError();
-  }
   make_tables(gridlet_order, pl->tab);
   hpm_status s = precompute_green(pl, 0);
   if (s == HPM_OK) s = tc_precompute(pl, 0);

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <vector>
 
 #include "../../include/hpm.h"
@@ -28,6 +29,19 @@ enum : uint8_t {
 // Device error word bits.
 enum : int { kErrDomain = 1, kErrCapacity = 2, kErrTimeout = 4 };
 
+// Radix sort and single-pass scan sizing (sort.cu): elements per sort tile,
+// digits per pass, elements per scan tile. The no-allocation sort sizes its
+// static scratch from these.
+constexpr int kSortTileElems = 4096;
+constexpr int kRadixDigits = 256;
+constexpr int kScanTileElems = 2048;
+// ints of histogram and offsets radix_sort_pairs needs for n elements
+constexpr int64_t sort_scratch_ints(int64_t n) {
+  return 2 * (int64_t)kRadixDigits * ((n + kSortTileElems - 1) / kSortTileElems);
+}
+// scan tiles (status words) of a scan over n elements
+constexpr int64_t scan_tiles_of(int64_t n) { return (n + kScanTileElems - 1) / kScanTileElems; }
+
 // Near-field work item size: pairs per warp-sized item (and at least this many
 // sources per item).
 constexpr int64_t kP2PPairsPerItem = 16384;
@@ -35,7 +49,27 @@ constexpr int kP2PMinSources = 32;
 
 const char *set_cuda_error(cudaError_t e);
 
-// Grow-only device buffer on the stream-ordered allocator.
+// Devices a process may use the library on (per-device caches below).
+constexpr int kMaxDevices = 64;
+
+// A value set up once per device (a function attribute, an occupancy, the
+// SM count), under a lock: the serving loop's workers and callers on other
+// devices share these.
+struct DeviceCache {
+  std::mutex mu;
+  int value[kMaxDevices] = {};
+  bool ready[kMaxDevices] = {};
+};
+
+// Device memory pool owned by the library on the current device (created on
+// first use, kept until the process exits). Its release threshold keeps freed
+// blocks for reuse between solves; the device's default pool, which other
+// code in the caller's process may use, is left as it is.
+hpm_status lib_pool(cudaMemPool_t *out);
+// Stream-ordered allocation from that pool.
+hpm_status lib_malloc_async(void **p, size_t bytes, cudaStream_t s);
+
+// Grow-only device buffer on the library's stream-ordered pool.
 struct DevBuf {
   void *p = nullptr;
   size_t cap = 0;
@@ -155,6 +189,7 @@ struct hpm_plan_s {
   int depth_reached = -1;
   int64_t nbox = 0, ntgt = 0, nleaf = 0, np2g = 0, ncell = 0;
   int64_t nitem = 0, npart = 0;   // near-field work items, partial-sum rows
+  int64_t npairs = 0;              // near-zone pairs (i, j), j != i
   int64_t npar = 0;                // internal cells at levels >= 1 (parents of targets)
   std::vector<int64_t> tgt_lvl_off;  // target offsets per level (levels 2..D)
   std::vector<int64_t> leaf_lvl_off;
@@ -224,6 +259,26 @@ hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches);
     hpm_status s_ = (call);           \
     if (s_ != HPM_OK) return s_;      \
   } while (0)
+
+namespace hpm {
+// The cached value of `c` for the current device, computed by `compute(int *)`
+// (an hpm_status-returning callable) the first time.
+template <class F>
+hpm_status device_cached(DeviceCache &c, F &&compute, int *out) {
+  int dev = 0;
+  HPM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return HPM_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(c.mu);
+  if (!c.ready[dev]) {
+    int v = 0;
+    HPM_TRY(compute(&v));
+    c.value[dev] = v;
+    c.ready[dev] = true;
+  }
+  *out = c.value[dev];
+  return HPM_OK;
+}
+}  // namespace hpm
 
 #define HPM_LAUNCHED(counter)                           \
   do {                                                  \

@@ -654,26 +654,32 @@ __global__ void __launch_bounds__(kThreads) k_m2l_generic(const __grid_constant_
 template <int NG>
 hpm_status launch_xd(const xd::Params &p, int64_t grid, cudaStream_t st) {
   constexpr size_t smem = xd::Geo<NG>::kSmem;
-  static bool attr = false;
-  if (!attr) {
+  static DeviceCache attr_cache;
+  int done = 0;
+  HPM_TRY(device_cached(attr_cache, [](int *v) -> hpm_status {
     HPM_CUDA(cudaFuncSetAttribute(xd::k_m2l_xdft<NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+    *v = 1;
+    return HPM_OK;
+  }, &done));
   xd::k_m2l_xdft<NG><<<(unsigned)grid, xd::Launch<NG>::threads, smem, st>>>(p);
   return HPM_OK;
 }
 
 }  // namespace
 
-// Streaming multiprocessors of the current device (cached).
+// Streaming multiprocessors of the current device (cached per device; 1 if
+// the query fails).
 int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
+  static DeviceCache cache;
+  int n = 1;
+  if (device_cached(cache, [](int *v) -> hpm_status {
+        int dev = 0;
+        HPM_CUDA(cudaGetDevice(&dev));
+        HPM_CUDA(cudaDeviceGetAttribute(v, cudaDevAttrMultiProcessorCount, dev));
+        if (*v <= 0) *v = 1;
+        return HPM_OK;
+      }, &n) != HPM_OK)
+    return 1;
   return n;
 }
 
@@ -709,11 +715,13 @@ hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
     p.kz_stride = pl->kz_green_stride;
     p.tblk = pl->t.tgt_blk.as<int>();
     p.tinfo = pl->t.tgt_info.as<int>();
-    static bool attr = false;
-    if (!attr) {
+    static DeviceCache attr_cache;
+    int done = 0;
+    HPM_TRY(device_cached(attr_cache, [](int *v) -> hpm_status {
       HPM_CUDA(cudaFuncSetAttribute(f4::k_m2l4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f4::kSmem));
-      attr = true;
-    }
+      *v = 1;
+      return HPM_OK;
+    }, &done));
     const int per_sm = pl->tuning.m2l_ctas_per_sm == 1 ? 1 : 2;  // 2 fit (111 KB each)
     const int64_t grid = std::min<int64_t>(pl->ntgt, (int64_t)per_sm * nsm);
     f4::k_m2l4<<<(unsigned)grid, f4::kThreads, f4::kSmem, st>>>(p);

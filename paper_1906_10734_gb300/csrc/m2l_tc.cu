@@ -823,7 +823,7 @@ hpm_status tc_precompute(hpm_plan_s *pl, cudaStream_t st) {
   const int64_t nthr = (int64_t)tc::kQuarters * tc::kChunks * tc::kRows;
   const unsigned nblk = (unsigned)((nthr + 255) / 256);
   int *rowmax = nullptr;
-  HPM_CUDA(cudaMallocAsync((void **)&rowmax, sizeof(int) * tc::kQuarters * tc::kRows, st));
+  HPM_TRY(lib_malloc_async((void **)&rowmax, sizeof(int) * tc::kQuarters * tc::kRows, st));
   for (int l = 2; l <= D; ++l) {
     const double h = pl->dom.side / (double)(1u << l) / (double)pl->ng;
     const double *mean_l = pl->tc_mean.as<double>() + 8 * l;
@@ -916,21 +916,22 @@ hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   p.stall = pl->test_stall;
   for (int l = 0; l <= kMaxDepth && 8 * l + 7 < (int)pl->tc_mean_host.size(); ++l)
     for (int o = 0; o < 8; ++o) p.mean[l][o] = pl->tc_mean_host[8 * l + o];
-  static bool attr = false;
-  if (!attr) {
+  static DeviceCache attr_cache;
+  int attr_ok = 0;
+  HPM_TRY(device_cached(attr_cache, [](int *v) -> hpm_status {
     HPM_CUDA(cudaFuncSetAttribute(tc::k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem));
     // The drain warps raise their register count to kRegsHigh with registers
     // the other warpgroups give back; that only adds up if the kernel was
     // compiled with kLaunchRegs per thread. Never launch it otherwise.
     cudaFuncAttributes fa{};
     HPM_CUDA(cudaFuncGetAttributes(&fa, tc::k_m2l_tc));
-    if (fa.numRegs != tc::kLaunchRegs) {
+    if (fa.numRegs != tc::kLaunchRegs)
       fprintf(stderr, "hpm: k_m2l_tc compiled with %d registers per thread, expected %d\n", fa.numRegs,
               tc::kLaunchRegs);
-      return HPM_ERR_UNSUPPORTED;
-    }
-    attr = true;
-  }
+    *v = fa.numRegs == tc::kLaunchRegs ? 1 : 0;
+    return HPM_OK;
+  }, &attr_ok));
+  if (!attr_ok) return HPM_ERR_UNSUPPORTED;
   const int64_t grid = pl->tc_ntiles * tc::kQuarters;
   if (pl->events_ready) cudaEventRecord(pl->ev[10], st);
   tc::k_m2l_tc<<<(unsigned)grid, tc::kThreads, tc::kSmem, st>>>(p);

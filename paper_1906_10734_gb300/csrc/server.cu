@@ -58,13 +58,40 @@ struct hpm_server_s {
   int64_t inflight_bytes = 0;
   int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, cancelled = 0, failed = 0;
   int64_t particles_done = 0;
+  // latencies of the last kLatencyWindow completions (a ring), and the sum
+  // and count of all completions since the last reset
   std::vector<double> latencies_ms;
+  size_t lat_next = 0;
+  double lat_sum = 0.0;
+  int64_t lat_count = 0;
+  int waiters = 0;                  // threads inside hpm_server_wait
+  std::condition_variable cv_idle;  // signalled when waiters drops to zero while stopping
   hpm::Clock::time_point t_first, t_last;
   bool any_done = false;
 };
 
 namespace hpm {
 namespace {
+
+// p50 / p99 are taken over this many most recent completions
+constexpr size_t kLatencyWindow = 65536;
+
+void record_latency(hpm_server_s *sv, double ms) {
+  if (sv->latencies_ms.size() < kLatencyWindow) {
+    sv->latencies_ms.push_back(ms);
+  } else {
+    sv->latencies_ms[sv->lat_next] = ms;
+    sv->lat_next = (sv->lat_next + 1) % kLatencyWindow;
+  }
+  sv->lat_sum += ms;
+  ++sv->lat_count;
+}
+
+// A request whose final state has been reported to the caller is forgotten.
+void release_request(hpm_server_s *sv, Request *r) {
+  sv->reqs.erase(r->id);
+  delete r;
+}
 
 // Device bytes a request needs while its batch runs: packed inputs and
 // outputs, keys and permutation (double buffered), sorted copies, and the
@@ -146,7 +173,7 @@ void worker_loop(hpm_server_s *sv, Worker *w) {
         if (s == HPM_OK) {
           ++sv->completed;
           sv->particles_done += r->req.n;
-          sv->latencies_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
+          record_latency(sv, std::chrono::duration<double, std::milli>(now - r->t_submit).count());
           if (!sv->any_done) sv->t_first = r->t_submit;
           sv->any_done = true;
           sv->t_last = now;
@@ -242,7 +269,9 @@ hpm_status hpm_server_poll(hpm_server_t sv, uint64_t ticket, int *done, double *
   *done = r->state == 2 ? 1 : (r->state < 0 ? -1 : 0);
   if (latency_ms)
     *latency_ms = r->state == 2 ? std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count() : 0.0;
-  return r->state == -2 ? r->status : HPM_OK;
+  const hpm_status s = r->state == -2 ? r->status : HPM_OK;
+  if (*done != 0) release_request(sv, r);  // final state reported: the ticket ends here
+  return s;
 }
 
 hpm_status hpm_server_wait(hpm_server_t sv, uint64_t ticket, int timeout_ms, double *latency_ms) {
@@ -251,13 +280,17 @@ hpm_status hpm_server_wait(hpm_server_t sv, uint64_t ticket, int timeout_ms, dou
   auto it = sv->reqs.find(ticket);
   if (it == sv->reqs.end()) return HPM_ERR_INVALID_ARG;
   Request *r = it->second;
+  ++sv->waiters;
   const bool ok = sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
-                                       [r] { return r->state == 2 || r->state < 0; });
+                                       [sv, r] { return sv->stop || r->state == 2 || r->state < 0; });
+  if (--sv->waiters == 0 && sv->stop) sv->cv_idle.notify_all();
+  if (sv->stop) return HPM_ERR_BUSY;  // the server is being destroyed
   if (!ok) return HPM_ERR_TIMEOUT;
   if (latency_ms)
     *latency_ms = r->state == 2 ? std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count() : 0.0;
-  if (r->state == -1) return HPM_ERR_INVALID_ARG;
-  return r->state == 2 ? HPM_OK : r->status;
+  const hpm_status s = r->state == -1 ? HPM_ERR_INVALID_ARG : (r->state == 2 ? HPM_OK : r->status);
+  release_request(sv, r);  // final state reported: the ticket ends here
+  return s;
 }
 
 hpm_status hpm_server_cancel(hpm_server_t sv, uint64_t ticket) {
@@ -269,6 +302,9 @@ hpm_status hpm_server_cancel(hpm_server_t sv, uint64_t ticket) {
     Request *r = it->second;
     if (r->state != 0) return HPM_ERR_BUSY;  // already running or finished
     r->state = -1;
+    // out of the queue now, so that the request can be freed once its state
+    // has been reported
+    sv->queue.erase(std::remove(sv->queue.begin(), sv->queue.end(), r), sv->queue.end());
     ++sv->cancelled;
   }
   sv->cv_done.notify_all();
@@ -294,9 +330,7 @@ hpm_status hpm_server_get_stats(hpm_server_t sv, hpm_server_stats *st) {
   st->particles = sv->particles_done;
   st->p50_ms = percentile(sv->latencies_ms, 0.50);
   st->p99_ms = percentile(sv->latencies_ms, 0.99);
-  double mean = 0.0;
-  for (double v : sv->latencies_ms) mean += v;
-  st->mean_ms = sv->latencies_ms.empty() ? 0.0 : mean / (double)sv->latencies_ms.size();
+  st->mean_ms = sv->lat_count ? sv->lat_sum / (double)sv->lat_count : 0.0;
   if (sv->any_done) {
     const double span = std::chrono::duration<double>(sv->t_last - sv->t_first).count();
     st->particles_per_s = span > 0 ? (double)sv->particles_done / span : 0.0;
@@ -308,6 +342,9 @@ hpm_status hpm_server_reset_stats(hpm_server_t sv) {
   if (!sv) return HPM_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(sv->mu);
   sv->latencies_ms.clear();
+  sv->lat_next = 0;
+  sv->lat_sum = 0.0;
+  sv->lat_count = 0;
   sv->particles_done = 0;
   sv->completed = sv->submitted = sv->batches = sv->rejected = sv->cancelled = sv->failed = 0;
   sv->any_done = false;
@@ -317,8 +354,12 @@ hpm_status hpm_server_reset_stats(hpm_server_t sv) {
 hpm_status hpm_server_destroy(hpm_server_t sv) {
   if (!sv) return HPM_OK;
   {
-    std::lock_guard<std::mutex> lk(sv->mu);
+    // wake the threads blocked in hpm_server_wait (they return HPM_ERR_BUSY)
+    // and wait until none is left inside before anything is freed
+    std::unique_lock<std::mutex> lk(sv->mu);
     sv->stop = true;
+    sv->cv_done.notify_all();
+    sv->cv_idle.wait(lk, [sv] { return sv->waiters == 0; });
   }
   sv->cv_work.notify_all();
   for (Worker *w : sv->workers)

@@ -946,8 +946,8 @@ hpm_status precompute_green(hpm_plan_s *pl, cudaStream_t st) {
   HPM_TRY(pl->gmean.ensure(sizeof(float) * (D + 1), st));
   HPM_CUDA(cudaMemsetAsync(pl->gmean.p, 0, sizeof(float) * (D + 1), st));
   double *a = nullptr, *b = nullptr;
-  HPM_CUDA(cudaMallocAsync((void **)&a, sizeof(double) * h3, st));
-  HPM_CUDA(cudaMallocAsync((void **)&b, sizeof(double) * h3, st));
+  HPM_TRY(lib_malloc_async((void **)&a, sizeof(double) * h3, st));
+  HPM_TRY(lib_malloc_async((void **)&b, sizeof(double) * h3, st));
   const double scale = -1.0 / ((double)P * P * P);
   if (pl->ng == 4) {
     pl->kz_green_stride = (int64_t)H * H * (4 * pl->ng);
@@ -1026,6 +1026,7 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
   pl->stats.m2l_targets = pl->ntgt;
   pl->stats.m2l_parents = 0;
   pl->stats.ms_m2l_kernel = 0.f;
+  pl->stats.p2p_pairs = pl->npairs;
   if (n == 0) return HPM_OK;
   const int ng = pl->ng, m3 = ng * ng * ng;
   const int D = pl->max_depth;
@@ -1108,11 +1109,13 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
     const float eps2 = (float)(eu * eu);
     const float s1 = (float)(1.0 / pl->dom.side), s2 = (float)(1.0 / (pl->dom.side * pl->dom.side));
     HPM_TRY(s.part.ensure(sizeof(float4) * (pl->npart > 0 ? pl->npart : 1), st));
-    static int p2p_resident = 0;
-    if (!p2p_resident) {
-      HPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2p_resident, k_p2p, kThreads, 0));
-      if (p2p_resident < 1) p2p_resident = 1;
-    }
+    static DeviceCache p2p_cache;
+    int p2p_resident = 1;
+    HPM_TRY(device_cached(p2p_cache, [](int *v) -> hpm_status {
+      HPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(v, k_p2p, kThreads, 0));
+      if (*v < 1) *v = 1;
+      return HPM_OK;
+    }, &p2p_resident));
     HPM_TRY(s.work.ensure(sizeof(unsigned long long), st));
     HPM_CUDA(cudaMemsetAsync(s.work.p, 0, sizeof(unsigned long long), st));
     const unsigned p2p_grid = (unsigned)std::min<int64_t>(warp_blocks(pl->nitem), (int64_t)p2p_resident * sm_count());

@@ -136,6 +136,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortRounds = 16;
 constexpr int kSortTile = kSortThreads * kSortRounds;
 constexpr int kRadix = 256;
+static_assert(kSortTile == kSortTileElems && kRadix == kRadixDigits, "sort sizing shared with the static sort");
 
 __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t n, int shift,
                              int *__restrict__ hist, int nblk) {
@@ -268,7 +269,8 @@ hpm_status exclusive_scan_i32(const int *in, int *out, int64_t n, int *d_total, 
   return HPM_OK;
 }
 
-int64_t scan_tiles(int64_t n) { return (n + kLbTile - 1) / kLbTile; }
+static_assert(kLbTile == kScanTileElems, "scan sizing shared with the static sort");
+int64_t scan_tiles(int64_t n) { return scan_tiles_of(n); }
 
 // Control words of the scan in a buffer of its own, zeroed when it grows.
 hpm_status ensure_scan_ctl(DevBuf &buf, int64_t tiles, int *err, cudaStream_t st, ScanCtl *out) {
@@ -297,11 +299,13 @@ hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&val
   HPM_TRY(scratch.ensure(sizeof(int) * 2 * hn, st));
   int *hist = scratch.as<int>();
   int *offs = hist + hn;
-  static bool attr = false;
-  if (!attr) {
+  static DeviceCache attr_cache;
+  int done = 0;
+  HPM_TRY(device_cached(attr_cache, [](int *v) -> hpm_status {
     HPM_CUDA(cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, kScatterSmem));
-    attr = true;
-  }
+    *v = 1;
+    return HPM_OK;
+  }, &done));
   bool first = true;
   for (int shift = 0; shift < bits || first; shift += 8) {
     k_radix_hist<<<nblk, kSortThreads, 0, st>>>(keys, n, shift, hist, nblk);

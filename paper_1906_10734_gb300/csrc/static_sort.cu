@@ -8,22 +8,24 @@ namespace hpm {
 namespace {
 
 constexpr int64_t kMaxN = HPM_STATIC_SORT_MAX_N;
-constexpr int64_t kTile = 4096;                              // particles per sort block
-constexpr int64_t kMaxBlocks = (kMaxN + kTile - 1) / kTile;
-constexpr int64_t kHist = 256 * kMaxBlocks;                  // digit x block counters
-constexpr int64_t kScanStatus = (kHist + 2047) / 2048 + 64;    // tiles of the histogram scan
+// the sort's histogram and offsets (2 x digits x sort tiles ints) and the
+// status words of the scan over the histogram, sized from the sort's own
+// constants so that radix_sort_pairs never finds its scratch too small
+constexpr int64_t kHistInts = sort_scratch_ints(kMaxN);
+constexpr int64_t kScanStatus = scan_tiles_of(kHistInts / 2) + 64;
 constexpr size_t kHeader = 256;                              // error word
 constexpr size_t kKeysOff = kHeader;
 constexpr size_t kPermOff = kKeysOff + sizeof(uint64_t) * kMaxN;
 constexpr size_t kHistOff = kPermOff + sizeof(uint32_t) * kMaxN;
-constexpr size_t kHistBytes = sizeof(int) * 2 * kHist;
+constexpr size_t kHistBytes = sizeof(int) * kHistInts;
+static_assert(kHistBytes >= sizeof(int) * sort_scratch_ints(kMaxN), "histogram scratch");
+static_assert(kScanStatus >= scan_tiles_of(kHistInts / 2), "scan status words");
 constexpr size_t kScanOff = (kHistOff + kHistBytes + 255) / 256 * 256;  // ticket, then status words
 constexpr size_t kBytes = kScanOff + 256 + sizeof(unsigned long long) * kScanStatus;
 
 // Held by every device that loads the library, for the life of the process.
 static __device__ __align__(256) unsigned char g_sort_scratch[kBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
 

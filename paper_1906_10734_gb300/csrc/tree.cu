@@ -575,16 +575,25 @@ __global__ void k_box_tgt(int64_t ntgt, const int *__restrict__ tgt_box, int *__
 // items of at most kP2PPairsPerItem pairs and at least kP2PMinSources sources.
 __global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, const int *__restrict__ nb,
                             const int *__restrict__ beg, const int *__restrict__ end, int *__restrict__ nitem,
-                            int *__restrict__ npart) {
+                            int *__restrict__ npart, unsigned long long *__restrict__ npairs) {
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= nleaf) return;
-  const int box = leaf_box[l];
-  int64_t ns = 0;
-  for (int k = 0; k < 27; ++k) {
-    const int q = nb[(int64_t)box * 27 + k];
-    if (q >= 0) ns += end[q] - beg[q];
+  // near-zone pairs (i, j), j != i, of all leaves: the near field's work count
+  unsigned long long pairs = 0;
+  int box = -1;
+  int64_t ns = 0, nt = 0;
+  if (l < nleaf) {
+    box = leaf_box[l];
+    for (int k = 0; k < 27; ++k) {
+      const int q = nb[(int64_t)box * 27 + k];
+      if (q >= 0) ns += end[q] - beg[q];
+    }
+    nt = end[box] - beg[box];
+    pairs = (unsigned long long)(nt * ns - nt);
   }
-  const int64_t nt = end[box] - beg[box];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+  if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(npairs, pairs);
+  if (l >= nleaf) return;
   int64_t items = (nt * ns + kP2PPairsPerItem - 1) / kP2PPairsPerItem;
   const int64_t cap = (ns + kP2PMinSources - 1) / kP2PMinSources;
   if (items > cap) items = cap;
@@ -775,11 +784,12 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   int hc[64];
   // Levels 1..D in one cooperative launch (all blocks resident, grid-wide
   // barriers between the phases of a level); one read-back at the end.
-  static int level_max_per_sm = 0;  // resident CTAs per SM the kernel allows
-  if (!level_max_per_sm) {
-    HPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&level_max_per_sm, k_levels, kThreads, 0));
-    if (level_max_per_sm <= 0) return HPM_ERR_CUDA;
-  }
+  static DeviceCache level_cache;  // resident CTAs per SM the kernel allows
+  int level_max_per_sm = 0;
+  HPM_TRY(device_cached(level_cache, [](int *v) -> hpm_status {
+    HPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(v, k_levels, kThreads, 0));
+    return *v > 0 ? HPM_OK : HPM_ERR_CUDA;
+  }, &level_max_per_sm));
   // CTAs per SM: the plan's tuned value (2 by default), never above what fits
   const int level_per_sm = std::min(level_max_per_sm, pl->tuning.level_blocks_per_sm > 0 ? pl->tuning.level_blocks_per_sm : 2);
   const int level_grid = level_per_sm * sm_count();
@@ -814,12 +824,17 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
       la.err = t.err.as<int>();
       la.gb = reinterpret_cast<GridBar *>(t.counters.as<int>() + 96);
       void *args[] = {&la};
-      // One level kernel on the device at a time, whatever the stream: two
+      // One level kernel on a device at a time, whatever the stream: two
       // cooperative grids that each hold part of the GPU could wait on each
-      // other's blocks. Each launch waits for the previous one to finish.
+      // other's blocks. Each launch waits for the previous one on the same
+      // device to finish (one event per device).
       static std::mutex mu;
-      static cudaEvent_t last = nullptr;
+      static cudaEvent_t last_ev[kMaxDevices] = {};
+      int dev = 0;
+      HPM_CUDA(cudaGetDevice(&dev));
+      if (dev < 0 || dev >= kMaxDevices) return HPM_ERR_UNSUPPORTED;
       std::lock_guard<std::mutex> lock(mu);
+      cudaEvent_t &last = last_ev[dev];
       if (!last) HPM_CUDA(cudaEventCreateWithFlags(&last, cudaEventDisableTiming));
       HPM_CUDA(cudaStreamWaitEvent(st, last, 0));
       HPM_CUDA(cudaLaunchCooperativeKernel((const void *)k_levels, dim3(level_grid), dim3(kThreads), args, 0, st));
@@ -904,16 +919,18 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     HPM_TRY(t.leaf_item0.ensure(sizeof(int) * (nl + 1), st));
     HPM_TRY(t.leaf_part0.ensure(sizeof(int) * (nl + 1), st));
     HPM_TRY(t.cnt.ensure(sizeof(int) * (nl + 1), st));
+    // counters[76..77]: the near-zone pair count (64 bits), zeroed with the others
     k_leaf_work<<<blocks_for(nl), kThreads, 0, st>>>(nl, t.leaf_box.as<int>(), t.box_nb.as<int>(),
                                                      t.box_beg.as<int>(), t.box_end.as<int>(),
-                                                     t.leaf_nitem.as<int>(), t.cnt.as<int>());
+                                                     t.leaf_nitem.as<int>(), t.cnt.as<int>(),
+                                                     reinterpret_cast<unsigned long long *>(t.counters.as<int>() + 76));
     HPM_LAUNCHED(&launches);
     HPM_TRY(exclusive_scan_i32(t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(), nl, t.counters.as<int>() + 64,
                                t.scan, st, &launches));
     HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.leaf_part0.as<int>(), nl, t.counters.as<int>() + 65,
                                t.scan, st, &launches));
-    int hv[10] = {0}, herr2[2] = {0, 0};
-    HPM_CUDA(cudaMemcpyAsync(hv, t.counters.as<int>() + 64, sizeof(int) * 10, cudaMemcpyDeviceToHost, st));
+    int hv[14] = {0}, herr2[2] = {0, 0};
+    HPM_CUDA(cudaMemcpyAsync(hv, t.counters.as<int>() + 64, sizeof(int) * 14, cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaMemcpyAsync(herr2, t.err.as<int>(), sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaStreamSynchronize(st));
     if (herr2[1] & kErrTimeout) {
@@ -924,6 +941,11 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     if (herr2[0] & kErrTimeout) return HPM_ERR_TIMEOUT;
     pl->nitem = hv[0];
     pl->npart = hv[1];
+    {
+      unsigned long long pairs = 0;
+      memcpy(&pairs, hv + 12, sizeof(pairs));
+      pl->npairs = (int64_t)pairs;
+    }
     pl->np2g = hv[8];
     // the work-list sizes the host derived must be what the device selected
     if (hv[6] != pl->ntgt || hv[7] != pl->nleaf || hv[9] != pl->npar) {

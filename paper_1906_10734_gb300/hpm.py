@@ -73,12 +73,17 @@ class hpm_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_float) for k in ("ms_tree", "ms_p2g", "ms_m2m", "ms_m2l", "ms_l2l", "ms_g2p",
                                               "ms_p2p", "ms_total")] + \
                [("launches", ctypes.c_int64), ("m2l_launches", ctypes.c_int64), ("m2l_targets", ctypes.c_int64),
-                ("ms_m2l_kernel", ctypes.c_float), ("m2l_parents", ctypes.c_int64)]
+                ("ms_m2l_kernel", ctypes.c_float), ("m2l_parents", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64)]
 
 
 class hpm_tuning(ctypes.Structure):
     _fields_ = [("level_blocks_per_sm", ctypes.c_int), ("gridlet_warps", ctypes.c_int),
                 ("m2l_ctas_per_sm", ctypes.c_int)]
+
+
+class hpm_alu_peaks(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("fp32_tflops", "fp64_tflops", "rsqrt_gops", "ms_fp32", "ms_fp64",
+                                               "ms_rsqrt")] + [("sm_count", ctypes.c_int)]
 
 
 SIGNATURES = {
@@ -107,6 +112,7 @@ SIGNATURES = {
     "hpm_get_tuning": ([_vp, ctypes.POINTER(hpm_tuning)], _i32),
     "hpm_tune": ([_vp, _vp, _vp, _i64, _vp, ctypes.POINTER(hpm_tuning)], _i32),
     "hpm_test_stall": ([_vp, _i32, ctypes.c_longlong], _i32),
+    "hpm_measure_alu_peaks": ([ctypes.POINTER(hpm_alu_peaks), _vp], _i32),
     "hpm_destroy": ([_vp], _i32),
     "hpm_status_str": ([_i32], ctypes.c_char_p),
     "hpm_last_cuda_error": ([], ctypes.c_char_p),
@@ -412,3 +418,10 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def hpm_measure_alu_peaks(stream=None) -> dict:
+    """Measured FP32 / FP64 FMA and rsqrt rates of the current device (see include/hpm.h)."""
+    out = hpm_alu_peaks()
+    _check("hpm_measure_alu_peaks", load().hpm_measure_alu_peaks(ctypes.byref(out), _stream(stream)))
+    return {k: getattr(out, k) for k, _ in hpm_alu_peaks._fields_}

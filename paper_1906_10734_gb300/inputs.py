@@ -75,6 +75,23 @@ def equal_masses(n: int, total: float = 1.0) -> np.ndarray:
     return np.full(n, total / max(n, 1), dtype=np.float64)
 
 
+def log_uniform_masses(n: int, seed: int, decades: float = 6.0, total: float = 1.0) -> np.ndarray:
+    """Masses log-uniform over ``decades`` decades (10^(decades u), u uniform in [0, 1)),
+    scaled to sum to ``total``: boxes of one level then differ in mass by up to that span."""
+    m = 10.0 ** (decades * uniform01(seed, 0, n))
+    return m * (total / m.sum()) if n else m
+
+
+def heavy_body_masses(n: int, seed: int, ratio: float = 1e4, total_light: float = 1.0):
+    """Equal masses total_light / n, except one particle (index drawn from stream
+    ``seed``) of mass ``ratio`` times the total of all the others. Returns (masses, index)."""
+    m = equal_masses(n, total_light)
+    k = int(uniform01(seed, 0, 1)[0] * n) if n else 0
+    if n:
+        m[k] = ratio * (m.sum() - m[k])
+    return m, k
+
+
 @dataclass
 class Workload:
     """One gravity problem: particles, masses, tree and gridlet parameters."""

@@ -1,9 +1,12 @@
 """Host-side arithmetic of bench.py, without a GPU.
 
-The roofline object must be the executed tensor work of the dense kernel over
-its own duration against the measured peak; the DRAM traffic must come from a
-committed ncu summary only while the kernel source still has the sha256 the
-summary names; the clock sampler must report throttle reasons it sees.
+The roofline object must be the algorithmic work of the source-to-target step
+(the nominal FFT-convolution count per target times the targets) over the
+dense kernel's own duration against the measured peak, with the executed
+tensor work beside it; the DRAM traffic must come from a committed ncu summary
+only while the kernel source still has the sha256 the summary names; the FP32
+peak must be the measured one; the clock sampler must report throttle reasons
+it sees.
 """
 import os
 import tempfile
@@ -13,24 +16,36 @@ import pytest
 import bench
 
 
-def test_dense_roofline_is_executed_work_over_kernel_time():
+def test_dense_roofline_is_nominal_work_over_kernel_time():
     steps = [{"ms_m2l": 1.2, "ms_m2l_kernel": 1.0, "m2l_parents": 30000},
              {"ms_m2l": 1.2, "ms_m2l_kernel": 1.0, "m2l_parents": 30000}]
     r = bench.roofline_of(steps, 4, 240000, None)
-    flop = 3 * 2 * 512 * 13824 * 30000
+    nominal = bench.m2l_flops_per_target(4) * 240000
     assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
-    assert r["achieved"] == pytest.approx(flop / 1.0e-3 / 1e12)
+    assert r["achieved"] == pytest.approx(nominal / 1.0e-3 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["traffic"] is None
-    # the nominal FFT rate of the whole stage rides along
-    assert r["stage_nominal_fft_tflops"] == pytest.approx(bench.m2l_flops_per_target(4) * 240000 / 1.2e-3 / 1e12)
+    # the executed dense work and the whole stage ride along under their own keys
+    flop = 3 * 2 * 512 * 13824 * 30000
+    assert r["executed"]["achieved"] == pytest.approx(flop / 1.0e-3 / 1e12)
+    assert r["stage"]["achieved"] == pytest.approx(nominal / 1.2e-3 / 1e12)
 
 
-def test_fft_roofline_against_fp32_peak():
+def test_fft_roofline_against_measured_fp32_peak():
     steps = [{"ms_m2l": 8.0, "ms_m2l_kernel": 0.0, "m2l_parents": 0}]
-    r = bench.roofline_of(steps, 4, 100000, None)
+    r = bench.roofline_of(steps, 4, 100000, None, {"fp32_tflops": 70.0})
     assert r["bound"] == "alu"
     assert r["achieved"] == pytest.approx(bench.m2l_flops_per_target(4) * 100000 / 8.0e-3 / 1e12)
+    committed = bench.alu_peaks().get("fp32_tflops")
+    assert r["peak"] == pytest.approx(committed if committed else 70.0)
+    assert "measured" in r["peak_basis"]
+
+
+def test_p2p_roofline_counts_pairs():
+    steps = [{"ms_p2p": 1.0, "p2p_pairs": 10 ** 9}]
+    r = bench.p2p_roofline(steps, {"fp32_tflops": 80.0, "rsqrt_gops": 5000.0})
+    assert r["achieved"] == pytest.approx(20 * 1e9 / 1e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
 
 
 def test_nominal_fft_count_at_order_4():

@@ -51,6 +51,39 @@ def test_admission_cancel_and_bounded_wait_without_workers(hpm):
     sv.close()
 
 
+def test_tickets_end_with_their_final_state_and_destroy_wakes_waiters(hpm):
+    import threading
+    sv = hpm.Server(workers=0, max_batch=4, hbm_budget_bytes=64 << 20)
+    t1 = sv.submit(*host_request(500, 3))
+    t2 = sv.submit(*host_request(500, 4))
+    sv.cancel(t1)
+    # the cancelled request left the queue at once; its final state is reported
+    # once, after which the server has forgotten the ticket
+    assert sv.stats()["queued"] == 1
+    assert sv.poll(t1)[0] == -1
+    with pytest.raises(hpm.HpmError) as e:
+        sv.poll(t1)
+    assert e.value.status == -1
+    # a thread blocked on a request nothing will run is woken by destroy and
+    # told the server is going away (HPM_ERR_BUSY) before anything is freed
+    got = {}
+
+    def waiter():
+        try:
+            sv.wait(t2, timeout_ms=60000)
+            got["status"] = 0
+        except hpm.HpmError as err:
+            got["status"] = err.status
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    time.sleep(0.2)
+    t0 = time.perf_counter()
+    sv.close()
+    th.join(timeout=10)
+    assert not th.is_alive() and got["status"] == -7 and time.perf_counter() - t0 < 5.0
+
+
 @pytest.mark.gpu
 def test_results_in_a_mix_equal_each_request_alone(hpm):
     torch = pytest.importorskip("torch")
