@@ -12,8 +12,9 @@
  * over its interaction zone (Sec. 2.1), parent-to-child transformation and
  * evaluation (Sec. 2.4); the near zone is summed directly (Sec. 1, item 1).
  *
- * Kernel: g(r) = 1/sqrt(r^2 + eps^2) with G = 1 (eps = 0: Newtonian 1/r; the
- * 1/(4 pi) of Eq. gf is not used). Outputs:
+ * Kernel: a radial Green function g(r) (hpm_green below; the default is
+ * g(r) = 1/sqrt(r^2 + eps^2)) with G = 1 (the 1/(4 pi) of Eq. gf is not
+ * used). Outputs:
  *   phi_i = -sum_{j != i} m_j g(|x_i - x_j|)   (self term excluded)
  *   a_i   = -grad phi_i
  * approximated by the method (exact for pairs in the near zone).
@@ -64,13 +65,33 @@ typedef struct {
   double side;
 } hpm_domain;
 
-/* Green function. The paper's method only convolves with it (Sec. 4: "any
- * Green function ... would work equally well"); this build provides the
- * Plummer-softened Newtonian kernel. */
-enum { HPM_GREEN_PLUMMER = 0 };
+/* Green function g(r), radial (Sec. 4: the method only convolves with the
+ * Green function, so any kernel serves; Sec. 2.1 tabulates it exactly on the
+ * gridlet lattice). phi_i = -sum_{j != i} m_j g(r_ij), a_i = -grad phi_i.
+ *   HPM_GREEN_PLUMMER  g = 1 / sqrt(r^2 + eps^2)                 (eps >= 0)
+ *   HPM_GREEN_NEWTON   g = 1 / r                                  (eps ignored)
+ *   HPM_GREEN_YUKAWA   g = exp(-s / lambda) / s, s = sqrt(r^2 + eps^2)
+ *                      (eps >= 0, lambda > 0)
+ *   HPM_GREEN_USER     g = user_g(r, ctx), any radial kernel: called on the
+ *                      calling thread during hpm_plan (and hpm_server_create)
+ *                      only, never kept; it must return finite values for
+ *                      r >= side * 2^-32. The library evaluates it in FP64 on
+ *                      the lattice of every level (the far-field tables) and
+ *                      tabulates g and -g'(r)/r (g' by fourth-order central
+ *                      differences at step r/512) for the near field as
+ *                      piecewise cubics, 32 per octave of (r/side)^2 over
+ *                      [2^-64, 4) side^2 (relative interpolation error about
+ *                      1e-7); pairs closer than side * 2^-32 take the values
+ *                      at that distance. The value at r = 0 is never used.
+ * Values that are not finite at the points the plan needs make hpm_plan
+ * return HPM_ERR_INVALID_ARG. */
+enum { HPM_GREEN_PLUMMER = 0, HPM_GREEN_NEWTON = 1, HPM_GREEN_YUKAWA = 2, HPM_GREEN_USER = 3 };
 typedef struct {
-  int kind;    /* HPM_GREEN_PLUMMER                                    */
-  double eps;  /* softening length, >= 0 (0 = Newtonian)               */
+  int kind;                                 /* HPM_GREEN_*                          */
+  double eps;                               /* softening length (Plummer, Yukawa)   */
+  double lambda;                            /* screening length (Yukawa)            */
+  double (*user_g)(double r, void *ctx);    /* HPM_GREEN_USER                       */
+  void *ctx;                                /* passed to user_g                     */
 } hpm_green;
 
 /* Tree options (Sec. 1: the tree "may or may not be of uniform depth").

@@ -29,6 +29,12 @@ enum : uint8_t {
 // Device error word bits.
 enum : int { kErrDomain = 1, kErrCapacity = 2, kErrTimeout = 4 };
 
+// Near-field table of a user kernel: 32 cubic segments per octave of r_u^2
+// (r_u = distance / domain side) over [2^-64, 2^2); see green.cu.
+constexpr int kNearTabE0 = -64;
+constexpr int kNearTabOctaves = 66;
+constexpr int kNearTabSeg = 32;
+
 // Radix sort and single-pass scan sizing (sort.cu): elements per sort tile,
 // digits per pass, elements per scan tile. The no-allocation sort sizes its
 // static scratch from these.
@@ -154,6 +160,14 @@ struct hpm_plan_s {
   hpm_plan_opts opts;
   int device;
   hpm::GridletTables tab;
+  // the kernel on the gridlet lattice, FP64, per level l: G_l[n] = g(h_l sqrt(n)),
+  // n = 0 .. lattice_nmax(Ng) (G_l[0] = G_l[1]); glat_stride values per level
+  hpm::DevBuf glat;
+  int64_t glat_stride = 0;
+  std::vector<double> glat_host;
+  // user kernels: near-field table, per segment 4 cubic coefficients of g then
+  // 4 of F = -g'(r) / r_u (FP32)
+  hpm::DevBuf near_tab;
   // Green transforms, reduced (P/2+1)^3 FP32 tables per level, scaled -1/P^3
   hpm::DevBuf ghat;
   int64_t ghat_level_stride;  // floats per level
@@ -221,6 +235,11 @@ hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&val
                             cudaStream_t st, int64_t *launches);
 hpm_status exclusive_scan_i32(const int *in, int *out, int64_t n, int *d_total, const ScanCtl &ctl,
                               cudaStream_t st, int64_t *launches);
+// green.cu
+double green_g(const hpm_green &g, double r);
+int64_t lattice_nmax(int ng);
+hpm_status build_lattice(hpm_plan_s *pl, cudaStream_t st);
+hpm_status build_near_table(hpm_plan_s *pl, cudaStream_t st);
 // solve.cu
 // warps (gridlets) per CTA of the Ng = 4 child-to-parent and parent-to-child kernels
 inline int gridlet_warps(const hpm_plan_s *pl) {

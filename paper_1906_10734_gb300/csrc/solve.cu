@@ -815,12 +815,13 @@ __global__ void __launch_bounds__(kThreads) k_p2p_combine(int64_t nleaf, const i
 }
 
 // ---------------------------------------------------------------------------
-// Green function transform, FP64. g(d) = 1/sqrt(h^2 |d|_p^2 + eps^2) on the
-// P^3 periodic grid, g(0) := g(unit offset). g is real and even in every
-// axis, so its transform is the separable cosine sum
+// Green function transform, FP64. g(d) = g(h |d|_p) on the P^3 periodic grid,
+// read from the level's lattice table gl[|d|_p^2] (gl[0] = g(unit offset)).
+// g is real and even in every axis, so its transform is the separable cosine
+// sum
 //   G^(k) = sum_d g(d) cos(2 pi kx dx/P) cos(2 pi ky dy/P) cos(2 pi kz dz/P),
 // real and even; only k in [0, P/2]^3 is stored.
-__global__ void k_green_pass(int P, int pass, double h, double eps, const double *__restrict__ in,
+__global__ void k_green_pass(int P, int pass, const double *__restrict__ gl, const double *__restrict__ in,
                              double *__restrict__ out) {
   const int H = P / 2 + 1;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -833,9 +834,7 @@ __global__ void k_green_pass(int P, int pass, double h, double eps, const double
     const int dr = d <= P / 2 ? d : P - d;
     double v;
     if (pass == 0) {
-      double r2 = (double)dr * dr + (double)b * b + (double)c * c;
-      if (r2 == 0.0) r2 = 1.0;
-      v = 1.0 / sqrt(h * h * r2 + eps * eps);
+      v = gl[dr * dr + b * b + c * c];
     } else if (pass == 1) {
       v = in[a + (int64_t)H * (dr + (int64_t)H * c)];
     } else {
@@ -849,7 +848,7 @@ __global__ void k_green_pass(int P, int pass, double h, double eps, const double
 // Green function transformed along x only (used by the x-transform / direct
 // (y, z) convolution kernel): K[kx][a][b] = -(1/P) sum_{dx=0}^{P-1}
 // (G(|dx|_p, a, b) - mean) cos(2 pi kx dx / P), FP64, stored FP32.
-__global__ void k_green_kx(int P, int R, double h, double eps, const float *__restrict__ mean, int level,
+__global__ void k_green_kx(int P, int R, const double *__restrict__ gl, const float *__restrict__ mean, int level,
                            float *__restrict__ out) {
   const int H = P / 2 + 1;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -859,9 +858,7 @@ __global__ void k_green_kx(int P, int R, double h, double eps, const float *__re
   double s = 0.0;
   for (int d = 0; d < P; ++d) {
     const int dr = d <= P / 2 ? d : P - d;
-    double r2 = (double)dr * dr + (double)a * a + (double)b * b;
-    if (r2 == 0.0) r2 = 1.0;
-    s += (1.0 / sqrt(h * h * r2 + eps * eps) - m) * cospi(2.0 * (double)((kx * d) % P) / (double)P);
+    s += (gl[dr * dr + a * a + b * b] - m) * cospi(2.0 * (double)((kx * d) % P) / (double)P);
   }
   out[i] = (float)(-s / (double)P);
 }
@@ -937,6 +934,8 @@ __global__ void k_batch_scatter(const hpm_problem *__restrict__ desc, const int6
 }  // namespace
 
 hpm_status precompute_green(hpm_plan_s *pl, cudaStream_t st) {
+  HPM_TRY(build_lattice(pl, st));
+  HPM_TRY(build_near_table(pl, st));
   const int P = 8 * pl->ng, H = P / 2 + 1;
   const int64_t h3 = (int64_t)H * H * H;
   const int D = pl->max_depth;
@@ -955,12 +954,12 @@ hpm_status precompute_green(hpm_plan_s *pl, cudaStream_t st) {
     HPM_CUDA(cudaMemsetAsync(pl->kz_green.p, 0, sizeof(float) * pl->kz_green_stride * (D + 1), st));
   }
   for (int l = 2; l <= D; ++l) {
-    const double h = pl->dom.side / (double)(1u << l) / (double)pl->ng;
-    k_green_pass<<<blocks_for(h3), kThreads, 0, st>>>(P, 0, h, pl->green.eps, nullptr, a);
+    const double *gl = pl->glat.as<double>() + pl->glat_stride * l;
+    k_green_pass<<<blocks_for(h3), kThreads, 0, st>>>(P, 0, gl, nullptr, a);
     HPM_LAUNCHED((int64_t *)nullptr);
-    k_green_pass<<<blocks_for(h3), kThreads, 0, st>>>(P, 1, h, pl->green.eps, a, b);
+    k_green_pass<<<blocks_for(h3), kThreads, 0, st>>>(P, 1, gl, a, b);
     HPM_LAUNCHED((int64_t *)nullptr);
-    k_green_pass<<<blocks_for(h3), kThreads, 0, st>>>(P, 2, h, pl->green.eps, b, a);
+    k_green_pass<<<blocks_for(h3), kThreads, 0, st>>>(P, 2, gl, b, a);
     HPM_LAUNCHED((int64_t *)nullptr);
     k_green_store<<<blocks_for(h3), kThreads, 0, st>>>(h3, a, scale, pl->ghat.as<float>() + h3 * l,
                                                        pl->gmean.as<float>() + l, -scale);
@@ -980,9 +979,9 @@ hpm_status precompute_green(hpm_plan_s *pl, cudaStream_t st) {
     HPM_TRY(pl->kx_green.ensure(sizeof(float) * pl->kx_green_stride * (D + 1), st));
     HPM_CUDA(cudaMemsetAsync(pl->kx_green.p, 0, sizeof(float) * pl->kx_green_stride * (D + 1), st));
     for (int l = 2; l <= D; ++l) {
-      const double h = pl->dom.side / (double)(1u << l) / (double)pl->ng;
       k_green_kx<<<blocks_for(pl->kx_green_stride), kThreads, 0, st>>>(
-          P, R, h, pl->green.eps, pl->gmean.as<float>(), l, pl->kx_green.as<float>() + pl->kx_green_stride * l);
+          P, R, pl->glat.as<double>() + pl->glat_stride * l, pl->gmean.as<float>(), l,
+          pl->kx_green.as<float>() + pl->kx_green_stride * l);
       HPM_LAUNCHED((int64_t *)nullptr);
     }
   }
