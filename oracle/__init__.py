@@ -62,15 +62,16 @@ def lib():
             "or_moments": ([i32, i64, vp, vp, vp, vp, vp, vp], None),
             "or_p2g_paper": ([i32, i64, vp, vp, vp, vp], None),
             "or_t_paper": ([i32, vp, vp, i32, vp], None),
-            "or_m2l_direct": ([i32, f64, i64, vp, vp, vp, vp, vp, vp, vp], None),
+            "or_m2l_direct": ([i32, vp, i64, vp, vp, vp, vp, vp, vp, vp], None),
             "or_fft1d": ([vp, vp, i32, i32, vp, vp], None),
-            "or_green_hat": ([i32, f64, f64, vp, vp], None),
+            "or_green_hat": ([i32, vp, f64, vp, vp], None),
             "or_m2l_fft": ([i32, i64, vp, vp, vp, vp, vp, vp], None),
             "or_far_eval": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp], None),
             "or_g2p_paper": ([i32, i64, vp, vp, vp, vp, vp, vp, vp], None),
-            "or_p2p": ([f64, i64, vp, vp, vp, vp, vp, vp, vp, vp], None),
-            "or_direct": ([f64, i64, vp, i64, vp, vp, vp, vp], None),
-            "or_p2p_leaves": ([f64, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp], None),
+            "or_p2p": ([vp, i64, vp, vp, vp, vp, vp, vp, vp, vp], None),
+            "or_direct": ([vp, i64, vp, i64, vp, vp, vp, vp], None),
+            "or_p2p_leaves": ([vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp], None),
+            "or_kernel_eval": ([vp, i64, vp, vp, vp], None),
             "or_apply": ([i32, i64, vp, i32, vp, vp], None),
         }
         for name, (args, res) in sig.items():
@@ -117,6 +118,69 @@ def _i64(a):
 
 def num_threads() -> int:
     return int(_call("or_num_threads"))
+
+
+# ---------------------------------------------------------------------------
+# The Green function (Sec. 4: any radial kernel; Sec. 2.1, Eq. gf)
+# ---------------------------------------------------------------------------
+_KFN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_void_p)
+
+
+class _or_kernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("eps", ctypes.c_double), ("lam", ctypes.c_double),
+                ("rmin", ctypes.c_double), ("user_g", _KFN), ("user_dg", _KFN), ("ctx", ctypes.c_void_p)]
+
+
+class Kernel:
+    """Radial Green function g: Plummer 1/sqrt(r^2 + eps^2), Newton 1/r, Yukawa
+    exp(-s/lam)/s with s = sqrt(r^2 + eps^2), or a user C function g(r, ctx) with an
+    optional derivative dg(r, ctx). A user kernel is evaluated at r >= rmin (pairs
+    closer than rmin take its values there): the library's cut-off is side * 2^-32."""
+    PLUMMER, NEWTON, YUKAWA, USER = 0, 1, 2, 3
+
+    def __init__(self, kind=0, eps=0.0, lam=0.0, user_g=None, user_dg=None, ctx=None, rmin=0.0):
+        self.kind, self.eps, self.lam, self.rmin = kind, float(eps), float(lam), float(rmin)
+        self.user_g, self.user_dg, self.ctx = user_g, user_dg, ctx
+
+    @classmethod
+    def plummer(cls, eps):
+        return cls(cls.PLUMMER, eps)
+
+    @classmethod
+    def newton(cls):
+        return cls(cls.NEWTON)
+
+    @classmethod
+    def yukawa(cls, lam, eps=0.0):
+        return cls(cls.YUKAWA, eps, lam)
+
+    @classmethod
+    def user(cls, g, dg=None, ctx=None, side=1.0):
+        return cls(cls.USER, user_g=g, user_dg=dg, ctx=ctx, rmin=side * 2.0 ** -32)
+
+    def struct(self) -> _or_kernel:
+        k = _or_kernel(self.kind, self.eps, self.lam, self.rmin)
+        if self.user_g is not None:
+            k.user_g = ctypes.cast(self.user_g, _KFN)
+        if self.user_dg is not None:
+            k.user_dg = ctypes.cast(self.user_dg, _KFN)
+        if self.ctx is not None:
+            k.ctx = ctypes.cast(self.ctx, ctypes.c_void_p)
+        return k
+
+
+def _kern(eps_or_kernel):
+    """A float is the Plummer softening; a Kernel is passed through. Returns a pointer arg."""
+    k = eps_or_kernel if isinstance(eps_or_kernel, Kernel) else Kernel.plummer(float(eps_or_kernel))
+    return ctypes.pointer(k.struct())
+
+
+def kernel_eval(kernel, r):
+    """g(r) and F(r) = -g'(r)/r of the oracle's kernel at the distances r."""
+    r = _f64(np.atleast_1d(r))
+    g, f = np.zeros_like(r), np.zeros_like(r)
+    _call("or_kernel_eval", _kern(kernel), r.shape[0], _p(r), _p(g), _p(f))
+    return g, f
 
 
 # ---------------------------------------------------------------------------
@@ -209,18 +273,19 @@ def fft1d(x: np.ndarray, sign: int = -1) -> np.ndarray:
     return ore + 1j * oim
 
 
-def green_hat(ng: int, eps: float, h: float):
+def green_hat(ng: int, eps, h: float):
+    """Transform of the kernel (eps: Plummer softening or a Kernel) on the (8 Ng)^3 grid."""
     P = 8 * ng
     re = np.zeros(P ** 3)
     im = np.zeros(P ** 3)
-    _call("or_green_hat", P, float(eps), float(h), _p(re), _p(im))
+    _call("or_green_hat", P, _kern(eps), float(h), _p(re), _p(im))
     return re, im
 
 
 def m2l_direct(ng, eps, tcenter, tside, soff, sidx, scenter, sgrid) -> np.ndarray:
     tcenter, tside, soff, sidx = _f64(tcenter), _f64(tside), _i64(soff), _i64(sidx)
     out = np.zeros((tcenter.shape[0], ng ** 3))
-    _call("or_m2l_direct", ng, float(eps), tcenter.shape[0], _p(tcenter), _p(tside), _p(soff), _p(sidx),
+    _call("or_m2l_direct", ng, _kern(eps), tcenter.shape[0], _p(tcenter), _p(tside), _p(soff), _p(sidx),
                         _p(_f64(scenter)), _p(_f64(sgrid)), _p(out))
     return out
 
@@ -248,7 +313,7 @@ def p2p(eps, tidx, roff, rbeg, rend, spos, smass):
     tidx = _i64(tidx)
     phi = np.zeros(tidx.shape[0])
     acc = np.zeros((tidx.shape[0], 3))
-    _call("or_p2p", float(eps), tidx.shape[0], _p(tidx), _p(_i64(roff)), _p(_i64(rbeg)), _p(_i64(rend)),
+    _call("or_p2p", _kern(eps), tidx.shape[0], _p(tidx), _p(_i64(roff)), _p(_i64(rbeg)), _p(_i64(rend)),
                  _p(spos), _p(smass), _p(phi), _p(acc))
     return phi, acc
 
@@ -259,7 +324,7 @@ def p2p_leaves(eps, lbeg, lend, roff, rbeg, rend, spos, smass):
     phi = np.zeros(n)
     acc = np.zeros((n, 3))
     lbeg = _i64(lbeg)
-    _call("or_p2p_leaves", float(eps), lbeg.shape[0], _p(lbeg), _p(_i64(lend)), _p(_i64(roff)),
+    _call("or_p2p_leaves", _kern(eps), lbeg.shape[0], _p(lbeg), _p(_i64(lend)), _p(_i64(roff)),
                         _p(_i64(rbeg)), _p(_i64(rend)), _p(spos), _p(smass), _p(phi), _p(acc))
     return phi, acc
 
@@ -271,7 +336,7 @@ def direct_sum(pos, mass, eps, targets=None):
     t = _i64(np.arange(n) if targets is None else targets)
     phi = np.zeros(t.shape[0])
     acc = np.zeros((t.shape[0], 3))
-    _call("or_direct", float(eps), t.shape[0], _p(t), n, _p(pos), _p(mass), _p(phi), _p(acc))
+    _call("or_direct", _kern(eps), t.shape[0], _p(t), n, _p(pos), _p(mass), _p(phi), _p(acc))
     return phi, acc
 
 

@@ -23,7 +23,10 @@
  *     analytic gradient;
  *   - near-zone and all-pairs direct summation.
  *
- * Kernel: g(r) = 1/sqrt(r^2 + eps^2), potential phi_i = -sum_j m_j g(r_ij),
+ * Kernel: any radial Green function g (Sec. 4: the method only convolves
+ * with it), given as an or_kernel: Plummer 1/sqrt(r^2 + eps^2), Newton 1/r,
+ * Yukawa exp(-s/lambda)/s with s = sqrt(r^2 + eps^2), or a user function
+ * g(r, ctx) with an optional derivative. Potential phi_i = -sum_j m_j g(r_ij),
  * acceleration a = -grad phi (G = 1, the 1/(4 pi) of Eq. gf dropped).
  */
 #include <complex.h>
@@ -36,6 +39,69 @@
 #endif
 
 typedef double complex cplx;
+
+/* ---------------------------------------------------------------------------
+ * The Green function. kind: 0 Plummer, 1 Newton, 2 Yukawa, 3 user.
+ * A user kernel gives g(r, ctx) and, optionally, dg(r, ctx) = g'(r); without
+ * dg the derivative is the sixth-order central difference at step r/1000.
+ * User kernels are evaluated at r >= rmin (closer pairs take the values at
+ * rmin, the library's documented cut-off side * 2^-32).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int kind;
+  double eps, lambda, rmin;
+  double (*user_g)(double r, void *ctx);
+  double (*user_dg)(double r, void *ctx);
+  void *ctx;
+} or_kernel;
+
+static double or_g(const or_kernel *k, double r) {
+  switch (k->kind) {
+    case 1: return 1.0 / r;
+    case 2: {
+      const double s = sqrt(r * r + k->eps * k->eps);
+      return exp(-s / k->lambda) / s;
+    }
+    case 3: return k->user_g(r < k->rmin ? k->rmin : r, k->ctx);
+    default: return 1.0 / sqrt(r * r + k->eps * k->eps);
+  }
+}
+
+/* F(r) = -g'(r)/r: the pair term of the acceleration is a_i += m_j F (x_j - x_i). */
+static double or_force_factor(const or_kernel *k, double r) {
+  switch (k->kind) {
+    case 1: return 1.0 / (r * r * r);
+    case 2: {
+      const double s = sqrt(r * r + k->eps * k->eps);
+      return exp(-s / k->lambda) * (1.0 + s / k->lambda) / (s * s * s);
+    }
+    case 3: {
+      const double x = r < k->rmin ? k->rmin : r;
+      double d;
+      if (k->user_dg) {
+        d = k->user_dg(x, k->ctx);
+      } else {
+        const double h = x / 1000.0;
+        d = (-k->user_g(x - 3 * h, k->ctx) + 9 * k->user_g(x - 2 * h, k->ctx) - 45 * k->user_g(x - h, k->ctx) +
+             45 * k->user_g(x + h, k->ctx) - 9 * k->user_g(x + 2 * h, k->ctx) + k->user_g(x + 3 * h, k->ctx)) /
+            (60.0 * h);
+      }
+      return -d / x;
+    }
+    default: {
+      const double r2 = r * r + k->eps * k->eps;
+      return 1.0 / (r2 * sqrt(r2));
+    }
+  }
+}
+
+/* Exported for the pins: g(r) and F(r) at n distances. */
+void or_kernel_eval(const or_kernel *k, int64_t n, const double *r, double *g, double *f) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (g) g[i] = or_g(k, r[i]);
+    if (f) f[i] = or_force_factor(k, r[i]);
+  }
+}
 
 int or_num_threads(void) {
 #ifdef _OPENMP
@@ -232,7 +298,7 @@ void or_t_paper(int ng, const double *A, const double *B, int child, double *T) 
  * node positions y = c + L x_p. Sources of target t are rows
  * sidx[soff[t] .. soff[t+1]) of the source tables.
  * ------------------------------------------------------------------------- */
-void or_m2l_direct(int ng, double eps, int64_t ntgt, const double *tcenter, const double *tside,
+void or_m2l_direct(int ng, const or_kernel *kern, int64_t ntgt, const double *tcenter, const double *tside,
                    const int64_t *soff, const int64_t *sidx, const double *scenter,
                    const double *sgrid, double *out) {
   const int m3 = ng * ng * ng;
@@ -250,7 +316,7 @@ void or_m2l_direct(int ng, double eps, int64_t ntgt, const double *tcenter, cons
           double dx = yp[0] - (scenter[3 * b + 0] + L * node_x(q % ng, ng));
           double dy = yp[1] - (scenter[3 * b + 1] + L * node_x((q / ng) % ng, ng));
           double dz = yp[2] - (scenter[3 * b + 2] + L * node_x(q / (ng * ng), ng));
-          s += sgrid[b * m3 + q] / sqrt(dx * dx + dy * dy + dz * dz + eps * eps);
+          s += sgrid[b * m3 + q] * or_g(kern, sqrt(dx * dx + dy * dy + dz * dz));
         }
       }
       out[t * m3 + p] = -s;
@@ -318,10 +384,10 @@ void or_fft1d(const double *re_in, const double *im_in, int n, int sign, double 
 }
 
 /* Exact Green function on the P^3 periodic grid of spacing h, Eq. gf with
- * g(r) = 1/sqrt(r^2 + eps^2) in place of 1/(4 pi r): G[d] = g(h |d|_p),
+ * the kernel g in place of 1/(4 pi r): G[d] = g(h |d|_p),
  * |d|_p the periodic distance per axis; G at d = 0 takes the value at unit
  * offset (Sec. 2.1). Returns its forward transform (complex, P^3). */
-void or_green_hat(int P, double eps, double h, double *re, double *im) {
+void or_green_hat(int P, const or_kernel *kern, double h, double *re, double *im) {
   const int64_t n3 = (int64_t)P * P * P;
   cplx *a = (cplx *)malloc(sizeof(cplx) * n3);
   for (int k = 0; k < P; ++k)
@@ -330,7 +396,7 @@ void or_green_hat(int P, double eps, double h, double *re, double *im) {
         int di = i <= P / 2 ? i : P - i, dj = j <= P / 2 ? j : P - j, dk = k <= P / 2 ? k : P - k;
         double r2 = (double)di * di + (double)dj * dj + (double)dk * dk;
         if (r2 == 0.0) r2 = 1.0;
-        a[i + (int64_t)P * (j + (int64_t)P * k)] = 1.0 / sqrt(h * h * r2 + eps * eps);
+        a[i + (int64_t)P * (j + (int64_t)P * k)] = or_g(kern, h * sqrt(r2));
       }
   fft3d(a, P, -1);
   for (int64_t e = 0; e < n3; ++e) { re[e] = creal(a[e]); im[e] = cimag(a[e]); }
@@ -450,7 +516,7 @@ void or_g2p_paper(int ng, int64_t npart, const double *pos, const int64_t *cell,
  * particle index ranges [rbeg[e], rend[e]) for e in roff[i] .. roff[i+1],
  * skipping j == tidx[i].
  * ------------------------------------------------------------------------- */
-void or_p2p(double eps, int64_t ntp, const int64_t *tidx, const int64_t *roff,
+void or_p2p(const or_kernel *kern, int64_t ntp, const int64_t *tidx, const int64_t *roff,
             const int64_t *rbeg, const int64_t *rend, const double *pos, const double *mass,
             double *phi, double *acc) {
 #pragma omp parallel for schedule(dynamic, 64)
@@ -462,10 +528,9 @@ void or_p2p(double eps, int64_t ntp, const int64_t *tidx, const int64_t *roff,
         if (j == i) continue;
         double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1],
                dz = pos[3 * i + 2] - pos[3 * j + 2];
-        double r2 = dx * dx + dy * dy + dz * dz + eps * eps;
-        double ir = 1.0 / sqrt(r2), ir3 = ir * ir * ir;
-        f -= mass[j] * ir;
-        a[0] -= mass[j] * dx * ir3; a[1] -= mass[j] * dy * ir3; a[2] -= mass[j] * dz * ir3;
+        const double r = sqrt(dx * dx + dy * dy + dz * dz), F = or_force_factor(kern, r);
+        f -= mass[j] * or_g(kern, r);
+        a[0] -= mass[j] * dx * F; a[1] -= mass[j] * dy * F; a[2] -= mass[j] * dz * F;
       }
     phi[t] = f;
     for (int d = 0; d < 3; ++d) acc[3 * t + d] = a[d];
@@ -473,7 +538,7 @@ void or_p2p(double eps, int64_t ntp, const int64_t *tidx, const int64_t *roff,
 }
 
 /* All-pairs direct sum for the targets tidx[] against all n particles. */
-void or_direct(double eps, int64_t nt, const int64_t *tidx, int64_t n, const double *pos,
+void or_direct(const or_kernel *kern, int64_t nt, const int64_t *tidx, int64_t n, const double *pos,
                const double *mass, double *phi, double *acc) {
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t t = 0; t < nt; ++t) {
@@ -483,10 +548,9 @@ void or_direct(double eps, int64_t nt, const int64_t *tidx, int64_t n, const dou
       if (j == i) continue;
       double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1],
              dz = pos[3 * i + 2] - pos[3 * j + 2];
-      double r2 = dx * dx + dy * dy + dz * dz + eps * eps;
-      double ir = 1.0 / sqrt(r2), ir3 = ir * ir * ir;
-      f -= mass[j] * ir;
-      a[0] -= mass[j] * dx * ir3; a[1] -= mass[j] * dy * ir3; a[2] -= mass[j] * dz * ir3;
+      const double r = sqrt(dx * dx + dy * dy + dz * dz), F = or_force_factor(kern, r);
+      f -= mass[j] * or_g(kern, r);
+      a[0] -= mass[j] * dx * F; a[1] -= mass[j] * dy * F; a[2] -= mass[j] * dz * F;
     }
     phi[t] = f;
     for (int d = 0; d < 3; ++d) acc[3 * t + d] = a[d];
@@ -508,7 +572,7 @@ void or_apply(int m, int64_t nrow, const double *T, int transpose, const double 
 /* Near field of every particle of each leaf: leaf k holds particles
  * [lbeg[k], lend[k]) and its near zone is the ranges e in roff[k] .. roff[k+1].
  * Writes phi/acc at the particles' (sorted) indices. */
-void or_p2p_leaves(double eps, int64_t nleaf, const int64_t *lbeg, const int64_t *lend,
+void or_p2p_leaves(const or_kernel *kern, int64_t nleaf, const int64_t *lbeg, const int64_t *lend,
                    const int64_t *roff, const int64_t *rbeg, const int64_t *rend,
                    const double *pos, const double *mass, double *phi, double *acc) {
 #pragma omp parallel for schedule(dynamic, 16)
@@ -520,10 +584,9 @@ void or_p2p_leaves(double eps, int64_t nleaf, const int64_t *lbeg, const int64_t
           if (j == i) continue;
           double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1],
                  dz = pos[3 * i + 2] - pos[3 * j + 2];
-          double r2 = dx * dx + dy * dy + dz * dz + eps * eps;
-          double ir = 1.0 / sqrt(r2), ir3 = ir * ir * ir;
-          f -= mass[j] * ir;
-          a[0] -= mass[j] * dx * ir3; a[1] -= mass[j] * dy * ir3; a[2] -= mass[j] * dz * ir3;
+          const double r = sqrt(dx * dx + dy * dy + dz * dz), F = or_force_factor(kern, r);
+          f -= mass[j] * or_g(kern, r);
+          a[0] -= mass[j] * dx * F; a[1] -= mass[j] * dy * F; a[2] -= mass[j] * dz * F;
         }
       phi[i] += f;
       for (int d = 0; d < 3; ++d) acc[3 * i + d] += a[d];

@@ -106,7 +106,7 @@ static void make_tables(int ng, GridletTables &tb) {
 static void release_all(hpm_plan_s *pl, cudaStream_t s) {
   DevBuf *bufs[] = {&pl->ghat, &pl->t.keys, &pl->t.keys_alt, &pl->t.perm, &pl->t.perm_alt, &pl->t.spm, &pl->t.pbox,
                     &pl->t.box_key, &pl->t.box_beg, &pl->t.box_end, &pl->t.box_parent, &pl->t.box_flags,
-                    &pl->t.box_child, &pl->t.box_nb, &pl->t.cnt, &pl->t.off, &pl->t.bnd, &pl->t.p2g_off, &pl->t.par_box, &pl->t.tgt_blk, &pl->t.tgt_info, &pl->kx_green, &pl->kz_green, &pl->tc_w, &pl->tc_wexp, &pl->tc_mean, &pl->t.tc_rows, &pl->t.tc_tgt, &pl->t.tgt_box,
+                    &pl->t.box_child, &pl->t.box_nb, &pl->t.cnt, &pl->t.off, &pl->t.bnd, &pl->t.p2g_off, &pl->t.par_box, &pl->t.tgt_blk, &pl->t.tgt_info, &pl->kx_green, &pl->kz_green, &pl->tc_w, &pl->tc_wexp, &pl->glat, &pl->near_tab, &pl->tc_mean, &pl->t.tc_rows, &pl->t.tc_tgt, &pl->t.tgt_box,
                     &pl->t.box_tgt, &pl->t.leaf_box, &pl->t.p2g_box, &pl->t.item_leaf, &pl->t.item_s0,
                     &pl->t.item_s1, &pl->t.leaf_nitem, &pl->t.leaf_item0, &pl->t.leaf_part0, &pl->s.part, &pl->t.err, &pl->t.lvl_dev, &pl->t.counters, &pl->t.scan_buf,
                     &pl->s.grid, &pl->s.m2l_raw, &pl->s.loc, &pl->s.locc, &pl->s.m2lc, &pl->gmean, &pl->s.far, &pl->s.m2l_scratch, &pl->s.work, &pl->s.grid_hl, &pl->s.box_exp, &pl->s.box_mass, &pl->s.col_exp, &pl->s.zone_mass, &pl->s.level_amax,
@@ -147,8 +147,21 @@ hpm_status hpm_plan(const hpm_domain *dom, int max_depth, int gridlet_order, con
   if (!(dom->side > 0.0) || !std::isfinite(dom->side)) return HPM_ERR_INVALID_ARG;
   for (int d = 0; d < 3; ++d)
     if (!std::isfinite(dom->origin[d])) return HPM_ERR_INVALID_ARG;
-  if (green->kind != HPM_GREEN_PLUMMER) return HPM_ERR_UNSUPPORTED;
-  if (!(green->eps >= 0.0) || !std::isfinite(green->eps)) return HPM_ERR_INVALID_ARG;
+  switch (green->kind) {
+    case HPM_GREEN_PLUMMER:
+    case HPM_GREEN_YUKAWA:
+      if (!(green->eps >= 0.0) || !std::isfinite(green->eps)) return HPM_ERR_INVALID_ARG;
+      if (green->kind == HPM_GREEN_YUKAWA && (!(green->lambda > 0.0) || !std::isfinite(green->lambda)))
+        return HPM_ERR_INVALID_ARG;
+      break;
+    case HPM_GREEN_NEWTON:
+      break;
+    case HPM_GREEN_USER:
+      if (!green->user_g) return HPM_ERR_INVALID_ARG;
+      break;
+    default:
+      return HPM_ERR_UNSUPPORTED;
+  }
   if (opts && opts->leaf_max < 0) return HPM_ERR_INVALID_ARG;
   hpm_plan_s *pl = new (std::nothrow) hpm_plan_s();
   if (!pl) return HPM_ERR_OOM;
@@ -156,6 +169,7 @@ hpm_status hpm_plan(const hpm_domain *dom, int max_depth, int gridlet_order, con
   pl->max_depth = max_depth;
   pl->ng = gridlet_order;
   pl->green = *green;
+  if (pl->green.kind == HPM_GREEN_NEWTON) pl->green.eps = 0.0;
   pl->opts = opts ? *opts : hpm_plan_opts{0, 0};
   cudaGetDevice(&pl->device);
   make_tables(gridlet_order, pl->tab);

@@ -279,7 +279,7 @@ __host__ __device__ __forceinline__ int sw64(int r, int k) { return (r >> 3) * 5
 // Entry (row r of quarter q, K-chunk c, source node jj of the chunk's plane)
 // of W_l: -g(h |d|) for the child's node, minus the same for node 0 (rows of
 // nodes >= 1) or minus the row mean m_o (node 0); zero in the near zone.
-__device__ __forceinline__ double w_entry(int q, int r, int c, int jj, double h, double eps,
+__device__ __forceinline__ double w_entry(int q, int r, int c, int jj, const double *__restrict__ gl,
                                           const double *__restrict__ mean) {
   const int o = 2 * q + (r >> 6), node = r & 63;
   const int px = 2 + (o & 1), py = 2 + ((o >> 1) & 1), pz = 2 + (o >> 2);  // child in the 6^3 block
@@ -287,11 +287,11 @@ __device__ __forceinline__ double w_entry(int q, int r, int c, int jj, double h,
   const int sx = s % 6, sy = (s / 6) % 6, sz = s / 36;
   if (max(abs(sx - px), max(abs(sy - py), abs(sz - pz))) <= 1) return 0.0;
   const int bx = 4 * sx + (jj & 3), by = 4 * sy + (jj >> 2), bz = 4 * sz + zq;  // source node, grid units
-  const double dx = 4 * px + (node & 3) - bx, dy = 4 * py + ((node >> 2) & 3) - by, dz = 4 * pz + (node >> 4) - bz;
-  double w = -1.0 / sqrt(h * h * (dx * dx + dy * dy + dz * dz) + eps * eps);
+  const int dx = 4 * px + (node & 3) - bx, dy = 4 * py + ((node >> 2) & 3) - by, dz = 4 * pz + (node >> 4) - bz;
+  double w = -gl[dx * dx + dy * dy + dz * dz];  // -g(h |d|), the level's lattice table
   if (node != 0) {
-    const double ex = 4 * px - bx, ey = 4 * py - by, ez = 4 * pz - bz;
-    w -= -1.0 / sqrt(h * h * (ex * ex + ey * ey + ez * ez) + eps * eps);
+    const int ex = 4 * px - bx, ey = 4 * py - by, ez = 4 * pz - bz;
+    w += gl[ex * ex + ey * ey + ez * ez];
   } else {
     w -= mean[o];
   }
@@ -300,12 +300,12 @@ __device__ __forceinline__ double w_entry(int q, int r, int c, int jj, double h,
 
 // Largest |entry| of each of the 512 rows (as float bits, nonnegative floats
 // order like their bits). One thread per (q, c, row).
-__global__ void k_w_rowmax(double h, double eps, const double *__restrict__ mean, int *__restrict__ rowmax) {
+__global__ void k_w_rowmax(const double *__restrict__ gl, const double *__restrict__ mean, int *__restrict__ rowmax) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)kQuarters * kChunks * kRows) return;
   const int r = (int)(i % kRows), c = (int)((i / kRows) % kChunks), q = (int)(i / ((int64_t)kRows * kChunks));
   double m = 0.0;
-  for (int jj = 0; jj < kKC; ++jj) m = fmax(m, fabs(w_entry(q, r, c, jj, h, eps, mean)));
+  for (int jj = 0; jj < kKC; ++jj) m = fmax(m, fabs(w_entry(q, r, c, jj, gl, mean)));
   atomicMax(rowmax + q * kRows + r, __float_as_int((float)m));
 }
 
@@ -314,7 +314,7 @@ __global__ void k_w_rowmax(double h, double eps, const double *__restrict__ mean
 // of 128 rows x (16 hi, 16 lo) FP16 values of the row-scaled entries, swizzled
 // as the MMA reads it. One thread per (q, c, row); the c = 0 threads also
 // store the row exponents.
-__global__ void k_w_table(double h, double eps, const double *__restrict__ mean, const int *__restrict__ rowmax,
+__global__ void k_w_table(const double *__restrict__ gl, const double *__restrict__ mean, const int *__restrict__ rowmax,
                           unsigned char *__restrict__ out, int *__restrict__ w_exp) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)kQuarters * kChunks * kRows) return;
@@ -324,7 +324,7 @@ __global__ void k_w_table(double h, double eps, const double *__restrict__ mean,
   const double sc = ldexp(1.0, e);
   uint32_t hw[8], lw[8];
   for (int jj = 0; jj < kKC; jj += 2) {
-    const double a = w_entry(q, r, c, jj, h, eps, mean) * sc, b = w_entry(q, r, c, jj + 1, h, eps, mean) * sc;
+    const double a = w_entry(q, r, c, jj, gl, mean) * sc, b = w_entry(q, r, c, jj + 1, gl, mean) * sc;
     const __half ah = __double2half(a), bh = __double2half(b);
     hw[jj / 2] = pack_h2(ah, bh);
     lw[jj / 2] = pack_h2(__double2half(a - (double)__half2float(ah)), __double2half(b - (double)__half2float(bh)));
@@ -800,7 +800,7 @@ hpm_status tc_precompute(hpm_plan_s *pl, cudaStream_t st) {
   // m_o: mean of -g(h |y_{o,0} - y_{s,j}|) over the zone's 189 slots x 64 nodes
   std::vector<double> mean(8 * (D + 1), 0.0);
   for (int l = 2; l <= D; ++l) {
-    const double h = pl->dom.side / (double)(1u << l) / (double)pl->ng, eps = pl->green.eps;
+    const double *gl = pl->glat_host.data() + pl->glat_stride * l;
     for (int o = 0; o < 8; ++o) {
       const int px = 2 + (o & 1), py = 2 + ((o >> 1) & 1), pz = 2 + (o >> 2);
       double sum = 0.0;
@@ -809,9 +809,9 @@ hpm_status tc_precompute(hpm_plan_s *pl, cudaStream_t st) {
         const int sx = s % 6, sy = (s / 6) % 6, sz = s / 36;
         if (std::max(std::abs(sx - px), std::max(std::abs(sy - py), std::abs(sz - pz))) <= 1) continue;
         for (int j = 0; j < tc::kM3; ++j) {
-          const double dx = 4 * px - (4 * sx + (j & 3)), dy = 4 * py - (4 * sy + ((j >> 2) & 3)),
-                       dz = 4 * pz - (4 * sz + (j >> 4));
-          sum += -1.0 / std::sqrt(h * h * (dx * dx + dy * dy + dz * dz) + eps * eps);
+          const int dx = 4 * px - (4 * sx + (j & 3)), dy = 4 * py - (4 * sy + ((j >> 2) & 3)),
+                    dz = 4 * pz - (4 * sz + (j >> 4));
+          sum += -gl[dx * dx + dy * dy + dz * dz];
           ++cnt;
         }
       }
@@ -825,13 +825,13 @@ hpm_status tc_precompute(hpm_plan_s *pl, cudaStream_t st) {
   int *rowmax = nullptr;
   HPM_TRY(lib_malloc_async((void **)&rowmax, sizeof(int) * tc::kQuarters * tc::kRows, st));
   for (int l = 2; l <= D; ++l) {
-    const double h = pl->dom.side / (double)(1u << l) / (double)pl->ng;
+    const double *gl = pl->glat.as<double>() + pl->glat_stride * l;
     const double *mean_l = pl->tc_mean.as<double>() + 8 * l;
     int *wexp = pl->tc_wexp.as<int>() + tc::kQuarters * tc::kRows * (l - 2);
     HPM_CUDA(cudaMemsetAsync(rowmax, 0, sizeof(int) * tc::kQuarters * tc::kRows, st));
-    tc::k_w_rowmax<<<nblk, 256, 0, st>>>(h, pl->green.eps, mean_l, rowmax);
+    tc::k_w_rowmax<<<nblk, 256, 0, st>>>(gl, mean_l, rowmax);
     HPM_LAUNCHED((int64_t *)nullptr);
-    tc::k_w_table<<<nblk, 256, 0, st>>>(h, pl->green.eps, mean_l, rowmax,
+    tc::k_w_table<<<nblk, 256, 0, st>>>(gl, mean_l, rowmax,
                                         pl->tc_w.as<unsigned char>() + tc::kLevelBytes * (l - 2), wexp);
     HPM_LAUNCHED((int64_t *)nullptr);
   }

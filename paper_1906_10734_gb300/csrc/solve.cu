@@ -557,38 +557,88 @@ __device__ __forceinline__ float2 rel_split(float h, float c0, float lo) {
   return make_float2(r, (hr - r) + lo);
 }
 
+// Near-field kernel forms: 0 Plummer (Newton with eps = 0), 1 Yukawa, 2 a
+// user kernel from its table (green.cu). Pairs are summed in unit-cube
+// coordinates; the closed forms are scaled back by 1/S (potential) and 1/S^2
+// (acceleration) once per target, the table holds physical g and the force
+// factor -g'(r) / r_u directly.
+struct NearKernel {
+  float eps2;         // (eps / S)^2, forms 0 and 1
+  float inv_lambda;   // S / lambda, form 1
+  const float4 *tab;  // form 2: per segment the cubic coefficients of g, then of the force factor
+};
+
+// m g(r) and m F(r), F the force factor (a_i += m F (x_j - x_i)), of a pair at
+// squared distance r2 (softening included for forms 0 and 1).
+template <int KIND>
+__device__ __forceinline__ void pair_coef(const NearKernel &nk, float r2, float m, float &mg, float &mf) {
+  if constexpr (KIND == 0) {
+    const float ir = rsqrtf(r2);
+    mg = m * ir;
+    mf = mg * ir * ir;
+  } else if constexpr (KIND == 1) {
+    const float ir = rsqrtf(r2);
+    const float sl = r2 * ir * nk.inv_lambda;  // s / lambda
+    mg = m * ir * __expf(-sl);
+    mf = mg * ir * ir * (1.f + sl);
+  } else {
+    // segment: (exponent - E0) * 32 + the top 5 mantissa bits of r2; the
+    // position in it: the remaining 18 mantissa bits
+    const unsigned b = __float_as_uint(r2);
+    int seg = (int)(b >> 18) - ((127 + kNearTabE0) << 5);
+    float t = (float)(b & 0x3FFFFu) * (1.f / 262144.f);
+    if (seg < 0) {
+      seg = 0;
+      t = 0.f;
+    } else if (seg >= kNearTabOctaves * kNearTabSeg) {
+      seg = kNearTabOctaves * kNearTabSeg - 1;
+      t = 1.f;
+    }
+    const float4 cg = __ldg(nk.tab + 2 * seg), cf = __ldg(nk.tab + 2 * seg + 1);
+    mg = m * fmaf(fmaf(fmaf(cg.w, t, cg.z), t, cg.y), t, cg.x);
+    mf = m * fmaf(fmaf(fmaf(cf.w, t, cf.z), t, cf.y), t, cf.x);
+  }
+}
+
 // One source's contribution to a target, accumulated into a short plain-FP32
 // block sum. pair_fast takes the difference of the rounded relative positions
 // (error below 2^-23 of the leaf side) and returns r^2 for the block's check;
 // pair_exact takes (r_s - r_t) + (e_s - e_t), which keeps FP32 precision
 // relative to the pair distance however small it is, and skips the target
 // itself. sr.w holds the mass, se.w the particle index.
-__device__ __forceinline__ float pair_fast(const float4 &tr, const float4 &s, float eps2, float &bp, float &bx,
-                                           float &by, float &bz) {
+template <int KIND>
+__device__ __forceinline__ float pair_fast(const float4 &tr, const float4 &s, const NearKernel &nk, float &bp,
+                                           float &bx, float &by, float &bz) {
   const float dx = s.x - tr.x, dy = s.y - tr.y, dz = s.z - tr.z;
-  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-  const float ir = rsqrtf(r2);
-  const float mir = s.w * ir;
-  const float mir3 = mir * ir * ir;
-  bp -= mir;
-  bx = fmaf(mir3, dx, bx);
-  by = fmaf(mir3, dy, by);
-  bz = fmaf(mir3, dz, bz);
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, nk.eps2)));
+  float mg, mf;
+  pair_coef<KIND>(nk, r2, s.w, mg, mf);
+  bp -= mg;
+  bx = fmaf(mf, dx, bx);
+  by = fmaf(mf, dy, by);
+  bz = fmaf(mf, dz, bz);
   return r2;
 }
 
+template <int KIND>
 __device__ __forceinline__ void pair_exact(const float4 &tr, const float4 &te, const float4 &s, const float4 &e,
-                                           float eps2, float &bp, float &bx, float &by, float &bz) {
+                                           const NearKernel &nk, float &bp, float &bx, float &by, float &bz) {
   const float dx = (s.x - tr.x) + (e.x - te.x), dy = (s.y - tr.y) + (e.y - te.y), dz = (s.z - tr.z) + (e.z - te.z);
-  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-  float ir = rsqrtf(r2);
-  if (__float_as_int(e.w) == __float_as_int(te.w)) ir = 0.f;  // the target itself
-  const float mir = s.w * ir;
-  const float mir3 = mir * ir * ir;
-  bp -= mir;
-  bx = fmaf(mir3, dx, bx);
-  by = fmaf(mir3, dy, by);
-  bz = fmaf(mir3, dz, bz);
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, nk.eps2)));
+  float mg, mf;
+  if constexpr (KIND == 0) {
+    float ir = rsqrtf(r2);
+    if (__float_as_int(e.w) == __float_as_int(te.w)) ir = 0.f;  // the target itself
+    mg = s.w * ir;
+    mf = mg * ir * ir;
+  } else {
+    pair_coef<KIND>(nk, r2, s.w, mg, mf);
+    if (__float_as_int(e.w) == __float_as_int(te.w)) mg = mf = 0.f;  // the target itself
+  }
+  bp -= mg;
+  bx = fmaf(mf, dx, bx);
+  by = fmaf(mf, dy, by);
+  bz = fmaf(mf, dz, bz);
 }
 
 // Near zone by direct summation (Sec. 1, item 1), one warp per work item: an
@@ -605,6 +655,7 @@ __device__ __forceinline__ void pair_exact(const float4 &tr, const float4 &te, c
 // ends early starts the next one instead of idling until its block retires.
 constexpr int kP2PChunk = 128;
 
+template <int KIND>
 __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *__restrict__ item_leaf,
                                                   const int *__restrict__ item_s0, const int *__restrict__ item_s1,
                                                   const int *__restrict__ leaf_nitem,
@@ -615,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
                                                   const float4 *__restrict__ hi, const float4 *__restrict__ lo,
                                                   const float4 *__restrict__ far,
                                                   const uint32_t *__restrict__ perm, const uint64_t *__restrict__ key,
-                                                  LevelTable lt, float eps2, float sc_phi,
+                                                  LevelTable lt, NearKernel nk, float sc_phi,
                                                   float sc_acc, float *__restrict__ out_phi, float *__restrict__ out_acc,
                                                   float4 *__restrict__ part, unsigned long long *__restrict__ next) {
   __shared__ int rb[kWarpsPerBlock][28], cum[kWarpsPerBlock][28];
@@ -669,7 +720,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
   float near2;
   {
     const float side = 1.f / (float)(1u << level_of(lt, box));  // the leaf's side (unit cube)
-    near2 = eps2 + side * side * (1.f / 64.f);  // r^2 of a pair 1/8 of the side apart
+    near2 = nk.eps2 + side * side * (1.f / 64.f);  // r^2 of a pair 1/8 of the side apart
   }
   const int kidx = (int)(it - leaf_item0[leaf]);
   for (int t0 = tb; t0 < te; t0 += per) {
@@ -724,13 +775,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
           // difference 0, r2 = eps2 <= near2) the block is summed again exactly
           float bp = 0.f, bx = 0.f, by = 0.f, bz = 0.f, r2min = 3.4e38f;
 #pragma unroll
-          for (int u = 0; u < 8; ++u) r2min = fminf(r2min, pair_fast(th, srh[w][k + u * G], eps2, bp, bx, by, bz));
+          for (int u = 0; u < 8; ++u) r2min = fminf(r2min, pair_fast<KIND>(th, srh[w][k + u * G], nk, bp, bx, by, bz));
           if (__any_sync(__activemask(), r2min <= near2)) {
             bp = bx = by = bz = 0.f;
 #pragma unroll 4
             for (int u = 0; u < 8; ++u) {
               const int kk = k + u * G;
-              pair_exact(th, tl, srh[w][kk], srl[w][kk], eps2, bp, bx, by, bz);
+              pair_exact<KIND>(th, tl, srh[w][kk], srl[w][kk], nk, bp, bx, by, bz);
             }
           }
           kahan_add(sp, cp, bp);
@@ -739,7 +790,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
           kahan_add(sz, cz, bz);
         }
         float bp = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
-        for (; k < cn; k += G) pair_exact(th, tl, srh[w][k], srl[w][k], eps2, bp, bx, by, bz);
+        for (; k < cn; k += G) pair_exact<KIND>(th, tl, srh[w][k], srl[w][k], nk, bp, bx, by, bz);
         kahan_add(sp, cp, bp);
         kahan_add(sx, cx, bx);
         kahan_add(sy, cy, by);
@@ -1102,27 +1153,34 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
   HPM_LAUNCHED(&launches);
   record(pl, 6, st);
   {
-    // pairs are summed in unit-cube coordinates (eps / S), scaled back by 1/S
-    // (potential) and 1/S^2 (acceleration) once per target
-    const double eu = pl->green.eps / pl->dom.side;
-    const float eps2 = (float)(eu * eu);
-    const float s1 = (float)(1.0 / pl->dom.side), s2 = (float)(1.0 / (pl->dom.side * pl->dom.side));
+    // pairs are summed in unit-cube coordinates (eps / S, lambda / S); the
+    // closed forms are scaled back by 1/S (potential) and 1/S^2 (acceleration)
+    // once per target, the user kernel's table is in physical units already
+    const double S = pl->dom.side;
+    const double eu = pl->green.eps / S;
+    const int kind = pl->green.kind == HPM_GREEN_USER ? 2 : (pl->green.kind == HPM_GREEN_YUKAWA ? 1 : 0);
+    NearKernel nk{};
+    nk.eps2 = kind == 2 ? 0.f : (float)(eu * eu);
+    nk.inv_lambda = kind == 1 ? (float)(S / pl->green.lambda) : 0.f;
+    nk.tab = pl->near_tab.as<float4>();
+    const float s1 = kind == 2 ? 1.f : (float)(1.0 / S), s2 = kind == 2 ? 1.f : (float)(1.0 / (S * S));
     HPM_TRY(s.part.ensure(sizeof(float4) * (pl->npart > 0 ? pl->npart : 1), st));
-    static DeviceCache p2p_cache;
+    auto kp = kind == 0 ? k_p2p<0> : (kind == 1 ? k_p2p<1> : k_p2p<2>);
+    static DeviceCache p2p_cache[3];
     int p2p_resident = 1;
-    HPM_TRY(device_cached(p2p_cache, [](int *v) -> hpm_status {
-      HPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(v, k_p2p, kThreads, 0));
+    HPM_TRY(device_cached(p2p_cache[kind], [kp](int *v) -> hpm_status {
+      HPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(v, kp, kThreads, 0));
       if (*v < 1) *v = 1;
       return HPM_OK;
     }, &p2p_resident));
     HPM_TRY(s.work.ensure(sizeof(unsigned long long), st));
     HPM_CUDA(cudaMemsetAsync(s.work.p, 0, sizeof(unsigned long long), st));
     const unsigned p2p_grid = (unsigned)std::min<int64_t>(warp_blocks(pl->nitem), (int64_t)p2p_resident * sm_count());
-    k_p2p<<<p2p_grid, kThreads, 0, st>>>(
+    kp<<<p2p_grid, kThreads, 0, st>>>(
         pl->nitem, t.item_leaf.as<int>(), t.item_s0.as<int>(), t.item_s1.as<int>(), t.leaf_nitem.as<int>(),
         t.leaf_item0.as<int>(), t.leaf_part0.as<int>(), t.leaf_box.as<int>(), t.box_nb.as<int>(),
         t.box_beg.as<int>(), t.box_end.as<int>(), hi, lo, s.far.as<float4>(), t.perm.as<uint32_t>(),
-        t.box_key.as<uint64_t>(), lt, eps2, s1, s2, d_phi, d_acc, s.part.as<float4>(),
+        t.box_key.as<uint64_t>(), lt, nk, s1, s2, d_phi, d_acc, s.part.as<float4>(),
         s.work.as<unsigned long long>());
     HPM_LAUNCHED(&launches);
     if (pl->npart > 0) {

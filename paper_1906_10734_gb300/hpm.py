@@ -18,7 +18,7 @@ HPM_OK = 0
 STATUS = {0: "HPM_OK", -1: "HPM_ERR_INVALID_ARG", -2: "HPM_ERR_OUT_OF_DOMAIN", -3: "HPM_ERR_OOM",
           -4: "HPM_ERR_CUDA", -5: "HPM_ERR_TIMEOUT", -6: "HPM_ERR_NOT_BUILT", -7: "HPM_ERR_BUSY",
           -8: "HPM_ERR_UNSUPPORTED"}
-HPM_GREEN_PLUMMER = 0
+HPM_GREEN_PLUMMER, HPM_GREEN_NEWTON, HPM_GREEN_YUKAWA, HPM_GREEN_USER = 0, 1, 2, 3
 HPM_FLAG_TIMINGS = 1
 HPM_FLAG_GENERIC_M2L = 2
 HPM_FLAG_XTRANSFORM_M2L = 4
@@ -33,8 +33,52 @@ class hpm_domain(ctypes.Structure):
     _fields_ = [("origin", ctypes.c_double * 3), ("side", ctypes.c_double)]
 
 
+USER_G = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_void_p)   # double (*)(double r, void *ctx)
+
+
 class hpm_green(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("eps", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int), ("eps", ctypes.c_double), ("lam", ctypes.c_double),
+                ("user_g", USER_G), ("ctx", ctypes.c_void_p)]
+
+
+class Green:
+    """A Green function descriptor (hpm_green): Plummer (default), Newton, Yukawa, or a user
+    kernel given as a C function pointer ``double g(double r, void *ctx)`` (a ctypes
+    function from a shared library, or a ``USER_G`` wrapping a Python callable; the library
+    calls it only while a plan is made)."""
+
+    def __init__(self, kind=HPM_GREEN_PLUMMER, eps=0.0, lam=0.0, user_g=None, ctx=None):
+        self.kind, self.eps, self.lam, self.ctx = kind, float(eps), float(lam), ctx
+        self.user_g = None if user_g is None else ctypes.cast(user_g, USER_G)
+        self._keep = (user_g, ctx)
+
+    @classmethod
+    def plummer(cls, eps):
+        return cls(HPM_GREEN_PLUMMER, eps)
+
+    @classmethod
+    def newton(cls):
+        return cls(HPM_GREEN_NEWTON)
+
+    @classmethod
+    def yukawa(cls, lam, eps=0.0):
+        return cls(HPM_GREEN_YUKAWA, eps, lam)
+
+    @classmethod
+    def user(cls, fn, ctx=None):
+        return cls(HPM_GREEN_USER, user_g=fn, ctx=ctx)
+
+    def struct(self) -> hpm_green:
+        g = hpm_green(self.kind, self.eps, self.lam)
+        if self.user_g is not None:
+            g.user_g = self.user_g
+        if self.ctx is not None:
+            g.ctx = ctypes.cast(self.ctx, ctypes.c_void_p)
+        return g
+
+
+def _green(eps, green) -> hpm_green:
+    return (green if green is not None else Green.plummer(eps)).struct()
 
 
 class hpm_plan_opts(ctypes.Structure):
@@ -170,10 +214,11 @@ def _stream(stream) -> int:
 
 
 def hpm_plan(origin=(0.0, 0.0, 0.0), side=1.0, max_depth=3, gridlet_order=4, eps=0.0, leaf_max=0,
-             flags=0) -> int:
+             flags=0, green: Green | None = None) -> int:
+    """A plan (hpm_plan). The kernel is `green` if given, else Plummer with softening eps."""
     L = load()
     dom = hpm_domain((ctypes.c_double * 3)(*origin), side)
-    green = hpm_green(HPM_GREEN_PLUMMER, eps)
+    green = _green(eps, green)
     opts = hpm_plan_opts(leaf_max, flags)
     out = _vp()
     _check("hpm_plan", L.hpm_plan(ctypes.byref(dom), max_depth, gridlet_order, ctypes.byref(green),
@@ -309,10 +354,10 @@ class Server:
     host numpy arrays or device tensors and must stay alive until it is done."""
 
     def __init__(self, max_depth=12, gridlet_order=4, eps=1e-4, leaf_max=32, workers=2, max_batch=64,
-                 hbm_budget_bytes=150 << 30, origin=(0.0, 0.0, 0.0), side=1.0):
+                 hbm_budget_bytes=150 << 30, origin=(0.0, 0.0, 0.0), side=1.0, green: Green | None = None):
         L = load()
         opts = hpm_server_opts(hpm_domain((ctypes.c_double * 3)(*origin), side), max_depth, gridlet_order,
-                               hpm_green(HPM_GREEN_PLUMMER, eps), leaf_max, workers, max_batch, hbm_budget_bytes)
+                               _green(eps, green), leaf_max, workers, max_batch, hbm_budget_bytes)
         h = _vp()
         _check("hpm_server_create", L.hpm_server_create(ctypes.byref(opts), ctypes.byref(h)))
         self.h = h.value
@@ -383,10 +428,10 @@ class Solver:
     """Convenience owner of one plan: build + solve on torch device tensors."""
 
     def __init__(self, max_depth, gridlet_order=4, eps=0.0, leaf_max=0, origin=(0.0, 0.0, 0.0), side=1.0,
-                 timings=False, flags=0):
+                 timings=False, flags=0, green: Green | None = None):
         self.ng = gridlet_order
         self.plan = hpm_plan(origin, side, max_depth, gridlet_order, eps, leaf_max,
-                             (HPM_FLAG_TIMINGS if timings else 0) | flags)
+                             (HPM_FLAG_TIMINGS if timings else 0) | flags, green)
 
     def __call__(self, pos, mass, phi=None, acc=None, stream=None):
         import torch

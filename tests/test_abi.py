@@ -67,3 +67,18 @@ def test_null_plan_is_rejected(lib):
     assert lib.hpm_get_tuning(None, None) == -1
     assert lib.hpm_tune(None, None, None, 0, None, None) == -1
     assert lib.hpm_destroy(None) == 0
+
+
+def test_plan_refuses_invalid_green_functions(lib):
+    """Kernel checks of hpm_plan return before any CUDA call: a Yukawa kernel needs a
+    positive screening length and a nonnegative softening, a user kernel a function, and
+    an unknown kind is unsupported."""
+    from paper_1906_10734_gb300 import hpm
+    for g in (hpm.Green(hpm.HPM_GREEN_YUKAWA, 0.0, 0.0), hpm.Green(hpm.HPM_GREEN_YUKAWA, -1.0, 0.1),
+              hpm.Green(hpm.HPM_GREEN_USER)):
+        with pytest.raises(hpm.HpmError) as e:
+            hpm.hpm_plan((0.0, 0.0, 0.0), 1.0, 3, 4, green=g)
+        assert e.value.status == -1
+    with pytest.raises(hpm.HpmError) as e:
+        hpm.hpm_plan((0.0, 0.0, 0.0), 1.0, 3, 4, green=hpm.Green(7))
+    assert e.value.status == -8

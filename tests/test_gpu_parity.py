@@ -35,9 +35,9 @@ def hpm():
     return H
 
 
-def gpu_solve(H, pos, mass, depth, ng, eps, leaf_max, lists=False):
+def gpu_solve(H, pos, mass, depth, ng, eps, leaf_max, lists=False, green=None, flags=0):
     dev = torch.device("cuda:0")
-    s = H.Solver(depth, ng, eps, leaf_max)
+    s = H.Solver(depth, ng, eps, leaf_max, green=green, flags=flags)
     p = torch.from_numpy(np.ascontiguousarray(pos)).to(dev)
     m = torch.from_numpy(np.ascontiguousarray(mass)).to(dev)
     phi, acc = s(p, m)

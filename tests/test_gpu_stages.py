@@ -25,9 +25,9 @@ def hpm():
     return H
 
 
-def run(H, w, flags=0):
+def run(H, w, flags=0, green=None):
     dev = torch.device("cuda:0")
-    s = H.Solver(w.max_depth, w.ng, w.eps, w.leaf_max, flags=flags)
+    s = H.Solver(w.max_depth, w.ng, w.eps, w.leaf_max, flags=flags, green=green)
     s(torch.from_numpy(w.pos).to(dev), torch.from_numpy(w.mass).to(dev))
     torch.cuda.synchronize()
     out = {"boxes": s.boxes(), "lists": s.lists(), "masses": s.stage(H.HPM_STAGE_MASSES),
@@ -42,8 +42,11 @@ def variation_err(gpu_vals, ref_vals):
     return float(np.sqrt(np.sum((g - r) ** 2) / np.sum(r * r)))
 
 
-def check_stages(H, w, flags=0, max_targets=None, seed=0, var_tol=1e-5):
-    g = run(H, w, flags)
+def check_stages(H, w, flags=0, max_targets=None, seed=0, var_tol=1e-5, green=None, kernel=None):
+    """Stage parity; `green` (library) and `kernel` (oracle) name another Green function
+    than the workload's Plummer softening."""
+    g = run(H, w, flags, green)
+    kern = kernel if kernel is not None else w.eps
     tr = O.Tree(w.pos, max_depth=w.max_depth, leaf_max=w.leaf_max)
     b = g["boxes"]
     sel = np.flatnonzero(b["level"] >= 2)
@@ -57,11 +60,11 @@ def check_stages(H, w, flags=0, max_targets=None, seed=0, var_tol=1e-5):
     if max_targets and pick.size > max_targets:
         pick = np.sort(np.random.default_rng(seed).choice(pick.size, max_targets, replace=False))
     m3 = w.ng ** 3
-    ref = O.m2l_values(tr, w.mass, w.ng, w.eps, tl[pick], tk[pick])
+    ref = O.m2l_values(tr, w.mass, w.ng, kern, tl[pick], tk[pick])
     got = g["m2l"][pick, :m3].astype(np.float64) + g["m2l"][pick, m3:].astype(np.float64)
     assert variation_err(got, ref) < var_tol
     assert O.rel_rms(got, ref) < 1e-6
-    ref = O.local_values(tr, w.mass, w.ng, w.eps, tl[pick], tk[pick])
+    ref = O.local_values(tr, w.mass, w.ng, kern, tl[pick], tk[pick])
     got = g["local"][pick, :m3].astype(np.float64) + g["local"][pick, m3:].astype(np.float64)
     assert variation_err(got, ref) < var_tol
     assert O.rel_rms(got, ref) < 1e-6
