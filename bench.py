@@ -45,7 +45,17 @@ def m2l_flops_per_target(ng: int) -> float:
     return 5.0 * P ** 3 * math.log2(P ** 3) + 2.0 * P * P * (P // 2 + 1)
 
 
-DENSE_FLOP_PER_PARENT = 3 * 2 * 512 * 216 * 64   # three FP16 products per term of the 512 x 13824 product
+def dense_flop_per_parent(ng: int) -> int:
+    """Executed tensor work of the dense source-to-target product per parent: three FP16
+    products (hi*hi, hi*lo, lo*hi) x 2 x rows x K, rows = 8 Ng^3 padded to 128-row blocks,
+    K = 216 slots x Ng^3 nodes padded to 16 (Ng = 4: 512 x 13824; Ng = 6: 1792 x 48384)."""
+    m3 = ng ** 3
+    rows = -(-8 * m3 // 128) * 128
+    k = 216 * (-(-m3 // 16) * 16)
+    return 3 * 2 * rows * k
+
+
+DENSE_FLOP_PER_PARENT = dense_flop_per_parent(4)
 
 
 def alu_peaks() -> dict:
@@ -91,18 +101,19 @@ def roofline_of(stats_steps, ng, n_targets, traffic_src, live_peaks=None):
     if parents:
         kms = statistics.mean(s["ms_m2l_kernel"] for s in stats_steps)
         achieved = nominal_flop / (kms / 1e3) / 1e12
-        executed = DENSE_FLOP_PER_PARENT * parents / (kms / 1e3) / 1e12
+        executed = dense_flop_per_parent(ng) * parents / (kms / 1e3) / 1e12
         peak = peaks.get("bf16_tflops", 1900.0)
-        return {"kernel": "k_m2l_tc: Ng = 4 source-to-target as a dense FP16-pair tcgen05 product per parent block",
+        return {"kernel": f"k_m2l_tc<{ng}>: source-to-target as a dense FP16-pair tcgen05 product per parent block",
                 "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": profile_traffic(traffic_src) if traffic_src else None, "ms_per_launch": kms,
                 "launches_per_step": 1, "flop_per_target": m2l_flops_per_target(ng),
                 "targets_per_launch": n_targets,
                 "flop_basis": "nominal FFT convolution work per target x targets (algorithmic)",
                 "peak_basis": "MEASURED_PEAKS.json bf16_tflops (dense, burst) of measured; FP16 has the bf16 tensor rate",
-                "executed": {"achieved": executed, "frac": executed / peak, "flop_per_parent": DENSE_FLOP_PER_PARENT,
+                "executed": {"achieved": executed, "frac": executed / peak, "flop_per_parent": dense_flop_per_parent(ng),
                              "parents_per_launch": parents,
-                             "basis": "3 FP16 products (hi*hi, hi*lo, lo*hi) x 2 x 512 rows x 13824 K per parent"},
+                             "basis": "3 FP16 products (hi*hi, hi*lo, lo*hi) x 2 x rows x K per parent, rows and K "
+                                      "padded as the kernel runs them"},
                 "stage": {"ms": stage_ms, "achieved": nominal_flop / (stage_ms / 1e3) / 1e12,
                           "frac": nominal_flop / (stage_ms / 1e3) / 1e12 / peak,
                           "basis": "same nominal work over the whole source-to-target stage (preparation "
@@ -110,7 +121,7 @@ def roofline_of(stats_steps, ng, n_targets, traffic_src, live_peaks=None):
     peak, basis = fp32_peak(live_peaks)
     achieved = nominal_flop / (stage_ms / 1e3) / 1e12
     return {"kernel": "source-to-target FFT convolution (k_m2l4)" if ng == 4 else
-                      "source-to-target convolution, x-transform kernel (k_m2l_xdft)",
+                      "source-to-target convolution, x-transform or any-order kernel (k_m2l_xdft / k_m2l_generic)",
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": profile_traffic(traffic_src) if traffic_src else None, "ms_per_launch": stage_ms,
             "launches_per_step": 1, "flop_per_target": m2l_flops_per_target(ng), "targets_per_launch": n_targets,

@@ -300,8 +300,14 @@ typedef struct {
   int gridlet_warps;       /* Ng = 4 child-to-parent and parent-to-child: warps
                               (one gridlet each) per CTA, 2, 4 or 8 (0 = 8)      */
   int m2l_ctas_per_sm;     /* FFT-form source-to-target kernels (HPM_FLAG_FFT_M2L,
-                              HPM_FLAG_XTRANSFORM_M2L, Ng != 4): persistent CTAs
-                              per SM, 1 or 2 (0 = the most that fit)             */
+                              HPM_FLAG_XTRANSFORM_M2L, other orders): persistent
+                              CTAs per SM, 1 or 2 (0 = the most that fit)        */
+  int m2l_block_order;     /* dense tensor-core source-to-target (Ng = 4, 6): the
+                              order of its CTAs, 1 tile-major (the row blocks of
+                              W for one tile of parents run together), 2 row-
+                              block-major (one pair of row blocks runs over every
+                              tile first: that part of W stays in L2 while the
+                              parents' gridlets stream); 0 = 1                   */
 } hpm_tuning;
 
 /* Sets the plan's launch shapes (values outside the ranges above are

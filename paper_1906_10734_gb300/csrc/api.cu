@@ -99,6 +99,7 @@ static void make_tables(int ng, GridletTables &tb) {
         for (int k = 0; k < ng; ++k)
           if (k != p) v *= (t - x[k]) / (x[p] - x[k]);
         tb.t1[s][p][q] = (float)v;
+        tb.t1lo[s][p][q] = (float)(v - (double)tb.t1[s][p][q]);
       }
   }
 }

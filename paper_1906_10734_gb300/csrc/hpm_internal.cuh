@@ -98,6 +98,7 @@ struct GridletTables {
   int ng;
   float node[kMaxNg];                // x_j = (j + 1/2)/Ng - 1/2
   float t1[2][kMaxNg][kMaxNg];       // T^{s}_{pq} = ell_p((a_s + x_q)/2), a_0 = -1/2, a_1 = +1/2
+  float t1lo[2][kMaxNg][kMaxNg];     // T^{s}_{pq} - t1 (the rest of the FP64 value)
   double node_d[kMaxNg];
   double inv_den_d[kMaxNg];          // 1 / prod_{k != j} (x_j - x_k)
   double inv_den_u[kMaxNg];          // the same for the nodes 2 Ng x_j = 2j + 1 - Ng (integers)
@@ -262,6 +263,8 @@ hpm_status tc_precompute(hpm_plan_s *pl, cudaStream_t st);
 hpm_status tc_build_tiles(hpm_plan_s *pl, const std::vector<int64_t> &par_per_level, cudaStream_t st,
                           int64_t *launches);
 hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches);
+// block order of the dense source-to-target kernel: 1 tile-major, 2 row-block-major
+int m2l_block_order(const hpm_plan_s *pl);
 }  // namespace hpm
 
 #define HPM_CUDA(call)                                  \

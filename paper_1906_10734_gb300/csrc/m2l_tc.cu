@@ -59,19 +59,16 @@
 namespace hpm {
 namespace tc {
 
-constexpr int kM3 = 64;                         // nodes per gridlet, Ng = 4
 constexpr int kSlots = 216;                     // 6^3 source block
-constexpr int kKC = 16;                         // K elements per stage (one z plane of a gridlet)
-constexpr int kChunks = kSlots * kM3 / kKC;     // 864 stages per tile
+constexpr int kKC = 16;                         // K elements per chunk (a 64-byte row of FP16 hi, lo)
 constexpr int kTileN = 256;                     // parents per tile
-constexpr int kRows = 128;                      // rows per CTA (2 children x 64 nodes)
-constexpr int kQuarters = 4;                    // CTAs per tile: two CTA pairs
+constexpr int kRows = 128;                      // rows of W per CTA
 constexpr int kHalfN = kTileN / 2;              // parents gathered by each CTA of a pair
-// One stage holds the 4 K-chunks (z planes) of one slot, so the MMA thread
-// issues 12 MMAs per barrier wait and commit: the per-stage synchronisation
-// cost (a few hundred cycles of the issuing thread) stays well below the
-// MMAs' 1536 cycles. Each CTA of a pair loads its own 128 rows of W and half
-// of the parents, so a stage is 64 KB and three fit.
+// One stage holds 4 K-chunks, so the MMA thread issues 12 MMAs per barrier
+// wait and commit: the per-stage synchronisation cost (a few hundred cycles of
+// the issuing thread) stays well below the MMAs' 1536 cycles. Each CTA of a
+// pair loads its own 128 rows of W and half of the parents, so a stage is
+// 64 KB and three fit.
 constexpr int kStageChunks = 4;
 constexpr int kStages = 3;
 constexpr int kRowBytes = 2 * kKC * 2;          // one tile row: 16 hi then 16 lo FP16 values
@@ -79,14 +76,35 @@ constexpr int kABytes = kRows * kRowBytes;      // W tile of one K-chunk: 8 KB
 constexpr int kBBytes = kHalfN * kRowBytes;     // gathered tile of one K-chunk: 8 KB
 constexpr int kStageABytes = kStageChunks * kABytes;                  // 32 KB, one bulk copy
 constexpr int kStageBytes = kStageChunks * (kABytes + kBBytes);       // 64 KB: 4 W tiles, then 4 B tiles
-constexpr int kSlotUses = kChunks / kStageChunks;                     // 216 stage uses per CTA
 // 1 KB for aligning the stages, 8 KB of slack past the last one
 constexpr int kSmem = kStages * kStageBytes + 1024 + 8192;
 constexpr int kScaleTop = 14;                   // scaled maxima lie in [2^13, 2^14)
 constexpr int kNoExp = 1 << 20;                 // exponent of a row without mass
 
-constexpr int kBlockChunks = 16;                // accumulator drained every 4 slots
-constexpr int kBlocks = kChunks / kBlockChunks;
+constexpr int kBlockChunks = 16;                // accumulator drained every 16 K-chunks
+
+// Sizes per gridlet order. K runs over the 216 source slots, each slot's
+// gridlet padded to a multiple of 16 nodes (kCPS K-chunks per slot); the rows
+// of W are the 8 children's nodes (kRowsReal), padded to 128-row blocks, one
+// per CTA (pairs of CTAs take consecutive blocks of one tile). Ng = 4: 4
+// chunks per slot, 864 per tile, 512 rows in 4 blocks; Ng = 6: 216 nodes in
+// 14 chunks, 3024 per tile, 1728 rows in 14 blocks (64 padding rows).
+template <int NG>
+struct Cfg {
+  static constexpr int kM3 = NG * NG * NG;                      // nodes per gridlet
+  static constexpr int kCPS = (kM3 + kKC - 1) / kKC;            // K-chunks per source slot
+  static constexpr int kChunks = kSlots * kCPS;                 // K-chunks per tile
+  static constexpr int kRowsReal = 8 * kM3;                     // rows of W that exist
+  static constexpr int kQuarters = (kRowsReal + kRows - 1) / kRows;   // 128-row blocks (CTAs per tile)
+  static constexpr int kSlotUses = kChunks / kStageChunks;      // stage uses per CTA
+  static constexpr int kBlocks = kChunks / kBlockChunks;        // accumulator drains per CTA
+  static constexpr int64_t kLevelBytes = (int64_t)kQuarters * kChunks * kABytes;  // W bytes per level
+  static_assert(kChunks % kBlockChunks == 0, "drain blocks tile the K loop");
+  static_assert(kBlockChunks % kStageChunks == 0, "drain blocks hold whole stages");
+  static_assert(kQuarters % 2 == 0, "CTA pairs");
+  static_assert(kCPS >= kStageChunks, "a gather warp's next chunk is in the same or the next slot");
+};
+
 // 4 warpgroups: 0 = W copy (warp 0), tensor memory and MMA issue (warp 1),
 // relays of the peer's stages (warps 2, 3); 1 = gather; 2, 3 = drain. The drain warps keep the running totals in
 // registers (128 per thread), so they take registers from the other two:
@@ -94,21 +112,17 @@ constexpr int kBlocks = kChunks / kBlockChunks;
 // launch's total.
 constexpr int kWarps = 16, kThreads = kWarps * 32;
 constexpr int kProdWarp0 = 4, kEpiWarp0 = 8;
-constexpr int kGatherWarps = kEpiWarp0 - kProdWarp0;  // one per z plane of a gridlet
+constexpr int kGatherWarps = kEpiWarp0 - kProdWarp0;  // one per K-chunk of a stage
 constexpr int kLaunchRegs = 128, kRegsCtl = 40, kRegsGather = 104, kRegsHigh = 184;
 static_assert(128 * kRegsCtl + 128 * kRegsGather + 2 * 128 * kRegsHigh == kThreads * kLaunchRegs, "register split");
-static_assert(kGatherWarps == 4, "gather warp g copies the z plane g of every slot");
+static_assert(kGatherWarps == kStageChunks, "gather warp g copies K-chunk g of every stage");
 // setmaxnreg: .dec only lowers, .inc only raises; counts are multiples of 8 in [24, 256]
 static_assert(kRegsCtl <= kLaunchRegs && kRegsGather <= kLaunchRegs && kRegsHigh >= kLaunchRegs, "dec / inc");
 static_assert(kRegsCtl % 8 == 0 && kRegsGather % 8 == 0 && kRegsHigh % 8 == 0 && kRegsCtl >= 24 && kRegsHigh <= 256,
               "register counts");
-constexpr int64_t kLevelBytes = (int64_t)kQuarters * kChunks * kABytes;  // W bytes per level
-static_assert(kChunks % kBlockChunks == 0, "drain blocks tile the K loop");
-static_assert(kStageChunks == 4 && kBlockChunks % kStageChunks == 0, "a stage is one slot; drain blocks hold whole stages");
-static_assert(kQuarters % 2 == 0, "CTA pairs");
 
 struct Params {
-  const unsigned char *w;  // W tables, level l at w + (l - 2) * kLevelBytes
+  const unsigned char *w;  // W tables, level l at w + (l - 2) * Cfg<NG>::kLevelBytes
   const int *w_exp;        // per level (from 2) and row: the row's scale exponent
   const int *col_exp;      // per tile and parent: the column's scale exponent
   const unsigned char *hl; // per row and z plane: 16 hi then 16 lo FP16 values at its level's scale
@@ -116,6 +130,10 @@ struct Params {
   const int *rows;         // per tile: [216][256] source row or -1
   const int *tgt;          // per tile: [256][8] target index or -1
   int64_t tile_off[kMaxDepth + 2];  // tiles of target level l start at tile_off[l]
+  int64_t ntiles;
+  int qmajor;              // block order: 0 tile-major (the row blocks of a tile are
+                           // consecutive), 1 row-block-major (a pair of row blocks
+                           // runs over every tile before the next pair)
   int nlev;                // target levels 0..nlev-1 (tiles only at l >= 2)
   float *out;              // per target Ng^3: deviations from node 0 (node 0 holds 0)
   float *outc;             // per target: the value at node 0
@@ -124,6 +142,7 @@ struct Params {
   int stall;               // test hook: the leader's MMA thread first waits on a barrier nothing arrives at
   double mean[kMaxDepth + 1][8];  // m_o per target level: mean of row (o, 0) over the zone
 };
+// (NG in the comments above: the gridlet order of the launch)
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -276,21 +295,28 @@ __device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
 __host__ __device__ __forceinline__ int sw64(int r, int k) { return (r >> 3) * 512 + (r & 7) * 64 + ((k ^ ((r >> 1) & 3)) << 4); }
 
 // ---------------------------------------------------------------------------
-// Entry (row r of quarter q, K-chunk c, source node jj of the chunk's plane)
-// of W_l: -g(h |d|) for the child's node, minus the same for node 0 (rows of
-// nodes >= 1) or minus the row mean m_o (node 0); zero in the near zone.
+// Entry (row r of row block q, K-chunk c, node jj of the chunk) of W_l:
+// -g(h |d|) for the child's node, minus the same for node 0 (rows of nodes
+// >= 1) or minus the row mean m_o (node 0); zero in the near zone and in the
+// padding (rows beyond the 8 children, nodes beyond a gridlet's Ng^3).
+template <int NG>
 __device__ __forceinline__ double w_entry(int q, int r, int c, int jj, const double *__restrict__ gl,
                                           const double *__restrict__ mean) {
-  const int o = 2 * q + (r >> 6), node = r & 63;
+  using C = Cfg<NG>;
+  const int R = q * kRows + r;
+  if (R >= C::kRowsReal) return 0.0;
+  const int o = R / C::kM3, node = R - o * C::kM3;
   const int px = 2 + (o & 1), py = 2 + ((o >> 1) & 1), pz = 2 + (o >> 2);  // child in the 6^3 block
-  const int s = c >> 2, zq = c & 3;
+  const int s = c / C::kCPS, jn = kKC * (c - s * C::kCPS) + jj;           // source slot, node in its gridlet
+  if (jn >= C::kM3) return 0.0;
   const int sx = s % 6, sy = (s / 6) % 6, sz = s / 36;
   if (max(abs(sx - px), max(abs(sy - py), abs(sz - pz))) <= 1) return 0.0;
-  const int bx = 4 * sx + (jj & 3), by = 4 * sy + (jj >> 2), bz = 4 * sz + zq;  // source node, grid units
-  const int dx = 4 * px + (node & 3) - bx, dy = 4 * py + ((node >> 2) & 3) - by, dz = 4 * pz + (node >> 4) - bz;
+  const int bx = NG * sx + jn % NG, by = NG * sy + (jn / NG) % NG, bz = NG * sz + jn / (NG * NG);  // grid units
+  const int nx = node % NG, ny = (node / NG) % NG, nz = node / (NG * NG);
+  const int dx = NG * px + nx - bx, dy = NG * py + ny - by, dz = NG * pz + nz - bz;
   double w = -gl[dx * dx + dy * dy + dz * dz];  // -g(h |d|), the level's lattice table
   if (node != 0) {
-    const int ex = 4 * px - bx, ey = 4 * py - by, ez = 4 * pz - bz;
+    const int ex = NG * px - bx, ey = NG * py - by, ez = NG * pz - bz;
     w += gl[ex * ex + ey * ey + ez * ez];
   } else {
     w -= mean[o];
@@ -298,38 +324,41 @@ __device__ __forceinline__ double w_entry(int q, int r, int c, int jj, const dou
   return w;
 }
 
-// Largest |entry| of each of the 512 rows (as float bits, nonnegative floats
-// order like their bits). One thread per (q, c, row).
+// Largest |entry| of each row (as float bits, nonnegative floats order like
+// their bits). One thread per (q, c, row).
+template <int NG>
 __global__ void k_w_rowmax(const double *__restrict__ gl, const double *__restrict__ mean, int *__restrict__ rowmax) {
+  using C = Cfg<NG>;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)kQuarters * kChunks * kRows) return;
-  const int r = (int)(i % kRows), c = (int)((i / kRows) % kChunks), q = (int)(i / ((int64_t)kRows * kChunks));
+  if (i >= (int64_t)C::kQuarters * C::kChunks * kRows) return;
+  const int r = (int)(i % kRows), c = (int)((i / kRows) % C::kChunks), q = (int)(i / ((int64_t)kRows * C::kChunks));
   double m = 0.0;
-  for (int jj = 0; jj < kKC; ++jj) m = fmax(m, fabs(w_entry(q, r, c, jj, gl, mean)));
-  atomicMax(rowmax + q * kRows + r, __float_as_int((float)m));
+  for (int jj = 0; jj < kKC; ++jj) m = fmax(m, fabs(w_entry<NG>(q, r, c, jj, gl, mean)));
+  if (m > 0.0) atomicMax(rowmax + q * kRows + r, __float_as_int((float)m));
 }
 
-// W_l in the order the kernel streams it: for each quarter q (children 2q,
-// 2q+1) and K-chunk c (slot c / 4, z plane c % 4 of its gridlet) an 8 KB tile
-// of 128 rows x (16 hi, 16 lo) FP16 values of the row-scaled entries, swizzled
-// as the MMA reads it. One thread per (q, c, row); the c = 0 threads also
-// store the row exponents.
+// W_l in the order the kernel streams it: for each row block q and K-chunk c
+// an 8 KB tile of 128 rows x (16 hi, 16 lo) FP16 values of the row-scaled
+// entries, swizzled as the MMA reads it. One thread per (q, c, row); the c = 0
+// threads also store the row exponents.
+template <int NG>
 __global__ void k_w_table(const double *__restrict__ gl, const double *__restrict__ mean, const int *__restrict__ rowmax,
                           unsigned char *__restrict__ out, int *__restrict__ w_exp) {
+  using C = Cfg<NG>;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)kQuarters * kChunks * kRows) return;
-  const int r = (int)(i % kRows), c = (int)((i / kRows) % kChunks), q = (int)(i / ((int64_t)kRows * kChunks));
+  if (i >= (int64_t)C::kQuarters * C::kChunks * kRows) return;
+  const int r = (int)(i % kRows), c = (int)((i / kRows) % C::kChunks), q = (int)(i / ((int64_t)kRows * C::kChunks));
   const int e = scale_exp(__int_as_float(rowmax[q * kRows + r]));
   if (c == 0) w_exp[q * kRows + r] = e;
   const double sc = ldexp(1.0, e);
   uint32_t hw[8], lw[8];
   for (int jj = 0; jj < kKC; jj += 2) {
-    const double a = w_entry(q, r, c, jj, gl, mean) * sc, b = w_entry(q, r, c, jj + 1, gl, mean) * sc;
+    const double a = w_entry<NG>(q, r, c, jj, gl, mean) * sc, b = w_entry<NG>(q, r, c, jj + 1, gl, mean) * sc;
     const __half ah = __double2half(a), bh = __double2half(b);
     hw[jj / 2] = pack_h2(ah, bh);
     lw[jj / 2] = pack_h2(__double2half(a - (double)__half2float(ah)), __double2half(b - (double)__half2float(bh)));
   }
-  unsigned char *tile = out + ((int64_t)q * kChunks + c) * kABytes;
+  unsigned char *tile = out + ((int64_t)q * C::kChunks + c) * kABytes;
   *reinterpret_cast<uint4 *>(tile + sw64(r, 0)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
   *reinterpret_cast<uint4 *>(tile + sw64(r, 1)) = make_uint4(hw[4], hw[5], hw[6], hw[7]);
   *reinterpret_cast<uint4 *>(tile + sw64(r, 2)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -400,8 +429,10 @@ __device__ __forceinline__ int row_scale_slot(const RowLevels &rl, const uint64_
 
 // One thread per row: atomic max of its largest |value| into its (problem,
 // level) slot, aggregated over the lanes that share the slot.
+template <int NG>
 __global__ void k_level_amax(int64_t nrow, const float *__restrict__ grid, const uint64_t *__restrict__ box_key,
                              RowLevels rl, int *__restrict__ amax) {
+  constexpr int kM3 = Cfg<NG>::kM3;
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = row < nrow;
   unsigned m = 0u;
@@ -423,24 +454,33 @@ __global__ void k_level_amax(int64_t nrow, const float *__restrict__ grid, const
 }
 
 // Effective masses of every row as FP16 pairs at the row's (problem, level)
-// scale, in the order the gather copies them: per z plane 16 hi then 16 lo
-// values (64 bytes); also the row's scale exponent (kNoExp without mass) and
-// total mass. 4 lanes per row, one z plane each.
+// scale, in the order the gather copies them: per K-chunk (16 nodes) 16 hi
+// then 16 lo values (64 bytes), nodes beyond Ng^3 zero; also the row's scale
+// exponent (kNoExp without mass) and total mass. kL lanes per row (a power of
+// two >= the chunks per row), one K-chunk each.
+template <int NG>
 __global__ void k_split(int64_t nrow, const float *__restrict__ grid, const uint64_t *__restrict__ box_key,
                         RowLevels rl, const int *__restrict__ amax, unsigned char *__restrict__ hl,
                         int *__restrict__ box_exp, float *__restrict__ box_mass) {
+  using C = Cfg<NG>;
+  constexpr int kL = C::kCPS <= 4 ? 4 : (C::kCPS <= 8 ? 8 : (C::kCPS <= 16 ? 16 : 32));
+  static_assert(C::kCPS <= kL && C::kM3 % 4 == 0, "lanes per row");
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t row = i >> 2;
-  const int zq = (int)(i & 3);
-  const bool live = row < nrow;
+  const int64_t row = i / kL;
+  const int zq = (int)(i % kL);
+  const bool live = row < nrow && zq < C::kCPS;
   float v[kKC];
   float m = 0.f, sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < kKC; ++k) v[k] = 0.f;
   if (live) {
-    const float4 *g = reinterpret_cast<const float4 *>(grid + row * kM3 + zq * kKC);
+    const float4 *g = reinterpret_cast<const float4 *>(grid + row * C::kM3 + zq * kKC);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const float4 a = g[k];
-      v[4 * k] = a.x; v[4 * k + 1] = a.y; v[4 * k + 2] = a.z; v[4 * k + 3] = a.w;
+      if (zq * kKC + 4 * k < C::kM3) {
+        const float4 a = g[k];
+        v[4 * k] = a.x; v[4 * k + 1] = a.y; v[4 * k + 2] = a.z; v[4 * k + 3] = a.w;
+      }
     }
 #pragma unroll
     for (int k = 0; k < kKC; ++k) {
@@ -448,11 +488,11 @@ __global__ void k_split(int64_t nrow, const float *__restrict__ grid, const uint
       sum += v[k];
     }
   }
-  // the row's four planes are four consecutive lanes
-  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
-  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-  sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-  sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+  // the row's chunks are kL consecutive lanes
+#pragma unroll
+  for (int o = 1; o < kL; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+#pragma unroll
+  for (int o = 1; o < kL; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   if (!live) return;
   const int e = scale_exp(__int_as_float(amax[row_scale_slot(rl, box_key, row)]));
   const float sc = pow2f(e);
@@ -464,7 +504,7 @@ __global__ void k_split(int64_t nrow, const float *__restrict__ grid, const uint
     hw[k / 2] = pack_h2(ah, bh);
     lw[k / 2] = pack_h2(__float2half_rn(a - __half2float(ah)), __float2half_rn(b - __half2float(bh)));
   }
-  uint4 *dst = reinterpret_cast<uint4 *>(hl + (row * 4 + zq) * kRowBytes);
+  uint4 *dst = reinterpret_cast<uint4 *>(hl + (row * C::kCPS + zq) * kRowBytes);
   dst[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
   dst[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
   dst[2] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -546,7 +586,9 @@ __global__ void k_col_exp(int64_t ntiles, const int *__restrict__ rows, const in
   }
 }
 
+template <int NG>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ Params pr) {
+  using C = Cfg<NG>;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   // full: this CTA's stage landed; pfull (leader): the peer's stage landed;
@@ -558,8 +600,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long lim = pr.wait_limit;
   const uint32_t rank = cluster_rank();  // 0: leader (issues the MMAs), 1: peer
-  const int64_t tile = blockIdx.x / kQuarters;
-  const int q = (int)(blockIdx.x % kQuarters);  // this CTA's 128 rows of W: quarter q; rank = q & 1
+  // this CTA's tile and row block q (rows 128 q ... of W); the two CTAs of a
+  // cluster take the row blocks 2k and 2k + 1 of one tile (rank = q & 1)
+  int64_t tile;
+  int q;
+  if (pr.qmajor) {
+    const int64_t cid = blockIdx.x >> 1;
+    tile = cid % pr.ntiles;
+    q = 2 * (int)(cid / pr.ntiles) + (int)(blockIdx.x & 1);
+  } else {
+    tile = blockIdx.x / C::kQuarters;
+    q = (int)(blockIdx.x % C::kQuarters);
+  }
   int lev = 2;
   while (lev + 1 < pr.nlev && pr.tile_off[lev + 1] <= tile) ++lev;
 
@@ -592,11 +644,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
   if (warp < kProdWarp0) {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsCtl));
     if (warp == 0) {
-      // W tiles: the 4 K-chunks of a slot are one contiguous 32 KB block
+      // W tiles: the 4 K-chunks of a stage are one contiguous 32 KB block
       if (lane == 0) {
-        const unsigned char *src = pr.w + (int64_t)(lev - 2) * kLevelBytes + (int64_t)q * kChunks * kABytes;
+        const unsigned char *src = pr.w + (int64_t)(lev - 2) * C::kLevelBytes + (int64_t)q * C::kChunks * kABytes;
         bool ok = true;
-        for (int u = 0; u < kSlotUses; ++u) {
+        for (int u = 0; u < C::kSlotUses; ++u) {
           const int st = u % kStages;
           if (!bar_wait(&empty[st], ((u / kStages) & 1) ^ 1, lim)) {
             failed = 1;
@@ -608,7 +660,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
         }
         // the releases of the last stages are the leader's final arrivals on
         // this CTA's barriers: wait for them before the CTA may leave
-        for (int u = kSlotUses; ok && u < kSlotUses + kStages; ++u)
+        for (int u = C::kSlotUses; ok && u < C::kSlotUses + kStages; ++u)
           if (!bar_wait(&empty[u % kStages], ((u / kStages) & 1) ^ 1, lim)) {
             failed = 1;
             ok = false;
@@ -619,7 +671,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
         // test hook: a wait that runs out; the CTAs give up and report it
         const bool stalled = pr.stall && !bar_wait(&never, 0, lim);
         if (stalled) failed = 1;
-        for (int u = 0; !stalled && u < kSlotUses; ++u) {
+        for (int u = 0; !stalled && u < C::kSlotUses; ++u) {
           const int st = u % kStages;
           const int c0 = u * kStageChunks;  // first K-chunk of the stage
           const int b = c0 / kBlockChunks, x = b & 1;
@@ -658,7 +710,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
       // peer: relay each landed stage to the leader (warp 2 the even stage
       // uses, warp 3 the odd ones, so each has two stages' time per arrival)
       if (lane == 0) {
-        for (int u = warp - 2; u < kSlotUses; u += 2) {
+        for (int u = warp - 2; u < C::kSlotUses; u += 2) {
           const int st = u % kStages;
           if (!bar_wait(&full[st], (u / kStages) & 1, lim)) {
             failed = 1;
@@ -671,58 +723,73 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
     }
   } else if (warp < kEpiWarp0) {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsGather));
-    // Gather warp g fills the B tile of K-chunk 4 s + g (z plane g of slot
-    // s) in the stage of slot s with this CTA's 128 parents (128 rank ...):
-    // 64 bytes each, 4 lanes per parent (one 16-byte piece each), parents
-    // 8 m + lane / 4 for m = 0..15. Each thread's copies arrive on the
-    // stage's full barrier when they land (cp.async.mbarrier.arrive.noinc);
-    // the thread that consumes the stage (the leader's MMA thread, the
-    // peer's relay) makes them visible to the tensor core's proxy with one
-    // fence per stage, much cheaper there than a fence per gathering warp
-    // after its copies. Row indices of the next slot are loaded while the
-    // current one is copied.
+    // Gather warp g fills the B tile of K-chunk 4 u + g of every stage use u
+    // (node chunk j of source slot s: nodes 16 j ... of the slot's gridlet)
+    // with this CTA's 128 parents (128 rank ...): 64 bytes each, 4 lanes per
+    // parent (one 16-byte piece each), parents 8 m + lane / 4 for m = 0..15.
+    // Each thread's copies arrive on the stage's full barrier when they land
+    // (cp.async.mbarrier.arrive.noinc); the thread that consumes the stage
+    // (the leader's MMA thread, the peer's relay) makes them visible to the
+    // tensor core's proxy with one fence per stage, much cheaper there than a
+    // fence per gathering warp after its copies. When the warp's next chunk
+    // lies in the next slot, that slot's row indices are loaded while the
+    // current chunk is copied.
     const int g = warp - kProdWarp0, sub = lane & 3, grp = lane >> 2;
     const int *rp = pr.rows + tile * kSlots * kTileN + (int)rank * kHalfN + grp;
     // sw64 position of parent 8 m + grp, piece sub: 512 m + this lane's offset
     const uint32_t lane_off = (uint32_t)(grp * 64 + ((sub ^ ((grp >> 1) & 3)) << 4));
     const uint32_t bsh = su32(sm + kStageABytes + g * kBBytes) + lane_off;
-    const unsigned char *hsub = pr.hl + 16 * sub + g * kRowBytes;
+    const unsigned char *hsub = pr.hl + 16 * sub;
     constexpr int kPer = kHalfN / 8;
     int rows[kPer], next[kPer];
+    {
+      const int s0 = g / C::kCPS;
 #pragma unroll
-    for (int m = 0; m < kPer; ++m) rows[m] = __ldg(rp + 8 * m);
-    for (int s = 0; s < kSlots; ++s) {
-      const int st = s % kStages;
+      for (int m = 0; m < kPer; ++m) rows[m] = __ldg(rp + s0 * kTileN + 8 * m);
+    }
+    for (int u = 0; u < C::kSlotUses; ++u) {
+      const int st = u % kStages;
+      const int c = u * kStageChunks + g, s = c / C::kCPS, j = c - s * C::kCPS;
+      const int sn = (c + kStageChunks) / C::kCPS;  // slot of this warp's next chunk (s or s + 1)
+      // at Ng = 4 a stage is one slot: the next chunk is always in the next slot
+      constexpr bool kSlotPerStage = C::kCPS == kStageChunks;
+      if (kSlotPerStage || sn != s) {
 #pragma unroll
-      for (int m = 0; m < kPer; ++m) next[m] = s + 1 < kSlots ? __ldg(rp + (s + 1) * kTileN + 8 * m) : -1;
+        for (int m = 0; m < kPer; ++m) next[m] = sn < kSlots ? __ldg(rp + sn * kTileN + 8 * m) : -1;
+      }
       int ok = 1;
-      if (lane == 0) ok = bar_wait(&empty[st], ((s / kStages) & 1) ^ 1, lim);
+      if (lane == 0) ok = bar_wait(&empty[st], ((u / kStages) & 1) ^ 1, lim);
       if (!__shfl_sync(0xffffffffu, ok, 0)) {
         failed = 1;
         break;
       }
       const uint32_t dst = bsh + st * kStageBytes;
+      const unsigned char *hj = hsub + j * kRowBytes;
 #pragma unroll
       for (int m = 0; m < kPer; ++m) {
         const int row = rows[m];
-        cp16(dst + m * 512, hsub + (int64_t)(row >= 0 ? row : 0) * 4 * kRowBytes, row >= 0 ? 16u : 0u);
+        cp16(dst + m * 512, hj + (int64_t)(row >= 0 ? row : 0) * C::kCPS * kRowBytes, row >= 0 ? 16u : 0u);
       }
       asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(&full[st])) : "memory");
+      if (kSlotPerStage || sn != s) {
 #pragma unroll
-      for (int m = 0; m < kPer; ++m) rows[m] = next[m];
+        for (int m = 0; m < kPer; ++m) rows[m] = next[m];
+      }
     }
   } else {
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsHigh));
     // drain: total += block accumulator (registers); after the last block
     // write the values. Warp w reads TMEM lanes 32 (w mod 4) ...
     const int lq = warp & 3, half = (warp - kEpiWarp0) >> 2;
-    const int r = lq * 32 + lane;                 // row of this thread
-    const int o = 2 * q + (r >> 6), node = r & 63;
+    const int r = lq * 32 + lane;                 // row of this thread in the CTA's block
+    const int R = q * kRows + r;                  // row of W: child o, node
+    const bool real_row = C::kRowsReal % kRows == 0 || R < C::kRowsReal;  // no padding rows at Ng = 4
+    const int o = real_row ? R / C::kM3 : 0, node = R - o * C::kM3;
     const uint32_t lane_off = (uint32_t)(lq * 32) << 16;
-    const int e_row = __ldg(pr.w_exp + (lev - 2) * (kQuarters * kRows) + q * kRows + r);
+    const int e_row = __ldg(pr.w_exp + (lev - 2) * (C::kQuarters * kRows) + q * kRows + r);
     float tot[128];
     bool ok = true;
-    for (int b = 0; b < kBlocks; ++b) {
+    for (int b = 0; b < C::kBlocks; ++b) {
       const int x = b & 1;
       if (!__all_sync(0xffffffffu, bar_wait_cl(&accf[x], (b >> 1) & 1, lim))) {
         failed = 1;
@@ -750,7 +817,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
         else bar_arrive_remote(&acce[x], 0);
       }
     }
-    if (ok) {
+    if (ok && real_row) {
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
         const int col = half * 128 + cc * 32;
@@ -763,9 +830,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
             const float v = (tot[cc * 32 + j] * pow2f(-e_row)) * pow2f(-__ldg(ce + j));
             if (node == 0) {
               pr.outc[t_idx] = (float)((double)v + pr.mean[lev][o] * (double)__ldg(pr.zone_mass + (tile * kTileN + col + j) * 8 + o));
-              pr.out[(int64_t)t_idx * kM3] = 0.f;
+              pr.out[(int64_t)t_idx * C::kM3] = 0.f;
             } else {
-              pr.out[(int64_t)t_idx * kM3 + node] = v;
+              pr.out[(int64_t)t_idx * C::kM3 + node] = v;
             }
           }
         }
@@ -785,19 +852,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
 }  // namespace tc
 
 bool use_tc_m2l(const hpm_plan_s *pl) {
-  return pl->ng == 4 &&
+  return (pl->ng == 4 || pl->ng == 6) &&
          !(pl->opts.flags & (HPM_FLAG_GENERIC_M2L | HPM_FLAG_XTRANSFORM_M2L | HPM_FLAG_FFT_M2L));
 }
 
-hpm_status tc_precompute(hpm_plan_s *pl, cudaStream_t st) {
-  if (!use_tc_m2l(pl)) return HPM_OK;
+namespace {
+
+template <int NG>
+hpm_status tc_precompute_ng(hpm_plan_s *pl, cudaStream_t st) {
+  using C = tc::Cfg<NG>;
   const int D = pl->max_depth;
-  if (D < 2) return HPM_OK;
-  HPM_TRY(pl->tc_w.ensure((size_t)tc::kLevelBytes * (D - 1), st));
-  HPM_TRY(pl->tc_wexp.ensure(sizeof(int) * tc::kQuarters * tc::kRows * (D - 1), st));
-  HPM_CUDA(cudaMemsetAsync(pl->tc_wexp.p, 0, sizeof(int) * tc::kQuarters * tc::kRows * (D - 1), st));
+  HPM_TRY(pl->tc_w.ensure((size_t)C::kLevelBytes * (D - 1), st));
+  HPM_TRY(pl->tc_wexp.ensure(sizeof(int) * C::kQuarters * tc::kRows * (D - 1), st));
+  HPM_CUDA(cudaMemsetAsync(pl->tc_wexp.p, 0, sizeof(int) * C::kQuarters * tc::kRows * (D - 1), st));
   HPM_TRY(pl->tc_mean.ensure(sizeof(double) * 8 * (D + 1), st));
-  // m_o: mean of -g(h |y_{o,0} - y_{s,j}|) over the zone's 189 slots x 64 nodes
+  // m_o: mean of -g(h |y_{o,0} - y_{s,j}|) over the zone's 189 slots x Ng^3 nodes
   std::vector<double> mean(8 * (D + 1), 0.0);
   for (int l = 2; l <= D; ++l) {
     const double *gl = pl->glat_host.data() + pl->glat_stride * l;
@@ -808,9 +877,9 @@ hpm_status tc_precompute(hpm_plan_s *pl, cudaStream_t st) {
       for (int s = 0; s < tc::kSlots; ++s) {
         const int sx = s % 6, sy = (s / 6) % 6, sz = s / 36;
         if (std::max(std::abs(sx - px), std::max(std::abs(sy - py), std::abs(sz - pz))) <= 1) continue;
-        for (int j = 0; j < tc::kM3; ++j) {
-          const int dx = 4 * px - (4 * sx + (j & 3)), dy = 4 * py - (4 * sy + ((j >> 2) & 3)),
-                    dz = 4 * pz - (4 * sz + (j >> 4));
+        for (int j = 0; j < C::kM3; ++j) {
+          const int dx = NG * px - (NG * sx + j % NG), dy = NG * py - (NG * sy + (j / NG) % NG),
+                    dz = NG * pz - (NG * sz + j / (NG * NG));
           sum += -gl[dx * dx + dy * dy + dz * dz];
           ++cnt;
         }
@@ -820,23 +889,110 @@ hpm_status tc_precompute(hpm_plan_s *pl, cudaStream_t st) {
   }
   pl->tc_mean_host = mean;
   HPM_CUDA(cudaMemcpyAsync(pl->tc_mean.p, mean.data(), sizeof(double) * mean.size(), cudaMemcpyHostToDevice, st));
-  const int64_t nthr = (int64_t)tc::kQuarters * tc::kChunks * tc::kRows;
+  const int64_t nthr = (int64_t)C::kQuarters * C::kChunks * tc::kRows;
   const unsigned nblk = (unsigned)((nthr + 255) / 256);
   int *rowmax = nullptr;
-  HPM_TRY(lib_malloc_async((void **)&rowmax, sizeof(int) * tc::kQuarters * tc::kRows, st));
+  HPM_TRY(lib_malloc_async((void **)&rowmax, sizeof(int) * C::kQuarters * tc::kRows, st));
   for (int l = 2; l <= D; ++l) {
     const double *gl = pl->glat.as<double>() + pl->glat_stride * l;
     const double *mean_l = pl->tc_mean.as<double>() + 8 * l;
-    int *wexp = pl->tc_wexp.as<int>() + tc::kQuarters * tc::kRows * (l - 2);
-    HPM_CUDA(cudaMemsetAsync(rowmax, 0, sizeof(int) * tc::kQuarters * tc::kRows, st));
-    tc::k_w_rowmax<<<nblk, 256, 0, st>>>(gl, mean_l, rowmax);
+    int *wexp = pl->tc_wexp.as<int>() + C::kQuarters * tc::kRows * (l - 2);
+    HPM_CUDA(cudaMemsetAsync(rowmax, 0, sizeof(int) * C::kQuarters * tc::kRows, st));
+    tc::k_w_rowmax<NG><<<nblk, 256, 0, st>>>(gl, mean_l, rowmax);
     HPM_LAUNCHED((int64_t *)nullptr);
-    tc::k_w_table<<<nblk, 256, 0, st>>>(gl, mean_l, rowmax,
-                                        pl->tc_w.as<unsigned char>() + tc::kLevelBytes * (l - 2), wexp);
+    tc::k_w_table<NG><<<nblk, 256, 0, st>>>(gl, mean_l, rowmax,
+                                            pl->tc_w.as<unsigned char>() + C::kLevelBytes * (l - 2), wexp);
     HPM_LAUNCHED((int64_t *)nullptr);
   }
   HPM_CUDA(cudaFreeAsync(rowmax, st));
+  // the mean vector is host memory the copy above reads
+  HPM_CUDA(cudaStreamSynchronize(st));
   return HPM_OK;
+}
+
+template <int NG>
+hpm_status launch_m2l_tc_ng(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
+  using C = tc::Cfg<NG>;
+  const int64_t off2 = pl->lvl_off[2], nrow = pl->nbox - off2;
+  if (nrow <= 0) return HPM_OK;
+  HPM_TRY(pl->s.grid_hl.ensure((size_t)nrow * C::kCPS * tc::kRowBytes, st));
+  HPM_TRY(pl->s.box_exp.ensure(sizeof(int) * nrow, st));
+  HPM_TRY(pl->s.box_mass.ensure(sizeof(float) * nrow, st));
+  HPM_TRY(pl->s.col_exp.ensure(sizeof(int) * pl->tc_ntiles * tc::kTileN, st));
+  HPM_TRY(pl->s.zone_mass.ensure(sizeof(float) * pl->tc_ntiles * tc::kTileN * 8, st));
+  tc::RowLevels rl{};
+  rl.nlev = pl->max_depth + 1;
+  for (int l = 0; l <= pl->max_depth + 1; ++l) rl.off[l] = pl->lvl_off[l];
+  rl.off2 = off2;
+  const size_t nslot = (size_t)(pl->nprob > 0 ? pl->nprob : 1) * rl.nlev;
+  HPM_TRY(pl->s.level_amax.ensure(sizeof(int) * nslot, st));
+  HPM_CUDA(cudaMemsetAsync(pl->s.level_amax.p, 0, sizeof(int) * nslot, st));
+  tc::k_level_amax<NG><<<(unsigned)((nrow + 255) / 256), 256, 0, st>>>(
+      nrow, pl->s.grid.as<float>(), pl->t.box_key.as<uint64_t>(), rl, pl->s.level_amax.as<int>());
+  HPM_LAUNCHED(launches);
+  constexpr int kL = C::kCPS <= 4 ? 4 : (C::kCPS <= 8 ? 8 : (C::kCPS <= 16 ? 16 : 32));
+  tc::k_split<NG><<<(unsigned)((kL * nrow + 255) / 256), 256, 0, st>>>(
+      nrow, pl->s.grid.as<float>(), pl->t.box_key.as<uint64_t>(), rl, pl->s.level_amax.as<int>(),
+      pl->s.grid_hl.as<unsigned char>(), pl->s.box_exp.as<int>(), pl->s.box_mass.as<float>());
+  HPM_LAUNCHED(launches);
+  tc::k_col_exp<<<(unsigned)((pl->tc_ntiles * tc::kTileN * 32 + 255) / 256), 256, 0, st>>>(
+      pl->tc_ntiles, pl->t.tc_rows.as<int>(), pl->s.box_exp.as<int>(), pl->s.box_mass.as<float>(),
+      pl->s.col_exp.as<int>(), pl->s.zone_mass.as<float>());
+  HPM_LAUNCHED(launches);
+  tc::Params p{};
+  p.w = pl->tc_w.as<unsigned char>();
+  p.w_exp = pl->tc_wexp.as<int>();
+  p.col_exp = pl->s.col_exp.as<int>();
+  p.hl = pl->s.grid_hl.as<unsigned char>();
+  p.zone_mass = pl->s.zone_mass.as<float>();
+  p.rows = pl->t.tc_rows.as<int>();
+  p.tgt = pl->t.tc_tgt.as<int>();
+  for (int l = 0; l <= kMaxDepth + 1; ++l) p.tile_off[l] = l < (int)pl->tc_tile_off.size() ? pl->tc_tile_off[l] : 0;
+  p.ntiles = pl->tc_ntiles;
+  p.qmajor = m2l_block_order(pl) == 2 ? 1 : 0;
+  p.nlev = pl->max_depth + 1;
+  p.out = pl->s.m2l_raw.as<float>();
+  p.outc = pl->s.m2lc.as<float>();
+  p.err = pl->t.err.as<int>() + 1;  // the solves' error word
+  p.wait_limit = pl->test_wait_limit > 0 ? pl->test_wait_limit : (1ll << 32);
+  p.stall = pl->test_stall;
+  for (int l = 0; l <= kMaxDepth && 8 * l + 7 < (int)pl->tc_mean_host.size(); ++l)
+    for (int o = 0; o < 8; ++o) p.mean[l][o] = pl->tc_mean_host[8 * l + o];
+  static DeviceCache attr_cache;
+  int attr_ok = 0;
+  HPM_TRY(device_cached(attr_cache, [](int *v) -> hpm_status {
+    HPM_CUDA(cudaFuncSetAttribute(tc::k_m2l_tc<NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem));
+    // The drain warps raise their register count to kRegsHigh with registers
+    // the other warpgroups give back; that only adds up if the kernel was
+    // compiled with kLaunchRegs per thread. Never launch it otherwise.
+    cudaFuncAttributes fa{};
+    HPM_CUDA(cudaFuncGetAttributes(&fa, tc::k_m2l_tc<NG>));
+    if (fa.numRegs != tc::kLaunchRegs)
+      fprintf(stderr, "hpm: k_m2l_tc<%d> compiled with %d registers per thread, expected %d\n", NG, fa.numRegs,
+              tc::kLaunchRegs);
+    *v = fa.numRegs == tc::kLaunchRegs ? 1 : 0;
+    return HPM_OK;
+  }, &attr_ok));
+  if (!attr_ok) return HPM_ERR_UNSUPPORTED;
+  const int64_t grid = pl->tc_ntiles * C::kQuarters;
+  if (pl->events_ready) cudaEventRecord(pl->ev[10], st);
+  tc::k_m2l_tc<NG><<<(unsigned)grid, tc::kThreads, tc::kSmem, st>>>(p);
+  HPM_LAUNCHED(launches);
+  if (pl->events_ready) cudaEventRecord(pl->ev[11], st);
+  pl->stats.m2l_parents = pl->npar;
+  return HPM_OK;
+}
+
+}  // namespace
+
+int m2l_block_order(const hpm_plan_s *pl) {
+  const int o = pl->tuning.m2l_block_order;
+  return o == 1 || o == 2 ? o : 1;  // tile-major unless tuned otherwise
+}
+
+hpm_status tc_precompute(hpm_plan_s *pl, cudaStream_t st) {
+  if (!use_tc_m2l(pl) || pl->max_depth < 2) return HPM_OK;
+  return pl->ng == 6 ? tc_precompute_ng<6>(pl, st) : tc_precompute_ng<4>(pl, st);
 }
 
 hpm_status tc_build_tiles(hpm_plan_s *pl, const std::vector<int64_t> &par_per_level, cudaStream_t st,
@@ -874,71 +1030,7 @@ hpm_status tc_build_tiles(hpm_plan_s *pl, const std::vector<int64_t> &par_per_le
 
 hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   if (!pl->tc_ntiles) return HPM_OK;
-  const int64_t off2 = pl->lvl_off[2], nrow = pl->nbox - off2;
-  if (nrow <= 0) return HPM_OK;
-  HPM_TRY(pl->s.grid_hl.ensure((size_t)nrow * 4 * tc::kRowBytes, st));
-  HPM_TRY(pl->s.box_exp.ensure(sizeof(int) * nrow, st));
-  HPM_TRY(pl->s.box_mass.ensure(sizeof(float) * nrow, st));
-  HPM_TRY(pl->s.col_exp.ensure(sizeof(int) * pl->tc_ntiles * tc::kTileN, st));
-  HPM_TRY(pl->s.zone_mass.ensure(sizeof(float) * pl->tc_ntiles * tc::kTileN * 8, st));
-  tc::RowLevels rl{};
-  rl.nlev = pl->max_depth + 1;
-  for (int l = 0; l <= pl->max_depth + 1; ++l) rl.off[l] = pl->lvl_off[l];
-  rl.off2 = off2;
-  const size_t nslot = (size_t)(pl->nprob > 0 ? pl->nprob : 1) * rl.nlev;
-  HPM_TRY(pl->s.level_amax.ensure(sizeof(int) * nslot, st));
-  HPM_CUDA(cudaMemsetAsync(pl->s.level_amax.p, 0, sizeof(int) * nslot, st));
-  tc::k_level_amax<<<(unsigned)((nrow + 255) / 256), 256, 0, st>>>(
-      nrow, pl->s.grid.as<float>(), pl->t.box_key.as<uint64_t>(), rl, pl->s.level_amax.as<int>());
-  HPM_LAUNCHED(launches);
-  tc::k_split<<<(unsigned)((4 * nrow + 255) / 256), 256, 0, st>>>(
-      nrow, pl->s.grid.as<float>(), pl->t.box_key.as<uint64_t>(), rl, pl->s.level_amax.as<int>(),
-      pl->s.grid_hl.as<unsigned char>(), pl->s.box_exp.as<int>(), pl->s.box_mass.as<float>());
-  HPM_LAUNCHED(launches);
-  tc::k_col_exp<<<(unsigned)((pl->tc_ntiles * tc::kTileN * 32 + 255) / 256), 256, 0, st>>>(
-      pl->tc_ntiles, pl->t.tc_rows.as<int>(), pl->s.box_exp.as<int>(), pl->s.box_mass.as<float>(),
-      pl->s.col_exp.as<int>(), pl->s.zone_mass.as<float>());
-  HPM_LAUNCHED(launches);
-  tc::Params p{};
-  p.w = pl->tc_w.as<unsigned char>();
-  p.w_exp = pl->tc_wexp.as<int>();
-  p.col_exp = pl->s.col_exp.as<int>();
-  p.hl = pl->s.grid_hl.as<unsigned char>();
-  p.zone_mass = pl->s.zone_mass.as<float>();
-  p.rows = pl->t.tc_rows.as<int>();
-  p.tgt = pl->t.tc_tgt.as<int>();
-  for (int l = 0; l <= kMaxDepth + 1; ++l) p.tile_off[l] = l < (int)pl->tc_tile_off.size() ? pl->tc_tile_off[l] : 0;
-  p.nlev = pl->max_depth + 1;
-  p.out = pl->s.m2l_raw.as<float>();
-  p.outc = pl->s.m2lc.as<float>();
-  p.err = pl->t.err.as<int>() + 1;  // the solves' error word
-  p.wait_limit = pl->test_wait_limit > 0 ? pl->test_wait_limit : (1ll << 32);
-  p.stall = pl->test_stall;
-  for (int l = 0; l <= kMaxDepth && 8 * l + 7 < (int)pl->tc_mean_host.size(); ++l)
-    for (int o = 0; o < 8; ++o) p.mean[l][o] = pl->tc_mean_host[8 * l + o];
-  static DeviceCache attr_cache;
-  int attr_ok = 0;
-  HPM_TRY(device_cached(attr_cache, [](int *v) -> hpm_status {
-    HPM_CUDA(cudaFuncSetAttribute(tc::k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem));
-    // The drain warps raise their register count to kRegsHigh with registers
-    // the other warpgroups give back; that only adds up if the kernel was
-    // compiled with kLaunchRegs per thread. Never launch it otherwise.
-    cudaFuncAttributes fa{};
-    HPM_CUDA(cudaFuncGetAttributes(&fa, tc::k_m2l_tc));
-    if (fa.numRegs != tc::kLaunchRegs)
-      fprintf(stderr, "hpm: k_m2l_tc compiled with %d registers per thread, expected %d\n", fa.numRegs,
-              tc::kLaunchRegs);
-    *v = fa.numRegs == tc::kLaunchRegs ? 1 : 0;
-    return HPM_OK;
-  }, &attr_ok));
-  if (!attr_ok) return HPM_ERR_UNSUPPORTED;
-  const int64_t grid = pl->tc_ntiles * tc::kQuarters;
-  if (pl->events_ready) cudaEventRecord(pl->ev[10], st);
-  tc::k_m2l_tc<<<(unsigned)grid, tc::kThreads, tc::kSmem, st>>>(p);
-  HPM_LAUNCHED(launches);
-  if (pl->events_ready) cudaEventRecord(pl->ev[11], st);
-  pl->stats.m2l_parents = pl->npar;
-  return HPM_OK;
+  return pl->ng == 6 ? launch_m2l_tc_ng<6>(pl, st, launches) : launch_m2l_tc_ng<4>(pl, st, launches);
 }
 
 }  // namespace hpm

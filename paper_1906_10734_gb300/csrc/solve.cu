@@ -347,8 +347,9 @@ __global__ void __launch_bounds__(kW * 32) k_m2m4(int64_t b, int64_t e, GridletT
   }
 }
 
-// Ng = 4 parent-to-child as k_l2l, one target per warp with the three axis
-// passes unrolled: loc_C = (Tx^T (x) Ty^T (x) Tz^T) loc_P + own values.
+// Ng = 4 parent-to-child (Sec. 2.4), one target per warp with the three axis
+// passes unrolled in FP32: loc_C = (Tx^T (x) Ty^T (x) Tz^T) loc_P + own
+// values, kept as (constant, deviations) as in k_l2l_df.
 template <int kW>
 __global__ void __launch_bounds__(kW * 32) k_l2l4(int64_t tb0, int64_t tb1, int level, GridletTables tab,
                                                          const int *__restrict__ tgt_box,
@@ -416,51 +417,108 @@ __global__ void __launch_bounds__(kW * 32) k_l2l4(int64_t tb0, int64_t tb1, int 
   if (lane == 0) locc[t] = cpar + (mean + m2lc[t]);
 }
 
-// Parent-to-child plus the target's own source-to-target values, with the
-// local kept as (constant, deviations): the interpolation reproduces
-// constants exactly (the Lagrange weights sum to one), so the constant is
-// carried separately and the FP32 deviations only hold the variation across
-// the cell.
-__global__ void __launch_bounds__(kGThreads) k_l2l(int64_t tb0, int64_t tb1, int level,
-                                                  GridletTables tab, const int *__restrict__ tgt_box,
-                                                  const int *__restrict__ box_tgt,
-                                                  const int *__restrict__ parent,
-                                                  const uint64_t *__restrict__ key,
-                                                  const float *__restrict__ raw,
-                                                  float *__restrict__ loc, float *__restrict__ locc,
-                                                  const float *__restrict__ m2lc) {
-  __shared__ float T[2][kMaxNg * kMaxNg];
-  __shared__ float bufA[kGWarps][512], bufB[kGWarps][512], res[kGWarps][512];
-  for (int i = threadIdx.x; i < 2 * kMaxNg * kMaxNg; i += blockDim.x)
-    T[i / (kMaxNg * kMaxNg)][i % (kMaxNg * kMaxNg)] = tab.t1[i / (kMaxNg * kMaxNg)][(i / kMaxNg) % kMaxNg][i % kMaxNg];
+// Double-float arithmetic (a value is hi + lo, |lo| <= ulp(hi) / 2) on the
+// FP32 pipe, for the parent-to-child pass of the orders other than 4: at
+// Ng >= 5 the interpolation from the parent's nodes to the child's amplifies
+// the FP32 rounding of plain products into the force beyond 1e-5, while FP64
+// arithmetic runs about 70 times slower than FP32 on this GPU.
+struct dfloat {
+  float h, l;
+};
+__device__ __forceinline__ dfloat df_quick_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+  const float s = a.h + b.h, bb = s - a.h;
+  const float e = (a.h - (s - bb)) + (b.h - bb);  // two-sum error of a.h + b.h
+  return df_quick_two_sum(s, e + (a.l + b.l));
+}
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);  // exact error of the product
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return df_quick_two_sum(p, e);
+}
+
+// One axis pass in double-float: dst[.., p_axis, ..] = sum_q T[q][p] src[.., q, ..]
+// (the transposed 1-D operator, parent-to-child), T = hi + lo.
+__device__ __forceinline__ void apply_axis_df(const float *__restrict__ th, const float *__restrict__ tl, int axis,
+                                              int ng, const dfloat *src, dfloat *dst) {
+  const int lane = threadIdx.x & 31, m3 = ng * ng * ng;
+  const int stride = axis == 0 ? 1 : (axis == 1 ? ng : ng * ng);
+  for (int p = lane; p < m3; p += 32) {
+    const int c = (p / stride) % ng;
+    const int base = p - c * stride;
+    dfloat s = {0.f, 0.f};
+    for (int q = 0; q < ng; ++q)
+      s = df_add(s, df_mul({th[q * kMaxNg + c], tl[q * kMaxNg + c]}, src[base + q * stride]));
+    dst[p] = s;
+  }
+  __syncwarp();
+}
+
+// Parent-to-child plus the target's own source-to-target values (Sec. 2.4),
+// for the orders other than 4, one target per warp. The local is kept as
+// (constant, deviations): the interpolation reproduces constants exactly (the
+// Lagrange weights sum to one), so the constant is carried separately and the
+// FP32 deviations only hold the variation across the cell. The interpolation,
+// the addition of the target's own values and the mean are evaluated in
+// double-float.
+constexpr int kDfWarps = 2;
+__global__ void __launch_bounds__(32 * kDfWarps) k_l2l_df(int64_t tb0, int64_t tb1, int level, GridletTables tab,
+                                                       const int *__restrict__ tgt_box,
+                                                       const int *__restrict__ box_tgt,
+                                                       const int *__restrict__ parent,
+                                                       const uint64_t *__restrict__ key,
+                                                       const float *__restrict__ raw, float *__restrict__ loc,
+                                                       float *__restrict__ locc, const float *__restrict__ m2lc) {
+  __shared__ float Th[2][kMaxNg * kMaxNg], Tl[2][kMaxNg * kMaxNg];
+  __shared__ dfloat bufA[kDfWarps][512], bufB[kDfWarps][512];
+  for (int i = threadIdx.x; i < 2 * kMaxNg * kMaxNg; i += blockDim.x) {
+    const int sgn = i / (kMaxNg * kMaxNg), pq = i % (kMaxNg * kMaxNg);
+    Th[sgn][pq] = tab.t1[sgn][pq / kMaxNg][pq % kMaxNg];
+    Tl[sgn][pq] = tab.t1lo[sgn][pq / kMaxNg][pq % kMaxNg];
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t t = tb0 + (int64_t)blockIdx.x * kGWarps + w;
+  const int64_t t = tb0 + (int64_t)blockIdx.x * kDfWarps + w;
   if (t >= tb1) return;
   const int ng = tab.ng, m3 = ng * ng * ng;
-  float *mine = loc + t * m3;
-  for (int p = lane; p < m3; p += 32) res[w][p] = raw[t * m3 + p];
+  dfloat *res = bufB[w];
   float cpar = 0.f;
   if (level >= 3) {
     const int box = tgt_box[t];
     const int tp = box_tgt[parent[box]];
     const int o = (int)(key[box] & 7u);
     const float *pl = loc + (int64_t)tp * m3;
-    for (int p = lane; p < m3; p += 32) bufA[w][p] = pl[p];
+    for (int p = lane; p < m3; p += 32) bufA[w][p] = {pl[p], 0.f};
     __syncwarp();
-    apply_axis(T[o & 1], true, 0, ng, bufA[w], bufB[w], false);
-    apply_axis(T[(o >> 1) & 1], true, 1, ng, bufB[w], bufA[w], false);
-    apply_axis(T[(o >> 2) & 1], true, 2, ng, bufA[w], res[w], true);
+    apply_axis_df(Th[o & 1], Tl[o & 1], 0, ng, bufA[w], bufB[w]);
+    apply_axis_df(Th[(o >> 1) & 1], Tl[(o >> 1) & 1], 1, ng, bufB[w], bufA[w]);
+    apply_axis_df(Th[(o >> 2) & 1], Tl[(o >> 2) & 1], 2, ng, bufA[w], bufB[w]);
+    for (int p = lane; p < m3; p += 32) res[p] = df_add(res[p], {raw[t * m3 + p], 0.f});
     cpar = locc[tp];
+  } else {
+    for (int p = lane; p < m3; p += 32) res[p] = {raw[t * m3 + p], 0.f};
   }
   __syncwarp();
-  float s = 0.f;
-  for (int p = lane; p < m3; p += 32) s += res[w][p];
+  dfloat s = {0.f, 0.f};
+  for (int p = lane; p < m3; p += 32) s = df_add(s, res[p]);
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  const float mean = s / (float)m3;
-  for (int p = lane; p < m3; p += 32) mine[p] = res[w][p] - mean;
-  if (lane == 0) locc[t] = cpar + (mean + m2lc[t]);
+  for (int off = 16; off > 0; off >>= 1)
+    s = df_add(s, {__shfl_xor_sync(0xffffffffu, s.h, off), __shfl_xor_sync(0xffffffffu, s.l, off)});
+  // mean = s / m3 in double-float: quotient, then the remainder's correction
+  const float qh = s.h / (float)m3;
+  const float rem = fmaf(-qh, (float)m3, s.h) + s.l;
+  const dfloat mean = df_quick_two_sum(qh, rem / (float)m3);
+  float *mine = loc + t * m3;
+  for (int p = lane; p < m3; p += 32) {
+    const dfloat d = df_add(res[p], {-mean.h, -mean.l});
+    mine[p] = d.h + d.l;
+  }
+  if (lane == 0) locc[t] = cpar + (mean.h + m2lc[t]);
 }
 
 // 1-D Lagrange weights and derivatives, FP32 (NG as for lagrange_d).
@@ -1139,10 +1197,10 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
           t.box_key.as<uint64_t>(), s.m2l_raw.as<float>(), s.loc.as<float>(), s.locc.as<float>(),
           s.m2lc.as<float>());
     } else
-      k_l2l<<<gwarp_blocks(e - b), kGThreads, 0, st>>>(b, e, l, pl->tab, t.tgt_box.as<int>(), t.box_tgt.as<int>(),
-                                                     t.box_parent.as<int>(), t.box_key.as<uint64_t>(),
-                                                     s.m2l_raw.as<float>(), s.loc.as<float>(), s.locc.as<float>(),
-                                                     s.m2lc.as<float>());
+      k_l2l_df<<<(unsigned)((e - b + kDfWarps - 1) / kDfWarps), 32 * kDfWarps, 0, st>>>(
+          b, e, l, pl->tab, t.tgt_box.as<int>(), t.box_tgt.as<int>(), t.box_parent.as<int>(),
+          t.box_key.as<uint64_t>(), s.m2l_raw.as<float>(), s.loc.as<float>(), s.locc.as<float>(),
+          s.m2lc.as<float>());
     HPM_LAUNCHED(&launches);
   }
   record(pl, 5, st);

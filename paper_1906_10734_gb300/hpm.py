@@ -122,7 +122,7 @@ class hpm_stats(ctypes.Structure):
 
 class hpm_tuning(ctypes.Structure):
     _fields_ = [("level_blocks_per_sm", ctypes.c_int), ("gridlet_warps", ctypes.c_int),
-                ("m2l_ctas_per_sm", ctypes.c_int)]
+                ("m2l_ctas_per_sm", ctypes.c_int), ("m2l_block_order", ctypes.c_int)]
 
 
 class hpm_alu_peaks(ctypes.Structure):
@@ -308,8 +308,8 @@ def hpm_get_stage(plan: int, stage: int, ng: int) -> np.ndarray:
     return np.concatenate([vals, const[:, None]], axis=1)
 
 
-def hpm_set_tuning(plan: int, level_blocks_per_sm=0, gridlet_warps=0, m2l_ctas_per_sm=0):
-    t = hpm_tuning(level_blocks_per_sm, gridlet_warps, m2l_ctas_per_sm)
+def hpm_set_tuning(plan: int, level_blocks_per_sm=0, gridlet_warps=0, m2l_ctas_per_sm=0, m2l_block_order=0):
+    t = hpm_tuning(level_blocks_per_sm, gridlet_warps, m2l_ctas_per_sm, m2l_block_order)
     _check("hpm_set_tuning", load().hpm_set_tuning(plan, ctypes.byref(t)))
 
 

@@ -77,3 +77,9 @@ def test_clock_summary_reports_reasons():
     assert out["sm_mhz"] == 2010 and out["sm_max_mhz"] == 2070 and out["samples"] == 3
     assert out["reasons"] == ["sw_power_cap"]
     assert not os.path.exists(s.path)
+
+
+def test_dense_work_per_parent_by_order():
+    assert bench.dense_flop_per_parent(4) == 3 * 2 * 512 * 216 * 64
+    # Ng = 6: 1728 rows padded to 14 blocks of 128, 216 nodes padded to 224 per slot
+    assert bench.dense_flop_per_parent(6) == 3 * 2 * 1792 * 216 * 224

@@ -14,14 +14,19 @@ from paper_1906_10734_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
-# Force bars per gridlet order. FP32 nodal potentials carry an absolute error of
-# about eps32 |Phi| and the gradient of the degree-(Ng-1) interpolant amplifies
-# nodal noise by a factor that grows fast with Ng. Rounding only the FP64
-# oracle's source-to-target values to FP32 already costs 3e-6 (Ng 4), 6e-6 (5),
-# 1.7e-5 (6) and 2.3e-4 (8) in relative RMS force on these inputs; the FP32 FFT
-# adds its own round-off on top. The bar is 1e-5 up to Ng = 5 and a few times
-# the rounding-only floor above it.
-TOL_BY_NG = {1: TOL, 2: TOL, 3: TOL, 4: TOL, 5: TOL, 6: 6e-5, 7: 4e-4, 8: 3e-3}
+# Force bars per gridlet order. The gradient of the degree-(Ng-1) interpolant
+# amplifies nodal noise by a factor that grows fast with Ng: rounding the FP64
+# oracle's full source-to-target values to FP32 costs 3e-6 (Ng 4), 6e-6 (5),
+# 1.7e-5 (6) and 2.3e-4 (8) in relative RMS force, rounding only their
+# deviations from the cell's mean 1e-7 (4) and 1e-6 (6). Ng = 4 and 6 run the
+# dense tensor-core product, whose rows are such deviations, and (Ng != 4) a
+# double-float parent-to-child pass: their bar is 1e-5 like every order up to
+# 5. Ng = 7 and 8 run the FFT-form kernels on full FP32 values: a few times
+# that rounding floor.
+TOL_BY_NG = {1: TOL, 2: TOL, 3: TOL, 4: TOL, 5: TOL, 6: TOL, 7: 4e-4, 8: 3e-3}
+# the x-transform kernel at Ng = 6 (HPM_FLAG_XTRANSFORM_M2L) evaluates full FP32
+# values: a few times the full-value rounding floor of 1.7e-5
+TOL_XTRANSFORM_NG6 = 6e-5
 
 torch = pytest.importorskip("torch")
 
@@ -92,6 +97,18 @@ def test_gridlet_orders_generic_kernel(hpm, ng):
     print(f"Ng={ng}: rel RMS acc {O.rel_rms(acc[sample], a_ref):.3e} phi {O.rel_rms(phi[sample], p_ref):.3e}")
     assert O.rel_rms(acc[sample], a_ref) < TOL_BY_NG[ng]
     assert O.rel_rms(phi[sample], p_ref) < TOL
+
+
+def test_xtransform_kernel_order_6(hpm):
+    """Ng = 6 on the x-transform FFT-form kernel (HPM_FLAG_XTRANSFORM_M2L): full FP32 values,
+    held to its own bar (the default Ng = 6 path is the dense product, held to 1e-5)."""
+    pos, mass = I.uniform_cube(2500, 36), I.equal_masses(2500)
+    phi, acc, _ = gpu_solve(hpm, pos, mass, 3, 6, 1e-3, 0, flags=hpm.HPM_FLAG_XTRANSFORM_M2L)
+    tr = O.Tree(pos, max_depth=3, leaf_max=0)
+    sample = np.arange(0, 2500, 5)
+    p_ref, a_ref = O.solve_direct(tr, mass, 6, 1e-3, sample)
+    print(f"Ng=6 x-transform: rel RMS acc {O.rel_rms(acc[sample], a_ref):.3e}")
+    assert O.rel_rms(acc[sample], a_ref) < TOL_XTRANSFORM_NG6 and O.rel_rms(phi[sample], p_ref) < TOL
 
 
 @pytest.mark.parametrize("depth", [0, 1, 2])

@@ -93,8 +93,18 @@ def test_stages_xtransform_kernel_at_order_4(hpm):
                  max_targets=400)
 
 
-@pytest.mark.parametrize("ng", [2, 3, 6])
+@pytest.mark.parametrize("ng", [2, 3, 5, 6])
 def test_stages_other_orders(hpm, ng):
     w = I.Workload(f"u{ng}", I.uniform_cube(2500, 30 + ng), I.equal_masses(2500), max_depth=3, leaf_max=0,
                    ng=ng, eps=1e-3)
-    check_stages(hpm, w, max_targets=200, var_tol=3e-5 if ng >= 6 else 1e-5)
+    check_stages(hpm, w, max_targets=200)
+
+
+def test_stages_order_6_adaptive(hpm):
+    check_stages(hpm, I.small_plummer(12000, 63, leaf_max=32, ng=6), max_targets=300)
+
+
+def test_stages_xtransform_kernel_at_order_6(hpm):
+    # full FP32 values on this kernel: the variation bar is a few times their rounding
+    w = I.Workload("u6x", I.uniform_cube(2500, 36), I.equal_masses(2500), max_depth=3, leaf_max=0, ng=6, eps=1e-3)
+    check_stages(hpm, w, flags=hpm.HPM_FLAG_XTRANSFORM_M2L, max_targets=200, var_tol=3e-5)

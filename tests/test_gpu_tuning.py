@@ -40,13 +40,16 @@ def test_shapes_keep_results_tensor_path(hpm):
     w = I.small_plummer(20000, 61, leaf_max=16)
     ref = solve_with(hpm, w, {})
     for shapes in (dict(level_blocks_per_sm=1), dict(level_blocks_per_sm=3), dict(level_blocks_per_sm=4),
-                   dict(gridlet_warps=2), dict(gridlet_warps=4)):
+                   dict(gridlet_warps=2), dict(gridlet_warps=4), dict(m2l_block_order=2)):
         assert_same(solve_with(hpm, w, shapes), ref)
+    # Ng = 6 runs on the dense tensor-core path too
+    ref6 = solve_with(hpm, w, {}, ng=6)
+    assert_same(solve_with(hpm, w, dict(m2l_block_order=2), ng=6), ref6)
 
 
 def test_shapes_keep_results_fft_paths(hpm):
     w = I.small_plummer(12000, 62, leaf_max=16)
-    for flags, ng in ((hpm.HPM_FLAG_FFT_M2L, 4), (0, 6)):
+    for flags, ng in ((hpm.HPM_FLAG_FFT_M2L, 4), (hpm.HPM_FLAG_XTRANSFORM_M2L, 6), (0, 5)):
         ref = solve_with(hpm, w, {}, flags=flags, ng=ng)
         assert_same(solve_with(hpm, w, dict(m2l_ctas_per_sm=1), flags=flags, ng=ng), ref)
 
@@ -61,6 +64,7 @@ def test_tune_picks_valid_shapes_and_keeps_results(hpm):
     t = hpm.hpm_tune(s.plan, p, m)
     assert t["level_blocks_per_sm"] in (1, 2, 3, 4)
     assert t["gridlet_warps"] in (2, 4, 8)
+    assert t["m2l_block_order"] in (1, 2)
     assert hpm.hpm_get_tuning(s.plan) == t
     phi, acc = s(p, m)
     torch.cuda.synchronize()
@@ -71,7 +75,7 @@ def test_tune_picks_valid_shapes_and_keeps_results(hpm):
 def test_bad_shapes_are_refused(hpm):
     s = hpm.Solver(3, 4, 0.0, 0)
     for shapes in (dict(level_blocks_per_sm=5), dict(gridlet_warps=3), dict(m2l_ctas_per_sm=3),
-                   dict(level_blocks_per_sm=-1)):
+                   dict(level_blocks_per_sm=-1), dict(m2l_block_order=3)):
         with pytest.raises(hpm.HpmError) as e:
             hpm.hpm_set_tuning(s.plan, **shapes)
         assert e.value.status == -1
