@@ -62,11 +62,12 @@ def lib():
             "or_moments": ([i32, i64, vp, vp, vp, vp, vp, vp], None),
             "or_p2g_paper": ([i32, i64, vp, vp, vp, vp], None),
             "or_t_paper": ([i32, vp, vp, i32, vp], None),
-            "or_m2l_direct": ([i32, vp, i64, vp, vp, vp, vp, vp, vp, vp], None),
+            "or_m2l_direct": ([i32, i32, vp, i64, vp, vp, vp, vp, vp, vp, vp], None),
+            "or_lagrange_ext": ([i32, i32, f64, vp, vp], None),
             "or_fft1d": ([vp, vp, i32, i32, vp, vp], None),
             "or_green_hat": ([i32, vp, f64, vp, vp], None),
-            "or_m2l_fft": ([i32, i64, vp, vp, vp, vp, vp, vp], None),
-            "or_far_eval": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp], None),
+            "or_m2l_fft": ([i32, i32, i64, vp, vp, vp, vp, vp, vp], None),
+            "or_far_eval": ([i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp], None),
             "or_g2p_paper": ([i32, i64, vp, vp, vp, vp, vp, vp, vp], None),
             "or_p2p": ([vp, i64, vp, vp, vp, vp, vp, vp, vp, vp], None),
             "or_direct": ([vp, i64, vp, i64, vp, vp, vp, vp], None),
@@ -198,6 +199,19 @@ def lagrange(ng: int, t: float):
     return w, dw
 
 
+def nodes_ext(ng: int, ext: int) -> np.ndarray:
+    """Nodes of the extended gridlet (Sec. 2.5): x_j for j = -ext .. Ng - 1 + ext."""
+    return (np.arange(-ext, ng + ext) + 0.5) / ng - 0.5
+
+
+def lagrange_ext(ng: int, ext: int, t: float):
+    ne = ng + 2 * ext
+    w = np.zeros(ne)
+    dw = np.zeros(ne)
+    _call("or_lagrange_ext", ng, int(ext), float(t), _p(w), _p(dw))
+    return w, dw
+
+
 def vandermonde(ng: int) -> np.ndarray:
     m3 = ng ** 3
     A = np.zeros((m3, m3))
@@ -282,29 +296,31 @@ def green_hat(ng: int, eps, h: float):
     return re, im
 
 
-def m2l_direct(ng, eps, tcenter, tside, soff, sidx, scenter, sgrid) -> np.ndarray:
+def m2l_direct(ng, eps, tcenter, tside, soff, sidx, scenter, sgrid, ext=0) -> np.ndarray:
+    """Direct interaction-zone sum at the targets' (Ng + 2 ext)^3 nodes (ext = 1: the
+    extended gridlet of Sec. 2.5)."""
     tcenter, tside, soff, sidx = _f64(tcenter), _f64(tside), _i64(soff), _i64(sidx)
-    out = np.zeros((tcenter.shape[0], ng ** 3))
-    _call("or_m2l_direct", ng, _kern(eps), tcenter.shape[0], _p(tcenter), _p(tside), _p(soff), _p(sidx),
+    out = np.zeros((tcenter.shape[0], (ng + 2 * ext) ** 3))
+    _call("or_m2l_direct", ng, int(ext), _kern(eps), tcenter.shape[0], _p(tcenter), _p(tside), _p(soff), _p(sidx),
                         _p(_f64(scenter)), _p(_f64(sgrid)), _p(out))
     return out
 
 
-def m2l_fft(ng, blk, tpos, grid, ghat) -> np.ndarray:
+def m2l_fft(ng, blk, tpos, grid, ghat, ext=0) -> np.ndarray:
     blk = np.ascontiguousarray(blk, dtype=np.int32)
     tpos = np.ascontiguousarray(tpos, dtype=np.int32)
-    out = np.zeros((blk.shape[0], ng ** 3))
-    _call("or_m2l_fft", ng, blk.shape[0], _p(blk), _p(tpos), _p(_f64(grid)), _p(_f64(ghat[0])),
+    out = np.zeros((blk.shape[0], (ng + 2 * ext) ** 3))
+    _call("or_m2l_fft", ng, int(ext), blk.shape[0], _p(blk), _p(tpos), _p(_f64(grid)), _p(_f64(ghat[0])),
                      _p(_f64(ghat[1])), _p(out))
     return out
 
 
-def far_eval(ng, pos, coff, ccell, ccenter, cside, cphi):
+def far_eval(ng, pos, coff, ccell, ccenter, cside, cphi, ext=0):
     pos = _f64(pos)
     n = pos.shape[0]
     phi = np.zeros(n)
     acc = np.zeros((n, 3))
-    _call("or_far_eval", ng, n, _p(pos), _p(_i64(coff)), _p(_i64(ccell)), _p(_f64(ccenter)),
+    _call("or_far_eval", ng, int(ext), n, _p(pos), _p(_i64(coff)), _p(_i64(ccell)), _p(_f64(ccenter)),
                       _p(_f64(cside)), _p(_f64(cphi)), _p(phi), _p(acc))
     return phi, acc
 
@@ -526,13 +542,15 @@ def canonical_lists(tree: Tree, iz_levels=None, chunk: int = 20000) -> dict:
 # ---------------------------------------------------------------------------
 # Solve, plain definitions (parity oracle)
 # ---------------------------------------------------------------------------
-def solve_direct(tree: Tree, mass, ng: int, eps: float, sample=None):
+def solve_direct(tree: Tree, mass, ng: int, eps: float, sample=None, ext: int = 0):
     """FP64 HPM by plain definitions: effective masses of every source box by P2G from its
     particles, source-to-target as the direct interaction-zone double sum, far field at a
     particle as the sum of the interpolants of its leaf and the leaf's ancestors down to
     level 2, near field by direct summation over near(leaf).
 
     ``sample``: original indices of the particles to evaluate (default all).
+    ``ext`` = 1: extended target gridlets (Sec. 2.5), the potential evaluated at the
+    cell's nodes widened by one node on each side and interpolated with degree Ng + 1.
     Returns (phi, acc) for those particles, in the order given.
     """
     n = tree.n
@@ -610,11 +628,11 @@ def solve_direct(tree: Tree, mass, ng: int, eps: float, sample=None):
         sgrid = p2g(ng, sbeg, send, scen, sside, tree.spos, smass) if s_level.size else np.zeros((0, ng ** 3))
         tcen, tside, _, _ = geom(t_level, t_box)
         tphi = m2l_direct(ng, eps, tcen, tside, np.asarray(soff), np.asarray(sidx, dtype=np.int64),
-                          scen if s_level.size else np.zeros((0, 3)), sgrid)
+                          scen if s_level.size else np.zeros((0, 3)), sgrid, ext=ext)
         coff = np.zeros(ns + 1, dtype=np.int64)
         coff[1:] = np.cumsum([len(c) for c in chain])
         ccell = np.asarray([x for c in chain for x in c], dtype=np.int64)
-        phi_far, acc_far = far_eval(ng, tree.spos[s], coff, ccell, tcen, tside, tphi)
+        phi_far, acc_far = far_eval(ng, tree.spos[s], coff, ccell, tcen, tside, tphi, ext=ext)
 
     # near field over near(leaf)
     roff = [0]
@@ -833,12 +851,13 @@ def box_masses(tree: Tree, mass, ng, levels, keys):
     return p2g(ng, beg, end, cen, side, tree.spos, smass)
 
 
-def m2l_values(tree: Tree, mass, ng, eps, levels, keys):
-    """Source-to-target values Phi_{t,p} of the given target cells, direct IZ sum (Sec. 2.1)."""
+def m2l_values(tree: Tree, mass, ng, eps, levels, keys, ext=0):
+    """Source-to-target values Phi_{t,p} of the given target cells, direct IZ sum (Sec. 2.1), at
+    the (Ng + 2 ext)^3 nodes of their (extended, Sec. 2.5) gridlets."""
     levels = np.asarray(levels, dtype=np.int64)
     keys = np.asarray(keys, dtype=np.uint64)
     idx = _boxes(tree, levels, keys)
-    out = np.zeros((levels.shape[0], ng ** 3))
+    out = np.zeros((levels.shape[0], (ng + 2 * ext) ** 3))
     for l in np.unique(levels):
         sel = np.flatnonzero(levels == l)
         rows, _ = tree.iz_rows(int(l), idx[sel])
@@ -853,11 +872,11 @@ def m2l_values(tree: Tree, mass, ng, eps, levels, keys):
             soff.append(len(sidx))
         out[sel] = m2l_direct(ng, eps, tree.centers(int(l), idx[sel]), np.full(sel.shape[0], tree.box_side(int(l))),
                               np.asarray(soff), np.asarray(sidx, dtype=np.int64),
-                              tree.centers(int(l), src) if src.size else np.zeros((0, 3)), grid)
+                              tree.centers(int(l), src) if src.size else np.zeros((0, 3)), grid, ext=ext)
     return out
 
 
-def local_values(tree: Tree, mass, ng, eps, levels, keys):
+def local_values(tree: Tree, mass, ng, eps, levels, keys, ext=0):
     """Local gridlet of each target after the parent-to-child pass: the sum over the target
     and its ancestors down to level 2 of their interpolants (Eqs. c2pmat/phix), evaluated at
     the target's nodes (Sec. 2.4: Phi^C_p = Phi^P((a^C + x_p)/2) plus its own values)."""
@@ -875,7 +894,7 @@ def local_values(tree: Tree, mass, ng, eps, levels, keys):
         uniq.setdefault((int(a), int(b)), len(uniq))
     ul = np.asarray([a for a, _ in uniq], dtype=np.int64)
     uk = np.asarray([b for _, b in uniq], dtype=np.uint64)
-    phi_c = m2l_values(tree, mass, ng, eps, ul, uk)
+    phi_c = m2l_values(tree, mass, ng, eps, ul, uk, ext=ext)
     idx_c = _boxes(tree, ul, uk)
     cen_c = np.zeros((ul.shape[0], 3))
     side_c = np.zeros(ul.shape[0])
@@ -883,9 +902,10 @@ def local_values(tree: Tree, mass, ng, eps, levels, keys):
         m = ul == l
         cen_c[m] = tree.centers(int(l), idx_c[m])
         side_c[m] = tree.box_side(int(l))
-    x = nodes(ng)
-    m3 = ng ** 3
-    node_off = np.array([[x[p % ng], x[(p // ng) % ng], x[p // (ng * ng)]] for p in range(m3)])
+    x = nodes_ext(ng, ext)
+    ne = ng + 2 * ext
+    m3 = ne ** 3
+    node_off = np.array([[x[p % ne], x[(p // ne) % ne], x[p // (ne * ne)]] for p in range(m3)])
     idx = _boxes(tree, levels, keys)
     pts = np.zeros((levels.shape[0] * m3, 3))
     coff = [0]
@@ -897,5 +917,5 @@ def local_values(tree: Tree, mass, ng, eps, levels, keys):
         for _ in range(m3):
             ccell.extend(chain)
             coff.append(len(ccell))
-    phi, _ = far_eval(ng, pts, np.asarray(coff), np.asarray(ccell, dtype=np.int64), cen_c, side_c, phi_c)
+    phi, _ = far_eval(ng, pts, np.asarray(coff), np.asarray(ccell, dtype=np.int64), cen_c, side_c, phi_c, ext=ext)
     return phi.reshape(levels.shape[0], m3)

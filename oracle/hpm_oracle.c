@@ -135,6 +135,32 @@ void or_lagrange(int ng, double t, double *w, double *dw) {
   }
 }
 
+/* Lagrange basis on the extended target gridlet of Sec. 2.5: the Ng nodes of
+ * the cell widened by `ext` nodes of the same spacing on each side, nodes
+ * x_j = (j + 1/2)/Ng - 1/2 for j = -ext .. Ng - 1 + ext (ext = 0: the gridlet
+ * itself). w and dw get Ng + 2 ext values. */
+void or_lagrange_ext(int ng, int ext, double t, double *w, double *dw) {
+  const int ne = ng + 2 * ext;
+  for (int j = 0; j < ne; ++j) {
+    const double xj = node_x(j - ext, ng);
+    double v = 1.0;
+    for (int k = 0; k < ne; ++k)
+      if (k != j) v *= (t - node_x(k - ext, ng)) / (xj - node_x(k - ext, ng));
+    w[j] = v;
+    if (dw) {
+      double d = 0.0;
+      for (int m = 0; m < ne; ++m) {
+        if (m == j) continue;
+        double term = 1.0 / (xj - node_x(m - ext, ng));
+        for (int k = 0; k < ne; ++k)
+          if (k != j && k != m) term *= (t - node_x(k - ext, ng)) / (xj - node_x(k - ext, ng));
+        d += term;
+      }
+      dw[j] = d;
+    }
+  }
+}
+
 /* ---------------------------------------------------------------------------
  * P2G, Lagrange form. For box b with centre c and side L:
  *   M_{b,p} = sum_{i in b} m_i prod_d ell_{p_d}(xi_{i,d}),  xi = (x_i - c)/L.
@@ -296,19 +322,21 @@ void or_t_paper(int ng, const double *A, const double *B, int child, double *T) 
  * Source-to-target transformation, direct double sum (plain definition):
  *   Phi_{t,p} = - sum_{b in IZ(t)} sum_q M_{b,q} g(|y_{t,p} - y_{b,q}|),
  * node positions y = c + L x_p. Sources of target t are rows
- * sidx[soff[t] .. soff[t+1]) of the source tables.
+ * sidx[soff[t] .. soff[t+1]) of the source tables. The target's nodes may be
+ * the extended gridlet of Sec. 2.5 (ext = 1: one more node on each side,
+ * (Ng + 2)^3 values per target); the sources are always Ng^3 gridlets.
  * ------------------------------------------------------------------------- */
-void or_m2l_direct(int ng, const or_kernel *kern, int64_t ntgt, const double *tcenter, const double *tside,
-                   const int64_t *soff, const int64_t *sidx, const double *scenter,
+void or_m2l_direct(int ng, int ext, const or_kernel *kern, int64_t ntgt, const double *tcenter,
+                   const double *tside, const int64_t *soff, const int64_t *sidx, const double *scenter,
                    const double *sgrid, double *out) {
-  const int m3 = ng * ng * ng;
+  const int m3 = ng * ng * ng, ne = ng + 2 * ext, me = ne * ne * ne;
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t t = 0; t < ntgt; ++t) {
     const double L = tside[t];
-    for (int p = 0; p < m3; ++p) {
-      double yp[3] = {tcenter[3 * t + 0] + L * node_x(p % ng, ng),
-                      tcenter[3 * t + 1] + L * node_x((p / ng) % ng, ng),
-                      tcenter[3 * t + 2] + L * node_x(p / (ng * ng), ng)};
+    for (int p = 0; p < me; ++p) {
+      double yp[3] = {tcenter[3 * t + 0] + L * node_x(p % ne - ext, ng),
+                      tcenter[3 * t + 1] + L * node_x((p / ne) % ne - ext, ng),
+                      tcenter[3 * t + 2] + L * node_x(p / (ne * ne) - ext, ng)};
       double s = 0.0;
       for (int64_t e = soff[t]; e < soff[t + 1]; ++e) {
         const int64_t b = sidx[e];
@@ -319,7 +347,7 @@ void or_m2l_direct(int ng, const or_kernel *kern, int64_t ntgt, const double *tc
           s += sgrid[b * m3 + q] * or_g(kern, sqrt(dx * dx + dy * dy + dz * dz));
         }
       }
-      out[t * m3 + p] = -s;
+      out[t * me + p] = -s;
     }
   }
 }
@@ -409,12 +437,13 @@ void or_green_hat(int P, const or_kernel *kern, double h, double *re, double *im
  * of that box's effective masses in grid[], or -1 where the box is empty,
  * outside the domain or in the target's near zone. The block is zero padded
  * to P^3 = (8 Ng)^3, convolved with the Green function (forward FFT, product
- * with ghat, backward FFT, 1/P^3), and the Ng^3 values at the target's nodes
- * are read; tpos[t] is the target's box position in the block (2 or 3 per
+ * with ghat, backward FFT, 1/P^3), and the values at the target's nodes are
+ * read, the (Ng + 2 ext)^3 nodes of its gridlet widened by ext on each side
+ * (Sec. 2.5); tpos[t] is the target's box position in the block (2 or 3 per
  * axis). Output: Phi_{t,p} = -(G * rho)(target node p). */
-void or_m2l_fft(int ng, int64_t ntgt, const int32_t *blk, const int32_t *tpos,
+void or_m2l_fft(int ng, int ext, int64_t ntgt, const int32_t *blk, const int32_t *tpos,
                 const double *grid, const double *ghat_re, const double *ghat_im, double *out) {
-  const int P = 8 * ng, m3 = ng * ng * ng;
+  const int P = 8 * ng, m3 = ng * ng * ng, ne = ng + 2 * ext, me = ne * ne * ne;
   const int64_t n3 = (int64_t)P * P * P;
 #pragma omp parallel
   {
@@ -435,10 +464,11 @@ void or_m2l_fft(int ng, int64_t ntgt, const int32_t *blk, const int32_t *tpos,
       fft3d(a, P, -1);
       for (int64_t e = 0; e < n3; ++e) a[e] *= ghat_re[e] + I * ghat_im[e];
       fft3d(a, P, +1);
-      for (int p = 0; p < m3; ++p) {
-        int x = tpos[3 * t + 0] * ng + p % ng, y = tpos[3 * t + 1] * ng + (p / ng) % ng,
-            z = tpos[3 * t + 2] * ng + p / (ng * ng);
-        out[t * m3 + p] = -creal(a[x + (int64_t)P * (y + (int64_t)P * z)]) / (double)n3;
+      for (int p = 0; p < me; ++p) {
+        /* periodic positions: the grid repeats every P points */
+        int x = (tpos[3 * t + 0] * ng - ext + p % ne + P) % P, y = (tpos[3 * t + 1] * ng - ext + (p / ne) % ne + P) % P,
+            z = (tpos[3 * t + 2] * ng - ext + p / (ne * ne) + P) % P;
+        out[t * me + p] = -creal(a[x + (int64_t)P * (y + (int64_t)P * z)]) / (double)n3;
       }
     }
     free(a);
@@ -452,11 +482,13 @@ void or_m2l_fft(int ng, int64_t ntgt, const int32_t *blk, const int32_t *tpos,
  *   phi_i = sum_cells sum_p Phi_{c,p} prod_d ell_{p_d}(xi_d),
  *   a_i   = - sum_cells (1/L_c) sum_p Phi_{c,p} grad_xi prod_d ell_{p_d}(xi_d),
  * xi = (x_i - c)/L_c. Cells of particle i are ccell[coff[i] .. coff[i+1]).
+ * The gridlets may be extended by ext nodes on each side (Sec. 2.5): the
+ * interpolant is then of degree Ng - 1 + 2 ext through (Ng + 2 ext)^3 values.
  * ------------------------------------------------------------------------- */
-void or_far_eval(int ng, int64_t npart, const double *pos, const int64_t *coff,
+void or_far_eval(int ng, int ext, int64_t npart, const double *pos, const int64_t *coff,
                  const int64_t *ccell, const double *ccenter, const double *cside,
                  const double *cphi, double *phi, double *acc) {
-  const int m3 = ng * ng * ng;
+  const int ne = ng + 2 * ext, m3 = ne * ne * ne;
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t i = 0; i < npart; ++i) {
     double f = 0.0, g[3] = {0.0, 0.0, 0.0};
@@ -464,9 +496,9 @@ void or_far_eval(int ng, int64_t npart, const double *pos, const int64_t *coff,
       const int64_t c = ccell[e];
       const double L = cside[c];
       double w[3][16], dw[3][16];
-      for (int d = 0; d < 3; ++d) or_lagrange(ng, (pos[3 * i + d] - ccenter[3 * c + d]) / L, w[d], dw[d]);
+      for (int d = 0; d < 3; ++d) or_lagrange_ext(ng, ext, (pos[3 * i + d] - ccenter[3 * c + d]) / L, w[d], dw[d]);
       for (int p = 0; p < m3; ++p) {
-        int px = p % ng, py = (p / ng) % ng, pz = p / (ng * ng);
+        int px = p % ne, py = (p / ne) % ne, pz = p / (ne * ne);
         double v = cphi[c * m3 + p];
         f += v * w[0][px] * w[1][py] * w[2][pz];
         g[0] += v * dw[0][px] * w[1][py] * w[2][pz] / L;

@@ -85,6 +85,8 @@ static void make_tables(int ng, GridletTables &tb) {
     tb.node_d[j] = x[j];
     tb.inv_den_d[j] = 1.0 / den;
     tb.inv_den[j] = (float)(1.0 / den);
+    tb.node_lo[j] = (float)(x[j] - (double)tb.node[j]);
+    tb.inv_den_lo[j] = (float)(1.0 / den - (double)tb.inv_den[j]);
     double den_u = 1.0;
     for (int k = 0; k < ng; ++k)
       if (k != j) den_u *= (double)(2 * (j - k));

@@ -103,6 +103,8 @@ struct GridletTables {
   double inv_den_d[kMaxNg];          // 1 / prod_{k != j} (x_j - x_k)
   double inv_den_u[kMaxNg];          // the same for the nodes 2 Ng x_j = 2j + 1 - Ng (integers)
   float inv_den[kMaxNg];
+  float node_lo[kMaxNg];             // x_j - node[j], and 1 / prod(...) - inv_den[j]: the
+  float inv_den_lo[kMaxNg];          // double-float rests of the FP64 values
 };
 
 struct TreeDev {

@@ -49,6 +49,7 @@
 //                values
 // Every wait is bounded; a wait that runs out sets kErrTimeout in the error
 // word and the CTA leaves its loops.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -61,27 +62,12 @@ namespace tc {
 
 constexpr int kSlots = 216;                     // 6^3 source block
 constexpr int kKC = 16;                         // K elements per chunk (a 64-byte row of FP16 hi, lo)
-constexpr int kTileN = 256;                     // parents per tile
 constexpr int kRows = 128;                      // rows of W per CTA
-constexpr int kHalfN = kTileN / 2;              // parents gathered by each CTA of a pair
-// One stage holds 4 K-chunks, so the MMA thread issues 12 MMAs per barrier
-// wait and commit: the per-stage synchronisation cost (a few hundred cycles of
-// the issuing thread) stays well below the MMAs' 1536 cycles. Each CTA of a
-// pair loads its own 128 rows of W and half of the parents, so a stage is
-// 64 KB and three fit.
-constexpr int kStageChunks = 4;
-constexpr int kStages = 3;
 constexpr int kRowBytes = 2 * kKC * 2;          // one tile row: 16 hi then 16 lo FP16 values
 constexpr int kABytes = kRows * kRowBytes;      // W tile of one K-chunk: 8 KB
-constexpr int kBBytes = kHalfN * kRowBytes;     // gathered tile of one K-chunk: 8 KB
-constexpr int kStageABytes = kStageChunks * kABytes;                  // 32 KB, one bulk copy
-constexpr int kStageBytes = kStageChunks * (kABytes + kBBytes);       // 64 KB: 4 W tiles, then 4 B tiles
-// 1 KB for aligning the stages, 8 KB of slack past the last one
-constexpr int kSmem = kStages * kStageBytes + 1024 + 8192;
 constexpr int kScaleTop = 14;                   // scaled maxima lie in [2^13, 2^14)
 constexpr int kNoExp = 1 << 20;                 // exponent of a row without mass
 
-constexpr int kBlockChunks = 16;                // accumulator drained every 16 K-chunks
 
 // Sizes per gridlet order. K runs over the 216 source slots, each slot's
 // gridlet padded to a multiple of 16 nodes (kCPS K-chunks per slot); the rows
@@ -91,6 +77,44 @@ constexpr int kBlockChunks = 16;                // accumulator drained every 16 
 // 14 chunks, 3024 per tile, 1728 rows in 14 blocks (64 padding rows).
 template <int NG>
 struct Cfg {
+  // The tensor core's accumulation truncates: each MMA's sum is added to the
+  // accumulator rounded toward zero, and the error grows with the number of
+  // additions since the last drain into the round-to-nearest FP32 totals in
+  // registers. The K sum of the deviation rows cancels heavily, and more so
+  // at higher order, so the accumulator is drained more often there (every 16
+  // K-chunks at Ng = 4, every 8 at Ng = 6).
+  static constexpr int kBlockChunks = NG == 4 ? 16 : 8;
+  // Parents per tile (the MMA's N) and the drain's running totals: at Ng = 4
+  // 256 parents and FP32 totals (128 columns per drain thread in registers);
+  // at Ng = 6 the K sum of the deviation rows is longer and cancels more, and
+  // the FP32 additions of the drained blocks would dominate the error, so the
+  // totals are compensated (two-sum errors gathered in bf16 terms), which
+  // fits in registers for 64 columns per drain thread: 128 parents per tile.
+  static constexpr int kTileN = NG == 4 ? 256 : 128;
+  static constexpr bool kDfTotals = NG != 4;
+  // K-chunks per pipeline stage: the stage's synchronisation (barrier waits
+  // and commits of the issuing thread, a few hundred cycles) must stay below
+  // the MMAs' time, 3 x 4 x 128 cycles at 256 parents; 128 parents need 8
+  // chunks per stage for the same MMA time. Each CTA of a pair loads its own
+  // 128 rows of W and half of the parents per stage.
+  static constexpr int kStageChunks = NG == 4 ? 4 : 8;
+  static constexpr int kStageABytes = kStageChunks * kABytes;   // W of a stage, one bulk copy
+  static constexpr int kHalfN = kTileN / 2;                     // parents gathered by each CTA of a pair
+  static constexpr int kCols = kTileN / 2;                      // columns per drain thread (2 warps per lane quadrant)
+  static constexpr int kBBytes = kHalfN * kRowBytes;            // gathered tile of one K-chunk
+  static constexpr int kStageBytes = kStageChunks * (kABytes + kBBytes);  // 4 W tiles, then 4 B tiles
+  static constexpr int kStages = NG == 4 ? 3 : 2;               // 3 x 64 KB or 2 x 96 KB
+  // 1 KB for aligning the stages, 8 KB of slack past the last one
+  static constexpr int kSmem = kStages * kStageBytes + 1024 + 8192;
+  // instruction descriptor, kind::f16: FP32 accumulator, FP16 A and B (format
+  // 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24. The MMA spans a CTA
+  // pair: M = 256 rows (128 in each CTA's shared and tensor memory), N = the
+  // tile's parents (each CTA's B rows are half of them).
+  static constexpr uint32_t kIdesc =
+      (1u << 4) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)((2 * kRows) >> 4) << 24);
+  static_assert(kTileN % 16 == 0 && kTileN <= 256 && 2 * kTileN <= 512, "MMA N and two accumulator buffers");
+  static_assert(kCols % 32 == 0 && kHalfN % 8 == 0, "drain column groups, gather groups");
+  static_assert(kSmem <= 227 * 1024, "shared memory");
   static constexpr int kM3 = NG * NG * NG;                      // nodes per gridlet
   static constexpr int kCPS = (kM3 + kKC - 1) / kKC;            // K-chunks per source slot
   static constexpr int kChunks = kSlots * kCPS;                 // K-chunks per tile
@@ -102,7 +126,7 @@ struct Cfg {
   static_assert(kChunks % kBlockChunks == 0, "drain blocks tile the K loop");
   static_assert(kBlockChunks % kStageChunks == 0, "drain blocks hold whole stages");
   static_assert(kQuarters % 2 == 0, "CTA pairs");
-  static_assert(kCPS >= kStageChunks, "a gather warp's next chunk is in the same or the next slot");
+  static_assert(kCPS >= 4, "a gather warp's next chunk (4 chunks on) is in the same or the next slot");
 };
 
 // 4 warpgroups: 0 = W copy (warp 0), tensor memory and MMA issue (warp 1),
@@ -112,10 +136,10 @@ struct Cfg {
 // launch's total.
 constexpr int kWarps = 16, kThreads = kWarps * 32;
 constexpr int kProdWarp0 = 4, kEpiWarp0 = 8;
-constexpr int kGatherWarps = kEpiWarp0 - kProdWarp0;  // one per K-chunk of a stage
+constexpr int kGatherWarps = kEpiWarp0 - kProdWarp0;  // chunk g, g + 4, ... of every stage
 constexpr int kLaunchRegs = 128, kRegsCtl = 40, kRegsGather = 104, kRegsHigh = 184;
 static_assert(128 * kRegsCtl + 128 * kRegsGather + 2 * 128 * kRegsHigh == kThreads * kLaunchRegs, "register split");
-static_assert(kGatherWarps == kStageChunks, "gather warp g copies K-chunk g of every stage");
+static_assert(kGatherWarps == 4, "gather warp g copies K-chunks g, g + 4, ... of every stage");
 // setmaxnreg: .dec only lowers, .inc only raises; counts are multiples of 8 in [24, 256]
 static_assert(kRegsCtl <= kLaunchRegs && kRegsGather <= kLaunchRegs && kRegsHigh >= kLaunchRegs, "dec / inc");
 static_assert(kRegsCtl % 8 == 0 && kRegsGather % 8 == 0 && kRegsHigh % 8 == 0 && kRegsCtl >= 24 && kRegsHigh <= 256,
@@ -194,17 +218,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
-// Instruction descriptor, kind::f16: FP32 accumulator, FP16 A and B (format
-// 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24. The MMA spans a CTA
-// pair: M = 256 rows (128 in each CTA's shared and tensor memory), N = 256
-// parents (each CTA's B rows are half of them).
-constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)((2 * kRows) >> 4) << 24);
-
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, int accumulate) {
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, int accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
           d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 // arrive on the barrier at this offset in both CTAs of the pair once the MMAs
@@ -273,6 +291,13 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
       "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
       HPM_W32(v)
       : "memory");
+}
+// 32 lanes x 8 consecutive columns
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr)
+               : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
@@ -366,16 +391,16 @@ __global__ void k_w_table(const double *__restrict__ gl, const double *__restric
 }
 
 // Source rows and target indices of every tile: tiles group the parents of one
-// level (par_box is level-major), 256 per tile, the last one padded with -1.
+// level (par_box is level-major), kTileN per tile, the last one padded with -1.
 struct TileLevels {
   int64_t tile_off[kMaxDepth + 2];  // by target level
   int64_t par_off[kMaxDepth + 2];   // parents of target level l: par_box[par_off[l] .. par_off[l + 1])
   int nlev;
 };
 
-__global__ void k_tiles(int64_t ntiles, TileLevels tl, const int *__restrict__ par_box, const int *__restrict__ nb,
-                        const int *__restrict__ child, const int *__restrict__ box_tgt, int64_t off2,
-                        int *__restrict__ rows, int *__restrict__ tgt) {
+__global__ void k_tiles(int64_t ntiles, int kTileN, TileLevels tl, const int *__restrict__ par_box,
+                        const int *__restrict__ nb, const int *__restrict__ child, const int *__restrict__ box_tgt,
+                        int64_t off2, int *__restrict__ rows, int *__restrict__ tgt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ntiles * kTileN) return;
   const int64_t tile = i / kTileN;
@@ -546,7 +571,7 @@ __device__ __forceinline__ void warp_sum_pair(float &s, float &e) {
   }
 }
 
-__global__ void k_col_exp(int64_t ntiles, const int *__restrict__ rows, const int *__restrict__ box_exp,
+__global__ void k_col_exp(int64_t ntiles, int kTileN, const int *__restrict__ rows, const int *__restrict__ box_exp,
                           const float *__restrict__ box_mass, int *__restrict__ col_exp,
                           float *__restrict__ zone_mass) {
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -594,7 +619,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
   // full: this CTA's stage landed; pfull (leader): the peer's stage landed;
   // empty: the pair's MMAs are done with the stage; accf[x] / acce[x]:
   // accumulator buffer x filled by the MMAs / drained by both CTAs (leader)
-  __shared__ uint64_t full[kStages], pfull[kStages], empty[kStages], accf[2], acce[2], never;
+  __shared__ uint64_t full[C::kStages], pfull[C::kStages], empty[C::kStages], accf[2], acce[2], never;
   __shared__ uint32_t tmem_base;
   __shared__ int failed;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -616,7 +641,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
   while (lev + 1 < pr.nlev && pr.tile_off[lev + 1] <= tile) ++lev;
 
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < C::kStages; ++s) {
       bar_init(&full[s], 1 + 32 * kGatherWarps);  // the W copy (with its byte count), then each gather thread
       bar_init(&pfull[s], 1);
       bar_init(&empty[s], 1);
@@ -639,7 +664,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
   __syncthreads();
   cluster_sync();  // tensor memory allocated in both CTAs before the first MMA
   tc_fence_after();
-  const uint32_t tbase = tmem_base;  // block b accumulates in columns 256 (b & 1) ...
+  const uint32_t tbase = tmem_base;  // block b accumulates in columns kTileN (b & 1) ...
 
   if (warp < kProdWarp0) {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsCtl));
@@ -649,19 +674,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
         const unsigned char *src = pr.w + (int64_t)(lev - 2) * C::kLevelBytes + (int64_t)q * C::kChunks * kABytes;
         bool ok = true;
         for (int u = 0; u < C::kSlotUses; ++u) {
-          const int st = u % kStages;
-          if (!bar_wait(&empty[st], ((u / kStages) & 1) ^ 1, lim)) {
+          const int st = u % C::kStages;
+          if (!bar_wait(&empty[st], ((u / C::kStages) & 1) ^ 1, lim)) {
             failed = 1;
             ok = false;
             break;
           }
-          bar_expect(&full[st], kStageABytes);
-          bulk_load(sm + st * kStageBytes, src + (int64_t)u * kStageABytes, kStageABytes, &full[st]);
+          bar_expect(&full[st], C::kStageABytes);
+          bulk_load(sm + st * C::kStageBytes, src + (int64_t)u * C::kStageABytes, C::kStageABytes, &full[st]);
         }
         // the releases of the last stages are the leader's final arrivals on
         // this CTA's barriers: wait for them before the CTA may leave
-        for (int u = C::kSlotUses; ok && u < C::kSlotUses + kStages; ++u)
-          if (!bar_wait(&empty[u % kStages], ((u / kStages) & 1) ^ 1, lim)) {
+        for (int u = C::kSlotUses; ok && u < C::kSlotUses + C::kStages; ++u)
+          if (!bar_wait(&empty[u % C::kStages], ((u / C::kStages) & 1) ^ 1, lim)) {
             failed = 1;
             ok = false;
           }
@@ -672,10 +697,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
         const bool stalled = pr.stall && !bar_wait(&never, 0, lim);
         if (stalled) failed = 1;
         for (int u = 0; !stalled && u < C::kSlotUses; ++u) {
-          const int st = u % kStages;
-          const int c0 = u * kStageChunks;  // first K-chunk of the stage
-          const int b = c0 / kBlockChunks, x = b & 1;
-          const bool first = (c0 % kBlockChunks) == 0;
+          const int st = u % C::kStages;
+          const int c0 = u * C::kStageChunks;  // first K-chunk of the stage
+          const int b = c0 / C::kBlockChunks, x = b & 1;
+          const bool first = (c0 % C::kBlockChunks) == 0;
           if (first && b >= 2) {
             // buffer x was last filled by block b - 2: wait for both CTAs' drains
             if (!bar_wait_cl(&acce[x], ((b >> 1) - 1) & 1, lim)) {
@@ -684,7 +709,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
             }
             tc_fence_after();
           }
-          if (!bar_wait(&full[st], (u / kStages) & 1, lim) || !bar_wait_cl(&pfull[st], (u / kStages) & 1, lim)) {
+          if (!bar_wait(&full[st], (u / C::kStages) & 1, lim) || !bar_wait_cl(&pfull[st], (u / C::kStages) & 1, lim)) {
             failed = 1;
             break;
           }
@@ -692,18 +717,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
           tc_fence_after();
           // rows hold 16 hi then 16 lo values: hi*hi, hi*lo, lo*hi; the same
           // offsets in the peer CTA hold its 128 rows of W and 128 parents
-          const uint32_t sa = su32(sm + st * kStageBytes), sb = sa + kStageABytes;
-          const uint32_t tacc = tbase + 256u * (uint32_t)x;
+          const uint32_t sa = su32(sm + st * C::kStageBytes), sb = sa + C::kStageABytes;
+          const uint32_t tacc = tbase + (uint32_t)C::kTileN * (uint32_t)x;
 #pragma unroll
-          for (int k = 0; k < kStageChunks; ++k) {
-            const uint32_t a = sa + k * kABytes, bb = sb + k * kBBytes;
+          for (int k = 0; k < C::kStageChunks; ++k) {
+            const uint32_t a = sa + k * kABytes, bb = sb + k * C::kBBytes;
             const uint64_t ah = sdesc(a), al = sdesc(a + 32), bh = sdesc(bb), bl = sdesc(bb + 32);
-            mma(tacc, ah, bh, !(first && k == 0));
-            mma(tacc, ah, bl, 1);
-            mma(tacc, al, bh, 1);
+            mma(tacc, ah, bh, C::kIdesc, !(first && k == 0));
+            mma(tacc, ah, bl, C::kIdesc, 1);
+            mma(tacc, al, bh, C::kIdesc, 1);
           }
           mma_commit(&empty[st]);
-          if ((c0 + kStageChunks) % kBlockChunks == 0) mma_commit(&accf[x]);
+          if ((c0 + C::kStageChunks) % C::kBlockChunks == 0) mma_commit(&accf[x]);
         }
       }
     } else if (warp >= 2 && rank == 1) {
@@ -711,8 +736,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
       // uses, warp 3 the odd ones, so each has two stages' time per arrival)
       if (lane == 0) {
         for (int u = warp - 2; u < C::kSlotUses; u += 2) {
-          const int st = u % kStages;
-          if (!bar_wait(&full[st], (u / kStages) & 1, lim)) {
+          const int st = u % C::kStages;
+          if (!bar_wait(&full[st], (u / C::kStages) & 1, lim)) {
             failed = 1;
             break;
           }
@@ -723,58 +748,62 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
     }
   } else if (warp < kEpiWarp0) {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsGather));
-    // Gather warp g fills the B tile of K-chunk 4 u + g of every stage use u
-    // (node chunk j of source slot s: nodes 16 j ... of the slot's gridlet)
-    // with this CTA's 128 parents (128 rank ...): 64 bytes each, 4 lanes per
-    // parent (one 16-byte piece each), parents 8 m + lane / 4 for m = 0..15.
-    // Each thread's copies arrive on the stage's full barrier when they land
-    // (cp.async.mbarrier.arrive.noinc); the thread that consumes the stage
-    // (the leader's MMA thread, the peer's relay) makes them visible to the
-    // tensor core's proxy with one fence per stage, much cheaper there than a
-    // fence per gathering warp after its copies. When the warp's next chunk
-    // lies in the next slot, that slot's row indices are loaded while the
-    // current chunk is copied.
+    // Gather warp g fills the B tiles of K-chunks g, g + 4, ... of every stage
+    // use u (chunk c = kStageChunks u + g + 4 i: node chunk j of source slot s,
+    // nodes 16 j ... of the slot's gridlet) with this CTA's kHalfN parents
+    // (kHalfN rank ...): 64 bytes each, 4 lanes per parent (one 16-byte piece
+    // each), parents 8 m + lane / 4. Each thread's copies arrive on the
+    // stage's full barrier when they land (cp.async.mbarrier.arrive.noinc);
+    // the thread that consumes the stage (the leader's MMA thread, the peer's
+    // relay) makes them visible to the tensor core's proxy with one fence per
+    // stage, much cheaper there than a fence per gathering warp after its
+    // copies. When the warp's next chunk lies in the next slot, that slot's row
+    // indices are loaded while the current chunk is copied.
     const int g = warp - kProdWarp0, sub = lane & 3, grp = lane >> 2;
-    const int *rp = pr.rows + tile * kSlots * kTileN + (int)rank * kHalfN + grp;
+    const int *rp = pr.rows + tile * kSlots * C::kTileN + (int)rank * C::kHalfN + grp;
     // sw64 position of parent 8 m + grp, piece sub: 512 m + this lane's offset
     const uint32_t lane_off = (uint32_t)(grp * 64 + ((sub ^ ((grp >> 1) & 3)) << 4));
-    const uint32_t bsh = su32(sm + kStageABytes + g * kBBytes) + lane_off;
+    const uint32_t bsh = su32(sm + C::kStageABytes + g * C::kBBytes) + lane_off;
     const unsigned char *hsub = pr.hl + 16 * sub;
-    constexpr int kPer = kHalfN / 8;
+    constexpr int kPer = C::kHalfN / 8;
+    constexpr int kGPer = C::kStageChunks / kGatherWarps;  // this warp's chunks per stage
+    // at Ng = 4 a slot is 4 chunks: the warp's next chunk is always in the next slot
+    constexpr bool kAlwaysNext = C::kCPS == kGatherWarps;
     int rows[kPer], next[kPer];
     {
       const int s0 = g / C::kCPS;
 #pragma unroll
-      for (int m = 0; m < kPer; ++m) rows[m] = __ldg(rp + s0 * kTileN + 8 * m);
+      for (int m = 0; m < kPer; ++m) rows[m] = __ldg(rp + s0 * C::kTileN + 8 * m);
     }
     for (int u = 0; u < C::kSlotUses; ++u) {
-      const int st = u % kStages;
-      const int c = u * kStageChunks + g, s = c / C::kCPS, j = c - s * C::kCPS;
-      const int sn = (c + kStageChunks) / C::kCPS;  // slot of this warp's next chunk (s or s + 1)
-      // at Ng = 4 a stage is one slot: the next chunk is always in the next slot
-      constexpr bool kSlotPerStage = C::kCPS == kStageChunks;
-      if (kSlotPerStage || sn != s) {
-#pragma unroll
-        for (int m = 0; m < kPer; ++m) next[m] = sn < kSlots ? __ldg(rp + sn * kTileN + 8 * m) : -1;
-      }
+      const int st = u % C::kStages;
       int ok = 1;
-      if (lane == 0) ok = bar_wait(&empty[st], ((u / kStages) & 1) ^ 1, lim);
+      if (lane == 0) ok = bar_wait(&empty[st], ((u / C::kStages) & 1) ^ 1, lim);
       if (!__shfl_sync(0xffffffffu, ok, 0)) {
         failed = 1;
         break;
       }
-      const uint32_t dst = bsh + st * kStageBytes;
-      const unsigned char *hj = hsub + j * kRowBytes;
 #pragma unroll
-      for (int m = 0; m < kPer; ++m) {
-        const int row = rows[m];
-        cp16(dst + m * 512, hj + (int64_t)(row >= 0 ? row : 0) * C::kCPS * kRowBytes, row >= 0 ? 16u : 0u);
+      for (int ch = 0; ch < kGPer; ++ch) {
+        const int c = u * C::kStageChunks + g + ch * kGatherWarps, s = c / C::kCPS, j = c - s * C::kCPS;
+        const int sn = (c + kGatherWarps) / C::kCPS;  // slot of this warp's next chunk (s or s + 1)
+        if (kAlwaysNext || sn != s) {
+#pragma unroll
+          for (int m = 0; m < kPer; ++m) next[m] = sn < kSlots ? __ldg(rp + sn * C::kTileN + 8 * m) : -1;
+        }
+        const uint32_t dst = bsh + st * C::kStageBytes + ch * kGatherWarps * C::kBBytes;
+        const unsigned char *hj = hsub + j * kRowBytes;
+#pragma unroll
+        for (int m = 0; m < kPer; ++m) {
+          const int row = rows[m];
+          cp16(dst + m * 512, hj + (int64_t)(row >= 0 ? row : 0) * C::kCPS * kRowBytes, row >= 0 ? 16u : 0u);
+        }
+        if (kAlwaysNext || sn != s) {
+#pragma unroll
+          for (int m = 0; m < kPer; ++m) rows[m] = next[m];
+        }
       }
       asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(&full[st])) : "memory");
-      if (kSlotPerStage || sn != s) {
-#pragma unroll
-        for (int m = 0; m < kPer; ++m) rows[m] = next[m];
-      }
     }
   } else {
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsHigh));
@@ -787,8 +816,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
     const int o = real_row ? R / C::kM3 : 0, node = R - o * C::kM3;
     const uint32_t lane_off = (uint32_t)(lq * 32) << 16;
     const int e_row = __ldg(pr.w_exp + (lev - 2) * (C::kQuarters * kRows) + q * kRows + r);
-    float tot[128];
+    // running totals of this thread's kCols columns: FP32, or compensated
+    // (the exact rounding error of every addition to tot accumulates in a
+    // bf16 compensation term, two columns per register: the total is
+    // tot + compensation, several bits beyond FP32 for a few registers)
+    constexpr int kCols = C::kCols, kGroups = kCols / 32;
+    float tot[kCols];
+    uint32_t comp[C::kDfTotals ? kCols / 2 : 1];
+    if constexpr (C::kDfTotals) {
+#pragma unroll
+      for (int j = 0; j < kCols; ++j) tot[j] = 0.f;  // two-sums into zero are exact
+#pragma unroll
+      for (int j = 0; j < kCols / 2; ++j) comp[j] = 0u;
+    }
     bool ok = true;
+#pragma unroll 1
     for (int b = 0; b < C::kBlocks; ++b) {
       const int x = b & 1;
       if (!__all_sync(0xffffffffu, bar_wait_cl(&accf[x], (b >> 1) & 1, lim))) {
@@ -797,17 +839,42 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
         break;
       }
       tc_fence_after();
+      if constexpr (C::kDfTotals) {
+        // 8 columns per load: the double-float totals leave few registers
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        uint32_t a[32];
-        tmem_ld32(tbase + 256u * (uint32_t)x + lane_off + half * 128 + cc * 32, a);
-        tmem_wait_ld();
-        if (b == 0) {
+        for (int cc = 0; cc < kCols / 8; ++cc) {
+          uint32_t a[8];
+          tmem_ld8(tbase + (uint32_t)C::kTileN * (uint32_t)x + lane_off + half * kCols + cc * 8, a);
+          tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) tot[cc * 32 + j] = __uint_as_float(a[j]);
-        } else {
+          for (int j = 0; j < 8; j += 2) {
+            float e[2];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) tot[cc * 32 + j] = __uint_as_float(a[j]) + tot[cc * 32 + j];
+            for (int h = 0; h < 2; ++h) {
+              const float v = __uint_as_float(a[j + h]);
+              const float s0 = tot[cc * 8 + j + h], t = s0 + v, bp = t - s0;
+              e[h] = (s0 - (t - bp)) + (v - bp);  // exact rounding error of s0 + v
+              tot[cc * 8 + j + h] = t;
+            }
+            uint32_t &cw = comp[(cc * 8 + j) / 2];
+            const __nv_bfloat162 nc = __floats2bfloat162_rn(__uint_as_float(cw << 16) + e[0],
+                                                            __uint_as_float(cw & 0xffff0000u) + e[1]);
+            cw = *reinterpret_cast<const uint32_t *>(&nc);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int cc = 0; cc < kGroups; ++cc) {
+          uint32_t a[32];
+          tmem_ld32(tbase + (uint32_t)C::kTileN * (uint32_t)x + lane_off + half * kCols + cc * 32, a);
+          tmem_wait_ld();
+          if (b == 0) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) tot[cc * 32 + j] = __uint_as_float(a[j]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) tot[cc * 32 + j] = __uint_as_float(a[j]) + tot[cc * 32 + j];
+          }
         }
       }
       tc_fence_before();
@@ -817,19 +884,26 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
         else bar_arrive_remote(&acce[x], 0);
       }
     }
+    if constexpr (C::kDfTotals) {
+#pragma unroll
+      for (int j = 0; j < kCols / 2; ++j) {  // the compensated totals, rounded once
+        tot[2 * j] += __uint_as_float(comp[j] << 16);
+        tot[2 * j + 1] += __uint_as_float(comp[j] & 0xffff0000u);
+      }
+    }
     if (ok && real_row) {
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        const int col = half * 128 + cc * 32;
-        const int *tg = pr.tgt + (tile * kTileN + col) * 8 + o;
-        const int *ce = pr.col_exp + tile * kTileN + col;
+      for (int cc = 0; cc < kGroups; ++cc) {
+        const int col = half * kCols + cc * 32;
+        const int *tg = pr.tgt + (tile * C::kTileN + col) * 8 + o;
+        const int *ce = pr.col_exp + tile * C::kTileN + col;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int t_idx = __ldg(tg + j * 8);
           if (t_idx >= 0) {
             const float v = (tot[cc * 32 + j] * pow2f(-e_row)) * pow2f(-__ldg(ce + j));
             if (node == 0) {
-              pr.outc[t_idx] = (float)((double)v + pr.mean[lev][o] * (double)__ldg(pr.zone_mass + (tile * kTileN + col + j) * 8 + o));
+              pr.outc[t_idx] = (float)((double)v + pr.mean[lev][o] * (double)__ldg(pr.zone_mass + (tile * C::kTileN + col + j) * 8 + o));
               pr.out[(int64_t)t_idx * C::kM3] = 0.f;
             } else {
               pr.out[(int64_t)t_idx * C::kM3 + node] = v;
@@ -918,8 +992,8 @@ hpm_status launch_m2l_tc_ng(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) 
   HPM_TRY(pl->s.grid_hl.ensure((size_t)nrow * C::kCPS * tc::kRowBytes, st));
   HPM_TRY(pl->s.box_exp.ensure(sizeof(int) * nrow, st));
   HPM_TRY(pl->s.box_mass.ensure(sizeof(float) * nrow, st));
-  HPM_TRY(pl->s.col_exp.ensure(sizeof(int) * pl->tc_ntiles * tc::kTileN, st));
-  HPM_TRY(pl->s.zone_mass.ensure(sizeof(float) * pl->tc_ntiles * tc::kTileN * 8, st));
+  HPM_TRY(pl->s.col_exp.ensure(sizeof(int) * pl->tc_ntiles * C::kTileN, st));
+  HPM_TRY(pl->s.zone_mass.ensure(sizeof(float) * pl->tc_ntiles * C::kTileN * 8, st));
   tc::RowLevels rl{};
   rl.nlev = pl->max_depth + 1;
   for (int l = 0; l <= pl->max_depth + 1; ++l) rl.off[l] = pl->lvl_off[l];
@@ -935,8 +1009,8 @@ hpm_status launch_m2l_tc_ng(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) 
       nrow, pl->s.grid.as<float>(), pl->t.box_key.as<uint64_t>(), rl, pl->s.level_amax.as<int>(),
       pl->s.grid_hl.as<unsigned char>(), pl->s.box_exp.as<int>(), pl->s.box_mass.as<float>());
   HPM_LAUNCHED(launches);
-  tc::k_col_exp<<<(unsigned)((pl->tc_ntiles * tc::kTileN * 32 + 255) / 256), 256, 0, st>>>(
-      pl->tc_ntiles, pl->t.tc_rows.as<int>(), pl->s.box_exp.as<int>(), pl->s.box_mass.as<float>(),
+  tc::k_col_exp<<<(unsigned)((pl->tc_ntiles * C::kTileN * 32 + 255) / 256), 256, 0, st>>>(
+      pl->tc_ntiles, C::kTileN, pl->t.tc_rows.as<int>(), pl->s.box_exp.as<int>(), pl->s.box_mass.as<float>(),
       pl->s.col_exp.as<int>(), pl->s.zone_mass.as<float>());
   HPM_LAUNCHED(launches);
   tc::Params p{};
@@ -961,7 +1035,7 @@ hpm_status launch_m2l_tc_ng(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) 
   static DeviceCache attr_cache;
   int attr_ok = 0;
   HPM_TRY(device_cached(attr_cache, [](int *v) -> hpm_status {
-    HPM_CUDA(cudaFuncSetAttribute(tc::k_m2l_tc<NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem));
+    HPM_CUDA(cudaFuncSetAttribute(tc::k_m2l_tc<NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
     // The drain warps raise their register count to kRegsHigh with registers
     // the other warpgroups give back; that only adds up if the kernel was
     // compiled with kLaunchRegs per thread. Never launch it otherwise.
@@ -976,7 +1050,7 @@ hpm_status launch_m2l_tc_ng(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) 
   if (!attr_ok) return HPM_ERR_UNSUPPORTED;
   const int64_t grid = pl->tc_ntiles * C::kQuarters;
   if (pl->events_ready) cudaEventRecord(pl->ev[10], st);
-  tc::k_m2l_tc<NG><<<(unsigned)grid, tc::kThreads, tc::kSmem, st>>>(p);
+  tc::k_m2l_tc<NG><<<(unsigned)grid, tc::kThreads, C::kSmem, st>>>(p);
   HPM_LAUNCHED(launches);
   if (pl->events_ready) cudaEventRecord(pl->ev[11], st);
   pl->stats.m2l_parents = pl->npar;
@@ -1001,6 +1075,7 @@ hpm_status tc_build_tiles(hpm_plan_s *pl, const std::vector<int64_t> &par_per_le
   pl->tc_tile_off.assign(kMaxDepth + 2, 0);
   if (!use_tc_m2l(pl)) return HPM_OK;
   const int D = pl->max_depth;
+  const int tile_n = pl->ng == 6 ? tc::Cfg<6>::kTileN : tc::Cfg<4>::kTileN;
   tc::TileLevels tl{};
   tl.nlev = D + 1;
   int64_t tiles = 0, pars = 0;
@@ -1010,7 +1085,7 @@ hpm_status tc_build_tiles(hpm_plan_s *pl, const std::vector<int64_t> &par_per_le
     pl->tc_tile_off[l] = tiles;
     if (l >= 2 && l <= D) {
       const int64_t np = par_per_level[l - 1];  // parents of level-l targets sit at level l - 1
-      tiles += (np + tc::kTileN - 1) / tc::kTileN;
+      tiles += (np + tile_n - 1) / tile_n;
       pars += np;
     }
   }
@@ -1018,11 +1093,11 @@ hpm_status tc_build_tiles(hpm_plan_s *pl, const std::vector<int64_t> &par_per_le
   pl->tc_ntiles = tiles;
   if (!tiles) return HPM_OK;
   const int64_t off2 = pl->lvl_off[2];
-  HPM_TRY(pl->t.tc_rows.ensure(sizeof(int) * tiles * tc::kSlots * tc::kTileN, st));
-  HPM_TRY(pl->t.tc_tgt.ensure(sizeof(int) * tiles * tc::kTileN * 8, st));
-  const int64_t nthr = tiles * tc::kTileN;
+  HPM_TRY(pl->t.tc_rows.ensure(sizeof(int) * tiles * tc::kSlots * tile_n, st));
+  HPM_TRY(pl->t.tc_tgt.ensure(sizeof(int) * tiles * tile_n * 8, st));
+  const int64_t nthr = tiles * tile_n;
   tc::k_tiles<<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(
-      tiles, tl, pl->t.par_box.as<int>(), pl->t.box_nb.as<int>(), pl->t.box_child.as<int>(),
+      tiles, tile_n, tl, pl->t.par_box.as<int>(), pl->t.box_nb.as<int>(), pl->t.box_child.as<int>(),
       pl->t.box_tgt.as<int>(), off2, pl->t.tc_rows.as<int>(), pl->t.tc_tgt.as<int>());
   HPM_LAUNCHED(launches);
   return HPM_OK;

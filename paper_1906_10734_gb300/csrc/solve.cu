@@ -599,6 +599,108 @@ __global__ void __launch_bounds__(kThreads) k_g2p(int64_t n, const int *__restri
   far[i] = make_float4(__ldg(locc + t) + f, -gx * invL, -gy * invL, -gz * invL);
 }
 
+// Far field for the orders other than 4, as k_g2p but with the weights and
+// the gradient's contraction in double-float: at Ng >= 5 the derivatives of
+// the Lagrange basis are large and of both signs, so plain FP32 products and
+// sums lose the deviations' precision (FP64 runs about 70 times slower than
+// FP32 on this GPU). The cell coordinate xi = (h 2^l - c) + lo 2^l is exact as
+// two floats; the weights follow the product form ell_j = prod_{k != j}
+// (xi - x_k) / (x_j - x_k) and its product-rule derivative; the contraction is
+// factorised x, then y, then z. The potential keeps the FP32 contraction.
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfloat df_mul_f(dfloat a, float b) {
+  const float p = a.h * b;
+  return df_quick_two_sum(p, fmaf(a.h, b, -p) + a.l * b);
+}
+template <int NG>
+__device__ __forceinline__ void lagrange_df(const GridletTables &tb, dfloat xi, float *w, dfloat *wd,
+                                            dfloat *dd) {
+  const int ng = NG > 0 ? NG : tb.ng;
+  dfloat diff[kMaxNg];
+#pragma unroll
+  for (int k = 0; k < (NG > 0 ? NG : kMaxNg); ++k)
+    if (k < ng) diff[k] = df_add(xi, {-tb.node[k], -tb.node_lo[k]});
+#pragma unroll
+  for (int j = 0; j < (NG > 0 ? NG : kMaxNg); ++j) {
+    if (j >= ng) break;
+    dfloat v = {tb.inv_den[j], tb.inv_den_lo[j]}, d = {0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < (NG > 0 ? NG : kMaxNg); ++k) {
+      if (k >= ng) break;
+      if (k == j) continue;
+      d = df_add(df_mul(d, diff[k]), v);
+      v = df_mul(v, diff[k]);
+    }
+    w[j] = v.h + v.l;
+    wd[j] = v;
+    dd[j] = d;
+  }
+}
+
+template <int NG>
+__global__ void __launch_bounds__(kThreads) k_g2p_df(int64_t n, const int *__restrict__ pbox,
+                                                     const int *__restrict__ box_tgt, LevelTable lt,
+                                                     GridletTables tb, float inv_side,
+                                                     const uint64_t *__restrict__ key,
+                                                     const float4 *__restrict__ uhi, const float4 *__restrict__ ulo,
+                                                     const float *__restrict__ loc,
+                                                     const float *__restrict__ locc, float4 *__restrict__ far) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int box = pbox[i];
+  const int t = box_tgt[box];
+  if (t < 0) {  // a leaf above level 2 has no far field
+    far[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  constexpr int kN = NG > 0 ? NG : kMaxNg;
+  const int ng = NG > 0 ? NG : tb.ng;
+  const int l = level_of(lt, box);
+  const uint64_t k = key[box] & ((1ull << (3 * l)) - 1ull);
+  const float sc = (float)(1u << l);
+  const float4 h = uhi[i], q = ulo[i];
+  float w[3][kN];
+  dfloat wd[3][kN], dd[3][kN];
+  lagrange_df<NG>(tb, df_two_sum(fmaf(h.x, sc, -((float)compact3(k) + 0.5f)), q.x * sc), w[0], wd[0], dd[0]);
+  lagrange_df<NG>(tb, df_two_sum(fmaf(h.y, sc, -((float)compact3(k >> 1) + 0.5f)), q.y * sc), w[1], wd[1], dd[1]);
+  lagrange_df<NG>(tb, df_two_sum(fmaf(h.z, sc, -((float)compact3(k >> 2) + 0.5f)), q.z * sc), w[2], wd[2], dd[2]);
+  const float *dl = loc + (int64_t)t * ng * ng * ng;
+  float f = 0.f;
+  dfloat gx = {0.f, 0.f}, gy = {0.f, 0.f}, gz = {0.f, 0.f};
+#pragma unroll
+  for (int pz = 0; pz < kN; ++pz) {
+    if (pz >= ng) break;
+    dfloat zx = {0.f, 0.f}, zy = {0.f, 0.f}, z0 = {0.f, 0.f};  // sums over y of the x-sums
+#pragma unroll
+    for (int py = 0; py < kN; ++py) {
+      if (py >= ng) break;
+      const float *row = dl + ng * (py + ng * pz);
+      dfloat r0 = {0.f, 0.f}, r1 = {0.f, 0.f};  // sum_x v w_x, sum_x v w_x'
+      float f0 = 0.f;
+#pragma unroll
+      for (int px = 0; px < kN; ++px) {
+        if (px >= ng) break;
+        const float v = __ldg(row + px);
+        f0 = fmaf(v, w[0][px], f0);
+        r0 = df_add(r0, df_mul_f(wd[0][px], v));
+        r1 = df_add(r1, df_mul_f(dd[0][px], v));
+      }
+      f = fmaf(f0, w[1][py] * w[2][pz], f);
+      zx = df_add(zx, df_mul(r1, wd[1][py]));
+      zy = df_add(zy, df_mul(r0, dd[1][py]));
+      z0 = df_add(z0, df_mul(r0, wd[1][py]));
+    }
+    gx = df_add(gx, df_mul(zx, wd[2][pz]));
+    gy = df_add(gy, df_mul(zy, wd[2][pz]));
+    gz = df_add(gz, df_mul(z0, dd[2][pz]));
+  }
+  const float invL = sc * inv_side;
+  far[i] = make_float4(__ldg(locc + t) + f, -(gx.h + gx.l) * invL, -(gy.h + gy.l) * invL, -(gz.h + gz.l) * invL);
+}
+
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
   const float y = x - c;
   const float t = s + y;
@@ -1204,7 +1306,7 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
     HPM_LAUNCHED(&launches);
   }
   record(pl, 5, st);
-  auto kg = ng == 4 ? k_g2p<4> : k_g2p<0>;
+  auto kg = ng == 4 ? k_g2p<4> : (ng == 6 ? k_g2p_df<6> : k_g2p_df<0>);
   kg<<<blocks_for(n), kThreads, 0, st>>>(n, t.pbox.as<int>(), t.box_tgt.as<int>(), lt, pl->tab,
                                             (float)(1.0 / pl->dom.side), t.box_key.as<uint64_t>(), hi, lo,
                                             s.loc.as<float>(), s.locc.as<float>(), s.far.as<float4>());
