@@ -109,7 +109,7 @@ enum {
   HPM_FLAG_XTRANSFORM_M2L = 4, /* Ng = 4: evaluate the convolution with the transform
                                   along x and direct (y, z) sums (Ng = 2, 3, 5, 6
                                   always do)                                          */
-  HPM_FLAG_FFT_M2L = 8         /* Ng = 4: evaluate the convolution by the FFT method of
+  HPM_FLAG_FFT_M2L = 8,        /* Ng = 4: evaluate the convolution by the FFT method of
                                   Sec. 2.1 (register FFT-32 kernel) instead of the
                                   default dense tensor-core product, which computes
                                   the same convolution over each parent's 6^3 block
@@ -117,6 +117,18 @@ enum {
                                   lo*hi of FP16 pairs; same result up to FP32
                                   rounding; needs 28.3 MB of device tables per level
                                   2..max_depth, built by hpm_plan)                   */
+  HPM_FLAG_EXTENDED_GRIDLET = 16 /* target gridlets widened by one node on each side
+                                  (Sec. 2.5): the source-to-target values are taken
+                                  at the (Ng + 2)^3 nodes x_j = (j + 1/2)/Ng - 1/2,
+                                  j = -1 .. Ng, which the (8 Ng)^3 convolution still
+                                  gives exactly (every node within 4 Ng = P/2 grid
+                                  points of every zone source), and the local
+                                  expansion is the degree-(Ng + 1) interpolant
+                                  through them; effective masses stay Ng^3. Uses
+                                  the any-order FFT-form kernel; Ng <= 6
+                                  (HPM_ERR_UNSUPPORTED above). Stage buffers of the
+                                  source-to-target and local values then hold
+                                  (Ng + 2)^3 values per target                       */
 };
 
 /*
@@ -264,7 +276,8 @@ hpm_status hpm_get_boxes(hpm_plan_t plan, int32_t *level, uint64_t *key, uint8_t
  *                     (Sec. 2.2 for leaves and virtual boxes, Sec. 2.3 for
  *                     internal cells)
  *   HPM_STAGE_M2L     source-to-target values of every target (cells at level
- *                     >= 2 in cell order), Ng^3 values then one constant per
+ *                     >= 2 in cell order), Ng^3 values ((Ng + 2)^3 with
+ *                     HPM_FLAG_EXTENDED_GRIDLET) then one constant per
  *                     target: Phi_p = row_p + const (Sec. 2.1)
  *   HPM_STAGE_LOCAL   local gridlet after the parent-to-child pass (Sec. 2.4),
  *                     same layout: deviations then one constant per target

@@ -71,12 +71,15 @@ void DevBuf::release(cudaStream_t s) {
   cap = 0;
 }
 
-// Gridlet constants (Sec. 2.2 nodes, Sec. 2.3 child-to-parent), FP64 -> FP32.
-static void make_tables(int ng, GridletTables &tb) {
+// Gridlet constants (Sec. 2.2 nodes, Sec. 2.3 child-to-parent), FP64 -> FP32,
+// for the Ng nodes x_j = (j + 1/2)/Ng - 1/2 widened by `ext` nodes of the same
+// spacing on each side (Sec. 2.5; ext = 0: the gridlet itself): tb.ng = Ng + 2 ext.
+static void make_tables(int ng0, int ext, GridletTables &tb) {
   memset(&tb, 0, sizeof(tb));
+  const int ng = ng0 + 2 * ext;
   tb.ng = ng;
   double x[kMaxNg];
-  for (int j = 0; j < ng; ++j) x[j] = (j + 0.5) / ng - 0.5;
+  for (int j = 0; j < ng; ++j) x[j] = (j - ext + 0.5) / ng0 - 0.5;
   for (int j = 0; j < ng; ++j) {
     double den = 1.0;
     for (int k = 0; k < ng; ++k)
@@ -166,6 +169,7 @@ hpm_status hpm_plan(const hpm_domain *dom, int max_depth, int gridlet_order, con
       return HPM_ERR_UNSUPPORTED;
   }
   if (opts && opts->leaf_max < 0) return HPM_ERR_INVALID_ARG;
+  if (opts && (opts->flags & HPM_FLAG_EXTENDED_GRIDLET) && gridlet_order + 2 > kMaxNg) return HPM_ERR_UNSUPPORTED;
   hpm_plan_s *pl = new (std::nothrow) hpm_plan_s();
   if (!pl) return HPM_ERR_OOM;
   pl->dom = *dom;
@@ -175,7 +179,10 @@ hpm_status hpm_plan(const hpm_domain *dom, int max_depth, int gridlet_order, con
   if (pl->green.kind == HPM_GREEN_NEWTON) pl->green.eps = 0.0;
   pl->opts = opts ? *opts : hpm_plan_opts{0, 0};
   cudaGetDevice(&pl->device);
-  make_tables(gridlet_order, pl->tab);
+  make_tables(gridlet_order, 0, pl->tab);
+  const int ext = (pl->opts.flags & HPM_FLAG_EXTENDED_GRIDLET) ? 1 : 0;
+  make_tables(gridlet_order, ext, pl->tab_loc);
+  pl->ng_loc = gridlet_order + 2 * ext;
   hpm_status s = precompute_green(pl, 0);
   if (s == HPM_OK) s = tc_precompute(pl, 0);
   if (s == HPM_OK) {
@@ -435,6 +442,7 @@ hpm_status hpm_get_stage(hpm_plan_t plan, int stage, float *h_out, int64_t count
   }
   if (stage == HPM_STAGE_M2L || stage == HPM_STAGE_LOCAL) {
     const int64_t nt = plan->ntgt;
+    const int64_t m3 = (int64_t)plan->ng_loc * plan->ng_loc * plan->ng_loc;  // target gridlet
     if (count < nt * (m3 + 1)) return HPM_ERR_INVALID_ARG;
     if (!nt) return HPM_OK;
     const DevBuf &v = stage == HPM_STAGE_M2L ? plan->s.m2l_raw : plan->s.loc;

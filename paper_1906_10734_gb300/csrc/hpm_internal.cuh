@@ -163,6 +163,10 @@ struct hpm_plan_s {
   hpm_plan_opts opts;
   int device;
   hpm::GridletTables tab;
+  // the target (local) gridlet: the same as tab, or with HPM_FLAG_EXTENDED_GRIDLET
+  // widened by one node on each side (ng_loc = ng + 2 nodes per axis)
+  hpm::GridletTables tab_loc;
+  int ng_loc = 0;
   // the kernel on the gridlet lattice, FP64, per level l: G_l[n] = g(h_l sqrt(n)),
   // n = 0 .. lattice_nmax(Ng) (G_l[0] = G_l[1]); glat_stride values per level
   hpm::DevBuf glat;

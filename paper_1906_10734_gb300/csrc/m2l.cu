@@ -524,7 +524,11 @@ __global__ void __launch_bounds__(Launch<NG>::threads, Launch<NG>::min_blocks)
 // ===========================================================================
 // Generic path, any Ng in 1..8: the same convolution done as separable
 // discrete Fourier sums per line with the same circular placement, one target
-// per block at a time, intermediate spectra in per-block global scratch.
+// per block at a time, intermediate spectra in per-block global scratch. The
+// inverse transforms are read at the target's nodes widened by `ext` on each
+// side (Sec. 2.5: ext = 1 with HPM_FLAG_EXTENDED_GRIDLET; those nodes are
+// within P/2 = 4 Ng grid points of every zone source, so the periodic images
+// do not reach them): positions -ext .. Ng - 1 + ext around the target's node 0.
 // ===========================================================================
 namespace gen {
 constexpr int kThreads = 256;
@@ -533,6 +537,7 @@ struct Params {
   TreeRefs r;
   Levels lt;
   int ng;
+  int ext;             // widening of the target gridlet, 0 or 1
   float2 *scratch;
   int64_t scratch_per_block;
 };
@@ -541,6 +546,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_generic(const __grid_constant_
   __shared__ float2 tw[64];
   __shared__ int blk[216];
   const int ng = pr.ng, P = 8 * ng, B = 6 * ng, H = P / 2 + 1, m3 = ng * ng * ng;
+  const int ext = pr.ext, ne = ng + 2 * ext, me = ne * ne * ne;  // target nodes per axis / in all
   for (int e = threadIdx.x; e < P; e += blockDim.x) {
     double s, c;
     sincospi(2.0 * e / P, &s, &c);
@@ -548,8 +554,8 @@ __global__ void __launch_bounds__(kThreads) k_m2l_generic(const __grid_constant_
   }
   float2 *X1 = pr.scratch + pr.scratch_per_block * blockIdx.x;  // [kx][z][y]   H*B*B
   float2 *X2 = X1 + (int64_t)H * B * B;                          // [kx][ky][z]  H*P*B
-  float2 *X4 = X2 + (int64_t)H * P * B;                          // [kx][ky][z'] H*P*ng
-  float2 *X5 = X4 + (int64_t)H * P * ng;                         // [kx][y'][z'] H*ng*ng
+  float2 *X4 = X2 + (int64_t)H * P * B;                          // [kx][ky][z'] H*P*ne
+  float2 *X5 = X4 + (int64_t)H * P * ne;                         // [kx][y'][z'] H*ne*ne
   __syncthreads();
   for (int64_t t = blockIdx.x; t < pr.r.ntgt; t += gridDim.x) {
     const int box = pr.r.tgt_box[t];
@@ -593,11 +599,11 @@ __global__ void __launch_bounds__(kThreads) k_m2l_generic(const __grid_constant_
       for (int z = 0; z < B; ++z) sum += X2[z].x;  // kx = ky = 0
       pr.r.outc[t] = -pr.r.gmean[lev] * sum;
     }
-    // z, Green product, inverse z to z' = 0..ng-1
+    // z, Green product, inverse z to z' = -ext .. ng - 1 + ext
     for (int64_t i = threadIdx.x; i < (int64_t)H * P; i += blockDim.x) {
       const int ky = (int)(i % P), kx = (int)(i / P);
       float2 acc[kMaxNg];
-      for (int q = 0; q < ng; ++q) acc[q] = make_float2(0.f, 0.f);
+      for (int q = 0; q < ne; ++q) acc[q] = make_float2(0.f, 0.f);
       const int kyr = ky <= P / 2 ? ky : P - ky;
       for (int kz = 0; kz < P; ++kz) {
         float2 s = make_float2(0.f, 0.f);
@@ -611,39 +617,39 @@ __global__ void __launch_bounds__(kThreads) k_m2l_generic(const __grid_constant_
         const float g = ghat[kx + H * (kyr + H * kzr)];
         s.x *= g;
         s.y *= g;
-        for (int q = 0; q < ng; ++q) {
-          const float2 c = tw[(kz * q) % P];
+        for (int q = 0; q < ne; ++q) {
+          const float2 c = tw[(kz * (q - ext + P)) % P];
           acc[q].x += s.x * c.x - s.y * c.y;
           acc[q].y += s.x * c.y + s.y * c.x;
         }
       }
-      for (int q = 0; q < ng; ++q) X4[i * ng + q] = acc[q];
+      for (int q = 0; q < ne; ++q) X4[i * ne + q] = acc[q];
     }
     __syncthreads();
-    // inverse y to y' = 0..ng-1
-    for (int64_t i = threadIdx.x; i < (int64_t)H * ng * ng; i += blockDim.x) {
-      const int zq = (int)(i % ng), yq = (int)((i / ng) % ng), kx = (int)(i / ((int64_t)ng * ng));
+    // inverse y to y' = -ext .. ng - 1 + ext
+    for (int64_t i = threadIdx.x; i < (int64_t)H * ne * ne; i += blockDim.x) {
+      const int zq = (int)(i % ne), yq = (int)((i / ne) % ne), kx = (int)(i / ((int64_t)ne * ne));
       float2 s = make_float2(0.f, 0.f);
       for (int ky = 0; ky < P; ++ky) {
-        const float2 v = X4[((int64_t)kx * P + ky) * ng + zq];
-        const float2 c = tw[(ky * yq) % P];
+        const float2 v = X4[((int64_t)kx * P + ky) * ne + zq];
+        const float2 c = tw[(ky * (yq - ext + P)) % P];
         s.x += v.x * c.x - v.y * c.y;
         s.y += v.x * c.y + v.y * c.x;
       }
       X5[i] = s;
     }
     __syncthreads();
-    // inverse x (complex to real) to x' = 0..ng-1
-    for (int p = threadIdx.x; p < m3; p += blockDim.x) {
-      const int xq = p % ng, yq = (p / ng) % ng, zq = p / (ng * ng);
+    // inverse x (complex to real) to x' = -ext .. ng - 1 + ext
+    for (int p = threadIdx.x; p < me; p += blockDim.x) {
+      const int xq = p % ne, yq = (p / ne) % ne, zq = p / (ne * ne);
       float s = 0.f;
       for (int kx = 0; kx < H; ++kx) {
-        const float2 v = X5[((int64_t)kx * ng + yq) * ng + zq];
-        const float2 c = tw[(kx * xq) % P];
+        const float2 v = X5[((int64_t)kx * ne + yq) * ne + zq];
+        const float2 c = tw[(kx * (xq - ext + P)) % P];
         const float re = v.x * c.x - v.y * c.y;
         s += (kx == 0 || 2 * kx == P) ? re : 2.f * re;
       }
-      pr.r.out[t * m3 + p] = s;
+      pr.r.out[t * me + p] = s;
     }
     __syncthreads();
   }
@@ -703,7 +709,8 @@ hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   for (int l = 0; l <= pl->max_depth + 1; ++l) lt.off[l] = pl->lvl_off[l];
   if (use_tc_m2l(pl)) return launch_m2l_tc(pl, st, launches);
   const int nsm = sm_count();
-  if (pl->ng == 4 && !(pl->opts.flags & (HPM_FLAG_GENERIC_M2L | HPM_FLAG_XTRANSFORM_M2L))) {
+  const bool extended = (pl->opts.flags & HPM_FLAG_EXTENDED_GRIDLET) != 0;  // any-order kernel only
+  if (pl->ng == 4 && !extended && !(pl->opts.flags & (HPM_FLAG_GENERIC_M2L | HPM_FLAG_XTRANSFORM_M2L))) {
     f4::Params p{};
     for (int e = 0; e < f4::kP; ++e) {
       const double a = -2.0 * M_PI * e / f4::kP;
@@ -730,7 +737,7 @@ hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   }
   const bool xd_order = pl->ng == 2 || pl->ng == 3 || pl->ng == 5 || pl->ng == 6 ||
                         (pl->ng == 4 && (pl->opts.flags & HPM_FLAG_XTRANSFORM_M2L));
-  if (!(pl->opts.flags & HPM_FLAG_GENERIC_M2L) && xd_order) {
+  if (!(pl->opts.flags & HPM_FLAG_GENERIC_M2L) && xd_order && !extended) {
     xd::Params p{};
     p.r = r;
     p.lt = lt;
@@ -757,9 +764,9 @@ hpm_status launch_m2l(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   p.r = r;
   p.lt = lt;
   p.ng = pl->ng;
-  const int P = 8 * pl->ng, B = 6 * pl->ng, H = P / 2 + 1;
-  p.scratch_per_block = (int64_t)H * B * B + (int64_t)H * P * B + (int64_t)H * P * pl->ng +
-                        (int64_t)H * pl->ng * pl->ng;
+  p.ext = extended ? 1 : 0;
+  const int P = 8 * pl->ng, B = 6 * pl->ng, H = P / 2 + 1, ne = pl->ng + 2 * p.ext;
+  p.scratch_per_block = (int64_t)H * B * B + (int64_t)H * P * B + (int64_t)H * P * ne + (int64_t)H * ne * ne;
   const int64_t grid = std::min<int64_t>(pl->ntgt, (int64_t)nsm);
   HPM_TRY(pl->s.m2l_scratch.ensure(sizeof(float2) * p.scratch_per_block * grid, st));
   p.scratch = pl->s.m2l_scratch.as<float2>();

@@ -927,7 +927,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
 
 bool use_tc_m2l(const hpm_plan_s *pl) {
   return (pl->ng == 4 || pl->ng == 6) &&
-         !(pl->opts.flags & (HPM_FLAG_GENERIC_M2L | HPM_FLAG_XTRANSFORM_M2L | HPM_FLAG_FFT_M2L));
+         !(pl->opts.flags &
+           (HPM_FLAG_GENERIC_M2L | HPM_FLAG_XTRANSFORM_M2L | HPM_FLAG_FFT_M2L | HPM_FLAG_EXTENDED_GRIDLET));
 }
 
 namespace {

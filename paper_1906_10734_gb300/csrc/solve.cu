@@ -1239,13 +1239,15 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
   pl->stats.p2p_pairs = pl->npairs;
   if (n == 0) return HPM_OK;
   const int ng = pl->ng, m3 = ng * ng * ng;
+  // target (local) gridlets: Ng^3 nodes, or (Ng + 2)^3 widened (Sec. 2.5)
+  const int ngl = pl->ng_loc, m3l = ngl * ngl * ngl;
   const int D = pl->max_depth;
   const int64_t off2 = D >= 2 ? pl->lvl_off[2] : pl->nbox;
   const int64_t nrow = pl->nbox - off2;
   HPM_TRY(t.spm.ensure(2 * sizeof(float4) * n, st));
   HPM_TRY(s.grid.ensure(sizeof(float) * m3 * (nrow > 0 ? nrow : 1), st));
-  HPM_TRY(s.loc.ensure(sizeof(float) * m3 * (pl->ntgt > 0 ? pl->ntgt : 1), st));
-  HPM_TRY(s.m2l_raw.ensure(sizeof(float) * m3 * (pl->ntgt > 0 ? pl->ntgt : 1), st));
+  HPM_TRY(s.loc.ensure(sizeof(float) * m3l * (pl->ntgt > 0 ? pl->ntgt : 1), st));
+  HPM_TRY(s.m2l_raw.ensure(sizeof(float) * m3l * (pl->ntgt > 0 ? pl->ntgt : 1), st));
   HPM_TRY(s.locc.ensure(sizeof(float) * (pl->ntgt > 0 ? pl->ntgt : 1), st));
   HPM_TRY(s.m2lc.ensure(sizeof(float) * (pl->ntgt > 0 ? pl->ntgt : 1), st));
   HPM_TRY(s.far.ensure(sizeof(float4) * n, st));
@@ -1291,23 +1293,23 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
   for (int l = 2; l <= pl->depth_reached; ++l) {
     const int64_t b = pl->tgt_lvl_off[l], e = pl->tgt_lvl_off[l + 1];
     if (e <= b) continue;
-    if (ng == 4) {
+    if (ngl == 4) {
       const int W = gridlet_warps(pl);
       auto kl = W == 2 ? k_l2l4<2> : (W == 4 ? k_l2l4<4> : k_l2l4<8>);
       kl<<<(unsigned)((e - b + W - 1) / W), W * 32, 0, st>>>(
-          b, e, l, pl->tab, t.tgt_box.as<int>(), t.box_tgt.as<int>(), t.box_parent.as<int>(),
+          b, e, l, pl->tab_loc, t.tgt_box.as<int>(), t.box_tgt.as<int>(), t.box_parent.as<int>(),
           t.box_key.as<uint64_t>(), s.m2l_raw.as<float>(), s.loc.as<float>(), s.locc.as<float>(),
           s.m2lc.as<float>());
     } else
       k_l2l_df<<<(unsigned)((e - b + kDfWarps - 1) / kDfWarps), 32 * kDfWarps, 0, st>>>(
-          b, e, l, pl->tab, t.tgt_box.as<int>(), t.box_tgt.as<int>(), t.box_parent.as<int>(),
+          b, e, l, pl->tab_loc, t.tgt_box.as<int>(), t.box_tgt.as<int>(), t.box_parent.as<int>(),
           t.box_key.as<uint64_t>(), s.m2l_raw.as<float>(), s.loc.as<float>(), s.locc.as<float>(),
           s.m2lc.as<float>());
     HPM_LAUNCHED(&launches);
   }
   record(pl, 5, st);
-  auto kg = ng == 4 ? k_g2p<4> : (ng == 6 ? k_g2p_df<6> : k_g2p_df<0>);
-  kg<<<blocks_for(n), kThreads, 0, st>>>(n, t.pbox.as<int>(), t.box_tgt.as<int>(), lt, pl->tab,
+  auto kg = ngl == 4 ? k_g2p<4> : (ngl == 6 ? k_g2p_df<6> : k_g2p_df<0>);
+  kg<<<blocks_for(n), kThreads, 0, st>>>(n, t.pbox.as<int>(), t.box_tgt.as<int>(), lt, pl->tab_loc,
                                             (float)(1.0 / pl->dom.side), t.box_key.as<uint64_t>(), hi, lo,
                                             s.loc.as<float>(), s.locc.as<float>(), s.far.as<float4>());
   HPM_LAUNCHED(&launches);

@@ -23,6 +23,7 @@ HPM_FLAG_TIMINGS = 1
 HPM_FLAG_GENERIC_M2L = 2
 HPM_FLAG_XTRANSFORM_M2L = 4
 HPM_FLAG_FFT_M2L = 8
+HPM_FLAG_EXTENDED_GRIDLET = 16
 HPM_STAGE_MASSES, HPM_STAGE_M2L, HPM_STAGE_LOCAL = 1, 2, 3
 
 # Every symbol include/hpm.h declares, with its ctypes signature.
@@ -289,11 +290,11 @@ def hpm_get_boxes(plan: int) -> dict:
     return out
 
 
-def hpm_get_stage(plan: int, stage: int, ng: int) -> np.ndarray:
-    """Stage buffer as float32: (rows, Ng^3) for masses; (targets, Ng^3 + 1) otherwise
-    (values then the constant)."""
+def hpm_get_stage(plan: int, stage: int, ng: int, ng_target: int | None = None) -> np.ndarray:
+    """Stage buffer as float32: (rows, Ng^3) for masses; (targets, Nt^3 + 1) otherwise
+    (values then the constant), Nt = ng_target (Ng + 2 for widened target gridlets)."""
     info = hpm_get_lists_info(plan)
-    m3 = ng ** 3
+    m3 = ng ** 3 if stage == HPM_STAGE_MASSES else (ng_target or ng) ** 3
     if stage == HPM_STAGE_MASSES:
         boxes = hpm_get_boxes(plan)
         rows = int(np.sum(boxes["level"] >= 2))
@@ -430,6 +431,7 @@ class Solver:
     def __init__(self, max_depth, gridlet_order=4, eps=0.0, leaf_max=0, origin=(0.0, 0.0, 0.0), side=1.0,
                  timings=False, flags=0, green: Green | None = None):
         self.ng = gridlet_order
+        self.ng_target = gridlet_order + (2 if flags & HPM_FLAG_EXTENDED_GRIDLET else 0)
         self.plan = hpm_plan(origin, side, max_depth, gridlet_order, eps, leaf_max,
                              (HPM_FLAG_TIMINGS if timings else 0) | flags, green)
 
@@ -451,7 +453,7 @@ class Solver:
         return hpm_get_boxes(self.plan)
 
     def stage(self, which):
-        return hpm_get_stage(self.plan, which, self.ng)
+        return hpm_get_stage(self.plan, which, self.ng, self.ng_target)
 
     def close(self):
         if self.plan:

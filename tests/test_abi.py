@@ -82,3 +82,12 @@ def test_plan_refuses_invalid_green_functions(lib):
     with pytest.raises(hpm.HpmError) as e:
         hpm.hpm_plan((0.0, 0.0, 0.0), 1.0, 3, 4, green=hpm.Green(7))
     assert e.value.status == -8
+
+
+def test_plan_refuses_widened_gridlets_above_order_6(lib):
+    """Widened target gridlets (Sec. 2.5) hold Ng + 2 nodes per axis, at most 8: Ng = 7
+    with HPM_FLAG_EXTENDED_GRIDLET is refused before any CUDA call."""
+    from paper_1906_10734_gb300 import hpm
+    with pytest.raises(hpm.HpmError) as e:
+        hpm.hpm_plan((0.0, 0.0, 0.0), 1.0, 3, 7, flags=hpm.HPM_FLAG_EXTENDED_GRIDLET)
+    assert e.value.status == -8

@@ -44,9 +44,11 @@ def variation_err(gpu_vals, ref_vals):
 
 def check_stages(H, w, flags=0, max_targets=None, seed=0, var_tol=1e-5, green=None, kernel=None):
     """Stage parity; `green` (library) and `kernel` (oracle) name another Green function
-    than the workload's Plummer softening."""
+    than the workload's Plummer softening. With HPM_FLAG_EXTENDED_GRIDLET the target
+    gridlets are compared at their (Ng + 2)^3 widened nodes."""
     g = run(H, w, flags, green)
     kern = kernel if kernel is not None else w.eps
+    ext = 1 if flags & H.HPM_FLAG_EXTENDED_GRIDLET else 0
     tr = O.Tree(w.pos, max_depth=w.max_depth, leaf_max=w.leaf_max)
     b = g["boxes"]
     sel = np.flatnonzero(b["level"] >= 2)
@@ -59,12 +61,12 @@ def check_stages(H, w, flags=0, max_targets=None, seed=0, var_tol=1e-5, green=No
     pick = np.arange(tl.shape[0])
     if max_targets and pick.size > max_targets:
         pick = np.sort(np.random.default_rng(seed).choice(pick.size, max_targets, replace=False))
-    m3 = w.ng ** 3
-    ref = O.m2l_values(tr, w.mass, w.ng, kern, tl[pick], tk[pick])
+    m3 = (w.ng + 2 * ext) ** 3
+    ref = O.m2l_values(tr, w.mass, w.ng, kern, tl[pick], tk[pick], ext=ext)
     got = g["m2l"][pick, :m3].astype(np.float64) + g["m2l"][pick, m3:].astype(np.float64)
     assert variation_err(got, ref) < var_tol
     assert O.rel_rms(got, ref) < 1e-6
-    ref = O.local_values(tr, w.mass, w.ng, kern, tl[pick], tk[pick])
+    ref = O.local_values(tr, w.mass, w.ng, kern, tl[pick], tk[pick], ext=ext)
     got = g["local"][pick, :m3].astype(np.float64) + g["local"][pick, m3:].astype(np.float64)
     assert variation_err(got, ref) < var_tol
     assert O.rel_rms(got, ref) < 1e-6
