@@ -52,6 +52,9 @@ constexpr int64_t scan_tiles_of(int64_t n) { return (n + kScanTileElems - 1) / k
 // sources per item).
 constexpr int64_t kP2PPairsPerItem = 16384;
 constexpr int kP2PMinSources = 32;
+// Leaves of more particles than this are split by targets instead (items of
+// 32 targets against all the leaf's near sources, no partial sums)
+constexpr int kP2PSplitTargets = 64;
 
 const char *set_cuda_error(cudaError_t e);
 
@@ -127,7 +130,9 @@ struct TreeDev {
   DevBuf tc_rows, tc_tgt;
   // near-field work items: each leaf's concatenated near sources split into
   // items of bounded pair count
-  DevBuf item_leaf, item_s0, item_s1, leaf_nitem, leaf_item0, leaf_part0;
+  // item_t: first target of a target-split item (32 targets), -1 for an item
+  // that covers all the leaf's targets
+  DevBuf item_leaf, item_s0, item_s1, item_t, leaf_nitem, leaf_item0, leaf_part0;
   DevBuf err;        // int error word
   DevBuf lvl_dev;    // box offsets per level on the device (int64, max_depth + 2)
   DevBuf offsets;    // problem offsets of a batched build (int64, nprob + 1)

@@ -808,8 +808,9 @@ __device__ __forceinline__ void pair_exact(const float4 &tr, const float4 &te, c
 // exact residual and index), so
 // the pair loop is one flat loop; floor(32 / nt) lanes share a target and split
 // the chunk; blocks of eight pairs are summed in plain FP32 and the block sums
-// are Kahan compensated. A leaf with one item writes far + near to the
-// caller's order; a leaf split over several items writes partial sums for
+// are Kahan compensated. A leaf with one item, and an item of a leaf split by
+// targets (32 of them against all near sources), writes far + near to the
+// caller's order; a leaf split over sources writes partial sums for
 // k_p2p_combine. Warps take items from a counter (zeroed before the launch) and
 // the grid holds as many blocks as are resident at once, so a warp whose item
 // ends early starts the next one instead of idling until its block retires.
@@ -818,6 +819,7 @@ constexpr int kP2PChunk = 128;
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *__restrict__ item_leaf,
                                                   const int *__restrict__ item_s0, const int *__restrict__ item_s1,
+                                                  const int *__restrict__ item_t,
                                                   const int *__restrict__ leaf_nitem,
                                                   const int *__restrict__ leaf_item0,
                                                   const int *__restrict__ leaf_part0,
@@ -864,6 +866,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
   __syncwarp();
   const int s0 = item_s0[it], s1 = item_s1[it];
   const int tb = beg[box], te = end[box], nt = te - tb;
+  // this item's targets: the whole leaf, or 32 of a leaf split by targets
+  const int tsel = item_t[it];
+  const int ta = tsel < 0 ? tb : tb + tsel, tz = tsel < 0 ? te : min(te, tb + tsel + 32), nti = tz - ta;
   // the target leaf's centre in unit-cube coordinates (exact in FP32)
   float cx0, cy0, cz0;
   {
@@ -874,7 +879,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
     cy0 = ((float)compact3(kk >> 1) + 0.5f) * inv;
     cz0 = ((float)compact3(kk >> 2) + 0.5f) * inv;
   }
-  const int G = nt >= 32 ? 1 : 32 / nt;
+  const int G = nti >= 32 ? 1 : 32 / nti;
   const int per = 32 / G;
   const int nitems = leaf_nitem[leaf];
   float near2;
@@ -883,10 +888,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
     near2 = nk.eps2 + side * side * (1.f / 64.f);  // r^2 of a pair 1/8 of the side apart
   }
   const int kidx = (int)(it - leaf_item0[leaf]);
-  for (int t0 = tb; t0 < te; t0 += per) {
+  for (int t0 = ta; t0 < tz; t0 += per) {
     const int slot = lane / G, sub = lane % G;
     const int ti = t0 + slot;
-    const bool active = slot < per && ti < te;
+    const bool active = slot < per && ti < tz;
     float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
     if (active) {
       const float4 h = hi[ti], q = lo[ti];
@@ -968,7 +973,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
         v.z += o.z;
         v.w += o.w;
       }
-      if (nitems == 1) {
+      if (nitems == 1 || tsel >= 0) {  // all of this target's near sources
         const float4 f = far[ti];
         const uint32_t o = perm[ti];
         if (out_phi) out_phi[o] = fmaf(v.x, sc_phi, f.x);
@@ -989,6 +994,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
 // Leaves whose near zone was split over several items: sum the items' partial
 // sums in item order (deterministic), add the far field, write the outputs.
 __global__ void __launch_bounds__(kThreads) k_p2p_combine(int64_t nleaf, const int *__restrict__ leaf_nitem,
+                                                          const int *__restrict__ leaf_item0,
+                                                          const int *__restrict__ item_t,
                                                           const int *__restrict__ leaf_part0,
                                                           const int *__restrict__ leaf_box,
                                                           const int *__restrict__ beg, const int *__restrict__ end,
@@ -1000,7 +1007,7 @@ __global__ void __launch_bounds__(kThreads) k_p2p_combine(int64_t nleaf, const i
   const int64_t leaf = (int64_t)blockIdx.x * kWarpsPerBlock + w;
   if (leaf >= nleaf) return;
   const int n = leaf_nitem[leaf];
-  if (n <= 1) return;
+  if (n <= 1 || item_t[leaf_item0[leaf]] >= 0) return;  // complete sums already written
   const int box = leaf_box[leaf];
   const int tb = beg[box], nt = end[box] - tb;
   const float4 *pp = part + leaf_part0[leaf];
@@ -1339,7 +1346,8 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
     HPM_CUDA(cudaMemsetAsync(s.work.p, 0, sizeof(unsigned long long), st));
     const unsigned p2p_grid = (unsigned)std::min<int64_t>(warp_blocks(pl->nitem), (int64_t)p2p_resident * sm_count());
     kp<<<p2p_grid, kThreads, 0, st>>>(
-        pl->nitem, t.item_leaf.as<int>(), t.item_s0.as<int>(), t.item_s1.as<int>(), t.leaf_nitem.as<int>(),
+        pl->nitem, t.item_leaf.as<int>(), t.item_s0.as<int>(), t.item_s1.as<int>(), t.item_t.as<int>(),
+        t.leaf_nitem.as<int>(),
         t.leaf_item0.as<int>(), t.leaf_part0.as<int>(), t.leaf_box.as<int>(), t.box_nb.as<int>(),
         t.box_beg.as<int>(), t.box_end.as<int>(), hi, lo, s.far.as<float4>(), t.perm.as<uint32_t>(),
         t.box_key.as<uint64_t>(), lt, nk, s1, s2, d_phi, d_acc, s.part.as<float4>(),
@@ -1347,7 +1355,7 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
     HPM_LAUNCHED(&launches);
     if (pl->npart > 0) {
       k_p2p_combine<<<warp_blocks(pl->nleaf), kThreads, 0, st>>>(
-          pl->nleaf, t.leaf_nitem.as<int>(), t.leaf_part0.as<int>(), t.leaf_box.as<int>(), t.box_beg.as<int>(),
+          pl->nleaf, t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(), t.item_t.as<int>(), t.leaf_part0.as<int>(), t.leaf_box.as<int>(), t.box_beg.as<int>(),
           t.box_end.as<int>(), s.part.as<float4>(), s.far.as<float4>(), t.perm.as<uint32_t>(), s1, s2, d_phi,
           d_acc);
       HPM_LAUNCHED(&launches);

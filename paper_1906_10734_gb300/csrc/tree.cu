@@ -573,6 +573,9 @@ __global__ void k_box_tgt(int64_t ntgt, const int *__restrict__ tgt_box, int *__
 
 // Near-field work per leaf: nt targets times ns near sources, split into
 // items of at most kP2PPairsPerItem pairs and at least kP2PMinSources sources.
+// A leaf of more than kP2PSplitTargets particles is split by targets instead:
+// one item per 32 targets, each against all ns sources, so no partial sums are
+// stored (a source split of such a leaf would need items * nt of them).
 __global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, const int *__restrict__ nb,
                             const int *__restrict__ beg, const int *__restrict__ end, int *__restrict__ nitem,
                             int *__restrict__ npart, unsigned long long *__restrict__ npairs) {
@@ -594,6 +597,12 @@ __global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, con
   for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
   if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(npairs, pairs);
   if (l >= nleaf) return;
+  if (nt > kP2PSplitTargets) {
+    // large leaf: items of 32 targets against all sources, complete sums
+    nitem[l] = (int)((nt + 31) / 32);
+    npart[l] = 0;
+    return;
+  }
   int64_t items = (nt * ns + kP2PPairsPerItem - 1) / kP2PPairsPerItem;
   const int64_t cap = (ns + kP2PMinSources - 1) / kP2PMinSources;
   if (items > cap) items = cap;
@@ -605,7 +614,8 @@ __global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, con
 __global__ void k_fill_items(int64_t nleaf, const int *__restrict__ leaf_box, const int *__restrict__ nb,
                              const int *__restrict__ beg, const int *__restrict__ end,
                              const int *__restrict__ nitem, const int *__restrict__ item0,
-                             int *__restrict__ item_leaf, int *__restrict__ item_s0, int *__restrict__ item_s1) {
+                             int *__restrict__ item_leaf, int *__restrict__ item_s0, int *__restrict__ item_s1,
+                             int *__restrict__ item_t) {
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= nleaf) return;
   const int box = leaf_box[l];
@@ -616,10 +626,12 @@ __global__ void k_fill_items(int64_t nleaf, const int *__restrict__ leaf_box, co
   }
   const int n = nitem[l];
   const int64_t i0 = item0[l];
+  const bool by_targets = end[box] - beg[box] > kP2PSplitTargets;
   for (int k = 0; k < n; ++k) {
     item_leaf[i0 + k] = (int)l;
-    item_s0[i0 + k] = (int)(ns * k / n);
-    item_s1[i0 + k] = (int)(ns * (k + 1) / n);
+    item_s0[i0 + k] = by_targets ? 0 : (int)(ns * k / n);
+    item_s1[i0 + k] = by_targets ? (int)ns : (int)(ns * (k + 1) / n);
+    item_t[i0 + k] = by_targets ? 32 * k : -1;
   }
 }
 
@@ -956,11 +968,12 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     HPM_TRY(t.item_leaf.ensure(sizeof(int) * (pl->nitem + 1), st));
     HPM_TRY(t.item_s0.ensure(sizeof(int) * (pl->nitem + 1), st));
     HPM_TRY(t.item_s1.ensure(sizeof(int) * (pl->nitem + 1), st));
+    HPM_TRY(t.item_t.ensure(sizeof(int) * (pl->nitem + 1), st));
     k_fill_items<<<blocks_for(nl), kThreads, 0, st>>>(nl, t.leaf_box.as<int>(), t.box_nb.as<int>(),
                                                       t.box_beg.as<int>(), t.box_end.as<int>(),
                                                       t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(),
                                                       t.item_leaf.as<int>(), t.item_s0.as<int>(),
-                                                      t.item_s1.as<int>());
+                                                      t.item_s1.as<int>(), t.item_t.as<int>());
     HPM_LAUNCHED(&launches);
   }
   // particle offsets of the P2G boxes (n + 1 entries, the last one the total)

@@ -149,6 +149,48 @@ def batch_problem(k: int, nmin: float = 1e3, nmax: float = 1e6, seed: int = 4,
                     ng=ng, eps=1e-4, meta={"kind": kind})
 
 
+def patch_grid_cells(geometry: str, k: int = 8) -> np.ndarray:
+    """Cell centres of a patch-based grid (the grid of the paper's accuracy test, Sec. 3.2):
+    the domain [0, 1)^3 is an oct-tree of patches of k^3 cells each.
+
+    ``uniform4`` / ``uniform5``: every patch at level 4 / 5 ((2^l k)^3 cells: 128^3, 256^3).
+    ``mixed``: level 3 everywhere, the first octant [0, 1/2)^3 refined to level 4 and the region
+    [1/8, 3/8)^3 refined to level 5 (720,896 cells). Cells are ordered patch by patch."""
+    levels = {"uniform4": [(4, (0.0, 1.0))], "uniform5": [(5, (0.0, 1.0))],
+              "mixed": [(3, (0.0, 1.0)), (4, (0.0, 0.5)), (5, (0.125, 0.375))]}[geometry]
+    # later entries refine earlier ones: a patch is kept where no finer one covers it
+    out = []
+    for idx, (lev, (lo, hi)) in enumerate(levels):
+        n = 1 << lev
+        c = (np.arange(n) + 0.5) / n
+        inside = (c > lo) & (c < hi)
+        pc = np.stack(np.meshgrid(c[inside], c[inside], c[inside], indexing="ij"), axis=-1).reshape(-1, 3)
+        keep = np.ones(pc.shape[0], dtype=bool)
+        for lev2, (lo2, hi2) in levels[idx + 1:]:
+            keep &= ~np.all((pc > lo2) & (pc < hi2), axis=1)
+        pc = pc[keep]
+        h = 1.0 / (n * k)
+        off = (np.arange(k) + 0.5) * h - 0.5 / n
+        cells = (pc[:, None, None, None, :] + np.stack(np.meshgrid(off, off, off, indexing="ij"), axis=-1)[None])
+        out.append(cells.reshape(-1, 3))
+    return np.concatenate(out)
+
+
+def point_source_patch_grid(geometry: str, ng: int = 4, k: int = 8) -> Workload:
+    """The accuracy test of Sec. 3.2 as particles: zero-mass particles at the cell centres of the
+    patch grid ``geometry`` (patch_grid_cells) and one unit mass at the corner (1, 1, 1) of the
+    domain, Newtonian kernel (eps = 0). A cell splits iff it holds more than k^3 + 1 particles,
+    so the tree's leaves are exactly the patches (the source adds one particle to the last
+    one). The source is particle 0."""
+    cells = patch_grid_cells(geometry, k)
+    pos = np.concatenate([np.ones((1, 3)), cells])
+    mass = np.zeros(pos.shape[0])
+    mass[0] = 1.0
+    depth = {"uniform4": 4, "uniform5": 5, "mixed": 5}[geometry]
+    return Workload(f"pointsource_{geometry}", pos, mass, max_depth=depth, leaf_max=k ** 3 + 1, ng=ng, eps=0.0,
+                    meta={"geometry": geometry, "source": 0})
+
+
 def small_plummer(n: int, seed: int, leaf_max: int = 32, max_depth: int = 12, ng: int = 4,
                   eps: float = 1e-4) -> Workload:
     """Reduced Plummer problem with the same recipe as the 2^21 workload."""
