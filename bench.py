@@ -507,7 +507,10 @@ def run_serve(args) -> None:
                    "seconds": args.serve_seconds},
         "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "mean": st["mean_ms"]},
         "offered_particles_per_s": offered / args.serve_seconds, "requests": st["completed"],
-        "batches": st["batches"], "clocks": clk.summary()}), flush=True)
+        "batches": st["batches"],
+        "admission": {"bytes_per_particle_measured": st["bytes_per_particle"],
+                      "estimate": "1.25 x measured bytes per particle x N + 1 MiB per request"},
+        "clocks": clk.summary()}), flush=True)
 
 
 def run_pointsource(args) -> None:

@@ -298,6 +298,12 @@ typedef struct {
                               multiplied (0 on the other paths)           */
   int64_t p2p_pairs;       /* near-zone pairs (i, j), j != i, summed by
                               the near field of the last solve            */
+  int64_t table_bytes;     /* device bytes of the plan's tables (Green
+                              transforms and lattice, W, near-field table),
+                              held from hpm_plan to hpm_destroy           */
+  int64_t work_bytes;      /* device bytes the last build and solve needed
+                              in the plan's other buffers (each buffer is
+                              kept at its largest size so far)            */
 } hpm_stats;
 
 hpm_status hpm_get_stats(hpm_plan_t plan, hpm_stats *stats);
@@ -321,6 +327,11 @@ typedef struct {
                               block-major (one pair of row blocks runs over every
                               tile first: that part of W stays in L2 while the
                               parents' gridlets stream); 0 = 1                   */
+  int m2l_tile_parents;    /* dense tensor-core source-to-target at Ng = 4:
+                              parents per tile (the MMA's N), 256, 224 or 192
+                              (0 = 256); a narrower tile spreads each level's
+                              parents over more CTA pairs. Applies from the
+                              next hpm_build_tree (the tiles are built there) */
 } hpm_tuning;
 
 /* Sets the plan's launch shapes (values outside the ranges above are
@@ -366,7 +377,16 @@ typedef struct {
                                requests but never runs them)                      */
   int max_batch;            /* requests per batch, >= 1                          */
   int64_t hbm_budget_bytes; /* admission bound on the estimated device memory of
-                               all batches in flight                              */
+                               all batches in flight; the worker plans' tables
+                               are outside it                                     */
+  double bytes_per_particle;/* the estimate's rate: a request of N particles is
+                               taken to need rate x N + 1 MiB. 0: calibrated,
+                               1.25 x the largest per-particle need measured on
+                               a completed batch (512 until the first one);
+                               > 0: this fixed rate. A queued request whose
+                               estimate exceeds the whole budget (after a
+                               recalibration) runs alone when nothing else is
+                               in flight                                          */
 } hpm_server_opts;
 
 /* One request. pos (N x 3 FP64) and mass (N FP64) are read, phi (N FP32) and
@@ -389,13 +409,16 @@ typedef struct {
                                last 65,536 completions                           */
   double mean_ms;           /* the same, over all completions since the last reset */
   double particles_per_s;   /* completed particles / (last completion - first submit) */
+  double bytes_per_particle;/* device bytes per particle that completed batches
+                               needed (largest seen; 0 before the first)        */
 } hpm_server_stats;
 
 /* Creates the worker plans (hpm_plan, synchronises) and starts the workers.
  * Errors: HPM_ERR_INVALID_ARG, and those of hpm_plan. */
 hpm_status hpm_server_create(const hpm_server_opts *opts, hpm_server_t *out);
 /* Queues a request; *ticket identifies it. A request whose estimated footprint
- * exceeds the whole budget is refused with HPM_ERR_OOM. Never blocks on the GPU. */
+ * (hpm_server_opts.bytes_per_particle) exceeds the whole budget is refused
+ * with HPM_ERR_OOM. Never blocks on the GPU. */
 hpm_status hpm_server_submit(hpm_server_t server, const hpm_request *req, uint64_t *ticket);
 /* *done: 1 finished, 0 pending, -1 cancelled or failed; latency in ms once done.
  * Once a call reports a final state (*done != 0) the server forgets the

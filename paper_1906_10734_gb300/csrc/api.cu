@@ -54,6 +54,7 @@ hpm_status lib_malloc_async(void **p, size_t bytes, cudaStream_t s) {
 }
 
 hpm_status DevBuf::ensure(size_t bytes, cudaStream_t s, bool keep) {
+  used = bytes;
   if (bytes <= cap && p) return HPM_OK;
   size_t ncap = bytes + bytes / 4 + 256;
   void *np = nullptr;
@@ -69,6 +70,7 @@ void DevBuf::release(cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
   p = nullptr;
   cap = 0;
+  used = 0;
 }
 
 // Gridlet constants (Sec. 2.2 nodes, Sec. 2.3 child-to-parent), FP64 -> FP32,
@@ -109,16 +111,41 @@ static void make_tables(int ng0, int ext, GridletTables &tb) {
   }
 }
 
-static void release_all(hpm_plan_s *pl, cudaStream_t s) {
-  DevBuf *bufs[] = {&pl->ghat, &pl->t.keys, &pl->t.keys_alt, &pl->t.perm, &pl->t.perm_alt, &pl->t.spm, &pl->t.pbox,
+// The plan's device buffers: first the plan-time tables (the Green
+// transforms and lattice, W and its exponents, the near-field table), then
+// the buffers of the tree build and the solve (the host_io ones stage
+// hpm_solve_host's and the batch's inputs and outputs on the device).
+constexpr int kPlanTables = 9;
+template <class F>
+static void for_each_buf(hpm_plan_s *pl, F &&f) {
+  DevBuf *bufs[] = {&pl->ghat, &pl->kx_green, &pl->kz_green, &pl->tc_w, &pl->tc_wexp, &pl->glat, &pl->near_tab,
+                    &pl->tc_mean, &pl->gmean,
+                    &pl->t.keys, &pl->t.keys_alt, &pl->t.perm, &pl->t.perm_alt, &pl->t.spm, &pl->t.pbox,
                     &pl->t.box_key, &pl->t.box_beg, &pl->t.box_end, &pl->t.box_parent, &pl->t.box_flags,
-                    &pl->t.box_child, &pl->t.box_nb, &pl->t.cnt, &pl->t.off, &pl->t.bnd, &pl->t.p2g_off, &pl->t.par_box, &pl->t.tgt_blk, &pl->t.tgt_info, &pl->kx_green, &pl->kz_green, &pl->tc_w, &pl->tc_wexp, &pl->glat, &pl->near_tab, &pl->tc_mean, &pl->t.tc_rows, &pl->t.tc_tgt, &pl->t.tgt_box,
+                    &pl->t.box_child, &pl->t.box_nb, &pl->t.cnt, &pl->t.off, &pl->t.bnd, &pl->t.p2g_off, &pl->t.par_box, &pl->t.tgt_blk, &pl->t.tgt_info, &pl->t.tc_rows, &pl->t.tc_tgt, &pl->t.tgt_box,
                     &pl->t.box_tgt, &pl->t.leaf_box, &pl->t.p2g_box, &pl->t.item_leaf, &pl->t.item_s0,
                     &pl->t.item_s1, &pl->t.item_t, &pl->t.leaf_nitem, &pl->t.leaf_item0, &pl->t.leaf_part0, &pl->s.part, &pl->t.err, &pl->t.lvl_dev, &pl->t.counters, &pl->t.scan_buf,
-                    &pl->s.grid, &pl->s.m2l_raw, &pl->s.loc, &pl->s.locc, &pl->s.m2lc, &pl->gmean, &pl->s.far, &pl->s.m2l_scratch, &pl->s.work, &pl->s.grid_hl, &pl->s.box_exp, &pl->s.box_mass, &pl->s.col_exp, &pl->s.zone_mass, &pl->s.level_amax,
-                    &pl->host_io_pos, &pl->host_io_mass, &pl->host_io_phi, &pl->host_io_acc, &pl->batch_desc,
-                    &pl->t.offsets};
-  for (DevBuf *b : bufs) b->release(s);
+                    &pl->s.grid, &pl->s.m2l_raw, &pl->s.loc, &pl->s.locc, &pl->s.m2lc, &pl->s.far, &pl->s.m2l_scratch, &pl->s.work, &pl->s.grid_hl, &pl->s.box_exp, &pl->s.box_mass, &pl->s.col_exp, &pl->s.zone_mass, &pl->s.level_amax,
+                    &pl->batch_desc, &pl->t.offsets,
+                    &pl->host_io_pos, &pl->host_io_mass, &pl->host_io_phi, &pl->host_io_acc};
+  constexpr int nb = (int)(sizeof(bufs) / sizeof(bufs[0]));
+  for (int i = 0; i < nb; ++i) f(bufs[i], i < kPlanTables ? 0 : 1);
+}
+
+static void release_all(hpm_plan_s *pl, cudaStream_t s) {
+  for_each_buf(pl, [s](DevBuf *b, int) { b->release(s); });
+}
+
+// Device bytes of the plan: its tables (held), and what the last build and
+// solve asked for in the per-input buffers.
+void plan_bytes(hpm_plan_s *pl, int64_t *tables, int64_t *work) {
+  int64_t t = 0, w = 0;
+  for_each_buf(pl, [&](DevBuf *b, int kind) {
+    if (kind == 0) t += (int64_t)b->cap;
+    else w += (int64_t)b->used;
+  });
+  *tables = t;
+  *work = w;
 }
 
 }  // namespace hpm
@@ -457,6 +484,7 @@ hpm_status hpm_get_stage(hpm_plan_t plan, int stage, float *h_out, int64_t count
 hpm_status hpm_get_stats(hpm_plan_t plan, hpm_stats *st) {
   if (!plan || !st) return HPM_ERR_INVALID_ARG;
   *st = plan->stats;
+  plan_bytes(plan, &st->table_bytes, &st->work_bytes);
   if (plan->events_ready) {
     HPM_CUDA(cudaEventSynchronize(plan->ev[7]));
     float v[8] = {0};

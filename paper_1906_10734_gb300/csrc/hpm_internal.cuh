@@ -82,6 +82,7 @@ hpm_status lib_malloc_async(void **p, size_t bytes, cudaStream_t s);
 struct DevBuf {
   void *p = nullptr;
   size_t cap = 0;
+  size_t used = 0;  // bytes the last ensure asked for (the need of the last call)
   hpm_status ensure(size_t bytes, cudaStream_t s, bool keep = false);
   void release(cudaStream_t s);
   template <class T> T *as() const { return static_cast<T *>(p); }
@@ -203,6 +204,7 @@ struct hpm_plan_s {
   hpm::DevBuf tc_mean;                // per target level and child: mean of row (o, 0)
   std::vector<double> tc_mean_host;
   int64_t tc_ntiles = 0;
+  int tc_tile_n = 256;  // parents per tile of the last tree build
   std::vector<int64_t> tc_tile_off;
   // tree
   hpm::TreeDev t;
@@ -276,6 +278,8 @@ hpm_status tc_build_tiles(hpm_plan_s *pl, const std::vector<int64_t> &par_per_le
 hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches);
 // block order of the dense source-to-target kernel: 1 tile-major, 2 row-block-major
 int m2l_block_order(const hpm_plan_s *pl);
+void plan_bytes(hpm_plan_s *pl, int64_t *tables, int64_t *work);
+int m2l_tile_parents(const hpm_plan_s *pl);
 }  // namespace hpm
 
 #define HPM_CUDA(call)                                  \

@@ -75,7 +75,7 @@ constexpr int kNoExp = 1 << 20;                 // exponent of a row without mas
 // per CTA (pairs of CTAs take consecutive blocks of one tile). Ng = 4: 4
 // chunks per slot, 864 per tile, 512 rows in 4 blocks; Ng = 6: 216 nodes in
 // 14 chunks, 3024 per tile, 1728 rows in 14 blocks (64 padding rows).
-template <int NG>
+template <int NG, int TN = (NG == 4 ? 256 : 128)>
 struct Cfg {
   // The tensor core's accumulation truncates: each MMA's sum is added to the
   // accumulator rounded toward zero, and the error grows with the number of
@@ -90,7 +90,11 @@ struct Cfg {
   // the FP32 additions of the drained blocks would dominate the error, so the
   // totals are compensated (two-sum errors gathered in bf16 terms), which
   // fits in registers for 64 columns per drain thread: 128 parents per tile.
-  static constexpr int kTileN = NG == 4 ? 256 : 128;
+  // At Ng = 4 the width is a launch shape (256, 224 or 192 parents): a
+  // narrower tile spreads a level's parents over more CTA pairs, which fills
+  // the last wave better when the tile count is just above a multiple of the
+  // pairs that fit; each column's K sum is the same whatever the width.
+  static constexpr int kTileN = TN;
   static constexpr bool kDfTotals = NG != 4;
   // K-chunks per pipeline stage: the stage's synchronisation (barrier waits
   // and commits of the issuing thread, a few hundred cycles) must stay below
@@ -101,6 +105,10 @@ struct Cfg {
   static constexpr int kStageABytes = kStageChunks * kABytes;   // W of a stage, one bulk copy
   static constexpr int kHalfN = kTileN / 2;                     // parents gathered by each CTA of a pair
   static constexpr int kCols = kTileN / 2;                      // columns per drain thread (2 warps per lane quadrant)
+  static constexpr int kColGroup = kCols % 32 == 0 ? 32 : 16;   // columns per tensor-memory load of the FP32 drain
+  // accumulator buffer x at tensor-memory column kAccStride x (the second
+  // buffer starts at column 256 for every width, as at 256 parents)
+  static constexpr int kAccStride = NG == 4 ? 256 : kTileN;
   static constexpr int kBBytes = kHalfN * kRowBytes;            // gathered tile of one K-chunk
   static constexpr int kStageBytes = kStageChunks * (kABytes + kBBytes);  // 4 W tiles, then 4 B tiles
   static constexpr int kStages = NG == 4 ? 3 : 2;               // 3 x 64 KB or 2 x 96 KB
@@ -112,8 +120,10 @@ struct Cfg {
   // tile's parents (each CTA's B rows are half of them).
   static constexpr uint32_t kIdesc =
       (1u << 4) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)((2 * kRows) >> 4) << 24);
-  static_assert(kTileN % 16 == 0 && kTileN <= 256 && 2 * kTileN <= 512, "MMA N and two accumulator buffers");
-  static_assert(kCols % 32 == 0 && kHalfN % 8 == 0, "drain column groups, gather groups");
+  static_assert(kTileN % 16 == 0 && kTileN <= 256 && kAccStride + kTileN <= 512, "MMA N and two accumulator buffers");
+  static_assert(kCols % kColGroup == 0 && kHalfN % 8 == 0, "drain column groups, gather groups");
+  static_assert(kBBytes % 512 == 0, "B tiles start on a 512-byte swizzle atom");
+  static_assert(NG == 4 || TN == 128, "the compensated drain holds 64 columns per thread");
   static_assert(kSmem <= 227 * 1024, "shared memory");
   static constexpr int kM3 = NG * NG * NG;                      // nodes per gridlet
   static constexpr int kCPS = (kM3 + kKC - 1) / kKC;            // K-chunks per source slot
@@ -290,6 +300,15 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
       "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
       "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
       HPM_W32(v)
+      : "memory");
+}
+// 32 lanes x 16 consecutive columns
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
       : "memory");
 }
 // 32 lanes x 8 consecutive columns
@@ -611,9 +630,9 @@ __global__ void k_col_exp(int64_t ntiles, int kTileN, const int *__restrict__ ro
   }
 }
 
-template <int NG>
+template <int NG, int TN>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ Params pr) {
-  using C = Cfg<NG>;
+  using C = Cfg<NG, TN>;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   // full: this CTA's stage landed; pfull (leader): the peer's stage landed;
@@ -664,7 +683,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
   __syncthreads();
   cluster_sync();  // tensor memory allocated in both CTAs before the first MMA
   tc_fence_after();
-  const uint32_t tbase = tmem_base;  // block b accumulates in columns kTileN (b & 1) ...
+  const uint32_t tbase = tmem_base;  // block b accumulates in columns kAccStride (b & 1) ...
 
   if (warp < kProdWarp0) {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsCtl));
@@ -718,7 +737,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
           // rows hold 16 hi then 16 lo values: hi*hi, hi*lo, lo*hi; the same
           // offsets in the peer CTA hold its 128 rows of W and 128 parents
           const uint32_t sa = su32(sm + st * C::kStageBytes), sb = sa + C::kStageABytes;
-          const uint32_t tacc = tbase + (uint32_t)C::kTileN * (uint32_t)x;
+          const uint32_t tacc = tbase + (uint32_t)C::kAccStride * (uint32_t)x;
 #pragma unroll
           for (int k = 0; k < C::kStageChunks; ++k) {
             const uint32_t a = sa + k * kABytes, bb = sb + k * C::kBBytes;
@@ -820,7 +839,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
     // (the exact rounding error of every addition to tot accumulates in a
     // bf16 compensation term, two columns per register: the total is
     // tot + compensation, several bits beyond FP32 for a few registers)
-    constexpr int kCols = C::kCols, kGroups = kCols / 32;
+    constexpr int kCols = C::kCols, kG = C::kColGroup, kGroups = kCols / kG;
     float tot[kCols];
     uint32_t comp[C::kDfTotals ? kCols / 2 : 1];
     if constexpr (C::kDfTotals) {
@@ -844,7 +863,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
 #pragma unroll
         for (int cc = 0; cc < kCols / 8; ++cc) {
           uint32_t a[8];
-          tmem_ld8(tbase + (uint32_t)C::kTileN * (uint32_t)x + lane_off + half * kCols + cc * 8, a);
+          tmem_ld8(tbase + (uint32_t)C::kAccStride * (uint32_t)x + lane_off + half * kCols + cc * 8, a);
           tmem_wait_ld();
 #pragma unroll
           for (int j = 0; j < 8; j += 2) {
@@ -865,15 +884,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
       } else {
 #pragma unroll
         for (int cc = 0; cc < kGroups; ++cc) {
-          uint32_t a[32];
-          tmem_ld32(tbase + (uint32_t)C::kTileN * (uint32_t)x + lane_off + half * kCols + cc * 32, a);
+          uint32_t a[kG];
+          const uint32_t ta = tbase + (uint32_t)C::kAccStride * (uint32_t)x + lane_off + half * kCols + cc * kG;
+          if constexpr (kG == 32) tmem_ld32(ta, a);
+          else tmem_ld16(ta, a);
           tmem_wait_ld();
           if (b == 0) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) tot[cc * 32 + j] = __uint_as_float(a[j]);
+            for (int j = 0; j < kG; ++j) tot[cc * kG + j] = __uint_as_float(a[j]);
           } else {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) tot[cc * 32 + j] = __uint_as_float(a[j]) + tot[cc * 32 + j];
+            for (int j = 0; j < kG; ++j) tot[cc * kG + j] = __uint_as_float(a[j]) + tot[cc * kG + j];
           }
         }
       }
@@ -894,14 +915,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
     if (ok && real_row) {
 #pragma unroll
       for (int cc = 0; cc < kGroups; ++cc) {
-        const int col = half * kCols + cc * 32;
+        const int col = half * kCols + cc * kG;
         const int *tg = pr.tgt + (tile * C::kTileN + col) * 8 + o;
         const int *ce = pr.col_exp + tile * C::kTileN + col;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < kG; ++j) {
           const int t_idx = __ldg(tg + j * 8);
           if (t_idx >= 0) {
-            const float v = (tot[cc * 32 + j] * pow2f(-e_row)) * pow2f(-__ldg(ce + j));
+            const float v = (tot[cc * kG + j] * pow2f(-e_row)) * pow2f(-__ldg(ce + j));
             if (node == 0) {
               pr.outc[t_idx] = (float)((double)v + pr.mean[lev][o] * (double)__ldg(pr.zone_mass + (tile * C::kTileN + col + j) * 8 + o));
               pr.out[(int64_t)t_idx * C::kM3] = 0.f;
@@ -985,9 +1006,9 @@ hpm_status tc_precompute_ng(hpm_plan_s *pl, cudaStream_t st) {
   return HPM_OK;
 }
 
-template <int NG>
+template <int NG, int TN>
 hpm_status launch_m2l_tc_ng(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
-  using C = tc::Cfg<NG>;
+  using C = tc::Cfg<NG, TN>;
   const int64_t off2 = pl->lvl_off[2], nrow = pl->nbox - off2;
   if (nrow <= 0) return HPM_OK;
   HPM_TRY(pl->s.grid_hl.ensure((size_t)nrow * C::kCPS * tc::kRowBytes, st));
@@ -1036,22 +1057,22 @@ hpm_status launch_m2l_tc_ng(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) 
   static DeviceCache attr_cache;
   int attr_ok = 0;
   HPM_TRY(device_cached(attr_cache, [](int *v) -> hpm_status {
-    HPM_CUDA(cudaFuncSetAttribute(tc::k_m2l_tc<NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+    HPM_CUDA(cudaFuncSetAttribute(tc::k_m2l_tc<NG, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
     // The drain warps raise their register count to kRegsHigh with registers
     // the other warpgroups give back; that only adds up if the kernel was
     // compiled with kLaunchRegs per thread. Never launch it otherwise.
     cudaFuncAttributes fa{};
-    HPM_CUDA(cudaFuncGetAttributes(&fa, tc::k_m2l_tc<NG>));
+    HPM_CUDA(cudaFuncGetAttributes(&fa, tc::k_m2l_tc<NG, TN>));
     if (fa.numRegs != tc::kLaunchRegs)
-      fprintf(stderr, "hpm: k_m2l_tc<%d> compiled with %d registers per thread, expected %d\n", NG, fa.numRegs,
-              tc::kLaunchRegs);
+      fprintf(stderr, "hpm: k_m2l_tc<%d, %d> compiled with %d registers per thread, expected %d\n", NG, TN,
+              fa.numRegs, tc::kLaunchRegs);
     *v = fa.numRegs == tc::kLaunchRegs ? 1 : 0;
     return HPM_OK;
   }, &attr_ok));
   if (!attr_ok) return HPM_ERR_UNSUPPORTED;
   const int64_t grid = pl->tc_ntiles * C::kQuarters;
   if (pl->events_ready) cudaEventRecord(pl->ev[10], st);
-  tc::k_m2l_tc<NG><<<(unsigned)grid, tc::kThreads, C::kSmem, st>>>(p);
+  tc::k_m2l_tc<NG, TN><<<(unsigned)grid, tc::kThreads, C::kSmem, st>>>(p);
   HPM_LAUNCHED(launches);
   if (pl->events_ready) cudaEventRecord(pl->ev[11], st);
   pl->stats.m2l_parents = pl->npar;
@@ -1059,6 +1080,12 @@ hpm_status launch_m2l_tc_ng(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) 
 }
 
 }  // namespace
+
+int m2l_tile_parents(const hpm_plan_s *pl) {
+  if (pl->ng != 4) return tc::Cfg<6>::kTileN;
+  const int t = pl->tuning.m2l_tile_parents;
+  return t == 224 || t == 192 ? t : 256;
+}
 
 int m2l_block_order(const hpm_plan_s *pl) {
   const int o = pl->tuning.m2l_block_order;
@@ -1076,7 +1103,8 @@ hpm_status tc_build_tiles(hpm_plan_s *pl, const std::vector<int64_t> &par_per_le
   pl->tc_tile_off.assign(kMaxDepth + 2, 0);
   if (!use_tc_m2l(pl)) return HPM_OK;
   const int D = pl->max_depth;
-  const int tile_n = pl->ng == 6 ? tc::Cfg<6>::kTileN : tc::Cfg<4>::kTileN;
+  const int tile_n = m2l_tile_parents(pl);  // the solve launches the kernel of this width
+  pl->tc_tile_n = tile_n;
   tc::TileLevels tl{};
   tl.nlev = D + 1;
   int64_t tiles = 0, pars = 0;
@@ -1106,7 +1134,12 @@ hpm_status tc_build_tiles(hpm_plan_s *pl, const std::vector<int64_t> &par_per_le
 
 hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   if (!pl->tc_ntiles) return HPM_OK;
-  return pl->ng == 6 ? launch_m2l_tc_ng<6>(pl, st, launches) : launch_m2l_tc_ng<4>(pl, st, launches);
+  if (pl->ng == 6) return launch_m2l_tc_ng<6, 128>(pl, st, launches);
+  switch (pl->tc_tile_n) {  // the width the tiles were built with
+    case 224: return launch_m2l_tc_ng<4, 224>(pl, st, launches);
+    case 192: return launch_m2l_tc_ng<4, 192>(pl, st, launches);
+    default: return launch_m2l_tc_ng<4, 256>(pl, st, launches);
+  }
 }
 
 }  // namespace hpm

@@ -3,7 +3,8 @@
 // Requests join a FIFO queue. Each worker thread owns a plan, a CUDA stream
 // and packed device buffers; when free it takes the longest prefix of the
 // queue that fits the batch limit and the device-memory budget (the estimated
-// footprint of every batch in flight counts against it), copies the requests'
+// footprint of every batch in flight counts against it; the estimate is
+// calibrated from the device bytes that completed batches needed), copies the requests'
 // particles into its packed buffers, builds one batched tree, solves, and
 // copies each request's results back. With two or more workers, a batch that
 // arrives while another is on the GPU is admitted as soon as memory allows and
@@ -29,7 +30,6 @@ using Clock = std::chrono::steady_clock;
 struct Request {
   uint64_t id = 0;
   hpm_request req{};
-  int64_t footprint = 0;
   Clock::time_point t_submit, t_done;
   int state = 0;  // 0 queued, 1 running, 2 done, -1 cancelled, -2 failed
   hpm_status status = HPM_OK;
@@ -68,6 +68,9 @@ struct hpm_server_s {
   std::condition_variable cv_idle;  // signalled when waiters drops to zero while stopping
   hpm::Clock::time_point t_first, t_last;
   bool any_done = false;
+  // device bytes per particle that completed batches needed (the largest
+  // seen; 0 until the first batch completes)
+  double bytes_per_particle = 0.0;
 };
 
 namespace hpm {
@@ -93,10 +96,20 @@ void release_request(hpm_server_s *sv, Request *r) {
   delete r;
 }
 
-// Device bytes a request needs while its batch runs: packed inputs and
-// outputs, keys and permutation (double buffered), sorted copies, and the
-// boxes, gridlets and locals of about one box per five particles.
-int64_t footprint_of(int64_t n) { return n * 512 + (1ll << 20); }
+// Device bytes a request of n particles needs while its batch runs: the
+// caller's fixed rate per particle, or else the largest per-particle need
+// measured on a completed batch (its plan's work buffers and the worker's
+// packed buffers over its particles) with a quarter in reserve for trees
+// denser in boxes than those seen so far; before any batch has completed,
+// 512 bytes per particle (packed inputs and outputs, keys and permutation
+// double buffered, sorted copies, and the boxes, gridlets and locals of
+// about one box per five particles). Plus 1 MiB.
+int64_t footprint_of(const hpm_server_s *sv, int64_t n) {
+  const double rate = sv->opts.bytes_per_particle > 0.0
+                          ? sv->opts.bytes_per_particle
+                          : (sv->bytes_per_particle > 0.0 ? 1.25 * sv->bytes_per_particle : 512.0);
+  return (int64_t)(rate * (double)n) + (1ll << 20);
+}
 
 void worker_loop(hpm_server_s *sv, Worker *w) {
   cudaSetDevice(sv->device);
@@ -110,7 +123,10 @@ void worker_loop(hpm_server_s *sv, Worker *w) {
         while (!sv->queue.empty() && sv->queue.front()->state == -1) sv->queue.pop_front();
         if (!sv->queue.empty()) {
           Request *r = sv->queue.front();
-          if (sv->inflight_bytes + r->footprint <= sv->opts.hbm_budget_bytes) break;
+          // a request over the whole budget (possible after a recalibration) runs alone
+          if (sv->inflight_bytes + footprint_of(sv, r->req.n) <= sv->opts.hbm_budget_bytes ||
+              sv->inflight_bytes == 0)
+            break;
         }
         sv->cv_work.wait(lk);
       }
@@ -120,10 +136,12 @@ void worker_loop(hpm_server_s *sv, Worker *w) {
           sv->queue.pop_front();
           continue;
         }
-        if (sv->inflight_bytes + bytes + r->footprint > sv->opts.hbm_budget_bytes) break;
+        const int64_t fp = footprint_of(sv, r->req.n);
+        if (sv->inflight_bytes + bytes + fp > sv->opts.hbm_budget_bytes && !(batch.empty() && sv->inflight_bytes == 0))
+          break;
         sv->queue.pop_front();
         r->state = 1;
-        bytes += r->footprint;
+        bytes += fp;
         batch.push_back(r);
       }
       sv->inflight_bytes += bytes;
@@ -163,9 +181,17 @@ void worker_loop(hpm_server_s *sv, Worker *w) {
     }
     if (cudaStreamSynchronize(w->stream) != cudaSuccess && s == HPM_OK) s = HPM_ERR_CUDA;
     const Clock::time_point now = Clock::now();
+    double need_pp = 0.0;
+    if (s == HPM_OK && n > 0) {
+      int64_t tables = 0, work = 0;
+      plan_bytes(w->plan, &tables, &work);
+      work += (int64_t)(w->pos.used + w->mass.used + w->phi.used + w->acc.used);
+      need_pp = (double)work / (double)n;
+    }
     {
       std::lock_guard<std::mutex> lk(sv->mu);
       sv->inflight_bytes -= bytes;
+      sv->bytes_per_particle = std::max(sv->bytes_per_particle, need_pp);
       for (Request *r : batch) {
         r->t_done = now;
         r->status = s;
@@ -206,7 +232,8 @@ extern "C" {
 hpm_status hpm_server_create(const hpm_server_opts *opts, hpm_server_t *out) {
   if (!opts || !out) return HPM_ERR_INVALID_ARG;
   *out = nullptr;
-  if (opts->workers < 0 || opts->workers > 16 || opts->max_batch < 1 || opts->hbm_budget_bytes <= 0)
+  if (opts->workers < 0 || opts->workers > 16 || opts->max_batch < 1 || opts->hbm_budget_bytes <= 0 ||
+      !(opts->bytes_per_particle >= 0.0))
     return HPM_ERR_INVALID_ARG;
   hpm_server_s *sv = new (std::nothrow) hpm_server_s();
   if (!sv) return HPM_ERR_OOM;
@@ -241,10 +268,9 @@ hpm_status hpm_server_submit(hpm_server_t sv, const hpm_request *req, uint64_t *
   Request *r = new (std::nothrow) Request();
   if (!r) return HPM_ERR_OOM;
   r->req = *req;
-  r->footprint = footprint_of(req->n);
   {
     std::lock_guard<std::mutex> lk(sv->mu);
-    if (r->footprint > sv->opts.hbm_budget_bytes) {
+    if (footprint_of(sv, req->n) > sv->opts.hbm_budget_bytes) {
       ++sv->rejected;
       delete r;
       return HPM_ERR_OOM;
@@ -327,6 +353,7 @@ hpm_status hpm_server_get_stats(hpm_server_t sv, hpm_server_stats *st) {
     if (r->state == 0) ++queued;
   st->queued = queued;
   st->in_flight_bytes = sv->inflight_bytes;
+  st->bytes_per_particle = sv->bytes_per_particle;
   st->particles = sv->particles_done;
   st->p50_ms = percentile(sv->latencies_ms, 0.50);
   st->p99_ms = percentile(sv->latencies_ms, 0.99);

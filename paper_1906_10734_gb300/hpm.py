@@ -94,7 +94,8 @@ class hpm_problem(ctypes.Structure):
 class hpm_server_opts(ctypes.Structure):
     _fields_ = [("dom", hpm_domain), ("max_depth", ctypes.c_int), ("gridlet_order", ctypes.c_int),
                 ("green", hpm_green), ("leaf_max", ctypes.c_int), ("workers", ctypes.c_int),
-                ("max_batch", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64)]
+                ("max_batch", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64),
+                ("bytes_per_particle", ctypes.c_double)]
 
 
 class hpm_request(ctypes.Structure):
@@ -105,7 +106,8 @@ class hpm_request(ctypes.Structure):
 class hpm_server_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "rejected", "cancelled", "failed",
                                               "batches", "queued", "in_flight_bytes", "particles")] + \
-               [(k, ctypes.c_double) for k in ("p50_ms", "p99_ms", "mean_ms", "particles_per_s")]
+               [(k, ctypes.c_double) for k in ("p50_ms", "p99_ms", "mean_ms", "particles_per_s",
+                                               "bytes_per_particle")]
 
 
 class hpm_lists_info(ctypes.Structure):
@@ -118,12 +120,14 @@ class hpm_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_float) for k in ("ms_tree", "ms_p2g", "ms_m2m", "ms_m2l", "ms_l2l", "ms_g2p",
                                               "ms_p2p", "ms_total")] + \
                [("launches", ctypes.c_int64), ("m2l_launches", ctypes.c_int64), ("m2l_targets", ctypes.c_int64),
-                ("ms_m2l_kernel", ctypes.c_float), ("m2l_parents", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64)]
+                ("ms_m2l_kernel", ctypes.c_float), ("m2l_parents", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
+                ("table_bytes", ctypes.c_int64), ("work_bytes", ctypes.c_int64)]
 
 
 class hpm_tuning(ctypes.Structure):
     _fields_ = [("level_blocks_per_sm", ctypes.c_int), ("gridlet_warps", ctypes.c_int),
-                ("m2l_ctas_per_sm", ctypes.c_int), ("m2l_block_order", ctypes.c_int)]
+                ("m2l_ctas_per_sm", ctypes.c_int), ("m2l_block_order", ctypes.c_int),
+                ("m2l_tile_parents", ctypes.c_int)]
 
 
 class hpm_alu_peaks(ctypes.Structure):
@@ -309,8 +313,9 @@ def hpm_get_stage(plan: int, stage: int, ng: int, ng_target: int | None = None) 
     return np.concatenate([vals, const[:, None]], axis=1)
 
 
-def hpm_set_tuning(plan: int, level_blocks_per_sm=0, gridlet_warps=0, m2l_ctas_per_sm=0, m2l_block_order=0):
-    t = hpm_tuning(level_blocks_per_sm, gridlet_warps, m2l_ctas_per_sm, m2l_block_order)
+def hpm_set_tuning(plan: int, level_blocks_per_sm=0, gridlet_warps=0, m2l_ctas_per_sm=0, m2l_block_order=0,
+                   m2l_tile_parents=0):
+    t = hpm_tuning(level_blocks_per_sm, gridlet_warps, m2l_ctas_per_sm, m2l_block_order, m2l_tile_parents)
     _check("hpm_set_tuning", load().hpm_set_tuning(plan, ctypes.byref(t)))
 
 
@@ -355,10 +360,12 @@ class Server:
     host numpy arrays or device tensors and must stay alive until it is done."""
 
     def __init__(self, max_depth=12, gridlet_order=4, eps=1e-4, leaf_max=32, workers=2, max_batch=64,
-                 hbm_budget_bytes=150 << 30, origin=(0.0, 0.0, 0.0), side=1.0, green: Green | None = None):
+                 hbm_budget_bytes=150 << 30, origin=(0.0, 0.0, 0.0), side=1.0, green: Green | None = None,
+                 bytes_per_particle=0.0):
         L = load()
         opts = hpm_server_opts(hpm_domain((ctypes.c_double * 3)(*origin), side), max_depth, gridlet_order,
-                               _green(eps, green), leaf_max, workers, max_batch, hbm_budget_bytes)
+                               _green(eps, green), leaf_max, workers, max_batch, hbm_budget_bytes,
+                               bytes_per_particle)
         h = _vp()
         _check("hpm_server_create", L.hpm_server_create(ctypes.byref(opts), ctypes.byref(h)))
         self.h = h.value

@@ -40,11 +40,24 @@ def test_shapes_keep_results_tensor_path(hpm):
     w = I.small_plummer(20000, 61, leaf_max=16)
     ref = solve_with(hpm, w, {})
     for shapes in (dict(level_blocks_per_sm=1), dict(level_blocks_per_sm=3), dict(level_blocks_per_sm=4),
-                   dict(gridlet_warps=2), dict(gridlet_warps=4), dict(m2l_block_order=2)):
+                   dict(gridlet_warps=2), dict(gridlet_warps=4), dict(m2l_block_order=2),
+                   dict(m2l_tile_parents=224), dict(m2l_tile_parents=192),
+                   dict(m2l_tile_parents=224, m2l_block_order=2)):
         assert_same(solve_with(hpm, w, shapes), ref)
     # Ng = 6 runs on the dense tensor-core path too
     ref6 = solve_with(hpm, w, {}, ng=6)
     assert_same(solve_with(hpm, w, dict(m2l_block_order=2), ng=6), ref6)
+
+
+def test_tile_widths_keep_results_over_many_tiles(hpm):
+    """Parents per tile of the Ng = 4 tensor-core kernel: with 2^18 Plummer particles the
+    deeper levels hold several tiles of every width and a ragged last tile; each parent's
+    sums are the same bit for bit."""
+    w = I.small_plummer(1 << 18, 65, leaf_max=32)
+    ref = solve_with(hpm, w, dict(m2l_tile_parents=256))
+    for tn in (224, 192):
+        assert_same(solve_with(hpm, w, dict(m2l_tile_parents=tn)), ref)
+        assert_same(solve_with(hpm, w, dict(m2l_tile_parents=tn, m2l_block_order=2)), ref)
 
 
 def test_shapes_keep_results_fft_paths(hpm):
@@ -65,6 +78,7 @@ def test_tune_picks_valid_shapes_and_keeps_results(hpm):
     assert t["level_blocks_per_sm"] in (1, 2, 3, 4)
     assert t["gridlet_warps"] in (2, 4, 8)
     assert t["m2l_block_order"] in (1, 2)
+    assert t["m2l_tile_parents"] in (256, 224, 192)
     assert hpm.hpm_get_tuning(s.plan) == t
     phi, acc = s(p, m)
     torch.cuda.synchronize()
@@ -75,7 +89,8 @@ def test_tune_picks_valid_shapes_and_keeps_results(hpm):
 def test_bad_shapes_are_refused(hpm):
     s = hpm.Solver(3, 4, 0.0, 0)
     for shapes in (dict(level_blocks_per_sm=5), dict(gridlet_warps=3), dict(m2l_ctas_per_sm=3),
-                   dict(level_blocks_per_sm=-1), dict(m2l_block_order=3)):
+                   dict(level_blocks_per_sm=-1), dict(m2l_block_order=3), dict(m2l_tile_parents=200),
+                   dict(m2l_tile_parents=512)):
         with pytest.raises(hpm.HpmError) as e:
             hpm.hpm_set_tuning(s.plan, **shapes)
         assert e.value.status == -1

@@ -122,8 +122,9 @@ def test_results_in_a_mix_equal_each_request_alone(hpm):
 @pytest.mark.gpu
 def test_budget_bounds_concurrency_and_all_requests_finish(hpm):
     ws = [I.batch_problem(k, 20000, 40000, 6) for k in range(6)]
-    # room for one request at a time: batches of one, served one after another
-    sv = hpm.Server(workers=2, max_batch=8, hbm_budget_bytes=40000 * 512 + (1 << 20) + 1)
+    # room for one request at a time at a fixed 512 bytes per particle: batches of
+    # one, served one after another
+    sv = hpm.Server(workers=2, max_batch=8, hbm_budget_bytes=40000 * 512 + (1 << 20) + 1, bytes_per_particle=512.0)
     bufs = [(np.ascontiguousarray(w.pos), np.ascontiguousarray(w.mass), np.zeros(w.n, np.float32),
              np.zeros((w.n, 3), np.float32)) for w in ws]
     ts = [sv.submit(*b) for b in bufs]
@@ -132,4 +133,61 @@ def test_budget_bounds_concurrency_and_all_requests_finish(hpm):
     st = sv.stats()
     sv.close()
     assert st["completed"] == 6 and st["batches"] == 6
+    assert all(np.abs(b[3]).sum() > 0 for b in bufs)
+
+
+@pytest.mark.gpu
+def test_admission_is_calibrated_from_measured_batches(hpm):
+    """With no fixed rate the server measures each completed batch's device need (its
+    plan's work buffers and packed buffers over its particles) and takes the largest;
+    a single-request batch needs what a plan solving that request alone reports."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    w = I.batch_problem(3, 50000, 50001, 7)
+    sv = hpm.Server(workers=1, max_batch=1)
+    b = (np.ascontiguousarray(w.pos), np.ascontiguousarray(w.mass), np.zeros(w.n, np.float32),
+         np.zeros((w.n, 3), np.float32))
+    assert sv.stats()["bytes_per_particle"] == 0.0
+    sv.wait(sv.submit(*b), 120000)
+    rate = sv.stats()["bytes_per_particle"]
+    sv.close()
+    s = hpm.Solver(w.max_depth, w.ng, w.eps, w.leaf_max)
+    s(torch.from_numpy(w.pos).to(dev), torch.from_numpy(w.mass).to(dev))
+    torch.cuda.synchronize()
+    st = hpm.hpm_get_stats(s.plan)
+    s.close()
+    packed = w.n * (24 + 8 + 4 + 12)
+    assert st["table_bytes"] > 0 and st["work_bytes"] > 0
+    # the batched build adds its problem-offset buffers to the single solve's need
+    assert (st["work_bytes"] + packed) / w.n <= rate < 1.5 * (st["work_bytes"] + packed) / w.n
+
+
+def test_admission_uses_a_fixed_rate(hpm):
+    """A caller's fixed rate replaces the calibrated estimate at submit (host logic,
+    no workers): 4096 bytes per particle puts 20,000 particles over a 64 MiB budget."""
+    sv = hpm.Server(workers=0, max_batch=4, hbm_budget_bytes=64 << 20, bytes_per_particle=4096.0)
+    with pytest.raises(hpm.HpmError) as e:
+        sv.submit(*host_request(20000, 1))   # 4096 x 20000 + 1 MiB > 64 MiB
+    assert e.value.status == -3
+    t = sv.submit(*host_request(10000, 2))
+    assert sv.poll(t)[0] == 0
+    sv.close()
+
+
+@pytest.mark.gpu
+def test_a_request_over_the_budget_after_calibration_runs_alone(hpm):
+    """Requests accepted under the 512-byte prior are not stranded when the first
+    batch's measurement raises the estimate above the whole budget: each runs alone
+    once nothing else is in flight."""
+    ws = [I.batch_problem(k, 30000, 30001, 8) for k in range(3)]
+    n = max(w.n for w in ws)
+    sv = hpm.Server(workers=1, max_batch=4, hbm_budget_bytes=512 * n + (1 << 20) + 1)
+    bufs = [(np.ascontiguousarray(w.pos), np.ascontiguousarray(w.mass), np.zeros(w.n, np.float32),
+             np.zeros((w.n, 3), np.float32)) for w in ws]
+    ts = [sv.submit(*b) for b in bufs]
+    for t in ts:
+        sv.wait(t, 120000)
+    st = sv.stats()
+    sv.close()
+    assert st["completed"] == 3 and st["batches"] == 3 and st["bytes_per_particle"] > 0
     assert all(np.abs(b[3]).sum() > 0 for b in bufs)
