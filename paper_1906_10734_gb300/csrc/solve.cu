@@ -728,16 +728,26 @@ struct NearKernel {
   const float4 *tab;  // form 2: per segment the cubic coefficients of g, then of the force factor
 };
 
+// 1 / sqrt(x) by the hardware approximation (rsqrt.approx, relative error
+// below 2^-22.9) with subnormal inputs flushed to zero: a squared pair
+// distance below 2^-126 of the domain side squared counts as 0 (the pair
+// coincides), which spares the subnormal rescaling of every pair.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // m g(r) and m F(r), F the force factor (a_i += m F (x_j - x_i)), of a pair at
 // squared distance r2 (softening included for forms 0 and 1).
 template <int KIND>
 __device__ __forceinline__ void pair_coef(const NearKernel &nk, float r2, float m, float &mg, float &mf) {
   if constexpr (KIND == 0) {
-    const float ir = rsqrtf(r2);
+    const float ir = rsqrt_ftz(r2);
     mg = m * ir;
     mf = mg * ir * ir;
   } else if constexpr (KIND == 1) {
-    const float ir = rsqrtf(r2);
+    const float ir = rsqrt_ftz(r2);
     const float sl = r2 * ir * nk.inv_lambda;  // s / lambda
     mg = m * ir * __expf(-sl);
     mf = mg * ir * ir * (1.f + sl);
@@ -787,7 +797,7 @@ __device__ __forceinline__ void pair_exact(const float4 &tr, const float4 &te, c
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, nk.eps2)));
   float mg, mf;
   if constexpr (KIND == 0) {
-    float ir = rsqrtf(r2);
+    float ir = rsqrt_ftz(r2);
     if (__float_as_int(e.w) == __float_as_int(te.w)) ir = 0.f;  // the target itself
     mg = s.w * ir;
     mf = mg * ir * ir;
@@ -805,8 +815,8 @@ __device__ __forceinline__ void pair_exact(const float4 &tr, const float4 &te, c
 // item is a leaf's targets against a contiguous part of the concatenation of
 // its near boxes' particles. The item's sources are staged in shared memory in
 // chunks (rounded position relative to the target leaf's centre and mass,
-// exact residual and index), so
-// the pair loop is one flat loop; floor(32 / nt) lanes share a target and split
+// exact residual and index; each source's range found from a bit mask of the
+// range starts in its 32-source window), so the pair loop is one flat loop; floor(32 / nt) lanes share a target and split
 // the chunk; blocks of eight pairs are summed in plain FP32 and the block sums
 // are Kahan compensated. A leaf with one item, and an item of a leaf split by
 // targets (32 of them against all near sources), writes far + near to the
@@ -831,8 +841,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
                                                   LevelTable lt, NearKernel nk, float sc_phi,
                                                   float sc_acc, float *__restrict__ out_phi, float *__restrict__ out_acc,
                                                   float4 *__restrict__ part, unsigned long long *__restrict__ next) {
-  __shared__ int rb[kWarpsPerBlock][28], cum[kWarpsPerBlock][28];
   __shared__ float4 red[kWarpsPerBlock][32];
+  __shared__ int2 rng[kWarpsPerBlock][27];
   __shared__ float4 srh[kWarpsPerBlock][kP2PChunk], srl[kWarpsPerBlock][kP2PChunk];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (;;) {
@@ -843,6 +853,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
   __syncwarp();
   const int leaf = item_leaf[it];
   const int box = leaf_box[leaf];
+  // the item's near boxes with particles, compacted: rng[w][k], k < nr, is
+  // the k-th one's first particle and the index of that particle in the
+  // concatenation of their particle ranges (strictly increasing in k)
+  int nr;
   {
     int b = 0, c = 0;
     if (lane < 27) {
@@ -858,12 +872,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
       const int t = __shfl_up_sync(0xffffffffu, inc, o);
       if (lane >= o) inc += t;
     }
-    if (lane < 28) {
-      rb[w][lane] = b;
-      cum[w][lane] = inc - c;  // exclusive prefix; cum[27] = total
-    }
+    const unsigned ne = __ballot_sync(0xffffffffu, c > 0);
+    nr = __popc(ne);
+    if (c > 0) rng[w][__popc(ne & ((1u << lane) - 1u))] = make_int2(b, inc - c);
+    __syncwarp();
   }
-  __syncwarp();
   const int s0 = item_s0[it], s1 = item_s1[it];
   const int tb = beg[box], te = end[box], nt = te - tb;
   // this item's targets: the whole leaf, or 32 of a leaf split by targets
@@ -908,12 +921,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
         float4 h[2], o[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-          const int q = c0 + min(k0 + lane + 32 * u, cn - 1);
-          int r = 0;  // range holding concatenated index q
-#pragma unroll
-          for (int step = 16; step >= 1; step >>= 1)
-            if (r + step < 28 && cum[w][r + step] <= q) r += step;
-          j[u] = rb[w][r] + (q - cum[w][r]);
+          // the range of concatenated index q = s + lane: the ranges that start
+          // before the window s ... s + 31, plus those starting in it up to q
+          const int s = c0 + k0 + 32 * u, q = s + lane;
+          const int ck = lane < nr ? rng[w][lane].y : 0x7fffffff;
+          const int before = __popc(__ballot_sync(0xffffffffu, ck < s));
+          const int d = ck - s;
+          const unsigned mask = __reduce_or_sync(0xffffffffu, d >= 0 && d < 32 ? 1u << d : 0u);
+          const int r = before - 1 + __popc(mask & (0xffffffffu >> (31 - lane)));
+          const int2 v = rng[w][r];
+          j[u] = q < c0 + cn ? v.x + (q - v.y) : v.x;
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
