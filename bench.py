@@ -509,7 +509,7 @@ def run_serve(args) -> None:
         "offered_particles_per_s": offered / args.serve_seconds, "requests": st["completed"],
         "batches": st["batches"],
         "admission": {"bytes_per_particle_measured": st["bytes_per_particle"],
-                      "estimate": "1.25 x measured bytes per particle x N + 1 MiB per request"},
+                      "estimate": "1.25 x measured bytes per particle x N + 8 MiB per request"},
         "clocks": clk.summary()}), flush=True)
 
 

@@ -303,7 +303,8 @@ typedef struct {
                               held from hpm_plan to hpm_destroy           */
   int64_t work_bytes;      /* device bytes the last build and solve needed
                               in the plan's other buffers (each buffer is
-                              kept at its largest size so far)            */
+                              kept at its largest size so far, so the plan
+                              may hold more)                              */
 } hpm_stats;
 
 hpm_status hpm_get_stats(hpm_plan_t plan, hpm_stats *stats);
@@ -380,9 +381,10 @@ typedef struct {
                                all batches in flight; the worker plans' tables
                                are outside it                                     */
   double bytes_per_particle;/* the estimate's rate: a request of N particles is
-                               taken to need rate x N + 1 MiB. 0: calibrated,
-                               1.25 x the largest per-particle need measured on
-                               a completed batch (512 until the first one);
+                               taken to need rate x N + 8 MiB. 0: calibrated,
+                               1.25 x the largest per-particle need beyond the
+                               8 MiB measured on a completed batch (512 until
+                               the first one);
                                > 0: this fixed rate. A queued request whose
                                estimate exceeds the whole budget (after a
                                recalibration) runs alone when nothing else is
@@ -409,8 +411,9 @@ typedef struct {
                                last 65,536 completions                           */
   double mean_ms;           /* the same, over all completions since the last reset */
   double particles_per_s;   /* completed particles / (last completion - first submit) */
-  double bytes_per_particle;/* device bytes per particle that completed batches
-                               needed (largest seen; 0 before the first)        */
+  double bytes_per_particle;/* device bytes per particle beyond 8 MiB that
+                               completed batches needed (largest seen; 0
+                               before the first)                                */
 } hpm_server_stats;
 
 /* Creates the worker plans (hpm_plan, synchronises) and starts the workers.

@@ -54,7 +54,7 @@ hpm_status lib_malloc_async(void **p, size_t bytes, cudaStream_t s) {
 }
 
 hpm_status DevBuf::ensure(size_t bytes, cudaStream_t s, bool keep) {
-  used = bytes;
+  used = std::max(used, bytes);
   if (bytes <= cap && p) return HPM_OK;
   size_t ncap = bytes + bytes / 4 + 256;
   void *np = nullptr;
@@ -136,8 +136,15 @@ static void release_all(hpm_plan_s *pl, cudaStream_t s) {
   for_each_buf(pl, [s](DevBuf *b, int) { b->release(s); });
 }
 
+// A tree build starts a new count of what the work buffers need.
+void reset_work_need(hpm_plan_s *pl) {
+  for_each_buf(pl, [](DevBuf *b, int kind) {
+    if (kind) b->used = 0;
+  });
+}
+
 // Device bytes of the plan: its tables (held), and what the last build and
-// solve asked for in the per-input buffers.
+// solve needed of the per-input buffers.
 void plan_bytes(hpm_plan_s *pl, int64_t *tables, int64_t *work) {
   int64_t t = 0, w = 0;
   for_each_buf(pl, [&](DevBuf *b, int kind) {

@@ -82,7 +82,7 @@ hpm_status lib_malloc_async(void **p, size_t bytes, cudaStream_t s);
 struct DevBuf {
   void *p = nullptr;
   size_t cap = 0;
-  size_t used = 0;  // bytes the last ensure asked for (the need of the last call)
+  size_t used = 0;  // the largest size asked for since the plan's last tree build began
   hpm_status ensure(size_t bytes, cudaStream_t s, bool keep = false);
   void release(cudaStream_t s);
   template <class T> T *as() const { return static_cast<T *>(p); }
@@ -279,6 +279,7 @@ hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches);
 // block order of the dense source-to-target kernel: 1 tile-major, 2 row-block-major
 int m2l_block_order(const hpm_plan_s *pl);
 void plan_bytes(hpm_plan_s *pl, int64_t *tables, int64_t *work);
+void reset_work_need(hpm_plan_s *pl);
 int m2l_tile_parents(const hpm_plan_s *pl);
 }  // namespace hpm
 

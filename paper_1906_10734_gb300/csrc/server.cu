@@ -96,19 +96,22 @@ void release_request(hpm_server_s *sv, Request *r) {
   delete r;
 }
 
-// Device bytes a request of n particles needs while its batch runs: the
-// caller's fixed rate per particle, or else the largest per-particle need
-// measured on a completed batch (its plan's work buffers and the worker's
-// packed buffers over its particles) with a quarter in reserve for trees
-// denser in boxes than those seen so far; before any batch has completed,
-// 512 bytes per particle (packed inputs and outputs, keys and permutation
-// double buffered, sorted copies, and the boxes, gridlets and locals of
-// about one box per five particles). Plus 1 MiB.
+// Device bytes a request of n particles needs while its batch runs: a rate
+// per particle times n plus kFixedBytes (per-level tiles of the dense
+// source-to-target kernel, counters, scan control: about 2.5 MB at depth 12).
+// The rate is the caller's, or else the largest per-particle need beyond
+// kFixedBytes measured on a completed batch (its plan's work buffers and the
+// worker's packed buffers) with a quarter in reserve for trees denser in
+// boxes than those seen so far; before any batch has completed, 512 bytes
+// (packed inputs and outputs, keys and permutation double buffered, sorted
+// copies, and the boxes, gridlets and locals of about one box per five
+// particles).
+constexpr int64_t kFixedBytes = 8ll << 20;
 int64_t footprint_of(const hpm_server_s *sv, int64_t n) {
   const double rate = sv->opts.bytes_per_particle > 0.0
                           ? sv->opts.bytes_per_particle
                           : (sv->bytes_per_particle > 0.0 ? 1.25 * sv->bytes_per_particle : 512.0);
-  return (int64_t)(rate * (double)n) + (1ll << 20);
+  return (int64_t)(rate * (double)n) + kFixedBytes;
 }
 
 void worker_loop(hpm_server_s *sv, Worker *w) {
@@ -153,6 +156,7 @@ void worker_loop(hpm_server_s *sv, Worker *w) {
     const int64_t n = off.back();
     hpm_status s = HPM_OK;
     const size_t nn = n > 0 ? (size_t)n : 1;
+    w->pos.used = w->mass.used = w->phi.used = w->acc.used = 0;  // this batch's need
     if (s == HPM_OK) s = w->pos.ensure(sizeof(double) * 3 * nn, w->stream);
     if (s == HPM_OK) s = w->mass.ensure(sizeof(double) * nn, w->stream);
     if (s == HPM_OK) s = w->phi.ensure(sizeof(float) * nn, w->stream);
@@ -186,7 +190,7 @@ void worker_loop(hpm_server_s *sv, Worker *w) {
       int64_t tables = 0, work = 0;
       plan_bytes(w->plan, &tables, &work);
       work += (int64_t)(w->pos.used + w->mass.used + w->phi.used + w->acc.used);
-      need_pp = (double)work / (double)n;
+      need_pp = std::max(0.0, (double)(work - kFixedBytes) / (double)n);
     }
     {
       std::lock_guard<std::mutex> lk(sv->mu);

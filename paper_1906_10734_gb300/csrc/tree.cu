@@ -707,6 +707,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   int64_t launches = 0;
   pl->built = false;
   pl->n = n;
+  reset_work_need(pl);
   // error words: [0] this build's, [1] the solves' (kept until reported)
   const bool fresh_err = t.err.p == nullptr;
   HPM_TRY(t.err.ensure(sizeof(int) * 4, st));
@@ -873,6 +874,17 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   }
   if (D == 0) pl->lvl_off[1] = nroot;  // the roots are the only boxes
   pl->nbox = pl->lvl_off[D + 1];
+  {
+    // what this build needed of the box arrays and the level scratch (their
+    // capacity was estimated beforehand, or kept from a larger build)
+    const size_t nb = (size_t)std::max<int64_t>(pl->nbox, 1);
+    t.box_key.used = sizeof(uint64_t) * nb;
+    t.box_beg.used = t.box_end.used = t.box_parent.used = sizeof(int) * nb;
+    t.box_flags.used = (nb + 15) & ~size_t(15);
+    t.box_child.used = sizeof(int) * 8 * nb;
+    t.box_nb.used = sizeof(int) * 27 * nb;
+    t.bnd.used = std::max<size_t>(sizeof(int) * 8 * nb, sizeof(int) * ((size_t)nprob + 1));
+  }
   {
     // child maps of the deepest level are never filled: mark them empty
     const int64_t b = pl->lvl_off[D], e = pl->lvl_off[D + 1];
