@@ -133,7 +133,7 @@ struct TreeDev {
   // items of bounded pair count
   // item_t: first target of a target-split item (32 targets), -1 for an item
   // that covers all the leaf's targets
-  DevBuf item_leaf, item_s0, item_s1, item_t, leaf_nitem, leaf_item0, leaf_part0;
+  DevBuf item_leaf, item_s0, item_s1, item_t, leaf_nitem, leaf_item0, leaf_part0, leaf_ns;
   DevBuf err;        // int error word
   DevBuf lvl_dev;    // box offsets per level on the device (int64, max_depth + 2)
   DevBuf offsets;    // problem offsets of a batched build (int64, nprob + 1)

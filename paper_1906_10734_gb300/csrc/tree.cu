@@ -578,7 +578,7 @@ __global__ void k_box_tgt(int64_t ntgt, const int *__restrict__ tgt_box, int *__
 // stored (a source split of such a leaf would need items * nt of them).
 __global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, const int *__restrict__ nb,
                             const int *__restrict__ beg, const int *__restrict__ end, int *__restrict__ nitem,
-                            int *__restrict__ npart, unsigned long long *__restrict__ npairs) {
+                            int *__restrict__ npart, int *__restrict__ nsrc, unsigned long long *__restrict__ npairs) {
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // near-zone pairs (i, j), j != i, of all leaves: the near field's work count
   unsigned long long pairs = 0;
@@ -597,6 +597,7 @@ __global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, con
   for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
   if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(npairs, pairs);
   if (l >= nleaf) return;
+  nsrc[l] = (int)ns;
   if (nt > kP2PSplitTargets) {
     // large leaf: items of 32 targets against all sources, complete sums
     nitem[l] = (int)((nt + 31) / 32);
@@ -611,7 +612,8 @@ __global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, con
   npart[l] = items > 1 ? (int)(items * nt) : 0;
 }
 
-__global__ void k_fill_items(int64_t nleaf, const int *__restrict__ leaf_box, const int *__restrict__ nb,
+// The items of each leaf (k_leaf_work's counts and near-source totals).
+__global__ void k_fill_items(int64_t nleaf, const int *__restrict__ leaf_box, const int *__restrict__ nsrc,
                              const int *__restrict__ beg, const int *__restrict__ end,
                              const int *__restrict__ nitem, const int *__restrict__ item0,
                              int *__restrict__ item_leaf, int *__restrict__ item_s0, int *__restrict__ item_s1,
@@ -619,11 +621,7 @@ __global__ void k_fill_items(int64_t nleaf, const int *__restrict__ leaf_box, co
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= nleaf) return;
   const int box = leaf_box[l];
-  int64_t ns = 0;
-  for (int k = 0; k < 27; ++k) {
-    const int q = nb[(int64_t)box * 27 + k];
-    if (q >= 0) ns += end[q] - beg[q];
-  }
+  const int64_t ns = nsrc[l];
   const int n = nitem[l];
   const int64_t i0 = item0[l];
   const bool by_targets = end[box] - beg[box] > kP2PSplitTargets;
@@ -943,10 +941,11 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     HPM_TRY(t.leaf_item0.ensure(sizeof(int) * (nl + 1), st));
     HPM_TRY(t.leaf_part0.ensure(sizeof(int) * (nl + 1), st));
     HPM_TRY(t.cnt.ensure(sizeof(int) * (nl + 1), st));
+    HPM_TRY(t.leaf_ns.ensure(sizeof(int) * (nl + 1), st));
     // counters[76..77]: the near-zone pair count (64 bits), zeroed with the others
     k_leaf_work<<<blocks_for(nl), kThreads, 0, st>>>(nl, t.leaf_box.as<int>(), t.box_nb.as<int>(),
                                                      t.box_beg.as<int>(), t.box_end.as<int>(),
-                                                     t.leaf_nitem.as<int>(), t.cnt.as<int>(),
+                                                     t.leaf_nitem.as<int>(), t.cnt.as<int>(), t.leaf_ns.as<int>(),
                                                      reinterpret_cast<unsigned long long *>(t.counters.as<int>() + 76));
     HPM_LAUNCHED(&launches);
     HPM_TRY(exclusive_scan_i32(t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(), nl, t.counters.as<int>() + 64,
@@ -981,7 +980,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     HPM_TRY(t.item_s0.ensure(sizeof(int) * (pl->nitem + 1), st));
     HPM_TRY(t.item_s1.ensure(sizeof(int) * (pl->nitem + 1), st));
     HPM_TRY(t.item_t.ensure(sizeof(int) * (pl->nitem + 1), st));
-    k_fill_items<<<blocks_for(nl), kThreads, 0, st>>>(nl, t.leaf_box.as<int>(), t.box_nb.as<int>(),
+    k_fill_items<<<blocks_for(nl), kThreads, 0, st>>>(nl, t.leaf_box.as<int>(), t.leaf_ns.as<int>(),
                                                       t.box_beg.as<int>(), t.box_end.as<int>(),
                                                       t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(),
                                                       t.item_leaf.as<int>(), t.item_s0.as<int>(),
