@@ -144,11 +144,16 @@ __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t n, int s
   cnt[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll 4
+  // all of the thread's keys in flight at once, then the counts
+  uint64_t k[kSortRounds];
+#pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
-    int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 0xff], 1);
+    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    k[r] = i < n ? keys[i] : 0;
   }
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r)
+    if (base + (int64_t)r * kSortThreads + threadIdx.x < n) atomicAdd(&cnt[(k[r] >> shift) & 0xff], 1);
   __syncthreads();
   hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
 }
@@ -202,11 +207,20 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   uint32_t vv[kWarpRounds];
   int rk[kWarpRounds];
   const int64_t wb = base + (int64_t)w * (kWarpRounds * 32);
+  // the warp's keys and values in flight at once (the ranking below orders
+  // its shared-memory counters with warp barriers, which loads do not cross)
 #pragma unroll
   for (int r = 0; r < kWarpRounds; ++r) {
     const int64_t i = wb + r * 32 + lane;
     const bool valid = i < n;
-    const uint64_t key = valid ? keys[i] : 0;
+    kk[r] = valid ? keys[i] : 0;
+    vv[r] = valid ? (vals ? vals[i] : (uint32_t)i) : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kWarpRounds; ++r) {
+    const int64_t i = wb + r * 32 + lane;
+    const bool valid = i < n;
+    const uint64_t key = kk[r];
     const int d = valid ? (int)((key >> shift) & 0xff) : kRadix;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const int leader = __ffs(peers) - 1, rank = __popc(peers & lt);
@@ -218,8 +232,6 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     old = __shfl_sync(0xffffffffu, old, leader);
     __syncwarp();
     rk[r] = old + rank;
-    kk[r] = key;
-    vv[r] = valid ? (vals ? vals[i] : (uint32_t)i) : 0u;
   }
   __syncthreads();
   {
