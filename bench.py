@@ -469,7 +469,8 @@ def run_serve(args) -> None:
                      torch.zeros((w.n, 3), dtype=torch.float32).pin_memory()))
     rng = np.random.default_rng(5)
     sv = hpm.Server(max_depth=12, gridlet_order=4, eps=1e-4, leaf_max=32, workers=args.workers,
-                    max_batch=args.max_batch, hbm_budget_bytes=150 << 30)
+                    max_batch=args.max_batch, hbm_budget_bytes=150 << 30,
+                    max_batch_particles=args.max_batch_particles)
 
     def drive(seconds):
         t0 = time.perf_counter()
@@ -504,6 +505,7 @@ def run_serve(args) -> None:
                                f"{args.pool} seeded payloads, Plummer or uniform), adaptive <=32/leaf, depth<=12, "
                                "gridlet 4^3, eps=1e-4, pinned host buffers in and out",
                    "workers": args.workers, "max_batch": args.max_batch, "hbm_budget_gb": 150,
+                   "max_batch_particles": args.max_batch_particles,
                    "seconds": args.serve_seconds},
         "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "mean": st["mean_ms"]},
         "offered_particles_per_s": offered / args.serve_seconds, "requests": st["completed"],
@@ -644,6 +646,8 @@ def main():
     ap.add_argument("--pool", type=int, default=32)
     ap.add_argument("--workers", type=int, default=2)
     ap.add_argument("--max-batch", type=int, default=32)
+    ap.add_argument("--max-batch-particles", type=int, default=1 << 20,
+                    help="serving: particles per batch; larger requests run alone, one at a time (0: FIFO)")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-warmup-s", type=float, default=3.0)
     ap.add_argument("--n", type=int, default=None, help="particles per problem (default 2^21)")

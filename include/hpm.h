@@ -389,6 +389,13 @@ typedef struct {
                                estimate exceeds the whole budget (after a
                                recalibration) runs alone when nothing else is
                                in flight                                          */
+  int64_t max_batch_particles;/* particles per batch (0: no bound, plain FIFO
+                               batches); a batch's solve time grows with its
+                               particles, and every request in it waits for all
+                               of them. A request larger than the bound is large:
+                               it runs alone, and one large request at a time;
+                               while one runs, small requests queued behind a
+                               waiting large one go ahead of it               */
 } hpm_server_opts;
 
 /* One request. pos (N x 3 FP64) and mass (N FP64) are read, phi (N FP32) and

@@ -55,6 +55,9 @@ constexpr int kP2PMinSources = 32;
 // Leaves of more particles than this are split by targets instead (items of
 // 32 targets against all the leaf's near sources, no partial sums)
 constexpr int kP2PSplitTargets = 64;
+// Leaves split over more items than this have their partial sums added by a
+// block each (lanes over items) instead of a warp each (lanes over targets)
+constexpr int kP2PCombineWarp = 32;
 
 const char *set_cuda_error(cudaError_t e);
 
@@ -133,7 +136,8 @@ struct TreeDev {
   // items of bounded pair count
   // item_t: first target of a target-split item (32 targets), -1 for an item
   // that covers all the leaf's targets
-  DevBuf item_leaf, item_s0, item_s1, item_t, leaf_nitem, leaf_item0, leaf_part0, leaf_ns;
+  // big_leaf: leaves split over more than kP2PCombineWarp items (order not fixed)
+  DevBuf item_leaf, item_s0, item_s1, item_t, leaf_nitem, leaf_item0, leaf_part0, leaf_ns, big_leaf;
   DevBuf err;        // int error word
   DevBuf lvl_dev;    // box offsets per level on the device (int64, max_depth + 2)
   DevBuf offsets;    // problem offsets of a batched build (int64, nprob + 1)
@@ -218,6 +222,7 @@ struct hpm_plan_s {
   int64_t nbox = 0, ntgt = 0, nleaf = 0, np2g = 0, ncell = 0;
   int64_t nitem = 0, npart = 0;   // near-field work items, partial-sum rows
   int64_t npairs = 0;              // near-zone pairs (i, j), j != i
+  int64_t nbig = 0;                // leaves split over more than kP2PCombineWarp items
   int64_t npar = 0;                // internal cells at levels >= 1 (parents of targets)
   std::vector<int64_t> tgt_lvl_off;  // target offsets per level (levels 2..D)
   std::vector<int64_t> leaf_lvl_off;

@@ -71,6 +71,7 @@ struct hpm_server_s {
   // device bytes per particle that completed batches needed (the largest
   // seen; 0 until the first batch completes)
   double bytes_per_particle = 0.0;
+  bool large_running = false;  // a request over the particle bound is on the GPU
 };
 
 namespace hpm {
@@ -114,40 +115,66 @@ int64_t footprint_of(const hpm_server_s *sv, int64_t n) {
   return (int64_t)(rate * (double)n) + kFixedBytes;
 }
 
+// Takes the next batch from the queue (caller holds the lock), or nothing if
+// no request can start now. Requests join in arrival order while they fit
+// the batch limit, the particle bound and the device-memory budget. A request
+// over the particle bound is large: it runs alone, and only while no other
+// large one runs (two on the GPU at once slow each other and everything
+// queued behind them); while one runs, the small requests behind a waiting
+// large one go ahead of it. A request over the whole memory budget (possible
+// after a recalibration) runs alone when nothing else is in flight.
+bool take_batch(hpm_server_s *sv, std::vector<Request *> &batch, int64_t &bytes, bool &large) {
+  const int64_t bound = sv->opts.max_batch_particles;
+  int64_t batch_n = 0;
+  bytes = 0;
+  large = false;
+  for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)batch.size() < sv->opts.max_batch;) {
+    Request *r = *it;
+    if (r->state == -1) {
+      it = sv->queue.erase(it);
+      continue;
+    }
+    const int64_t fp = footprint_of(sv, r->req.n);
+    const bool fits_mem = sv->inflight_bytes + bytes + fp <= sv->opts.hbm_budget_bytes ||
+                          (batch.empty() && sv->inflight_bytes == 0);
+    if (bound > 0 && r->req.n > bound) {
+      if (batch.empty() && !sv->large_running && fits_mem) {
+        it = sv->queue.erase(it);
+        r->state = 1;
+        bytes = fp;
+        batch.push_back(r);
+        large = true;
+        break;
+      }
+      if (!sv->large_running) break;  // it waits at the front for a free worker or memory
+      ++it;  // a large one runs: the small ones behind this one may go
+      continue;
+    }
+    if ((bound > 0 && !batch.empty() && batch_n + r->req.n > bound) || !fits_mem) break;
+    it = sv->queue.erase(it);
+    r->state = 1;
+    bytes += fp;
+    batch_n += r->req.n;
+    batch.push_back(r);
+  }
+  return !batch.empty();
+}
+
 void worker_loop(hpm_server_s *sv, Worker *w) {
   cudaSetDevice(sv->device);
   for (;;) {
     std::vector<Request *> batch;
     int64_t bytes = 0;
+    bool large = false;
     {
       std::unique_lock<std::mutex> lk(sv->mu);
       for (;;) {
         if (sv->stop) return;
-        while (!sv->queue.empty() && sv->queue.front()->state == -1) sv->queue.pop_front();
-        if (!sv->queue.empty()) {
-          Request *r = sv->queue.front();
-          // a request over the whole budget (possible after a recalibration) runs alone
-          if (sv->inflight_bytes + footprint_of(sv, r->req.n) <= sv->opts.hbm_budget_bytes ||
-              sv->inflight_bytes == 0)
-            break;
-        }
+        if (take_batch(sv, batch, bytes, large)) break;
         sv->cv_work.wait(lk);
       }
-      while (!sv->queue.empty() && (int)batch.size() < sv->opts.max_batch) {
-        Request *r = sv->queue.front();
-        if (r->state == -1) {
-          sv->queue.pop_front();
-          continue;
-        }
-        const int64_t fp = footprint_of(sv, r->req.n);
-        if (sv->inflight_bytes + bytes + fp > sv->opts.hbm_budget_bytes && !(batch.empty() && sv->inflight_bytes == 0))
-          break;
-        sv->queue.pop_front();
-        r->state = 1;
-        bytes += fp;
-        batch.push_back(r);
-      }
       sv->inflight_bytes += bytes;
+      if (large) sv->large_running = true;
       ++sv->batches;
     }
     // run the batch
@@ -195,6 +222,7 @@ void worker_loop(hpm_server_s *sv, Worker *w) {
     {
       std::lock_guard<std::mutex> lk(sv->mu);
       sv->inflight_bytes -= bytes;
+      if (large) sv->large_running = false;
       sv->bytes_per_particle = std::max(sv->bytes_per_particle, need_pp);
       for (Request *r : batch) {
         r->t_done = now;
@@ -237,7 +265,7 @@ hpm_status hpm_server_create(const hpm_server_opts *opts, hpm_server_t *out) {
   if (!opts || !out) return HPM_ERR_INVALID_ARG;
   *out = nullptr;
   if (opts->workers < 0 || opts->workers > 16 || opts->max_batch < 1 || opts->hbm_budget_bytes <= 0 ||
-      !(opts->bytes_per_particle >= 0.0))
+      !(opts->bytes_per_particle >= 0.0) || opts->max_batch_particles < 0)
     return HPM_ERR_INVALID_ARG;
   hpm_server_s *sv = new (std::nothrow) hpm_server_s();
   if (!sv) return HPM_ERR_OOM;

@@ -1024,7 +1024,8 @@ __global__ void __launch_bounds__(kThreads) k_p2p_combine(int64_t nleaf, const i
   const int64_t leaf = (int64_t)blockIdx.x * kWarpsPerBlock + w;
   if (leaf >= nleaf) return;
   const int n = leaf_nitem[leaf];
-  if (n <= 1 || item_t[leaf_item0[leaf]] >= 0) return;  // complete sums already written
+  // complete sums already written, or a leaf for k_p2p_combine_big
+  if (n <= 1 || n > kP2PCombineWarp || item_t[leaf_item0[leaf]] >= 0) return;
   const int box = leaf_box[leaf];
   const int tb = beg[box], nt = end[box] - tb;
   const float4 *pp = part + leaf_part0[leaf];
@@ -1045,6 +1046,66 @@ __global__ void __launch_bounds__(kThreads) k_p2p_combine(int64_t nleaf, const i
       out_acc[3 * (int64_t)o] = fmaf(sx - cx, s2, f.y);
       out_acc[3 * (int64_t)o + 1] = fmaf(sy - cy, s2, f.z);
       out_acc[3 * (int64_t)o + 2] = fmaf(sz - cz, s2, f.w);
+    }
+  }
+}
+
+__device__ __forceinline__ void two_sum_acc(float &s, float &e, float s2, float e2) {
+  const float t = s + s2, bp = t - s;
+  e = e + e2 + ((s - (t - bp)) + (s2 - bp));
+  s = t;
+}
+
+// Leaves split over more than kP2PCombineWarp items (a small leaf beside
+// large neighbour boxes, thousands of items): a block per leaf, a warp per
+// target; the lanes take the items lane-strided (Kahan) and their sums meet
+// in a fixed butterfly of two-sums (deterministic), lane 0 writing the output.
+__global__ void __launch_bounds__(kThreads) k_p2p_combine_big(const int *__restrict__ big,
+                                                              const int *__restrict__ leaf_nitem,
+                                                              const int *__restrict__ leaf_part0,
+                                                              const int *__restrict__ leaf_box,
+                                                              const int *__restrict__ beg,
+                                                              const int *__restrict__ end,
+                                                              const float4 *__restrict__ part,
+                                                              const float4 *__restrict__ far,
+                                                              const uint32_t *__restrict__ perm, float s1, float s2,
+                                                              float *__restrict__ out_phi,
+                                                              float *__restrict__ out_acc) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int leaf = big[blockIdx.x];
+  const int n = leaf_nitem[leaf];
+  const int box = leaf_box[leaf];
+  const int tb = beg[box], nt = end[box] - tb;
+  const float4 *pp = part + leaf_part0[leaf];
+  for (int t = w; t < nt; t += kWarpsPerBlock) {
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = lane; k < n; k += 32) {
+      const float4 v = pp[(int64_t)k * nt + t];
+      kahan_add(s[0], c[0], v.x);
+      kahan_add(s[1], c[1], v.y);
+      kahan_add(s[2], c[2], v.z);
+      kahan_add(s[3], c[3], v.w);
+    }
+    float e[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      e[q] = -c[q];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, s[q], off), eo = __shfl_xor_sync(0xffffffffu, e[q], off);
+        two_sum_acc(s[q], e[q], so, eo);
+      }
+    }
+    if (lane == 0) {
+      const int ti = tb + t;
+      const float4 f = far[ti];
+      const uint32_t o = perm[ti];
+      if (out_phi) out_phi[o] = fmaf(s[0] + e[0], s1, f.x);
+      if (out_acc) {
+        out_acc[3 * (int64_t)o] = fmaf(s[1] + e[1], s2, f.y);
+        out_acc[3 * (int64_t)o + 1] = fmaf(s[2] + e[2], s2, f.z);
+        out_acc[3 * (int64_t)o + 2] = fmaf(s[3] + e[3], s2, f.w);
+      }
     }
   }
 }
@@ -1375,6 +1436,13 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
           pl->nleaf, t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(), t.item_t.as<int>(), t.leaf_part0.as<int>(), t.leaf_box.as<int>(), t.box_beg.as<int>(),
           t.box_end.as<int>(), s.part.as<float4>(), s.far.as<float4>(), t.perm.as<uint32_t>(), s1, s2, d_phi,
           d_acc);
+      HPM_LAUNCHED(&launches);
+    }
+    if (pl->nbig > 0) {
+      k_p2p_combine_big<<<(unsigned)pl->nbig, kThreads, 0, st>>>(
+          t.big_leaf.as<int>(), t.leaf_nitem.as<int>(), t.leaf_part0.as<int>(), t.leaf_box.as<int>(),
+          t.box_beg.as<int>(), t.box_end.as<int>(), s.part.as<float4>(), s.far.as<float4>(),
+          t.perm.as<uint32_t>(), s1, s2, d_phi, d_acc);
       HPM_LAUNCHED(&launches);
     }
   }

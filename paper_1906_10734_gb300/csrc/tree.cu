@@ -334,12 +334,41 @@ __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
   for (int l = 1; l <= a.depth; ++l) {
     // 1. boundaries, counts, block-local offsets
     const int64_t m = pe - pb;
-    const int64_t chunk = ((m + gridDim.x - 1) / gridDim.x + 31) & ~int64_t(31);
+    // a level of at most one box per block (the top of the tree, where the
+    // boxes are large): one box per block, one octant per warp, each warp a
+    // 32-ary search (log33 of the box's particles rounds of loads instead of
+    // log2); otherwise runs of boxes per block, binary searches per thread
+    const bool warp_search = m <= (int64_t)gridDim.x;
+    const int64_t chunk = warp_search ? 1 : ((m + gridDim.x - 1) / gridDim.x + 31) & ~int64_t(31);
     const int64_t r0 = min((int64_t)blockIdx.x * chunk, m), r1 = min(r0 + chunk, m);
     const int shift = 3 * (a.depth - l);
     {
+      static_assert(kThreads / 32 == 8, "one warp per octant");
+      if (warp_search && r0 < r1) {
+        const int64_t i = pb + r0;
+        const int oct = wid;
+        int lo = a.beg[i], hi = lo;
+        uint64_t kc = 0;
+        if (oct > 0 && (a.flags[i] & kExpand)) {
+          hi = a.end[i];
+          kc = (a.key[i] << 3) | (uint64_t)oct;
+        }
+        // first particle of the box at or after octant `oct`: keys in [lo, hi)
+        // are sorted, so the probes below kc are a prefix of the lanes
+        while (hi - lo > 32) {
+          const int p = lo + (int)((int64_t)(lane + 1) * (hi - lo) / 33);
+          const unsigned below = __ballot_sync(0xffffffffu, (a.skeys[p] >> shift) < kc);
+          const int c = __popc(below);
+          const int plo = __shfl_sync(0xffffffffu, p, c > 0 ? c - 1 : 0), phi = __shfl_sync(0xffffffffu, p, c < 32 ? c : 31);
+          if (c > 0) lo = plo + 1;
+          if (c < 32) hi = phi;
+        }
+        const bool lt = lane < hi - lo && (a.skeys[lo + lane] >> shift) < kc;
+        const int b0 = lo + __popc(__ballot_sync(0xffffffffu, lt));
+        if (lane == 0) a.bnd[r0 * 8 + oct] = b0;
+      }
       // (box, octant) items of this block: 4 binary searches in lockstep per thread
-      const int64_t nit = 8 * (r1 - r0);
+      const int64_t nit = warp_search ? 0 : 8 * (r1 - r0);
       for (int64_t t0 = tid; t0 < nit; t0 += 4 * kThreads) {
         int lo[4], hi[4];
         uint64_t kc[4];
@@ -578,7 +607,8 @@ __global__ void k_box_tgt(int64_t ntgt, const int *__restrict__ tgt_box, int *__
 // stored (a source split of such a leaf would need items * nt of them).
 __global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, const int *__restrict__ nb,
                             const int *__restrict__ beg, const int *__restrict__ end, int *__restrict__ nitem,
-                            int *__restrict__ npart, int *__restrict__ nsrc, unsigned long long *__restrict__ npairs) {
+                            int *__restrict__ npart, int *__restrict__ nsrc, int *__restrict__ big,
+                            int *__restrict__ nbig, unsigned long long *__restrict__ npairs) {
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // near-zone pairs (i, j), j != i, of all leaves: the near field's work count
   unsigned long long pairs = 0;
@@ -610,6 +640,7 @@ __global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, con
   if (items < 1) items = 1;
   nitem[l] = (int)items;
   npart[l] = items > 1 ? (int)(items * nt) : 0;
+  if (items > kP2PCombineWarp) big[atomicAdd(nbig, 1)] = (int)l;
 }
 
 // The items of each leaf (k_leaf_work's counts and near-source totals).
@@ -619,17 +650,39 @@ __global__ void k_fill_items(int64_t nleaf, const int *__restrict__ leaf_box, co
                              int *__restrict__ item_leaf, int *__restrict__ item_s0, int *__restrict__ item_s1,
                              int *__restrict__ item_t) {
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= nleaf) return;
-  const int box = leaf_box[l];
-  const int64_t ns = nsrc[l];
-  const int n = nitem[l];
-  const int64_t i0 = item0[l];
-  const bool by_targets = end[box] - beg[box] > kP2PSplitTargets;
-  for (int k = 0; k < n; ++k) {
-    item_leaf[i0 + k] = (int)l;
-    item_s0[i0 + k] = by_targets ? 0 : (int)(ns * k / n);
-    item_s1[i0 + k] = by_targets ? (int)ns : (int)(ns * (k + 1) / n);
-    item_t[i0 + k] = by_targets ? 32 * k : -1;
+  const int lane = threadIdx.x & 31;
+  const bool valid = l < nleaf;
+  int64_t ns = 0, i0 = 0;
+  int n = 0;
+  bool by_targets = false;
+  if (valid) {
+    const int box = leaf_box[l];
+    ns = nsrc[l];
+    n = nitem[l];
+    i0 = item0[l];
+    by_targets = end[box] - beg[box] > kP2PSplitTargets;
+  }
+  // item k of a leaf: its targets (all, or 32 from 32 k) and its part of the
+  // concatenated near sources
+  auto put = [&](int64_t leaf, int64_t base, int nn, int64_t nsrc_l, bool bt, int k) {
+    item_leaf[base + k] = (int)leaf;
+    item_s0[base + k] = bt ? 0 : (int)(nsrc_l * k / nn);
+    item_s1[base + k] = bt ? (int)nsrc_l : (int)(nsrc_l * (k + 1) / nn);
+    item_t[base + k] = bt ? 32 * k : -1;
+  };
+  // most leaves have one item or a few; a leaf with many (a small leaf beside
+  // large neighbour boxes) is written by the whole warp
+  if (valid && n <= 4)
+    for (int k = 0; k < n; ++k) put(l, i0, n, ns, by_targets, k);
+  unsigned many = __ballot_sync(0xffffffffu, valid && n > 4);
+  while (many) {
+    const int src = __ffs(many) - 1;
+    many &= many - 1;
+    const int64_t lb = __shfl_sync(0xffffffffu, l, src), ib = __shfl_sync(0xffffffffu, i0, src),
+                  nsb = __shfl_sync(0xffffffffu, ns, src);
+    const int nb = __shfl_sync(0xffffffffu, n, src);
+    const bool bt = __shfl_sync(0xffffffffu, by_targets, src);
+    for (int k = lane; k < nb; k += 32) put(lb, ib, nb, nsb, bt, k);
   }
 }
 
@@ -720,7 +773,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   pl->lvl_off.assign(D + 2, 0);
   pl->depth_reached = -1;
   pl->nbox = pl->ntgt = pl->nleaf = pl->np2g = pl->ncell = 0;
-  pl->nitem = pl->npart = 0;
+  pl->nitem = pl->npart = pl->nbig = 0;
   pl->npar = 0;
   pl->tgt_lvl_off.assign(D + 2, 0);
   pl->leaf_lvl_off.assign(D + 2, 0);
@@ -942,18 +995,20 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     HPM_TRY(t.leaf_part0.ensure(sizeof(int) * (nl + 1), st));
     HPM_TRY(t.cnt.ensure(sizeof(int) * (nl + 1), st));
     HPM_TRY(t.leaf_ns.ensure(sizeof(int) * (nl + 1), st));
+    HPM_TRY(t.big_leaf.ensure(sizeof(int) * (nl + 1), st));
     // counters[76..77]: the near-zone pair count (64 bits), zeroed with the others
     k_leaf_work<<<blocks_for(nl), kThreads, 0, st>>>(nl, t.leaf_box.as<int>(), t.box_nb.as<int>(),
                                                      t.box_beg.as<int>(), t.box_end.as<int>(),
                                                      t.leaf_nitem.as<int>(), t.cnt.as<int>(), t.leaf_ns.as<int>(),
+                                                     t.big_leaf.as<int>(), t.counters.as<int>() + 78,
                                                      reinterpret_cast<unsigned long long *>(t.counters.as<int>() + 76));
     HPM_LAUNCHED(&launches);
     HPM_TRY(exclusive_scan_i32(t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(), nl, t.counters.as<int>() + 64,
                                t.scan, st, &launches));
     HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.leaf_part0.as<int>(), nl, t.counters.as<int>() + 65,
                                t.scan, st, &launches));
-    int hv[14] = {0}, herr2[2] = {0, 0};
-    HPM_CUDA(cudaMemcpyAsync(hv, t.counters.as<int>() + 64, sizeof(int) * 14, cudaMemcpyDeviceToHost, st));
+    int hv[15] = {0}, herr2[2] = {0, 0};
+    HPM_CUDA(cudaMemcpyAsync(hv, t.counters.as<int>() + 64, sizeof(int) * 15, cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaMemcpyAsync(herr2, t.err.as<int>(), sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaStreamSynchronize(st));
     if (herr2[1] & kErrTimeout) {
@@ -964,6 +1019,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     if (herr2[0] & kErrTimeout) return HPM_ERR_TIMEOUT;
     pl->nitem = hv[0];
     pl->npart = hv[1];
+    pl->nbig = hv[14];
     {
       unsigned long long pairs = 0;
       memcpy(&pairs, hv + 12, sizeof(pairs));

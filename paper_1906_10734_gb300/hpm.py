@@ -95,7 +95,7 @@ class hpm_server_opts(ctypes.Structure):
     _fields_ = [("dom", hpm_domain), ("max_depth", ctypes.c_int), ("gridlet_order", ctypes.c_int),
                 ("green", hpm_green), ("leaf_max", ctypes.c_int), ("workers", ctypes.c_int),
                 ("max_batch", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64),
-                ("bytes_per_particle", ctypes.c_double)]
+                ("bytes_per_particle", ctypes.c_double), ("max_batch_particles", ctypes.c_int64)]
 
 
 class hpm_request(ctypes.Structure):
@@ -361,11 +361,11 @@ class Server:
 
     def __init__(self, max_depth=12, gridlet_order=4, eps=1e-4, leaf_max=32, workers=2, max_batch=64,
                  hbm_budget_bytes=150 << 30, origin=(0.0, 0.0, 0.0), side=1.0, green: Green | None = None,
-                 bytes_per_particle=0.0):
+                 bytes_per_particle=0.0, max_batch_particles=0):
         L = load()
         opts = hpm_server_opts(hpm_domain((ctypes.c_double * 3)(*origin), side), max_depth, gridlet_order,
                                _green(eps, green), leaf_max, workers, max_batch, hbm_budget_bytes,
-                               bytes_per_particle)
+                               bytes_per_particle, max_batch_particles)
         h = _vp()
         _check("hpm_server_create", L.hpm_server_create(ctypes.byref(opts), ctypes.byref(h)))
         self.h = h.value

@@ -163,6 +163,24 @@ def test_admission_is_calibrated_from_measured_batches(hpm):
     assert need <= rate < need + 64.0
 
 
+@pytest.mark.gpu
+def test_particle_bound_splits_batches(hpm):
+    """With a bound of particles per batch no two of these requests share a batch (each
+    is over half the bound), and a request over the bound still runs (alone)."""
+    ws = [I.batch_problem(k, 20000, 30000, 9) for k in range(5)]
+    sv = hpm.Server(workers=1, max_batch=8, max_batch_particles=35000)
+    bufs = [(np.ascontiguousarray(w.pos), np.ascontiguousarray(w.mass), np.zeros(w.n, np.float32),
+             np.zeros((w.n, 3), np.float32)) for w in ws]
+    big = host_request(40000, 10)
+    ts = [sv.submit(*b) for b in bufs] + [sv.submit(*big)]
+    for t in ts:
+        sv.wait(t, 120000)
+    st = sv.stats()
+    sv.close()
+    assert st["completed"] == 6 and st["batches"] == 6
+    assert all(np.abs(b[3]).sum() > 0 for b in bufs + [big])
+
+
 def test_admission_uses_a_fixed_rate(hpm):
     """A caller's fixed rate replaces the calibrated estimate at submit (host logic,
     no workers): 4096 bytes per particle puts 20,000 particles over a 64 MiB budget."""
