@@ -159,7 +159,7 @@ struct SolveDev {
   // Ng = 4 tensor-core path: effective masses as FP16 (hi, lo) planes at a
   // per-row scale, row scale exponents and total masses, the scale exponent of
   // each tile column (parent) and the zone mass of each of its 8 children
-  DevBuf grid_hl, box_exp, box_mass, col_exp, zone_mass;
+  DevBuf grid_hl, box_em, col_exp, zone_mass;  // box_em: (scale exponent, total mass bits) per row
   DevBuf level_amax;  // per (problem, level): largest |effective mass| (float bits)
 };
 

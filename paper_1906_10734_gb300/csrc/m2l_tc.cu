@@ -435,17 +435,25 @@ __global__ void k_tiles(int64_t ntiles, int kTileN, TileLevels tl, const int *__
     return;
   }
   const int p = par_box[pi];
+  // the 27 neighbours at once, then each one's 8 children as two 16-byte
+  // loads (a box's child row is 32 contiguous bytes), all independent
+  int q[27];
+#pragma unroll
+  for (int k = 0; k < 27; ++k) q[k] = __ldg(nb + (int64_t)p * 27 + k);
+  const int4 *child4 = reinterpret_cast<const int4 *>(child);
+#pragma unroll
   for (int k = 0; k < 27; ++k) {
-    const int q = nb[(int64_t)p * 27 + k];
     const int dx = k % 3, dy = (k / 3) % 3, dz = k / 9;
+    int4 c0 = make_int4(-1, -1, -1, -1), c1 = c0;
+    if (q[k] >= 0) {
+      c0 = __ldg(child4 + (int64_t)q[k] * 2);
+      c1 = __ldg(child4 + (int64_t)q[k] * 2 + 1);
+    }
+    const int ch[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int bx = 2 * dx + (c & 1), by = 2 * dy + ((c >> 1) & 1), bz = 2 * dz + (c >> 2);
-      int row = -1;
-      if (q >= 0) {
-        const int ch = child[(int64_t)q * 8 + c];
-        if (ch >= 0) row = (int)(ch - off2);
-      }
-      rr[(int64_t)(bx + 6 * by + 36 * bz) * kTileN] = row;
+      rr[(int64_t)(bx + 6 * by + 36 * bz) * kTileN] = ch[c] >= 0 ? (int)(ch[c] - off2) : -1;
     }
   }
   for (int o = 0; o < 8; ++o) {
@@ -471,32 +479,6 @@ __device__ __forceinline__ int row_scale_slot(const RowLevels &rl, const uint64_
   return (int)p * rl.nlev + l;
 }
 
-// One thread per row: atomic max of its largest |value| into its (problem,
-// level) slot, aggregated over the lanes that share the slot.
-template <int NG>
-__global__ void k_level_amax(int64_t nrow, const float *__restrict__ grid, const uint64_t *__restrict__ box_key,
-                             RowLevels rl, int *__restrict__ amax) {
-  constexpr int kM3 = Cfg<NG>::kM3;
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = row < nrow;
-  unsigned m = 0u;
-  int slot = -1;
-  if (live) {
-    const float4 *g = reinterpret_cast<const float4 *>(grid + row * kM3);
-    float a = 0.f;
-#pragma unroll
-    for (int k = 0; k < kM3 / 4; ++k) {
-      const float4 v = g[k];
-      a = fmaxf(a, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
-    }
-    m = __float_as_uint(a);
-    slot = row_scale_slot(rl, box_key, row);
-  }
-  const unsigned peers = __match_any_sync(0xffffffffu, slot);
-  const unsigned gm = __reduce_max_sync(peers, m);
-  if (live && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicMax(amax + slot, (int)gm);
-}
-
 // Effective masses of every row as FP16 pairs at the row's (problem, level)
 // scale, in the order the gather copies them: per K-chunk (16 nodes) 16 hi
 // then 16 lo values (64 bytes), nodes beyond Ng^3 zero; also the row's scale
@@ -505,7 +487,7 @@ __global__ void k_level_amax(int64_t nrow, const float *__restrict__ grid, const
 template <int NG>
 __global__ void k_split(int64_t nrow, const float *__restrict__ grid, const uint64_t *__restrict__ box_key,
                         RowLevels rl, const int *__restrict__ amax, unsigned char *__restrict__ hl,
-                        int *__restrict__ box_exp, float *__restrict__ box_mass) {
+                        int2 *__restrict__ box_em) {
   using C = Cfg<NG>;
   constexpr int kL = C::kCPS <= 4 ? 4 : (C::kCPS <= 8 ? 8 : (C::kCPS <= 16 ? 16 : 32));
   static_assert(C::kCPS <= kL && C::kM3 % 4 == 0, "lanes per row");
@@ -554,18 +536,18 @@ __global__ void k_split(int64_t nrow, const float *__restrict__ grid, const uint
   dst[2] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
   dst[3] = make_uint4(lw[4], lw[5], lw[6], lw[7]);
   if (zq == 0) {
-    box_exp[row] = m > 0.f ? e : kNoExp;
-    box_mass[row] = sum;
+    box_em[row] = make_int2(m > 0.f ? e : kNoExp, __float_as_int(sum));  // one 8-byte read for k_col_exp
   }
 }
 
 // Per tile column (parent): the column scale exponent (the smallest row
 // exponent of its block, i.e. the scale of its largest |value|) and the total
 // mass of each child's interaction zone (block total minus the child's 3^3
-// near slots). One warp per column, the lanes splitting the 216 slots with
-// compensated FP32 sums (s, c); the lane pairs are combined with error-free
-// TwoSum steps, so no FP64 instruction is needed (each would hold the FP64
-// pipe for a whole warp).
+// near slots). A block of 8 warps takes 32 columns, lane = column (the rows
+// of a slot are read coalesced), warp w the slots w, w + 8, ... with
+// compensated FP32 sums (s, c); the 8 warps' sums of a column are then added
+// in warp order with error-free two-sums (deterministic), so no FP64
+// instruction is needed (each would hold the FP64 pipe for a whole warp).
 __device__ __forceinline__ void kahan_add_f(float &s, float &c, float x) {
   const float y = x - c;
   const float t = s + y;
@@ -573,60 +555,77 @@ __device__ __forceinline__ void kahan_add_f(float &s, float &c, float x) {
   s = t;
 }
 
-// (s, e) += (s2, e2) where s + e is the value held and e is small
-__device__ __forceinline__ void twosum_add(float &s, float &e, float s2, float e2) {
+// (s, e) += (s2, e2), the value held being s + e with e small
+__device__ __forceinline__ void two_sum_add(float &s, float &e, float s2, float e2) {
   const float t = s + s2;
   const float bp = t - s;
-  const float err = (s - (t - bp)) + (s2 - bp);
+  e = e + e2 + ((s - (t - bp)) + (s2 - bp));
   s = t;
-  e = e + e2 + err;
 }
 
-__device__ __forceinline__ void warp_sum_pair(float &s, float &e) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const float s2 = __shfl_xor_sync(0xffffffffu, s, off), e2 = __shfl_xor_sync(0xffffffffu, e, off);
-    twosum_add(s, e, s2, e2);
-  }
-}
-
-__global__ void k_col_exp(int64_t ntiles, int kTileN, const int *__restrict__ rows, const int *__restrict__ box_exp,
-                          const float *__restrict__ box_mass, int *__restrict__ col_exp,
-                          float *__restrict__ zone_mass) {
-  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= ntiles * kTileN) return;  // whole warps
-  const int *rr = rows + (i / kTileN) * kSlots * kTileN + (i % kTileN);
+constexpr int kColWarps = 8;
+__global__ void __launch_bounds__(32 * kColWarps) k_col_exp(int64_t ntiles, int kTileN, const int *__restrict__ rows,
+                                                           const int2 *__restrict__ box_em,
+                                                           int *__restrict__ col_exp,
+                                                           float *__restrict__ zone_mass) {
+  __shared__ float sh_s[kColWarps][9][32], sh_e[kColWarps][9][32];
+  __shared__ int sh_x[kColWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * 32 + lane;  // this lane's column
+  const bool live = i < ntiles * kTileN;
   int e = kNoExp;
   float ts = 0.f, tc = 0.f, ns[8], nc[8];
 #pragma unroll
   for (int o = 0; o < 8; ++o) ns[o] = nc[o] = 0.f;
-  for (int s = lane; s < kSlots; s += 32) {
-    const int row = rr[(int64_t)s * kTileN];
-    if (row < 0) continue;
-    e = min(e, box_exp[row]);
-    const float m = box_mass[row];
-    kahan_add_f(ts, tc, m);
-    const int sx = s % 6, sy = (s / 6) % 6, sz = s / 36;
+  if (live) {
+    const int *rr = rows + (i / kTileN) * kSlots * kTileN + (i % kTileN);
+#pragma unroll 3
+    for (int s = w; s < kSlots; s += kColWarps) {
+      const int row = __ldg(rr + (int64_t)s * kTileN);
+      if (row < 0) continue;
+      const int2 em = __ldg(box_em + row);
+      e = min(e, em.x);
+      const float m = __int_as_float(em.y);
+      kahan_add_f(ts, tc, m);
+      // child o = ox + 2 oy + 4 oz is near slot s iff each coordinate lies in
+      // [1 + o_axis, 3 + o_axis]: per axis the children (bit 0: o_axis = 0,
+      // bit 1: o_axis = 1) are 0, 1, 3, 3, 2, 0 for coordinates 0 .. 5
+      const unsigned mx = (0x2F4u >> (2 * (s % 6))) & 3u, my = (0x2F4u >> (2 * ((s / 6) % 6))) & 3u,
+                     mz = (0x2F4u >> (2 * (s / 36))) & 3u;
+      if (mx && my && mz) {
 #pragma unroll
-    for (int o = 0; o < 8; ++o) {
-      const int px = 2 + (o & 1), py = 2 + ((o >> 1) & 1), pz = 2 + (o >> 2);
-      if (max(abs(sx - px), max(abs(sy - py), abs(sz - pz))) <= 1) kahan_add_f(ns[o], nc[o], m);
+        for (int o = 0; o < 8; ++o)
+          if ((mx >> (o & 1)) & (my >> ((o >> 1) & 1)) & (mz >> (o >> 2)) & 1u) kahan_add_f(ns[o], nc[o], m);
+      }
     }
   }
-  e = __reduce_min_sync(0xffffffffu, e);
   // Kahan's (s, c) holds s - c
-  tc = -tc;
-  warp_sum_pair(ts, tc);
+  sh_s[w][8][lane] = ts;
+  sh_e[w][8][lane] = -tc;
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
-    nc[o] = -nc[o];
-    warp_sum_pair(ns[o], nc[o]);
+    sh_s[w][o][lane] = ns[o];
+    sh_e[w][o][lane] = -nc[o];
   }
-  if (lane == 0) {
-    col_exp[i] = e == kNoExp ? 0 : e;
+  sh_x[w][lane] = e;
+  __syncthreads();
+  if (w == 0 && live) {
+    float s9[9], e9[9];
+    int x = kNoExp;
 #pragma unroll
-    for (int o = 0; o < 8; ++o) zone_mass[i * 8 + o] = (ts - ns[o]) + (tc - nc[o]);
+    for (int q = 0; q < 9; ++q) {
+      s9[q] = sh_s[0][q][lane];
+      e9[q] = sh_e[0][q][lane];
+    }
+    for (int v = 0; v < kColWarps; ++v) {
+      x = min(x, sh_x[v][lane]);
+      if (v == 0) continue;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) two_sum_add(s9[q], e9[q], sh_s[v][q][lane], sh_e[v][q][lane]);
+    }
+    col_exp[i] = x == kNoExp ? 0 : x;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) zone_mass[i * 8 + o] = (s9[8] - s9[o]) + (e9[8] - e9[o]);
   }
 }
 
@@ -1012,27 +1011,22 @@ hpm_status launch_m2l_tc_ng(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) 
   const int64_t off2 = pl->lvl_off[2], nrow = pl->nbox - off2;
   if (nrow <= 0) return HPM_OK;
   HPM_TRY(pl->s.grid_hl.ensure((size_t)nrow * C::kCPS * tc::kRowBytes, st));
-  HPM_TRY(pl->s.box_exp.ensure(sizeof(int) * nrow, st));
-  HPM_TRY(pl->s.box_mass.ensure(sizeof(float) * nrow, st));
+  HPM_TRY(pl->s.box_em.ensure(sizeof(int2) * nrow, st));
   HPM_TRY(pl->s.col_exp.ensure(sizeof(int) * pl->tc_ntiles * C::kTileN, st));
   HPM_TRY(pl->s.zone_mass.ensure(sizeof(float) * pl->tc_ntiles * C::kTileN * 8, st));
   tc::RowLevels rl{};
   rl.nlev = pl->max_depth + 1;
   for (int l = 0; l <= pl->max_depth + 1; ++l) rl.off[l] = pl->lvl_off[l];
   rl.off2 = off2;
-  const size_t nslot = (size_t)(pl->nprob > 0 ? pl->nprob : 1) * rl.nlev;
-  HPM_TRY(pl->s.level_amax.ensure(sizeof(int) * nslot, st));
-  HPM_CUDA(cudaMemsetAsync(pl->s.level_amax.p, 0, sizeof(int) * nslot, st));
-  tc::k_level_amax<NG><<<(unsigned)((nrow + 255) / 256), 256, 0, st>>>(
-      nrow, pl->s.grid.as<float>(), pl->t.box_key.as<uint64_t>(), rl, pl->s.level_amax.as<int>());
-  HPM_LAUNCHED(launches);
+  // the per-(problem, level) maxima were taken by the P2G and child-to-parent
+  // kernels as they wrote the rows (s.level_amax)
   constexpr int kL = C::kCPS <= 4 ? 4 : (C::kCPS <= 8 ? 8 : (C::kCPS <= 16 ? 16 : 32));
   tc::k_split<NG><<<(unsigned)((kL * nrow + 255) / 256), 256, 0, st>>>(
       nrow, pl->s.grid.as<float>(), pl->t.box_key.as<uint64_t>(), rl, pl->s.level_amax.as<int>(),
-      pl->s.grid_hl.as<unsigned char>(), pl->s.box_exp.as<int>(), pl->s.box_mass.as<float>());
+      pl->s.grid_hl.as<unsigned char>(), pl->s.box_em.as<int2>());
   HPM_LAUNCHED(launches);
-  tc::k_col_exp<<<(unsigned)((pl->tc_ntiles * C::kTileN * 32 + 255) / 256), 256, 0, st>>>(
-      pl->tc_ntiles, C::kTileN, pl->t.tc_rows.as<int>(), pl->s.box_exp.as<int>(), pl->s.box_mass.as<float>(),
+  tc::k_col_exp<<<(unsigned)((pl->tc_ntiles * C::kTileN + 31) / 32), 32 * tc::kColWarps, 0, st>>>(
+      pl->tc_ntiles, C::kTileN, pl->t.tc_rows.as<int>(), pl->s.box_em.as<int2>(),
       pl->s.col_exp.as<int>(), pl->s.zone_mass.as<float>());
   HPM_LAUNCHED(launches);
   tc::Params p{};

@@ -131,17 +131,27 @@ __device__ __forceinline__ void lagrange4_d(float A, float B, float *w) {
 // all its threads evaluate the FP64 weights of the (box, particle) pairs of
 // those boxes, 256 pairs at a time, then warp w accumulates box w from shared
 // memory.
+// The largest |effective mass| of a warp's gridlet (a = this lane's) into its
+// (problem, level) slot: the per-level scale of the dense source-to-target
+// kernel's FP16 planes, taken here as the rows are written (amax null on the
+// other paths). Positive floats order as their bit patterns.
+__device__ __forceinline__ void row_amax(int *amax, float a, const uint64_t *__restrict__ key, int64_t box,
+                                         int level, int nlev) {
+  const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(a)));
+  if (amax && (threadIdx.x & 31) == 0) atomicMax(amax + (int)(key[box] >> (3 * level)) * nlev + level, (int)m);
+}
+
 template <int NG>
 __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__restrict__ list,
                                                   const int *__restrict__ pair_off, LevelTable lt,
                                                   GridletTables tb, const uint64_t *__restrict__ key,
                                                   const int *__restrict__ beg, const float4 *__restrict__ uhi,
                                                   const float4 *__restrict__ ulo, int64_t off2,
-                                                  float *__restrict__ grid) {
+                                                  float *__restrict__ grid, int *__restrict__ amax, int nlev) {
   __shared__ float ws[kThreads][3][kMaxNg];
   __shared__ float ms[kThreads];
   __shared__ int off[kWarpsPerBlock + 1];
-  __shared__ int bx[kWarpsPerBlock], bbeg[kWarpsPerBlock];
+  __shared__ int bx[kWarpsPerBlock], bbeg[kWarpsPerBlock], blev[kWarpsPerBlock];
   __shared__ float bc[kWarpsPerBlock][3], bscale[kWarpsPerBlock];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t b0 = (int64_t)blockIdx.x * kWarpsPerBlock;
@@ -152,6 +162,7 @@ __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__res
     const int l = level_of(lt, box);
     const uint64_t k = key[box] & ((1ull << (3 * l)) - 1ull);
     bx[threadIdx.x] = box;
+    blev[threadIdx.x] = l;
     bbeg[threadIdx.x] = beg[box];
     bscale[threadIdx.x] = (float)(1u << l);
     bc[threadIdx.x][0] = (float)compact3(k) + 0.5f;
@@ -216,9 +227,14 @@ __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__res
   }
   if (w < nb) {
     float *out = grid + (int64_t)(bx[w] - off2) * m3;
+    float a = 0.f;
 #pragma unroll
     for (int r = 0; r < kR; ++r)
-      if (r * 32 + lane < m3) out[r * 32 + lane] = acc[r];
+      if (r * 32 + lane < m3) {
+        out[r * 32 + lane] = acc[r];
+        a = fmaxf(a, fabsf(acc[r]));
+      }
+    row_amax(amax, a, key, bx[w], blev[w], nlev);
   }
 
 }
@@ -247,7 +263,8 @@ __device__ __forceinline__ void apply_axis(const float *__restrict__ op, bool tr
 __global__ void __launch_bounds__(kGThreads) k_m2m(int64_t b, int64_t e, GridletTables tb,
                                                   const uint8_t *__restrict__ flags,
                                                   const int *__restrict__ child, int64_t off2,
-                                                  float *__restrict__ grid) {
+                                                  float *__restrict__ grid, const uint64_t *__restrict__ key,
+                                                  int level, int *__restrict__ amax, int nlev) {
   __shared__ float T[2][kMaxNg * kMaxNg];
   __shared__ float bufA[kGWarps][512], bufB[kGWarps][512], res[kGWarps][512];
   for (int i = threadIdx.x; i < 2 * kMaxNg * kMaxNg; i += blockDim.x)
@@ -269,7 +286,12 @@ __global__ void __launch_bounds__(kGThreads) k_m2m(int64_t b, int64_t e, Gridlet
     apply_axis(T[(o >> 2) & 1], false, 2, ng, bufA[w], res[w], true);
   }
   float *dst = grid + (int64_t)(box - off2) * m3;
-  for (int p = lane; p < m3; p += 32) dst[p] = res[w][p];
+  float a = 0.f;
+  for (int p = lane; p < m3; p += 32) {
+    dst[p] = res[w][p];
+    a = fmaxf(a, fabsf(res[w][p]));
+  }
+  row_amax(amax, a, key, box, level, nlev);
 }
 
 // Ng = 4 child-to-parent, one parent per warp, with the transform factored
@@ -282,7 +304,8 @@ template <int kW>
 __global__ void __launch_bounds__(kW * 32) k_m2m4(int64_t b, int64_t e, GridletTables tb,
                                                          const uint8_t *__restrict__ flags,
                                                          const int *__restrict__ child, int64_t off2,
-                                                         float *__restrict__ grid) {
+                                                         float *__restrict__ grid, const uint64_t *__restrict__ key,
+                                                         int level, int *__restrict__ amax, int nlev) {
   __shared__ float T[2][4][4];
   __shared__ float ch[kW][8][64], X[kW][4][64], Y[kW][2][64];
   if (threadIdx.x < 32) T[threadIdx.x >> 4][(threadIdx.x >> 2) & 3][threadIdx.x & 3] =
@@ -335,6 +358,7 @@ __global__ void __launch_bounds__(kW * 32) k_m2m4(int64_t b, int64_t e, GridletT
   __syncwarp();
   // z: M^P[p] = sum_cz sum_qz T[cz][pz][qz] Y[cz][px, py, qz]
   float *out = grid + (int64_t)(box - off2) * 64;
+  float a = 0.f;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int p = r * 32 + lane, pz = p >> 4, base = p & 15;
@@ -344,7 +368,9 @@ __global__ void __launch_bounds__(kW * 32) k_m2m4(int64_t b, int64_t e, GridletT
 #pragma unroll
       for (int qz = 0; qz < 4; ++qz) acc = fmaf(T[cz][pz][qz], Y[w][cz][base + 16 * qz], acc);
     out[p] = acc;
+    a = fmaxf(a, fabsf(acc));
   }
+  row_amax(amax, a, key, box, level, nlev);
 }
 
 // Ng = 4 parent-to-child (Sec. 2.4), one target per warp with the three axis
@@ -1346,11 +1372,21 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
                                                1.0 / pl->dom.side, hi, lo);
   HPM_LAUNCHED(&launches);
   record(pl, 1, st);
+  // the dense source-to-target kernel's per-(problem, level) scales, taken
+  // as the P2G and child-to-parent kernels write the rows
+  int *amax = nullptr;
+  const int nlev = D + 1;
+  if (use_tc_m2l(pl) && nrow > 0) {
+    const size_t nslot = (size_t)(pl->nprob > 0 ? pl->nprob : 1) * nlev;
+    HPM_TRY(s.level_amax.ensure(sizeof(int) * nslot, st));
+    HPM_CUDA(cudaMemsetAsync(s.level_amax.p, 0, sizeof(int) * nslot, st));
+    amax = s.level_amax.as<int>();
+  }
   if (pl->np2g) {
     auto kp = ng == 4 ? k_p2g<4> : k_p2g<0>;
     kp<<<warp_blocks(pl->np2g), kThreads, 0, st>>>(pl->np2g, t.p2g_box.as<int>(), t.p2g_off.as<int>(), lt, pl->tab,
                                                    t.box_key.as<uint64_t>(), t.box_beg.as<int>(), hi, lo, off2,
-                                                   s.grid.as<float>());
+                                                   s.grid.as<float>(), amax, nlev);
     HPM_LAUNCHED(&launches);
   }
   record(pl, 2, st);
@@ -1361,10 +1397,12 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
       const int W = gridlet_warps(pl);
       auto km = W == 2 ? k_m2m4<2> : (W == 4 ? k_m2m4<4> : k_m2m4<8>);
       km<<<(unsigned)((e - b + W - 1) / W), W * 32, 0, st>>>(b, e, pl->tab, t.box_flags.as<uint8_t>(),
-                                                            t.box_child.as<int>(), off2, s.grid.as<float>());
+                                                            t.box_child.as<int>(), off2, s.grid.as<float>(),
+                                                            t.box_key.as<uint64_t>(), l, amax, nlev);
     } else
       k_m2m<<<gwarp_blocks(e - b), kGThreads, 0, st>>>(b, e, pl->tab, t.box_flags.as<uint8_t>(),
-                                                     t.box_child.as<int>(), off2, s.grid.as<float>());
+                                                     t.box_child.as<int>(), off2, s.grid.as<float>(),
+                                                     t.box_key.as<uint64_t>(), l, amax, nlev);
     HPM_LAUNCHED(&launches);
   }
   record(pl, 3, st);
