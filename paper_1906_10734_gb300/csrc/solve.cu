@@ -882,7 +882,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
   // the item's near boxes with particles, compacted: rng[w][k], k < nr, is
   // the k-th one's first particle and the index of that particle in the
   // concatenation of their particle ranges (strictly increasing in k)
-  int nr;
+  int nr, own0;
   {
     int b = 0, c = 0;
     if (lane < 27) {
@@ -898,6 +898,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
       const int t = __shfl_up_sync(0xffffffffu, inc, o);
       if (lane >= o) inc += t;
     }
+    // the target leaf's own particles start at this concatenated index (its
+    // own box is neighbour 13)
+    own0 = __shfl_sync(0xffffffffu, inc - c, 13);
     const unsigned ne = __ballot_sync(0xffffffffu, c > 0);
     nr = __popc(ne);
     if (c > 0) rng[w][__popc(ne & ((1u << lane) - 1u))] = make_int2(b, inc - c);
@@ -976,15 +979,25 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
       }
       __syncwarp();
       if (active) {
+        // the chunk positions of this pass's targets as sources: a block that
+        // reaches them holds some lane's own particle and is summed exactly
+        // at once
+        const int self0 = own0 + (t0 - tb) - c0, self1 = own0 + (min(t0 + per, tz) - tb) - c0;
         int k = sub;
         for (; k + 7 * G < cn; k += 8 * G) {
           // eight pairs from the rounded positions; if some lane of the warp
-          // has a pair closer than near2 in them (or meets its own particle:
-          // difference 0, r2 = eps2 <= near2) the block is summed again exactly
-          float bp = 0.f, bx = 0.f, by = 0.f, bz = 0.f, r2min = 3.4e38f;
+          // has a pair closer than near2 in them the block is summed again
+          // exactly
+          float bp = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+          const int kb = k - sub;  // the warp's block: positions kb ... kb + 8 G - 1
+          bool exact = kb < self1 && kb + 8 * G > self0;
+          if (!exact) {
+            float r2min = 3.4e38f;
 #pragma unroll
-          for (int u = 0; u < 8; ++u) r2min = fminf(r2min, pair_fast<KIND>(th, srh[w][k + u * G], nk, bp, bx, by, bz));
-          if (__any_sync(__activemask(), r2min <= near2)) {
+            for (int u = 0; u < 8; ++u) r2min = fminf(r2min, pair_fast<KIND>(th, srh[w][k + u * G], nk, bp, bx, by, bz));
+            exact = __any_sync(__activemask(), r2min <= near2);
+          }
+          if (exact) {
             bp = bx = by = bz = 0.f;
 #pragma unroll 4
             for (int u = 0; u < 8; ++u) {
