@@ -118,19 +118,14 @@ __device__ __forceinline__ void lagrange4_d(float A, float B, float *w) {
   const double u = (double)A + (double)B;
   const double d0 = u + 3.0, d1 = u + 1.0, d2 = u - 1.0, d3 = u - 3.0;
   const double e = d2 * d3, f = d0 * d1;
-  w[0] = (float)((d1 * e) * (-1.0 / 48.0));
+  // the products in FP64, rounded to FP32 once, then the denominators (+-16
+  // exactly, +-48 to one more FP32 rounding)
+  w[0] = (float)(d1 * e) * (-1.f / 48.f);
   w[1] = (float)(d0 * e) * 0.0625f;
   w[2] = (float)(f * d3) * -0.0625f;
-  w[3] = (float)((f * d2) * (1.0 / 48.0));
+  w[3] = (float)(f * d2) * (1.f / 48.f);
 }
 
-// Effective masses, M_p = sum_i m_i prod_d ell_{p_d}(xi_d) (Eq. mp in Lagrange
-// form: sum_n B_pn t^n = ell_p(t)), for the boxes that are not expanded: each
-// particle's finest box (an expanded box, internal or not, gets its gridlet
-// from its children by the child-to-parent transform). A block takes 8 boxes;
-// all its threads evaluate the FP64 weights of the (box, particle) pairs of
-// those boxes, 256 pairs at a time, then warp w accumulates box w from shared
-// memory.
 // The largest |effective mass| of a warp's gridlet (a = this lane's) into its
 // (problem, level) slot: the per-level scale of the dense source-to-target
 // kernel's FP16 planes, taken here as the rows are written (amax null on the
@@ -141,6 +136,13 @@ __device__ __forceinline__ void row_amax(int *amax, float a, const uint64_t *__r
   if (amax && (threadIdx.x & 31) == 0) atomicMax(amax + (int)(key[box] >> (3 * level)) * nlev + level, (int)m);
 }
 
+// Effective masses, M_p = sum_i m_i prod_d ell_{p_d}(xi_d) (Eq. mp in Lagrange
+// form: sum_n B_pn t^n = ell_p(t)), for the boxes that are not expanded: each
+// particle's finest box (an expanded box, internal or not, gets its gridlet
+// from its children by the child-to-parent transform). A block takes 8 boxes;
+// all its threads evaluate the FP64 weights of the (box, particle) pairs of
+// those boxes, 256 pairs at a time, then warp w accumulates box w from shared
+// memory.
 template <int NG>
 __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__restrict__ list,
                                                   const int *__restrict__ pair_off, LevelTable lt,
