@@ -853,6 +853,12 @@ __device__ __forceinline__ void pair_exact(const float4 &tr, const float4 &te, c
 // the grid holds as many blocks as are resident at once, so a warp whose item
 // ends early starts the next one instead of idling until its block retires.
 constexpr int kP2PChunk = 128;
+// Targets of an item's first pass, by its number of targets (the rest, if
+// any, in a second pass): the split that minimises the passes' time per source,
+// 1 / lanes per target of each pass plus its staging (about 0.09 of a one-lane
+// pass), over the two-pass splits and the single pass
+__constant__ unsigned char c_p2p_first_pass[33] = {0,  1,  2,  3,  4,  5,  6,  7,  8,  9,  10, 3,  4,  13, 14, 15, 16,
+                                                   1,  2,  3,  4,  5,  6,  7,  8,  9,  10, 27, 28, 29, 30, 31, 32};
 
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *__restrict__ item_leaf,
@@ -923,8 +929,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
     cy0 = ((float)compact3(kk >> 1) + 0.5f) * inv;
     cz0 = ((float)compact3(kk >> 2) + 0.5f) * inv;
   }
-  const int G = nti >= 32 ? 1 : 32 / nti;
-  const int per = 32 / G;
   const int nitems = leaf_nitem[leaf];
   float near2;
   {
@@ -932,10 +936,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
     near2 = nk.eps2 + side * side * (1.f / 64.f);  // r^2 of a pair 1/8 of the side apart
   }
   const int kidx = (int)(it - leaf_item0[leaf]);
-  for (int t0 = ta; t0 < tz; t0 += per) {
+  // one or two passes over the targets, each with floor(32 / its targets)
+  // lanes per target (at most 16): a leaf of 17 targets takes 1 then 16 (16
+  // then 2 lanes per target) instead of 17 at 1 lane
+  const int split = nti <= 32 ? c_p2p_first_pass[nti] : 32;
+  for (int pass = 0; pass < 2; ++pass) {
+  const int pa = pass == 0 ? ta : ta + split, pz = pass == 0 ? ta + split : tz;
+  if (pa >= pz) break;
+  const int G = pz - pa >= 32 ? 1 : min(16, 32 / (pz - pa));
+  const int per = 32 / G;
+  for (int t0 = pa; t0 < pz; t0 += per) {
     const int slot = lane / G, sub = lane % G;
     const int ti = t0 + slot;
-    const bool active = slot < per && ti < tz;
+    const bool active = slot < per && ti < pz;
     float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
     if (active) {
       const float4 h = hi[ti], q = lo[ti];
@@ -984,7 +997,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
         // the chunk positions of this pass's targets as sources: a block that
         // reaches them holds some lane's own particle and is summed exactly
         // at once
-        const int self0 = own0 + (t0 - tb) - c0, self1 = own0 + (min(t0 + per, tz) - tb) - c0;
+        const int self0 = own0 + (t0 - tb) - c0, self1 = own0 + (min(t0 + per, pz) - tb) - c0;
         int k = sub;
         for (; k + 7 * G < cn; k += 8 * G) {
           // eight pairs from the rounded positions; if some lane of the warp
@@ -1045,6 +1058,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
       }
     }
     __syncwarp();
+  }
   }
   }
 }
