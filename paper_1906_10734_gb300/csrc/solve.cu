@@ -50,6 +50,7 @@ __device__ __forceinline__ int level_of(const LevelTable &lt, int64_t box) {
 }
 
 // ---------------------------------------------------------------------------
+template <bool kUnit>
 __global__ void k_gather(int64_t n, const uint32_t *__restrict__ perm, const double *__restrict__ pos,
                          const double *__restrict__ mass, double ox, double oy, double oz, double inv_side,
                          float4 *__restrict__ hi, float4 *__restrict__ lo) {
@@ -60,8 +61,11 @@ __global__ void k_gather(int64_t n, const uint32_t *__restrict__ perm, const dou
   // position in the unit cube of the domain, u = (x - o) / S, as an
   // unevaluated sum hi + lo of two floats: a cell-relative coordinate
   // u 2^l - c is then exact in FP32 up to one rounding, and differences of
-  // nearby particles keep FP32 precision relative to themselves
-  const double ux = (x - ox) * inv_side, uy = (y - oy) * inv_side, uz = (z - oz) * inv_side;
+  // nearby particles keep FP32 precision relative to themselves. kUnit: the
+  // domain is the unit cube at the origin, u = x (two FP64 operations fewer
+  // per axis on this GPU's narrow FP64 pipe)
+  const double ux = kUnit ? x : (x - ox) * inv_side, uy = kUnit ? y : (y - oy) * inv_side,
+               uz = kUnit ? z : (z - oz) * inv_side;
   const float hx = (float)ux, hy = (float)uy, hz = (float)uz;
   hi[i] = make_float4(hx, hy, hz, (float)mass[p]);
   lo[i] = make_float4((float)(ux - (double)hx), (float)(uy - (double)hy), (float)(uz - (double)hz), 0.f);
@@ -603,25 +607,33 @@ __global__ void __launch_bounds__(kThreads) k_g2p(int64_t n, const int *__restri
   lagrange_f<NG>(tb, cell_coord(h.y, q.y, sc, (float)compact3(k >> 1) + 0.5f), wv[1], dw[1]);
   lagrange_f<NG>(tb, cell_coord(h.z, q.z, sc, (float)compact3(k >> 2) + 0.5f), wv[2], dw[2]);
   const float *dl = loc + (int64_t)t * ng * ng * ng;
+  // contracted axis by axis: x for every (y, z) row (the value and its x
+  // derivative), then y for every z (value, y and x derivatives), then z
   float f = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
   for (int pz = 0; pz < (NG > 0 ? NG : kMaxNg); ++pz) {
     if (pz >= ng) break;
+    float fy = 0.f, yy = 0.f, xy = 0.f;
 #pragma unroll
     for (int py = 0; py < (NG > 0 ? NG : kMaxNg); ++py) {
       if (py >= ng) break;
-      const float wyz = wv[1][py] * wv[2][pz], dyz = dw[1][py] * wv[2][pz], ydz = wv[1][py] * dw[2][pz];
       const float *row = dl + ng * (py + ng * pz);
+      float fx = 0.f, xx = 0.f;
 #pragma unroll
       for (int px = 0; px < (NG > 0 ? NG : kMaxNg); ++px) {
         if (px >= ng) break;
         const float v = __ldg(row + px);
-        f += v * wv[0][px] * wyz;
-        gx += v * dw[0][px] * wyz;
-        gy += v * wv[0][px] * dyz;
-        gz += v * wv[0][px] * ydz;
+        fx = fmaf(v, wv[0][px], fx);
+        xx = fmaf(v, dw[0][px], xx);
       }
+      fy = fmaf(fx, wv[1][py], fy);
+      yy = fmaf(fx, dw[1][py], yy);
+      xy = fmaf(xx, wv[1][py], xy);
     }
+    f = fmaf(fy, wv[2][pz], f);
+    gz = fmaf(fy, dw[2][pz], gz);
+    gy = fmaf(yy, wv[2][pz], gy);
+    gx = fmaf(xy, wv[2][pz], gx);
   }
   const float invL = sc * inv_side;
   far[i] = make_float4(__ldg(locc + t) + f, -gx * invL, -gy * invL, -gz * invL);
@@ -1397,8 +1409,9 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
   const double *o = pl->dom.origin;
 
   record(pl, 0, st);
-  k_gather<<<blocks_for(n), kThreads, 0, st>>>(n, t.perm.as<uint32_t>(), d_pos, d_mass, o[0], o[1], o[2],
-                                               1.0 / pl->dom.side, hi, lo);
+  const bool unit = o[0] == 0.0 && o[1] == 0.0 && o[2] == 0.0 && pl->dom.side == 1.0;
+  (unit ? k_gather<true> : k_gather<false>)<<<blocks_for(n), kThreads, 0, st>>>(
+      n, t.perm.as<uint32_t>(), d_pos, d_mass, o[0], o[1], o[2], 1.0 / pl->dom.side, hi, lo);
   HPM_LAUNCHED(&launches);
   record(pl, 1, st);
   // the dense source-to-target kernel's per-(problem, level) scales, taken
