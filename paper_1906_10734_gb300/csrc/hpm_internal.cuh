@@ -136,8 +136,9 @@ struct TreeDev {
   // items of bounded pair count
   // item_t: first target of a target-split item (32 targets), -1 for an item
   // that covers all the leaf's targets
-  // big_leaf: leaves split over more than kP2PCombineWarp items (order not fixed)
-  DevBuf item_leaf, item_s0, item_s1, item_t, leaf_nitem, leaf_item0, leaf_part0, leaf_ns, big_leaf;
+  // big_leaf / split_leaf: leaves split over sources into more than
+  // kP2PCombineWarp items / into 2 .. kP2PCombineWarp items (order not fixed)
+  DevBuf item_leaf, item_s0, item_s1, item_t, leaf_nitem, leaf_item0, leaf_part0, leaf_ns, big_leaf, split_leaf;
   DevBuf err;        // int error word
   DevBuf lvl_dev;    // box offsets per level on the device (int64, max_depth + 2)
   DevBuf offsets;    // problem offsets of a batched build (int64, nprob + 1)
@@ -223,6 +224,7 @@ struct hpm_plan_s {
   int64_t nitem = 0, npart = 0;   // near-field work items, partial-sum rows
   int64_t npairs = 0;              // near-zone pairs (i, j), j != i
   int64_t nbig = 0;                // leaves split over more than kP2PCombineWarp items
+  int64_t nsplit = 0;              // leaves split over 2 .. kP2PCombineWarp items
   int64_t npar = 0;                // internal cells at levels >= 1 (parents of targets)
   std::vector<int64_t> tgt_lvl_off;  // target offsets per level (levels 2..D)
   std::vector<int64_t> leaf_lvl_off;

@@ -619,12 +619,20 @@ __global__ void __launch_bounds__(kThreads) k_g2p(int64_t n, const int *__restri
       if (py >= ng) break;
       const float *row = dl + ng * (py + ng * pz);
       float fx = 0.f, xx = 0.f;
+      if constexpr (NG == 4) {
+        // a row is one 16-byte load (four lanes of a warp on different leaves
+        // cost one L1 wavefront per load instead of four)
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(row));
+        fx = fmaf(v.w, wv[0][3], fmaf(v.z, wv[0][2], fmaf(v.y, wv[0][1], v.x * wv[0][0])));
+        xx = fmaf(v.w, dw[0][3], fmaf(v.z, dw[0][2], fmaf(v.y, dw[0][1], v.x * dw[0][0])));
+      } else {
 #pragma unroll
-      for (int px = 0; px < (NG > 0 ? NG : kMaxNg); ++px) {
-        if (px >= ng) break;
-        const float v = __ldg(row + px);
-        fx = fmaf(v, wv[0][px], fx);
-        xx = fmaf(v, dw[0][px], xx);
+        for (int px = 0; px < (NG > 0 ? NG : kMaxNg); ++px) {
+          if (px >= ng) break;
+          const float v = __ldg(row + px);
+          fx = fmaf(v, wv[0][px], fx);
+          xx = fmaf(v, dw[0][px], xx);
+        }
       }
       fy = fmaf(fx, wv[1][py], fy);
       yy = fmaf(fx, dw[1][py], yy);
@@ -1075,9 +1083,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2p(int64_t nitem, const int *_
   }
 }
 
-// Leaves whose near zone was split over several items: sum the items' partial
-// sums in item order (deterministic), add the far field, write the outputs.
-__global__ void __launch_bounds__(kThreads) k_p2p_combine(int64_t nleaf, const int *__restrict__ leaf_nitem,
+// Leaves whose near zone was split over 2 .. kP2PCombineWarp items (listed by
+// the tree build): sum the items' partial sums in item order (deterministic),
+// add the far field, write the outputs.
+__global__ void __launch_bounds__(kThreads) k_p2p_combine(int64_t nsplit, const int *__restrict__ split,
+                                                          const int *__restrict__ leaf_nitem,
                                                           const int *__restrict__ leaf_item0,
                                                           const int *__restrict__ item_t,
                                                           const int *__restrict__ leaf_part0,
@@ -1088,8 +1098,9 @@ __global__ void __launch_bounds__(kThreads) k_p2p_combine(int64_t nleaf, const i
                                                           const uint32_t *__restrict__ perm, float s1, float s2,
                                                           float *__restrict__ out_phi, float *__restrict__ out_acc) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t leaf = (int64_t)blockIdx.x * kWarpsPerBlock + w;
-  if (leaf >= nleaf) return;
+  const int64_t si = (int64_t)blockIdx.x * kWarpsPerBlock + w;
+  if (si >= nsplit) return;
+  const int leaf = split[si];
   const int n = leaf_nitem[leaf];
   // complete sums already written, or a leaf for k_p2p_combine_big
   if (n <= 1 || n > kP2PCombineWarp || item_t[leaf_item0[leaf]] >= 0) return;
@@ -1511,9 +1522,9 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
         t.box_key.as<uint64_t>(), lt, nk, s1, s2, d_phi, d_acc, s.part.as<float4>(),
         s.work.as<unsigned long long>());
     HPM_LAUNCHED(&launches);
-    if (pl->npart > 0) {
-      k_p2p_combine<<<warp_blocks(pl->nleaf), kThreads, 0, st>>>(
-          pl->nleaf, t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(), t.item_t.as<int>(), t.leaf_part0.as<int>(), t.leaf_box.as<int>(), t.box_beg.as<int>(),
+    if (pl->nsplit > 0) {
+      k_p2p_combine<<<warp_blocks(pl->nsplit), kThreads, 0, st>>>(
+          pl->nsplit, t.split_leaf.as<int>(), t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(), t.item_t.as<int>(), t.leaf_part0.as<int>(), t.leaf_box.as<int>(), t.box_beg.as<int>(),
           t.box_end.as<int>(), s.part.as<float4>(), s.far.as<float4>(), t.perm.as<uint32_t>(), s1, s2, d_phi,
           d_acc);
       HPM_LAUNCHED(&launches);

@@ -607,8 +607,10 @@ __global__ void k_box_tgt(int64_t ntgt, const int *__restrict__ tgt_box, int *__
 // stored (a source split of such a leaf would need items * nt of them).
 __global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, const int *__restrict__ nb,
                             const int *__restrict__ beg, const int *__restrict__ end, int *__restrict__ nitem,
-                            int *__restrict__ npart, int *__restrict__ nsrc, int *__restrict__ big,
-                            int *__restrict__ nbig, unsigned long long *__restrict__ npairs) {
+                            int *__restrict__ part0, int *__restrict__ npart, int *__restrict__ nsrc,
+                            int *__restrict__ big,
+                            int *__restrict__ nbig, int *__restrict__ split, int *__restrict__ nsplit,
+                            unsigned long long *__restrict__ npairs) {
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // near-zone pairs (i, j), j != i, of all leaves: the near field's work count
   unsigned long long pairs = 0;
@@ -631,7 +633,7 @@ __global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, con
   if (nt > kP2PSplitTargets) {
     // large leaf: items of 32 targets against all sources, complete sums
     nitem[l] = (int)((nt + 31) / 32);
-    npart[l] = 0;
+    part0[l] = 0;
     return;
   }
   int64_t items = (nt * ns + kP2PPairsPerItem - 1) / kP2PPairsPerItem;
@@ -639,8 +641,11 @@ __global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, con
   if (items > cap) items = cap;
   if (items < 1) items = 1;
   nitem[l] = (int)items;
-  npart[l] = items > 1 ? (int)(items * nt) : 0;
+  // a split leaf's partial sums: items x nt of them, placed by an atomic
+  // counter (each leaf reads back only its own)
+  part0[l] = items > 1 ? atomicAdd(npart, (int)(items * nt)) : 0;
   if (items > kP2PCombineWarp) big[atomicAdd(nbig, 1)] = (int)l;
+  else if (items > 1) split[atomicAdd(nsplit, 1)] = (int)l;
 }
 
 // The items of each leaf (k_leaf_work's counts and near-source totals).
@@ -773,7 +778,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   pl->lvl_off.assign(D + 2, 0);
   pl->depth_reached = -1;
   pl->nbox = pl->ntgt = pl->nleaf = pl->np2g = pl->ncell = 0;
-  pl->nitem = pl->npart = pl->nbig = 0;
+  pl->nitem = pl->npart = pl->nbig = pl->nsplit = 0;
   pl->npar = 0;
   pl->tgt_lvl_off.assign(D + 2, 0);
   pl->leaf_lvl_off.assign(D + 2, 0);
@@ -996,19 +1001,20 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     HPM_TRY(t.cnt.ensure(sizeof(int) * (nl + 1), st));
     HPM_TRY(t.leaf_ns.ensure(sizeof(int) * (nl + 1), st));
     HPM_TRY(t.big_leaf.ensure(sizeof(int) * (nl + 1), st));
+    HPM_TRY(t.split_leaf.ensure(sizeof(int) * (nl + 1), st));
     // counters[76..77]: the near-zone pair count (64 bits), zeroed with the others
     k_leaf_work<<<blocks_for(nl), kThreads, 0, st>>>(nl, t.leaf_box.as<int>(), t.box_nb.as<int>(),
                                                      t.box_beg.as<int>(), t.box_end.as<int>(),
-                                                     t.leaf_nitem.as<int>(), t.cnt.as<int>(), t.leaf_ns.as<int>(),
+                                                     t.leaf_nitem.as<int>(), t.leaf_part0.as<int>(),
+                                                     t.counters.as<int>() + 65, t.leaf_ns.as<int>(),
                                                      t.big_leaf.as<int>(), t.counters.as<int>() + 78,
+                                                     t.split_leaf.as<int>(), t.counters.as<int>() + 79,
                                                      reinterpret_cast<unsigned long long *>(t.counters.as<int>() + 76));
     HPM_LAUNCHED(&launches);
     HPM_TRY(exclusive_scan_i32(t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(), nl, t.counters.as<int>() + 64,
                                t.scan, st, &launches));
-    HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.leaf_part0.as<int>(), nl, t.counters.as<int>() + 65,
-                               t.scan, st, &launches));
-    int hv[15] = {0}, herr2[2] = {0, 0};
-    HPM_CUDA(cudaMemcpyAsync(hv, t.counters.as<int>() + 64, sizeof(int) * 15, cudaMemcpyDeviceToHost, st));
+    int hv[16] = {0}, herr2[2] = {0, 0};
+    HPM_CUDA(cudaMemcpyAsync(hv, t.counters.as<int>() + 64, sizeof(int) * 16, cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaMemcpyAsync(herr2, t.err.as<int>(), sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaStreamSynchronize(st));
     if (herr2[1] & kErrTimeout) {
@@ -1020,6 +1026,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     pl->nitem = hv[0];
     pl->npart = hv[1];
     pl->nbig = hv[14];
+    pl->nsplit = hv[15];
     {
       unsigned long long pairs = 0;
       memcpy(&pairs, hv + 12, sizeof(pairs));
