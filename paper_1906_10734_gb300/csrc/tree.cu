@@ -515,28 +515,74 @@ __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
   }
 }
 
-// Work-list selection. mode 0: real cells; 1: leaves; 2: boxes that get their
-// effective masses by P2G (not expanded: each particle's finest box); 3:
-// internal cells.
-__global__ void k_select(int64_t b, int64_t e, const uint8_t *__restrict__ flags, int mode,
-                         int *__restrict__ sel) {
-  const int64_t i = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= e) return;
+// The four work lists of a build at once (box order kept): 0 real cells at
+// level >= 2 (targets), 1 leaves, 2 boxes at level >= 2 that are not
+// expanded (P2G), 3 internal cells at level >= 1 (parents of targets).
+// Pass 1 counts each list per block of kThreads boxes (warp ballots); one
+// exclusive scan over the four lists' block counts, list after list; pass 2
+// recomputes the ballots and writes every selected box at its list position.
+__device__ __forceinline__ unsigned list_bits(int64_t i, int64_t nbox, int64_t off2, int64_t off1,
+                                              const uint8_t *__restrict__ flags) {
+  if (i >= nbox) return 0u;
   const uint8_t f = flags[i];
-  int v;
-  if (mode == 0) v = (f & kReal) != 0;
-  else if (mode == 1) v = (f & kLeaf) != 0;
-  else if (mode == 2) v = (f & kExpand) == 0;
-  else v = (f & kInternal) != 0;
-  sel[i - b] = v;
+  return (i >= off2 && (f & kReal) ? 1u : 0u) | (f & kLeaf ? 2u : 0u) | (i >= off2 && !(f & kExpand) ? 4u : 0u) |
+         (i >= off1 && (f & kInternal) ? 8u : 0u);
 }
 
-__global__ void k_compact(int64_t b, int64_t e, const int *__restrict__ sel,
-                          const int *__restrict__ pos, int *__restrict__ out) {
-  const int64_t i = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= e) return;
-  if (sel[i - b]) out[pos[i - b]] = (int)i;
+__global__ void __launch_bounds__(kThreads) k_lists_count(int64_t nbox, int64_t off2, int64_t off1,
+                                                          const uint8_t *__restrict__ flags, int nblk,
+                                                          int *__restrict__ cnt) {
+  __shared__ int wsum[4][kThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned bits = list_bits((int64_t)blockIdx.x * kThreads + threadIdx.x, nbox, off2, off1, flags);
+#pragma unroll
+  for (int L = 0; L < 4; ++L) {
+    const int c = __popc(__ballot_sync(0xffffffffu, (bits >> L) & 1u));
+    if (lane == 0) wsum[L][w] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    int t = 0;
+    for (int k = 0; k < kThreads / 32; ++k) t += wsum[threadIdx.x][k];
+    cnt[(int64_t)threadIdx.x * nblk + blockIdx.x] = t;
+  }
 }
+
+__global__ void __launch_bounds__(kThreads) k_lists_write(int64_t nbox, int64_t off2, int64_t off1,
+                                                          const uint8_t *__restrict__ flags, int nblk,
+                                                          const int *__restrict__ off, const int *__restrict__ total,
+                                                          int *__restrict__ out0, int *__restrict__ out1,
+                                                          int *__restrict__ out2, int *__restrict__ out3,
+                                                          int *__restrict__ totals) {
+  __shared__ int wsum[4][kThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const unsigned bits = list_bits(i, nbox, off2, off1, flags);
+  unsigned ball[4];
+#pragma unroll
+  for (int L = 0; L < 4; ++L) {
+    ball[L] = __ballot_sync(0xffffffffu, (bits >> L) & 1u);
+    if (lane == 0) wsum[L][w] = __popc(ball[L]);
+  }
+  __syncthreads();
+  int *outs[4] = {out0, out1, out2, out3};
+#pragma unroll
+  for (int L = 0; L < 4; ++L) {
+    if (!((bits >> L) & 1u)) continue;
+    int before = 0;
+    for (int k = 0; k < w; ++k) before += wsum[L][k];
+    const int pos = off[(int64_t)L * nblk + blockIdx.x] - off[(int64_t)L * nblk] + before +
+                    __popc(ball[L] & ((1u << lane) - 1u));
+    outs[L][pos] = (int)i;
+  }
+  // each list's total: its scanned base of the next list, less its own base
+  if (blockIdx.x == 0 && threadIdx.x < 4) {
+    const int L = threadIdx.x;
+    const int next = L < 3 ? off[(int64_t)(L + 1) * nblk] : *total;
+    totals[L] = next - off[(int64_t)L * nblk];
+  }
+}
+
 
 // Interaction zone of each target (cells at level >= 2) as its parent's 6^3
 // block: box j = bx + 6 by + 36 bz is a child of the parent's neighbour
@@ -699,32 +745,6 @@ hpm_status ensure_boxes(TreeDev &t, int64_t nbox, cudaStream_t st) {
   HPM_TRY(t.box_flags.ensure(sizeof(uint8_t) * ((nbox + 15) & ~int64_t(15)), st, true));  // word-wide atomics in k_expand
   HPM_TRY(t.box_child.ensure(sizeof(int) * 8 * nbox, st, true));
   HPM_TRY(t.box_nb.ensure(sizeof(int) * 27 * nbox, st, true));
-  return HPM_OK;
-}
-
-// Compacts the boxes in [b, e) selected by `mode` into out (resized); returns the count.
-// Boxes of [b, e) passing `mode`, compacted into `out` in order. Their number
-// is known on the host from the per-level counts, so nothing is read back: the
-// device total goes to counters[total_slot] for the consistency check of the
-// build, and `out` is sized for the whole range (the compaction never writes
-// past e - b).
-hpm_status select_boxes(hpm_plan_s *pl, int64_t b, int64_t e, int mode, DevBuf &out, int total_slot,
-                        cudaStream_t st, int64_t *launches) {
-  TreeDev &t = pl->t;
-  const int64_t n = e - b;
-  HPM_TRY(out.ensure(sizeof(int) * (n > 0 ? n : 1), st));
-  if (n <= 0) {
-    HPM_CUDA(cudaMemsetAsync(t.counters.as<int>() + total_slot, 0, sizeof(int), st));
-    return HPM_OK;
-  }
-  HPM_TRY(t.cnt.ensure(sizeof(int) * n, st));
-  HPM_TRY(t.off.ensure(sizeof(int) * (n + 1), st));
-  k_select<<<blocks_for(n), kThreads, 0, st>>>(b, e, t.box_flags.as<uint8_t>(), mode, t.cnt.as<int>());
-  HPM_LAUNCHED(launches);
-  HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), n, t.counters.as<int>() + total_slot, t.scan, st,
-                             launches));
-  k_compact<<<blocks_for(n), kThreads, 0, st>>>(b, e, t.cnt.as<int>(), t.off.as<int>(), out.as<int>());
-  HPM_LAUNCHED(launches);
   return HPM_OK;
 }
 
@@ -981,10 +1001,32 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     pl->np2g = -1;  // counted on the device (boxes at level >= 2 that are not expanded)
     pl->npar = internal1;
   }
-  HPM_TRY(select_boxes(pl, off2, pl->nbox, 0, t.tgt_box, 70, st, &launches));
-  HPM_TRY(select_boxes(pl, 0, pl->nbox, 1, t.leaf_box, 71, st, &launches));
-  HPM_TRY(select_boxes(pl, off2, pl->nbox, 2, t.p2g_box, 72, st, &launches));
-  HPM_TRY(select_boxes(pl, D >= 1 ? pl->lvl_off[1] : pl->nbox, pl->nbox, 3, t.par_box, 73, st, &launches));
+  {
+    // the four work lists (totals to counters[70..73]) in three launches
+    const int64_t nb = pl->nbox > 0 ? pl->nbox : 1;
+    const int nblk = (int)((pl->nbox + kThreads - 1) / kThreads);
+    const int64_t off1 = D >= 1 ? pl->lvl_off[1] : pl->nbox;
+    HPM_TRY(t.tgt_box.ensure(sizeof(int) * nb, st));
+    HPM_TRY(t.leaf_box.ensure(sizeof(int) * nb, st));
+    HPM_TRY(t.p2g_box.ensure(sizeof(int) * nb, st));
+    HPM_TRY(t.par_box.ensure(sizeof(int) * nb, st));
+    if (nblk > 0) {
+      HPM_TRY(t.cnt.ensure(sizeof(int) * 4 * nblk, st));
+      HPM_TRY(t.off.ensure(sizeof(int) * (4 * nblk + 1), st));
+      k_lists_count<<<nblk, kThreads, 0, st>>>(pl->nbox, off2, off1, t.box_flags.as<uint8_t>(), nblk,
+                                               t.cnt.as<int>());
+      HPM_LAUNCHED(&launches);
+      HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), 4 * (int64_t)nblk, t.off.as<int>() + 4 * nblk,
+                                 t.scan, st, &launches));
+      k_lists_write<<<nblk, kThreads, 0, st>>>(pl->nbox, off2, off1, t.box_flags.as<uint8_t>(), nblk,
+                                               t.off.as<int>(), t.off.as<int>() + 4 * nblk, t.tgt_box.as<int>(),
+                                               t.leaf_box.as<int>(), t.p2g_box.as<int>(), t.par_box.as<int>(),
+                                               t.counters.as<int>() + 70);
+      HPM_LAUNCHED(&launches);
+    } else {
+      HPM_CUDA(cudaMemsetAsync(t.counters.as<int>() + 70, 0, sizeof(int) * 4, st));
+    }
+  }
   // leaf of every particle
   HPM_TRY(t.pbox.ensure(sizeof(int) * (n > 0 ? n : 1), st));
   if (pl->nleaf) {
