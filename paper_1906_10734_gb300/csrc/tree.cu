@@ -116,13 +116,17 @@ __global__ void k_keys(const double *__restrict__ pos, int64_t n, double ox, dou
 
 // Particle range of problem p in the sorted order (its level-0 key is p).
 __global__ void k_problem_ranges(int nprob, int64_t n, const uint64_t *__restrict__ skeys, int shift,
-                                 int *__restrict__ rb, int *__restrict__ cnt) {
+                                 int *__restrict__ rb, int *__restrict__ cnt, int *__restrict__ off,
+                                 int *__restrict__ total) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nprob) return;
   if (nprob == 1) {
-    // a single problem holds every particle (no searches: 2 x log2 n dependent loads)
+    // a single problem holds every particle (no searches: 2 x log2 n dependent
+    // loads), and the root offsets need no scan
     rb[0] = 0;
     cnt[0] = n > 0 ? 1 : 0;
+    off[0] = 0;
+    *total = cnt[0];
     return;
   }
   int lo = 0, hi = (int)n;
@@ -499,10 +503,9 @@ __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
     // 3. neighbour tables of level l, expansion marks for level l + 1
     for (int64_t i = pe + gtid; i < ne; i += gthreads) {
       const uint8_t f = a.flags[i];
-      if (!(f & kReal)) {
-        for (int k = 0; k < 27; ++k) a.nb[i * 27 + k] = -1;
-        continue;
-      }
+      // a virtual box's row is never read (neighbour tables are read for real
+      // boxes and their parents only): left unwritten
+      if (!(f & kReal)) continue;
       int q[27];
       neighbours_of(i, l, a.key, a.parent, a.child, a.nb, q);
 #pragma unroll
@@ -674,19 +677,26 @@ __global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, con
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
   if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(npairs, pairs);
+  // the leaf's items: a large leaf (more than kP2PSplitTargets particles) by
+  // 32 targets against all sources, complete sums; else by its sources
+  int64_t items = 0;
+  if (l < nleaf) {
+    if (nt > kP2PSplitTargets) {
+      items = (nt + 31) / 32;
+    } else {
+      items = (nt * ns + kP2PPairsPerItem - 1) / kP2PPairsPerItem;
+      const int64_t cap = (ns + kP2PMinSources - 1) / kP2PMinSources;
+      if (items > cap) items = cap;
+      if (items < 1) items = 1;
+    }
+  }
   if (l >= nleaf) return;
   nsrc[l] = (int)ns;
+  nitem[l] = (int)items;
   if (nt > kP2PSplitTargets) {
-    // large leaf: items of 32 targets against all sources, complete sums
-    nitem[l] = (int)((nt + 31) / 32);
     part0[l] = 0;
     return;
   }
-  int64_t items = (nt * ns + kP2PPairsPerItem - 1) / kP2PPairsPerItem;
-  const int64_t cap = (ns + kP2PMinSources - 1) / kP2PMinSources;
-  if (items > cap) items = cap;
-  if (items < 1) items = 1;
-  nitem[l] = (int)items;
   // a split leaf's partial sums: items x nt of them, placed by an atomic
   // counter (each leaf reads back only its own)
   part0[l] = items > 1 ? atomicAdd(npart, (int)(items * nt)) : 0;
@@ -845,10 +855,12 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   HPM_TRY(t.off.ensure(sizeof(int) * (nprob + 1), st));
   HPM_TRY(t.bnd.ensure(sizeof(int) * (nprob + 1), st));
   k_problem_ranges<<<blocks_for(nprob), kThreads, 0, st>>>(nprob, n, skeys, 3 * D, t.bnd.as<int>(),
-                                                           t.cnt.as<int>());
+                                                           t.cnt.as<int>(), t.off.as<int>(),
+                                                           t.counters.as<int>() + 64);
   HPM_LAUNCHED(&launches);
-  HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), nprob, t.counters.as<int>() + 64, t.scan, st,
-                             &launches));
+  if (nprob > 1)
+    HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), nprob, t.counters.as<int>() + 64, t.scan, st,
+                               &launches));
   // one problem with n > 0 particles has one root; a batch reads its count back
   int nroot = 1;
   if (nprob > 1) {
@@ -1053,10 +1065,12 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
                                                      t.split_leaf.as<int>(), t.counters.as<int>() + 79,
                                                      reinterpret_cast<unsigned long long *>(t.counters.as<int>() + 76));
     HPM_LAUNCHED(&launches);
-    HPM_TRY(exclusive_scan_i32(t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(), nl, t.counters.as<int>() + 64,
+    // items in leaf order (the near field takes them in index order: a leaf's
+    // neighbours' particles are then still in cache for the next leaf)
+    HPM_TRY(exclusive_scan_i32(t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(), nl, t.counters.as<int>() + 80,
                                t.scan, st, &launches));
-    int hv[16] = {0}, herr2[2] = {0, 0};
-    HPM_CUDA(cudaMemcpyAsync(hv, t.counters.as<int>() + 64, sizeof(int) * 16, cudaMemcpyDeviceToHost, st));
+    int hv[17] = {0}, herr2[2] = {0, 0};
+    HPM_CUDA(cudaMemcpyAsync(hv, t.counters.as<int>() + 64, sizeof(int) * 17, cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaMemcpyAsync(herr2, t.err.as<int>(), sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaStreamSynchronize(st));
     if (herr2[1] & kErrTimeout) {
@@ -1065,7 +1079,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
       return HPM_ERR_TIMEOUT;
     }
     if (herr2[0] & kErrTimeout) return HPM_ERR_TIMEOUT;
-    pl->nitem = hv[0];
+    pl->nitem = hv[16];
     pl->npart = hv[1];
     pl->nbig = hv[14];
     pl->nsplit = hv[15];
