@@ -122,7 +122,7 @@ static void for_each_buf(hpm_plan_s *pl, F &&f) {
                     &pl->tc_mean, &pl->gmean,
                     &pl->t.keys, &pl->t.keys_alt, &pl->t.perm, &pl->t.perm_alt, &pl->t.spm, &pl->t.pbox,
                     &pl->t.box_key, &pl->t.box_beg, &pl->t.box_end, &pl->t.box_parent, &pl->t.box_flags,
-                    &pl->t.box_child, &pl->t.box_nb, &pl->t.cnt, &pl->t.off, &pl->t.bnd, &pl->t.p2g_off, &pl->t.par_box, &pl->t.tgt_blk, &pl->t.tgt_info, &pl->t.tc_rows, &pl->t.tc_tgt, &pl->t.tgt_box,
+                    &pl->t.box_child, &pl->t.box_nb, &pl->t.cnt, &pl->t.off, &pl->t.bnd, &pl->t.par_box, &pl->t.tgt_blk, &pl->t.tgt_info, &pl->t.tc_rows, &pl->t.tc_tgt, &pl->t.tgt_box,
                     &pl->t.box_tgt, &pl->t.leaf_box, &pl->t.p2g_box, &pl->t.item_leaf, &pl->t.item_s0,
                     &pl->t.item_s1, &pl->t.item_t, &pl->t.leaf_nitem, &pl->t.leaf_ns, &pl->t.big_leaf, &pl->t.split_leaf, &pl->t.leaf_item0, &pl->t.leaf_part0, &pl->s.part, &pl->t.err, &pl->t.lvl_dev, &pl->t.counters, &pl->t.scan_buf,
                     &pl->s.grid, &pl->s.m2l_raw, &pl->s.loc, &pl->s.locc, &pl->s.m2lc, &pl->s.far, &pl->s.m2l_scratch, &pl->s.work, &pl->s.grid_hl, &pl->s.box_em, &pl->s.col_exp, &pl->s.zone_mass, &pl->s.level_amax,

@@ -122,7 +122,7 @@ struct TreeDev {
   DevBuf box_key, box_beg, box_end, box_parent, box_flags, box_child, box_nb;
   DevBuf cnt, off, bnd;   // per-box scratch for child counting
   // work lists
-  DevBuf tgt_box, box_tgt, leaf_box, p2g_box, p2g_off, par_box;
+  DevBuf tgt_box, box_tgt, leaf_box, p2g_box, par_box;
   DevBuf pbox;       // leaf box of every sorted particle
   // interaction zone of every target as its 6^3 parent block: row of each box's
   // effective masses, -1 where empty, outside the domain or in the near zone;

@@ -148,10 +148,10 @@ __device__ __forceinline__ void row_amax(int *amax, float a, const uint64_t *__r
 // those boxes, 256 pairs at a time, then warp w accumulates box w from shared
 // memory.
 template <int NG>
-__global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__restrict__ list,
-                                                  const int *__restrict__ pair_off, LevelTable lt,
+__global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__restrict__ list, LevelTable lt,
                                                   GridletTables tb, const uint64_t *__restrict__ key,
-                                                  const int *__restrict__ beg, const float4 *__restrict__ uhi,
+                                                  const int *__restrict__ beg, const int *__restrict__ end,
+                                                  const float4 *__restrict__ uhi,
                                                   const float4 *__restrict__ ulo, int64_t off2,
                                                   float *__restrict__ grid, int *__restrict__ amax, int nlev) {
   __shared__ float ws[kThreads][3][kMaxNg];
@@ -162,7 +162,22 @@ __global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__res
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t b0 = (int64_t)blockIdx.x * kWarpsPerBlock;
   const int nb = (int)min((int64_t)kWarpsPerBlock, nbox - b0);
-  if (threadIdx.x <= nb) off[threadIdx.x] = pair_off[b0 + threadIdx.x];
+  // the block's (box, particle) pairs: the boxes' particle counts, prefixed
+  int cnt = 0;
+  if (threadIdx.x < nb) {
+    const int box = list[b0 + threadIdx.x];
+    cnt = end[box] - beg[box];
+  }
+  if (threadIdx.x < 32) {
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < kWarpsPerBlock; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if ((threadIdx.x & 31) >= o) inc += t;
+    }
+    if (threadIdx.x < nb) off[threadIdx.x + 1] = inc;
+    if (threadIdx.x == 0) off[0] = 0;
+  }
   if (threadIdx.x < nb) {
     const int box = list[b0 + threadIdx.x];
     const int l = level_of(lt, box);
@@ -1437,8 +1452,9 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
   }
   if (pl->np2g) {
     auto kp = ng == 4 ? k_p2g<4> : k_p2g<0>;
-    kp<<<warp_blocks(pl->np2g), kThreads, 0, st>>>(pl->np2g, t.p2g_box.as<int>(), t.p2g_off.as<int>(), lt, pl->tab,
-                                                   t.box_key.as<uint64_t>(), t.box_beg.as<int>(), hi, lo, off2,
+    kp<<<warp_blocks(pl->np2g), kThreads, 0, st>>>(pl->np2g, t.p2g_box.as<int>(), lt, pl->tab,
+                                                   t.box_key.as<uint64_t>(), t.box_beg.as<int>(),
+                                                   t.box_end.as<int>(), hi, lo, off2,
                                                    s.grid.as<float>(), amax, nlev);
     HPM_LAUNCHED(&launches);
   }

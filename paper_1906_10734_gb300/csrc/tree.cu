@@ -320,6 +320,7 @@ __device__ __forceinline__ void mark_neighbours(const int *q, uint8_t *flags) {
 //      neighbours for the next level's expansion right away
 // Three grid barriers per level (and one after the roots' marks); the launch
 // ends at the first empty level.
+constexpr int kSearchWays = 8;  // binary searches in flight per thread
 __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
   __shared__ int s_warp[kThreads / 32];
   __shared__ long long s_red[2][kThreads / 32];
@@ -371,13 +372,13 @@ __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
         const int b0 = lo + __popc(__ballot_sync(0xffffffffu, lt));
         if (lane == 0) a.bnd[r0 * 8 + oct] = b0;
       }
-      // (box, octant) items of this block: 4 binary searches in lockstep per thread
+      // (box, octant) items of this block: kSearchWays binary searches in lockstep per thread
       const int64_t nit = warp_search ? 0 : 8 * (r1 - r0);
-      for (int64_t t0 = tid; t0 < nit; t0 += 4 * kThreads) {
-        int lo[4], hi[4];
-        uint64_t kc[4];
+      for (int64_t t0 = tid; t0 < nit; t0 += kSearchWays * kThreads) {
+        int lo[kSearchWays], hi[kSearchWays];
+        uint64_t kc[kSearchWays];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < kSearchWays; ++j) {
           const int64_t t = t0 + (int64_t)j * kThreads;
           lo[j] = 0;
           hi[j] = 0;
@@ -396,7 +397,7 @@ __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
         for (;;) {
           bool any = false;
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
+          for (int j = 0; j < kSearchWays; ++j)
             if (lo[j] < hi[j]) {
               any = true;
               const int mid = lo[j] + ((hi[j] - lo[j]) >> 1);
@@ -406,7 +407,7 @@ __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
           if (!any) break;
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < kSearchWays; ++j) {
           const int64_t t = t0 + (int64_t)j * kThreads;
           if (t < nit) a.bnd[r0 * 8 + t] = lo[j];
         }
@@ -629,11 +630,6 @@ __global__ void k_target_blocks(int64_t ntgt, const int *__restrict__ tgt_box, c
   }
 }
 
-__global__ void k_box_counts(int64_t n, const int *__restrict__ list, const int *__restrict__ beg,
-                             const int *__restrict__ end, int *__restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = end[list[i]] - beg[list[i]];
-}
 
 // Leaf box of every sorted particle (a leaf's particles are contiguous).
 __global__ void k_particle_box(int64_t nleaf, const int *__restrict__ leaf_box, const int *__restrict__ beg,
@@ -1105,16 +1101,6 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
                                                       t.item_leaf.as<int>(), t.item_s0.as<int>(),
                                                       t.item_s1.as<int>(), t.item_t.as<int>());
     HPM_LAUNCHED(&launches);
-  }
-  // particle offsets of the P2G boxes (n + 1 entries, the last one the total)
-  HPM_TRY(t.p2g_off.ensure(sizeof(int) * (pl->np2g + 1), st));
-  if (pl->np2g) {
-    HPM_TRY(t.cnt.ensure(sizeof(int) * pl->np2g, st));
-    k_box_counts<<<blocks_for(pl->np2g), kThreads, 0, st>>>(pl->np2g, t.p2g_box.as<int>(), t.box_beg.as<int>(),
-                                                            t.box_end.as<int>(), t.cnt.as<int>());
-    HPM_LAUNCHED(&launches);
-    HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.p2g_off.as<int>(), pl->np2g, t.p2g_off.as<int>() + pl->np2g,
-                               t.scan, st, &launches));
   }
   HPM_TRY(t.box_tgt.ensure(sizeof(int) * (pl->nbox > 0 ? pl->nbox : 1), st));
   HPM_CUDA(cudaMemsetAsync(t.box_tgt.p, 0xff, sizeof(int) * pl->nbox, st));
