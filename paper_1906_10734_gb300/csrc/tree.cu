@@ -320,7 +320,7 @@ __device__ __forceinline__ void mark_neighbours(const int *q, uint8_t *flags) {
 //      neighbours for the next level's expansion right away
 // Three grid barriers per level (and one after the roots' marks); the launch
 // ends at the first empty level.
-constexpr int kSearchWays = 8;  // binary searches in flight per thread
+constexpr int kSearchWays = 4;  // binary searches in flight per thread (8 measured slower)
 __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
   __shared__ int s_warp[kThreads / 32];
   __shared__ long long s_red[2][kThreads / 32];
