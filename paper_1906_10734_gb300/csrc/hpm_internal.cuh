@@ -251,9 +251,11 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
 // sort.cu
 int64_t scan_tiles(int64_t n);
 hpm_status ensure_scan_ctl(DevBuf &buf, int64_t tiles, int *err, cudaStream_t st, ScanCtl *out);
+// (wide_digits: 9-bit digits where they take fewer passes; the scratch then
+// needs 512 counters per tile of kSortTileElems, not kRadixDigits)
 hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&vals,
                             uint32_t *&vals_alt, int64_t n, int bits, DevBuf &scratch, const ScanCtl &ctl,
-                            cudaStream_t st, int64_t *launches);
+                            cudaStream_t st, int64_t *launches, bool wide_digits = false);
 hpm_status exclusive_scan_i32(const int *in, int *out, int64_t n, int *d_total, const ScanCtl &ctl,
                               cudaStream_t st, int64_t *launches);
 // green.cu

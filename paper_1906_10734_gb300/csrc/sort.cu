@@ -138,10 +138,22 @@ constexpr int kSortTile = kSortThreads * kSortRounds;
 constexpr int kRadix = 256;
 static_assert(kSortTile == kSortTileElems && kRadix == kRadixDigits, "sort sizing shared with the static sort");
 
+// Digits of RB bits (8 or 9: 256 or 512 counters, kDigitsPerThread per thread).
+template <int RB>
+struct Digits {
+  static constexpr int kN = 1 << RB;
+  static constexpr unsigned kMask = kN - 1;
+  static constexpr int kPerThread = kN / kSortThreads;
+  static_assert(kPerThread >= 1 && kN % kSortThreads == 0, "whole digits per thread");
+};
+
+template <int RB>
 __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t n, int shift,
                              int *__restrict__ hist, int nblk) {
-  __shared__ int cnt[kRadix];
-  cnt[threadIdx.x] = 0;
+  using Dg = Digits<RB>;
+  __shared__ int cnt[Dg::kN];
+#pragma unroll
+  for (int q = 0; q < Dg::kPerThread; ++q) cnt[q * kSortThreads + threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   // all of the thread's keys in flight at once, then the counts
@@ -153,13 +165,17 @@ __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t n, int s
   }
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r)
-    if (base + (int64_t)r * kSortThreads + threadIdx.x < n) atomicAdd(&cnt[(k[r] >> shift) & 0xff], 1);
+    if (base + (int64_t)r * kSortThreads + threadIdx.x < n) atomicAdd(&cnt[(k[r] >> shift) & Dg::kMask], 1);
   __syncthreads();
-  hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+#pragma unroll
+  for (int q = 0; q < Dg::kPerThread; ++q) {
+    const int d = q * kSortThreads + threadIdx.x;
+    hist[(int64_t)d * nblk + blockIdx.x] = cnt[d];
+  }
 }
 
 // Stable scatter of one tile (kSortTile consecutive elements) by the current
-// 8-bit digit. Each warp ranks its own 512 elements (16 rounds of 32) within
+// digit. Each warp ranks its own 512 elements (16 rounds of 32) within
 // (warp, digit) with warp-private counters, so no block barrier per round;
 // the tile is then put in digit order in shared memory (order within a digit:
 // warp, round, lane, i.e. the input order) and written out with consecutive
@@ -168,25 +184,36 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kWarpRounds = kSortTile / kSortThreads;  // 16 rounds of 32 per warp
 constexpr int kScatterSmem = kSortTile * (int)(sizeof(uint64_t) + sizeof(uint32_t));
 
+template <int RB>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n, int shift,
     const int *__restrict__ hist, const int *__restrict__ offs, int nblk, uint64_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out) {
+  using Dg = Digits<RB>;
+  constexpr int P = Dg::kPerThread;
   extern __shared__ __align__(16) unsigned char sraw[];
   uint64_t *sk = reinterpret_cast<uint64_t *>(sraw);
   uint32_t *sv = reinterpret_cast<uint32_t *>(sk + kSortTile);
-  __shared__ int wcnt[kSortWarps][kRadix];  // per warp and digit: count, then the warp's offset in the digit
-  __shared__ int dstart[kRadix];            // first position of each digit in the sorted tile
-  __shared__ int gbase[kRadix];             // global position of the tile's first element of each digit
+  __shared__ int wcnt[kSortWarps][Dg::kN];  // per warp and digit: count, then the warp's offset in the digit
+  __shared__ int dstart[Dg::kN];            // first position of each digit in the sorted tile
+  __shared__ int gbase[Dg::kN];             // global position of the tile's first element of each digit
   __shared__ int wsum[kSortWarps];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
 #pragma unroll
-  for (int k = 0; k < kSortWarps; ++k) wcnt[k][tid] = 0;
+  for (int k = 0; k < kSortWarps; ++k)
+#pragma unroll
+    for (int q = 0; q < P; ++q) wcnt[k][q * kSortThreads + tid] = 0;
   {
     // digit starts: exclusive scan over the digits of this tile's counts
-    const int c = hist[(int64_t)tid * nblk + blockIdx.x];
-    int inc = c;
+    // (thread t holds digits P t ... P t + P - 1)
+    int c[P], sum = 0;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      c[q] = hist[(int64_t)(P * tid + q) * nblk + blockIdx.x];
+      sum += c[q];
+    }
+    int inc = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int v = __shfl_up_sync(0xffffffffu, inc, o);
@@ -197,8 +224,13 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     int before = 0;
 #pragma unroll
     for (int k = 0; k < kSortWarps; ++k) before += k < w ? wsum[k] : 0;
-    dstart[tid] = before + inc - c;
-    gbase[tid] = offs[(int64_t)tid * nblk + blockIdx.x];
+    int run = before + inc - sum;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      dstart[P * tid + q] = run;
+      run += c[q];
+      gbase[P * tid + q] = offs[(int64_t)(P * tid + q) * nblk + blockIdx.x];
+    }
   }
   __syncthreads();
   // ranks within (warp, digit), warp by warp
@@ -221,7 +253,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const int64_t i = wb + r * 32 + lane;
     const bool valid = i < n;
     const uint64_t key = kk[r];
-    const int d = valid ? (int)((key >> shift) & 0xff) : kRadix;
+    const int d = valid ? (int)((key >> shift) & Dg::kMask) : Dg::kN;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const int leader = __ffs(peers) - 1, rank = __popc(peers & lt);
     int old = 0;
@@ -234,12 +266,14 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     rk[r] = old + rank;
   }
   __syncthreads();
-  {
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int d = q * kSortThreads + tid;
     int s = 0;
 #pragma unroll
     for (int k = 0; k < kSortWarps; ++k) {
-      const int c = wcnt[k][tid];
-      wcnt[k][tid] = s;
+      const int c = wcnt[k][d];
+      wcnt[k][d] = s;
       s += c;
     }
   }
@@ -247,7 +281,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
 #pragma unroll
   for (int r = 0; r < kWarpRounds; ++r) {
     if (wb + r * 32 + lane < n) {
-      const int d = (int)((kk[r] >> shift) & 0xff);
+      const int d = (int)((kk[r] >> shift) & Dg::kMask);
       const int pos = dstart[d] + wcnt[w][d] + rk[r];
       sk[pos] = kk[r];
       sv[pos] = vv[r];
@@ -257,7 +291,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   const int nt = (int)min((int64_t)kSortTile, n - base);
   for (int j = tid; j < nt; j += kSortThreads) {
     const uint64_t key = sk[j];
-    const int d = (int)((key >> shift) & 0xff);
+    const int d = (int)((key >> shift) & Dg::kMask);
     const int p = gbase[d] + (j - dstart[d]);
     keys_out[p] = key;
     vals_out[p] = sv[j];
@@ -298,33 +332,35 @@ hpm_status ensure_scan_ctl(DevBuf &buf, int64_t tiles, int *err, cudaStream_t st
   return HPM_OK;
 }
 
-// Sorts by the low `bits` bits of the keys, stably. On return keys/vals point
-// at the sorted arrays (the pointers may have been swapped with the *_alt
-// buffers). vals may be null on entry: the original index is used then (the
-// first pass writes it).
-hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&vals,
-                            uint32_t *&vals_alt, int64_t n, int bits, DevBuf &scratch, const ScanCtl &ctl,
-                            cudaStream_t st, int64_t *launches) {
-  if (n <= 0) return HPM_OK;
+// Sorts by the low `bits` bits of the keys, stably, in passes of 8-bit
+// digits, or of 9-bit digits where that takes fewer passes and wide_digits is
+// set (the scratch then holds 512 counters per tile instead of 256). On
+// return keys/vals point at the sorted arrays (the pointers may have been
+// swapped with the *_alt buffers). vals may be null on entry: the original
+// index is used then (the first pass writes it).
+template <int RB>
+static hpm_status sort_passes(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&vals, uint32_t *&vals_alt,
+                              int64_t n, int bits, DevBuf &scratch, const ScanCtl &ctl, cudaStream_t st,
+                              int64_t *launches) {
   const int nblk = (int)((n + kSortTile - 1) / kSortTile);
-  const int64_t hn = (int64_t)kRadix * nblk;
+  const int64_t hn = (int64_t)Digits<RB>::kN * nblk;
   HPM_TRY(scratch.ensure(sizeof(int) * 2 * hn, st));
   int *hist = scratch.as<int>();
   int *offs = hist + hn;
   static DeviceCache attr_cache;
   int done = 0;
   HPM_TRY(device_cached(attr_cache, [](int *v) -> hpm_status {
-    HPM_CUDA(cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, kScatterSmem));
+    HPM_CUDA(cudaFuncSetAttribute(k_radix_scatter<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kScatterSmem));
     *v = 1;
     return HPM_OK;
   }, &done));
   bool first = true;
-  for (int shift = 0; shift < bits || first; shift += 8) {
-    k_radix_hist<<<nblk, kSortThreads, 0, st>>>(keys, n, shift, hist, nblk);
+  for (int shift = 0; shift < bits || first; shift += RB) {
+    k_radix_hist<RB><<<nblk, kSortThreads, 0, st>>>(keys, n, shift, hist, nblk);
     HPM_LAUNCHED(launches);
     HPM_TRY(exclusive_scan_i32(hist, offs, hn, nullptr, ctl, st, launches));
-    k_radix_scatter<<<nblk, kSortThreads, kScatterSmem, st>>>(keys, first ? nullptr : vals, n, shift, hist,
-                                                               offs, nblk, keys_alt, vals_alt);
+    k_radix_scatter<RB><<<nblk, kSortThreads, kScatterSmem, st>>>(keys, first ? nullptr : vals, n, shift, hist,
+                                                                   offs, nblk, keys_alt, vals_alt);
     HPM_LAUNCHED(launches);
     uint64_t *tk = keys;
     keys = keys_alt;
@@ -335,6 +371,15 @@ hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&val
     first = false;
   }
   return HPM_OK;
+}
+
+hpm_status radix_sort_pairs(uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&vals, uint32_t *&vals_alt, int64_t n,
+                            int bits, DevBuf &scratch, const ScanCtl &ctl, cudaStream_t st, int64_t *launches,
+                            bool wide_digits) {
+  if (n <= 0) return HPM_OK;
+  if (wide_digits && (bits + 8) / 9 < (bits + 7) / 8)
+    return sort_passes<9>(keys, keys_alt, vals, vals_alt, n, bits, scratch, ctl, st, launches);
+  return sort_passes<8>(keys, keys_alt, vals, vals_alt, n, bits, scratch, ctl, st, launches);
 }
 
 }  // namespace hpm

@@ -324,6 +324,7 @@ constexpr int kSearchWays = 4;  // binary searches in flight per thread (8 measu
 __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
   __shared__ int s_warp[kThreads / 32];
   __shared__ long long s_red[2][kThreads / 32];
+  __shared__ int s_nb[kThreads / 32][32 * 27];  // a warp's 32 neighbour rows
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x, gtid = (int64_t)blockIdx.x * blockDim.x + tid;
   int64_t pb = a.lvl[0], pe = a.lvl[1];
@@ -501,17 +502,31 @@ __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
       return;
     }
     if (!grid_sync(a.gb, a.err)) return;
-    // 3. neighbour tables of level l, expansion marks for level l + 1
-    for (int64_t i = pe + gtid; i < ne; i += gthreads) {
-      const uint8_t f = a.flags[i];
-      // a virtual box's row is never read (neighbour tables are read for real
-      // boxes and their parents only): left unwritten
-      if (!(f & kReal)) continue;
-      int q[27];
-      neighbours_of(i, l, a.key, a.parent, a.child, a.nb, q);
+    // 3. neighbour tables of level l, expansion marks for level l + 1: each
+    // warp takes 32 consecutive boxes, whose rows are one contiguous run of
+    // nb, staged in shared memory and written with whole-warp stores
+    for (int64_t i0 = pe + gtid - lane; i0 < ne; i0 += gthreads) {
+      const int64_t i = i0 + lane;
+      bool real = false;
+      if (i < ne) {
+        const uint8_t f = a.flags[i];
+        // a virtual box's row is never read (neighbour tables are read for
+        // real boxes and their parents only): left unwritten
+        real = f & kReal;
+        if (real) {
+          int q[27];
+          neighbours_of(i, l, a.key, a.parent, a.child, a.nb, q);
 #pragma unroll
-      for (int k = 0; k < 27; ++k) a.nb[i * 27 + k] = q[k];
-      if (l < a.depth && (f & kInternal)) mark_neighbours(q, a.flags);
+          for (int k = 0; k < 27; ++k) s_nb[wid][lane * 27 + k] = q[k];
+          if (l < a.depth && (f & kInternal)) mark_neighbours(q, a.flags);
+        }
+      }
+      const unsigned rows = __ballot_sync(0xffffffffu, real);
+      __syncwarp();
+      const int cnt = (int)min((int64_t)32, ne - i0) * 27;
+      for (int x = lane; x < cnt; x += 32)
+        if (rows >> (x / 27) & 1u) a.nb[i0 * 27 + x] = s_nb[wid][x];
+      __syncwarp();
     }
     if (!grid_sync(a.gb, a.err)) return;
     pb = pe;
@@ -834,7 +849,7 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   uint64_t *k0 = t.keys.as<uint64_t>(), *k1 = t.keys_alt.as<uint64_t>();
   uint32_t *v0 = t.perm.as<uint32_t>(), *v1 = t.perm_alt.as<uint32_t>();
   DevBuf &scratch = t.off;
-  HPM_TRY(radix_sort_pairs(k0, k1, v0, v1, n, 3 * D + pbits, scratch, t.scan, st, &launches));
+  HPM_TRY(radix_sort_pairs(k0, k1, v0, v1, n, 3 * D + pbits, scratch, t.scan, st, &launches, true));
   // keep the sorted arrays in keys/perm
   if (k0 != t.keys.as<uint64_t>()) {
     std::swap(t.keys.p, t.keys_alt.p);
