@@ -84,7 +84,7 @@ def fp32_peak(live: dict | None) -> tuple[float, str]:
     return float("nan"), "no measured FP32 peak"
 
 
-def roofline_of(stats_steps, ng, n_targets, traffic_src, live_peaks=None):
+def roofline_of(stats_steps, ng, n_targets, traffic_src, live_peaks=None, tile_n=None):
     """Roofline object of the source-to-target kernel of the last steps.
 
     `achieved` is the ALGORITHMIC work: the nominal FFT-convolution count per target
@@ -105,7 +105,7 @@ def roofline_of(stats_steps, ng, n_targets, traffic_src, live_peaks=None):
         peak = peaks.get("bf16_tflops", 1900.0)
         return {"kernel": f"k_m2l_tc<{ng}>: source-to-target as a dense FP16-pair tcgen05 product per parent block",
                 "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": profile_traffic(traffic_src) if traffic_src else None, "ms_per_launch": kms,
+                "traffic": profile_traffic(traffic_src, tile_n) if traffic_src else None, "ms_per_launch": kms,
                 "launches_per_step": 1, "flop_per_target": m2l_flops_per_target(ng),
                 "targets_per_launch": n_targets,
                 "flop_basis": "nominal FFT convolution work per target x targets (algorithmic)",
@@ -236,9 +236,10 @@ def measured_peaks() -> dict:
         return {}
 
 
-def profile_traffic(kernel_src: str) -> float | None:
+def profile_traffic(kernel_src: str, tile_n: int | None = None) -> float | None:
     """DRAM bytes per full launch from the committed ncu summary, if it was taken on the
-    kernel source as it is now (its sha256 matches); else None."""
+    kernel source as it is now (its sha256 matches); else None. With tile_n, the figure
+    of that tile width (`dram_bytes_per_full_launch_tn<N>:`) where the summary has one."""
     h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
@@ -248,8 +249,11 @@ def profile_traffic(kernel_src: str) -> float | None:
             continue
         text = open(os.path.join(pdir, fn)).read()
         m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
-        m_tr = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
-        if m_sha and m_tr and m_sha.group(1) == h:
+        if not m_sha or m_sha.group(1) != h:
+            continue
+        m_tn = re.search(rf"dram_bytes_per_full_launch_tn{tile_n}:\s*([0-9.eE+]+)", text) if tile_n else None
+        m_tr = m_tn or re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+        if m_tr:
             return float(m_tr.group(1))
     return None
 
@@ -362,7 +366,8 @@ def run_gpu(args) -> None:
     traffic_src = None
     if args.workload == "plummer" and w.ng == 4:
         traffic_src = os.path.join(csrc, "m2l_tc.cu" if args.m2l == "tensor" else "m2l.cu")
-    roofline = roofline_of(stats_steps, w.ng, info["n_targets"], traffic_src, live_peaks)
+    roofline = roofline_of(stats_steps, w.ng, info["n_targets"], traffic_src, live_peaks,
+                           tuning.get("m2l_tile_parents") or 256)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -329,10 +329,11 @@ typedef struct {
                               tile first: that part of W stays in L2 while the
                               parents' gridlets stream); 0 = 1                   */
   int m2l_tile_parents;    /* dense tensor-core source-to-target at Ng = 4:
-                              parents per tile (the MMA's N), 256, 224 or 192
-                              (0 = 256); a narrower tile spreads each level's
-                              parents over more CTA pairs. Applies from the
-                              next hpm_build_tree (the tiles are built there) */
+                              parents per tile (the MMA's N), 256, 224, 208 or
+                              192 (0 = 256); a narrower tile spreads each
+                              level's parents over more CTA pairs. Applies from
+                              the next hpm_build_tree (the tiles are built
+                              there) */
 } hpm_tuning;
 
 /* Sets the plan's launch shapes (values outside the ranges above are

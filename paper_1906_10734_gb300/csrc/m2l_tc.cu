@@ -105,7 +105,7 @@ struct Cfg {
   static constexpr int kStageABytes = kStageChunks * kABytes;   // W of a stage, one bulk copy
   static constexpr int kHalfN = kTileN / 2;                     // parents gathered by each CTA of a pair
   static constexpr int kCols = kTileN / 2;                      // columns per drain thread (2 warps per lane quadrant)
-  static constexpr int kColGroup = kCols % 32 == 0 ? 32 : 16;   // columns per tensor-memory load of the FP32 drain
+  static constexpr int kColGroup = kCols % 32 == 0 ? 32 : (kCols % 16 == 0 ? 16 : 8);  // columns per tensor-memory load of the FP32 drain
   // accumulator buffer x at tensor-memory column kAccStride x (the second
   // buffer starts at column 256 for every width, as at 256 parents)
   static constexpr int kAccStride = NG == 4 ? 256 : kTileN;
@@ -886,7 +886,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_m2l_t
           uint32_t a[kG];
           const uint32_t ta = tbase + (uint32_t)C::kAccStride * (uint32_t)x + lane_off + half * kCols + cc * kG;
           if constexpr (kG == 32) tmem_ld32(ta, a);
-          else tmem_ld16(ta, a);
+          else if constexpr (kG == 16) tmem_ld16(ta, a);
+          else tmem_ld8(ta, a);
           tmem_wait_ld();
           if (b == 0) {
 #pragma unroll
@@ -1078,7 +1079,7 @@ hpm_status launch_m2l_tc_ng(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) 
 int m2l_tile_parents(const hpm_plan_s *pl) {
   if (pl->ng != 4) return tc::Cfg<6>::kTileN;
   const int t = pl->tuning.m2l_tile_parents;
-  return t == 224 || t == 192 ? t : 256;
+  return t == 224 || t == 208 || t == 192 ? t : 256;
 }
 
 int m2l_block_order(const hpm_plan_s *pl) {
@@ -1131,6 +1132,7 @@ hpm_status launch_m2l_tc(hpm_plan_s *pl, cudaStream_t st, int64_t *launches) {
   if (pl->ng == 6) return launch_m2l_tc_ng<6, 128>(pl, st, launches);
   switch (pl->tc_tile_n) {  // the width the tiles were built with
     case 224: return launch_m2l_tc_ng<4, 224>(pl, st, launches);
+    case 208: return launch_m2l_tc_ng<4, 208>(pl, st, launches);
     case 192: return launch_m2l_tc_ng<4, 192>(pl, st, launches);
     default: return launch_m2l_tc_ng<4, 256>(pl, st, launches);
   }

@@ -16,7 +16,7 @@ bool valid_tuning(const hpm_tuning &t) {
          (t.gridlet_warps == 0 || t.gridlet_warps == 2 || t.gridlet_warps == 4 || t.gridlet_warps == 8) &&
          t.m2l_ctas_per_sm >= 0 && t.m2l_ctas_per_sm <= 2 && t.m2l_block_order >= 0 && t.m2l_block_order <= 2 &&
          (t.m2l_tile_parents == 0 || t.m2l_tile_parents == 256 || t.m2l_tile_parents == 224 ||
-          t.m2l_tile_parents == 192);
+          t.m2l_tile_parents == 208 || t.m2l_tile_parents == 192);
 }
 
 // One build + solve; the device time of the stages `stage` selects (0 tree,
@@ -116,7 +116,7 @@ hpm_status hpm_tune(hpm_plan_t plan, const double *d_pos, const double *d_mass, 
     }
     if (s == HPM_OK && use_tc_m2l(plan) && plan->ng == 4) {
       if (t.m2l_tile_parents == 0) t.m2l_tile_parents = 256;
-      s = tune_knob(plan, &t.m2l_tile_parents, {256, 224, 192}, d_pos, d_mass, n, st, phi.as<float>(),
+      s = tune_knob(plan, &t.m2l_tile_parents, {256, 224, 208, 192}, d_pos, d_mass, n, st, phi.as<float>(),
                     acc.as<float>(), 2);
     }
     if (s == HPM_OK && !use_tc_m2l(plan) && !(plan->opts.flags & HPM_FLAG_GENERIC_M2L)) {

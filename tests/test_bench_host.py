@@ -58,6 +58,9 @@ def test_traffic_only_for_the_profiled_source():
     t = bench.profile_traffic(src)
     if t is not None:
         assert t > 1e8      # a full-size launch moves hundreds of MB
+        # per tile width where the summary has it, else the launch's figure
+        assert bench.profile_traffic(src, 256) > 1e8
+        assert bench.profile_traffic(src, 100) == t
     with tempfile.NamedTemporaryFile("w", suffix=".cu", delete=False) as f:
         f.write("// another kernel source\n")
     try:

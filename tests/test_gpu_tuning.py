@@ -41,7 +41,7 @@ def test_shapes_keep_results_tensor_path(hpm):
     ref = solve_with(hpm, w, {})
     for shapes in (dict(level_blocks_per_sm=1), dict(level_blocks_per_sm=3), dict(level_blocks_per_sm=4),
                    dict(gridlet_warps=2), dict(gridlet_warps=4), dict(m2l_block_order=2),
-                   dict(m2l_tile_parents=224), dict(m2l_tile_parents=192),
+                   dict(m2l_tile_parents=224), dict(m2l_tile_parents=208), dict(m2l_tile_parents=192),
                    dict(m2l_tile_parents=224, m2l_block_order=2)):
         assert_same(solve_with(hpm, w, shapes), ref)
     # Ng = 6 runs on the dense tensor-core path too
@@ -55,7 +55,7 @@ def test_tile_widths_keep_results_over_many_tiles(hpm):
     sums are the same bit for bit."""
     w = I.small_plummer(1 << 18, 65, leaf_max=32)
     ref = solve_with(hpm, w, dict(m2l_tile_parents=256))
-    for tn in (224, 192):
+    for tn in (224, 208, 192):
         assert_same(solve_with(hpm, w, dict(m2l_tile_parents=tn)), ref)
         assert_same(solve_with(hpm, w, dict(m2l_tile_parents=tn, m2l_block_order=2)), ref)
 
@@ -78,7 +78,7 @@ def test_tune_picks_valid_shapes_and_keeps_results(hpm):
     assert t["level_blocks_per_sm"] in (1, 2, 3, 4)
     assert t["gridlet_warps"] in (2, 4, 8)
     assert t["m2l_block_order"] in (1, 2)
-    assert t["m2l_tile_parents"] in (256, 224, 192)
+    assert t["m2l_tile_parents"] in (256, 224, 208, 192)
     assert hpm.hpm_get_tuning(s.plan) == t
     phi, acc = s(p, m)
     torch.cuda.synchronize()
