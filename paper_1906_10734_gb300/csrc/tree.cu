@@ -177,7 +177,7 @@ __global__ void k_roots(int nprob, int64_t n, int depth, int leaf_max, const int
 // from cb + off[q - pb] on, with their keys, ranges, parent and flags.
 __device__ void fill_children_of(int64_t q, int64_t pb, int64_t cb, int level, int depth, int leaf_max,
                                  uint8_t *flags, uint64_t *key, int *beg, int *end, int *parent, int *child,
-                                 const int *bnds, const int *off, int *counters) {
+                                 const int *bnds, const int *off, int &nreal_sum, int &nleaf_sum) {
   int bnd[9];
   const uint64_t kq = key[q];
 #pragma unroll
@@ -204,8 +204,8 @@ __device__ void fill_children_of(int64_t q, int64_t pb, int64_t cb, int level, i
       child[q * 8 + o] = -1;
     }
   }
-  if (nreal) atomicAdd(&counters[level], nreal);
-  if (nleaf) atomicAdd(&counters[32 + level], nleaf);
+  nreal_sum += nreal;
+  nleaf_sum += nleaf;
 }
 
 // 27-neighbour list of box i at `level` into q (-1 where absent): the
@@ -485,15 +485,26 @@ __global__ void __launch_bounds__(kThreads) k_levels(LevelArgs a) {
       return;
     }
     if (blockIdx.x == 0 && tid == 0) a.lvl[l + 1] = ne;
-    for (int64_t bi = r0 + tid; bi < r1; bi += kThreads) {
-      const int64_t q = pb + bi;
-      if (!(a.flags[q] & kExpand)) {
+    {
+      // the level's cells and leaves, counted per warp (one atomic each, not
+      // one per box on the same two words)
+      int nreal = 0, nleaf = 0;
+      for (int64_t bi = r0 + tid; bi < r1; bi += kThreads) {
+        const int64_t q = pb + bi;
+        if (!(a.flags[q] & kExpand)) {
 #pragma unroll
-        for (int o = 0; o < 8; ++o) a.child[q * 8 + o] = -1;
-        continue;
+          for (int o = 0; o < 8; ++o) a.child[q * 8 + o] = -1;
+          continue;
+        }
+        fill_children_of(q, pb, pe + base, l, a.depth, a.leaf_max, a.flags, a.key, a.beg, a.end, a.parent,
+                         a.child, a.bnd, a.off, nreal, nleaf);
       }
-      fill_children_of(q, pb, pe + base, l, a.depth, a.leaf_max, a.flags, a.key, a.beg, a.end, a.parent, a.child,
-                       a.bnd, a.off, a.counters);
+      nreal = __reduce_add_sync(0xffffffffu, nreal);
+      nleaf = __reduce_add_sync(0xffffffffu, nleaf);
+      if (lane == 0) {
+        if (nreal) atomicAdd(&a.counters[l], nreal);
+        if (nleaf) atomicAdd(&a.counters[32 + l], nleaf);
+      }
     }
     if (total == 0) {
       // level l is empty, and so is every deeper one (every block sees the same total)
@@ -701,18 +712,36 @@ __global__ void k_leaf_work(int64_t nleaf, const int *__restrict__ leaf_box, con
       if (items < 1) items = 1;
     }
   }
+  // a split leaf's partial sums: items x nt of them, placed by an atomic
+  // counter (each leaf reads back only its own), one atomic per warp; the
+  // same for the lists of split leaves
+  const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+  const bool by_src = l < nleaf && nt <= kP2PSplitTargets && items > 1;
+  const int want = by_src ? (int)(items * nt) : 0;
+  int inc = want;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  int pbase = 0;
+  if (lane == 31 && inc) pbase = atomicAdd(npart, inc);
+  pbase = __shfl_sync(0xffffffffu, pbase, 31);
+  const bool is_big = by_src && items > kP2PCombineWarp, is_split = by_src && !is_big;
+  const unsigned mb = __ballot_sync(0xffffffffu, is_big), ms = __ballot_sync(0xffffffffu, is_split);
+  int bb = 0, sb = 0;
+  if (lane == 0) {
+    if (mb) bb = atomicAdd(nbig, __popc(mb));
+    if (ms) sb = atomicAdd(nsplit, __popc(ms));
+  }
+  bb = __shfl_sync(0xffffffffu, bb, 0);
+  sb = __shfl_sync(0xffffffffu, sb, 0);
   if (l >= nleaf) return;
   nsrc[l] = (int)ns;
   nitem[l] = (int)items;
-  if (nt > kP2PSplitTargets) {
-    part0[l] = 0;
-    return;
-  }
-  // a split leaf's partial sums: items x nt of them, placed by an atomic
-  // counter (each leaf reads back only its own)
-  part0[l] = items > 1 ? atomicAdd(npart, (int)(items * nt)) : 0;
-  if (items > kP2PCombineWarp) big[atomicAdd(nbig, 1)] = (int)l;
-  else if (items > 1) split[atomicAdd(nsplit, 1)] = (int)l;
+  part0[l] = by_src ? pbase + inc - want : 0;
+  if (is_big) big[bb + __popc(mb & lt)] = (int)l;
+  if (is_split) split[sb + __popc(ms & lt)] = (int)l;
 }
 
 // The items of each leaf (k_leaf_work's counts and near-source totals).
