@@ -309,8 +309,11 @@ hpm_status hpm_solve(hpm_plan_t plan, const double *d_pos, const double *d_mass,
 static hpm_status take_solve_error(hpm_plan_t plan, cudaStream_t st) {
   if (!plan->t.err.p) return HPM_OK;
   int e = 0;
-  HPM_CUDA(cudaMemcpyAsync(&e, plan->t.err.as<int>() + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  // through the plan's pinned read-back buffer where the build allocated it
+  int *he = plan->h_pin ? reinterpret_cast<int *>(plan->h_pin + 768) : &e;
+  HPM_CUDA(cudaMemcpyAsync(he, plan->t.err.as<int>() + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
   HPM_CUDA(cudaStreamSynchronize(st));
+  e = *he;
   if (!(e & hpm::kErrTimeout)) return HPM_OK;
   HPM_CUDA(cudaMemsetAsync(plan->t.err.as<int>() + 1, 0, sizeof(int), st));
   HPM_CUDA(cudaStreamSynchronize(st));
@@ -527,6 +530,7 @@ hpm_status hpm_destroy(hpm_plan_t plan) {
   for (auto &ev : plan->io_ev)
     if (ev) cudaEventDestroy(ev);
   if (plan->io_stream) cudaStreamDestroy(plan->io_stream);
+  if (plan->h_pin) cudaFreeHost(plan->h_pin);
   cudaGetLastError();
   delete plan;
   return HPM_OK;

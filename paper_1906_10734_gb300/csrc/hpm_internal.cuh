@@ -233,6 +233,9 @@ struct hpm_plan_s {
   int test_stall = 0;              // failure test hook (hpm_test_stall)
   long long test_wait_limit = 0;   // cycles per bounded wait in that test (0 = default)
   cudaEvent_t ev[12] = {};  // stage boundaries 0..7, tree 8..9, dense product kernel 10..11
+  // pinned host memory for the tree build's small read-backs (copies into
+  // pageable memory would each wait for their own round trip)
+  unsigned char *h_pin = nullptr;
   bool events_ready = false;
   hpm::DevBuf host_io_pos, host_io_mass, host_io_phi, host_io_acc;
   // hpm_solve_host: the masses' host-to-device copy runs on a stream of its

@@ -826,6 +826,15 @@ hpm_status launch_morton_keys(const hpm_domain &dom, int depth, const double *d_
   return HPM_OK;
 }
 
+// The plan's pinned read-back buffer (kPinBytes), allocated at its first build
+// (bytes 768.. hold the solve's error word read by the host entry points).
+constexpr size_t kPinBytes = 1024;
+static hpm_status pinned(hpm_plan_s *pl, unsigned char **out) {
+  if (!pl->h_pin) HPM_CUDA(cudaMallocHost(reinterpret_cast<void **>(&pl->h_pin), kPinBytes));
+  *out = pl->h_pin;
+  return HPM_OK;
+}
+
 hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int64_t *h_offsets, int nprob,
                       cudaStream_t st) {
   TreeDev &t = pl->t;
@@ -902,10 +911,13 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     HPM_TRY(exclusive_scan_i32(t.cnt.as<int>(), t.off.as<int>(), nprob, t.counters.as<int>() + 64, t.scan, st,
                                &launches));
   // one problem with n > 0 particles has one root; a batch reads its count back
+  unsigned char *hp = nullptr;
+  HPM_TRY(pinned(pl, &hp));
   int nroot = 1;
   if (nprob > 1) {
-    HPM_CUDA(cudaMemcpyAsync(&nroot, t.counters.as<int>() + 64, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaMemcpyAsync(hp, t.counters.as<int>() + 64, sizeof(int), cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaStreamSynchronize(st));
+    memcpy(&nroot, hp, sizeof(int));
   }
   // Box capacity: grow-only across builds; the first build guesses n / 4 + 1024
   // (trees here hold 0.14-0.19 n boxes) and retries with more if it overflows.
@@ -982,11 +994,17 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
       HPM_LAUNCHED(&launches);
       HPM_CUDA(cudaEventRecord(last, st));
     }
+    // level offsets at 0 (at most 8 (kMaxDepth + 2) bytes), the error word
+    // at 256, the per-level counts at 512 of the pinned buffer
+    static_assert(8 * (kMaxDepth + 2) <= 256 && 512 + sizeof(int) * 64 <= kPinBytes, "read-back layout");
     int herr = 0;
-    HPM_CUDA(cudaMemcpyAsync(pl->lvl_off.data(), lvl, sizeof(int64_t) * (D + 2), cudaMemcpyDeviceToHost, st));
-    HPM_CUDA(cudaMemcpyAsync(&herr, t.err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
-    HPM_CUDA(cudaMemcpyAsync(hc, t.counters.p, sizeof(int) * 64, cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaMemcpyAsync(hp, lvl, sizeof(int64_t) * (D + 2), cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaMemcpyAsync(hp + 256, t.err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaMemcpyAsync(hp + 512, t.counters.p, sizeof(int) * 64, cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaStreamSynchronize(st));
+    memcpy(pl->lvl_off.data(), hp, sizeof(int64_t) * (D + 2));
+    memcpy(&herr, hp + 256, sizeof(int));
+    memcpy(hc, hp + 512, sizeof(int) * 64);
     if (herr & kErrDomain) return HPM_ERR_OUT_OF_DOMAIN;
     if (herr & kErrTimeout) return HPM_ERR_TIMEOUT;
     if (!(herr & kErrCapacity)) break;
@@ -1110,9 +1128,11 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
     HPM_TRY(exclusive_scan_i32(t.leaf_nitem.as<int>(), t.leaf_item0.as<int>(), nl, t.counters.as<int>() + 80,
                                t.scan, st, &launches));
     int hv[17] = {0}, herr2[2] = {0, 0};
-    HPM_CUDA(cudaMemcpyAsync(hv, t.counters.as<int>() + 64, sizeof(int) * 17, cudaMemcpyDeviceToHost, st));
-    HPM_CUDA(cudaMemcpyAsync(herr2, t.err.as<int>(), sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaMemcpyAsync(hp, t.counters.as<int>() + 64, sizeof(int) * 17, cudaMemcpyDeviceToHost, st));
+    HPM_CUDA(cudaMemcpyAsync(hp + 256, t.err.as<int>(), sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
     HPM_CUDA(cudaStreamSynchronize(st));
+    memcpy(hv, hp, sizeof(int) * 17);
+    memcpy(herr2, hp + 256, sizeof(int) * 2);
     if (herr2[1] & kErrTimeout) {
       // a bounded wait of an earlier solve on this plan ran out: report it once
       HPM_CUDA(cudaMemsetAsync(t.err.as<int>() + 1, 0, sizeof(int), st));
