@@ -306,18 +306,34 @@ hpm_status hpm_solve(hpm_plan_t plan, const double *d_pos, const double *d_mass,
 
 // The solves' error word (a bounded device wait that ran out): read after the
 // stream has drained, cleared once reported.
-static hpm_status take_solve_error(hpm_plan_t plan, cudaStream_t st) {
-  if (!plan->t.err.p) return HPM_OK;
-  int e = 0;
-  // through the plan's pinned read-back buffer where the build allocated it
-  int *he = plan->h_pin ? reinterpret_cast<int *>(plan->h_pin + 768) : &e;
-  HPM_CUDA(cudaMemcpyAsync(he, plan->t.err.as<int>() + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-  HPM_CUDA(cudaStreamSynchronize(st));
-  e = *he;
+// The solve's error word: its copy to the host is enqueued on `st` (through
+// the plan's pinned read-back buffer where the build allocated it), read after
+// the caller's synchronisation; a timeout is reported once and cleared.
+static int *enqueue_solve_error(hpm_plan_t plan, cudaStream_t st, int *local, hpm_status *s) {
+  *local = 0;
+  *s = HPM_OK;
+  if (!plan->t.err.p) return local;
+  int *he = plan->h_pin ? reinterpret_cast<int *>(plan->h_pin + 768) : local;
+  const cudaError_t e = cudaMemcpyAsync(he, plan->t.err.as<int>() + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) {
+    hpm::set_cuda_error(e);
+    *s = HPM_ERR_CUDA;
+  }
+  return he;
+}
+static hpm_status solve_error_status(hpm_plan_t plan, int e, cudaStream_t st) {
   if (!(e & hpm::kErrTimeout)) return HPM_OK;
   HPM_CUDA(cudaMemsetAsync(plan->t.err.as<int>() + 1, 0, sizeof(int), st));
   HPM_CUDA(cudaStreamSynchronize(st));
   return HPM_ERR_TIMEOUT;
+}
+static hpm_status take_solve_error(hpm_plan_t plan, cudaStream_t st) {
+  int local = 0;
+  hpm_status s = HPM_OK;
+  const int *he = enqueue_solve_error(plan, st, &local, &s);
+  HPM_TRY(s);
+  HPM_CUDA(cudaStreamSynchronize(st));
+  return solve_error_status(plan, *he, st);
 }
 
 hpm_status hpm_solve_host(hpm_plan_t plan, const double *h_pos, const double *h_mass, int64_t n, float *h_phi,
@@ -363,8 +379,13 @@ hpm_status hpm_solve_host(hpm_plan_t plan, const double *h_pos, const double *h_
     HPM_CUDA(cudaMemcpyAsync(h_phi, plan->host_io_phi.p, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
   if (n > 0 && h_acc)
     HPM_CUDA(cudaMemcpyAsync(h_acc, plan->host_io_acc.p, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, st));
+  // the error word rides on the same synchronisation as the results
+  int local = 0;
+  hpm_status es = HPM_OK;
+  const int *he = enqueue_solve_error(plan, st, &local, &es);
   HPM_CUDA(cudaStreamSynchronize(st));
-  return take_solve_error(plan, st);
+  HPM_TRY(es);
+  return solve_error_status(plan, *he, st);
 }
 
 hpm_status hpm_get_lists_info(hpm_plan_t plan, hpm_lists_info *info) {
