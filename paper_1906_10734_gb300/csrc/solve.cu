@@ -50,6 +50,31 @@ __device__ __forceinline__ int level_of(const LevelTable &lt, int64_t box) {
 }
 
 // ---------------------------------------------------------------------------
+// IEEE 754 conversions between binary32 and binary64 by bit manipulation on
+// the integer units (the FP64 pipe of this GPU issues about 2 operations per
+// SM-cycle, conversions included): float -> double is exact, the exponent
+// re-biased by 1023 - 127 = 896 and the 23-bit fraction shifted up by 29;
+// double -> float rounds to nearest, ties to even, on the 29 dropped fraction
+// bits (a carry out of the fraction steps the exponent, which is the IEEE
+// result, up to infinity). Zeros are signed zeros; subnormals, infinities,
+// NaNs and doubles outside the float normal range take the hardware
+// conversion. Both give the hardware's bits.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned b = __float_as_uint(f), a = b & 0x7FFFFFFFu;
+  if (a - 0x00800000u >= 0x7F000000u) return a ? (double)f : __hiloint2double((int)(b & 0x80000000u), 0);
+  return __hiloint2double((int)((b & 0x80000000u) | ((a >> 3) + 0x38000000u)), (int)(b << 29));
+}
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned ha = hi & 0x7FFFFFFFu;
+  // biased double exponent 897 .. 1150: the float normal range
+  if (ha - 0x38100000u >= 0x0FE00000u) return (ha | lo) ? (float)x : __uint_as_float(hi & 0x80000000u);
+  unsigned r = ((ha - 0x38000000u) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1FFFFFFFu;
+  r += (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ? 1u : 0u;
+  return __uint_as_float((hi & 0x80000000u) | r);
+}
+
 template <bool kUnit>
 __global__ void k_gather(int64_t n, const uint32_t *__restrict__ perm, const double *__restrict__ pos,
                          const double *__restrict__ mass, double ox, double oy, double oz, double inv_side,
@@ -66,9 +91,12 @@ __global__ void k_gather(int64_t n, const uint32_t *__restrict__ perm, const dou
   // per axis on this GPU's narrow FP64 pipe)
   const double ux = kUnit ? x : (x - ox) * inv_side, uy = kUnit ? y : (y - oy) * inv_side,
                uz = kUnit ? z : (z - oz) * inv_side;
-  const float hx = (float)ux, hy = (float)uy, hz = (float)uz;
-  hi[i] = make_float4(hx, hy, hz, (float)mass[p]);
-  lo[i] = make_float4((float)(ux - (double)hx), (float)(uy - (double)hy), (float)(uz - (double)hz), 0.f);
+  // (the conversions on the integer units: this kernel is otherwise bound by
+  // the FP64 pipe's conversions)
+  const float hx = f64_to_f32_rn(ux), hy = f64_to_f32_rn(uy), hz = f64_to_f32_rn(uz);
+  hi[i] = make_float4(hx, hy, hz, f64_to_f32_rn(mass[p]));
+  lo[i] = make_float4(f64_to_f32_rn(ux - f32_to_f64(hx)), f64_to_f32_rn(uy - f32_to_f64(hy)),
+                      f64_to_f32_rn(uz - f32_to_f64(hz)), 0.f);
 }
 
 // The same in FP64 (exact up to one FP64 rounding): the input of the
