@@ -498,6 +498,19 @@ typedef struct {
 } hpm_alu_peaks;
 hpm_status hpm_measure_alu_peaks(hpm_alu_peaks *out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Self-check of the float <-> double conversions the library does by
+ * IEEE 754 bit manipulation on the integer units (in the gather of the
+ * sorted particles: exact float -> double; double -> float rounded to
+ * nearest, ties to even): converts the n_d doubles at d_in and the n_f
+ * floats at f_in (device memory, either may be empty) both ways, its own and
+ * the hardware's, and returns in *mismatches the number of inputs whose
+ * results differ in any bit (NaNs compared by class). Synchronises `stream`.
+ * Errors: HPM_ERR_INVALID_ARG, HPM_ERR_CUDA, HPM_ERR_OOM.
+ * ------------------------------------------------------------------------ */
+hpm_status hpm_check_conversions(const double *d_in, int64_t n_d, const float *f_in, int64_t n_f,
+                                 int64_t *mismatches, void *stream);
+
 /* Frees the plan and everything it owns. NULL is allowed. */
 hpm_status hpm_destroy(hpm_plan_t plan);
 

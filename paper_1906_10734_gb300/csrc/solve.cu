@@ -75,6 +75,23 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
   return __uint_as_float((hi & 0x80000000u) | r);
 }
 
+// Self-check of the two conversions against the hardware's (NaNs compare by
+// class): the number of inputs whose bits differ.
+__global__ void k_check_conversions(const double *__restrict__ d, int64_t nd, const float *__restrict__ f,
+                                    int64_t nf, unsigned long long *__restrict__ bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned c = 0;
+  if (i < nd) {
+    const float a = f64_to_f32_rn(d[i]), h = (float)d[i];
+    c += (__float_as_uint(a) != __float_as_uint(h)) && !(isnan(a) && isnan(h));
+  }
+  if (i < nf) {
+    const double a = f32_to_f64(f[i]), h = (double)f[i];
+    c += (__double_as_longlong(a) != __double_as_longlong(h)) && !(isnan(a) && isnan(h));
+  }
+  if (c) atomicAdd(bad, (unsigned long long)c);
+}
+
 template <bool kUnit>
 __global__ void k_gather(int64_t n, const uint32_t *__restrict__ perm, const double *__restrict__ pos,
                          const double *__restrict__ mass, double ox, double oy, double oz, double inv_side,
@@ -1587,3 +1604,30 @@ hpm_status solve(hpm_plan_s *pl, const double *d_pos, const double *d_mass, floa
 }
 
 }  // namespace hpm
+
+extern "C" hpm_status hpm_check_conversions(const double *d_in, int64_t n_d, const float *f_in, int64_t n_f,
+                                            int64_t *mismatches, void *stream) {
+  if (!mismatches || n_d < 0 || n_f < 0 || (n_d > 0 && !d_in) || (n_f > 0 && !f_in)) return HPM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  hpm::DevBuf cnt;
+  HPM_TRY(cnt.ensure(sizeof(unsigned long long), st));
+  hpm_status s = HPM_OK;
+  cudaError_t e = cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), st);
+  const int64_t n = std::max(n_d, n_f);
+  if (e == cudaSuccess && n > 0) {
+    hpm::k_check_conversions<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_in, n_d, f_in, n_f,
+                                                                          cnt.as<unsigned long long>());
+    e = cudaGetLastError();
+  }
+  unsigned long long h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, cnt.p, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    hpm::set_cuda_error(e);
+    s = HPM_ERR_CUDA;
+  }
+  cnt.release(st);
+  cudaStreamSynchronize(st);
+  *mismatches = (int64_t)h;
+  return s;
+}

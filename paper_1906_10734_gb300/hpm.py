@@ -162,6 +162,7 @@ SIGNATURES = {
     "hpm_tune": ([_vp, _vp, _vp, _i64, _vp, ctypes.POINTER(hpm_tuning)], _i32),
     "hpm_test_stall": ([_vp, _i32, ctypes.c_longlong], _i32),
     "hpm_measure_alu_peaks": ([ctypes.POINTER(hpm_alu_peaks), _vp], _i32),
+    "hpm_check_conversions": ([_vp, _i64, _vp, _i64, ctypes.POINTER(ctypes.c_int64), _vp], _i32),
     "hpm_destroy": ([_vp], _i32),
     "hpm_status_str": ([_i32], ctypes.c_char_p),
     "hpm_last_cuda_error": ([], ctypes.c_char_p),
@@ -479,3 +480,12 @@ def hpm_measure_alu_peaks(stream=None) -> dict:
     out = hpm_alu_peaks()
     _check("hpm_measure_alu_peaks", load().hpm_measure_alu_peaks(ctypes.byref(out), _stream(stream)))
     return {k: getattr(out, k) for k, _ in hpm_alu_peaks._fields_}
+
+
+def hpm_check_conversions(d, f, stream=None) -> int:
+    """Bits in which the library's integer-unit float <-> double conversions differ from the
+    hardware's, over device tensors d (float64) and f (float32): the count of such inputs."""
+    out = ctypes.c_int64(0)
+    _check("hpm_check_conversions", load().hpm_check_conversions(_ptr(d), int(d.numel()), _ptr(f), int(f.numel()),
+                                                                 ctypes.byref(out), _stream(stream)))
+    return int(out.value)
