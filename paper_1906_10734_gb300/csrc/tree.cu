@@ -62,6 +62,9 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
 // the one FP64 subtraction (the same integer as the IEEE evaluation, without
 // its further FP64 instructions, of which this GPU issues few per cycle).
 constexpr int kNoPow2 = -100000;
+// kOrigin0: the domain's origin is +0 in every axis, where x - o = x exactly
+// (-0 included), so the subtraction (an FP64-pipe instruction) is skipped.
+template <bool kOrigin0>
 __global__ void k_keys(const double *__restrict__ pos, int64_t n, double ox, double oy, double oz,
                        double side, int side_exp, unsigned long long neg_zero, int depth,
                        uint64_t *__restrict__ keys,
@@ -83,7 +86,7 @@ __global__ void k_keys(const double *__restrict__ pos, int64_t n, double ox, dou
   bool bad = false;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double diff = __dsub_rn(pos[3 * i + d], o[d]);
+    const double diff = kOrigin0 ? pos[3 * i + d] : __dsub_rn(pos[3 * i + d], o[d]);
     uint32_t q = 0;
     if (side_exp != kNoPow2) {
       unsigned long long b = (unsigned long long)__double_as_longlong(diff);
@@ -817,10 +820,21 @@ static unsigned long long neg_zero_bits(int e) {
   return b;
 }
 
+// The origin is +0 in every axis (bit patterns: -0 does not qualify).
+static bool origin_is_zero(const hpm_domain &dom) {
+  for (int d = 0; d < 3; ++d) {
+    uint64_t b;
+    memcpy(&b, &dom.origin[d], sizeof(b));
+    if (b != 0) return false;
+  }
+  return true;
+}
+
 hpm_status launch_morton_keys(const hpm_domain &dom, int depth, const double *d_pos, int64_t n,
                               uint64_t *d_keys, int *d_err, cudaStream_t st) {
   if (n <= 0) return HPM_OK;
-  k_keys<<<blocks_for(n), kThreads, 0, st>>>(d_pos, n, dom.origin[0], dom.origin[1], dom.origin[2], dom.side,
+  (origin_is_zero(dom) ? k_keys<true> : k_keys<false>)<<<blocks_for(n), kThreads, 0, st>>>(
+      d_pos, n, dom.origin[0], dom.origin[1], dom.origin[2], dom.side,
                                              pow2_exponent(dom.side), neg_zero_bits(pow2_exponent(dom.side)), depth, d_keys, d_err, nullptr, 1);
   HPM_LAUNCHED((int64_t *)nullptr);
   return HPM_OK;
@@ -878,7 +892,8 @@ hpm_status build_tree(hpm_plan_s *pl, const double *d_pos, int64_t n, const int6
   HPM_TRY(t.offsets.ensure(sizeof(int64_t) * (nprob + 1), st));
   if (nprob > 1)
     HPM_CUDA(cudaMemcpyAsync(t.offsets.p, h_offsets, sizeof(int64_t) * (nprob + 1), cudaMemcpyHostToDevice, st));
-  k_keys<<<blocks_for(n), kThreads, 0, st>>>(d_pos, n, pl->dom.origin[0], pl->dom.origin[1],
+  (origin_is_zero(pl->dom) ? k_keys<true> : k_keys<false>)<<<blocks_for(n), kThreads, 0, st>>>(
+      d_pos, n, pl->dom.origin[0], pl->dom.origin[1],
                                              pl->dom.origin[2], pl->dom.side, pow2_exponent(pl->dom.side),
                                              neg_zero_bits(pow2_exponent(pl->dom.side)), D,
                                              t.keys.as<uint64_t>(),
