@@ -193,13 +193,16 @@ __device__ __forceinline__ void row_amax(int *amax, float a, const uint64_t *__r
 // those boxes, 256 pairs at a time, then warp w accumulates box w from shared
 // memory.
 template <int NG>
-__global__ void __launch_bounds__(kThreads) k_p2g(int64_t nbox, const int *__restrict__ list, LevelTable lt,
+__global__ void __launch_bounds__(kThreads, NG == 4 ? 8 : 1) k_p2g(int64_t nbox, const int *__restrict__ list, LevelTable lt,
                                                   GridletTables tb, const uint64_t *__restrict__ key,
                                                   const int *__restrict__ beg, const int *__restrict__ end,
                                                   const float4 *__restrict__ uhi,
                                                   const float4 *__restrict__ ulo, int64_t off2,
                                                   float *__restrict__ grid, int *__restrict__ amax, int nlev) {
-  __shared__ float ws[kThreads][3][kMaxNg];
+  // (weights of the block's pairs: Ng per axis; at Ng = 4 the smaller array and
+  // 32 registers let 8 blocks share an SM, whose phases of FP64 weights and of
+  // accumulation then overlap across blocks)
+  __shared__ float ws[kThreads][3][NG > 0 ? NG : kMaxNg];
   __shared__ float ms[kThreads];
   __shared__ int off[kWarpsPerBlock + 1];
   __shared__ int bx[kWarpsPerBlock], bbeg[kWarpsPerBlock], blev[kWarpsPerBlock];
