@@ -644,7 +644,7 @@ __device__ __forceinline__ void lagrange_f(const GridletTables &tb, float t, flo
 // sorted particle, FP32 throughout): phi = c + sum_p delta_p prod ell,
 // a = -(2^l / S) sum_p delta_p grad_xi prod ell (Eq. phix and its gradient).
 template <int NG>
-__global__ void __launch_bounds__(kThreads) k_g2p(int64_t n, const int *__restrict__ pbox,
+__global__ void __launch_bounds__(kThreads, NG == 4 ? 6 : 1) k_g2p(int64_t n, const int *__restrict__ pbox,
                                                   const int *__restrict__ box_tgt, LevelTable lt,
                                                   GridletTables tb, float inv_side,
                                                   const uint64_t *__restrict__ key,
