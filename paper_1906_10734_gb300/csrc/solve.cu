@@ -193,7 +193,7 @@ __device__ __forceinline__ void row_amax(int *amax, float a, const uint64_t *__r
 // those boxes, 256 pairs at a time, then warp w accumulates box w from shared
 // memory.
 template <int NG>
-__global__ void __launch_bounds__(kThreads, NG == 4 ? 8 : 1) k_p2g(int64_t nbox, const int *__restrict__ list, LevelTable lt,
+__global__ void __launch_bounds__(kThreads, NG == 4 ? 8 : 2) k_p2g(int64_t nbox, const int *__restrict__ list, LevelTable lt,
                                                   GridletTables tb, const uint64_t *__restrict__ key,
                                                   const int *__restrict__ beg, const int *__restrict__ end,
                                                   const float4 *__restrict__ uhi,
